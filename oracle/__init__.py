@@ -1,0 +1,249 @@
+"""CPU oracle of the DiFVM face-operator / PISO path -- TEST INFRASTRUCTURE.
+
+A plain, slow FP64 implementation written from the paper (arxiv 2603.15920,
+Sec. 2.3-2.6) in ``difvm_oracle.c`` and loaded here through ctypes.  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It shares no code with the CUDA library: the two meet
+only in the seeded inputs of ``paper_2603_15920_b300.meshgen``, which this
+package does not import either (callers pass plain numpy arrays).
+
+Every function works in the mesh's own (input) numbering, component-major
+fields ``[ncomp, nc]``, boundary values ``[ncomp, nb]``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "difvm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+BC_FIXED, BC_ZEROGRAD, BC_EMPTY = 0, 1, 2
+PT_WALL, PT_INLET, PT_OUTLET, PT_EMPTY = 0, 1, 2, 3
+DIV_UPWIND, DIV_LINEAR = 0, 1
+WK_EXACT, WK_FE, WK_BE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc -O2 -ffp-contract=off, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+    return _lib
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("nc", C.c_int), ("nint", C.c_int), ("nf", C.c_int), ("npatch", C.c_int),
+                ("owner", C.c_void_p), ("neighbour", C.c_void_p),
+                ("Sf", C.c_void_p), ("Cf", C.c_void_p), ("V", C.c_void_p), ("C", C.c_void_p),
+                ("patch_start", C.c_void_p), ("patch_size", C.c_void_p),
+                ("patch_type", C.c_void_p)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("res0", C.c_double), ("res", C.c_double),
+                ("bnorm", C.c_double), ("status", C.c_int)]
+
+
+class _PisoOpts(C.Structure):
+    _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("ncorr", C.c_int), ("nonorth", C.c_int),
+                ("tolU", C.c_double), ("tolp", C.c_double), ("tol_abs", C.c_double),
+                ("maxitU", C.c_int), ("maxitp", C.c_int), ("pref_cell", C.c_int),
+                ("wk_scheme", C.c_int), ("n_out", C.c_int), ("wk_patch", C.c_void_p),
+                ("Rp", C.c_void_p), ("Cw", C.c_void_p), ("Rd", C.c_void_p)]
+
+
+class _PisoInfo(C.Structure):
+    _fields_ = [("itU", C.c_int * 3), ("itp", C.c_int * 4), ("status", C.c_int),
+                ("Q", C.c_double * 8), ("po", C.c_double * 8)]
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class OMesh:
+    """Holds the oracle's view of a mesh (plain arrays, input numbering)."""
+
+    def __init__(self, n_cells, n_internal, owner, neighbour, Sf, Cf, V, Cc,
+                 patch_start, patch_size, patch_type):
+        self.keep = [_i32(owner), _i32(neighbour), _f64(Sf), _f64(Cf), _f64(V), _f64(Cc),
+                     _i32(patch_start), _i32(patch_size), _i32(patch_type)]
+        o, n, S, X, Vv, Cv, ps, pz, pt = self.keep
+        self.nc, self.nint, self.nf = int(n_cells), int(n_internal), int(o.shape[0])
+        self.nb = self.nf - self.nint
+        self.npatch = int(ps.shape[0])
+        self.patch_start, self.patch_size, self.patch_type = ps, pz, pt
+        self.s = _Mesh(self.nc, self.nint, self.nf, self.npatch, _p(o), _p(n), _p(S), _p(X),
+                       _p(Vv), _p(Cv), _p(ps), _p(pz), _p(pt))
+
+    @classmethod
+    def from_mesh(cls, m):
+        return cls(m.n_cells, m.n_internal, m.owner, m.neighbour, m.Sf, m.Cf, m.V, m.C,
+                   m.patch_start, m.patch_size, m.patch_type)
+
+    def ref(self):
+        return C.byref(self.s)
+
+    def bc_U(self):
+        return np.array([BC_EMPTY if t == PT_EMPTY else (BC_ZEROGRAD if t == PT_OUTLET else BC_FIXED)
+                         for t in self.patch_type], np.int32)
+
+    def bc_p(self):
+        return np.array([BC_EMPTY if t == PT_EMPTY else (BC_FIXED if t == PT_OUTLET else BC_ZEROGRAD)
+                         for t in self.patch_type], np.int32)
+
+
+def face_coeffs(m: OMesh):
+    w = np.zeros(m.nint + 1); c = np.zeros(m.nf + 1); k = np.zeros(3 * (m.nint + 1))
+    lib().om_face_coeffs(m.ref(), _p(w), _p(c), _p(k))
+    return w[:m.nint], c[:m.nf], k[:3 * m.nint].reshape(m.nint, 3)
+
+
+def check_geometry(m: OMesh):
+    cl = C.c_double(0)
+    bad = lib().om_check_geometry(m.ref(), _p(m.bc_U()), C.byref(cl))
+    return int(bad), float(cl.value)
+
+
+def _bcarr(bc, m):
+    return _i32(np.broadcast_to(np.asarray(bc, np.int32), (m.npatch,)))
+
+
+def grad_gauss(m: OMesh, bc, phi, phi_b=None):
+    phi = _f64(np.atleast_2d(phi)); nq = phi.shape[0]
+    pb = None if phi_b is None else _f64(np.reshape(phi_b, (nq, m.nb)))
+    out = np.zeros((nq, 3, m.nc))
+    lib().om_grad_gauss(m.ref(), _p(_bcarr(bc, m)), nq, _p(phi), _p(pb), _p(out))
+    return out
+
+
+def div_flux(m: OMesh, bc, scheme, mf, phi, phi_b=None):
+    phi = _f64(np.atleast_2d(phi)); nq = phi.shape[0]
+    pb = None if phi_b is None else _f64(np.reshape(phi_b, (nq, m.nb)))
+    out = np.zeros((nq, m.nc))
+    lib().om_div_flux(m.ref(), _p(_bcarr(bc, m)), int(scheme), nq, _p(_f64(mf)), _p(phi),
+                      _p(pb), _p(out))
+    return out
+
+
+def laplacian(m: OMesh, bc, gamma, phi, phi_b=None, grad=None):
+    phi = _f64(np.atleast_2d(phi)); nq = phi.shape[0]
+    pb = None if phi_b is None else _f64(np.reshape(phi_b, (nq, m.nb)))
+    g = None if grad is None else _f64(np.reshape(grad, (nq, 3, m.nc)))
+    out = np.zeros((nq, m.nc))
+    lib().om_laplacian(m.ref(), _p(_bcarr(bc, m)), nq, C.c_double(gamma), _p(phi), _p(pb),
+                       _p(g), _p(out))
+    return out
+
+
+def ldu_apply(m: OMesh, D, L, U, x):
+    x = _f64(np.atleast_2d(x)); nq = x.shape[0]
+    y = np.zeros_like(x)
+    lib().om_ldu_apply(m.ref(), nq, _p(_f64(D)), _p(_f64(L)),
+                       _p(None if U is None else _f64(U)), _p(x), _p(y))
+    return y
+
+
+def _solve(fn, m, D, L, U, b, x0, tol_rel, tol_abs, maxit):
+    x = _f64(np.zeros(m.nc) if x0 is None else np.array(x0, np.float64))
+    info = _Info()
+    getattr(lib(), fn)(m.ref(), _p(_f64(D)), _p(_f64(L)), _p(None if U is None else _f64(U)),
+                       _p(_f64(b)), _p(x), C.c_double(tol_rel), C.c_double(tol_abs), int(maxit),
+                       C.byref(info))
+    return x, dict(iters=info.iters, res0=info.res0, res=info.res, bnorm=info.bnorm,
+                   status=info.status)
+
+
+def pcg(m, D, L, U, b, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
+    return _solve("om_pcg", m, D, L, U, b, x0, tol_rel, tol_abs, maxit)
+
+
+def bicgstab(m, D, L, U, b, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
+    return _solve("om_bicgstab", m, D, L, U, b, x0, tol_rel, tol_abs, maxit)
+
+
+def windkessel_update(scheme, Rp, Cw, Rd, Q, dt, pc):
+    Rp, Cw, Rd, Q = (_f64(np.atleast_1d(a)) for a in (Rp, Cw, Rd, Q))
+    pc = _f64(np.array(np.atleast_1d(pc), np.float64))
+    po = np.zeros_like(pc)
+    lib().om_windkessel_update(int(pc.shape[0]), int(scheme), _p(Rp), _p(Cw), _p(Rd), _p(Q),
+                               C.c_double(dt), _p(pc), _p(po))
+    return pc, po
+
+
+def momentum_assemble(m: OMesh, nu, dt, mf, Uold, Ub, gradU=None):
+    D = np.zeros(m.nc); Lo = np.zeros(m.nint + 1); Up = np.zeros(m.nint + 1)
+    b = np.zeros((3, m.nc))
+    lib().om_momentum_assemble(m.ref(), _p(m.bc_U()), C.c_double(nu), C.c_double(dt),
+                               _p(_f64(mf)), _p(_f64(Uold)), _p(_f64(np.reshape(Ub, (3, m.nb)))),
+                               _p(None if gradU is None else _f64(gradU)), _p(D), _p(Lo), _p(Up),
+                               _p(b))
+    return D, Lo[:m.nint], Up[:m.nint], b
+
+
+def H_op(m: OMesh, Lo, Up, b, U):
+    H = np.zeros((3, m.nc))
+    lib().om_H(m.ref(), _p(_f64(Lo)), _p(_f64(Up)), _p(_f64(b)), _p(_f64(U)), _p(H))
+    return H
+
+
+def pressure_assemble(m: OMesh, rAU, HbyA, Ub, pb, gradp=None):
+    Dp = np.zeros(m.nc); Lp = np.zeros(m.nint + 1); bp = np.zeros(m.nc)
+    phiH = np.zeros(m.nf); af = np.zeros(m.nf); no = np.zeros(m.nint + 1)
+    lib().om_pressure_assemble(m.ref(), _p(m.bc_U()), _p(m.bc_p()), _p(_f64(rAU)), _p(_f64(HbyA)),
+                               _p(_f64(np.reshape(Ub, (3, m.nb)))), _p(_f64(pb)),
+                               _p(None if gradp is None else _f64(gradp)), _p(Dp), _p(Lp), _p(bp),
+                               _p(phiH), _p(af), _p(no))
+    return dict(Dp=Dp, Lp=Lp[:m.nint], bp=bp, phiHbyA=phiH, af=af, nonorth=no[:m.nint])
+
+
+def flux_from_U(m: OMesh, U, Ub):
+    phi = np.zeros(m.nf)
+    lib().om_flux_from_U(m.ref(), _p(_f64(U)), _p(_f64(np.reshape(Ub, (3, m.nb)))), _p(phi))
+    return phi
+
+
+def piso_step(m: OMesh, U, p, phi, Ub, pb, *, nu, dt, ncorr=2, nonorth=True, tolU=1e-10,
+              tolp=1e-10, tol_abs=0.0, maxitU=1000, maxitp=20000, pref_cell=0,
+              wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(), wk_scheme=WK_EXACT):
+    """One PISO step in place on copies; returns (U, p, phi, pb, pc, info)."""
+    U = _f64(np.array(U, np.float64)); p = _f64(np.array(p, np.float64))
+    phi = _f64(np.array(phi, np.float64)); pb = _f64(np.array(pb, np.float64))
+    Ub = _f64(np.reshape(Ub, (3, m.nb)))
+    wk_patch = _i32(np.atleast_1d(np.asarray(wk_patch, np.int32)))
+    Rp, Cw, Rd = (_f64(np.atleast_1d(np.asarray(a, np.float64))) for a in (Rp, Cw, Rd))
+    pc = _f64(np.array(np.atleast_1d(np.asarray(pc, np.float64))))
+    opts = _PisoOpts(nu, dt, ncorr, int(nonorth), tolU, tolp, tol_abs, maxitU, maxitp, pref_cell,
+                     wk_scheme, int(wk_patch.shape[0]), _p(wk_patch), _p(Rp), _p(Cw), _p(Rd))
+    info = _PisoInfo()
+    lib().om_piso_step(m.ref(), C.byref(opts), _p(U), _p(p), _p(phi), _p(Ub), _p(pb), _p(pc),
+                       C.byref(info))
+    n_out = int(wk_patch.shape[0])
+    return U, p, phi, pb, pc, dict(itU=list(info.itU), itp=list(info.itp)[:ncorr],
+                                   status=info.status, Q=list(info.Q)[:n_out],
+                                   po=list(info.po)[:n_out])

@@ -1,0 +1,639 @@
+/*
+ * difvm_oracle.c -- plain, slow, FP64 CPU oracle of the DiFVM face-operator /
+ * PISO path (arxiv 2603.15920, Sec. 2.3-2.6).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file's library.  It shares no
+ * code, header, constant or helper with the CUDA library; both are fed the same
+ * seeded mesh arrays and nothing else.
+ *
+ * Every operator is the textbook face loop of the paper's message-passing form
+ * (Sec. 2.4.1, Eqs. message/aggregate): visit faces in ascending face id,
+ * compute the face quantity once, add it to the owner and subtract it from the
+ * neighbour (sigma = +1 owner, -1 neighbour).  Boundary faces are edges from a
+ * ghost node: they touch only their owner.  No blocking, fusion or reordering.
+ *
+ * Conventions
+ *   mesh arrays: owner[nf], neighbour[nint], Sf/Cf [nf][3], V[nc], C[nc][3];
+ *                boundary faces nint..nf-1 grouped by patch.
+ *   fields:      component-major, phi[c*nc + i]; boundary values
+ *                phib[c*nb + (f - nint)].
+ *   bc[patch]:   0 fixed value (use phib), 1 zero gradient (use the owner
+ *                value), 2 empty (face excluded from every sum).
+ *   gradient:    grad[(c*3 + d)*nc + i] = d phi_c / d x_d.
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   w_f  = S.(C_N - x_f) / S.(C_N - C_O)   owner weight of linear interpolation
+ *   c_f  = |S|^2 / (S.d)                   |Delta_f|/|d| for the over-relaxed
+ *                                          split Delta = (|S|/|S^.d^|) d^ (Eq. nonortho_flux)
+ *   k_f  = S - c_f d                        non-orthogonal remainder
+ *   boundary diffusion is orthogonal only, d = x_f - C_O.
+ *   a boundary face carries its boundary-condition value for every scheme.
+ *
+ * Parity pins: see tests/test_oracle_*.py (closed forms, invariants, dense
+ * solves, the manufactured Poisson solution of Sec. 3.1.1).
+ * Parity unpinned: the interpolation weight on non-uniform meshes (w_f above
+ * is a reading; every choice gives 0.5 on the uniform hex meshes that pin it).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  int nc, nint, nf, npatch;
+  const int *owner, *neighbour;
+  const double *Sf, *Cf, *V, *C;
+  const int *patch_start, *patch_size, *patch_type;
+} om_mesh;
+
+enum { BC_FIXED = 0, BC_ZEROGRAD = 1, BC_EMPTY = 2 };
+enum { PT_WALL = 0, PT_INLET = 1, PT_OUTLET = 2, PT_EMPTY = 3 };
+enum { DIV_UPWIND = 0, DIV_LINEAR = 1 };
+enum { WK_EXACT = 0, WK_FE = 1, WK_BE = 2 };
+
+static double dot3(const double *a, const double *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static int patch_of_face(const om_mesh *m, int f) {
+  for (int p = 0; p < m->npatch; ++p)
+    if (f >= m->patch_start[p] && f < m->patch_start[p] + m->patch_size[p]) return p;
+  return -1;
+}
+
+/* bc kind of the velocity / pressure fields implied by a patch type */
+static int bc_of_U(int pt) { return pt == PT_EMPTY ? BC_EMPTY : (pt == PT_OUTLET ? BC_ZEROGRAD : BC_FIXED); }
+static int bc_of_p(int pt) { return pt == PT_EMPTY ? BC_EMPTY : (pt == PT_OUTLET ? BC_FIXED : BC_ZEROGRAD); }
+
+/* ---------------------------------------------------------------- geometry */
+/* Derived face coefficients (Sec. 2.3.2): w[nint], c[nf], k[nint*3]. */
+void om_face_coeffs(const om_mesh *m, double *w, double *c, double *k) {
+  for (int f = 0; f < m->nf; ++f) {
+    const double *S = m->Sf + 3 * f, *xf = m->Cf + 3 * f, *CO = m->C + 3 * m->owner[f];
+    double d[3];
+    if (f < m->nint) {
+      const double *CN = m->C + 3 * m->neighbour[f];
+      double dN[3] = {CN[0] - xf[0], CN[1] - xf[1], CN[2] - xf[2]};
+      for (int a = 0; a < 3; ++a) d[a] = CN[a] - CO[a];
+      w[f] = dot3(S, dN) / dot3(S, d);
+      c[f] = dot3(S, S) / dot3(S, d);
+      for (int a = 0; a < 3; ++a) k[3 * f + a] = S[a] - c[f] * d[a];
+    } else {
+      for (int a = 0; a < 3; ++a) d[a] = xf[a] - CO[a];
+      c[f] = dot3(S, S) / dot3(S, d);
+    }
+  }
+}
+
+/* Geometry checks: V > 0, S.d > 0 on every face, and the closure residual
+ * max_i |sum sigma S_f| / (sum |S_f|) over cells with no empty faces.
+ * Returns the number of violations; *closure gets the worst residual. */
+int om_check_geometry(const om_mesh *m, const int *bcU, double *closure) {
+  int bad = 0;
+  double *r = calloc((size_t)m->nc * 3, sizeof(double));
+  double *a = calloc((size_t)m->nc, sizeof(double));
+  char *hasempty = calloc((size_t)m->nc, 1);
+  for (int i = 0; i < m->nc; ++i) bad += !(m->V[i] > 0);
+  for (int f = 0; f < m->nf; ++f) {
+    const double *S = m->Sf + 3 * f, *CO = m->C + 3 * m->owner[f];
+    double d[3];
+    int O = m->owner[f];
+    if (f < m->nint) {
+      int N = m->neighbour[f];
+      for (int q = 0; q < 3; ++q) d[q] = m->C[3 * N + q] - CO[q];
+      for (int q = 0; q < 3; ++q) { r[3 * O + q] += S[q]; r[3 * N + q] -= S[q]; }
+      a[O] += sqrt(dot3(S, S)); a[N] += sqrt(dot3(S, S));
+    } else {
+      for (int q = 0; q < 3; ++q) d[q] = m->Cf[3 * f + q] - CO[q];
+      for (int q = 0; q < 3; ++q) r[3 * O + q] += S[q];
+      a[O] += sqrt(dot3(S, S));
+      if (bcU && bcU[patch_of_face(m, f)] == BC_EMPTY) hasempty[O] = 1;
+    }
+    bad += !(dot3(S, d) > 0);
+  }
+  double worst = 0;
+  for (int i = 0; i < m->nc; ++i) {
+    if (hasempty[i]) continue;
+    double e = sqrt(dot3(r + 3 * i, r + 3 * i)) / a[i];
+    if (e > worst) worst = e;
+  }
+  *closure = worst;
+  free(r); free(a); free(hasempty);
+  return bad;
+}
+
+/* ------------------------------------------------------- face interpolation */
+/* Face value of component `comp` on face f (Sec. 2.3.2, linear interpolation;
+ * boundary faces take their boundary-condition value).  Returns 0 if the face
+ * is empty (excluded), 1 otherwise. */
+static int face_value(const om_mesh *m, const double *w, const int *bc, const double *phi,
+                      const double *phib, int f, double *out) {
+  int O = m->owner[f];
+  if (f < m->nint) {
+    int N = m->neighbour[f];
+    *out = w[f] * phi[O] + (1.0 - w[f]) * phi[N];
+    return 1;
+  }
+  int kind = bc[patch_of_face(m, f)];
+  if (kind == BC_EMPTY) return 0;
+  *out = (kind == BC_FIXED) ? phib[f - m->nint] : phi[O];
+  return 1;
+}
+
+/* -------------------------------------------------------------- Gauss grad */
+/* (grad phi)_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green) */
+void om_grad_gauss(const om_mesh *m, const int *bc, int ncomp, const double *phi,
+                   const double *phib, double *grad) {
+  int nc = m->nc, nb = m->nf - m->nint;
+  double *w = malloc(sizeof(double) * (m->nint + 1));
+  double *c = malloc(sizeof(double) * (m->nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (m->nint + 1));
+  om_face_coeffs(m, w, c, k);
+  memset(grad, 0, sizeof(double) * (size_t)ncomp * 3 * nc);
+  for (int q = 0; q < ncomp; ++q) {
+    const double *ph = phi + (size_t)q * nc, *pb = phib ? phib + (size_t)q * nb : NULL;
+    double *g = grad + (size_t)q * 3 * nc;
+    for (int f = 0; f < m->nf; ++f) {
+      double pf;
+      if (!face_value(m, w, bc, ph, pb, f, &pf)) continue;
+      const double *S = m->Sf + 3 * f;
+      int O = m->owner[f];
+      for (int d = 0; d < 3; ++d) g[d * nc + O] += pf * S[d];
+      if (f < m->nint) {
+        int N = m->neighbour[f];
+        for (int d = 0; d < 3; ++d) g[d * nc + N] -= pf * S[d];
+      }
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < nc; ++i) g[d * nc + i] /= m->V[i];
+  }
+  free(w); free(c); free(k);
+}
+
+/* ------------------------------------------------------------- convection */
+/* R_i = sum_f sigma m_f phi_f   (Eq. conv_face_flux; upwind Eq. upwind with
+ * m_f >= 0 taking the owner value; linear = central interpolation) */
+void om_div_flux(const om_mesh *m, const int *bc, int scheme, int ncomp, const double *mf,
+                 const double *phi, const double *phib, double *out) {
+  int nc = m->nc, nb = m->nf - m->nint;
+  double *w = malloc(sizeof(double) * (m->nint + 1));
+  double *c = malloc(sizeof(double) * (m->nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (m->nint + 1));
+  om_face_coeffs(m, w, c, k);
+  memset(out, 0, sizeof(double) * (size_t)ncomp * nc);
+  for (int q = 0; q < ncomp; ++q) {
+    const double *ph = phi + (size_t)q * nc, *pb = phib ? phib + (size_t)q * nb : NULL;
+    double *r = out + (size_t)q * nc;
+    for (int f = 0; f < m->nf; ++f) {
+      double pf;
+      int O = m->owner[f];
+      if (f < m->nint) {
+        int N = m->neighbour[f];
+        if (scheme == DIV_UPWIND) pf = (mf[f] >= 0.0) ? ph[O] : ph[N];
+        else pf = w[f] * ph[O] + (1.0 - w[f]) * ph[N];
+        r[O] += mf[f] * pf;
+        r[N] -= mf[f] * pf;
+      } else {
+        if (!face_value(m, w, bc, ph, pb, f, &pf)) continue;
+        r[O] += mf[f] * pf;
+      }
+    }
+  }
+  free(w); free(c); free(k);
+}
+
+/* -------------------------------------------------------------- diffusion */
+/* R_i = sum_f sigma gamma [ c_f (phi_N - phi_O) + (grad phi)_f . k_f ]
+ * (Eq. nonortho_flux, over-relaxed), boundary fixed value: gamma c_f (phi_b - phi_O),
+ * zero gradient and empty: 0.  grad == NULL gives the orthogonal part only. */
+void om_laplacian(const om_mesh *m, const int *bc, int ncomp, double gamma, const double *phi,
+                  const double *phib, const double *grad, double *out) {
+  int nc = m->nc, nb = m->nf - m->nint;
+  double *w = malloc(sizeof(double) * (m->nint + 1));
+  double *c = malloc(sizeof(double) * (m->nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (m->nint + 1));
+  om_face_coeffs(m, w, c, k);
+  memset(out, 0, sizeof(double) * (size_t)ncomp * nc);
+  for (int q = 0; q < ncomp; ++q) {
+    const double *ph = phi + (size_t)q * nc, *pb = phib ? phib + (size_t)q * nb : NULL;
+    const double *g = grad ? grad + (size_t)q * 3 * nc : NULL;
+    double *r = out + (size_t)q * nc;
+    for (int f = 0; f < m->nf; ++f) {
+      int O = m->owner[f];
+      if (f < m->nint) {
+        int N = m->neighbour[f];
+        double F = gamma * c[f] * (ph[N] - ph[O]);
+        if (g) {
+          double gf[3];
+          for (int d = 0; d < 3; ++d) gf[d] = w[f] * g[d * nc + O] + (1.0 - w[f]) * g[d * nc + N];
+          F += gamma * dot3(gf, k + 3 * f);
+        }
+        r[O] += F;
+        r[N] -= F;
+      } else {
+        int kind = bc[patch_of_face(m, f)];
+        if (kind == BC_FIXED) r[O] += gamma * c[f] * (pb[f - m->nint] - ph[O]);
+      }
+    }
+  }
+  free(w); free(c); free(k);
+}
+
+/* ------------------------------------------------------------- LDU apply */
+/* y_i = D_i x_i + sum_{f: O=i} U_f x_N + sum_{f: N=i} L_f x_O   (Eq. Ap_H).
+ * U == NULL means symmetric (U = L).  Swapping L and U gives A^T. */
+void om_ldu_apply(const om_mesh *m, int ncomp, const double *D, const double *L,
+                  const double *U, const double *x, double *y) {
+  int nc = m->nc;
+  if (!U) U = L;
+  for (int q = 0; q < ncomp; ++q) {
+    const double *xq = x + (size_t)q * nc;
+    double *yq = y + (size_t)q * nc;
+    for (int i = 0; i < nc; ++i) yq[i] = D[i] * xq[i];
+    for (int f = 0; f < m->nint; ++f) {
+      int O = m->owner[f], N = m->neighbour[f];
+      yq[O] += U[f] * xq[N];
+      yq[N] += L[f] * xq[O];
+    }
+  }
+}
+
+/* ---------------------------------------------------------------- Krylov */
+static double vdot(int n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+typedef struct { int iters; double res0, res, bnorm; int status; } om_info;
+
+/* Jacobi-preconditioned conjugate gradient (SPD pressure system, Sec. 2.6.1).
+ * Stops when ||b - A x||_2 (recursive residual) <= max(tol_rel ||b||_2, tol_abs).
+ * status 0 converged, 3 not converged, 5 non-finite. */
+int om_pcg(const om_mesh *m, const double *D, const double *L, const double *U, const double *b,
+           double *x, double tol_rel, double tol_abs, int maxit, om_info *info) {
+  int n = m->nc;
+  double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+  double *p = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
+  double bn = sqrt(vdot(n, b, b));
+  info->bnorm = bn; info->iters = 0; info->status = 0;
+  if (bn == 0.0) {
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    info->res0 = info->res = 0.0;
+    free(r); free(z); free(p); free(q);
+    return 0;
+  }
+  double tol = fmax(tol_rel * bn, tol_abs);
+  om_ldu_apply(m, 1, D, L, U, x, q);
+  for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+  double rn = sqrt(vdot(n, r, r));
+  info->res0 = rn;
+  for (int i = 0; i < n; ++i) { z[i] = r[i] / D[i]; p[i] = z[i]; }
+  double rz = vdot(n, r, z);
+  int it = 0;
+  while (rn > tol && it < maxit) {
+    om_ldu_apply(m, 1, D, L, U, p, q);
+    double alpha = rz / vdot(n, p, q);
+    for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+    ++it;
+    rn = sqrt(vdot(n, r, r));
+    if (!isfinite(rn)) { info->status = 5; break; }
+    if (rn <= tol) break;
+    for (int i = 0; i < n; ++i) z[i] = r[i] / D[i];
+    double rz1 = vdot(n, r, z);
+    double beta = rz1 / rz;
+    rz = rz1;
+    for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+  }
+  info->iters = it; info->res = rn;
+  if (info->status == 0 && rn > tol) info->status = 3;
+  free(r); free(z); free(p); free(q);
+  return info->status;
+}
+
+/* Right-Jacobi-preconditioned BiCGStab (van der Vorst 1992) for the
+ * non-symmetric momentum system (Sec. 2.6.1).  Same stopping rule as om_pcg. */
+int om_bicgstab(const om_mesh *m, const double *D, const double *L, const double *U,
+                const double *b, double *x, double tol_rel, double tol_abs, int maxit, om_info *info) {
+  int n = m->nc;
+  double *r = malloc(sizeof(double) * n), *rh = malloc(sizeof(double) * n);
+  double *p = calloc(n, sizeof(double)), *v = calloc(n, sizeof(double));
+  double *y = malloc(sizeof(double) * n), *s = malloc(sizeof(double) * n);
+  double *z = malloc(sizeof(double) * n), *t = malloc(sizeof(double) * n);
+  double bn = sqrt(vdot(n, b, b));
+  info->bnorm = bn; info->iters = 0; info->status = 0;
+  if (bn == 0.0) {
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    info->res0 = info->res = 0.0;
+    goto done;
+  }
+  double tol = fmax(tol_rel * bn, tol_abs);
+  om_ldu_apply(m, 1, D, L, U, x, t);
+  for (int i = 0; i < n; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; }
+  double rn = sqrt(vdot(n, r, r));
+  info->res0 = rn;
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  while (rn > tol && it < maxit) {
+    double rho1 = vdot(n, rh, r);
+    if (rho1 == 0.0 || omega == 0.0) { info->status = 4; break; }
+    double beta = (rho1 / rho) * (alpha / omega);
+    rho = rho1;
+    for (int i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    for (int i = 0; i < n; ++i) y[i] = p[i] / D[i];
+    om_ldu_apply(m, 1, D, L, U, y, v);
+    alpha = rho / vdot(n, rh, v);
+    for (int i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+    ++it;
+    double sn = sqrt(vdot(n, s, s));
+    if (sn <= tol) {
+      for (int i = 0; i < n; ++i) x[i] += alpha * y[i];
+      rn = sn;
+      break;
+    }
+    for (int i = 0; i < n; ++i) z[i] = s[i] / D[i];
+    om_ldu_apply(m, 1, D, L, U, z, t);
+    double tt = vdot(n, t, t);
+    omega = tt > 0.0 ? vdot(n, t, s) / tt : 0.0;
+    for (int i = 0; i < n; ++i) { x[i] += alpha * y[i] + omega * z[i]; r[i] = s[i] - omega * t[i]; }
+    rn = sqrt(vdot(n, r, r));
+    if (!isfinite(rn)) { info->status = 5; break; }
+  }
+  info->iters = it; info->res = rn;
+  if (info->status == 0 && rn > tol) info->status = 3;
+done:
+  free(r); free(rh); free(p); free(v); free(y); free(s); free(z); free(t);
+  return info->status;
+}
+
+/* ------------------------------------------------------------ Windkessel */
+/* One RCR step per outlet (Eqs. windkessel_ode, windkessel_discrete):
+ *   exact: p_c <- p_c e + R_d Q (1 - e),  e = exp(-dt/(R_d C))
+ *   FE:    p_c <- p_c + dt (Q - p_c/R_d)/C
+ *   BE:    p_c <- (p_c + dt Q/C) / (1 + dt/(R_d C))
+ * then p_o = p_c + R_p Q. */
+void om_windkessel_update(int n, int scheme, const double *Rp, const double *Cc, const double *Rd,
+                          const double *Q, double dt, double *pc, double *pout) {
+  for (int o = 0; o < n; ++o) {
+    if (scheme == WK_EXACT) {
+      double e = exp(-dt / (Rd[o] * Cc[o]));
+      pc[o] = pc[o] * e + Rd[o] * Q[o] * (1.0 - e);
+    } else if (scheme == WK_FE) {
+      pc[o] = pc[o] + dt * (Q[o] - pc[o] / Rd[o]) / Cc[o];
+    } else {
+      pc[o] = (pc[o] + dt * Q[o] / Cc[o]) / (1.0 + dt / (Rd[o] * Cc[o]));
+    }
+    pout[o] = pc[o] + Rp[o] * Q[o];
+  }
+}
+
+/* --------------------------------------------------- momentum assembly */
+/* Backward-Euler, implicit upwind convection with the current face flux m,
+ * implicit orthogonal diffusion, explicit non-orthogonal correction from
+ * gradU (may be NULL).  Rows:  D_i U_i + sum offdiag = b_i  with
+ *   D_i  = V_i/dt + sum_{O=i}(max(m,0) + nu c) + sum_{N=i}(max(-m,0) + nu c) + bnd
+ *   Up_f = min(m,0) - nu c   (row O, column N)
+ *   Lo_f = -max(m,0) - nu c  (row N, column O)
+ *   b_i  = V_i/dt U^n_i + sigma nu (gradU)_f . k_f + bnd
+ * boundary fixed U: D += nu c, b += (nu c - m) U_b;  zero gradient: D += m. */
+void om_momentum_assemble(const om_mesh *m, const int *bcU, double nu, double dt,
+                          const double *mf, const double *Uold, const double *Ub,
+                          const double *gradU, double *D, double *Lo, double *Up, double *b) {
+  int nc = m->nc, nb = m->nf - m->nint;
+  double *w = malloc(sizeof(double) * (m->nint + 1));
+  double *c = malloc(sizeof(double) * (m->nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (m->nint + 1));
+  om_face_coeffs(m, w, c, k);
+  for (int i = 0; i < nc; ++i) {
+    D[i] = m->V[i] / dt;
+    for (int q = 0; q < 3; ++q) b[q * nc + i] = m->V[i] / dt * Uold[q * nc + i];
+  }
+  for (int f = 0; f < m->nf; ++f) {
+    int O = m->owner[f];
+    double mm = mf[f];
+    if (f < m->nint) {
+      int N = m->neighbour[f];
+      double a = nu * c[f];
+      D[O] += fmax(mm, 0.0) + a;
+      D[N] += fmax(-mm, 0.0) + a;
+      Up[f] = fmin(mm, 0.0) - a;
+      Lo[f] = -fmax(mm, 0.0) - a;
+      if (gradU) {
+        for (int q = 0; q < 3; ++q) {
+          const double *g = gradU + (size_t)q * 3 * nc;
+          double gf[3];
+          for (int d = 0; d < 3; ++d) gf[d] = w[f] * g[d * nc + O] + (1.0 - w[f]) * g[d * nc + N];
+          double corr = nu * dot3(gf, k + 3 * f);
+          b[q * nc + O] += corr;
+          b[q * nc + N] -= corr;
+        }
+      }
+    } else {
+      int kind = bcU[patch_of_face(m, f)];
+      int bf = f - m->nint;
+      if (kind == BC_FIXED) {
+        double a = nu * c[f];
+        D[O] += a;
+        for (int q = 0; q < 3; ++q) b[q * nc + O] += (a - mm) * Ub[q * nb + bf];
+      } else if (kind == BC_ZEROGRAD) {
+        D[O] += mm;
+      }
+    }
+  }
+  free(w); free(c); free(k);
+}
+
+/* H_i = b_i - sum_{f:O=i} Up_f U_N - sum_{f:N=i} Lo_f U_O  (Eq. Ap_H off-diagonal part) */
+void om_H(const om_mesh *m, const double *Lo, const double *Up, const double *b,
+          const double *U, double *H) {
+  int nc = m->nc;
+  for (int q = 0; q < 3; ++q) {
+    const double *u = U + (size_t)q * nc;
+    double *h = H + (size_t)q * nc;
+    for (int i = 0; i < nc; ++i) h[i] = b[q * nc + i];
+    for (int f = 0; f < m->nint; ++f) {
+      int O = m->owner[f], N = m->neighbour[f];
+      h[O] -= Up[f] * u[N];
+      h[N] -= Lo[f] * u[O];
+    }
+  }
+}
+
+/* --------------------------------------------------- pressure assembly */
+/* Pressure equation of one PISO corrector (Eqs. pressure_poisson, velocity_correction):
+ *   phiHbyA_f = HbyA_f . S_f   (boundary: fixed U -> U_b.S, zero-gradient U -> HbyA_O.S)
+ *   a_f       = rAU_f c_f,   rAU_f = w rAU_O + (1-w) rAU_N  (boundary fixed p: rAU_O c_f)
+ *   nonorth_f = rAU_f (grad p)_f . k_f   (lagged, gradp may be NULL)
+ * SPD form  Dp p - sum a_f p_other = -div(phiHbyA) + div(nonorth) + sum_bnd a_f p_b
+ * with Dp_i = sum a_f, Lp_f = -a_f.  af[nf] and nonorth[nint] are returned for the
+ * flux correction. */
+void om_pressure_assemble(const om_mesh *m, const int *bcU, const int *bcp, const double *rAU,
+                          const double *HbyA, const double *Ub, const double *pb,
+                          const double *gradp, double *Dp, double *Lp, double *bp,
+                          double *phiHbyA, double *af, double *nonorth) {
+  int nc = m->nc, nb = m->nf - m->nint;
+  double *w = malloc(sizeof(double) * (m->nint + 1));
+  double *c = malloc(sizeof(double) * (m->nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (m->nint + 1));
+  om_face_coeffs(m, w, c, k);
+  for (int i = 0; i < nc; ++i) { Dp[i] = 0.0; bp[i] = 0.0; }
+  for (int f = 0; f < m->nf; ++f) {
+    const double *S = m->Sf + 3 * f;
+    int O = m->owner[f];
+    if (f < m->nint) {
+      int N = m->neighbour[f];
+      double hf[3];
+      for (int d = 0; d < 3; ++d) hf[d] = w[f] * HbyA[d * nc + O] + (1.0 - w[f]) * HbyA[d * nc + N];
+      phiHbyA[f] = dot3(hf, S);
+      double rf = w[f] * rAU[O] + (1.0 - w[f]) * rAU[N];
+      af[f] = rf * c[f];
+      nonorth[f] = 0.0;
+      if (gradp) {
+        double gf[3];
+        for (int d = 0; d < 3; ++d) gf[d] = w[f] * gradp[d * nc + O] + (1.0 - w[f]) * gradp[d * nc + N];
+        nonorth[f] = rf * dot3(gf, k + 3 * f);
+      }
+      Dp[O] += af[f];
+      Dp[N] += af[f];
+      Lp[f] = -af[f];
+      bp[O] += -phiHbyA[f] + nonorth[f];
+      bp[N] -= -phiHbyA[f] + nonorth[f];
+    } else {
+      int p = patch_of_face(m, f), bf = f - m->nint;
+      int ku = bcU[p], kp = bcp[p];
+      if (ku == BC_EMPTY) { phiHbyA[f] = 0.0; af[f] = 0.0; continue; }
+      if (ku == BC_FIXED) {
+        double ub[3] = {Ub[bf], Ub[nb + bf], Ub[2 * nb + bf]};
+        phiHbyA[f] = dot3(ub, S);
+      } else {
+        double h[3] = {HbyA[O], HbyA[nc + O], HbyA[2 * nc + O]};
+        phiHbyA[f] = dot3(h, S);
+      }
+      bp[O] += -phiHbyA[f];
+      if (kp == BC_FIXED) {
+        af[f] = rAU[O] * c[f];
+        Dp[O] += af[f];
+        bp[O] += af[f] * pb[bf];
+      } else {
+        af[f] = 0.0;
+      }
+    }
+  }
+  free(w); free(c); free(k);
+}
+
+/* ------------------------------------------------------------------ PISO */
+typedef struct {
+  double nu, dt;
+  int ncorr, nonorth;           /* nonorth: explicit non-orthogonal corrections on/off */
+  double tolU, tolp, tol_abs;
+  int maxitU, maxitp;
+  int pref_cell;                /* pinned cell when no patch fixes p */
+  int wk_scheme;
+  int n_out;                    /* Windkessel outlets */
+  const int *wk_patch;          /* [n_out] patch ids */
+  const double *Rp, *Cw, *Rd;   /* [n_out] */
+} om_piso_opts;
+
+typedef struct { int itU[3], itp[4], status; double Q[8], po[8]; } om_piso_info;
+
+/* One PISO step (Sec. 2.4.2): Windkessel outlet update, momentum predictor
+ * (BiCGStab per component), then ncorr pressure correctors (PCG) with the
+ * Rhie-Chow flux correction and the velocity correction.  U[3][nc], p[nc],
+ * phi[nf] are updated in place; Ub[3][nb] and pb[nb] hold the boundary values
+ * at the new time level (pb is overwritten on Windkessel outlets); pc[n_out]
+ * is the capacitor pressure, updated in place. */
+int om_piso_step(const om_mesh *m, const om_piso_opts *o, double *U, double *p, double *phi,
+                 const double *Ub, double *pb, double *pc, om_piso_info *info) {
+  int nc = m->nc, nf = m->nf, ni = m->nint, nb = nf - ni;
+  int *bcU = malloc(sizeof(int) * m->npatch), *bcp = malloc(sizeof(int) * m->npatch);
+  int has_fixed_p = 0;
+  for (int q = 0; q < m->npatch; ++q) {
+    bcU[q] = bc_of_U(m->patch_type[q]);
+    bcp[q] = bc_of_p(m->patch_type[q]);
+    if (bcp[q] == BC_FIXED) has_fixed_p = 1;
+  }
+  memset(info, 0, sizeof(*info));
+  /* 1. Windkessel outlets: Q from the current face flux, p_o imposed on the patch */
+  for (int j = 0; j < o->n_out; ++j) {
+    int q = o->wk_patch[j];
+    double Q = 0.0;
+    for (int f = m->patch_start[q]; f < m->patch_start[q] + m->patch_size[q]; ++f) Q += phi[f];
+    double po;
+    om_windkessel_update(1, o->wk_scheme, o->Rp + j, o->Cw + j, o->Rd + j, &Q, o->dt, pc + j, &po);
+    for (int f = m->patch_start[q]; f < m->patch_start[q] + m->patch_size[q]; ++f) pb[f - ni] = po;
+    if (j < 8) { info->Q[j] = Q; info->po[j] = po; }
+  }
+  double *gradp = malloc(sizeof(double) * 3 * nc), *gradU = malloc(sizeof(double) * 9 * nc);
+  double *D = malloc(sizeof(double) * nc), *Lo = malloc(sizeof(double) * (ni + 1));
+  double *Up = malloc(sizeof(double) * (ni + 1)), *b = malloc(sizeof(double) * 3 * nc);
+  double *rhs = malloc(sizeof(double) * nc), *rAU = malloc(sizeof(double) * nc);
+  double *H = malloc(sizeof(double) * 3 * nc), *HbyA = malloc(sizeof(double) * 3 * nc);
+  double *Dp = malloc(sizeof(double) * nc), *Lp = malloc(sizeof(double) * (ni + 1));
+  double *bp = malloc(sizeof(double) * nc), *phiHbyA = malloc(sizeof(double) * nf);
+  double *af = malloc(sizeof(double) * nf), *nonorth = malloc(sizeof(double) * (ni + 1));
+  om_info si;
+  /* 2. momentum predictor: A U* = b - V grad p^n */
+  om_grad_gauss(m, bcp, 1, p, pb, gradp);
+  if (o->nonorth) om_grad_gauss(m, bcU, 3, U, Ub, gradU);
+  om_momentum_assemble(m, bcU, o->nu, o->dt, phi, U, Ub, o->nonorth ? gradU : NULL, D, Lo, Up, b);
+  for (int q = 0; q < 3; ++q) {
+    for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gradp[q * nc + i];
+    int st = om_bicgstab(m, D, Lo, Up, rhs, U + (size_t)q * nc, o->tolU, o->tol_abs, o->maxitU, &si);
+    info->itU[q] = si.iters;
+    if (st > info->status) info->status = st;
+  }
+  for (int i = 0; i < nc; ++i) rAU[i] = m->V[i] / D[i];
+  /* 3. pressure correctors */
+  for (int corr = 0; corr < o->ncorr; ++corr) {
+    om_H(m, Lo, Up, b, U, H);
+    for (int q = 0; q < 3; ++q)
+      for (int i = 0; i < nc; ++i) HbyA[q * nc + i] = H[q * nc + i] / D[i];
+    if (o->nonorth) om_grad_gauss(m, bcp, 1, p, pb, gradp);
+    om_pressure_assemble(m, bcU, bcp, rAU, HbyA, Ub, pb, o->nonorth ? gradp : NULL,
+                         Dp, Lp, bp, phiHbyA, af, nonorth);
+    if (!has_fixed_p) Dp[o->pref_cell] += Dp[o->pref_cell];   /* p_ref = 0 */
+    int st = om_pcg(m, Dp, Lp, NULL, bp, p, o->tolp, o->tol_abs, o->maxitp, &si);
+    if (corr < 4) info->itp[corr] = si.iters;
+    if (st > info->status) info->status = st;
+    /* Rhie-Chow flux correction */
+    for (int f = 0; f < nf; ++f) {
+      if (f < ni) {
+        phi[f] = phiHbyA[f] - af[f] * (p[m->neighbour[f]] - p[m->owner[f]]) - nonorth[f];
+      } else if (bcp[patch_of_face(m, f)] == BC_FIXED) {
+        phi[f] = phiHbyA[f] - af[f] * (pb[f - ni] - p[m->owner[f]]);
+      } else {
+        phi[f] = phiHbyA[f];
+      }
+    }
+    /* velocity correction U = HbyA - rAU grad p */
+    om_grad_gauss(m, bcp, 1, p, pb, gradp);
+    for (int q = 0; q < 3; ++q)
+      for (int i = 0; i < nc; ++i) U[q * nc + i] = HbyA[q * nc + i] - rAU[i] * gradp[q * nc + i];
+  }
+  (void)nb;
+  free(bcU); free(bcp); free(gradp); free(gradU); free(D); free(Lo); free(Up); free(b);
+  free(rhs); free(rAU); free(H); free(HbyA); free(Dp); free(Lp); free(bp); free(phiHbyA);
+  free(af); free(nonorth);
+  return info->status;
+}
+
+/* Initial face flux from a cell velocity: phi_f = U_f . S_f with linear
+ * interpolation; boundary: U_b.S (fixed U), U_O.S (zero gradient), 0 (empty). */
+void om_flux_from_U(const om_mesh *m, const double *U, const double *Ub, double *phi) {
+  int nc = m->nc, ni = m->nint, nb = m->nf - ni;
+  int *bcU = malloc(sizeof(int) * m->npatch);
+  for (int q = 0; q < m->npatch; ++q) bcU[q] = bc_of_U(m->patch_type[q]);
+  double *w = malloc(sizeof(double) * (ni + 1));
+  double *c = malloc(sizeof(double) * (m->nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (ni + 1));
+  om_face_coeffs(m, w, c, k);
+  for (int f = 0; f < m->nf; ++f) {
+    double uf[3];
+    int ok = 1;
+    for (int q = 0; q < 3; ++q)
+      ok &= face_value(m, w, bcU, U + (size_t)q * nc, Ub ? Ub + (size_t)q * nb : NULL, f, &uf[q]);
+    phi[f] = ok ? dot3(uf, m->Sf + 3 * f) : 0.0;
+  }
+  free(bcU); free(w); free(c); free(k);
+}
