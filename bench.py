@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: PISO steps/s on the 1.6M-cell Kuhn-tet lid-driven cavity.
+
+Workload (one "step" = one PISO time step, i.e. one pass of the whole hot
+path: Gauss gradients, momentum assembly with upwind convection and
+over-relaxed diffusion, BiCGStab momentum solve on the matrix-free LDU
+operator, two pressure correctors with the graph-Laplacian assembly, PCG with
+FP64 iterative refinement, Rhie-Chow flux and velocity correction):
+  mesh   Kuhn tetrahedra of a 64^3 hex grid of the unit cube, interior vertices
+         jittered by U(-0.2h, 0.2h) (seed 0), RCM-renumbered: 1,572,864 cells,
+         3,170,304 faces (synthetic; no dataset exists for it)
+  flow   lid-driven cavity, lid u = (1,0,0) on y = 1, Re = 100 (nu = 0.01),
+         dt = 0.004, two correctors, pressure pinned at one cell
+  solve  pressure PCG to ||r|| <= 1e-10 ||b|| in FP64 refinement residuals;
+         momentum BiCGStab to 1e-6 (F32) / 1e-10 (F64)
+  prec   headline: FP32 fields and operators, FP64 dots + pressure refinement;
+         the plain FP64 run is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one process per GPU): every rank runs its own replica of the
+cavity ("replicas only": the path has no exchange step); value = steps of all
+ranks / max-over-ranks time.  The working set (about 0.9 GB in F32) is far
+larger than the 126 MB L2, so no L2 flush is needed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PISO steps/s & fwd+adjoint/fwd time at 1.6M-cell tet mesh; face-op HBM GB/s %"
+WORKLOAD = "kuhn64_cavity_re100"
+N_KUHN, JITTER, SEED = 64, 0.2, 0
+NU, DT = 0.01, 0.004
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def make_mesh(n=N_KUHN):
+    from paper_2603_15920_b300 import meshgen as mg
+    return mg.kuhn_cube(n, JITTER, SEED)
+
+
+def lid_bc(m):
+    Ub = np.zeros((3, m.n_boundary))
+    Ub[0, m.patch_faces("y1") - m.n_internal] = 1.0
+    return Ub
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU baseline
+def cpu_oracle_step_rate(m, steps=1, warm_steps=0):
+    """The FP64 CPU oracle (single thread, as it stands) on the same cavity.
+    Returns (steps/s, seconds, sample description)."""
+    import oracle as O
+    om = O.OMesh.from_mesh(m)
+    Ub = lid_bc(m)
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    phi = O.flux_from_U(om, U, Ub)
+    kw = dict(nu=NU, dt=DT, tolU=1e-10, tolp=1e-10, pref_cell=0)
+    for _ in range(warm_steps):
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, **kw)
+    t = time.perf_counter()
+    for _ in range(steps):
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, **kw)
+    dt = time.perf_counter() - t
+    return steps / dt, dt
+
+
+def reference_arm(args):
+    """--impl reference: the oracle timed on the host cores, same metric/unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    m = make_mesh()
+    # each step of this arm is one full oracle PISO step of the cavity
+    import oracle as O
+    om = O.OMesh.from_mesh(m)
+    Ub = lid_bc(m)
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    phi = O.flux_from_U(om, U, Ub)
+    kw = dict(nu=NU, dt=DT, tolU=1e-10, tolp=1e-10, pref_cell=0)
+    W, K = min(args.warmup, 1), min(args.steps, 2)
+    for _ in range(W):
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, **kw)
+    t = time.perf_counter()
+    for _ in range(K):
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, **kw)
+    el = time.perf_counter() - t
+    v = K / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": f"kuhn{N_KUHN}^3 jitter {JITTER} seed {SEED}",
+                   "cells": m.n_cells, "faces": m.n_faces, "nu": NU, "dt": DT},
+        "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{K} full oracle PISO steps of the cavity after {W} warm-up step(s) "
+                                   f"(requested --steps {args.steps} --warmup {args.warmup}, capped "
+                                   "to keep the run within minutes)"},
+        "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_15920_b300 import difvm as D
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    m = make_mesh()
+    dm = D.Mesh(m, device=local)
+    Ub_h = lid_bc(m)
+    pref = int(dm.cell_new_of_old[0])
+
+    def new_state(dt_):
+        U = torch.zeros(3, dm.nc, dtype=dt_, device="cuda")
+        p = torch.zeros(dm.nc, dtype=dt_, device="cuda")
+        Ub = torch.as_tensor(dm.to_bnd(Ub_h), dtype=dt_, device="cuda").contiguous()
+        pb = torch.zeros(dm.nb, dtype=dt_, device="cuda")
+        phi = D.difvm_flux_from_U(dm, U, Ub)
+        return [U, p, phi, Ub, pb]
+
+    def piso(prec):
+        if prec == D.F32:
+            return D.Piso(dm, D.F32, D.piso_opts(
+                NU, DT, 2, True, solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
+                solve_p=D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=32, refine_max=20,
+                                     inner_tol=1e-4),
+                pref_cell=pref))
+        return D.Piso(dm, D.F64, D.piso_opts(
+            NU, DT, 2, True, solve_U=D.solve_opts(D.BICGSTAB, 1e-10, max_iter=1000, check_every=4),
+            solve_p=D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=32), pref_cell=pref))
+
+    info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(prec, W, K, prof_tag=None):
+        dt_ = torch.float32 if prec == D.F32 else torch.float64
+        h = piso(prec)
+        s = new_state(dt_)
+        for _ in range(W):
+            st, _ = h.step(*s, info=info)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if prof_tag:
+            D.difvm_prof_start(prof_tag, 200000)
+        l0 = D.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        worst = 0
+        for _ in range(K):
+            st, _ = h.step(*s, info=info)
+            worst = max(worst, st)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = D.launch_count() - l0
+        prof = D.difvm_prof_stop() if prof_tag else None
+        return dict(ms=ms, launches=launches, status=worst, prof=prof, info=D.decode_piso_info(info),
+                    state=s, handle=h)
+
+    W, K = max(args.warmup, 3), args.steps
+    clocks = Clocks(local)
+    clocks.start()
+    r32 = timed(D.F32, W, K, prof_tag=D.PROF_PCG_SPMV)
+    ck = clocks.stop()
+    ms_local = r32["ms"] / K
+    if world > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    else:
+        ms_step = ms_local
+    value = world * 1e3 / ms_step
+
+    # roofline of the dominant kernel: PCG SpMV + p.q (sym LDU, F32), algorithmic bytes
+    # per launch = internal faces x (owner + neighbour + coefficient) + cells x (D, p, q)
+    peak, peak_kind = measured_peaks()
+    spmv_ms, spmv_n = r32["prof"]
+    alg_bytes = dm.ni * (4 + 4 + 4) + dm.nc * (4 + 4 + 4)
+    avg_ms = spmv_ms / max(spmv_n, 1)
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if spmv_n else None
+    traffic = None
+    tf_path = os.path.join(ROOT, "profiles", "traffic_pcg_spmv_f32_kuhn64.json")
+    if os.path.exists(tf_path):
+        try:
+            traffic = json.load(open(tf_path)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # plain FP64 form, same workload (fewer steps: it is the slow form)
+    r64 = timed(D.F64, 3, max(2, min(K, 5)))
+    ms64 = r64["ms"] / max(2, min(K, 5))
+
+    # end to end through the public API: per step the lid boundary values go
+    # host -> device from pinned memory and the step's info record comes back
+    dt_ = torch.float32
+    h = r32["handle"]
+    s = r32["state"]
+    Ub_pin = torch.as_tensor(dm.to_bnd(Ub_h), dtype=dt_).contiguous().pin_memory()
+    pb_pin = torch.zeros(dm.nb, dtype=dt_).pin_memory()
+    info_pin = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        s[3].copy_(Ub_pin, non_blocking=True)
+        s[4].copy_(pb_pin, non_blocking=True)
+        h.step(*s, info=info)
+        info_pin.copy_(info, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / K
+    h2d = (Ub_pin.numel() + pb_pin.numel()) * 4
+    d2h = info_pin.numel()
+
+    if rank != 0:
+        return 0
+    # CPU baseline: one full oracle PISO step of the same cavity (single thread)
+    cpu = None
+    if not args.no_cpu:
+        rate, secs = cpu_oracle_step_rate(m, steps=1)
+        cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 full FP64 oracle PISO step of the same cavity from rest ({secs:.1f} s)"}
+    gi = r32["info"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": f"kuhn{N_KUHN}^3 jitter {JITTER} seed {SEED} RCM",
+                   "cells": dm.nc, "faces": dm.nf, "nu": NU, "dt": DT, "n_corr": 2,
+                   "precision": "f32 fields/operators, f64 dots + f64 pressure refinement to 1e-10",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set (~0.9 GB) > 126 MB L2; no flush needed"},
+        "gpu_launches": int(r32["launches"]),
+        "status": int(r32["status"]),
+        "pressure_iters_last_step": gi["itp"][:2], "momentum_iters_last_step": gi["itU"],
+        "f64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64},
+        "fwd_adjoint_over_fwd": None,
+        "roofline": {"kernel": "k_pcg_spmv<float,1> (LDU SpMV + p.q)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,
+                     "launches_timed": spmv_n, "peak_kind": peak_kind},
+        "e2e": {"value": 1e3 / e2e_ms * world, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

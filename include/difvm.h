@@ -1,0 +1,312 @@
+/*
+ * difvm.h -- C ABI of the B300 (sm_103a) face-operator / PISO library.
+ *
+ * The operations follow the finite-volume method as a message-passing graph of
+ * arxiv 2603.15920 ("DiFVM"):  cells are nodes, internal faces are edges
+ * owner -> neighbour, boundary faces are edges from ghost nodes (Sec. 2.4.1).
+ * Every operator computes a per-face message and reduces it onto cells with
+ * sigma = +1 for the owner and -1 for the neighbour (Eq. aggregate).  The
+ * reduction is a deterministic cell-CSR segmented sum in ascending face id:
+ * no atomics, bitwise reproducible run to run.
+ *
+ * Conventions shared by all calls
+ *  - Numbering.  difvm_mesh_create renumbers cells (reverse Cuthill-McKee) and
+ *    faces (internal faces oriented owner < neighbour and sorted by
+ *    (owner, neighbour); boundary faces kept grouped by patch, in patch order,
+ *    sorted by owner inside a patch).  All field pointers below are in this
+ *    INTERNAL numbering; difvm_mesh_permutation returns the maps.
+ *  - Layout.  Cell fields are component-major  x[c * n_cells + i]  (SoA).
+ *    Face fields  m[f], f < n_faces.  Boundary values  xb[c * n_boundary + b],
+ *    b = f - n_internal.  Gradients  g[(c*3 + d) * n_cells + i] = d x_c / d x_d.
+ *  - Precision.  prec selects the element type of every field pointer of the
+ *    call: DIFVM_F64 (double) or DIFVM_F32 (float).  Krylov inner products and
+ *    norms are always accumulated in double.
+ *  - Memory.  Field pointers are DEVICE pointers owned by the caller; the
+ *    library never frees them.  The mesh handle owns its own device copies of
+ *    the geometry.  Hot calls allocate nothing (workspace comes from the caller
+ *    or from a handle created beforehand) and are asynchronous on `stream`
+ *    (a cudaStream_t; NULL = legacy default stream).
+ *  - Errors.  Every call returns a difvm_status.  Argument and mesh errors are
+ *    returned synchronously (nothing is launched); solver outcomes (not
+ *    converged, breakdown, non-finite residual) are written to device-resident
+ *    info structs so that calls never synchronise.  difvm_last_error() gives a
+ *    thread-local message for the last non-OK status of the calling thread.
+ */
+#ifndef DIFVM_H
+#define DIFVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DIFVM_OK = 0,
+  DIFVM_EINVAL = 1,     /* bad argument or mesh */
+  DIFVM_ENOMEM = 2,     /* device or host allocation failed (create calls only) */
+  DIFVM_ECUDA = 3,      /* a CUDA runtime call failed */
+  DIFVM_ENOTCONV = 4,   /* Krylov solve hit max_iter before the tolerance */
+  DIFVM_EBREAKDOWN = 5, /* BiCGStab breakdown (rho or omega exactly 0) */
+  DIFVM_ENONFINITE = 6, /* NaN / Inf residual */
+  DIFVM_ETIMEOUT = 7    /* a bounded device wait gave up */
+} difvm_status;
+
+typedef enum { DIFVM_F32 = 0, DIFVM_F64 = 1 } difvm_prec;
+
+/* Patch types of difvm_mesh_desc.patch_type (boundary conditions, Sec. 2.6.2):
+ *   WALL   fixed velocity (value per face), zero-gradient pressure  (no-slip or moving wall)
+ *   INLET  fixed velocity, zero-gradient pressure
+ *   OUTLET zero-gradient velocity, fixed pressure (also the Windkessel outlet, Sec. 2.6.3)
+ *   EMPTY  excluded from every face sum (2D runs) */
+enum { DIFVM_PATCH_WALL = 0, DIFVM_PATCH_INLET = 1, DIFVM_PATCH_OUTLET = 2, DIFVM_PATCH_EMPTY = 3 };
+
+/* Boundary-condition class of a field, chosen per operator call.  A class maps
+ * every patch to one of FIXED (face value = the boundary value passed in),
+ * ZEROGRAD (face value = owner cell value) or EMPTY (face skipped).
+ *   VELOCITY  derived from patch types: WALL/INLET fixed, OUTLET zero-gradient
+ *   PRESSURE  derived from patch types: OUTLET fixed, WALL/INLET zero-gradient
+ *   ALL_FIXED / ALL_ZEROGRAD  every non-empty patch fixed / zero-gradient */
+enum { DIFVM_BC_VELOCITY = 0, DIFVM_BC_PRESSURE = 1, DIFVM_BC_ALL_FIXED = 2, DIFVM_BC_ALL_ZEROGRAD = 3 };
+enum { DIFVM_FACE_FIXED = 0, DIFVM_FACE_ZEROGRAD = 1, DIFVM_FACE_EMPTY = 2 };
+
+enum { DIFVM_DIV_UPWIND = 0, DIFVM_DIV_LINEAR = 1 };           /* Eq. upwind / central */
+enum { DIFVM_WK_EXACT = 0, DIFVM_WK_FE = 1, DIFVM_WK_BE = 2 };  /* Eq. windkessel_discrete */
+enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
+enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1 };
+enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };
+
+typedef struct difvm_mesh* difvm_mesh_t;
+
+/* Mesh description (Sec. 2.4.1, static graph arrays).  All HOST pointers,
+ * FP64 geometry, read during difvm_mesh_create only (copied).
+ *   owner[n_faces], neighbour[n_internal]: cell ids; internal faces first,
+ *     then boundary faces grouped by patch (patch p covers faces
+ *     [patch_start[p], patch_start[p] + patch_size[p]) ).
+ *   Sf[3*n_faces]: face area vector, AoS xyz, pointing out of the owner.
+ *   Cf[3*n_faces]: face centroid.  V[n_cells]: volume.  C[3*n_cells]: centroid.
+ *   n_cases / case_cell_start[n_cases+1]: a batch of independent meshes laid
+ *     out as one disjoint union (cells of case k in [start[k], start[k+1]));
+ *     n_cases <= 1 and NULL for a single mesh.
+ *   flags: DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES (internal faces are always
+ *     re-oriented so that owner < neighbour).
+ *   device: CUDA device ordinal the handle lives on. */
+typedef struct {
+  int32_t n_cells, n_internal, n_faces, n_patches;
+  const int32_t *owner, *neighbour;
+  const double *Sf, *Cf, *V, *C;
+  const int32_t *patch_start, *patch_size, *patch_type;
+  int32_t n_cases;
+  const int32_t *case_cell_start;
+  uint32_t flags;
+  int32_t device;
+} difvm_mesh_desc;
+
+/* Validate, renumber, build the cell-CSR and the derived face coefficients
+ * (w_f, c_f = |S|^2/(S.d), k_f = S - c_f d, 1/V; Sec. 2.3.2) and upload them.
+ * Errors: EINVAL with a message for index out of range, owner == neighbour,
+ * patches not covering the boundary faces contiguously, V <= 0 or S.d <= 0;
+ * ENOMEM / ECUDA on allocation or copy failure.  Synchronous. */
+difvm_status difvm_mesh_create(const difvm_mesh_desc* desc, difvm_mesh_t* out);
+/* Maps between input and internal numbering, HOST outputs (any may be NULL):
+ *   cell_new_of_old[n_cells], face_old_of_new[n_faces],
+ *   face_flip[n_faces] (1 where the internal face was re-oriented: its S, and
+ *   every face flux, changes sign). */
+difvm_status difvm_mesh_permutation(difvm_mesh_t, int32_t* cell_new_of_old,
+                                    int32_t* face_old_of_new, int8_t* face_flip);
+/* Sizes: n_cells, n_internal, n_faces, n_boundary, n_patches, csr_entries. */
+difvm_status difvm_mesh_info(difvm_mesh_t, int64_t out[6]);
+void difvm_mesh_destroy(difvm_mesh_t);
+const char* difvm_last_error(void);
+/* Number of kernels this library has launched on the calling process (all
+ * devices).  For launch accounting in benchmarks. */
+uint64_t difvm_launch_count(void);
+/* Per-kernel device timing for benchmarks: while active, every launch of the
+ * kernel named by `tag` is bracketed by a pair of CUDA events on its own
+ * stream (at most max_launches pairs; later launches are not timed).
+ * difvm_prof_stop synchronises on the recorded events and returns the summed
+ * kernel time and the number of timed launches.  Process-wide, one tag at a
+ * time, not thread-safe; start/stop allocate and free the events. */
+enum { DIFVM_PROF_PCG_SPMV = 1, DIFVM_PROF_PCG_UPDATE = 2, DIFVM_PROF_PCG_PUPDATE = 3 };
+difvm_status difvm_prof_start(int tag, int max_launches);
+difvm_status difvm_prof_stop(double* total_ms, int64_t* launches);
+
+/* ---------------------------------------------------------------- operators */
+/* Gauss gradient (Eq. gauss_green): grad_i = (1/V_i) sum_f sigma phi_f S_f,
+ * phi_f linearly interpolated (owner weight w_f) on internal faces and given by
+ * the bc class on boundary faces.  phi[ncomp][nc], phi_b[ncomp][nb] (may be NULL
+ * when the class has no FIXED patch), grad[ncomp][3][nc] (overwritten).
+ * ncomp in 1..3. */
+difvm_status difvm_grad_gauss(difvm_mesh_t, difvm_prec, int bc_class, const void* phi,
+                              const void* phi_b, int ncomp, void* grad, void* stream);
+/* Adjoint of difvm_grad_gauss: phi_bar += G^T grad_bar, phi_b_bar += G_b^T grad_bar
+ * (accumulates; phi_b_bar may be NULL). */
+difvm_status difvm_grad_gauss_bwd(difvm_mesh_t, difvm_prec, int bc_class, const void* grad_bar,
+                                  int ncomp, void* phi_bar, void* phi_b_bar, void* stream);
+
+/* Convective flux divergence (Eqs. conv_face_flux, upwind):
+ * out_i = sum_f sigma m_f phi_f, phi_f upwind (m_f >= 0 -> owner) or linear on
+ * internal faces, the bc-class value on boundary faces.  m[nf], phi/out [ncomp][nc]. */
+difvm_status difvm_div_flux(difvm_mesh_t, difvm_prec, int scheme, int bc_class,
+                            const void* mflux, const void* phi, const void* phi_b, int ncomp,
+                            void* out, void* stream);
+/* Adjoint: mflux_bar += dout/dm^T out_bar, phi_bar += ..., phi_b_bar += ...
+ * (accumulates; any output may be NULL). */
+difvm_status difvm_div_flux_bwd(difvm_mesh_t, difvm_prec, int scheme, int bc_class,
+                                const void* mflux, const void* phi, const void* phi_b, int ncomp,
+                                const void* out_bar, void* mflux_bar, void* phi_bar,
+                                void* phi_b_bar, void* stream);
+
+/* Diffusive flux (Eq. nonortho_flux, over-relaxed):
+ * out_i = sum_f sigma gamma [c_f (phi_N - phi_O) + (grad phi)_f . k_f], boundary
+ * FIXED faces gamma c_f (phi_b - phi_O) (orthogonal), others 0.  grad may be NULL
+ * (orthogonal part only); (grad phi)_f is linearly interpolated. */
+difvm_status difvm_laplacian(difvm_mesh_t, difvm_prec, int bc_class, double gamma,
+                             const void* phi, const void* phi_b, const void* grad, int ncomp,
+                             void* out, void* stream);
+/* Adjoint of difvm_laplacian w.r.t. phi, phi_b and grad (accumulates). */
+difvm_status difvm_laplacian_bwd(difvm_mesh_t, difvm_prec, int bc_class, double gamma,
+                                 const void* out_bar, int ncomp, void* phi_bar, void* phi_b_bar,
+                                 void* grad_bar, void* stream);
+
+/* Matrix-free LDU operator (Eq. Ap_H, the implicit momentum / pressure matrix):
+ * y_i = D_i x_i + sum_{f: O(f)=i} U_f x_N(f) + sum_{f: N(f)=i} L_f x_O(f).
+ * diag[nc], lower[ni], upper[ni] (NULL = symmetric, U = L); x, y [ncomp][nc].
+ * transpose != 0 applies A^T (L and U swapped). */
+difvm_status difvm_laplacian_apply(difvm_mesh_t, difvm_prec, const void* diag, const void* lower,
+                                   const void* upper, const void* x, int ncomp, int transpose,
+                                   void* y, void* stream);
+/* Adjoint: x_bar += A^T y_bar; diag_bar_i += sum_c y_bar_i x_i;
+ * lower_bar_f += sum_c y_bar_N x_O; upper_bar_f += sum_c y_bar_O x_N
+ * (accumulates; any output may be NULL; with upper == NULL the symmetric
+ * coefficient gets both contributions in lower_bar).  tmp: device scratch of
+ * ncomp*n_cells elements, required when x_bar != NULL. */
+difvm_status difvm_laplacian_apply_bwd(difvm_mesh_t, difvm_prec, const void* diag,
+                                       const void* lower, const void* upper, const void* x,
+                                       const void* y_bar, int ncomp, void* x_bar, void* diag_bar,
+                                       void* lower_bar, void* upper_bar, void* tmp, void* stream);
+
+/* ------------------------------------------------------------------- Krylov */
+typedef struct {
+  int32_t method;      /* DIFVM_PCG (SPD) or DIFVM_BICGSTAB */
+  int32_t precond;     /* DIFVM_PRECOND_NONE or DIFVM_PRECOND_JACOBI */
+  int32_t max_iter;
+  int32_t check_every; /* iterations between host convergence checks (0 = 8) */
+  double tol_rel;      /* stop when ||b - A x||_2 <= max(tol_rel ||b||_2, tol_abs) */
+  double tol_abs;
+  int32_t refine_max;  /* refinement sweeps (difvm_krylov_solve_refine; in PISO a value > 0
+                          with DIFVM_F32 selects the mixed-precision pressure solve) */
+  double inner_tol;    /* refinement: relative tolerance of each inner F32 solve (0 = 1e-4) */
+} difvm_solve_opts;
+
+/* Per-component outcome, written on the DEVICE (no host sync needed). */
+typedef struct {
+  int32_t iters, refinements, status, pad;
+  double res0, res, bnorm;
+} difvm_solve_info;
+
+/* Bytes of workspace difvm_krylov_solve needs for (prec, method, ncomp). */
+size_t difvm_krylov_workspace_bytes(difvm_mesh_t, difvm_prec, int method, int ncomp);
+/* Solve A x_c = b_c for each of ncomp right-hand sides with the LDU matrix
+ * (diag, lower, upper; upper NULL = symmetric) by Jacobi-preconditioned CG or
+ * BiCGStab (Sec. 2.6.1: CG for the SPD pressure system, BiCGStab for the
+ * momentum system).  x is the initial guess on entry and the solution on exit.
+ * Inner products and norms are accumulated in FP64.  info_dev[ncomp] is device
+ * memory.  The call synchronises `stream` every check_every iterations to read
+ * the convergence flags (iterations issued past convergence do nothing).
+ * Returns OK or the worst solver status (ENOTCONV, EBREAKDOWN, ENONFINITE);
+ * x holds the last iterate in every case. */
+difvm_status difvm_krylov_solve(difvm_mesh_t, difvm_prec, const difvm_solve_opts* opts,
+                                const void* diag, const void* lower, const void* upper,
+                                const void* b, void* x, int ncomp, void* workspace,
+                                size_t workspace_bytes, difvm_solve_info* info_dev, void* stream);
+/* Bytes of workspace difvm_krylov_solve_refine needs. */
+size_t difvm_krylov_refine_workspace_bytes(difvm_mesh_t, int method, int ncomp);
+/* Mixed-precision solve with iterative refinement: the matrix is FP32
+ * (diag/lower/upper float), b64 and x64 are FP64.  Each sweep forms the FP64
+ * residual r = b - A x (FP32 coefficients are exact in FP64), solves A e = r in
+ * FP32 to opts->inner_tol (relative, 0 = 1e-4) and adds e to x64 in FP64, until
+ * ||r||_2 <= max(tol_rel ||b||_2, tol_abs) or refine_max sweeps (0 = 20); a
+ * sweep that fails to cut the residual by 4x stops with ENOTCONV.
+ * info.iters = total inner iterations, info.refinements = sweeps. */
+difvm_status difvm_krylov_solve_refine(difvm_mesh_t, const difvm_solve_opts* opts, const float* diag,
+                                       const float* lower, const float* upper, const double* b64,
+                                       double* x64, int ncomp, void* workspace,
+                                       size_t workspace_bytes, difvm_solve_info* info_dev,
+                                       void* stream);
+/* Adjoint of a converged solve (implicit differentiation, Eq. implicit_diff):
+ * b_bar_c = A^{-T} x_bar_c (same method on the transposed matrix), then
+ * diag_bar_i -= sum_c b_bar_i x_i, lower_bar_f -= sum_c b_bar_N x_O,
+ * upper_bar_f -= sum_c b_bar_O x_N.  b_bar is OVERWRITTEN with A^{-T} x_bar
+ * (the caller accumulates it where needed); coefficient grads accumulate. */
+difvm_status difvm_krylov_solve_bwd(difvm_mesh_t, difvm_prec, const difvm_solve_opts* opts,
+                                    const void* diag, const void* lower, const void* upper,
+                                    const void* x, const void* x_bar, int ncomp, void* b_bar,
+                                    void* diag_bar, void* lower_bar, void* upper_bar,
+                                    void* workspace, size_t workspace_bytes,
+                                    difvm_solve_info* info_dev, void* stream);
+
+/* --------------------------------------------------------------- Windkessel */
+/* One RCR step per outlet (Eqs. windkessel_ode, windkessel_discrete), all
+ * DEVICE double arrays [n_out]:  EXACT  p_c <- p_c e + R_d Q (1-e), e = exp(-dt/(R_d C));
+ * FE  p_c <- p_c + dt (Q - p_c/R_d)/C;  BE  p_c <- (p_c + dt Q/C)/(1 + dt/(R_d C));
+ * then p_out = p_c + R_p Q.  pc is updated in place. */
+difvm_status difvm_windkessel_update(int n_out, int scheme, const double* Rp, const double* C,
+                                     const double* Rd, const double* Q, double dt, double* pc,
+                                     double* p_out, void* stream);
+/* Adjoint of one step given the inputs (pc_in = p_c before the step):
+ * from pc_out_bar, p_out_bar accumulate pc_in_bar, Q_bar, Rp_bar, C_bar, Rd_bar
+ * (device double [n_out]; pc_in_bar is overwritten, the others accumulate). */
+difvm_status difvm_windkessel_update_bwd(int n_out, int scheme, const double* Rp, const double* C,
+                                         const double* Rd, const double* Q, double dt,
+                                         const double* pc_in, const double* pc_out_bar,
+                                         const double* p_out_bar, double* pc_in_bar, double* Q_bar,
+                                         double* Rp_bar, double* C_bar, double* Rd_bar, void* stream);
+
+/* --------------------------------------------------------------------- PISO */
+typedef struct {
+  double nu, dt;
+  int32_t n_corr;       /* pressure correctors (Sec. 2.4.2: typically 2) */
+  int32_t nonorth;      /* explicit over-relaxed non-orthogonal corrections on/off */
+  difvm_solve_opts solve_U, solve_p;
+  int32_t pref_cell;    /* internal id of the pinned cell when no patch fixes p */
+  int32_t wk_scheme;    /* DIFVM_WK_* */
+  int32_t n_out;        /* Windkessel outlets (0..16) */
+  int32_t wk_patch[16]; /* patch ids of the outlets */
+} difvm_piso_opts;
+
+typedef struct difvm_piso* difvm_piso_t;
+/* Create a PISO driver for one mesh and precision; owns all step workspace. */
+difvm_status difvm_piso_create(difvm_mesh_t, difvm_prec, const difvm_piso_opts*, difvm_piso_t*);
+void difvm_piso_destroy(difvm_piso_t);
+/* Per-step outcome (device): solver iterations and the Windkessel values. */
+typedef struct {
+  int32_t itU[3], itp[4], status, pad;
+  double Q[16], p_out[16];
+} difvm_piso_info;
+/* One PISO step (Sec. 2.4.2), in place on U[3][nc], p[nc], phi[nf]:
+ *  1. Windkessel outlets: Q_o = sum over the patch of phi, p_c update,
+ *     p_out = p_c + R_p Q imposed as the fixed pressure of the patch (p_b);
+ *  2. momentum predictor: backward Euler, implicit upwind convection with the
+ *     current phi, implicit orthogonal + explicit non-orthogonal diffusion,
+ *     A U* = b - V grad p^n, BiCGStab per component;
+ *  3. n_corr times: HbyA = (b - offdiag U)/D, phiHbyA_f = HbyA_f.S_f, pressure
+ *     equation with face coefficient (V/D)_f c_f (PCG), Rhie-Chow flux
+ *     correction phi = phiHbyA - (V/D)_f (c_f dp + (grad p)_f.k_f), velocity
+ *     correction U = HbyA - (V/D) grad p.
+ * U_b[3][nb], p_b[nb] boundary values at the new time level (p_b is rewritten
+ * on Windkessel patches); wk: DEVICE double [4*n_out] = (Rp, C, Rd, p_c) with
+ * p_c updated; info_dev device.  All device pointers of the handle's precision
+ * except wk (double).  Synchronises on Krylov convergence checks. */
+difvm_status difvm_piso_step(difvm_piso_t, void* U, void* p, void* phi, const void* U_b, void* p_b,
+                             double* wk, difvm_piso_info* info_dev, void* stream);
+/* Initial face flux phi_f = U_f . S_f (linear interpolation; boundary: U_b.S
+ * for fixed velocity, U_O.S for zero gradient, 0 for empty). */
+difvm_status difvm_flux_from_U(difvm_mesh_t, difvm_prec, const void* U, const void* U_b,
+                               void* phi, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIFVM_H */

@@ -1,0 +1,131 @@
+// Internal declarations of the sm_103a face-operator / PISO library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/difvm.h"
+
+namespace difvm {
+
+// ----------------------------------------------------------------- errors
+difvm_status set_error(difvm_status st, const char* fmt, ...);
+void count_launch();
+difvm_status check_launch(const char* what);
+
+// --------------------------------------------------- per-kernel event timing
+// When difvm_prof_start(tag) is active, launches wrapped in prof_before /
+// prof_after with the same tag get a pair of CUDA events on their stream.
+void prof_before(int tag, cudaStream_t s);
+void prof_after(int tag, cudaStream_t s);
+
+#define DIFVM_CUDA(call)                                                            \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ::difvm::set_error(DIFVM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define DIFVM_TRY(expr)                 \
+  do {                                  \
+    difvm_status s_ = (expr);           \
+    if (s_ != DIFVM_OK) return s_;      \
+  } while (0)
+
+// ------------------------------------------------------------ vector types
+template <typename T> struct V4;
+template <> struct __align__(16) V4<float> { float x, y, z, w; };
+template <> struct __align__(32) V4<double> { double x, y, z, w; };
+
+template <typename T>
+__device__ __forceinline__ V4<T> ld4(const V4<T>* p);
+template <>
+__device__ __forceinline__ V4<float> ld4<float>(const V4<float>* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return V4<float>{v.x, v.y, v.z, v.w};
+}
+template <>
+__device__ __forceinline__ V4<double> ld4<double>(const V4<double>* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return V4<double>{a.x, a.y, b.x, b.y};
+}
+
+// Per-precision device geometry, internal numbering.
+template <typename T> struct Geo {
+  const V4<T>* Sw;  // [nf] (Sx, Sy, Sz, w_f); w_f = owner weight (1 on boundary faces)
+  const V4<T>* ck;  // [nf] (c_f, kx, ky, kz); k = 0 on boundary faces
+  const T* V;       // [nc]
+  const T* rV;      // [nc]
+};
+
+// Topology, internal numbering, passed by value to kernels.
+struct Topo {
+  int nc, ni, nf, nb;
+  const int2* on;          // [ni] (owner, neighbour), owner < neighbour, sorted
+  const int* bown;         // [nb] owner of boundary face ni + b
+  const int* cptr;         // [nc+1] cell-CSR row pointers
+  const int* cent;         // [nnz]  (face << 1) | side, ascending face id per cell
+  const uint8_t* bkind;    // [nb] 2 bits per bc class: kind = (bkind >> (2*cls)) & 3
+  const uint16_t* bpatch;  // [nb] patch id
+};
+
+__device__ __forceinline__ int face_kind(const Topo& t, int b, int cls) {
+  return (t.bkind[b] >> (2 * cls)) & 3;
+}
+
+struct difvm_mesh_impl;
+}  // namespace difvm
+
+// The opaque handle of the C ABI.
+struct difvm_mesh {
+  int device;
+  int nc, ni, nf, nb, npatch, ncases;
+  int64_t nnz;
+  int max_row;                       // largest CSR row length
+  std::vector<int32_t> cell_new_of_old, face_old_of_new, case_start;
+  std::vector<int8_t> face_flip;
+  std::vector<int32_t> patch_start, patch_size, patch_type;
+  // device allocations
+  int2* on = nullptr;
+  int* bown = nullptr;
+  int* cptr = nullptr;
+  int* cent = nullptr;
+  uint8_t* bkind = nullptr;
+  uint16_t* bpatch = nullptr;
+  difvm::V4<double>* Sw64 = nullptr;
+  difvm::V4<double>* ck64 = nullptr;
+  difvm::V4<float>* Sw32 = nullptr;
+  difvm::V4<float>* ck32 = nullptr;
+  double *V64 = nullptr, *rV64 = nullptr, *C64 = nullptr, *Cf64 = nullptr;
+  float *V32 = nullptr, *rV32 = nullptr;
+  int num_sms = 148;
+
+  difvm::Topo topo() const {
+    return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
+  }
+  difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }
+  difvm::Geo<float> geo32() const { return {Sw32, ck32, V32, rV32}; }
+};
+
+namespace difvm {
+template <typename T> inline Geo<T> geo(const difvm_mesh* m);
+template <> inline Geo<double> geo<double>(const difvm_mesh* m) { return m->geo64(); }
+template <> inline Geo<float> geo<float>(const difvm_mesh* m) { return m->geo32(); }
+
+inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+difvm_status check_mesh(const difvm_mesh* m);
+difvm_status check_prec(difvm_prec p);
+
+// cross-file launchers (ops.cu)
+template <typename T>
+difvm_status grad_gauss_t(difvm_mesh_t m, int cls, const void* phi, const void* phib, int ncomp,
+                          void* grad, cudaStream_t s);
+template <typename T>
+difvm_status ldu_apply_t(difvm_mesh_t m, const void* D, const void* L, const void* U,
+                         const void* x, int ncomp, int transpose, void* y, cudaStream_t s);
+}  // namespace difvm

@@ -1,0 +1,675 @@
+// Face operators of the message-passing form (Sec. 2.4.1) and their adjoints.
+//
+// Every operator is one cell-centric kernel: thread i walks the cell-CSR row of
+// cell i (faces in ascending id), recomputes the face message of each face
+// exactly as the owner side does (same operands, same instruction order, so
+// the owner and the neighbour see bitwise the same message), and accumulates
+// sigma * message in registers.  This is the aggregation of Eq. aggregate as a
+// deterministic segmented sum: no atomics, no stored face fluxes.  Face data
+// (S_f, w_f packed in one 16/32-byte record; c_f, k_f in another) and the
+// neighbour cell values are gathered through the read-only path; RCM ordering
+// keeps the second visit of a face within L2 reach of the first.
+#include <algorithm>
+#include <utility>
+
+#include "difvm_internal.cuh"
+
+namespace difvm {
+
+constexpr int kBlock = 256;
+
+template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// ----------------------------------------------------------- Gauss gradient
+// grad_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green)
+template <typename T, int NC>
+__global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Geo<T> g, int cls,
+                                                       const T* __restrict__ phi,
+                                                       const T* __restrict__ phib,
+                                                       T* __restrict__ grad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, nb = t.nb;
+  T pi[NC], acc[NC][3];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    pi[c] = ldg(phi + c * nc + i);
+    acc[c][0] = acc[c][1] = acc[c][2] = T(0);
+  }
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    const V4<T> s = ld4(g.Sw + f);
+    T pf[NC];
+    T sg = T(1);
+    if (f < t.ni) {
+      const int2 on = ldg(t.on + f);
+      const bool nside = ent & 1;
+      const int j = nside ? on.x : on.y;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T pj = ldg(phi + c * nc + j);
+        const T pO = nside ? pj : pi[c], pN = nside ? pi[c] : pj;
+        pf[c] = s.w * pO + (T(1) - s.w) * pN;
+      }
+      if (nside) sg = T(-1);
+    } else {
+      const int b = f - t.ni;
+      const int kind = face_kind(t, b, cls);
+      if (kind == DIFVM_FACE_EMPTY) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pf[c] = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T q = sg * pf[c];
+      acc[c][0] += q * s.x;
+      acc[c][1] += q * s.y;
+      acc[c][2] += q * s.z;
+    }
+  }
+  const T r = ldg(g.rV + i);
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) grad[(c * 3 + d) * nc + i] = acc[c][d] * r;
+}
+
+// Adjoint: with a_i = grad_bar_i / V_i, a face carries (a_O - a_N).S back to
+// its two cells with weights w and 1-w (zero-gradient boundary faces to the
+// owner, fixed boundary faces to phi_b_bar).
+template <typename T, int NC>
+__global__ void __launch_bounds__(kBlock) k_grad_gauss_bwd(Topo t, Geo<T> g, int cls,
+                                                           const T* __restrict__ gbar,
+                                                           T* __restrict__ phibar,
+                                                           T* __restrict__ phibbar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, nb = t.nb;
+  T ai[NC][3], acc[NC];
+  const T ri = ldg(g.rV + i);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    acc[c] = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ai[c][d] = ldg(gbar + (c * 3 + d) * nc + i) * ri;
+  }
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    const V4<T> s = ld4(g.Sw + f);
+    if (f < t.ni) {
+      const int2 on = ldg(t.on + f);
+      const bool nside = ent & 1;
+      const int j = nside ? on.x : on.y;
+      const T rj = ldg(g.rV + j);
+      const T wi = nside ? (T(1) - s.w) : s.w;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T aj[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) aj[d] = ldg(gbar + (c * 3 + d) * nc + j) * rj;
+        // (a_O - a_N).S
+        T dO = (ai[c][0] - aj[0]) * s.x + (ai[c][1] - aj[1]) * s.y + (ai[c][2] - aj[2]) * s.z;
+        if (nside) dO = -dO;
+        acc[c] += wi * dO;
+      }
+    } else {
+      const int b = f - t.ni;
+      const int kind = face_kind(t, b, cls);
+      if (kind == DIFVM_FACE_EMPTY) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T v = ai[c][0] * s.x + ai[c][1] * s.y + ai[c][2] * s.z;
+        if (kind == DIFVM_FACE_FIXED) {
+          if (phibbar) phibbar[c * nb + b] += v;
+        } else {
+          acc[c] += v;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) phibar[c * nc + i] += acc[c];
+}
+
+// ------------------------------------------------------------ convection
+// out_i = sum_f sigma m_f phi_f   (Eqs. conv_face_flux, upwind; tie m=0 -> owner)
+template <typename T, int NC, bool UPWIND>
+__global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Geo<T> g, int cls,
+                                                     const T* __restrict__ mf,
+                                                     const T* __restrict__ phi,
+                                                     const T* __restrict__ phib,
+                                                     T* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, nb = t.nb;
+  T pi[NC], acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    pi[c] = ldg(phi + c * nc + i);
+    acc[c] = T(0);
+  }
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    const T m = ldg(mf + f);
+    if (f < t.ni) {
+      const int2 on = ldg(t.on + f);
+      const bool nside = ent & 1;
+      const int j = nside ? on.x : on.y;
+      T w = T(0);
+      if (!UPWIND) w = ld4(g.Sw + f).w;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T pj = ldg(phi + c * nc + j);
+        const T pO = nside ? pj : pi[c], pN = nside ? pi[c] : pj;
+        const T pf = UPWIND ? (m >= T(0) ? pO : pN) : w * pO + (T(1) - w) * pN;
+        const T F = m * pf;
+        acc[c] += nside ? -F : F;
+      }
+    } else {
+      const int b = f - t.ni;
+      const int kind = face_kind(t, b, cls);
+      if (kind == DIFVM_FACE_EMPTY) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T pf = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
+        acc[c] += m * pf;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c * nc + i] = acc[c];
+}
+
+// Adjoint.  delta_f = obar_O - obar_N (internal) or obar_O (boundary):
+//   mbar_f += sum_c phi_f delta_f  (written by the owner side / boundary entry)
+//   phi_f's operands receive m delta_f with the scheme's weights.
+template <typename T, int NC, bool UPWIND>
+__global__ void __launch_bounds__(kBlock) k_div_flux_bwd(Topo t, Geo<T> g, int cls,
+                                                         const T* __restrict__ mf,
+                                                         const T* __restrict__ phi,
+                                                         const T* __restrict__ phib,
+                                                         const T* __restrict__ obar,
+                                                         T* __restrict__ mbar,
+                                                         T* __restrict__ phibar,
+                                                         T* __restrict__ phibbar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, nb = t.nb;
+  T pi[NC], oi[NC], acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    pi[c] = ldg(phi + c * nc + i);
+    oi[c] = ldg(obar + c * nc + i);
+    acc[c] = T(0);
+  }
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    const T m = ldg(mf + f);
+    if (f < t.ni) {
+      const int2 on = ldg(t.on + f);
+      const bool nside = ent & 1;
+      const int j = nside ? on.x : on.y;
+      T w = T(0);
+      if (!UPWIND) w = ld4(g.Sw + f).w;
+      T macc = T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T oj = ldg(obar + c * nc + j);
+        const T delta = nside ? (oj - oi[c]) : (oi[c] - oj);
+        T wi;
+        if (UPWIND) wi = (m >= T(0)) == !nside ? T(1) : T(0);
+        else wi = nside ? (T(1) - w) : w;
+        acc[c] += wi * m * delta;
+        if (mbar && !nside) {
+          const T pj = ldg(phi + c * nc + j);
+          const T pf = UPWIND ? (m >= T(0) ? pi[c] : pj) : w * pi[c] + (T(1) - w) * pj;
+          macc += pf * delta;
+        }
+      }
+      if (mbar && !nside) mbar[f] += macc;
+    } else {
+      const int b = f - t.ni;
+      const int kind = face_kind(t, b, cls);
+      if (kind == DIFVM_FACE_EMPTY) continue;
+      T macc = T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T pf = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
+        macc += pf * oi[c];
+        if (kind == DIFVM_FACE_FIXED) {
+          if (phibbar) phibbar[c * nb + b] += m * oi[c];
+        } else {
+          acc[c] += m * oi[c];
+        }
+      }
+      if (mbar) mbar[f] += macc;
+    }
+  }
+  if (phibar) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) phibar[c * nc + i] += acc[c];
+  }
+}
+
+// --------------------------------------------------------------- diffusion
+// out_i = sum_f sigma gamma [c_f (phi_N - phi_O) + (grad phi)_f . k_f]   (Eq. nonortho_flux)
+template <typename T, int NC, bool NONORTH>
+__global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Geo<T> g, int cls, T gamma,
+                                                      const T* __restrict__ phi,
+                                                      const T* __restrict__ phib,
+                                                      const T* __restrict__ grad,
+                                                      T* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, nb = t.nb;
+  T pi[NC], acc[NC], gi[NC][3];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    pi[c] = ldg(phi + c * nc + i);
+    acc[c] = T(0);
+    if (NONORTH)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) gi[c][d] = ldg(grad + (c * 3 + d) * nc + i);
+  }
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    const V4<T> ck = ld4(g.ck + f);
+    if (f < t.ni) {
+      const int2 on = ldg(t.on + f);
+      const bool nside = ent & 1;
+      const int j = nside ? on.x : on.y;
+      T w = T(0);
+      if (NONORTH) w = ld4(g.Sw + f).w;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T pj = ldg(phi + c * nc + j);
+        const T pO = nside ? pj : pi[c], pN = nside ? pi[c] : pj;
+        T F = ck.x * (pN - pO);
+        if (NONORTH) {
+          T gk = T(0);
+          const T kk[3] = {ck.y, ck.z, ck.w};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const T gj = ldg(grad + (c * 3 + d) * nc + j);
+            const T gO = nside ? gj : gi[c][d], gN = nside ? gi[c][d] : gj;
+            gk += (w * gO + (T(1) - w) * gN) * kk[d];
+          }
+          F += gk;
+        }
+        F *= gamma;
+        acc[c] += nside ? -F : F;
+      }
+    } else {
+      const int b = f - t.ni;
+      if (face_kind(t, b, cls) != DIFVM_FACE_FIXED) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += gamma * (ck.x * (ldg(phib + c * nb + b) - pi[c]));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c * nc + i] = acc[c];
+}
+
+// Adjoint: delta_f = obar_O - obar_N;  phi_N += gamma c delta, phi_O -= gamma c delta,
+// grad_O += gamma w k delta, grad_N += gamma (1-w) k delta; fixed boundary: phi_b += gamma c obar_O.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kBlock) k_laplacian_bwd(Topo t, Geo<T> g, int cls, T gamma,
+                                                          const T* __restrict__ obar,
+                                                          T* __restrict__ phibar,
+                                                          T* __restrict__ phibbar,
+                                                          T* __restrict__ gradbar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, nb = t.nb;
+  T oi[NC], acc[NC], gacc[NC][3];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    oi[c] = ldg(obar + c * nc + i);
+    acc[c] = T(0);
+    gacc[c][0] = gacc[c][1] = gacc[c][2] = T(0);
+  }
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    const V4<T> ck = ld4(g.ck + f);
+    if (f < t.ni) {
+      const int2 on = ldg(t.on + f);
+      const bool nside = ent & 1;
+      const int j = nside ? on.x : on.y;
+      const T w = ld4(g.Sw + f).w;
+      const T wi = nside ? (T(1) - w) : w;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T oj = ldg(obar + c * nc + j);
+        const T delta = gamma * (nside ? (oj - oi[c]) : (oi[c] - oj));
+        acc[c] += nside ? ck.x * delta : -ck.x * delta;
+        gacc[c][0] += wi * ck.y * delta;
+        gacc[c][1] += wi * ck.z * delta;
+        gacc[c][2] += wi * ck.w * delta;
+      }
+    } else {
+      const int b = f - t.ni;
+      if (face_kind(t, b, cls) != DIFVM_FACE_FIXED) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T v = gamma * ck.x * oi[c];
+        acc[c] -= v;
+        if (phibbar) phibbar[c * nb + b] += v;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (phibar) phibar[c * nc + i] += acc[c];
+    if (gradbar)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) gradbar[(c * 3 + d) * nc + i] += gacc[c][d];
+  }
+}
+
+// ---------------------------------------------------------------- LDU apply
+// y_i = D_i x_i + sum_{O(f)=i} U_f x_N + sum_{N(f)=i} L_f x_O   (Eq. Ap_H)
+template <typename T, int NC>
+__global__ void __launch_bounds__(kBlock) k_ldu_apply(Topo t, const T* __restrict__ D,
+                                                      const T* __restrict__ L,
+                                                      const T* __restrict__ U,
+                                                      const T* __restrict__ x,
+                                                      T* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc;
+  const T d = ldg(D + i);
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = d * ldg(x + c * nc + i);
+  const int e1 = ldg(t.cptr + i + 1);
+  for (int e = ldg(t.cptr + i); e < e1; ++e) {
+    const int ent = ldg(t.cent + e);
+    const int f = ent >> 1;
+    if (f >= t.ni) break;  // boundary entries come last
+    const int2 on = ldg(t.on + f);
+    const bool nside = ent & 1;
+    const int j = nside ? on.x : on.y;
+    const T a = nside ? ldg(L + f) : ldg(U + f);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] += a * ldg(x + c * nc + j);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) y[c * nc + i] = acc[c];
+}
+
+// Coefficient adjoints of y = A x: Dbar_i += sum_c ybar_i x_i,
+// Lbar_f += sum_c ybar_N x_O, Ubar_f += sum_c ybar_O x_N (SYM: both into Lbar).
+template <typename T, int NC, bool SYM>
+__global__ void k_ldu_coeff_bwd(Topo t, const T* __restrict__ x, const T* __restrict__ ybar,
+                                T* __restrict__ Dbar, T* __restrict__ Lbar, T* __restrict__ Ubar) {
+  const int nc = t.nc;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < t.ni) {
+    const int2 on = ldg(t.on + k);
+    T lb = T(0), ub = T(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      lb += ldg(ybar + c * nc + on.y) * ldg(x + c * nc + on.x);
+      ub += ldg(ybar + c * nc + on.x) * ldg(x + c * nc + on.y);
+    }
+    if (SYM) {
+      if (Lbar) Lbar[k] += lb + ub;
+    } else {
+      if (Lbar) Lbar[k] += lb;
+      if (Ubar) Ubar[k] += ub;
+    }
+  }
+  if (Dbar && k < nc) {
+    T db = T(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) db += ldg(ybar + c * nc + k) * ldg(x + c * nc + k);
+    Dbar[k] += db;
+  }
+}
+
+template <typename T> __global__ void k_axpy_inplace(int n, const T* __restrict__ a, T* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] += a[i];
+}
+
+// ---------------------------------------------------------------- dispatch
+#define DIFVM_NC_SWITCH(nc, ...)                      \
+  switch (nc) {                                       \
+    case 1: { constexpr int NCc = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int NCc = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int NCc = 3; __VA_ARGS__; } break; \
+    default: return set_error(DIFVM_EINVAL, "ncomp must be 1..3 (got %d)", nc); \
+  }
+
+static difvm_status check_common(difvm_mesh_t m, difvm_prec prec, int ncomp) {
+  DIFVM_TRY(check_mesh(m));
+  DIFVM_TRY(check_prec(prec));
+  if (ncomp < 1 || ncomp > 3) return set_error(DIFVM_EINVAL, "ncomp must be 1..3 (got %d)", ncomp);
+  return DIFVM_OK;
+}
+
+static difvm_status check_cls(int cls) {
+  if (cls < 0 || cls > 3) return set_error(DIFVM_EINVAL, "bad bc class %d", cls);
+  return DIFVM_OK;
+}
+
+template <typename T>
+difvm_status grad_gauss_t(difvm_mesh_t m, int cls, const void* phi, const void* phib,
+                          int ncomp, void* grad, cudaStream_t s) {
+  DIFVM_NC_SWITCH(ncomp, k_grad_gauss<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                             m->topo(), geo<T>(m), cls, (const T*)phi, (const T*)phib, (T*)grad));
+  return check_launch("grad_gauss");
+}
+template difvm_status grad_gauss_t<float>(difvm_mesh_t, int, const void*, const void*, int, void*,
+                                          cudaStream_t);
+template difvm_status grad_gauss_t<double>(difvm_mesh_t, int, const void*, const void*, int, void*,
+                                           cudaStream_t);
+
+template <typename T>
+static difvm_status grad_gauss_bwd_t(difvm_mesh_t m, int cls, const void* gbar, int ncomp,
+                                     void* phibar, void* phibbar, cudaStream_t s) {
+  DIFVM_NC_SWITCH(ncomp, k_grad_gauss_bwd<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                             m->topo(), geo<T>(m), cls, (const T*)gbar, (T*)phibar, (T*)phibbar));
+  return check_launch("grad_gauss_bwd");
+}
+
+template <typename T>
+static difvm_status div_flux_t(difvm_mesh_t m, int scheme, int cls, const void* mf,
+                               const void* phi, const void* phib, int ncomp, void* out,
+                               cudaStream_t s) {
+  if (scheme == DIFVM_DIV_UPWIND) {
+    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), geo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               (const T*)phib, (T*)out));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), geo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               (const T*)phib, (T*)out));
+  }
+  return check_launch("div_flux");
+}
+
+template <typename T>
+static difvm_status div_flux_bwd_t(difvm_mesh_t m, int scheme, int cls, const void* mf,
+                                   const void* phi, const void* phib, int ncomp, const void* obar,
+                                   void* mbar, void* phibar, void* phibbar, cudaStream_t s) {
+  if (scheme == DIFVM_DIV_UPWIND) {
+    DIFVM_NC_SWITCH(ncomp, k_div_flux_bwd<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), geo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               (const T*)phib, (const T*)obar, (T*)mbar, (T*)phibar, (T*)phibbar));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, k_div_flux_bwd<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), geo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               (const T*)phib, (const T*)obar, (T*)mbar, (T*)phibar, (T*)phibbar));
+  }
+  return check_launch("div_flux_bwd");
+}
+
+template <typename T>
+static difvm_status laplacian_t(difvm_mesh_t m, int cls, double gamma, const void* phi,
+                                const void* phib, const void* grad, int ncomp, void* out,
+                                cudaStream_t s) {
+  if (grad) {
+    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), geo<T>(m), cls, (T)gamma, (const T*)phi, (const T*)phib,
+                               (const T*)grad, (T*)out));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), geo<T>(m), cls, (T)gamma, (const T*)phi, (const T*)phib,
+                               (const T*)nullptr, (T*)out));
+  }
+  return check_launch("laplacian");
+}
+
+template <typename T>
+static difvm_status laplacian_bwd_t(difvm_mesh_t m, int cls, double gamma, const void* obar,
+                                    int ncomp, void* phibar, void* phibbar, void* gradbar,
+                                    cudaStream_t s) {
+  DIFVM_NC_SWITCH(ncomp, k_laplacian_bwd<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                             m->topo(), geo<T>(m), cls, (T)gamma, (const T*)obar, (T*)phibar,
+                             (T*)phibbar, (T*)gradbar));
+  return check_launch("laplacian_bwd");
+}
+
+template <typename T>
+difvm_status ldu_apply_t(difvm_mesh_t m, const void* D, const void* L, const void* U,
+                         const void* x, int ncomp, int transpose, void* y, cudaStream_t s) {
+  const T* Lp = (const T*)L;
+  const T* Up = U ? (const T*)U : Lp;
+  if (transpose) std::swap(Lp, Up);
+  DIFVM_NC_SWITCH(ncomp, k_ldu_apply<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                             m->topo(), (const T*)D, Lp, Up, (const T*)x, (T*)y));
+  return check_launch("ldu_apply");
+}
+template difvm_status ldu_apply_t<float>(difvm_mesh_t, const void*, const void*, const void*,
+                                         const void*, int, int, void*, cudaStream_t);
+template difvm_status ldu_apply_t<double>(difvm_mesh_t, const void*, const void*, const void*,
+                                          const void*, int, int, void*, cudaStream_t);
+
+template <typename T>
+static difvm_status ldu_apply_bwd_t(difvm_mesh_t m, const void* D, const void* L, const void* U,
+                                    const void* x, const void* ybar, int ncomp, void* xbar,
+                                    void* Dbar, void* Lbar, void* Ubar, void* tmp, cudaStream_t s) {
+  if (xbar) {
+    DIFVM_TRY(ldu_apply_t<T>(m, D, L, U, ybar, ncomp, 1, tmp, s));
+    k_axpy_inplace<T><<<blocks_for((int64_t)ncomp * m->nc, kBlock), kBlock, 0, s>>>(
+        ncomp * m->nc, (const T*)tmp, (T*)xbar);
+    DIFVM_TRY(check_launch("axpy"));
+  }
+  if (Dbar || Lbar || Ubar) {
+    int n = std::max(m->ni, m->nc);
+    if (U) {
+      DIFVM_NC_SWITCH(ncomp, k_ldu_coeff_bwd<T, NCc, false><<<blocks_for(n, kBlock), kBlock, 0, s>>>(
+                                 m->topo(), (const T*)x, (const T*)ybar, (T*)Dbar, (T*)Lbar, (T*)Ubar));
+    } else {
+      DIFVM_NC_SWITCH(ncomp, k_ldu_coeff_bwd<T, NCc, true><<<blocks_for(n, kBlock), kBlock, 0, s>>>(
+                                 m->topo(), (const T*)x, (const T*)ybar, (T*)Dbar, (T*)Lbar, nullptr));
+    }
+    DIFVM_TRY(check_launch("ldu_coeff_bwd"));
+  }
+  return DIFVM_OK;
+}
+
+}  // namespace difvm
+
+using namespace difvm;
+
+#define DIFVM_PREC_DISPATCH(prec, fn, ...)                      \
+  ((prec) == DIFVM_F64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+extern "C" difvm_status difvm_grad_gauss(difvm_mesh_t m, difvm_prec prec, int cls, const void* phi,
+                                         const void* phib, int ncomp, void* grad, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  DIFVM_TRY(check_cls(cls));
+  if (!phi || !grad) return set_error(DIFVM_EINVAL, "null field");
+  return DIFVM_PREC_DISPATCH(prec, grad_gauss_t, m, cls, phi, phib, ncomp, grad, (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_grad_gauss_bwd(difvm_mesh_t m, difvm_prec prec, int cls,
+                                             const void* gbar, int ncomp, void* phibar,
+                                             void* phibbar, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  DIFVM_TRY(check_cls(cls));
+  if (!gbar || !phibar) return set_error(DIFVM_EINVAL, "null field");
+  return DIFVM_PREC_DISPATCH(prec, grad_gauss_bwd_t, m, cls, gbar, ncomp, phibar, phibbar,
+                             (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_div_flux(difvm_mesh_t m, difvm_prec prec, int scheme, int cls,
+                                       const void* mf, const void* phi, const void* phib, int ncomp,
+                                       void* out, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  DIFVM_TRY(check_cls(cls));
+  if (scheme != DIFVM_DIV_UPWIND && scheme != DIFVM_DIV_LINEAR)
+    return set_error(DIFVM_EINVAL, "bad scheme %d", scheme);
+  if (!mf || !phi || !out) return set_error(DIFVM_EINVAL, "null field");
+  return DIFVM_PREC_DISPATCH(prec, div_flux_t, m, scheme, cls, mf, phi, phib, ncomp, out,
+                             (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_div_flux_bwd(difvm_mesh_t m, difvm_prec prec, int scheme, int cls,
+                                           const void* mf, const void* phi, const void* phib,
+                                           int ncomp, const void* obar, void* mbar, void* phibar,
+                                           void* phibbar, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  DIFVM_TRY(check_cls(cls));
+  if (scheme != DIFVM_DIV_UPWIND && scheme != DIFVM_DIV_LINEAR)
+    return set_error(DIFVM_EINVAL, "bad scheme %d", scheme);
+  if (!mf || !phi || !obar) return set_error(DIFVM_EINVAL, "null field");
+  return DIFVM_PREC_DISPATCH(prec, div_flux_bwd_t, m, scheme, cls, mf, phi, phib, ncomp, obar,
+                             mbar, phibar, phibbar, (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_laplacian(difvm_mesh_t m, difvm_prec prec, int cls, double gamma,
+                                        const void* phi, const void* phib, const void* grad,
+                                        int ncomp, void* out, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  DIFVM_TRY(check_cls(cls));
+  if (!phi || !out) return set_error(DIFVM_EINVAL, "null field");
+  return DIFVM_PREC_DISPATCH(prec, laplacian_t, m, cls, gamma, phi, phib, grad, ncomp, out,
+                             (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_laplacian_bwd(difvm_mesh_t m, difvm_prec prec, int cls, double gamma,
+                                            const void* obar, int ncomp, void* phibar,
+                                            void* phibbar, void* gradbar, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  DIFVM_TRY(check_cls(cls));
+  if (!obar) return set_error(DIFVM_EINVAL, "null field");
+  return DIFVM_PREC_DISPATCH(prec, laplacian_bwd_t, m, cls, gamma, obar, ncomp, phibar, phibbar,
+                             gradbar, (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_laplacian_apply(difvm_mesh_t m, difvm_prec prec, const void* D,
+                                              const void* L, const void* U, const void* x,
+                                              int ncomp, int transpose, void* y, void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  if (!D || (!L && m->ni > 0) || !x || !y) return set_error(DIFVM_EINVAL, "null field");
+  if (x == y) return set_error(DIFVM_EINVAL, "x and y must not alias");
+  return DIFVM_PREC_DISPATCH(prec, ldu_apply_t, m, D, L, U, x, ncomp, transpose, y,
+                             (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_laplacian_apply_bwd(difvm_mesh_t m, difvm_prec prec, const void* D,
+                                                  const void* L, const void* U, const void* x,
+                                                  const void* ybar, int ncomp, void* xbar,
+                                                  void* Dbar, void* Lbar, void* Ubar, void* tmp,
+                                                  void* stream) {
+  DIFVM_TRY(check_common(m, prec, ncomp));
+  if (!D || (!L && m->ni > 0) || !x || !ybar) return set_error(DIFVM_EINVAL, "null field");
+  if (xbar && !tmp) return set_error(DIFVM_EINVAL, "x_bar needs a [ncomp][nc] scratch buffer");
+  return DIFVM_PREC_DISPATCH(prec, ldu_apply_bwd_t, m, D, L, U, x, ybar, ncomp, xbar, Dbar, Lbar,
+                             Ubar, tmp, (cudaStream_t)stream);
+}

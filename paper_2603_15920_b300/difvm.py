@@ -1,0 +1,494 @@
+"""Thin ctypes binding of libdifvm.so (the C ABI of include/difvm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Function names are the C names.  Field arguments are torch CUDA
+tensors in the library's internal numbering (see ``Mesh``); streams default to
+torch's current stream.  If the shared library is missing or fails to load,
+importing this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+# ---------------------------------------------------------------- constants
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT = range(8)
+F32, F64 = 0, 1
+PATCH_WALL, PATCH_INLET, PATCH_OUTLET, PATCH_EMPTY = 0, 1, 2, 3
+BC_VELOCITY, BC_PRESSURE, BC_ALL_FIXED, BC_ALL_ZEROGRAD = 0, 1, 2, 3
+DIV_UPWIND, DIV_LINEAR = 0, 1
+WK_EXACT, WK_FE, WK_BE = 0, 1, 2
+PCG, BICGSTAB = 0, 1
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
+RENUMBER_RCM, SORT_FACES = 1, 2
+
+_STATUS = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOTCONV: "ENOTCONV",
+           EBREAKDOWN: "EBREAKDOWN", ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT"}
+
+
+class DifvmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ------------------------------------------------------------------ structs
+class MeshDesc(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("n_internal", C.c_int32), ("n_faces", C.c_int32),
+                ("n_patches", C.c_int32), ("owner", C.c_void_p), ("neighbour", C.c_void_p),
+                ("Sf", C.c_void_p), ("Cf", C.c_void_p), ("V", C.c_void_p), ("C", C.c_void_p),
+                ("patch_start", C.c_void_p), ("patch_size", C.c_void_p), ("patch_type", C.c_void_p),
+                ("n_cases", C.c_int32), ("case_cell_start", C.c_void_p), ("flags", C.c_uint32),
+                ("device", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("max_iter", C.c_int32),
+                ("check_every", C.c_int32), ("tol_rel", C.c_double), ("tol_abs", C.c_double),
+                ("refine_max", C.c_int32), ("inner_tol", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("status", C.c_int32),
+                ("pad", C.c_int32), ("res0", C.c_double), ("res", C.c_double), ("bnorm", C.c_double)]
+
+
+class PisoOpts(C.Structure):
+    _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("n_corr", C.c_int32),
+                ("nonorth", C.c_int32), ("solve_U", SolveOpts), ("solve_p", SolveOpts),
+                ("pref_cell", C.c_int32), ("wk_scheme", C.c_int32), ("n_out", C.c_int32),
+                ("wk_patch", C.c_int32 * 16)]
+
+
+class PisoInfo(C.Structure):
+    _fields_ = [("itU", C.c_int32 * 3), ("itp", C.c_int32 * 4), ("status", C.c_int32),
+                ("pad", C.c_int32), ("Q", C.c_double * 16), ("p_out", C.c_double * 16)]
+
+
+SOLVE_INFO_NBYTES = C.sizeof(SolveInfo)
+PISO_INFO_NBYTES = C.sizeof(PisoInfo)
+
+# ------------------------------------------------------------------ library
+_lib = None
+_vp, _i, _d = C.c_void_p, C.c_int, C.c_double
+
+_SIGS = {
+    "difvm_mesh_create": [_vp, _vp],
+    "difvm_mesh_permutation": [_vp, _vp, _vp, _vp],
+    "difvm_mesh_info": [_vp, _vp],
+    "difvm_grad_gauss": [_vp, _i, _i, _vp, _vp, _i, _vp, _vp],
+    "difvm_grad_gauss_bwd": [_vp, _i, _i, _vp, _i, _vp, _vp, _vp],
+    "difvm_div_flux": [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp],
+    "difvm_div_flux_bwd": [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp],
+    "difvm_laplacian": [_vp, _i, _i, _d, _vp, _vp, _vp, _i, _vp, _vp],
+    "difvm_laplacian_bwd": [_vp, _i, _i, _d, _vp, _i, _vp, _vp, _vp, _vp],
+    "difvm_laplacian_apply": [_vp, _i, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp],
+    "difvm_laplacian_apply_bwd": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "difvm_krylov_workspace_bytes": [_vp, _i, _i, _i],
+    "difvm_krylov_solve": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, C.c_size_t, _vp, _vp],
+    "difvm_krylov_solve_refine": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, C.c_size_t, _vp, _vp],
+    "difvm_krylov_solve_bwd": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp,
+                               C.c_size_t, _vp, _vp],
+    "difvm_windkessel_update": [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp],
+    "difvm_windkessel_update_bwd": [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    _vp, _vp, _vp],
+    "difvm_krylov_refine_workspace_bytes": [_vp, _i, _i],
+    "difvm_piso_create": [_vp, _i, _vp, _vp],
+    "difvm_piso_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "difvm_flux_from_U": [_vp, _i, _vp, _vp, _vp, _vp],
+    "difvm_prof_start": [_i, _i],
+    "difvm_prof_stop": [_vp, _vp],
+}
+
+
+def lib():
+    """Load (building first if stale) the CUDA library; raises if unavailable."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build.stale():
+            try:
+                _build.build()
+            except Exception as e:  # nvcc missing or failed: fail loudly
+                if not os.path.exists(path):
+                    raise ImportError(f"libdifvm.so is missing and could not be built: {e}") from e
+        L = C.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is not None:
+                fn.argtypes = args
+                fn.restype = C.c_int
+        L.difvm_last_error.restype = C.c_char_p
+        L.difvm_launch_count.restype = C.c_uint64
+        L.difvm_mesh_destroy.argtypes = [_vp]
+        L.difvm_mesh_destroy.restype = None
+        for nm in ("difvm_krylov_workspace_bytes", "difvm_krylov_refine_workspace_bytes"):
+            if hasattr(L, nm):
+                getattr(L, nm).restype = C.c_size_t
+        if hasattr(L, "difvm_piso_destroy"):
+            L.difvm_piso_destroy.argtypes = [_vp]
+            L.difvm_piso_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != OK:
+        raise DifvmError(st, lib().difvm_last_error().decode())
+
+
+def launch_count() -> int:
+    return int(lib().difvm_launch_count())
+
+
+PROF_PCG_SPMV, PROF_PCG_UPDATE, PROF_PCG_PUPDATE = 1, 2, 3
+
+
+def difvm_prof_start(tag, max_launches=100000):
+    _check(lib().difvm_prof_start(tag, max_launches))
+
+
+def difvm_prof_stop():
+    """Returns (summed kernel milliseconds, number of timed launches)."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().difvm_prof_stop(C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_cuda and t.is_contiguous(), "fields must be contiguous CUDA tensors"
+        return t.data_ptr()
+    return int(t)
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _prec(t):
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+# --------------------------------------------------------------------- mesh
+class Mesh:
+    """A mesh uploaded to the GPU (difvm_mesh_create), with its numbering maps.
+
+    ``m`` is any object with the attributes of ``meshgen.Mesh`` (input
+    numbering).  ``to_cells``/``from_cells`` and friends move numpy or torch
+    data between the input numbering and the internal (RCM + sorted) one.
+    """
+
+    def __init__(self, m, device=0, flags=RENUMBER_RCM | SORT_FACES, case_cell_start=None):
+        self.src = m
+        self.device = device
+        keep = [np.ascontiguousarray(a, dt) for a, dt in (
+            (m.owner, np.int32), (m.neighbour, np.int32), (m.Sf, np.float64), (m.Cf, np.float64),
+            (m.V, np.float64), (m.C, np.float64), (m.patch_start, np.int32),
+            (m.patch_size, np.int32), (m.patch_type, np.int32))]
+        cs = None if case_cell_start is None else np.ascontiguousarray(case_cell_start, np.int32)
+        p = lambda a: None if a is None else a.ctypes.data
+        d = MeshDesc(m.n_cells, m.n_internal, int(keep[0].shape[0]), int(keep[6].shape[0]),
+                     *[p(a) for a in keep], 0 if cs is None else int(cs.shape[0] - 1), p(cs),
+                     flags, device)
+        h = C.c_void_p()
+        with torch.cuda.device(device):
+            _check(lib().difvm_mesh_create(C.byref(d), C.byref(h)))
+        self.h = h
+        info = (C.c_int64 * 6)()
+        _check(lib().difvm_mesh_info(h, info))
+        self.nc, self.ni, self.nf, self.nb, self.npatch, self.nnz = (int(v) for v in info)
+        cno = np.empty(self.nc, np.int32)
+        fon = np.empty(self.nf, np.int32)
+        flip = np.empty(self.nf, np.int8)
+        _check(lib().difvm_mesh_permutation(h, cno.ctypes.data, fon.ctypes.data, flip.ctypes.data))
+        self.cell_new_of_old, self.face_old_of_new, self.face_flip = cno, fon, flip
+        self.cell_old_of_new = np.empty_like(cno)
+        self.cell_old_of_new[cno] = np.arange(self.nc, dtype=np.int32)
+        self.face_sign = np.where(flip != 0, -1.0, 1.0)
+        self.bnd_old_of_new = fon[self.ni:] - self.ni
+        self.patch_start = np.asarray(m.patch_start, np.int64)
+        self.patch_size = np.asarray(m.patch_size, np.int64)
+        self.patch_type = np.asarray(m.patch_type, np.int64)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.difvm_mesh_destroy(h)
+            self.h = None
+
+    @property
+    def handle(self):
+        return self.h
+
+    # numbering maps (numpy or torch, leading component axes allowed)
+    def to_cells(self, x):
+        return x[..., self.cell_old_of_new] if isinstance(x, np.ndarray) else \
+            x[..., torch.as_tensor(self.cell_old_of_new, device=x.device, dtype=torch.long)]
+
+    def from_cells(self, x):
+        return x[..., self.cell_new_of_old] if isinstance(x, np.ndarray) else \
+            x[..., torch.as_tensor(self.cell_new_of_old, device=x.device, dtype=torch.long)]
+
+    def to_faces(self, f, flux=True):
+        """Input-numbered face field -> internal; fluxes change sign on flipped faces."""
+        y = f[..., self.face_old_of_new]
+        if flux:
+            y = y * (self.face_sign if isinstance(y, np.ndarray) else
+                     torch.as_tensor(self.face_sign, device=y.device, dtype=y.dtype))
+        return y
+
+    def from_faces(self, f, flux=True):
+        if flux:
+            f = f * (self.face_sign if isinstance(f, np.ndarray) else
+                     torch.as_tensor(self.face_sign, device=f.device, dtype=f.dtype))
+        out = np.empty_like(f) if isinstance(f, np.ndarray) else torch.empty_like(f)
+        out[..., self.face_old_of_new] = f
+        return out
+
+    def to_bnd(self, b):
+        return b[..., self.bnd_old_of_new] if isinstance(b, np.ndarray) else \
+            b[..., torch.as_tensor(self.bnd_old_of_new, device=b.device, dtype=torch.long)]
+
+    def from_bnd(self, b):
+        out = np.empty_like(b) if isinstance(b, np.ndarray) else torch.empty_like(b)
+        out[..., self.bnd_old_of_new] = b
+        return out
+
+
+def _mh(mesh):
+    return mesh.h if isinstance(mesh, Mesh) else mesh
+
+
+# ---------------------------------------------------------------- operators
+def difvm_grad_gauss(mesh, bc_class, phi, phi_b=None, grad=None, stream=None):
+    """grad[ncomp,3,nc] = Gauss gradient of phi[ncomp,nc] (Eq. gauss_green)."""
+    nq = phi.shape[0] if phi.dim() == 2 else 1
+    if grad is None:
+        grad = torch.empty((nq, 3, phi.shape[-1]), dtype=phi.dtype, device=phi.device)
+    _check(lib().difvm_grad_gauss(_mh(mesh), _prec(phi), bc_class, _ptr(phi), _ptr(phi_b), nq,
+                                  _ptr(grad), _stream(stream)))
+    return grad
+
+
+def difvm_grad_gauss_bwd(mesh, bc_class, grad_bar, phi_bar, phi_b_bar=None, stream=None):
+    nq = grad_bar.shape[0]
+    _check(lib().difvm_grad_gauss_bwd(_mh(mesh), _prec(grad_bar), bc_class, _ptr(grad_bar), nq,
+                                      _ptr(phi_bar), _ptr(phi_b_bar), _stream(stream)))
+
+
+def difvm_div_flux(mesh, scheme, bc_class, mflux, phi, phi_b=None, out=None, stream=None):
+    nq = phi.shape[0] if phi.dim() == 2 else 1
+    if out is None:
+        out = torch.empty_like(phi)
+    _check(lib().difvm_div_flux(_mh(mesh), _prec(phi), scheme, bc_class, _ptr(mflux), _ptr(phi),
+                                _ptr(phi_b), nq, _ptr(out), _stream(stream)))
+    return out
+
+
+def difvm_div_flux_bwd(mesh, scheme, bc_class, mflux, phi, phi_b, out_bar, mflux_bar=None,
+                       phi_bar=None, phi_b_bar=None, stream=None):
+    nq = phi.shape[0] if phi.dim() == 2 else 1
+    _check(lib().difvm_div_flux_bwd(_mh(mesh), _prec(phi), scheme, bc_class, _ptr(mflux), _ptr(phi),
+                                    _ptr(phi_b), nq, _ptr(out_bar), _ptr(mflux_bar), _ptr(phi_bar),
+                                    _ptr(phi_b_bar), _stream(stream)))
+
+
+def difvm_laplacian(mesh, bc_class, gamma, phi, phi_b=None, grad=None, out=None, stream=None):
+    nq = phi.shape[0] if phi.dim() == 2 else 1
+    if out is None:
+        out = torch.empty_like(phi)
+    _check(lib().difvm_laplacian(_mh(mesh), _prec(phi), bc_class, float(gamma), _ptr(phi),
+                                 _ptr(phi_b), _ptr(grad), nq, _ptr(out), _stream(stream)))
+    return out
+
+
+def difvm_laplacian_bwd(mesh, bc_class, gamma, out_bar, phi_bar=None, phi_b_bar=None,
+                        grad_bar=None, stream=None):
+    nq = out_bar.shape[0] if out_bar.dim() == 2 else 1
+    _check(lib().difvm_laplacian_bwd(_mh(mesh), _prec(out_bar), bc_class, float(gamma),
+                                     _ptr(out_bar), nq, _ptr(phi_bar), _ptr(phi_b_bar),
+                                     _ptr(grad_bar), _stream(stream)))
+
+
+def difvm_laplacian_apply(mesh, diag, lower, upper, x, transpose=False, y=None, stream=None):
+    nq = x.shape[0] if x.dim() == 2 else 1
+    if y is None:
+        y = torch.empty_like(x)
+    _check(lib().difvm_laplacian_apply(_mh(mesh), _prec(x), _ptr(diag), _ptr(lower), _ptr(upper),
+                                       _ptr(x), nq, int(bool(transpose)), _ptr(y), _stream(stream)))
+    return y
+
+
+def difvm_laplacian_apply_bwd(mesh, diag, lower, upper, x, y_bar, x_bar=None, diag_bar=None,
+                              lower_bar=None, upper_bar=None, stream=None):
+    nq = x.shape[0] if x.dim() == 2 else 1
+    tmp = torch.empty_like(x) if x_bar is not None else None
+    _check(lib().difvm_laplacian_apply_bwd(_mh(mesh), _prec(x), _ptr(diag), _ptr(lower),
+                                           _ptr(upper), _ptr(x), _ptr(y_bar), nq, _ptr(x_bar),
+                                           _ptr(diag_bar), _ptr(lower_bar), _ptr(upper_bar),
+                                           _ptr(tmp), _stream(stream)))
+
+
+# ------------------------------------------------------------------- Krylov
+def solve_opts(method=PCG, tol_rel=1e-10, tol_abs=0.0, max_iter=1000, precond=PRECOND_JACOBI,
+               check_every=8, refine_max=0, inner_tol=0.0):
+    return SolveOpts(method, precond, max_iter, check_every, tol_rel, tol_abs, refine_max, inner_tol)
+
+
+def decode_solve_info(buf, n):
+    raw = buf.cpu().numpy().tobytes()
+    out = []
+    for c in range(n):
+        s = SolveInfo.from_buffer_copy(raw[c * SOLVE_INFO_NBYTES:(c + 1) * SOLVE_INFO_NBYTES])
+        out.append(dict(iters=s.iters, refinements=s.refinements, status=s.status, res0=s.res0,
+                        res=s.res, bnorm=s.bnorm))
+    return out
+
+
+def _info_buf(n, device):
+    return torch.zeros(n * SOLVE_INFO_NBYTES, dtype=torch.uint8, device=device)
+
+
+def difvm_krylov_workspace_bytes(mesh, prec, method, ncomp):
+    return int(lib().difvm_krylov_workspace_bytes(_mh(mesh), prec, method, ncomp))
+
+
+def difvm_krylov_solve(mesh, diag, lower, upper, b, x, opts=None, workspace=None, stream=None,
+                       raise_on_fail=False, **kw):
+    """Solve A x = b in place (x is the initial guess).  Returns (status, [info per comp])."""
+    opts = opts or solve_opts(**kw)
+    nq = b.shape[0] if b.dim() == 2 else 1
+    prec = _prec(b)
+    nbytes = difvm_krylov_workspace_bytes(mesh, prec, opts.method, nq)
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=b.device)
+    info = _info_buf(nq, b.device)
+    st = lib().difvm_krylov_solve(_mh(mesh), prec, C.byref(opts), _ptr(diag), _ptr(lower), _ptr(upper),
+                                  _ptr(b), _ptr(x), nq, _ptr(workspace), workspace.numel(), _ptr(info),
+                                  _stream(stream))
+    if st in (EINVAL, ECUDA, ENOMEM) or (raise_on_fail and st != OK):
+        _check(st)
+    return st, decode_solve_info(info, nq)
+
+
+def difvm_krylov_solve_refine(mesh, diag32, lower32, upper32, b64, x64, opts=None, workspace=None,
+                              stream=None, **kw):
+    opts = opts or solve_opts(**kw)
+    nq = b64.shape[0] if b64.dim() == 2 else 1
+    nbytes = int(lib().difvm_krylov_refine_workspace_bytes(_mh(mesh), opts.method, nq))
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=b64.device)
+    info = _info_buf(nq, b64.device)
+    st = lib().difvm_krylov_solve_refine(_mh(mesh), C.byref(opts), _ptr(diag32), _ptr(lower32),
+                                         _ptr(upper32), _ptr(b64), _ptr(x64), nq, _ptr(workspace),
+                                         workspace.numel(), _ptr(info), _stream(stream))
+    if st in (EINVAL, ECUDA, ENOMEM):
+        _check(st)
+    return st, decode_solve_info(info, nq)
+
+
+def difvm_krylov_solve_bwd(mesh, diag, lower, upper, x, x_bar, b_bar, diag_bar=None, lower_bar=None,
+                           upper_bar=None, opts=None, workspace=None, stream=None, **kw):
+    opts = opts or solve_opts(**kw)
+    nq = x.shape[0] if x.dim() == 2 else 1
+    prec = _prec(x)
+    nbytes = difvm_krylov_workspace_bytes(mesh, prec, opts.method, nq)
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    info = _info_buf(nq, x.device)
+    st = lib().difvm_krylov_solve_bwd(_mh(mesh), prec, C.byref(opts), _ptr(diag), _ptr(lower),
+                                      _ptr(upper), _ptr(x), _ptr(x_bar), nq, _ptr(b_bar),
+                                      _ptr(diag_bar), _ptr(lower_bar), _ptr(upper_bar),
+                                      _ptr(workspace), workspace.numel(), _ptr(info), _stream(stream))
+    if st in (EINVAL, ECUDA, ENOMEM):
+        _check(st)
+    return st, decode_solve_info(info, nq)
+
+
+# --------------------------------------------------------------- Windkessel
+def difvm_windkessel_update(scheme, Rp, Cw, Rd, Q, dt, pc, p_out=None, stream=None):
+    """One RCR step on device double tensors [n_out]; pc is updated in place."""
+    n = pc.numel()
+    _check(lib().difvm_windkessel_update(n, scheme, _ptr(Rp), _ptr(Cw), _ptr(Rd), _ptr(Q), float(dt),
+                                         _ptr(pc), _ptr(p_out), _stream(stream)))
+    return pc, p_out
+
+
+def difvm_windkessel_update_bwd(scheme, Rp, Cw, Rd, Q, dt, pc_in, pc_out_bar, p_out_bar, pc_in_bar,
+                                Q_bar=None, Rp_bar=None, C_bar=None, Rd_bar=None, stream=None):
+    n = pc_in.numel()
+    _check(lib().difvm_windkessel_update_bwd(n, scheme, _ptr(Rp), _ptr(Cw), _ptr(Rd), _ptr(Q),
+                                             float(dt), _ptr(pc_in), _ptr(pc_out_bar),
+                                             _ptr(p_out_bar), _ptr(pc_in_bar), _ptr(Q_bar),
+                                             _ptr(Rp_bar), _ptr(C_bar), _ptr(Rd_bar), _stream(stream)))
+
+
+# --------------------------------------------------------------------- PISO
+def difvm_flux_from_U(mesh, U, U_b, phi=None, stream=None):
+    if phi is None:
+        phi = torch.empty(mesh.nf, dtype=U.dtype, device=U.device)
+    _check(lib().difvm_flux_from_U(_mh(mesh), _prec(U), _ptr(U), _ptr(U_b), _ptr(phi), _stream(stream)))
+    return phi
+
+
+def piso_opts(nu, dt, n_corr=2, nonorth=True, solve_U=None, solve_p=None, pref_cell=0,
+              wk_scheme=WK_EXACT, wk_patch=()):
+    o = PisoOpts()
+    o.nu, o.dt, o.n_corr, o.nonorth = float(nu), float(dt), int(n_corr), int(bool(nonorth))
+    o.solve_U = solve_U or solve_opts(BICGSTAB, 1e-10, max_iter=1000)
+    o.solve_p = solve_p or solve_opts(PCG, 1e-10, max_iter=20000)
+    o.pref_cell, o.wk_scheme, o.n_out = int(pref_cell), int(wk_scheme), len(wk_patch)
+    for k, p in enumerate(wk_patch):
+        o.wk_patch[k] = int(p)
+    return o
+
+
+def decode_piso_info(buf):
+    s = PisoInfo.from_buffer_copy(buf.cpu().numpy().tobytes())
+    return dict(itU=list(s.itU), itp=list(s.itp), status=s.status, Q=list(s.Q), p_out=list(s.p_out))
+
+
+class Piso:
+    """difvm_piso_create / difvm_piso_step on one mesh and precision."""
+
+    def __init__(self, mesh, prec, opts):
+        self.mesh, self.prec, self.opts = mesh, prec, opts
+        h = C.c_void_p()
+        _check(lib().difvm_piso_create(_mh(mesh), prec, C.byref(opts), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.difvm_piso_destroy(h)
+            self.h = None
+
+    def step(self, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
+        """One PISO step in place.  Returns (status, info buffer on device)."""
+        if info is None:
+            info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U.device)
+        st = lib().difvm_piso_step(self.h, _ptr(U), _ptr(p), _ptr(phi), _ptr(U_b), _ptr(p_b), _ptr(wk),
+                                   _ptr(info), _stream(stream))
+        if st in (EINVAL, ECUDA, ENOMEM):
+            _check(st)
+        return st, info
+
+
+def difvm_piso_step(piso, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
+    return piso.step(U, p, phi, U_b, p_b, wk, info, stream)

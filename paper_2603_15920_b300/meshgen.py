@@ -84,7 +84,8 @@ class Mesh:
         assert self.Sf.shape == (nf, 3) and self.Cf.shape == (nf, 3)
         assert self.V.shape == (nc,) and self.C.shape == (nc, 3)
         assert self.owner.min() >= 0 and self.owner.max() < nc
-        assert self.neighbour.min() >= 0 and self.neighbour.max() < nc
+        if ni > 0:
+            assert self.neighbour.min() >= 0 and self.neighbour.max() < nc
         assert np.all(self.V > 0)
         assert int(self.patch_start[0]) == ni
         assert int(self.patch_start[-1] + self.patch_size[-1]) == nf

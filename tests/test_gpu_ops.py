@@ -1,0 +1,336 @@
+"""GPU parity of the face operators against the CPU oracle (element by element).
+
+Meshes are shuffled (random cell / face numbering) so that the library's RCM
+renumbering, face re-orientation and sorting are exercised; every comparison
+is made in the input numbering after mapping the GPU result back.  Sizes span
+many 256-thread blocks with a ragged tail; the full 64^3 Kuhn mesh is checked
+at the launch configuration the benchmark uses.
+Tolerances: FP64 1e-12 and FP32 1e-5, normwise relative
+||x_gpu - x_ref||_inf / ||x_ref||_inf.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_15920_b300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2603_15920_b300 import difvm as D  # noqa: E402
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+DTYPES = [torch.float64, torch.float32]
+
+
+def nrel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def cuda(x, dt):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda").contiguous()
+
+
+MESHES = {
+    "kuhn10": lambda: mg.shuffle(mg.kuhn_cube(10, 0.2, 3, patch_types=dict(x0=mg.INLET, x1=mg.OUTLET)), 11),
+    "channel": lambda: mg.channel_2d(32, 8, seed=4),
+    "dbox": lambda: mg.shuffle(mg.distorted_box(9, 0.05, patch_types=dict(y1=mg.OUTLET)), 2),
+    "pipe": lambda: mg.pipe_ohgrid(8, 4, 6),
+}
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        m = MESHES[name]()
+        _cache[name] = (m, O.OMesh.from_mesh(m), D.Mesh(m))
+    return _cache[name]
+
+
+def bc_table(om, cls):
+    return {D.BC_VELOCITY: om.bc_U(), D.BC_PRESSURE: om.bc_p(),
+            D.BC_ALL_FIXED: np.where(om.patch_type == O.PT_EMPTY, O.BC_EMPTY, O.BC_FIXED).astype(np.int32),
+            D.BC_ALL_ZEROGRAD: np.where(om.patch_type == O.PT_EMPTY, O.BC_EMPTY, O.BC_ZEROGRAD).astype(np.int32)}[cls]
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_mesh_create_maps(name):
+    m, om, dm = get(name)
+    assert dm.nc == m.n_cells and dm.nf == m.n_faces
+    assert sorted(dm.cell_new_of_old.tolist()) == list(range(m.n_cells))
+    assert sorted(dm.face_old_of_new.tolist()) == list(range(m.n_faces))
+    # boundary faces stay inside their patch
+    for p in range(m.n_patches):
+        s, z = int(m.patch_start[p]), int(m.patch_size[p])
+        assert set(dm.face_old_of_new[s:s + z].tolist()) == set(range(s, s + z))
+    assert dm.nnz == 2 * m.n_internal + m.n_boundary
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("cls", [D.BC_VELOCITY, D.BC_PRESSURE, D.BC_ALL_FIXED, D.BC_ALL_ZEROGRAD])
+def test_grad_gauss(name, cls, dt):
+    m, om, dm = get(name)
+    f = mg.random_fields(m, 1)
+    for nq in (1, 3):
+        phi = f["U"][:nq]
+        phib = f["U_b"][:nq]
+        ref = O.grad_gauss(om, bc_table(om, cls), phi, phib)
+        out = D.difvm_grad_gauss(dm, cls, cuda(dm.to_cells(phi), dt), cuda(dm.to_bnd(phib), dt))
+        got = dm.from_cells(out.double().cpu().numpy())
+        assert nrel(got, ref) < TOL[dt], (nq, nrel(got, ref))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("scheme", [D.DIV_UPWIND, D.DIV_LINEAR])
+def test_div_flux(name, scheme, dt):
+    m, om, dm = get(name)
+    f = mg.random_fields(m, 2)
+    mflux = f["m"].copy()
+    mflux[::17] = 0.0                     # upwind tie: m = 0 takes the owner value
+    for cls in (D.BC_VELOCITY, D.BC_PRESSURE):
+        for nq in (1, 3):
+            ref = O.div_flux(om, bc_table(om, cls), scheme, mflux, f["U"][:nq], f["U_b"][:nq])
+            out = D.difvm_div_flux(dm, scheme, cls, cuda(dm.to_faces(mflux), dt),
+                                   cuda(dm.to_cells(f["U"][:nq]), dt), cuda(dm.to_bnd(f["U_b"][:nq]), dt))
+            got = dm.from_cells(out.double().cpu().numpy())
+            assert nrel(got, ref) < TOL[dt] * 4, (cls, nq, nrel(got, ref))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("nonorth", [False, True])
+def test_laplacian(name, nonorth, dt):
+    m, om, dm = get(name)
+    f = mg.random_fields(m, 3)
+    rng = np.random.default_rng(5)
+    for cls in (D.BC_VELOCITY, D.BC_PRESSURE, D.BC_ALL_FIXED):
+        for nq in (1, 3):
+            g = rng.standard_normal((nq, 3, m.n_cells)) if nonorth else None
+            ref = O.laplacian(om, bc_table(om, cls), 0.37, f["U"][:nq], f["U_b"][:nq], g)
+            out = D.difvm_laplacian(dm, cls, 0.37, cuda(dm.to_cells(f["U"][:nq]), dt),
+                                    cuda(dm.to_bnd(f["U_b"][:nq]), dt),
+                                    None if g is None else cuda(dm.to_cells(g), dt))
+            got = dm.from_cells(out.double().cpu().numpy())
+            assert nrel(got, ref) < TOL[dt] * 4, (cls, nq, nrel(got, ref))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("name", list(MESHES))
+def test_laplacian_apply(name, dt):
+    m, om, dm = get(name)
+    rng = np.random.default_rng(6)
+    Dg, L, U = rng.standard_normal(m.n_cells), rng.standard_normal(m.n_internal), rng.standard_normal(m.n_internal)
+    x = rng.standard_normal((3, m.n_cells))
+    # internal numbering of face coefficients: lower/upper swap on flipped faces
+    flip = dm.face_flip[:m.n_internal] != 0
+    Li = np.where(flip, U[dm.face_old_of_new[:m.n_internal]], L[dm.face_old_of_new[:m.n_internal]])
+    Ui = np.where(flip, L[dm.face_old_of_new[:m.n_internal]], U[dm.face_old_of_new[:m.n_internal]])
+    for nq in (1, 2, 3):
+        for tr in (False, True):
+            ref = O.ldu_apply(om, Dg, U if tr else L, L if tr else U, x[:nq])
+            out = D.difvm_laplacian_apply(dm, cuda(dm.to_cells(Dg), dt), cuda(Li, dt), cuda(Ui, dt),
+                                          cuda(dm.to_cells(x[:nq]), dt), transpose=tr)
+            got = dm.from_cells(out.double().cpu().numpy())
+            assert nrel(got, ref) < TOL[dt], (nq, tr, nrel(got, ref))
+        ref = O.ldu_apply(om, Dg, L, None, x[:nq])       # symmetric: one coefficient per face
+        out = D.difvm_laplacian_apply(dm, cuda(dm.to_cells(Dg), dt), cuda(L[dm.face_old_of_new[:m.n_internal]], dt),
+                                      None, cuda(dm.to_cells(x[:nq]), dt))
+        assert nrel(dm.from_cells(out.double().cpu().numpy()), ref) < TOL[dt]
+
+
+def test_operators_are_deterministic():
+    m, om, dm = get("kuhn10")
+    f = mg.random_fields(m, 7)
+    phi = cuda(dm.to_cells(f["U"]), torch.float64)
+    phib = cuda(dm.to_bnd(f["U_b"]), torch.float64)
+    a = D.difvm_grad_gauss(dm, D.BC_VELOCITY, phi, phib)
+    b = D.difvm_grad_gauss(dm, D.BC_VELOCITY, phi, phib)
+    assert torch.equal(a, b)
+
+
+def test_constant_field_conservation_bitwise_antisymmetry():
+    # the owner and neighbour see bitwise the same face message: the sum of a
+    # divergence over all cells equals the boundary flux up to summation rounding
+    m, om, dm = get("kuhn10")
+    f = mg.random_fields(m, 8)
+    mf = cuda(dm.to_faces(f["m"]), torch.float64)
+    phi = cuda(dm.to_cells(f["phi"]), torch.float64)
+    out = D.difvm_div_flux(dm, D.DIV_LINEAR, D.BC_ALL_ZEROGRAD, mf, phi).cpu().numpy()
+    ob = dm.to_cells(np.arange(m.n_cells))  # noqa: F841
+    bflux = (f["m"][m.n_internal:] * f["phi"][m.owner[m.n_internal:]]).sum()
+    assert abs(out.sum() - bflux) < 1e-11 * np.abs(out).sum()
+
+
+def test_bad_arguments_raise():
+    m, om, dm = get("channel")
+    phi = torch.zeros(5, 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(D.DifvmError) as e:     # unknown bc class
+        D._check(D.lib().difvm_grad_gauss(dm.h, 1, 9, phi.data_ptr(), None, 1, phi.data_ptr(), None))
+    assert e.value.status == D.EINVAL
+    with pytest.raises(D.DifvmError):          # ncomp out of range
+        D._check(D.lib().difvm_grad_gauss(dm.h, 1, 0, phi.data_ptr(), None, 4, phi.data_ptr(), None))
+    with pytest.raises(D.DifvmError):          # bad precision
+        D._check(D.lib().difvm_grad_gauss(dm.h, 7, 0, phi.data_ptr(), None, 1, phi.data_ptr(), None))
+
+
+def test_mesh_create_rejects_bad_meshes():
+    m = mg.kuhn_cube(2, 0.0, 0)
+    bad = mg.Mesh(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in m.__dict__.items()})
+    bad.neighbour[3] = m.n_cells + 5
+    with pytest.raises(D.DifvmError, match="out of range"):
+        D.Mesh(bad)
+    bad = mg.Mesh(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in m.__dict__.items()})
+    bad.Sf[7] *= -1.0                           # area vector pointing into the owner
+    with pytest.raises(D.DifvmError, match="S.d"):
+        D.Mesh(bad)
+    bad = mg.Mesh(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in m.__dict__.items()})
+    bad.V[0] = 0.0
+    with pytest.raises(D.DifvmError, match="not positive"):
+        D.Mesh(bad)
+
+
+def test_single_cell_mesh():
+    # no internal faces at all: every operator reduces boundary faces only
+    m = mg.hex_box(1, 1, 1, (1.0, 2.0, 3.0))
+    om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
+    phib = np.arange(6.0)[None]
+    ref = O.grad_gauss(om, O.BC_FIXED, np.ones((1, 1)), phib)
+    got = D.difvm_grad_gauss(dm, D.BC_ALL_FIXED, cuda(np.ones((1, 1)), torch.float64),
+                             cuda(dm.to_bnd(phib), torch.float64)).cpu().numpy()
+    assert nrel(got, ref) < 1e-14
+
+
+# ------------------------------------------------------------------ adjoints
+def _dense_T(apply, n_in, w):
+    """Oracle J^T w for a linear map, built column by column from unit vectors."""
+    out = np.zeros(n_in)
+    for k in range(n_in):
+        e = np.zeros(n_in); e[k] = 1.0
+        out[k] = np.dot(apply(e).ravel(), w.ravel())
+    return out
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    m = mg.shuffle(mg.kuhn_cube(3, 0.2, 9, patch_types=dict(x0=mg.INLET, x1=mg.OUTLET)), 3)
+    return m, O.OMesh.from_mesh(m), D.Mesh(m)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("cls", [D.BC_VELOCITY, D.BC_PRESSURE])
+def test_grad_gauss_bwd_is_oracle_transpose(tiny, cls, dt):
+    m, om, dm = tiny
+    nc, nb = m.n_cells, m.n_boundary
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal((1, 3, nc))
+    bc = bc_table(om, cls)
+    ref_phi = _dense_T(lambda e: O.grad_gauss(om, bc, e, np.zeros(nb)), nc, w)
+    ref_pb = _dense_T(lambda e: O.grad_gauss(om, bc, np.zeros(nc), e), nb, w)
+    pbar = torch.zeros(1, nc, dtype=dt, device="cuda")
+    pbbar = torch.zeros(1, nb, dtype=dt, device="cuda")
+    D.difvm_grad_gauss_bwd(dm, cls, cuda(dm.to_cells(w), dt), pbar, pbbar)
+    assert nrel(dm.from_cells(pbar.double().cpu().numpy())[0], ref_phi) < TOL[dt] * 10
+    if np.abs(ref_pb).max() > 0:
+        assert nrel(dm.from_bnd(pbbar.double().cpu().numpy())[0], ref_pb) < TOL[dt] * 10
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("scheme", [D.DIV_UPWIND, D.DIV_LINEAR])
+def test_div_flux_bwd_is_oracle_transpose(tiny, scheme, dt):
+    m, om, dm = tiny
+    nc, nb, nf = m.n_cells, m.n_boundary, m.n_faces
+    rng = np.random.default_rng(2)
+    mf = rng.standard_normal(nf); phi = rng.standard_normal(nc); pb = rng.standard_normal(nb)
+    w = rng.standard_normal(nc)
+    bc = om.bc_U()
+    ref_phi = _dense_T(lambda e: O.div_flux(om, bc, scheme, mf, e, np.zeros(nb)), nc, w)
+    ref_pb = _dense_T(lambda e: O.div_flux(om, bc, scheme, mf, np.zeros(nc), e), nb, w)
+    ref_m = _dense_T(lambda e: O.div_flux(om, bc, scheme, e * 1.0, phi, pb)
+                     if scheme == D.DIV_LINEAR else
+                     # upwind is piecewise linear in m: differentiate at the current m
+                     (O.div_flux(om, bc, scheme, mf + 1e-3 * e, phi, pb)
+                      - O.div_flux(om, bc, scheme, mf - 1e-3 * e, phi, pb)) / 2e-3, nf, w)
+    mbar = torch.zeros(nf, dtype=dt, device="cuda")
+    pbar = torch.zeros(1, nc, dtype=dt, device="cuda")
+    pbbar = torch.zeros(1, nb, dtype=dt, device="cuda")
+    D.difvm_div_flux_bwd(dm, scheme, D.BC_VELOCITY, cuda(dm.to_faces(mf), dt), cuda(dm.to_cells(phi)[None], dt),
+                         cuda(dm.to_bnd(pb)[None], dt), cuda(dm.to_cells(w)[None], dt), mbar, pbar, pbbar)
+    tol = TOL[dt] * 10 if scheme == D.DIV_LINEAR else max(TOL[dt] * 10, 1e-9)
+    assert nrel(dm.from_cells(pbar.double().cpu().numpy())[0], ref_phi) < TOL[dt] * 10
+    assert nrel(dm.from_bnd(pbbar.double().cpu().numpy())[0], ref_pb) < TOL[dt] * 10
+    assert nrel(dm.from_faces(mbar.double().cpu().numpy()), ref_m) < tol
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_laplacian_bwd_is_oracle_transpose(tiny, dt):
+    m, om, dm = tiny
+    nc, nb = m.n_cells, m.n_boundary
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal(nc)
+    bc = om.bc_U()
+    g0 = np.zeros((1, 3, nc))
+    ref_phi = _dense_T(lambda e: O.laplacian(om, bc, 0.7, e, np.zeros(nb), g0), nc, w)
+    ref_pb = _dense_T(lambda e: O.laplacian(om, bc, 0.7, np.zeros(nc), e, g0), nb, w)
+    ref_g = _dense_T(lambda e: O.laplacian(om, bc, 0.7, np.zeros(nc), np.zeros(nb), e.reshape(1, 3, nc)), 3 * nc, w)
+    pbar = torch.zeros(1, nc, dtype=dt, device="cuda")
+    pbbar = torch.zeros(1, nb, dtype=dt, device="cuda")
+    gbar = torch.zeros(1, 3, nc, dtype=dt, device="cuda")
+    D.difvm_laplacian_bwd(dm, D.BC_VELOCITY, 0.7, cuda(dm.to_cells(w)[None], dt), pbar, pbbar, gbar)
+    assert nrel(dm.from_cells(pbar.double().cpu().numpy())[0], ref_phi) < TOL[dt] * 10
+    assert nrel(dm.from_bnd(pbbar.double().cpu().numpy())[0], ref_pb) < TOL[dt] * 10
+    assert nrel(dm.from_cells(gbar.double().cpu().numpy()).ravel(), ref_g) < TOL[dt] * 10
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("sym", [False, True])
+def test_laplacian_apply_bwd_dot_product(tiny, sym, dt):
+    m, om, dm = tiny
+    rng = np.random.default_rng(4)
+    nc, ni = dm.nc, dm.ni
+    Dg = cuda(rng.standard_normal(nc), dt)
+    L = cuda(rng.standard_normal(ni), dt)
+    U = None if sym else cuda(rng.standard_normal(ni), dt)
+    x = cuda(rng.standard_normal((2, nc)), dt)
+    ybar = cuda(rng.standard_normal((2, nc)), dt)
+    xbar = torch.zeros_like(x)
+    Dbar, Lbar = torch.zeros_like(Dg), torch.zeros_like(L)
+    Ubar = None if sym else torch.zeros_like(L)
+    D.difvm_laplacian_apply_bwd(dm, Dg, L, U, x, ybar, xbar, Dbar, Lbar, Ubar)
+    y = D.difvm_laplacian_apply(dm, Dg, L, U, x)
+    # <A x, ybar> = <x, A^T ybar>, and the bilinear form's coefficient gradients
+    tol = TOL[dt] * 100
+    lhs = (y.double() * ybar.double()).sum().item()
+    assert abs(lhs - (x.double() * xbar.double()).sum().item()) < tol * abs(lhs) + tol
+    coef = (Dg.double() * Dbar.double()).sum() + (L.double() * Lbar.double()).sum()
+    if not sym:
+        coef = coef + (U.double() * Ubar.double()).sum()
+    assert abs(lhs - coef.item()) < tol * abs(lhs) + tol
+
+
+# ---------------------------------------------------------- full-size (64^3)
+@pytest.fixture(scope="module")
+def kuhn64():
+    m = mg.kuhn_cube(64, 0.2, 0)
+    return m, O.OMesh.from_mesh(m), D.Mesh(m)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_full_size_operators(kuhn64, dt):
+    m, om, dm = kuhn64
+    f = mg.random_fields(m, 0)
+    phi, phib = f["phi"], f["phi_b"]
+    ref = O.grad_gauss(om, om.bc_U(), phi, phib)
+    got = dm.from_cells(D.difvm_grad_gauss(dm, D.BC_VELOCITY, cuda(dm.to_cells(phi), dt),
+                                           cuda(dm.to_bnd(phib), dt)).double().cpu().numpy())
+    assert nrel(got, ref) < TOL[dt]
+    ref = O.div_flux(om, om.bc_U(), O.DIV_UPWIND, f["m"], f["U"], f["U_b"])
+    got = dm.from_cells(D.difvm_div_flux(dm, D.DIV_UPWIND, D.BC_VELOCITY, cuda(dm.to_faces(f["m"]), dt),
+                                         cuda(dm.to_cells(f["U"]), dt), cuda(dm.to_bnd(f["U_b"]), dt)
+                                         ).double().cpu().numpy())
+    assert nrel(got, ref) < TOL[dt] * 4
