@@ -53,9 +53,9 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-def make_mesh(n=N_KUHN):
+def make_mesh(n=None):
     from paper_2603_15920_b300 import meshgen as mg
-    return mg.kuhn_cube(n, JITTER, SEED)
+    return mg.kuhn_cube(n or N_KUHN, JITTER, SEED)
 
 
 def lid_bc(m):
@@ -184,7 +184,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    m = make_mesh()
+    m = make_mesh(args.mesh)
     dm = D.Mesh(m, device=local)
     Ub_h = lid_bc(m)
     pref = int(dm.cell_new_of_old[0])
@@ -266,6 +266,12 @@ def run_ours(args):
         except Exception:
             traffic = None
 
+    if args.only_f32:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "steps/s", "ms_per_step": ms_step,
+                              "mesh": args.mesh, "status": int(r32["status"]),
+                              "pcg_spmv_avg_us": avg_ms * 1e3, "info": r32["info"]}), flush=True)
+        return 0
     # plain FP64 form, same workload (fewer steps: it is the slow form)
     r64 = timed(D.F64, 3, max(2, min(K, 5)))
     ms64 = r64["ms"] / max(2, min(K, 5))
@@ -342,6 +348,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--mesh", type=int, default=N_KUHN, help="Kuhn hex grid size n (n^3 hexes)")
+    ap.add_argument("--only-f32", action="store_true",
+                    help="time only the F32 form (no F64 or end-to-end legs; for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

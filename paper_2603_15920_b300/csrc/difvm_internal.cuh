@@ -74,6 +74,18 @@ struct Topo {
   const uint16_t* bpatch;  // [nb] patch id
 };
 
+// Sliced-ELL (slice height 32) layout of the off-diagonal entries of the
+// LDU operator, used inside the Krylov solvers: row i lives in slice i/32 at
+// lane i%32; slot k of the row is at soff[slice] + 32 k + lane.  col is the
+// column (the row itself on padding), map the source entry (face << 1 | side,
+// side 1 = row is the neighbour) or -1 on padding.
+struct Ell {
+  int nsl;
+  const int* soff;  // [nsl+1]
+  const int* col;   // [nslots]
+  const int* map;   // [nslots]
+};
+
 __device__ __forceinline__ int face_kind(const Topo& t, int b, int cls) {
   return (t.bkind[b] >> (2 * cls)) & 3;
 }
@@ -97,6 +109,11 @@ struct difvm_mesh {
   int* cent = nullptr;
   uint8_t* bkind = nullptr;
   uint16_t* bpatch = nullptr;
+  int ell_nsl = 0;
+  int64_t ell_nslots = 0;
+  int* ell_soff = nullptr;
+  int* ell_col = nullptr;
+  int* ell_map = nullptr;
   difvm::V4<double>* Sw64 = nullptr;
   difvm::V4<double>* ck64 = nullptr;
   difvm::V4<float>* Sw32 = nullptr;
@@ -108,6 +125,7 @@ struct difvm_mesh {
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
   }
+  difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_soff, ell_col, ell_map}; }
   difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }
   difvm::Geo<float> geo32() const { return {Sw32, ck32, V32, rV32}; }
 };

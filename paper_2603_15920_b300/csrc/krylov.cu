@@ -46,11 +46,22 @@ struct KWork {
   double tol_rel, tol_abs;
 };
 
+// Matrix inside the solvers: diagonal + sliced-ELL off-diagonal values (filled
+// from the LDU face coefficients once per solve by k_ell_fill).
 template <typename T> struct Mat {
   const T* D;
-  const T* L;  // coefficient of x_O in row N
-  const T* U;  // coefficient of x_N in row O
+  Ell E;
+  const T* val;  // [nslots]
 };
+
+// val[slot] = side ? L_f : U_f  (row N holds L_f x_O, row O holds U_f x_N); 0 on padding
+template <typename T>
+__global__ void k_ell_fill(int nslots, const int* map, const T* L, const T* U, T* val) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nslots) return;
+  const int e = map[k];
+  val[k] = e < 0 ? T(0) : ((e & 1) ? L[e >> 1] : U[e >> 1]);
+}
 
 // ---------------------------------------------------------- accumulators
 template <typename T> struct DotAcc;
@@ -148,15 +159,14 @@ __device__ __forceinline__ void spmv_row(const Topo& t, const Mat<T>& A, int i, 
   const T d = __ldg(A.D + i);
 #pragma unroll
   for (int c = 0; c < NC; ++c) y[c] = (act >> c & 1) ? d * __ldg(x + c * nc + i) : T(0);
-  const int e1 = __ldg(t.cptr + i + 1);
-  for (int e = __ldg(t.cptr + i); e < e1; ++e) {
-    const int ent = __ldg(t.cent + e);
-    const int f = ent >> 1;
-    if (f >= t.ni) break;
-    const int2 on = __ldg(t.on + f);
-    const bool nside = ent & 1;
-    const int j = nside ? on.x : on.y;
-    const T a = nside ? __ldg(A.L + f) : __ldg(A.U + f);
+  const int sl = i >> 5, lane = i & 31;
+  const int o = __ldg(A.E.soff + sl), w = (__ldg(A.E.soff + sl + 1) - o) >> 5;
+  const int* col = A.E.col + o + lane;
+  const T* val = A.val + o + lane;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) {
+    const int j = __ldg(col + 32 * k);
+    const T a = __ldg(val + 32 * k);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
       if (act >> c & 1) y[c] += a * __ldg(x + c * nc + j);
@@ -581,7 +591,7 @@ __global__ void k_write_info(int ncomp, const KState* st, difvm_solve_info* info
 
 // ------------------------------------------------------------- workspace
 struct WsLayout {
-  size_t vec_bytes, n_vec, state_off, part_off, ticket_off, total;
+  size_t vec_bytes, n_vec, val_off, state_off, part_off, ticket_off, total;
 };
 
 static int grid_for(const difvm_mesh* m) {
@@ -589,16 +599,28 @@ static int grid_for(const difvm_mesh* m) {
   return std::max(1, std::min(need, m->num_sms * 8));
 }
 
+static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// [vectors | ELL values | solver states | block partials | ticket]
 static WsLayout layout(const difvm_mesh* m, size_t elt, int method, int ncomp) {
   WsLayout L;
-  L.vec_bytes = ((size_t)m->nc * elt + 255) / 256 * 256;
+  L.vec_bytes = up256((size_t)m->nc * elt);
   // PCG: r p q (per comp) + rD;  BiCGStab: r rh p v s t y z (per comp) + rD
   L.n_vec = (method == DIFVM_PCG ? 3 : 8) * (size_t)ncomp + 1;
-  L.state_off = L.n_vec * L.vec_bytes;
+  L.val_off = L.n_vec * L.vec_bytes;
+  L.state_off = L.val_off + up256((size_t)std::max<int64_t>(m->ell_nslots, 1) * elt);
   L.part_off = L.state_off + 256 * 4;
-  L.ticket_off = L.part_off + (size_t)grid_for(m) * kMaxParts * sizeof(double);
+  L.ticket_off = L.part_off + up256((size_t)grid_for(m) * kMaxParts * sizeof(double));
   L.total = L.ticket_off + 256;
   return L;
+}
+
+template <typename T>
+static difvm_status fill_ell(difvm_mesh_t m, const T* L, const T* U, T* val, cudaStream_t st) {
+  if (m->ell_nslots == 0) return DIFVM_OK;
+  k_ell_fill<T><<<blocks_for(m->ell_nslots, 256), 256, 0, st>>>((int)m->ell_nslots, m->ell_map, L,
+                                                                 U ? U : L, val);
+  return check_launch("ell_fill");
 }
 
 }  // namespace difvm
@@ -612,14 +634,7 @@ extern "C" size_t difvm_krylov_workspace_bytes(difvm_mesh_t m, difvm_prec prec, 
 
 namespace difvm {
 
-template <typename T, int NC>
-static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A, const T* b, T* x,
-                             char* ws, const WsLayout& L, difvm_solve_info* info, int refinements,
-                             cudaStream_t st, KState* host_state) {
-  const int nc = m->nc;
-  const int G = grid_for(m);
-  Topo t = m->topo();
-  auto vec = [&](int k) { return (T*)(ws + (size_t)k * L.vec_bytes); };
+static KWork make_work(char* ws, const WsLayout& L, const difvm_solve_opts* o) {
   KWork w;
   w.st = (KState*)(ws + L.state_off);
   w.part = (double*)(ws + L.part_off);
@@ -627,17 +642,32 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
   w.maxit = o->max_iter > 0 ? o->max_iter : 1000;
   w.tol_rel = o->tol_rel;
   w.tol_abs = o->tol_abs;
+  return w;
+}
+
+template <int NC>
+static difvm_status read_states(KState* host, const KWork& w, cudaStream_t st, bool& all_done) {
+  DIFVM_CUDA(cudaMemcpyAsync(host, w.st, sizeof(KState) * NC, cudaMemcpyDeviceToHost, st));
+  DIFVM_CUDA(cudaStreamSynchronize(st));
+  all_done = true;
+  for (int c = 0; c < NC; ++c) all_done &= host[c].done != 0;
+  return DIFVM_OK;
+}
+
+template <typename T, int NC>
+static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A, const T* b, T* x,
+                             char* ws, const WsLayout& L, difvm_solve_info* info, cudaStream_t st,
+                             KState* host_state) {
+  const int nc = m->nc;
+  const int G = grid_for(m);
+  Topo t = m->topo();
+  auto vec = [&](int k) { return (T*)(ws + (size_t)k * L.vec_bytes); };
+  KWork w = make_work(ws, L, o);
   const int jac = o->precond != DIFVM_PRECOND_NONE;
   const int chunk = o->check_every > 0 ? o->check_every : 8;
   DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
   T* rD = vec(L.n_vec - 1);
-  auto all_done = [&](bool& done) -> difvm_status {
-    DIFVM_CUDA(cudaMemcpyAsync(host_state, w.st, sizeof(KState) * NC, cudaMemcpyDeviceToHost, st));
-    DIFVM_CUDA(cudaStreamSynchronize(st));
-    done = true;
-    for (int c = 0; c < NC; ++c) done &= host_state[c].done != 0;
-    return DIFVM_OK;
-  };
+  bool done = false;
   if (o->method == DIFVM_PCG) {
     T *r = vec(0), *p = vec(NC), *q = vec(2 * NC);
     k_pcg_init<T, NC><<<G, kKB, 0, st>>>(t, A, jac, b, x, r, p, rD, w);
@@ -645,7 +675,6 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
     int it = 0;
-    bool done = false;
     while (it < w.maxit) {
       int n = std::min(chunk, w.maxit - it);
       for (int k = 0; k < n; ++k) {
@@ -662,7 +691,7 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
         DIFVM_TRY(check_launch("pcg_iter"));
       }
       it += n;
-      DIFVM_TRY(all_done(done));
+      DIFVM_TRY(read_states<NC>(host_state, w, st, done));
       if (done) break;
     }
   } else if (o->method == DIFVM_BICGSTAB) {
@@ -673,7 +702,6 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
     int it = 0;
-    bool done = false;
     while (it < w.maxit) {
       int n = std::min(chunk, w.maxit - it);
       for (int k = 0; k < n; ++k) {
@@ -689,184 +717,233 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
         DIFVM_TRY(check_launch("bicg_iter"));
       }
       it += n;
-      DIFVM_TRY(all_done(done));
+      DIFVM_TRY(read_states<NC>(host_state, w, st, done));
       if (done) break;
     }
   } else {
     return set_error(DIFVM_EINVAL, "unknown Krylov method %d", o->method);
   }
   if (info) {
-    k_write_info<<<1, 32, 0, st>>>(NC, w.st, info, refinements);
+    k_write_info<<<1, 32, 0, st>>>(NC, w.st, info, 0);
     DIFVM_TRY(check_launch("write_info"));
   }
-  DIFVM_CUDA(cudaMemcpyAsync(host_state, w.st, sizeof(KState) * NC, cudaMemcpyDeviceToHost, st));
-  DIFVM_CUDA(cudaStreamSynchronize(st));
+  DIFVM_TRY(read_states<NC>(host_state, w, st, done));
   int worst = DIFVM_OK;
   for (int c = 0; c < NC; ++c) worst = std::max(worst, host_state[c].status);
   return (difvm_status)worst;
 }
 
-}  // namespace difvm
+// ------------------------------------- mixed precision: reliable-update PCG
+// Single-RHS CG whose inner arithmetic (SpMV, vector updates, preconditioner)
+// is FP32 while the solution is accumulated in FP64 and the residual is
+// periodically REPLACED by the true FP64 residual r = b - A x64 (FP32 matrix
+// values are exact in FP64).  This is the iterative-refinement residual of the
+// pressure solve done without restarting the Krylov space (residual
+// replacement, van der Vorst & Ye, SIAM J. Sci. Comput. 22 (2000)): p keeps its
+// recursive update, r is replaced whenever the recursive residual norm has
+// dropped by 1e-2 since the last replacement, has reached the tolerance, or the
+// iteration cap is hit; the solve ends only when the TRUE FP64 residual meets
+// ||r|| <= max(tol_rel ||b||, tol_abs).
 
-namespace difvm {
-
-// ------------------------------------------------- mixed-precision refinement
-// r64 = b64 - A x64 in FP64 (FP32 coefficients are exact in FP64), r32 = r64,
-// e32 = 0; convergence of the outer iteration on ||r64||.
-template <int NC>
-__global__ void __launch_bounds__(kKB) k_refine_residual(Topo t, Mat<float> A, const double* b,
-                                                         const double* x, float* r32, float* e32,
-                                                         KWork w, int first) {
+// init: r64 = b - A x64, r = (float) r64, p = rD r; bb, rr (FP64), rz
+__global__ void __launch_bounds__(kKB) k_rr_init(Topo t, Mat<float> A, int jacobi, const double* b,
+                                                 const double* x, float* r, float* p, float* rD,
+                                                 KWork w) {
   const int nc = t.nc;
-  double bb[NC], rr[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) bb[c] = rr[c] = 0.0;
+  double bb = 0.0, rr = 0.0;
+  DotAcc<float> rz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    double y[NC];
-    const double d = (double)__ldg(A.D + i);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) y[c] = d * x[c * nc + i];
-    const int e1 = __ldg(t.cptr + i + 1);
-    for (int e = __ldg(t.cptr + i); e < e1; ++e) {
-      const int ent = __ldg(t.cent + e);
-      const int f = ent >> 1;
-      if (f >= t.ni) break;
-      const int2 on = __ldg(t.on + f);
-      const bool nside = ent & 1;
-      const int j = nside ? on.x : on.y;
-      const double a = (double)(nside ? __ldg(A.L + f) : __ldg(A.U + f));
-#pragma unroll
-      for (int c = 0; c < NC; ++c) y[c] = fma(a, x[c * nc + j], y[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const double bi = b[c * nc + i];
-      const double ri = bi - y[c];
-      r32[c * nc + i] = (float)ri;
-      e32[c * nc + i] = 0.f;
-      rr[c] = fma(ri, ri, rr[c]);
-      bb[c] = fma(bi, bi, bb[c]);
-    }
+    const float di = __ldg(A.D + i);
+    const float rd = jacobi ? 1.f / di : 1.f;
+    rD[i] = rd;
+    double y = (double)di * x[i];
+    const int sl = i >> 5, lane = i & 31;
+    const int o = __ldg(A.E.soff + sl), wd = (__ldg(A.E.soff + sl + 1) - o) >> 5;
+    for (int k = 0; k < wd; ++k)
+      y = fma((double)__ldg(A.val + o + lane + 32 * k), x[__ldg(A.E.col + o + lane + 32 * k)], y);
+    const double bi = b[i], ri = bi - y;
+    const float rf = (float)ri;
+    r[i] = rf;
+    p[i] = rf * rd;
+    bb = fma(bi, bi, bb);
+    rr = fma(ri, ri, rr);
+    rz.add(rf, rf * rd);
   }
-  double v[2 * NC], tot[2 * NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    v[2 * c] = bb[c];
-    v[2 * c + 1] = rr[c];
-  }
-  if (!grid_sum<2 * NC>(w, v, tot) || threadIdx.x != 0) return;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    KState& s = w.st[c];
-    s.bb = tot[2 * c];
-    s.rr = tot[2 * c + 1];
-    if (first) {
-      s.res0 = sqrt(s.rr);
-      s.iters = 0;
-      s.status = DIFVM_OK;
-      s.rho = INFINITY;  // previous outer residual norm^2
-    }
-    s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
-    s.zero_rhs = s.bb == 0.0;
-    if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; continue; }
-    s.done = s.zero_rhs || s.rr <= s.tol2;
-    // stagnation: the FP32 inner solve no longer reduces the FP64 residual
-    if (!s.done && !first && s.rr > 0.25 * s.rho) { s.done = 1; s.status = DIFVM_ENOTCONV; }
-    s.rho = s.rr;
-  }
+  double v[3] = {bb, rr, rz.get()}, tot[3];
+  if (!grid_sum<3>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.bb = tot[0];
+  s.rr = tot[1];
+  s.rz = tot[2];
+  s.res0 = sqrt(s.rr);
+  s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+  s.iters = 0;
+  s.status = DIFVM_OK;
+  s.zero_rhs = s.bb == 0.0;
+  s.done = s.zero_rhs || s.rr <= s.tol2;
+  s.rho = s.rr;  // residual norm^2 at the last replacement
+  s.sconv = 0;   // replacement pending
+  s.pad0 = 0;    // number of replacements
+  if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
 }
 
-template <int NC>
-__global__ void k_refine_add(int nc, const float* e32, double* x, const KWork w, const KState* inner) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (!w.st[c].done) x[c * nc + i] += (double)e32[c * nc + i];
-  if (blockIdx.x == 0 && threadIdx.x < NC) {
-    const int c = threadIdx.x;
-    if (!w.st[c].done) w.st[c].iters += inner[c].iters;
+// x64 += alpha p; r -= alpha q; recursive rr, rz; decide on replacement; beta
+__global__ void __launch_bounds__(kKB) k_rr_update(int nc, const float* p, const float* q,
+                                                   const float* rD, double* x, float* r, KWork w) {
+  if (w.st[0].done) return;
+  const float al = (float)w.st[0].alpha;
+  const double ald = w.st[0].alpha;
+  DotAcc<float> rr, rz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    x[i] = fma(ald, (double)p[i], x[i]);
+    const float ri = r[i] - al * q[i];
+    r[i] = ri;
+    rr.add(ri, ri);
+    rz.add(ri, ri * rD[i]);
   }
+  double v[2] = {rr.get(), rz.get()}, tot[2];
+  if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.iters += 1;
+  if (!finite_d(tot[0]) || !finite_d(s.alpha)) { s.done = 1; s.status = DIFVM_ENONFINITE; return; }
+  s.beta = tot[1] / s.rz;
+  s.rz = tot[1];
+  s.rr = tot[0];
+  s.sconv = (tot[0] <= s.tol2) || (tot[0] <= 1e-4 * s.rho) || (s.iters >= w.maxit);
 }
 
-template <int NC>
+// p = rD r + beta p (with the recursive r); on replacement steps also
+// r = (float)(b - A x64) and the FP64 true residual decides convergence.
+__global__ void __launch_bounds__(kKB) k_rr_pupdate(Topo t, Mat<float> A, const double* b,
+                                                    const double* x, float* r, const float* rD,
+                                                    float* p, KWork w) {
+  if (w.st[0].done) return;
+  const int nc = t.nc;
+  const float be = (float)w.st[0].beta;
+  const bool rep = w.st[0].sconv;
+  double rr = 0.0;
+  DotAcc<float> rz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const float rd = rD[i];
+    const float ri = r[i];
+    p[i] = ri * rd + be * p[i];
+    if (rep) {
+      double y = (double)__ldg(A.D + i) * x[i];
+      const int sl = i >> 5, lane = i & 31;
+      const int o = __ldg(A.E.soff + sl), wd = (__ldg(A.E.soff + sl + 1) - o) >> 5;
+      for (int k = 0; k < wd; ++k)
+        y = fma((double)__ldg(A.val + o + lane + 32 * k), x[__ldg(A.E.col + o + lane + 32 * k)], y);
+      const double rt = b[i] - y;
+      const float rf = (float)rt;
+      r[i] = rf;
+      rr = fma(rt, rt, rr);
+      rz.add(rf, rf * rd);
+    }
+  }
+  if (!rep) return;
+  double v[2] = {rr, rz.get()}, tot[2];
+  if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.sconv = 0;
+  s.pad0 += 1;
+  s.rr = tot[0];
+  s.rz = tot[1];
+  s.rho = tot[0];
+  if (!finite_d(tot[0])) { s.done = 1; s.status = DIFVM_ENONFINITE; return; }
+  if (tot[0] <= s.tol2) { s.done = 1; return; }
+  if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; }
+}
+
 __global__ void k_zero_x64(int nc, double* x, KWork w) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (w.st[c].zero_rhs) x[c * nc + i] = 0.0;
+  if (!w.st[0].zero_rhs) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x[i] = 0.0;
 }
 
-template <int NC>
-static difvm_status refine_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<float> A,
-                              const double* b64, double* x64, char* ws, size_t wsbytes,
-                              difvm_solve_info* info, cudaStream_t st) {
-  const int nc = m->nc;
-  const int G = grid_for(m);
-  WsLayout L = layout(m, 4, o->method, NC);
-  size_t vb = L.vec_bytes;
-  // [inner workspace | r32 (NC vecs) | e32 (NC vecs) | outer state | outer partials | ticket]
-  size_t r_off = (L.total + 255) / 256 * 256;
-  size_t e_off = r_off + NC * vb;
-  size_t so = e_off + NC * vb;
+__global__ void k_rr_info(const KState* st, difvm_solve_info* info) {
+  if (threadIdx.x != 0) return;
+  const KState& s = st[0];
+  difvm_solve_info o;
+  o.iters = s.iters;
+  o.refinements = s.pad0;
+  o.status = s.status;
+  o.pad = 0;
+  o.res0 = s.res0;
+  o.res = sqrt(s.rr);
+  o.bnorm = sqrt(s.bb);
+  *info = o;
+}
+
+static size_t rr_bytes(const difvm_mesh* m, size_t* val_off, size_t* st_off, size_t* part_off,
+                       size_t* tick_off) {
+  size_t vb = up256((size_t)m->nc * 4);
+  size_t v0 = 4 * vb;  // r p q rD
+  size_t so = v0 + up256((size_t)std::max<int64_t>(m->ell_nslots, 1) * 4);
   size_t po = so + 256 * 4;
-  size_t to = po + (size_t)G * kMaxParts * sizeof(double);
-  if (wsbytes < to + 256) return set_error(DIFVM_EINVAL, "workspace too small for refinement");
-  float* r32 = (float*)(ws + r_off);
-  float* e32 = (float*)(ws + e_off);
+  size_t to = po + up256((size_t)grid_for(m) * kMaxParts * sizeof(double));
+  if (val_off) *val_off = v0;
+  if (st_off) *st_off = so;
+  if (part_off) *part_off = po;
+  if (tick_off) *tick_off = to;
+  return to + 256;
+}
+
+static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const float* D, const float* L,
+                           const double* b64, double* x64, char* ws, size_t wsbytes,
+                           difvm_solve_info* info, cudaStream_t st) {
+  size_t vo, so, po, to;
+  size_t need = rr_bytes(m, &vo, &so, &po, &to);
+  if (wsbytes < need) return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed", wsbytes, need);
+  const int nc = m->nc, G = grid_for(m);
+  const size_t vb = up256((size_t)nc * 4);
+  float *r = (float*)ws, *p = (float*)(ws + vb), *q = (float*)(ws + 2 * vb), *rD = (float*)(ws + 3 * vb);
+  float* val = (float*)(ws + vo);
   KWork w;
   w.st = (KState*)(ws + so);
   w.part = (double*)(ws + po);
   w.ticket = (unsigned*)(ws + to);
-  w.maxit = o->max_iter;
+  w.maxit = o->max_iter > 0 ? o->max_iter : 1000;
   w.tol_rel = o->tol_rel;
   w.tol_abs = o->tol_abs;
-  DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
-  difvm_solve_opts in = *o;
-  in.tol_rel = o->inner_tol > 0 ? o->inner_tol : 1e-4;
-  in.tol_abs = 0.0;
-  in.refine_max = 0;
-  KState hs[3], his[3];
-  const int rmax = o->refine_max > 0 ? o->refine_max : 20;
-  int sweeps = 0, total_inner = 0;
+  DIFVM_TRY(fill_ell<float>(m, L, nullptr, val, st));
+  Mat<float> A{D, m->ell(), val};
   Topo t = m->topo();
-  for (int k = 0; k <= rmax; ++k) {
-    k_refine_residual<NC><<<G, kKB, 0, st>>>(t, A, b64, x64, r32, e32, w, k == 0);
-    DIFVM_TRY(check_launch("refine_residual"));
-    DIFVM_CUDA(cudaMemcpyAsync(hs, w.st, sizeof(KState) * NC, cudaMemcpyDeviceToHost, st));
-    DIFVM_CUDA(cudaStreamSynchronize(st));
-    bool done = true;
-    for (int c = 0; c < NC; ++c) done &= hs[c].done != 0;
-    if (done || k == rmax) break;
-    in.max_iter = std::max(1, o->max_iter - total_inner);
-    difvm_status s = solve_nc<float, NC>(m, &in, A, r32, e32, ws, L, nullptr, 0, st, his);
-    (void)s;  // the inner solve may stop at its own cap; the outer residual decides
-    int it = 0;
-    for (int c = 0; c < NC; ++c) it = std::max(it, his[c].iters);
-    total_inner += it;
-    k_refine_add<NC><<<G, kKB, 0, st>>>(nc, e32, x64, w, (const KState*)(ws + L.state_off));
-    DIFVM_TRY(check_launch("refine_add"));
-    ++sweeps;
-    if (total_inner >= o->max_iter) {
-      k_refine_residual<NC><<<G, kKB, 0, st>>>(t, A, b64, x64, r32, e32, w, 0);
-      DIFVM_TRY(check_launch("refine_residual"));
-      break;
+  const int jac = o->precond != DIFVM_PRECOND_NONE;
+  const int chunk = o->check_every > 0 ? o->check_every : 8;
+  DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
+  k_rr_init<<<G, kKB, 0, st>>>(t, A, jac, b64, x64, r, p, rD, w);
+  DIFVM_TRY(check_launch("rr_init"));
+  KState hs[1];
+  bool done = false;
+  int it = 0;
+  // the iteration cap is enforced on the device; the host loop is bounded as well
+  while (it < w.maxit + chunk) {
+    for (int k = 0; k < chunk; ++k) {
+      prof_before(DIFVM_PROF_PCG_SPMV, st);
+      k_pcg_spmv<float, 1><<<G, kKB, 0, st>>>(t, A, p, q, w);
+      prof_after(DIFVM_PROF_PCG_SPMV, st);
+      prof_before(DIFVM_PROF_PCG_UPDATE, st);
+      k_rr_update<<<G, kKB, 0, st>>>(nc, p, q, rD, x64, r, w);
+      prof_after(DIFVM_PROF_PCG_UPDATE, st);
+      prof_before(DIFVM_PROF_PCG_PUPDATE, st);
+      k_rr_pupdate<<<G, kKB, 0, st>>>(t, A, b64, x64, r, rD, p, w);
+      prof_after(DIFVM_PROF_PCG_PUPDATE, st);
+      count_launch(); count_launch();
+      DIFVM_TRY(check_launch("rr_iter"));
     }
+    it += chunk;
+    DIFVM_TRY(read_states<1>(hs, w, st, done));
+    if (done) break;
   }
-  k_zero_x64<NC><<<G, kKB, 0, st>>>(nc, x64, w);
+  k_zero_x64<<<G, kKB, 0, st>>>(nc, x64, w);
   DIFVM_TRY(check_launch("zero_x64"));
   if (info) {
-    k_write_info<<<1, 32, 0, st>>>(NC, w.st, info, sweeps);
-    DIFVM_TRY(check_launch("write_info"));
+    k_rr_info<<<1, 32, 0, st>>>(w.st, info);
+    DIFVM_TRY(check_launch("rr_info"));
   }
-  DIFVM_CUDA(cudaMemcpyAsync(hs, w.st, sizeof(KState) * NC, cudaMemcpyDeviceToHost, st));
-  DIFVM_CUDA(cudaStreamSynchronize(st));
-  int worst = DIFVM_OK;
-  for (int c = 0; c < NC; ++c) {
-    int sc = hs[c].status;
-    if (sc == DIFVM_OK && !(hs[c].rr <= hs[c].tol2) && !hs[c].zero_rhs) sc = DIFVM_ENOTCONV;
-    worst = std::max(worst, sc);
-  }
-  return (difvm_status)worst;
+  DIFVM_TRY(read_states<1>(hs, w, st, done));
+  int s = hs[0].status;
+  if (s == DIFVM_OK && !hs[0].done) s = DIFVM_ENOTCONV;
+  return (difvm_status)s;
 }
 
 // coefficient adjoint of a solve: Dbar -= bbar_i x_i, Lbar -= bbar_N x_O, Ubar -= bbar_O x_N
@@ -905,12 +982,14 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
   WsLayout Ly = layout(m, sizeof(T), o->method, ncomp);
   if (!ws || wsbytes < Ly.total)
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed", wsbytes, Ly.total);
-  Mat<T> A{(const T*)D, (const T*)L, U ? (const T*)U : (const T*)L};
+  T* val = (T*)((char*)ws + Ly.val_off);
+  DIFVM_TRY(fill_ell<T>(m, (const T*)L, (const T*)U, val, st));
+  Mat<T> A{(const T*)D, m->ell(), val};
   KState hs[3];
   switch (ncomp) {
-    case 1: return solve_nc<T, 1>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, 0, st, hs);
-    case 2: return solve_nc<T, 2>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, 0, st, hs);
-    case 3: return solve_nc<T, 3>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, 0, st, hs);
+    case 1: return solve_nc<T, 1>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs);
+    case 2: return solve_nc<T, 2>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs);
+    case 3: return solve_nc<T, 3>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs);
   }
   return set_error(DIFVM_EINVAL, "ncomp must be 1..3");
 }
@@ -942,11 +1021,8 @@ extern "C" difvm_status difvm_krylov_solve(difvm_mesh_t m, difvm_prec prec, cons
 }
 
 extern "C" size_t difvm_krylov_refine_workspace_bytes(difvm_mesh_t m, int method, int ncomp) {
-  if (!m || ncomp < 1 || ncomp > 3) return 0;
-  WsLayout L = layout(m, 4, method, ncomp);
-  size_t r_off = (L.total + 255) / 256 * 256;
-  return r_off + 2 * (size_t)ncomp * L.vec_bytes + 256 * 4 +
-         (size_t)grid_for(m) * kMaxParts * sizeof(double) + 256;
+  if (!m || ncomp != 1 || method != DIFVM_PCG) return 0;
+  return rr_bytes(m, nullptr, nullptr, nullptr, nullptr);
 }
 
 extern "C" difvm_status difvm_krylov_solve_refine(difvm_mesh_t m, const difvm_solve_opts* o,
@@ -954,14 +1030,11 @@ extern "C" difvm_status difvm_krylov_solve_refine(difvm_mesh_t m, const difvm_so
                                                   const double* b64, double* x64, int ncomp, void* ws,
                                                   size_t wsbytes, difvm_solve_info* info, void* stream) {
   DIFVM_TRY(check_solve(m, DIFVM_F32, o, ncomp, D, L));
+  if (ncomp != 1 || o->method != DIFVM_PCG)
+    return set_error(DIFVM_EINVAL, "the mixed-precision solve is single-RHS PCG");
+  if (U) return set_error(DIFVM_EINVAL, "the mixed-precision PCG needs a symmetric matrix (upper = NULL)");
   if (!b64 || !x64 || !ws) return set_error(DIFVM_EINVAL, "null vector or workspace");
-  Mat<float> A{D, L, U ? U : L};
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (ncomp) {
-    case 1: return refine_nc<1>(m, o, A, b64, x64, (char*)ws, wsbytes, info, st);
-    case 2: return refine_nc<2>(m, o, A, b64, x64, (char*)ws, wsbytes, info, st);
-    default: return refine_nc<3>(m, o, A, b64, x64, (char*)ws, wsbytes, info, st);
-  }
+  return rr_pcg(m, o, D, L, b64, x64, (char*)ws, wsbytes, info, (cudaStream_t)stream);
 }
 
 extern "C" difvm_status difvm_krylov_solve_bwd(difvm_mesh_t m, difvm_prec prec,

@@ -190,8 +190,9 @@ __global__ void k_cell_coeffs(int nc, const double* V, double* rV64, float* V32,
 
 static void free_mesh(difvm_mesh* m) {
   if (!m) return;
-  void* ptrs[] = {m->on, m->bown, m->cptr, m->cent, m->bkind, m->bpatch, m->Sw64, m->ck64,
-                  m->Sw32, m->ck32, m->V64, m->rV64, m->C64, m->Cf64, m->V32, m->rV32};
+  void* ptrs[] = {m->on,   m->bown, m->cptr, m->cent, m->bkind, m->bpatch, m->Sw64,
+                  m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
+                  m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map};
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
@@ -349,6 +350,33 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   for (int b = 0; b < nb; ++b) cent[fill[bown[b]]++] = ((ni + b) << 1);
   m->max_row = 0;
   for (int i = 0; i < nc; ++i) m->max_row = std::max(m->max_row, cptr[i + 1] - cptr[i]);
+  // sliced-ELL layout of the internal-face entries (slice height 32)
+  const int nsl = (nc + 31) / 32;
+  std::vector<int> soff(nsl + 1, 0);
+  for (int sl = 0; sl < nsl; ++sl) {
+    int w = 0;
+    for (int i = 32 * sl; i < std::min(nc, 32 * sl + 32); ++i) {
+      int k = 0;
+      for (int e = cptr[i]; e < cptr[i + 1]; ++e) k += (cent[e] >> 1) < ni;
+      w = std::max(w, k);
+    }
+    soff[sl + 1] = soff[sl] + 32 * w;
+  }
+  std::vector<int> ecol((size_t)std::max(soff[nsl], 1), 0), emap((size_t)std::max(soff[nsl], 1), -1);
+  for (int i = 0; i < nc; ++i) {
+    const int sl = i >> 5, lane = i & 31, w = (soff[sl + 1] - soff[sl]) / 32;
+    int k = 0;
+    for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
+      const int f = cent[e] >> 1;
+      if (f >= ni) continue;
+      ecol[soff[sl] + 32 * k + lane] = (cent[e] & 1) ? on[f].x : on[f].y;
+      emap[soff[sl] + 32 * k + lane] = cent[e];
+      ++k;
+    }
+    for (; k < w; ++k) ecol[soff[sl] + 32 * k + lane] = i;
+  }
+  m->ell_nsl = nsl;
+  m->ell_nslots = soff[nsl];
   // boundary kinds per bc class (2 bits each)
   std::vector<uint8_t> bkind(nb > 0 ? nb : 1);
   std::vector<uint16_t> bpatch(nb > 0 ? nb : 1);
@@ -377,6 +405,9 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload(&m->cent, cent.data(), cent.size()));
   DIFVM_TRY(upload(&m->bkind, bkind.data(), bkind.size()));
   DIFVM_TRY(upload(&m->bpatch, bpatch.data(), bpatch.size()));
+  DIFVM_TRY(upload(&m->ell_soff, soff.data(), soff.size()));
+  DIFVM_TRY(upload(&m->ell_col, ecol.data(), ecol.size()));
+  DIFVM_TRY(upload(&m->ell_map, emap.data(), emap.size()));
   double* Sf_d = nullptr;
   DIFVM_TRY(upload(&Sf_d, Sf.data(), Sf.size()));
   DIFVM_TRY(upload(&m->Cf64, Cf.data(), Cf.size()));
