@@ -186,6 +186,30 @@ difvm_status difvm_laplacian_apply_bwd(difvm_mesh_t, difvm_prec, const void* dia
                                        const void* lower, const void* upper, const void* x,
                                        const void* y_bar, int ncomp, void* x_bar, void* diag_bar,
                                        void* lower_bar, void* upper_bar, void* tmp, void* stream);
+/* Same adjoint as difvm_laplacian_apply_bwd, for callers that cannot allocate
+ * device memory -- for example a host whose device memory is all owned by
+ * another runtime's pool, or a time-critical loop in which a cudaMalloc (which
+ * may synchronise the whole device) is not acceptable.  It takes no tmp
+ * argument: A^T y_bar is formed in a 16 MiB scratch array built into the
+ * library (every GPU that loads the library keeps it reserved until the process
+ * exits).  The paper has no counterpart; this is a library convenience.
+ * Limits and behaviour:
+ *  - with x_bar != NULL, ncomp * n_cells * sizeof(element) must be at most
+ *    16 MiB (FP64: 2,097,152 elements, FP32: 4,194,304); larger calls return
+ *    EINVAL with a message and launch nothing;
+ *  - the first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture;
+ *  - calls share the one array and it keeps the last call's contents (every
+ *    element used is overwritten before it is read, so nothing needs
+ *    clearing); each GPU has its own copy, and calls on the same GPU that
+ *    can overlap (for example on two streams with no ordering between them)
+ *    race on it;
+ *  - no cudaMalloc, cudaFree or allocating library routine is called. */
+difvm_status difvm_laplacian_apply_bwd_noalloc(difvm_mesh_t, difvm_prec, const void* diag,
+                                               const void* lower, const void* upper, const void* x,
+                                               const void* y_bar, int ncomp, void* x_bar,
+                                               void* diag_bar, void* lower_bar, void* upper_bar,
+                                               void* stream);
 
 /* ------------------------------------------------------------------- Krylov */
 typedef struct {

@@ -103,6 +103,8 @@ _SIGS = {
     "difvm_piso_create": [_vp, _i, _vp, _vp],
     "difvm_piso_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "difvm_flux_from_U": [_vp, _i, _vp, _vp, _vp, _vp],
+    "difvm_laplacian_apply_bwd_noalloc": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
+                                          _vp],
     "difvm_prof_start": [_i, _i],
     "difvm_prof_stop": [_vp, _vp],
 }
@@ -343,6 +345,16 @@ def difvm_laplacian_apply_bwd(mesh, diag, lower, upper, x, y_bar, x_bar=None, di
                                            _ptr(upper), _ptr(x), _ptr(y_bar), nq, _ptr(x_bar),
                                            _ptr(diag_bar), _ptr(lower_bar), _ptr(upper_bar),
                                            _ptr(tmp), _stream(stream)))
+
+
+def difvm_laplacian_apply_bwd_noalloc(mesh, diag, lower, upper, x, y_bar, x_bar=None, diag_bar=None,
+                                      lower_bar=None, upper_bar=None, stream=None):
+    """Adjoint of the LDU apply with the library's built-in scratch (no allocation)."""
+    nq = x.shape[0] if x.dim() == 2 else 1
+    _check(lib().difvm_laplacian_apply_bwd_noalloc(_mh(mesh), _prec(x), _ptr(diag), _ptr(lower),
+                                                   _ptr(upper), _ptr(x), _ptr(y_bar), nq,
+                                                   _ptr(x_bar), _ptr(diag_bar), _ptr(lower_bar),
+                                                   _ptr(upper_bar), _stream(stream)))
 
 
 # ------------------------------------------------------------------- Krylov
