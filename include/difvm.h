@@ -76,6 +76,7 @@ enum { DIFVM_WK_EXACT = 0, DIFVM_WK_FE = 1, DIFVM_WK_BE = 2 };  /* Eq. windkesse
 enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
 enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1 };
 enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };
+enum { DIFVM_NONORTH_MOMENTUM = 1, DIFVM_NONORTH_PRESSURE = 2, DIFVM_NONORTH_ALL = 3 };
 
 typedef struct difvm_mesh* difvm_mesh_t;
 
@@ -292,12 +293,17 @@ difvm_status difvm_windkessel_update_bwd(int n_out, int scheme, const double* Rp
 typedef struct {
   double nu, dt;
   int32_t n_corr;       /* pressure correctors (Sec. 2.4.2: typically 2) */
-  int32_t nonorth;      /* explicit over-relaxed non-orthogonal corrections on/off */
+  int32_t nonorth;      /* explicit over-relaxed non-orthogonal corrections, bitmask of
+                           DIFVM_NONORTH_MOMENTUM (momentum diffusion) and
+                           DIFVM_NONORTH_PRESSURE (pressure Laplacian, lagged); 0 = none */
   difvm_solve_opts solve_U, solve_p;
   int32_t pref_cell;    /* internal id of the pinned cell when no patch fixes p */
   int32_t wk_scheme;    /* DIFVM_WK_* */
   int32_t n_out;        /* Windkessel outlets (0..16) */
   int32_t wk_patch[16]; /* patch ids of the outlets */
+  double nonorth_limit; /* psi in (0,1): cap each explicit non-orthogonal correction at
+                           psi/(1-psi) x the face's orthogonal part (the "limited" form of
+                           Eq. nonortho_flux); 0 or >= 1: unlimited over-relaxed correction */
 } difvm_piso_opts;
 
 typedef struct difvm_piso* difvm_piso_t;

@@ -66,7 +66,7 @@ class _PisoOpts(C.Structure):
                 ("tolU", C.c_double), ("tolp", C.c_double), ("tol_abs", C.c_double),
                 ("maxitU", C.c_int), ("maxitp", C.c_int), ("pref_cell", C.c_int),
                 ("wk_scheme", C.c_int), ("n_out", C.c_int), ("wk_patch", C.c_void_p),
-                ("Rp", C.c_void_p), ("Cw", C.c_void_p), ("Rd", C.c_void_p)]
+                ("Rp", C.c_void_p), ("Cw", C.c_void_p), ("Rd", C.c_void_p), ("psi", C.c_double)]
 
 
 class _PisoInfo(C.Structure):
@@ -196,13 +196,13 @@ def windkessel_update(scheme, Rp, Cw, Rd, Q, dt, pc):
     return pc, po
 
 
-def momentum_assemble(m: OMesh, nu, dt, mf, Uold, Ub, gradU=None):
+def momentum_assemble(m: OMesh, nu, dt, mf, Uold, Ub, gradU=None, psi=1.0):
     D = np.zeros(m.nc); Lo = np.zeros(m.nint + 1); Up = np.zeros(m.nint + 1)
     b = np.zeros((3, m.nc))
     lib().om_momentum_assemble(m.ref(), _p(m.bc_U()), C.c_double(nu), C.c_double(dt),
                                _p(_f64(mf)), _p(_f64(Uold)), _p(_f64(np.reshape(Ub, (3, m.nb)))),
-                               _p(None if gradU is None else _f64(gradU)), _p(D), _p(Lo), _p(Up),
-                               _p(b))
+                               _p(None if gradU is None else _f64(gradU)), C.c_double(psi), _p(D),
+                               _p(Lo), _p(Up), _p(b))
     return D, Lo[:m.nint], Up[:m.nint], b
 
 
@@ -212,12 +212,14 @@ def H_op(m: OMesh, Lo, Up, b, U):
     return H
 
 
-def pressure_assemble(m: OMesh, rAU, HbyA, Ub, pb, gradp=None):
+def pressure_assemble(m: OMesh, rAU, HbyA, Ub, pb, gradp=None, plag=None, psi=1.0):
     Dp = np.zeros(m.nc); Lp = np.zeros(m.nint + 1); bp = np.zeros(m.nc)
     phiH = np.zeros(m.nf); af = np.zeros(m.nf); no = np.zeros(m.nint + 1)
     lib().om_pressure_assemble(m.ref(), _p(m.bc_U()), _p(m.bc_p()), _p(_f64(rAU)), _p(_f64(HbyA)),
                                _p(_f64(np.reshape(Ub, (3, m.nb)))), _p(_f64(pb)),
-                               _p(None if gradp is None else _f64(gradp)), _p(Dp), _p(Lp), _p(bp),
+                               _p(None if gradp is None else _f64(gradp)),
+                               _p(_f64(np.zeros(m.nc) if plag is None else plag)), C.c_double(psi),
+                               _p(Dp), _p(Lp), _p(bp),
                                _p(phiH), _p(af), _p(no))
     return dict(Dp=Dp, Lp=Lp[:m.nint], bp=bp, phiHbyA=phiH, af=af, nonorth=no[:m.nint])
 
@@ -230,16 +232,19 @@ def flux_from_U(m: OMesh, U, Ub):
 
 def piso_step(m: OMesh, U, p, phi, Ub, pb, *, nu, dt, ncorr=2, nonorth=True, tolU=1e-10,
               tolp=1e-10, tol_abs=0.0, maxitU=1000, maxitp=20000, pref_cell=0,
-              wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(), wk_scheme=WK_EXACT):
-    """One PISO step in place on copies; returns (U, p, phi, pb, pc, info)."""
+              wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(), wk_scheme=WK_EXACT, psi=1.0):
+    """One PISO step in place on copies; returns (U, p, phi, pb, pc, info).
+
+    nonorth: True (both), False (none), or a mask: 1 momentum, 2 pressure."""
     U = _f64(np.array(U, np.float64)); p = _f64(np.array(p, np.float64))
     phi = _f64(np.array(phi, np.float64)); pb = _f64(np.array(pb, np.float64))
     Ub = _f64(np.reshape(Ub, (3, m.nb)))
     wk_patch = _i32(np.atleast_1d(np.asarray(wk_patch, np.int32)))
     Rp, Cw, Rd = (_f64(np.atleast_1d(np.asarray(a, np.float64))) for a in (Rp, Cw, Rd))
     pc = _f64(np.array(np.atleast_1d(np.asarray(pc, np.float64))))
-    opts = _PisoOpts(nu, dt, ncorr, int(nonorth), tolU, tolp, tol_abs, maxitU, maxitp, pref_cell,
-                     wk_scheme, int(wk_patch.shape[0]), _p(wk_patch), _p(Rp), _p(Cw), _p(Rd))
+    nonorth = 3 if nonorth is True else (0 if nonorth is False else int(nonorth))
+    opts = _PisoOpts(nu, dt, ncorr, nonorth, tolU, tolp, tol_abs, maxitU, maxitp, pref_cell,
+                     wk_scheme, int(wk_patch.shape[0]), _p(wk_patch), _p(Rp), _p(Cw), _p(Rd), psi)
     info = _PisoInfo()
     lib().om_piso_step(m.ref(), C.byref(opts), _p(U), _p(p), _p(phi), _p(Ub), _p(pb), _p(pc),
                        C.byref(info))

@@ -65,6 +65,17 @@ static int patch_of_face(const om_mesh *m, int f) {
 static int bc_of_U(int pt) { return pt == PT_EMPTY ? BC_EMPTY : (pt == PT_OUTLET ? BC_ZEROGRAD : BC_FIXED); }
 static int bc_of_p(int pt) { return pt == PT_EMPTY ? BC_EMPTY : (pt == PT_OUTLET ? BC_FIXED : BC_ZEROGRAD); }
 
+/* Limited explicit non-orthogonal correction ("limited corrected psi" of
+ * OpenFOAM, used where the plain over-relaxed correction of Eq. nonortho_flux
+ * is unstable): the correction is capped at psi/(1-psi) times the magnitude of
+ * the orthogonal part of the same face flux; psi >= 1 leaves it unlimited. */
+static double limit_corr(double corr, double orth, double psi) {
+  if (psi >= 1.0) return corr;
+  double cap = psi / (1.0 - psi) * fabs(orth);
+  if (fabs(corr) > cap) return corr > 0.0 ? cap : -cap;
+  return corr;
+}
+
 /* ---------------------------------------------------------------- geometry */
 /* Derived face coefficients (Sec. 2.3.2): w[nint], c[nf], k[nint*3]. */
 void om_face_coeffs(const om_mesh *m, double *w, double *c, double *k) {
@@ -394,11 +405,12 @@ void om_windkessel_update(int n, int scheme, const double *Rp, const double *Cc,
  *   D_i  = V_i/dt + sum_{O=i}(max(m,0) + nu c) + sum_{N=i}(max(-m,0) + nu c) + bnd
  *   Up_f = min(m,0) - nu c   (row O, column N)
  *   Lo_f = -max(m,0) - nu c  (row N, column O)
- *   b_i  = V_i/dt U^n_i + sigma nu (gradU)_f . k_f + bnd
+ *   b_i  = V_i/dt U^n_i + sigma nu (gradU)_f . k_f + bnd   (correction limited by psi)
  * boundary fixed U: D += nu c, b += (nu c - m) U_b;  zero gradient: D += m. */
 void om_momentum_assemble(const om_mesh *m, const int *bcU, double nu, double dt,
                           const double *mf, const double *Uold, const double *Ub,
-                          const double *gradU, double *D, double *Lo, double *Up, double *b) {
+                          const double *gradU, double psi, double *D, double *Lo, double *Up,
+                          double *b) {
   int nc = m->nc, nb = m->nf - m->nint;
   double *w = malloc(sizeof(double) * (m->nint + 1));
   double *c = malloc(sizeof(double) * (m->nf + 1));
@@ -423,7 +435,8 @@ void om_momentum_assemble(const om_mesh *m, const int *bcU, double nu, double dt
           const double *g = gradU + (size_t)q * 3 * nc;
           double gf[3];
           for (int d = 0; d < 3; ++d) gf[d] = w[f] * g[d * nc + O] + (1.0 - w[f]) * g[d * nc + N];
-          double corr = nu * dot3(gf, k + 3 * f);
+          double orth = c[f] * (Uold[q * nc + N] - Uold[q * nc + O]);
+          double corr = nu * limit_corr(dot3(gf, k + 3 * f), orth, psi);
           b[q * nc + O] += corr;
           b[q * nc + N] -= corr;
         }
@@ -463,14 +476,14 @@ void om_H(const om_mesh *m, const double *Lo, const double *Up, const double *b,
 /* Pressure equation of one PISO corrector (Eqs. pressure_poisson, velocity_correction):
  *   phiHbyA_f = HbyA_f . S_f   (boundary: fixed U -> U_b.S, zero-gradient U -> HbyA_O.S)
  *   a_f       = rAU_f c_f,   rAU_f = w rAU_O + (1-w) rAU_N  (boundary fixed p: rAU_O c_f)
- *   nonorth_f = rAU_f (grad p)_f . k_f   (lagged, gradp may be NULL)
+ *   nonorth_f = rAU_f (grad p)_f . k_f   (lagged from plag, limited by psi; gradp may be NULL)
  * SPD form  Dp p - sum a_f p_other = -div(phiHbyA) + div(nonorth) + sum_bnd a_f p_b
  * with Dp_i = sum a_f, Lp_f = -a_f.  af[nf] and nonorth[nint] are returned for the
  * flux correction. */
 void om_pressure_assemble(const om_mesh *m, const int *bcU, const int *bcp, const double *rAU,
                           const double *HbyA, const double *Ub, const double *pb,
-                          const double *gradp, double *Dp, double *Lp, double *bp,
-                          double *phiHbyA, double *af, double *nonorth) {
+                          const double *gradp, const double *plag, double psi, double *Dp,
+                          double *Lp, double *bp, double *phiHbyA, double *af, double *nonorth) {
   int nc = m->nc, nb = m->nf - m->nint;
   double *w = malloc(sizeof(double) * (m->nint + 1));
   double *c = malloc(sizeof(double) * (m->nf + 1));
@@ -491,7 +504,7 @@ void om_pressure_assemble(const om_mesh *m, const int *bcU, const int *bcp, cons
       if (gradp) {
         double gf[3];
         for (int d = 0; d < 3; ++d) gf[d] = w[f] * gradp[d * nc + O] + (1.0 - w[f]) * gradp[d * nc + N];
-        nonorth[f] = rf * dot3(gf, k + 3 * f);
+        nonorth[f] = rf * limit_corr(dot3(gf, k + 3 * f), c[f] * (plag[N] - plag[O]), psi);
       }
       Dp[O] += af[f];
       Dp[N] += af[f];
@@ -525,7 +538,7 @@ void om_pressure_assemble(const om_mesh *m, const int *bcU, const int *bcp, cons
 /* ------------------------------------------------------------------ PISO */
 typedef struct {
   double nu, dt;
-  int ncorr, nonorth;           /* nonorth: explicit non-orthogonal corrections on/off */
+  int ncorr, nonorth;           /* explicit non-orthogonal corrections: bit 0 momentum, bit 1 pressure */
   double tolU, tolp, tol_abs;
   int maxitU, maxitp;
   int pref_cell;                /* pinned cell when no patch fixes p */
@@ -533,6 +546,7 @@ typedef struct {
   int n_out;                    /* Windkessel outlets */
   const int *wk_patch;          /* [n_out] patch ids */
   const double *Rp, *Cw, *Rd;   /* [n_out] */
+  double psi;                   /* non-orthogonal limiter coefficient (1 = unlimited) */
 } om_piso_opts;
 
 typedef struct { int itU[3], itp[4], status; double Q[8], po[8]; } om_piso_info;
@@ -575,8 +589,9 @@ int om_piso_step(const om_mesh *m, const om_piso_opts *o, double *U, double *p, 
   om_info si;
   /* 2. momentum predictor: A U* = b - V grad p^n */
   om_grad_gauss(m, bcp, 1, p, pb, gradp);
-  if (o->nonorth) om_grad_gauss(m, bcU, 3, U, Ub, gradU);
-  om_momentum_assemble(m, bcU, o->nu, o->dt, phi, U, Ub, o->nonorth ? gradU : NULL, D, Lo, Up, b);
+  if (o->nonorth & 1) om_grad_gauss(m, bcU, 3, U, Ub, gradU);
+  om_momentum_assemble(m, bcU, o->nu, o->dt, phi, U, Ub, (o->nonorth & 1) ? gradU : NULL, o->psi,
+                       D, Lo, Up, b);
   for (int q = 0; q < 3; ++q) {
     for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gradp[q * nc + i];
     int st = om_bicgstab(m, D, Lo, Up, rhs, U + (size_t)q * nc, o->tolU, o->tol_abs, o->maxitU, &si);
@@ -589,9 +604,9 @@ int om_piso_step(const om_mesh *m, const om_piso_opts *o, double *U, double *p, 
     om_H(m, Lo, Up, b, U, H);
     for (int q = 0; q < 3; ++q)
       for (int i = 0; i < nc; ++i) HbyA[q * nc + i] = H[q * nc + i] / D[i];
-    if (o->nonorth) om_grad_gauss(m, bcp, 1, p, pb, gradp);
-    om_pressure_assemble(m, bcU, bcp, rAU, HbyA, Ub, pb, o->nonorth ? gradp : NULL,
-                         Dp, Lp, bp, phiHbyA, af, nonorth);
+    if (o->nonorth & 2) om_grad_gauss(m, bcp, 1, p, pb, gradp);
+    om_pressure_assemble(m, bcU, bcp, rAU, HbyA, Ub, pb, (o->nonorth & 2) ? gradp : NULL, p,
+                         o->psi, Dp, Lp, bp, phiHbyA, af, nonorth);
     if (!has_fixed_p) Dp[o->pref_cell] += Dp[o->pref_cell];   /* p_ref = 0 */
     int st = om_pcg(m, Dp, Lp, NULL, bp, p, o->tolp, o->tol_abs, o->maxitp, &si);
     if (corr < 4) info->itp[corr] = si.iters;

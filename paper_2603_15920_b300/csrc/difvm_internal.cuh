@@ -74,17 +74,33 @@ struct Topo {
   const uint16_t* bpatch;  // [nb] patch id
 };
 
-// Sliced-ELL (slice height 32) layout of the off-diagonal entries of the
-// LDU operator, used inside the Krylov solvers: row i lives in slice i/32 at
-// lane i%32; slot k of the row is at soff[slice] + 32 k + lane.  col is the
-// column (the row itself on padding), map the source entry (face << 1 | side,
-// side 1 = row is the neighbour) or -1 on padding.
+// ELL layout of the off-diagonal entries of the LDU operator, used inside the
+// Krylov solvers.  Uniform width W > 0: slot k of row i is at i W + k (row
+// major).  Otherwise sliced ELL (slice height 32): row i lives in slice i/32 at
+// lane i%32 and slot k is at soff[slice] + 32 k + lane.  col is the column (the
+// row itself on padding), map the source entry (face << 1 | side, side 1 = row
+// is the neighbour) or -1 on padding.
 struct Ell {
   int nsl;
+  int W;            // > 0: uniform row-major width; 0: sliced with per-slice widths
   const int* soff;  // [nsl+1]
   const int* col;   // [nslots]
   const int* map;   // [nslots]
 };
+
+// first slot and slot stride of row i
+__device__ __forceinline__ void ell_row(const Ell& E, int i, int& base, int& step, int& w) {
+  if (E.W > 0) {
+    base = i * E.W;
+    step = 1;
+    w = E.W;
+  } else {
+    const int o = __ldg(E.soff + (i >> 5));
+    base = o + (i & 31);
+    step = 32;
+    w = (__ldg(E.soff + (i >> 5) + 1) - o) >> 5;
+  }
+}
 
 __device__ __forceinline__ int face_kind(const Topo& t, int b, int cls) {
   return (t.bkind[b] >> (2 * cls)) & 3;
@@ -110,6 +126,8 @@ struct difvm_mesh {
   uint8_t* bkind = nullptr;
   uint16_t* bpatch = nullptr;
   int ell_nsl = 0;
+  int ell_w = 0;      // uniform slice width, or 0
+  int ell_wmax = 0;   // widest row
   int64_t ell_nslots = 0;
   int* ell_soff = nullptr;
   int* ell_col = nullptr;
@@ -125,7 +143,7 @@ struct difvm_mesh {
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
   }
-  difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_soff, ell_col, ell_map}; }
+  difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_w, ell_soff, ell_col, ell_map}; }
   difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }
   difvm::Geo<float> geo32() const { return {Sw32, ck32, V32, rV32}; }
 };

@@ -29,7 +29,7 @@ template <typename T>
 difvm_status ldu_apply_t(difvm_mesh_t m, const void* D, const void* L, const void* U,
                          const void* x, int ncomp, int transpose, void* y, cudaStream_t s);
 
-constexpr int kKB = 256;       // threads per block
+constexpr int kKB = 512;       // threads per block (four blocks per SM: few partials, few atomics)
 constexpr int kMaxParts = 12;  // partial sums per block (<= 4 per component x 3)
 
 struct KState {
@@ -66,9 +66,11 @@ __global__ void k_ell_fill(int nslots, const int* map, const T* L, const T* U, T
 // ---------------------------------------------------------- accumulators
 template <typename T> struct DotAcc;
 template <> struct DotAcc<double> {
+  using part_t = double;
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ double part() const { return s; }
 };
 // Dot2: error-free TwoProduct (fma) + TwoSum, errors accumulated in c.
 template <> struct DotAcc<float> {
@@ -83,7 +85,21 @@ template <> struct DotAcc<float> {
     c = __fadd_rn(c, __fadd_rn(q, r));
   }
   __device__ __forceinline__ double get() const { return (double)p + (double)c; }
+  // unevaluated (hi, lo) pair, reduced across threads in FP32 by ff_merge
+  using part_t = float2;
+  __device__ __forceinline__ float2 part() const { return make_float2(p, c); }
 };
+
+// error-free merge of two float-float pairs (TwoSum on the leading parts, then
+// renormalisation), so cross-thread sums stay on the FP32 pipes
+__device__ __forceinline__ float2 ff_merge(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(b.x, z));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
 
 // block reduction of K doubles; result valid in thread 0
 template <int K>
@@ -128,6 +144,73 @@ __device__ __forceinline__ bool grid_sum(const KWork& w, double (&v)[K], double 
   double a[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) a[k] = 0.0;
+#pragma unroll 4
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] += __ldcg(w.part + b * kMaxParts + k);
+  block_sum<K>(a);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) res[k] = a[k];
+    *w.ticket = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = res[k];
+  return true;
+}
+
+// FP32-pair version: warp and block trees merge (hi, lo) pairs with ff_merge;
+// one conversion to FP64 per block.
+template <int K>
+__device__ __forceinline__ bool grid_sum(const KWork& w, float2 (&v)[K], double (&tot)[K]) {
+  __shared__ float2 sm2[K][kKB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 t;
+      t.x = __shfl_down_sync(0xffffffffu, v[k].x, o);
+      t.y = __shfl_down_sync(0xffffffffu, v[k].y, o);
+      v[k] = ff_merge(v[k], t);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm2[k][warp] = v[k];
+  __syncthreads();
+  double d[K];
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      v[k] = lane < (int)(blockDim.x >> 5) ? sm2[k][lane] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float2 t;
+        t.x = __shfl_down_sync(0xffffffffu, v[k].x, o);
+        t.y = __shfl_down_sync(0xffffffffu, v[k].y, o);
+        v[k] = ff_merge(v[k], t);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) d[k] = threadIdx.x == 0 ? (double)v[k].x + (double)v[k].y : 0.0;
+  // the block result is in thread 0: store it and finish as in the FP64 path
+  __shared__ int amlast;
+  __shared__ double res[K];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) w.part[blockIdx.x * kMaxParts + k] = d[k];
+    __threadfence();
+    amlast = atomicAdd(w.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+  double a[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) a[k] = 0.0;
+#pragma unroll 4
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < K; ++k) a[k] += __ldcg(w.part + b * kMaxParts + k);
@@ -152,24 +235,69 @@ __device__ __forceinline__ unsigned active_mask(const KWork& w) {
   return m;
 }
 
-template <typename T, int NC>
+// One row of y = A x.  A uniform width-4 layout (Kuhn tetrahedra) reads the
+// row's columns and values with one 16-byte load each; otherwise MAXW > 0
+// unrolls the row to MAXW slots with predication (all loads issued before the
+// gathers) and MAXW = 0 is a plain loop.
+template <typename T> struct Vec4Load;
+template <> struct Vec4Load<float> {
+  static __device__ __forceinline__ void get(const float* v, int i, float (&a)[4]) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(v) + i);
+    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+  }
+};
+template <> struct Vec4Load<double> {
+  static __device__ __forceinline__ void get(const double* v, int i, double (&a)[4]) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(v) + 2 * i);
+    const double2 y = __ldg(reinterpret_cast<const double2*>(v) + 2 * i + 1);
+    a[0] = x.x; a[1] = x.y; a[2] = y.x; a[3] = y.y;
+  }
+};
+
+template <typename T, int NC, int MAXW>
 __device__ __forceinline__ void spmv_row(const Topo& t, const Mat<T>& A, int i, const T* x,
                                          T (&y)[NC], unsigned act) {
   const int nc = t.nc;
   const T d = __ldg(A.D + i);
 #pragma unroll
   for (int c = 0; c < NC; ++c) y[c] = (act >> c & 1) ? d * __ldg(x + c * nc + i) : T(0);
-  const int sl = i >> 5, lane = i & 31;
-  const int o = __ldg(A.E.soff + sl), w = (__ldg(A.E.soff + sl + 1) - o) >> 5;
-  const int* col = A.E.col + o + lane;
-  const T* val = A.val + o + lane;
-#pragma unroll 4
-  for (int k = 0; k < w; ++k) {
-    const int j = __ldg(col + 32 * k);
-    const T a = __ldg(val + 32 * k);
+  if (MAXW == 4 && A.E.W == 4) {
+    const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+    T a[4];
+    Vec4Load<T>::get(A.val, i, a);
+    const int j[4] = {j4.x, j4.y, j4.z, j4.w};
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (act >> c & 1) y[c] += a * __ldg(x + c * nc + j);
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (act >> c & 1) y[c] += a[k] * __ldg(x + c * nc + j[k]);
+    return;
+  }
+  int base, step, w;
+  ell_row(A.E, i, base, step, w);
+  const int* col = A.E.col + base;
+  const T* val = A.val + base;
+  if (MAXW > 0) {
+    int j[MAXW > 0 ? MAXW : 1];
+    T a[MAXW > 0 ? MAXW : 1];
+#pragma unroll
+    for (int k = 0; k < MAXW; ++k) {
+      j[k] = k < w ? __ldg(col + step * k) : i;
+      a[k] = k < w ? __ldg(val + step * k) : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < MAXW; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (act >> c & 1) y[c] += a[k] * __ldg(x + c * nc + j[k]);
+  } else {
+    for (int k = 0; k < w; ++k) {
+      const int jj = __ldg(col + step * k);
+      const T aa = __ldg(val + step * k);
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (act >> c & 1) y[c] += aa * __ldg(x + c * nc + jj);
+    }
   }
 }
 
@@ -187,7 +315,7 @@ __global__ void __launch_bounds__(kKB) k_pcg_init(Topo t, Mat<T> A, int jacobi, 
     const T rd = jacobi ? T(1) / di : T(1);
     rD[i] = rd;
     T ax[NC];
-    spmv_row<T, NC>(t, A, i, x, ax, (1u << NC) - 1);
+    spmv_row<T, NC, 0>(t, A, i, x, ax, (1u << NC) - 1);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const T bi = b[c * nc + i];
@@ -200,12 +328,13 @@ __global__ void __launch_bounds__(kKB) k_pcg_init(Topo t, Mat<T> A, int jacobi, 
       rz[c].add(ri, zi);
     }
   }
-  double v[3 * NC], tot[3 * NC];
+  typename DotAcc<T>::part_t v[3 * NC];
+  double tot[3 * NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    v[3 * c] = bb[c].get();
-    v[3 * c + 1] = rr[c].get();
-    v[3 * c + 2] = rz[c].get();
+    v[3 * c] = bb[c].part();
+    v[3 * c + 1] = rr[c].part();
+    v[3 * c + 2] = rz[c].part();
   }
   if (!grid_sum<3 * NC>(w, v, tot) || threadIdx.x != 0) return;
 #pragma unroll
@@ -224,26 +353,40 @@ __global__ void __launch_bounds__(kKB) k_pcg_init(Topo t, Mat<T> A, int jacobi, 
   }
 }
 
-// q = A p; alpha = rz / (p.q)
-template <typename T, int NC>
+// q = A p; alpha = rz / (p.q).  kRows rows per thread per pass (independent
+// load chains); trailing row indices are clamped so all loads are unconditional.
+constexpr int kRows = 4;
+template <typename T, int NC, int MAXW>
 __global__ void __launch_bounds__(kKB) k_pcg_spmv(Topo t, Mat<T> A, const T* p, T* q, KWork w) {
   const unsigned act = active_mask<NC>(w);
   if (!act) return;
   const int nc = t.nc;
+  const int stride = gridDim.x * blockDim.x;
   DotAcc<T> pq[NC];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    T y[NC];
-    spmv_row<T, NC>(t, A, i, p, y, act);
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < nc; i0 += kRows * stride) {
+    T y[kRows][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (act >> c & 1) {
-        q[c * nc + i] = y[c];
-        pq[c].add(p[c * nc + i], y[c]);
+    for (int r = 0; r < kRows; ++r) {
+      const int i = i0 + r * stride;
+      spmv_row<T, NC, MAXW>(t, A, i < nc ? i : i0, p, y[r], act);
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int i = i0 + r * stride;
+      if (i < nc) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (act >> c & 1) {
+            q[c * nc + i] = y[r][c];
+            pq[c].add(p[c * nc + i], y[r][c]);
+          }
       }
+    }
   }
-  double v[NC], tot[NC];
+  typename DotAcc<T>::part_t v[NC];
+  double tot[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) v[c] = pq[c].get();
+  for (int c = 0; c < NC; ++c) v[c] = pq[c].part();
   if (!grid_sum<NC>(w, v, tot) || threadIdx.x != 0) return;
 #pragma unroll
   for (int c = 0; c < NC; ++c)
@@ -273,11 +416,12 @@ __global__ void __launch_bounds__(kKB) k_pcg_update(int nc, const T* p, const T*
         rz[c].add(ri, ri * rd);
       }
   }
-  double v[2 * NC], tot[2 * NC];
+  typename DotAcc<T>::part_t v[2 * NC];
+  double tot[2 * NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    v[2 * c] = rr[c].get();
-    v[2 * c + 1] = rz[c].get();
+    v[2 * c] = rr[c].part();
+    v[2 * c + 1] = rz[c].part();
   }
   if (!grid_sum<2 * NC>(w, v, tot) || threadIdx.x != 0) return;
 #pragma unroll
@@ -332,7 +476,7 @@ __global__ void __launch_bounds__(kKB) k_bicg_init(Topo t, Mat<T> A, int jacobi,
     const T di = __ldg(A.D + i);
     rD[i] = jacobi ? T(1) / di : T(1);
     T ax[NC];
-    spmv_row<T, NC>(t, A, i, x, ax, (1u << NC) - 1);
+    spmv_row<T, NC, 0>(t, A, i, x, ax, (1u << NC) - 1);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int k = c * nc + i;
@@ -346,11 +490,12 @@ __global__ void __launch_bounds__(kKB) k_bicg_init(Topo t, Mat<T> A, int jacobi,
       rr[c].add(ri, ri);
     }
   }
-  double vv[2 * NC], tot[2 * NC];
+  typename DotAcc<T>::part_t vv[2 * NC];
+  double tot[2 * NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    vv[2 * c] = bb[c].get();
-    vv[2 * c + 1] = rr[c].get();
+    vv[2 * c] = bb[c].part();
+    vv[2 * c + 1] = rr[c].part();
   }
   if (!grid_sum<2 * NC>(w, vv, tot) || threadIdx.x != 0) return;
 #pragma unroll
@@ -393,7 +538,7 @@ __global__ void __launch_bounds__(kKB) k_bicg_p(int nc, const T* r, const T* v, 
 }
 
 // v = A (rD p); alpha = rho1 / (rh . v)
-template <typename T, int NC>
+template <typename T, int NC, int MAXW>
 __global__ void __launch_bounds__(kKB) k_bicg_spmv1(Topo t, Mat<T> A, const T* rh, const T* y,
                                                     T* v, KWork w) {
   const unsigned act = active_mask<NC>(w);
@@ -403,7 +548,7 @@ __global__ void __launch_bounds__(kKB) k_bicg_spmv1(Topo t, Mat<T> A, const T* r
   // y = rD p is complete before the gather (written by k_bicg_scale)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     T a[NC];
-    spmv_row<T, NC>(t, A, i, y, a, act);
+    spmv_row<T, NC, MAXW>(t, A, i, y, a, act);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
       if (act >> c & 1) {
@@ -411,9 +556,10 @@ __global__ void __launch_bounds__(kKB) k_bicg_spmv1(Topo t, Mat<T> A, const T* r
         rv[c].add(rh[c * nc + i], a[c]);
       }
   }
-  double vv[NC], tot[NC];
+  typename DotAcc<T>::part_t vv[NC];
+  double tot[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) vv[c] = rv[c].get();
+  for (int c = 0; c < NC; ++c) vv[c] = rv[c].part();
   if (!grid_sum<NC>(w, vv, tot) || threadIdx.x != 0) return;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -456,9 +602,10 @@ __global__ void __launch_bounds__(kKB) k_bicg_s(int nc, const T* r, const T* v, 
         s_[k] = si;
         ss[c].add(si, si);
       }
-  double vv[NC], tot[NC];
+  typename DotAcc<T>::part_t vv[NC];
+  double tot[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) vv[c] = ss[c].get();
+  for (int c = 0; c < NC; ++c) vv[c] = ss[c].part();
   if (!grid_sum<NC>(w, vv, tot) || threadIdx.x != 0) return;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -486,7 +633,7 @@ __global__ void k_bicg_sfinish(int nc, const T* y, T* x, KWork w) {
 }
 
 // t = A (rD s); omega = (t.s)/(t.t)
-template <typename T, int NC>
+template <typename T, int NC, int MAXW>
 __global__ void __launch_bounds__(kKB) k_bicg_spmv2(Topo t, Mat<T> A, const T* z, const T* s_,
                                                     T* tv, KWork w) {
   unsigned act = 0;
@@ -498,7 +645,7 @@ __global__ void __launch_bounds__(kKB) k_bicg_spmv2(Topo t, Mat<T> A, const T* z
   DotAcc<T> ts[NC], tt[NC];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     T a[NC];
-    spmv_row<T, NC>(t, A, i, z, a, act);
+    spmv_row<T, NC, MAXW>(t, A, i, z, a, act);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
       if (act >> c & 1) {
@@ -507,11 +654,12 @@ __global__ void __launch_bounds__(kKB) k_bicg_spmv2(Topo t, Mat<T> A, const T* z
         tt[c].add(a[c], a[c]);
       }
   }
-  double vv[2 * NC], tot[2 * NC];
+  typename DotAcc<T>::part_t vv[2 * NC];
+  double tot[2 * NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    vv[2 * c] = ts[c].get();
-    vv[2 * c + 1] = tt[c].get();
+    vv[2 * c] = ts[c].part();
+    vv[2 * c + 1] = tt[c].part();
   }
   if (!grid_sum<2 * NC>(w, vv, tot) || threadIdx.x != 0) return;
 #pragma unroll
@@ -553,11 +701,12 @@ __global__ void __launch_bounds__(kKB) k_bicg_update(int nc, const T* y, const T
         rr[c].add(ri, ri);
         rhr[c].add(rh[k], ri);
       }
-  double vv[2 * NC], tot[2 * NC];
+  typename DotAcc<T>::part_t vv[2 * NC];
+  double tot[2 * NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    vv[2 * c] = rr[c].get();
-    vv[2 * c + 1] = rhr[c].get();
+    vv[2 * c] = rr[c].part();
+    vv[2 * c + 1] = rhr[c].part();
   }
   if (!grid_sum<2 * NC>(w, vv, tot) || threadIdx.x != 0) return;
 #pragma unroll
@@ -596,7 +745,7 @@ struct WsLayout {
 
 static int grid_for(const difvm_mesh* m) {
   int need = (int)blocks_for(m->nc, kKB);
-  return std::max(1, std::min(need, m->num_sms * 8));
+  return std::max(1, std::min(need, m->num_sms * 4));
 }
 
 static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
@@ -654,7 +803,7 @@ static difvm_status read_states(KState* host, const KWork& w, cudaStream_t st, b
   return DIFVM_OK;
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int MW>
 static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A, const T* b, T* x,
                              char* ws, const WsLayout& L, difvm_solve_info* info, cudaStream_t st,
                              KState* host_state) {
@@ -679,7 +828,7 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
       int n = std::min(chunk, w.maxit - it);
       for (int k = 0; k < n; ++k) {
         prof_before(DIFVM_PROF_PCG_SPMV, st);
-        k_pcg_spmv<T, NC><<<G, kKB, 0, st>>>(t, A, p, q, w);
+        k_pcg_spmv<T, NC, MW><<<G, kKB, 0, st>>>(t, A, p, q, w);
         prof_after(DIFVM_PROF_PCG_SPMV, st);
         prof_before(DIFVM_PROF_PCG_UPDATE, st);
         k_pcg_update<T, NC><<<G, kKB, 0, st>>>(nc, p, q, rD, x, r, w);
@@ -707,11 +856,11 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
       for (int k = 0; k < n; ++k) {
         k_bicg_p<T, NC><<<G, kKB, 0, st>>>(nc, r, v, p, w);
         k_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, p, rD, y, w);
-        k_bicg_spmv1<T, NC><<<G, kKB, 0, st>>>(t, A, rh, y, v, w);
+        k_bicg_spmv1<T, NC, MW><<<G, kKB, 0, st>>>(t, A, rh, y, v, w);
         k_bicg_s<T, NC><<<G, kKB, 0, st>>>(nc, r, v, s_, w);
         k_bicg_sfinish<T, NC><<<G, kKB, 0, st>>>(nc, y, x, w);
         k_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, s_, rD, z, w);
-        k_bicg_spmv2<T, NC><<<G, kKB, 0, st>>>(t, A, z, s_, tv, w);
+        k_bicg_spmv2<T, NC, MW><<<G, kKB, 0, st>>>(t, A, z, s_, tv, w);
         k_bicg_update<T, NC><<<G, kKB, 0, st>>>(nc, y, z, s_, tv, rh, x, r, w);
         for (int q = 0; q < 7; ++q) count_launch();
         DIFVM_TRY(check_launch("bicg_iter"));
@@ -734,21 +883,43 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
 }
 
 // ------------------------------------- mixed precision: reliable-update PCG
-// Single-RHS CG whose inner arithmetic (SpMV, vector updates, preconditioner)
-// is FP32 while the solution is accumulated in FP64 and the residual is
-// periodically REPLACED by the true FP64 residual r = b - A x64 (FP32 matrix
-// values are exact in FP64).  This is the iterative-refinement residual of the
-// pressure solve done without restarting the Krylov space (residual
-// replacement, van der Vorst & Ye, SIAM J. Sci. Comput. 22 (2000)): p keeps its
-// recursive update, r is replaced whenever the recursive residual norm has
-// dropped by 1e-2 since the last replacement, has reached the tolerance, or the
-// iteration cap is hit; the solve ends only when the TRUE FP64 residual meets
-// ||r|| <= max(tol_rel ||b||, tol_abs).
+// Single-RHS CG whose inner arithmetic (SpMV, vector updates, preconditioner,
+// reductions) is FP32 while the solution is accumulated as an unevaluated sum
+// of two FP32 words (x = hi + lo, about 48 significant bits, updated with
+// error-free transformations) and the residual is periodically REPLACED by the
+// true FP64 residual r = b - A (hi + lo) (FP32 matrix values are exact in
+// FP64).  This is the iterative-refinement residual of the pressure solve done
+// without restarting the Krylov space (residual replacement, van der Vorst &
+// Ye, SIAM J. Sci. Comput. 22 (2000)): p keeps its recursive update, r is
+// replaced whenever the recursive residual norm has dropped by 1e-2 since the
+// last replacement, has reached the tolerance, or the iteration cap is hit;
+// the solve ends only when the TRUE FP64 residual meets
+// ||r|| <= max(tol_rel ||b||, tol_abs).  No FP64 operation is executed per
+// cell on the ordinary iterations (B300 runs FP64 at ~1/60 of FP32).
 
-// init: r64 = b - A x64, r = (float) r64, p = rD r; bb, rr (FP64), rz
+__device__ __forceinline__ double ffx(const float* hi, const float* lo, int j) {
+  return (double)__ldg(hi + j) + (double)__ldg(lo + j);
+}
+
+// r64 = b - A x, over a row, x = hi + lo or the FP64 input
+template <bool FROM64>
+__device__ __forceinline__ double rr_row_residual(const Mat<float>& A, int i, const double* b,
+                                                  const double* x64, const float* hi,
+                                                  const float* lo) {
+  int base, step, wd;
+  ell_row(A.E, i, base, step, wd);
+  double y = (double)__ldg(A.D + i) * (FROM64 ? x64[i] : ffx(hi, lo, i));
+  for (int k = 0; k < wd; ++k) {
+    const int j = __ldg(A.E.col + base + step * k);
+    y = fma((double)__ldg(A.val + base + step * k), FROM64 ? x64[j] : ffx(hi, lo, j), y);
+  }
+  return b[i] - y;
+}
+
+// init: (hi, lo) = x64, r64 = b - A x64, r = (float) r64, p = rD r; bb, rr (FP64), rz
 __global__ void __launch_bounds__(kKB) k_rr_init(Topo t, Mat<float> A, int jacobi, const double* b,
-                                                 const double* x, float* r, float* p, float* rD,
-                                                 KWork w) {
+                                                 const double* x, float* hi, float* lo, float* r,
+                                                 float* p, float* rD, KWork w) {
   const int nc = t.nc;
   double bb = 0.0, rr = 0.0;
   DotAcc<float> rz;
@@ -756,12 +927,12 @@ __global__ void __launch_bounds__(kKB) k_rr_init(Topo t, Mat<float> A, int jacob
     const float di = __ldg(A.D + i);
     const float rd = jacobi ? 1.f / di : 1.f;
     rD[i] = rd;
-    double y = (double)di * x[i];
-    const int sl = i >> 5, lane = i & 31;
-    const int o = __ldg(A.E.soff + sl), wd = (__ldg(A.E.soff + sl + 1) - o) >> 5;
-    for (int k = 0; k < wd; ++k)
-      y = fma((double)__ldg(A.val + o + lane + 32 * k), x[__ldg(A.E.col + o + lane + 32 * k)], y);
-    const double bi = b[i], ri = bi - y;
+    const double xi = x[i];
+    const float h = (float)xi;
+    hi[i] = h;
+    lo[i] = (float)(xi - (double)h);
+    const double ri = rr_row_residual<true>(A, i, b, x, nullptr, nullptr);
+    const double bi = b[i];
     const float rf = (float)ri;
     r[i] = rf;
     p[i] = rf * rd;
@@ -787,21 +958,61 @@ __global__ void __launch_bounds__(kKB) k_rr_init(Topo t, Mat<float> A, int jacob
   if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
 }
 
-// x64 += alpha p; r -= alpha q; recursive rr, rz; decide on replacement; beta
-__global__ void __launch_bounds__(kKB) k_rr_update(int nc, const float* p, const float* q,
-                                                   const float* rD, double* x, float* r, KWork w) {
+// (hi, lo) += alpha p (error-free: TwoProduct of alpha p, TwoSum into hi,
+// renormalisation); r -= alpha q; recursive rr, rz; replacement decision; beta.
+// All arrays live in the 256-byte aligned workspace: 128-bit loads, four cells
+// per thread step, scalar tail.
+__device__ __forceinline__ void rr_update_one(float al, float pi, float qi, float rdi, float& h,
+                                              float& l, float& ri, DotAcc<float>& rr,
+                                              DotAcc<float>& rz) {
+  const float t = __fmul_rn(al, pi);
+  const float et = __fmaf_rn(al, pi, -t);
+  const float s = __fadd_rn(h, t);
+  const float z = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(t, z));
+  e = __fadd_rn(e, __fadd_rn(l, et));
+  const float hn = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(hn, s));
+  h = hn;
+  ri = ri - al * qi;
+  rr.add(ri, ri);
+  rz.add(ri, ri * rdi);
+}
+
+__global__ void __launch_bounds__(kKB) k_rr_update(int nc, const float* __restrict__ p,
+                                                   const float* __restrict__ q,
+                                                   const float* __restrict__ rD,
+                                                   float* __restrict__ hi, float* __restrict__ lo,
+                                                   float* __restrict__ r, KWork w) {
   if (w.st[0].done) return;
   const float al = (float)w.st[0].alpha;
-  const double ald = w.st[0].alpha;
   DotAcc<float> rr, rz;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    x[i] = fma(ald, (double)p[i], x[i]);
-    const float ri = r[i] - al * q[i];
-    r[i] = ri;
-    rr.add(ri, ri);
-    rz.add(ri, ri * rD[i]);
+  const int n4 = nc >> 2;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int g = tid; g < n4; g += stride) {
+    const float4 p4 = reinterpret_cast<const float4*>(p)[g];
+    const float4 q4 = reinterpret_cast<const float4*>(q)[g];
+    const float4 d4 = reinterpret_cast<const float4*>(rD)[g];
+    float4 h4 = reinterpret_cast<float4*>(hi)[g];
+    float4 l4 = reinterpret_cast<float4*>(lo)[g];
+    float4 r4 = reinterpret_cast<float4*>(r)[g];
+    rr_update_one(al, p4.x, q4.x, d4.x, h4.x, l4.x, r4.x, rr, rz);
+    rr_update_one(al, p4.y, q4.y, d4.y, h4.y, l4.y, r4.y, rr, rz);
+    rr_update_one(al, p4.z, q4.z, d4.z, h4.z, l4.z, r4.z, rr, rz);
+    rr_update_one(al, p4.w, q4.w, d4.w, h4.w, l4.w, r4.w, rr, rz);
+    reinterpret_cast<float4*>(hi)[g] = h4;
+    reinterpret_cast<float4*>(lo)[g] = l4;
+    reinterpret_cast<float4*>(r)[g] = r4;
   }
-  double v[2] = {rr.get(), rz.get()}, tot[2];
+  for (int i = 4 * n4 + tid; i < nc; i += stride) {
+    float h = hi[i], l = lo[i], ri = r[i];
+    rr_update_one(al, p[i], q[i], rD[i], h, l, ri, rr, rz);
+    hi[i] = h;
+    lo[i] = l;
+    r[i] = ri;
+  }
+  float2 v[2] = {rr.part(), rz.part()};
+  double tot[2];
   if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
   KState& s = w.st[0];
   s.iters += 1;
@@ -813,34 +1024,41 @@ __global__ void __launch_bounds__(kKB) k_rr_update(int nc, const float* p, const
 }
 
 // p = rD r + beta p (with the recursive r); on replacement steps also
-// r = (float)(b - A x64) and the FP64 true residual decides convergence.
-__global__ void __launch_bounds__(kKB) k_rr_pupdate(Topo t, Mat<float> A, const double* b,
-                                                    const double* x, float* r, const float* rD,
-                                                    float* p, KWork w) {
+// r = (float)(b - A (hi + lo)) and the FP64 true residual decides convergence.
+__global__ void __launch_bounds__(kKB, 4) k_rr_pupdate(Topo t, Mat<float> A, const double* b,
+                                                       const float* hi, const float* lo, float* r,
+                                                       const float* rD, float* p, KWork w) {
   if (w.st[0].done) return;
   const int nc = t.nc;
   const float be = (float)w.st[0].beta;
   const bool rep = w.st[0].sconv;
+  if (!rep) {
+    const int n4 = nc >> 2;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int g = tid; g < n4; g += stride) {
+      const float4 r4 = reinterpret_cast<const float4*>(r)[g];
+      const float4 d4 = reinterpret_cast<const float4*>(rD)[g];
+      float4 p4 = reinterpret_cast<float4*>(p)[g];
+      p4.x = r4.x * d4.x + be * p4.x;
+      p4.y = r4.y * d4.y + be * p4.y;
+      p4.z = r4.z * d4.z + be * p4.z;
+      p4.w = r4.w * d4.w + be * p4.w;
+      reinterpret_cast<float4*>(p)[g] = p4;
+    }
+    for (int i = 4 * n4 + tid; i < nc; i += stride) p[i] = r[i] * rD[i] + be * p[i];
+    return;
+  }
   double rr = 0.0;
   DotAcc<float> rz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     const float rd = rD[i];
-    const float ri = r[i];
-    p[i] = ri * rd + be * p[i];
-    if (rep) {
-      double y = (double)__ldg(A.D + i) * x[i];
-      const int sl = i >> 5, lane = i & 31;
-      const int o = __ldg(A.E.soff + sl), wd = (__ldg(A.E.soff + sl + 1) - o) >> 5;
-      for (int k = 0; k < wd; ++k)
-        y = fma((double)__ldg(A.val + o + lane + 32 * k), x[__ldg(A.E.col + o + lane + 32 * k)], y);
-      const double rt = b[i] - y;
-      const float rf = (float)rt;
-      r[i] = rf;
-      rr = fma(rt, rt, rr);
-      rz.add(rf, rf * rd);
-    }
+    p[i] = r[i] * rd + be * p[i];
+    const double rt = rr_row_residual<false>(A, i, b, nullptr, hi, lo);
+    const float rf = (float)rt;
+    r[i] = rf;
+    rr = fma(rt, rt, rr);
+    rz.add(rf, rf * rd);
   }
-  if (!rep) return;
   double v[2] = {rr, rz.get()}, tot[2];
   if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
   KState& s = w.st[0];
@@ -854,9 +1072,11 @@ __global__ void __launch_bounds__(kKB) k_rr_pupdate(Topo t, Mat<float> A, const 
   if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; }
 }
 
-__global__ void k_zero_x64(int nc, double* x, KWork w) {
-  if (!w.st[0].zero_rhs) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x[i] = 0.0;
+// x64 = hi + lo (or 0 for a zero right-hand side)
+__global__ void k_rr_final(int nc, const float* hi, const float* lo, double* x, KWork w) {
+  const bool z = w.st[0].zero_rhs;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+    x[i] = z ? 0.0 : (double)hi[i] + (double)lo[i];
 }
 
 __global__ void k_rr_info(const KState* st, difvm_solve_info* info) {
@@ -873,10 +1093,11 @@ __global__ void k_rr_info(const KState* st, difvm_solve_info* info) {
   *info = o;
 }
 
+// workspace: [r p q rD hi lo | ELL values | state | block partials | ticket]
 static size_t rr_bytes(const difvm_mesh* m, size_t* val_off, size_t* st_off, size_t* part_off,
                        size_t* tick_off) {
   size_t vb = up256((size_t)m->nc * 4);
-  size_t v0 = 4 * vb;  // r p q rD
+  size_t v0 = 6 * vb;
   size_t so = v0 + up256((size_t)std::max<int64_t>(m->ell_nslots, 1) * 4);
   size_t po = so + 256 * 4;
   size_t to = po + up256((size_t)grid_for(m) * kMaxParts * sizeof(double));
@@ -887,6 +1108,7 @@ static size_t rr_bytes(const difvm_mesh* m, size_t* val_off, size_t* st_off, siz
   return to + 256;
 }
 
+template <int MW>
 static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const float* D, const float* L,
                            const double* b64, double* x64, char* ws, size_t wsbytes,
                            difvm_solve_info* info, cudaStream_t st) {
@@ -896,6 +1118,7 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
   const int nc = m->nc, G = grid_for(m);
   const size_t vb = up256((size_t)nc * 4);
   float *r = (float*)ws, *p = (float*)(ws + vb), *q = (float*)(ws + 2 * vb), *rD = (float*)(ws + 3 * vb);
+  float *hi = (float*)(ws + 4 * vb), *lo = (float*)(ws + 5 * vb);
   float* val = (float*)(ws + vo);
   KWork w;
   w.st = (KState*)(ws + so);
@@ -910,7 +1133,7 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
   const int jac = o->precond != DIFVM_PRECOND_NONE;
   const int chunk = o->check_every > 0 ? o->check_every : 8;
   DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
-  k_rr_init<<<G, kKB, 0, st>>>(t, A, jac, b64, x64, r, p, rD, w);
+  k_rr_init<<<G, kKB, 0, st>>>(t, A, jac, b64, x64, hi, lo, r, p, rD, w);
   DIFVM_TRY(check_launch("rr_init"));
   KState hs[1];
   bool done = false;
@@ -919,13 +1142,13 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
   while (it < w.maxit + chunk) {
     for (int k = 0; k < chunk; ++k) {
       prof_before(DIFVM_PROF_PCG_SPMV, st);
-      k_pcg_spmv<float, 1><<<G, kKB, 0, st>>>(t, A, p, q, w);
+      k_pcg_spmv<float, 1, MW><<<G, kKB, 0, st>>>(t, A, p, q, w);
       prof_after(DIFVM_PROF_PCG_SPMV, st);
       prof_before(DIFVM_PROF_PCG_UPDATE, st);
-      k_rr_update<<<G, kKB, 0, st>>>(nc, p, q, rD, x64, r, w);
+      k_rr_update<<<G, kKB, 0, st>>>(nc, p, q, rD, hi, lo, r, w);
       prof_after(DIFVM_PROF_PCG_UPDATE, st);
       prof_before(DIFVM_PROF_PCG_PUPDATE, st);
-      k_rr_pupdate<<<G, kKB, 0, st>>>(t, A, b64, x64, r, rD, p, w);
+      k_rr_pupdate<<<G, kKB, 0, st>>>(t, A, b64, hi, lo, r, rD, p, w);
       prof_after(DIFVM_PROF_PCG_PUPDATE, st);
       count_launch(); count_launch();
       DIFVM_TRY(check_launch("rr_iter"));
@@ -934,8 +1157,8 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
     DIFVM_TRY(read_states<1>(hs, w, st, done));
     if (done) break;
   }
-  k_zero_x64<<<G, kKB, 0, st>>>(nc, x64, w);
-  DIFVM_TRY(check_launch("zero_x64"));
+  k_rr_final<<<G, kKB, 0, st>>>(nc, hi, lo, x64, w);
+  DIFVM_TRY(check_launch("rr_final"));
   if (info) {
     k_rr_info<<<1, 32, 0, st>>>(w.st, info);
     DIFVM_TRY(check_launch("rr_info"));
@@ -945,6 +1168,8 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
   if (s == DIFVM_OK && !hs[0].done) s = DIFVM_ENOTCONV;
   return (difvm_status)s;
 }
+
+static int maxw_bucket(const difvm_mesh* m) { return m->ell_wmax <= 4 ? 4 : (m->ell_wmax <= 8 ? 8 : 0); }
 
 // coefficient adjoint of a solve: Dbar -= bbar_i x_i, Lbar -= bbar_N x_O, Ubar -= bbar_O x_N
 template <typename T, int NC>
@@ -986,11 +1211,20 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
   DIFVM_TRY(fill_ell<T>(m, (const T*)L, (const T*)U, val, st));
   Mat<T> A{(const T*)D, m->ell(), val};
   KState hs[3];
-  switch (ncomp) {
-    case 1: return solve_nc<T, 1>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs);
-    case 2: return solve_nc<T, 2>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs);
-    case 3: return solve_nc<T, 3>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs);
+  const int mw = maxw_bucket(m);
+#define DIFVM_SOLVE(NC, MW) solve_nc<T, NC, MW>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs)
+  switch (ncomp * 16 + mw) {
+    case 16 + 4: return DIFVM_SOLVE(1, 4);
+    case 16 + 8: return DIFVM_SOLVE(1, 8);
+    case 16 + 0: return DIFVM_SOLVE(1, 0);
+    case 32 + 4: return DIFVM_SOLVE(2, 4);
+    case 32 + 8: return DIFVM_SOLVE(2, 8);
+    case 32 + 0: return DIFVM_SOLVE(2, 0);
+    case 48 + 4: return DIFVM_SOLVE(3, 4);
+    case 48 + 8: return DIFVM_SOLVE(3, 8);
+    case 48 + 0: return DIFVM_SOLVE(3, 0);
   }
+#undef DIFVM_SOLVE
   return set_error(DIFVM_EINVAL, "ncomp must be 1..3");
 }
 
@@ -1034,7 +1268,12 @@ extern "C" difvm_status difvm_krylov_solve_refine(difvm_mesh_t m, const difvm_so
     return set_error(DIFVM_EINVAL, "the mixed-precision solve is single-RHS PCG");
   if (U) return set_error(DIFVM_EINVAL, "the mixed-precision PCG needs a symmetric matrix (upper = NULL)");
   if (!b64 || !x64 || !ws) return set_error(DIFVM_EINVAL, "null vector or workspace");
-  return rr_pcg(m, o, D, L, b64, x64, (char*)ws, wsbytes, info, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (maxw_bucket(m)) {
+    case 4: return rr_pcg<4>(m, o, D, L, b64, x64, (char*)ws, wsbytes, info, st);
+    case 8: return rr_pcg<8>(m, o, D, L, b64, x64, (char*)ws, wsbytes, info, st);
+    default: return rr_pcg<0>(m, o, D, L, b64, x64, (char*)ws, wsbytes, info, st);
+  }
 }
 
 extern "C" difvm_status difvm_krylov_solve_bwd(difvm_mesh_t m, difvm_prec prec,

@@ -361,19 +361,30 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
       w = std::max(w, k);
     }
     soff[sl + 1] = soff[sl] + 32 * w;
+    m->ell_wmax = std::max(m->ell_wmax, w);
   }
+  // one width for all slices when padding costs little (uniform meshes): the
+  // SpMV then computes slice offsets instead of loading them
+  // (row-major within the uniform layout: slot = i * W + k, so a row of width 4
+  // is one 16-byte load of columns and one of values)
+  if ((int64_t)32 * m->ell_wmax * nsl <= (int64_t)soff[nsl] + soff[nsl] / 20) {
+    for (int sl = 0; sl <= nsl; ++sl) soff[sl] = 32 * m->ell_wmax * sl;
+    m->ell_w = m->ell_wmax;
+  }
+  const int uw = m->ell_w;
+  auto slot = [&](int i, int k) { return uw > 0 ? i * uw + k : soff[i >> 5] + 32 * k + (i & 31); };
   std::vector<int> ecol((size_t)std::max(soff[nsl], 1), 0), emap((size_t)std::max(soff[nsl], 1), -1);
   for (int i = 0; i < nc; ++i) {
-    const int sl = i >> 5, lane = i & 31, w = (soff[sl + 1] - soff[sl]) / 32;
+    const int sl = i >> 5, w = (soff[sl + 1] - soff[sl]) / 32;
     int k = 0;
     for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
       const int f = cent[e] >> 1;
       if (f >= ni) continue;
-      ecol[soff[sl] + 32 * k + lane] = (cent[e] & 1) ? on[f].x : on[f].y;
-      emap[soff[sl] + 32 * k + lane] = cent[e];
+      ecol[slot(i, k)] = (cent[e] & 1) ? on[f].x : on[f].y;
+      emap[slot(i, k)] = cent[e];
       ++k;
     }
-    for (; k < w; ++k) ecol[soff[sl] + 32 * k + lane] = i;
+    for (; k < w; ++k) ecol[slot(i, k)] = i;
   }
   m->ell_nsl = nsl;
   m->ell_nslots = soff[nsl];

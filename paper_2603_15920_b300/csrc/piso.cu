@@ -133,6 +133,15 @@ __global__ void __launch_bounds__(kPB) k_piso_windkessel(int ni, const int* psta
   for (int k = threadIdx.x; k < z; k += blockDim.x) pb[s + k - ni] = po;
 }
 
+// Limited explicit non-orthogonal correction: capped at psi/(1-psi) times the
+// magnitude of the face's orthogonal part; psi outside (0,1) means unlimited.
+template <typename T>
+__device__ __forceinline__ T limit_corr(T corr, T orth, T psi) {
+  if (!(psi > T(0) && psi < T(1))) return corr;
+  const T cap = psi / (T(1) - psi) * fabs(orth);
+  return fabs(corr) > cap ? (corr > T(0) ? cap : -cap) : corr;
+}
+
 // -------------------------------------------------------------- momentum
 // internal faces: Up = min(m,0) - nu c (row O, col N), Lo = -max(m,0) - nu c (row N, col O)
 template <typename T>
@@ -148,7 +157,7 @@ __global__ void k_mom_faces(int ni, Geo<T> g, T nu, const T* phi, T* Lo, T* Up) 
 // cells: D = V/dt + sum over faces; b = V/dt U^n + sigma nu (gradU)_f.k + boundary;
 // rhs = b - V grad p
 template <typename T, bool NONORTH>
-__global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt, const T* phi,
+__global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt, T psi, const T* phi,
                                                    const T* U, const T* Ub, const T* gradU,
                                                    const T* gradp, T* D, T* b, T* rhs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,7 +197,9 @@ __global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt
             const T gO = nside ? gj : gi[c][k], gN = nside ? gi[c][k] : gj;
             gf[k] = w * gO + (T(1) - w) * gN;
           }
-          const T corr = nu * (gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w);
+          const T uj = U[c * nc + j], ui = U[c * nc + i];
+          const T orth = ck.x * (nside ? ui - uj : uj - ui);
+          const T corr = nu * limit_corr(gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w, orth, psi);
           bc[c] += nside ? -corr : corr;
         }
       }
@@ -243,8 +254,8 @@ __global__ void __launch_bounds__(kPB) k_HbyA(Topo t, Geo<T> g, const T* D, cons
 // ---------------------------------------------------------------- pressure
 // per face: phiHbyA, a_f = rAU_f c_f, nonorth_f = rAU_f (grad p)_f . k_f, Lp = -a_f
 template <typename T, bool NONORTH>
-__global__ void k_p_faces(Topo t, Geo<T> g, const T* HbyA, const T* rAU, const T* Ub,
-                          const T* gradp, T* phiHbyA, T* af, T* nonorth, T* Lp) {
+__global__ void k_p_faces(Topo t, Geo<T> g, T psi, const T* HbyA, const T* rAU, const T* Ub,
+                          const T* gradp, const T* p, T* phiHbyA, T* af, T* nonorth, T* Lp) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nf) return;
   const int nc = t.nc, nb = t.nb;
@@ -267,7 +278,7 @@ __global__ void k_p_faces(Topo t, Geo<T> g, const T* HbyA, const T* rAU, const T
       T gf[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) gf[k] = w * gradp[k * nc + O] + (T(1) - w) * gradp[k * nc + N];
-      no = rf * (gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w);
+      no = rf * limit_corr(gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w, ck.x * (p[N] - p[O]), psi);
     }
     nonorth[f] = no;
   } else {
@@ -425,15 +436,18 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   }
   // 2. momentum predictor
   DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
-  if (o.nonorth) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U, Ub, 3, gradU, st));
+  const bool no_U = (o.nonorth & DIFVM_NONORTH_MOMENTUM) != 0;
+  const bool no_p = (o.nonorth & DIFVM_NONORTH_PRESSURE) != 0;
+  if (no_U) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U, Ub, 3, gradU, st));
   if (ni > 0) {
     k_mom_faces<T><<<Bi, kPB, 0, st>>>(ni, g, (T)o.nu, phi, Lo, Up);
     DIFVM_TRY(check_launch("mom_faces"));
   }
-  if (o.nonorth)
-    k_mom_cells<T, true><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), phi, U, Ub, gradU, gradp, D, b, rhs);
+  const T psi = (T)o.nonorth_limit;
+  if (no_U)
+    k_mom_cells<T, true><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi, U, Ub, gradU, gradp, D, b, rhs);
   else
-    k_mom_cells<T, false><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), phi, U, Ub, gradU, gradp, D, b, rhs);
+    k_mom_cells<T, false><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi, U, Ub, gradU, gradp, D, b, rhs);
   DIFVM_TRY(check_launch("mom_cells"));
   {
     difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
@@ -447,11 +461,11 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   for (int corr = 0; corr < o.n_corr; ++corr) {
     k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, U, HbyA, rAU);
     DIFVM_TRY(check_launch("HbyA"));
-    if (o.nonorth) {
+    if (no_p) {
       DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
-      k_p_faces<T, true><<<Bf, kPB, 0, st>>>(t, g, HbyA, rAU, Ub, gradp, phiH, af, no, Lp);
+      k_p_faces<T, true><<<Bf, kPB, 0, st>>>(t, g, psi, HbyA, rAU, Ub, gradp, p, phiH, af, no, Lp);
     } else {
-      k_p_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, HbyA, rAU, Ub, gradp, phiH, af, no, Lp);
+      k_p_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, psi, HbyA, rAU, Ub, gradp, p, phiH, af, no, Lp);
     }
     DIFVM_TRY(check_launch("p_faces"));
     k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb, pin, Dp, bp);

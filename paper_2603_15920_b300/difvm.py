@@ -28,6 +28,7 @@ WK_EXACT, WK_FE, WK_BE = 0, 1, 2
 PCG, BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
 RENUMBER_RCM, SORT_FACES = 1, 2
+NONORTH_MOMENTUM, NONORTH_PRESSURE, NONORTH_ALL = 1, 2, 3
 
 _STATUS = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOTCONV: "ENOTCONV",
            EBREAKDOWN: "EBREAKDOWN", ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT"}
@@ -64,7 +65,7 @@ class PisoOpts(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("n_corr", C.c_int32),
                 ("nonorth", C.c_int32), ("solve_U", SolveOpts), ("solve_p", SolveOpts),
                 ("pref_cell", C.c_int32), ("wk_scheme", C.c_int32), ("n_out", C.c_int32),
-                ("wk_patch", C.c_int32 * 16)]
+                ("wk_patch", C.c_int32 * 16), ("nonorth_limit", C.c_double)]
 
 
 class PisoInfo(C.Structure):
@@ -460,14 +461,17 @@ def difvm_flux_from_U(mesh, U, U_b, phi=None, stream=None):
 
 
 def piso_opts(nu, dt, n_corr=2, nonorth=True, solve_U=None, solve_p=None, pref_cell=0,
-              wk_scheme=WK_EXACT, wk_patch=()):
+              wk_scheme=WK_EXACT, wk_patch=(), nonorth_limit=1.0):
     o = PisoOpts()
-    o.nu, o.dt, o.n_corr, o.nonorth = float(nu), float(dt), int(n_corr), int(bool(nonorth))
+    # nonorth: True = momentum and pressure corrections, False = none, or a bitmask
+    mask = NONORTH_ALL if nonorth is True else (0 if nonorth is False else int(nonorth))
+    o.nu, o.dt, o.n_corr, o.nonorth = float(nu), float(dt), int(n_corr), mask
     o.solve_U = solve_U or solve_opts(BICGSTAB, 1e-10, max_iter=1000)
     o.solve_p = solve_p or solve_opts(PCG, 1e-10, max_iter=20000)
     o.pref_cell, o.wk_scheme, o.n_out = int(pref_cell), int(wk_scheme), len(wk_patch)
     for k, p in enumerate(wk_patch):
         o.wk_patch[k] = int(p)
+    o.nonorth_limit = float(nonorth_limit)
     return o
 
 

@@ -210,11 +210,11 @@ def _state_to_gpu(dm, U, p, phi, Ub, pb, dt=torch.float64):
             cuda(dm.to_bnd(Ub), dt), cuda(dm.to_bnd(pb), dt))
 
 
-def _piso(dm, prec, nu, dt, pref=0, tol=1e-12, refine=0, wk_patch=(), ncorr=2):
-    o = D.piso_opts(nu, dt, ncorr, True,
+def _piso(dm, prec, nu, dt, pref=0, tol=1e-12, refine=0, wk_patch=(), ncorr=2, psi=1.0, nonorth=True):
+    o = D.piso_opts(nu, dt, ncorr, nonorth,
                     solve_U=D.solve_opts(D.BICGSTAB, tol, max_iter=2000),
                     solve_p=D.solve_opts(D.PCG, tol, max_iter=20000, refine_max=refine),
-                    pref_cell=int(dm.cell_new_of_old[pref]), wk_patch=wk_patch)
+                    pref_cell=int(dm.cell_new_of_old[pref]), wk_patch=wk_patch, nonorth_limit=psi)
     return D.Piso(dm, prec, o)
 
 
@@ -274,19 +274,20 @@ def _cavity(n=6, seed=8):
     return m, Ub
 
 
-def test_piso_lid_cavity_f64_pinned_pressure():
+@pytest.mark.parametrize("psi,mask", [(1.0, 3), (1.0 / 3.0, 3), (1.0, 1)])
+def test_piso_lid_cavity_f64_pinned_pressure(psi, mask):
     m, Ub = _cavity()
     om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
     pref = 17
     U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
     phi = O.flux_from_U(om, U, Ub)
-    pg = _piso(dm, D.F64, 0.01, 0.02, pref=pref)
+    pg = _piso(dm, D.F64, 0.01, 0.05, pref=pref, psi=psi, nonorth=mask)
     worst = 0.0
     for _ in range(4):
         g = _state_to_gpu(dm, U, p, phi, Ub, pb)
         assert pg.step(*g)[0] == D.OK
-        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.02, tolU=1e-12,
-                                          tolp=1e-12, pref_cell=pref)
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12,
+                                          tolp=1e-12, pref_cell=pref, psi=psi, nonorth=mask)
         worst = max(worst, nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p),
                     nrel(dm.from_faces(host(g[2])), phi))
     assert worst < 1e-9, worst

@@ -243,3 +243,55 @@ def test_piso_windkessel_outlet_coupling():
     # after the first step all inflow leaves through the outlet
     inflow = -phi[m.patch_faces("inlet")].sum()
     np.testing.assert_allclose(phi[m.patch_faces("outlet")].sum(), inflow, rtol=1e-9)
+
+
+# ----------------------------------------------------------- limited correction
+def _cavity_run(n, dt, psi, steps, jitter=0.2):
+    m = mg.kuhn_cube(n, jitter, 0)
+    om = _om(m)
+    Ub = np.zeros((3, m.n_boundary))
+    Ub[0, m.patch_faces("y1") - m.n_internal] = 1.0
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    phi = O.flux_from_U(om, U, Ub)
+    peak = []
+    for _ in range(steps):
+        U, p, phi, pb, _, info = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=dt, psi=psi)
+        assert info["status"] == 0
+        peak.append(np.abs(U).max())
+    return np.array(peak)
+
+
+def test_limited_nonorthogonal_correction_keeps_the_tet_cavity_bounded():
+    # jittered Kuhn tets (max non-orthogonality ~65 deg) at CFL ~0.25: the lagged,
+    # unlimited over-relaxed pressure correction feeds a growing mode; capping the
+    # explicit part at psi/(1-psi) = 1/2 of the orthogonal part keeps |U| below the lid speed
+    limited = _cavity_run(16, 0.016, 1.0 / 3.0, 14)
+    assert limited.max() < 1.0
+    unlimited = _cavity_run(16, 0.016, 1.0, 14)
+    assert unlimited.max() > 2.0
+
+
+def test_limiter_caps_the_explicit_correction():
+    m = mg.kuhn_cube(4, 0.2, 3)
+    om = _om(m)
+    rng = np.random.default_rng(0)
+    U = rng.standard_normal((3, m.n_cells))
+    g = 50.0 * rng.standard_normal((3, 3, m.n_cells))     # large gradients: the cap is active
+    zero = np.zeros((3, m.n_boundary))
+    mf = np.zeros(m.n_faces)
+    nu, dt, psi = 0.3, 1.0, 0.25
+    b_plain = O.momentum_assemble(om, nu, dt, mf, U, zero, None)[3]
+    b_full = O.momentum_assemble(om, nu, dt, mf, U, zero, g)[3]
+    b_lim = O.momentum_assemble(om, nu, dt, mf, U, zero, g, psi=psi)[3]
+    # per-cell bound: the limited correction of every face is at most psi/(1-psi) |orth|
+    w, c, k = O.face_coeffs(om)
+    ni = m.n_internal
+    orth = np.abs(c[:ni] * (U[:, m.neighbour] - U[:, m.owner[:ni]]))      # [3, ni]
+    bound = np.zeros((3, m.n_cells))
+    for q in range(3):
+        np.add.at(bound[q], m.owner[:ni], nu * psi / (1 - psi) * orth[q])
+        np.add.at(bound[q], m.neighbour, nu * psi / (1 - psi) * orth[q])
+    assert np.all(np.abs(b_lim - b_plain) <= bound * (1 + 1e-12) + 1e-15)
+    assert np.abs(b_full - b_plain).max() > 2 * np.abs(b_lim - b_plain).max()
+    # psi = 1 is the unlimited over-relaxed correction
+    np.testing.assert_array_equal(O.momentum_assemble(om, nu, dt, mf, U, zero, g, psi=1.0)[3], b_full)
