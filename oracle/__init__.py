@@ -252,3 +252,37 @@ def piso_step(m: OMesh, U, p, phi, Ub, pb, *, nu, dt, ncorr=2, nonorth=True, tol
     return U, p, phi, pb, pc, dict(itU=list(info.itU), itp=list(info.itp)[:ncorr],
                                    status=info.status, Q=list(info.Q)[:n_out],
                                    po=list(info.po)[:n_out])
+
+
+def piso_step_bwd(m: OMesh, U, p, phi, Ub, pb, Ubar, pbar, phibar, pbbar=None, pcbar=(), *, nu,
+                  dt, ncorr=2, nonorth=True, tolU=1e-10, tolp=1e-10, tol_abs=0.0, maxitU=1000,
+                  maxitp=20000, pref_cell=0, wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(),
+                  wk_scheme=WK_EXACT, psi=1.0):
+    """Adjoint of ``piso_step`` at the inputs (U, p, phi, Ub, pb, pc).
+
+    (Ubar, pbar, phibar, pbbar, pcbar) are the adjoints of the step's outputs
+    (U, p, phi, pb, pc).  Returns a dict with the adjoints of the inputs
+    U, p, phi, pb, pc and of the parameters Ub, nu, Rp, Cw, Rd."""
+    U = _f64(np.array(U, np.float64)); p = _f64(np.array(p, np.float64))
+    phi = _f64(np.array(phi, np.float64)); pb = _f64(np.array(pb, np.float64))
+    Ub = _f64(np.reshape(Ub, (3, m.nb)))
+    wk_patch = _i32(np.atleast_1d(np.asarray(wk_patch, np.int32)))
+    n_out = int(wk_patch.shape[0])
+    Rp, Cw, Rd = (_f64(np.atleast_1d(np.asarray(a, np.float64))) for a in (Rp, Cw, Rd))
+    pc = _f64(np.array(np.atleast_1d(np.asarray(pc, np.float64))))
+    Ub_ = _f64(np.array(np.reshape(Ubar, (3, m.nc)), np.float64))
+    pb_ = _f64(np.array(pbar, np.float64))
+    phib_ = _f64(np.array(phibar, np.float64))
+    pbb_ = _f64(np.zeros(m.nb) if pbbar is None else np.array(pbbar, np.float64))
+    pcb_ = _f64(np.zeros(n_out) if len(np.atleast_1d(pcbar)) == 0
+                else np.array(np.atleast_1d(pcbar), np.float64))
+    Ubbar = np.zeros((3, m.nb)); nubar = C.c_double(0.0)
+    Rpb, Cb, Rdb = np.zeros(max(n_out, 1)), np.zeros(max(n_out, 1)), np.zeros(max(n_out, 1))
+    nonorth = 3 if nonorth is True else (0 if nonorth is False else int(nonorth))
+    opts = _PisoOpts(nu, dt, ncorr, nonorth, tolU, tolp, tol_abs, maxitU, maxitp, pref_cell,
+                     wk_scheme, n_out, _p(wk_patch), _p(Rp), _p(Cw), _p(Rd), psi)
+    st = lib().om_piso_step_bwd(m.ref(), C.byref(opts), _p(U), _p(p), _p(phi), _p(Ub), _p(pb),
+                                _p(pc), _p(Ub_), _p(pb_), _p(phib_), _p(pbb_), _p(pcb_),
+                                _p(Ubbar), C.byref(nubar), _p(Rpb), _p(Cb), _p(Rdb))
+    return dict(U=Ub_, p=pb_, phi=phib_, pb=pbb_, pc=pcb_[:n_out], Ub=Ubbar, nu=nubar.value,
+                Rp=Rpb[:n_out], Cw=Cb[:n_out], Rd=Rdb[:n_out], status=st)

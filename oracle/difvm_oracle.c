@@ -31,7 +31,8 @@
  *   a boundary face carries its boundary-condition value for every scheme.
  *
  * Parity pins: see tests/test_oracle_*.py (closed forms, invariants, dense
- * solves, the manufactured Poisson solution of Sec. 3.1.1).
+ * solves, the manufactured Poisson solution of Sec. 3.1.1; the adjoint of a
+ * PISO step against central differences of the forward step).
  * Parity unpinned: the interpolation weight on non-uniform meshes (w_f above
  * is a reading; every choice gives 0.5 on the uniform hex meshes that pin it).
  */
@@ -651,4 +652,400 @@ void om_flux_from_U(const om_mesh *m, const double *U, const double *Ub, double 
     phi[f] = ok ? dot3(uf, m->Sf + 3 * f) : 0.0;
   }
   free(bcU); free(w); free(c); free(k);
+}
+
+/* ======================================================= adjoint of a step */
+/* Reverse-mode derivative of om_piso_step (Sec. 2.5, Eq. vjp): given the
+ * adjoints of the step's outputs, return those of its inputs.  Each stage of
+ * the forward step above is a plain function of its inputs; its adjoint is
+ * written out here stage by stage, last stage first.  The two linear solves
+ * are differentiated implicitly (Eq. implicit_diff): for x = A^{-1} r,
+ *   r_bar = A^{-T} x_bar,   A_bar_ij = -r_bar_i x_j,
+ * with A^{-T} applied by the same Krylov method on the transposed matrix
+ * (lower and upper swapped; the pressure matrix is symmetric).  The upwind
+ * switch max(m, 0) and the limiter take the derivative of the branch the
+ * forward step took (max(0, 0) counts as the zero branch). */
+
+/* G^T of om_grad_gauss for one component: phib_bar may be NULL */
+static void grad_gauss_T(const om_mesh *m, const double *w, const int *bc, const double *gbar,
+                         double *phibar, double *phibbar) {
+  int nc = m->nc;
+  for (int f = 0; f < m->nf; ++f) {
+    const double *S = m->Sf + 3 * f;
+    int O = m->owner[f];
+    double gO[3], t;
+    for (int d = 0; d < 3; ++d) gO[d] = gbar[d * nc + O] / m->V[O];
+    if (f < m->nint) {
+      int N = m->neighbour[f];
+      double gN[3];
+      for (int d = 0; d < 3; ++d) gN[d] = gbar[d * nc + N] / m->V[N];
+      t = dot3(gO, S) - dot3(gN, S);          /* adjoint of the face value phi_f */
+      phibar[O] += w[f] * t;
+      phibar[N] += (1.0 - w[f]) * t;
+    } else {
+      int kind = bc[patch_of_face(m, f)];
+      if (kind == BC_EMPTY) continue;
+      t = dot3(gO, S);
+      if (kind == BC_FIXED) { if (phibbar) phibbar[f - m->nint] += t; }
+      else phibar[O] += t;
+    }
+  }
+}
+
+/* adjoint of limit_corr(corr, orth, psi) * 1: returns d/dcorr, sets *dorth */
+static double limit_corr_d(double corr, double orth, double psi, double *dorth) {
+  *dorth = 0.0;
+  if (psi >= 1.0) return 1.0;
+  double cap = psi / (1.0 - psi) * fabs(orth);
+  if (fabs(corr) > cap) {
+    double sc = corr > 0.0 ? 1.0 : -1.0, so = orth > 0.0 ? 1.0 : (orth < 0.0 ? -1.0 : 0.0);
+    *dorth = sc * psi / (1.0 - psi) * so;
+    return 0.0;
+  }
+  return 1.0;
+}
+
+/* Inputs: the step's inputs U, p, phi, Ub, pb, pc exactly as om_piso_step takes
+ * them (they are not modified).  In/out: Ubar[3][nc], pbar[nc], phibar[nf],
+ * pbbar[nb], pcbar[n_out] hold the adjoints of the step's outputs on entry and
+ * those of its inputs on return.  Accumulated: Ubbar[3][nb], *nubar and the
+ * Windkessel parameter adjoints Rpbar, Cbar, Rdbar[n_out].  Returns the worst
+ * status of the forward replay and the adjoint solves. */
+int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in,
+                     const double *p_in, const double *phi_in, const double *Ub,
+                     const double *pb_in, const double *pc_in, double *Ubar, double *pbar,
+                     double *phibar, double *pbbar, double *pcbar, double *Ubbar, double *nubar,
+                     double *Rpbar, double *Cbar, double *Rdbar) {
+  const int nc = m->nc, nf = m->nf, ni = m->nint, nb = nf - ni, K = o->ncorr;
+  const int nonU = (o->nonorth & 1) != 0, nonP = (o->nonorth & 2) != 0;
+  int status = 0;
+  int *bcU = malloc(sizeof(int) * m->npatch), *bcp = malloc(sizeof(int) * m->npatch);
+  int has_fixed_p = 0;
+  for (int q = 0; q < m->npatch; ++q) {
+    bcU[q] = bc_of_U(m->patch_type[q]);
+    bcp[q] = bc_of_p(m->patch_type[q]);
+    if (bcp[q] == BC_FIXED) has_fixed_p = 1;
+  }
+  double *w = malloc(sizeof(double) * (ni + 1)), *c = malloc(sizeof(double) * (nf + 1));
+  double *k = malloc(sizeof(double) * 3 * (ni + 1));
+  om_face_coeffs(m, w, c, k);
+  om_info si;
+
+  /* ---- forward replay, keeping what the reverse sweep reads ---- */
+  double *pb = malloc(sizeof(double) * (nb + 1));   /* boundary p after the Windkessel */
+  memcpy(pb, pb_in, sizeof(double) * nb);
+  double *Qw = calloc(o->n_out + 1, sizeof(double));
+  for (int j = 0; j < o->n_out; ++j) {
+    int q = o->wk_patch[j];
+    double Q = 0.0, pc = pc_in[j], po;
+    for (int f = m->patch_start[q]; f < m->patch_start[q] + m->patch_size[q]; ++f) Q += phi_in[f];
+    om_windkessel_update(1, o->wk_scheme, o->Rp + j, o->Cw + j, o->Rd + j, &Q, o->dt, &pc, &po);
+    for (int f = m->patch_start[q]; f < m->patch_start[q] + m->patch_size[q]; ++f) pb[f - ni] = po;
+    Qw[j] = Q;
+  }
+  double *gradU = malloc(sizeof(double) * 9 * nc);
+  double *D = malloc(sizeof(double) * nc), *Lo = malloc(sizeof(double) * (ni + 1));
+  double *Up = malloc(sizeof(double) * (ni + 1)), *b = malloc(sizeof(double) * 3 * nc);
+  double *rhs = malloc(sizeof(double) * nc), *rAU = malloc(sizeof(double) * nc);
+  double *Dp = malloc(sizeof(double) * nc), *Lp = malloc(sizeof(double) * (ni + 1));
+  double *bp = malloc(sizeof(double) * nc), *phiH = malloc(sizeof(double) * nf);
+  double *af = malloc(sizeof(double) * nf), *nonorth = malloc(sizeof(double) * (ni + 1));
+  /* Us[s] = U_s (U_0 = predicted velocity), ps[s] = p_s (p_0 = p^n), gp[s] = grad p_s,
+   * HbyA[s] of corrector s */
+  double *Us = malloc(sizeof(double) * 3 * nc * (K + 1)), *ps = malloc(sizeof(double) * nc * (K + 1));
+  double *gp = malloc(sizeof(double) * 3 * nc * (K + 1)), *HbyA = malloc(sizeof(double) * 3 * nc * K);
+  double *H = malloc(sizeof(double) * 3 * nc);
+  memcpy(ps, p_in, sizeof(double) * nc);
+  om_grad_gauss(m, bcp, 1, p_in, pb, gp);
+  if (nonU) om_grad_gauss(m, bcU, 3, U_in, Ub, gradU);
+  om_momentum_assemble(m, bcU, o->nu, o->dt, phi_in, U_in, Ub, nonU ? gradU : NULL, o->psi, D, Lo,
+                       Up, b);
+  memcpy(Us, U_in, sizeof(double) * 3 * nc);
+  for (int q = 0; q < 3; ++q) {
+    for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gp[q * nc + i];
+    int st = om_bicgstab(m, D, Lo, Up, rhs, Us + (size_t)q * nc, o->tolU, o->tol_abs, o->maxitU, &si);
+    if (st > status) status = st;
+  }
+  for (int i = 0; i < nc; ++i) rAU[i] = m->V[i] / D[i];
+  for (int s = 0; s < K; ++s) {
+    double *Uk = Us + (size_t)3 * nc * s, *Un = Uk + 3 * nc, *Hk = HbyA + (size_t)3 * nc * s;
+    double *pk = ps + (size_t)nc * s, *pn = pk + nc;
+    om_H(m, Lo, Up, b, Uk, H);
+    for (int q = 0; q < 3; ++q)
+      for (int i = 0; i < nc; ++i) Hk[q * nc + i] = H[q * nc + i] / D[i];
+    om_pressure_assemble(m, bcU, bcp, rAU, Hk, Ub, pb, nonP ? gp + (size_t)3 * nc * s : NULL, pk,
+                         o->psi, Dp, Lp, bp, phiH, af, nonorth);
+    if (!has_fixed_p) Dp[o->pref_cell] += Dp[o->pref_cell];
+    memcpy(pn, pk, sizeof(double) * nc);
+    int st = om_pcg(m, Dp, Lp, NULL, bp, pn, o->tolp, o->tol_abs, o->maxitp, &si);
+    if (st > status) status = st;
+    om_grad_gauss(m, bcp, 1, pn, pb, gp + (size_t)3 * nc * (s + 1));
+    for (int q = 0; q < 3; ++q)
+      for (int i = 0; i < nc; ++i)
+        Un[q * nc + i] = Hk[q * nc + i] - rAU[i] * gp[(size_t)3 * nc * (s + 1) + q * nc + i];
+  }
+  /* Dp and af are the same in every corrector (they depend on rAU only) */
+
+  /* ---- reverse sweep ---- */
+  double *Ucur = malloc(sizeof(double) * 3 * nc), *pcur = malloc(sizeof(double) * nc);
+  double *phio = malloc(sizeof(double) * nf);
+  memcpy(Ucur, Ubar, sizeof(double) * 3 * nc);
+  memcpy(pcur, pbar, sizeof(double) * nc);
+  memcpy(phio, phibar, sizeof(double) * nf);
+  double *pbb = calloc(nb + 1, sizeof(double));          /* adjoint of pb after the Windkessel */
+  double *Db = calloc(nc, sizeof(double)), *bb = calloc(3 * nc, sizeof(double));
+  double *Lob = calloc(ni + 1, sizeof(double)), *Upb = calloc(ni + 1, sizeof(double));
+  double *rAUb = calloc(nc, sizeof(double)), *HAb = malloc(sizeof(double) * 3 * nc);
+  double *gnext = calloc(3 * nc, sizeof(double)), *gb = malloc(sizeof(double) * 3 * nc);
+  double *lam = malloc(sizeof(double) * nc), *phiHb = malloc(sizeof(double) * nf);
+  double *afb = malloc(sizeof(double) * nf), *nob = malloc(sizeof(double) * (ni + 1));
+  for (int s = K - 1; s >= 0; --s) {
+    const double *Uk = Us + (size_t)3 * nc * s, *Hk = HbyA + (size_t)3 * nc * s;
+    const double *pk = ps + (size_t)nc * s, *pn = pk + nc;
+    const double *gk = gp + (size_t)3 * nc * s, *gn = gk + 3 * nc;
+    /* U_{s+1} = HbyA_s - rAU grad p_{s+1} */
+    for (int i = 0; i < nc; ++i)
+      for (int q = 0; q < 3; ++q) {
+        HAb[q * nc + i] = Ucur[q * nc + i];
+        rAUb[i] -= Ucur[q * nc + i] * gn[q * nc + i];
+        gb[q * nc + i] = gnext[q * nc + i] - rAU[i] * Ucur[q * nc + i];
+      }
+    /* grad p_{s+1} */
+    grad_gauss_T(m, w, bcp, gb, pcur, pbb);
+    /* Rhie-Chow flux correction; only the last corrector's flux leaves the step */
+    for (int f = 0; f < nf; ++f) { phiHb[f] = 0.0; afb[f] = 0.0; }
+    for (int f = 0; f < ni; ++f) nob[f] = 0.0;
+    if (s == K - 1) {
+      for (int f = 0; f < nf; ++f) {
+        double g = phio[f];
+        int O = m->owner[f];
+        phiHb[f] = g;
+        if (f < ni) {
+          int N = m->neighbour[f];
+          afb[f] -= g * (pn[N] - pn[O]);
+          nob[f] -= g;
+          pcur[N] -= af[f] * g;
+          pcur[O] += af[f] * g;
+        } else if (bcp[patch_of_face(m, f)] == BC_FIXED) {
+          afb[f] -= g * (pb[f - ni] - pn[O]);
+          pbb[f - ni] -= af[f] * g;
+          pcur[O] += af[f] * g;
+        }
+      }
+    }
+    /* pressure solve: lam = Dp^{-T} p_bar_{s+1} (the matrix is symmetric) */
+    for (int i = 0; i < nc; ++i) lam[i] = 0.0;
+    int st = om_pcg(m, Dp, Lp, NULL, pcur, lam, o->tolp, o->tol_abs, o->maxitp, &si);
+    if (st > status) status = st;
+    for (int i = 0; i < nc; ++i) pcur[i] = 0.0;      /* from here on: adjoint of p_s */
+    /* pressure assembly: Dp (with the pinned cell doubled), Lp = -a_f, bp */
+    for (int f = 0; f < nf; ++f) {
+      int O = m->owner[f];
+      double mO = (!has_fixed_p && O == o->pref_cell) ? 2.0 : 1.0;
+      double DpbO = -lam[O] * pn[O] * mO;             /* d/d(sum of a_f) at the owner */
+      if (f < ni) {
+        int N = m->neighbour[f];
+        double mN = (!has_fixed_p && N == o->pref_cell) ? 2.0 : 1.0;
+        double DpbN = -lam[N] * pn[N] * mN;
+        double Lpb = -(lam[O] * pn[N] + lam[N] * pn[O]);
+        afb[f] += DpbO + DpbN - Lpb;
+        double qb = lam[O] - lam[N];                  /* adjoint of -phiHbyA + nonorth */
+        phiHb[f] -= qb;
+        nob[f] += qb;
+      } else {
+        int p = patch_of_face(m, f);
+        if (bcU[p] == BC_EMPTY) continue;
+        phiHb[f] -= lam[O];
+        if (bcp[p] == BC_FIXED) {
+          afb[f] += DpbO + lam[O] * pb[f - ni];
+          pbb[f - ni] += lam[O] * af[f];
+        }
+      }
+    }
+    /* face quantities phiHbyA, a_f, nonorth of om_pressure_assemble */
+    for (int i = 0; i < 3 * nc; ++i) gnext[i] = 0.0;  /* collects the adjoint of grad p_s */
+    for (int f = 0; f < nf; ++f) {
+      const double *S = m->Sf + 3 * f;
+      int O = m->owner[f];
+      if (f < ni) {
+        int N = m->neighbour[f];
+        for (int d = 0; d < 3; ++d) {
+          HAb[d * nc + O] += w[f] * phiHb[f] * S[d];
+          HAb[d * nc + N] += (1.0 - w[f]) * phiHb[f] * S[d];
+        }
+        double rf = w[f] * rAU[O] + (1.0 - w[f]) * rAU[N];
+        double rfb = afb[f] * c[f];
+        if (nonP) {
+          double gf[3];
+          for (int d = 0; d < 3; ++d) gf[d] = w[f] * gk[d * nc + O] + (1.0 - w[f]) * gk[d * nc + N];
+          double corr = dot3(gf, k + 3 * f), orth = c[f] * (pk[N] - pk[O]), dorth;
+          rfb += nob[f] * limit_corr(corr, orth, o->psi);
+          double dcorr = limit_corr_d(corr, orth, o->psi, &dorth);
+          double lb = nob[f] * rf;
+          for (int d = 0; d < 3; ++d) {
+            gnext[d * nc + O] += w[f] * lb * dcorr * k[3 * f + d];
+            gnext[d * nc + N] += (1.0 - w[f]) * lb * dcorr * k[3 * f + d];
+          }
+          pcur[N] += lb * dorth * c[f];
+          pcur[O] -= lb * dorth * c[f];
+        }
+        rAUb[O] += w[f] * rfb;
+        rAUb[N] += (1.0 - w[f]) * rfb;
+      } else {
+        int p = patch_of_face(m, f), bf = f - ni;
+        if (bcU[p] == BC_EMPTY) continue;
+        if (bcU[p] == BC_FIXED) {
+          for (int d = 0; d < 3; ++d) Ubbar[d * nb + bf] += phiHb[f] * S[d];
+        } else {
+          for (int d = 0; d < 3; ++d) HAb[d * nc + O] += phiHb[f] * S[d];
+        }
+        if (bcp[p] == BC_FIXED) rAUb[O] += afb[f] * c[f];
+      }
+    }
+    /* HbyA_s = H(U_s)/D,  H = b - offdiag U_s */
+    for (int i = 0; i < 3 * nc; ++i) Ucur[i] = 0.0;      /* from here on: adjoint of U_s */
+    for (int q = 0; q < 3; ++q)
+      for (int i = 0; i < nc; ++i) {
+        double hb = HAb[q * nc + i] / D[i];
+        Db[i] -= hb * Hk[q * nc + i];
+        bb[q * nc + i] += hb;
+        HAb[q * nc + i] = hb;                            /* now the adjoint of H */
+      }
+    for (int f = 0; f < ni; ++f) {
+      int O = m->owner[f], N = m->neighbour[f];
+      for (int q = 0; q < 3; ++q) {
+        Ucur[q * nc + N] -= Up[f] * HAb[q * nc + O];
+        Ucur[q * nc + O] -= Lo[f] * HAb[q * nc + N];
+        Upb[f] -= HAb[q * nc + O] * Uk[q * nc + N];
+        Lob[f] -= HAb[q * nc + N] * Uk[q * nc + O];
+      }
+    }
+  }
+  /* rAU = V/D */
+  for (int i = 0; i < nc; ++i) Db[i] -= rAUb[i] * m->V[i] / (D[i] * D[i]);
+  /* momentum predictor: U_0 = A^{-1}(b - V grad p^n), solved per component on A^T */
+  const double *U0 = Us;
+  for (int q = 0; q < 3; ++q) {
+    double *lq = gb + (size_t)q * nc;                     /* gb reused for lambda_U */
+    for (int i = 0; i < nc; ++i) lq[i] = 0.0;
+    int st = om_bicgstab(m, D, Up, Lo, Ucur + (size_t)q * nc, lq, o->tolU, o->tol_abs, o->maxitU, &si);
+    if (st > status) status = st;
+  }
+  for (int q = 0; q < 3; ++q) {
+    const double *lq = gb + (size_t)q * nc, *u = U0 + (size_t)q * nc;
+    for (int i = 0; i < nc; ++i) {
+      Db[i] -= lq[i] * u[i];
+      bb[q * nc + i] += lq[i];
+      gnext[q * nc + i] -= m->V[i] * lq[i];               /* adjoint of grad p^n */
+    }
+    for (int f = 0; f < ni; ++f) {
+      int O = m->owner[f], N = m->neighbour[f];
+      Lob[f] -= lq[N] * u[O];
+      Upb[f] -= lq[O] * u[N];
+    }
+  }
+  /* grad p^n (predictor, and the corrector-0 non-orthogonal term) */
+  grad_gauss_T(m, w, bcp, gnext, pcur, pbb);
+  /* momentum assembly */
+  double *Un_b = malloc(sizeof(double) * 3 * nc), *phin_b = calloc(nf, sizeof(double));
+  double *gUb = calloc(9 * nc, sizeof(double));
+  double nub = 0.0;
+  for (int q = 0; q < 3; ++q)
+    for (int i = 0; i < nc; ++i) Un_b[q * nc + i] = m->V[i] / o->dt * bb[q * nc + i];
+  for (int f = 0; f < nf; ++f) {
+    int O = m->owner[f];
+    double mm = phi_in[f];
+    if (f < ni) {
+      int N = m->neighbour[f];
+      double hp = mm > 0.0 ? 1.0 : 0.0, hn = mm < 0.0 ? 1.0 : 0.0;
+      phin_b[f] += Db[O] * hp - Db[N] * hn + Upb[f] * hn - Lob[f] * hp;
+      nub += c[f] * (Db[O] + Db[N] - Upb[f] - Lob[f]);
+      if (nonU) {
+        for (int q = 0; q < 3; ++q) {
+          const double *g = gradU + (size_t)q * 3 * nc;
+          double gf[3];
+          for (int d = 0; d < 3; ++d) gf[d] = w[f] * g[d * nc + O] + (1.0 - w[f]) * g[d * nc + N];
+          double corr = dot3(gf, k + 3 * f);
+          double orth = c[f] * (U_in[q * nc + N] - U_in[q * nc + O]), dorth;
+          double cb = bb[q * nc + O] - bb[q * nc + N];
+          nub += cb * limit_corr(corr, orth, o->psi);
+          double dcorr = limit_corr_d(corr, orth, o->psi, &dorth);
+          double lb = o->nu * cb;
+          double *gq = gUb + (size_t)q * 3 * nc;
+          for (int d = 0; d < 3; ++d) {
+            gq[d * nc + O] += w[f] * lb * dcorr * k[3 * f + d];
+            gq[d * nc + N] += (1.0 - w[f]) * lb * dcorr * k[3 * f + d];
+          }
+          Un_b[q * nc + N] += lb * dorth * c[f];
+          Un_b[q * nc + O] -= lb * dorth * c[f];
+        }
+      }
+    } else {
+      int kind = bcU[patch_of_face(m, f)], bf = f - ni;
+      if (kind == BC_FIXED) {
+        double a = o->nu * c[f], s = 0.0;
+        for (int q = 0; q < 3; ++q) {
+          s += bb[q * nc + O] * Ub[q * nb + bf];
+          Ubbar[q * nb + bf] += (a - mm) * bb[q * nc + O];
+        }
+        nub += c[f] * (Db[O] + s);
+        phin_b[f] -= s;
+      } else if (kind == BC_ZEROGRAD) {
+        phin_b[f] += Db[O];
+      }
+    }
+  }
+  if (nonU)
+    for (int q = 0; q < 3; ++q)
+      grad_gauss_T(m, w, bcU, gUb + (size_t)q * 3 * nc, Un_b + (size_t)q * nc, Ubbar + (size_t)q * nb);
+  /* Windkessel: pb on an outlet patch is p_o, both inside the step and in its output */
+  for (int bf = 0; bf < nb; ++bf) pbb[bf] += pbbar[bf];
+  for (int j = 0; j < o->n_out; ++j) {
+    int q = o->wk_patch[j];
+    double pob = 0.0;
+    for (int f = m->patch_start[q]; f < m->patch_start[q] + m->patch_size[q]; ++f) {
+      pob += pbb[f - ni];
+      pbb[f - ni] = 0.0;
+    }
+    double Rp = o->Rp[j], Cw = o->Cw[j], Rd = o->Rd[j], Q = Qw[j], p0 = pc_in[j], dt = o->dt;
+    double dp0, dQ, dRd, dC;    /* partial derivatives of the new p_c */
+    if (o->wk_scheme == WK_EXACT) {
+      double e = exp(-dt / (Rd * Cw));
+      double de_dRd = e * dt / (Rd * Rd * Cw), de_dC = e * dt / (Rd * Cw * Cw);
+      dp0 = e;
+      dQ = Rd * (1.0 - e);
+      dRd = Q * (1.0 - e) + (p0 - Rd * Q) * de_dRd;
+      dC = (p0 - Rd * Q) * de_dC;
+    } else if (o->wk_scheme == WK_FE) {
+      dp0 = 1.0 - dt / (Rd * Cw);
+      dQ = dt / Cw;
+      dRd = dt * p0 / (Cw * Rd * Rd);
+      dC = -dt * (Q - p0 / Rd) / (Cw * Cw);
+    } else {
+      double den = 1.0 + dt / (Rd * Cw), num = p0 + dt * Q / Cw;
+      dp0 = 1.0 / den;
+      dQ = dt / (Cw * den);
+      dRd = num / (den * den) * dt / (Rd * Rd * Cw);
+      dC = -dt * Q / (Cw * Cw * den) + num / (den * den) * dt / (Rd * Cw * Cw);
+    }
+    double G = pcbar[j] + pob;                       /* adjoint of the new p_c */
+    double Qb = G * dQ + pob * Rp;
+    Rpbar[j] += pob * Q;
+    Cbar[j] += G * dC;
+    Rdbar[j] += G * dRd;
+    pcbar[j] = G * dp0;
+    for (int f = m->patch_start[q]; f < m->patch_start[q] + m->patch_size[q]; ++f) phin_b[f] += Qb;
+  }
+  memcpy(Ubar, Un_b, sizeof(double) * 3 * nc);
+  memcpy(pbar, pcur, sizeof(double) * nc);
+  memcpy(phibar, phin_b, sizeof(double) * nf);
+  memcpy(pbbar, pbb, sizeof(double) * nb);
+  *nubar += nub;
+  free(bcU); free(bcp); free(w); free(c); free(k); free(pb); free(Qw); free(gradU); free(D);
+  free(Lo); free(Up); free(b); free(rhs); free(rAU); free(Dp); free(Lp); free(bp); free(phiH);
+  free(af); free(nonorth); free(Us); free(ps); free(gp); free(HbyA); free(H); free(Ucur);
+  free(pcur); free(phio); free(pbb); free(Db); free(bb); free(Lob); free(Upb); free(rAUb);
+  free(HAb); free(gnext); free(gb); free(lam); free(phiHb); free(afb); free(nob); free(Un_b);
+  free(phin_b); free(gUb);
+  return status;
 }

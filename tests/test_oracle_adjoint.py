@@ -1,0 +1,115 @@
+"""Pins of the oracle's adjoint of one PISO step (Sec. 2.5, Eqs. vjp, implicit_diff).
+
+The adjoint is checked against central differences of the oracle's own forward
+step, one input or parameter at a time: for random output weights w and a
+random direction v,  <w, (F(x + h v) - F(x - h v)) / 2h>  must equal
+<J^T w, v>.  The forward step is pinned elsewhere (free stream, Poiseuille,
+continuity, Windkessel closed forms), so this ties the hand-written reverse
+sweep to the method itself.  Solver tolerances are set near round-off so the
+difference quotient is limited by truncation (h^2) and round-off / h only.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_15920_b300 import meshgen as mg
+
+
+def _case(kind, seed):
+    if kind == "cavity":                    # all walls: pressure pinned at one cell
+        m = mg.shuffle(mg.kuhn_cube(3, 0.2, seed), seed + 7)
+    else:
+        m = mg.shuffle(mg.kuhn_cube(3, 0.2, seed, patch_types=dict(x0=mg.INLET, x1=mg.OUTLET)),
+                       seed + 7)
+    om = O.OMesh.from_mesh(m)
+    rng = np.random.default_rng(seed)
+    U = 0.5 * rng.normal(size=(3, m.n_cells))
+    Ub = 0.5 * rng.normal(size=(3, m.n_boundary))
+    x = dict(U=U, p=rng.normal(size=m.n_cells), Ub=Ub,
+             phi=O.flux_from_U(om, U, Ub) + 0.01 * rng.normal(size=m.n_faces),
+             pb=rng.normal(size=m.n_boundary), pc=np.zeros(0))
+    kw = dict(nu=0.05, dt=0.02, ncorr=2, tolU=1e-15, tolp=1e-15, maxitU=5000, maxitp=5000,
+              pref_cell=5)
+    if kind.startswith("wk"):
+        outlet = [k for k, t in enumerate(m.patch_type) if t == mg.OUTLET]
+        kw.update(wk_patch=outlet, Rp=[0.3], Cw=[0.8], Rd=[1.2],
+                  wk_scheme=dict(wk_exact=O.WK_EXACT, wk_fe=O.WK_FE, wk_be=O.WK_BE)[kind])
+        x["pc"] = np.array([0.4])
+    return om, x, kw
+
+
+def _fwd(om, x, kw):
+    U, p, phi, pb, pc, info = O.piso_step(om, x["U"], x["p"], x["phi"], x["Ub"], x["pb"],
+                                          pc=x["pc"], **kw)
+    return dict(U=U, p=p, phi=phi, pb=pb, pc=pc)
+
+
+CASES = [  # (mesh / outlet kind, non-orthogonal mask, limiter psi, correctors)
+    ("wk_exact", 3, 1.0, 2),
+    ("wk_exact", 3, 0.5, 2),
+    ("wk_fe", 1, 0.3, 2),
+    ("wk_be", 0, 1.0, 1),
+    ("outlet", 3, 0.5, 3),
+    ("cavity", 3, 0.5, 2),
+    ("cavity", 2, 1.0, 3),
+]
+
+
+@pytest.mark.parametrize("kind,mask,psi,ncorr", CASES)
+def test_piso_step_adjoint_matches_central_differences(kind, mask, psi, ncorr):
+    om, x, kw = _case(kind, seed=len(kind) + mask)
+    kw.update(nonorth=mask, psi=psi, ncorr=ncorr)
+    y = _fwd(om, x, kw)
+    rng = np.random.default_rng(11)
+    w = {k: rng.normal(size=np.shape(v)) for k, v in y.items()}
+    adj = O.piso_step_bwd(om, x["U"], x["p"], x["phi"], x["Ub"], x["pb"], w["U"], w["p"],
+                          w["phi"], w["pb"], w["pc"], pc=x["pc"], **kw)
+    assert adj["status"] == 0
+    keys = ["U", "p", "phi", "pb", "Ub", "nu"]
+    if kind.startswith("wk"):
+        keys += ["pc", "Rp", "Cw", "Rd"]
+    h = 1e-5
+    for key in keys:
+        v = rng.normal(size=np.shape(x[key])) if key in x else 1.0
+
+        def shifted(s):
+            xx = {k: np.array(a, float) for k, a in x.items()}
+            kk = dict(kw)
+            if key in xx:
+                xx[key] = xx[key] + s * h * v
+            elif key == "nu":
+                kk["nu"] = kw["nu"] + s * h
+            else:
+                kk[key] = [kw[key][0] + s * h]
+            return _fwd(om, xx, kk)
+
+        yp, ym = shifted(1), shifted(-1)
+        dp = sum(np.sum(w[k] * (yp[k] - y[k])) for k in w) / h
+        dm = sum(np.sum(w[k] * (y[k] - ym[k])) for k in w) / h
+        an = float(np.sum(np.asarray(adj[key]) * v))
+        s = max(abs(an), 1.0)
+        if abs(0.5 * (dp + dm) - an) > 2e-6 * s:   # central difference, O(h^2), failed:
+            # only acceptable if an upwind or limiter switch lies within h of x; the
+            # adjoint is then the derivative of the branch taken at x, which the
+            # one-sided difference on that side sees
+            assert min(abs(dp - an), abs(dm - an)) <= 1e-5 * s, (key, dp, dm, an)
+
+
+def test_adjoint_of_windkessel_outlet_pressure_is_the_flux_adjoint():
+    # With only p_out weighted (through pb on the outlet), the adjoint reaching the
+    # outlet face fluxes is the same on every face of the patch: Q = sum of phi_f.
+    om, x, kw = _case("wk_exact", 2)
+    kw.update(nonorth=0, psi=1.0)
+    nb = om.nb
+    pbbar = np.zeros(nb)
+    q = kw["wk_patch"][0]
+    f0, nq = int(om.patch_start[q]) - om.nint, int(om.patch_size[q])
+    pbbar[f0:f0 + nq] = 1.0 / nq
+    adj = O.piso_step_bwd(om, x["U"], x["p"], x["phi"], x["Ub"], x["pb"], np.zeros((3, om.nc)),
+                          np.zeros(om.nc), np.zeros(om.nf), pbbar, [0.0], pc=x["pc"], **kw)
+    e = np.exp(-kw["dt"] / (1.2 * 0.8))
+    dpo_dQ = 1.2 * (1 - e) + 0.3             # d p_out / d Q of the exact RCR update
+    g = adj["phi"][om.nint + f0:om.nint + f0 + nq]
+    np.testing.assert_allclose(g, dpo_dQ, rtol=1e-14)
+    assert np.all(adj["pb"][f0:f0 + nq] == 0.0)       # the input p_b there is overwritten
+    np.testing.assert_allclose(adj["pc"], e, rtol=1e-14)
