@@ -331,6 +331,48 @@ typedef struct {
  * except wk (double).  Synchronises on Krylov convergence checks. */
 difvm_status difvm_piso_step(difvm_piso_t, void* U, void* p, void* phi, const void* U_b, void* p_b,
                              double* wk, difvm_piso_info* info_dev, void* stream);
+
+/* ------------------------------------------------------ adjoint of a step */
+/* Reverse-mode derivative of one PISO step (Sec. 2.5, Eq. vjp), written by hand
+ * stage by stage; the two linear solves are differentiated implicitly
+ * (Eq. implicit_diff): for x = A^{-1} r, r_bar = A^{-T} x_bar solved by the
+ * step's own Krylov method and settings on A^T, and A_bar = -r_bar x^T.
+ * Non-smooth switches (upwind max(m,0), the limiter of nonorth_limit) take the
+ * derivative of the branch the forward step took.
+ *
+ * Tape: device memory the caller owns, at least difvm_piso_tape_bytes(h) bytes,
+ * 256-byte aligned.  difvm_piso_step_record is difvm_piso_step (same arguments,
+ * same results, bit for bit) that also writes into the tape what the reverse
+ * sweep needs: the step's input U, p, phi, p_b after the Windkessel update, the
+ * capacitor pressures before it and the outlet flows, the predicted velocity
+ * and every corrector's U and p.  A tape belongs to the handle that wrote it. */
+size_t difvm_piso_tape_bytes(difvm_piso_t);
+difvm_status difvm_piso_step_record(difvm_piso_t, void* U, void* p, void* phi, const void* U_b,
+                                    void* p_b, double* wk, difvm_piso_info* info_dev, void* tape,
+                                    size_t tape_bytes, void* stream);
+/* Adjoint of the recorded step.  U_b and wk (its R_p, C, R_d) must be the
+ * values the recorded step used.  In place, like the forward step:
+ *   U_bar[3][nc], p_bar[nc], phi_bar[nf], p_b_bar[nb] hold on entry the
+ *   adjoints of the step's outputs U, p, phi, p_b and on return those of its
+ *   inputs (p_b_bar may be NULL: zero on entry, not returned); on Windkessel
+ *   patches the input p_b is overwritten by the step, so its adjoint is 0;
+ *   wk_bar: DEVICE double [4*n_out]; entries 0..2 (R_p, C, R_d) accumulate,
+ *   entry 3 holds the adjoint of p_c after the step on entry and before it on
+ *   return (NULL allowed without outlets).
+ * Accumulated: U_b_bar[3][nb] (may be NULL), *nu_bar (device double, may be
+ * NULL; a fixed-order FP64 sum).  info_dev (may be NULL): itU = iterations of
+ * the transposed momentum solve, itp = those of each corrector's adjoint
+ * pressure solve, Q = the outlet-flow adjoints, p_out = the outlet-pressure
+ * adjoints.  Field pointers are of the handle's precision.  The first call
+ * allocates the adjoint workspace (about 30 x nc + 10 x n_internal values);
+ * the handle's forward workspace is reused, so a forward step and a
+ * backward step must not run concurrently on one handle.  Every sum has a
+ * fixed order: results are bitwise reproducible.  Returns OK or the worst
+ * status of the adjoint solves; EINVAL for a short or misaligned tape. */
+difvm_status difvm_piso_step_bwd(difvm_piso_t, const void* tape, size_t tape_bytes,
+                                 const void* U_b, const double* wk, void* U_bar, void* p_bar,
+                                 void* phi_bar, void* p_b_bar, double* wk_bar, void* U_b_bar,
+                                 double* nu_bar, difvm_piso_info* info_dev, void* stream);
 /* Initial face flux phi_f = U_f . S_f (linear interpolation; boundary: U_b.S
  * for fixed velocity, U_O.S for zero gradient, 0 for empty). */
 difvm_status difvm_flux_from_U(difvm_mesh_t, difvm_prec, const void* U, const void* U_b,

@@ -35,6 +35,13 @@ struct difvm_piso {
   double *p64 = nullptr, *b64 = nullptr;
   difvm_solve_info* sinfo = nullptr;  // [3 + 4] device
   std::vector<void*> allocs;
+  // adjoint workspace, allocated by the first difvm_piso_step_bwd
+  bool adj_ready = false;
+  void *a_HAb = nullptr, *a_gpb = nullptr, *a_gpn = nullptr, *a_rAUb = nullptr, *a_Db = nullptr;
+  void *a_bb = nullptr, *a_Lob = nullptr, *a_Upb = nullptr, *a_lam = nullptr, *a_lamU = nullptr;
+  void *a_phiHb = nullptr, *a_rfb = nullptr, *a_lk = nullptr, *a_ld = nullptr, *a_phio = nullptr;
+  void *a_pbb = nullptr, *a_gUb = nullptr, *a_lkU = nullptr, *a_ldU = nullptr, *a_gp2 = nullptr;
+  double *a_nuf = nullptr, *a_part = nullptr;
 };
 
 namespace difvm {
@@ -65,6 +72,32 @@ __global__ void k_windkessel(int n, int scheme, const double* Rp, const double* 
   if (po) po[o] = out;
 }
 
+// Partial derivatives of the new p_c of one RCR step with respect to the old
+// p_c, Q, R_d and C (closed forms of the three updates).
+__device__ __forceinline__ void wk_partials(int scheme, double C, double Rd, double Q, double dt,
+                                            double p0, double& dp0, double& dq, double& drd,
+                                            double& dc) {
+  if (scheme == DIFVM_WK_EXACT) {
+    const double e = exp(-dt / (Rd * C));
+    dp0 = e;
+    dq = Rd * (1.0 - e);
+    const double de = p0 - Rd * Q;                 // d pc_out / d e
+    drd = de * e * dt / (Rd * Rd * C) + Q * (1.0 - e);
+    dc = de * e * dt / (Rd * C * C);
+  } else if (scheme == DIFVM_WK_FE) {
+    dp0 = 1.0 - dt / (Rd * C);
+    dq = dt / C;
+    drd = dt * p0 / (Rd * Rd * C);
+    dc = -dt * (Q - p0 / Rd) / (C * C);
+  } else {
+    const double M = 1.0 + dt / (Rd * C), N = p0 + dt * Q / C;
+    dp0 = 1.0 / M;
+    dq = dt / (C * M);
+    drd = N * dt / (M * M * Rd * Rd * C);
+    dc = -dt * Q / (C * C * M) + N * dt / (M * M * Rd * C * C);
+  }
+}
+
 // Adjoint of one RCR step (closed-form derivatives of the three updates).
 __global__ void k_windkessel_bwd(int n, int scheme, const double* Rp, const double* C,
                                  const double* Rd, const double* Q, double dt, const double* pc_in,
@@ -72,29 +105,11 @@ __global__ void k_windkessel_bwd(int n, int scheme, const double* Rp, const doub
                                  double* Qb, double* Rpb, double* Cb, double* Rdb) {
   int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
-  const double rp = Rp[o], c = C[o], rd = Rd[o], q = Q[o], p0 = pc_in[o];
+  const double rp = Rp[o], q = Q[o];
   const double pob_ = pob ? pob[o] : 0.0;
   const double g = (pcb ? pcb[o] : 0.0) + pob_;
   double dp0, dq, drd, dc;
-  if (scheme == DIFVM_WK_EXACT) {
-    const double e = exp(-dt / (rd * c));
-    dp0 = e;
-    dq = rd * (1.0 - e);
-    const double de = p0 - rd * q;                 // d pc_out / d e
-    drd = de * e * dt / (rd * rd * c) + q * (1.0 - e);
-    dc = de * e * dt / (rd * c * c);
-  } else if (scheme == DIFVM_WK_FE) {
-    dp0 = 1.0 - dt / (rd * c);
-    dq = dt / c;
-    drd = dt * p0 / (rd * rd * c);
-    dc = -dt * (q - p0 / rd) / (c * c);
-  } else {
-    const double M = 1.0 + dt / (rd * c), N = p0 + dt * q / c;
-    dp0 = 1.0 / M;
-    dq = dt / (c * M);
-    drd = N * dt / (M * M * rd * rd * c);
-    dc = -dt * q / (c * c * M) + N * dt / (M * M * rd * c * c);
-  }
+  wk_partials(scheme, C[o], Rd[o], q, dt, pc_in[o], dp0, dq, drd, dc);
   if (pc_in_bar) pc_in_bar[o] = g * dp0;
   if (Qb) Qb[o] += g * dq + pob_ * rp;
   if (Rpb) Rpb[o] += pob_ * q;
@@ -407,10 +422,502 @@ __global__ void k_piso_info(const difvm_solve_info* si, int ncorr, int status, i
   *out = r;
 }
 
+// ---------------------------------------------------------------- adjoint
+// Reverse sweep of one PISO step (Sec. 2.5, Eqs. vjp, implicit_diff).  Face
+// kernels compute each face's adjoint message once; cell kernels gather those
+// messages over the cell-CSR rows in ascending face order, so every sum has a
+// fixed order (no atomics, bitwise reproducible).  Non-smooth switches (upwind
+// max(m, 0), the limiter) take the derivative of the branch the forward step
+// took.
+
+// Derivative of limit_corr(corr, orth, psi): returns d/dcorr, writes d/dorth.
+template <typename T>
+__device__ __forceinline__ T limit_corr_d(T corr, T orth, T psi, T& dorth) {
+  dorth = T(0);
+  if (!(psi > T(0) && psi < T(1))) return T(1);
+  const T r = psi / (T(1) - psi);
+  if (fabs(corr) > r * fabs(orth)) {
+    const T so = orth > T(0) ? T(1) : (orth < T(0) ? T(-1) : T(0));
+    dorth = (corr > T(0) ? r : -r) * so;
+    return T(0);
+  }
+  return T(1);
+}
+
+// U_{s+1} = HbyA_s - rAU grad p_{s+1}:  HbyA_bar = U_bar, rAU_bar -= U_bar . grad p,
+// (grad p_{s+1})_bar = gpn - rAU U_bar   (gpn: that gradient's use in the next corrector)
+template <typename T>
+__global__ void k_adj_Ucorr(int nc, const T* Ub_, const T* gradp, const T* rAU, const T* gpn,
+                            T* HAb, T* rAUb, T* gpb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  const T r = rAU[i];
+  T acc = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T u = Ub_[c * nc + i];
+    HAb[c * nc + i] = u;
+    acc += u * gradp[c * nc + i];
+    gpb[c * nc + i] = gpn[c * nc + i] - r * u;
+  }
+  rAUb[i] -= acc;
+}
+
+// Rhie-Chow flux of the last corrector: p_bar_i += sum sigma a_f phi_bar_f; fixed-p
+// boundary faces also move -a_f phi_bar_f to p_b.
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_adj_flux_cells(Topo t, const T* af, const T* phio,
+                                                        T* pbar, T* pbb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  T acc = T(0);
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int ent = t.cent[e];
+    const int f = ent >> 1;
+    const T g = af[f] * phio[f];
+    if (f < t.ni) {
+      acc += (ent & 1) ? -g : g;
+    } else {
+      const int bb = f - t.ni;
+      if (face_kind(t, bb, DIFVM_BC_PRESSURE) == DIFVM_FACE_FIXED &&
+          face_kind(t, bb, DIFVM_BC_VELOCITY) != DIFVM_FACE_EMPTY) {
+        acc += g;
+        pbb[bb] -= g;
+      }
+    }
+  }
+  pbar[i] += acc;
+}
+
+// Pressure solve and assembly of corrector s, per face.  lam = A_p^{-1} p_bar_{s+1};
+// coefficient adjoints Dp_bar_i = -lam_i p_i (times 2 at the pinned cell),
+// Lp_bar_f = -(lam_O p_N + lam_N p_O) are folded into a_f_bar; bp_bar = lam gives
+// phiHbyA_bar and nonorth_bar.  Then k_p_faces backwards: phiHb (the face's
+// phiHbyA adjoint), rfb (adjoint of the interpolated rAU_f, or of rAU_O on a
+// fixed-p boundary face), lk / ld (limited non-orthogonal term: weight of the
+// interpolated grad p_s . k_f, and of p_s,N - p_s,O).
+template <typename T, bool NONORTH, bool LAST>
+__global__ void k_adj_pfaces(Topo t, Geo<T> g, T psi, int pin, const T* lam, const T* pn,
+                             const T* pk, const T* gk, const T* rAU, const T* af, const T* pb,
+                             const T* phio, T* phiHb, T* rfb, T* lk, T* ld, T* pbb, T* Ubb) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nf) return;
+  const int nc = t.nc, nb = t.nb;
+  const V4<T> ck = ld4(g.ck + f);
+  if (f < t.ni) {
+    const int2 on = t.on[f];
+    const int O = on.x, N = on.y;
+    const T lO = lam[O], lN = lam[N], pO = pn[O], pN = pn[N];
+    const T mO = O == pin ? T(2) : T(1), mN = N == pin ? T(2) : T(1);
+    T afb = lO * pN + lN * pO - lO * pO * mO - lN * pN * mN;
+    const T qb = lO - lN;
+    T phb = -qb, nob = qb;
+    if (LAST) {
+      const T gg = phio[f];
+      phb += gg;
+      afb -= gg * (pN - pO);
+      nob -= gg;
+    }
+    const T w = ld4(g.Sw + f).w;
+    T r = afb * ck.x;
+    if (NONORTH) {
+      const T rf = w * rAU[O] + (T(1) - w) * rAU[N];
+      T gf[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gf[k] = w * gk[k * nc + O] + (T(1) - w) * gk[k * nc + N];
+      const T corr = gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w;
+      const T orth = ck.x * (pk[N] - pk[O]);
+      r += nob * limit_corr(corr, orth, psi);
+      T dorth;
+      const T dcorr = limit_corr_d(corr, orth, psi, dorth);
+      const T lb = nob * rf;
+      lk[f] = lb * dcorr;
+      ld[f] = lb * dorth * ck.x;
+    }
+    phiHb[f] = phb;
+    rfb[f] = r;
+  } else {
+    const int bb = f - t.ni;
+    const int O = t.bown[bb];
+    const int ku = face_kind(t, bb, DIFVM_BC_VELOCITY);
+    if (ku == DIFVM_FACE_EMPTY) {
+      phiHb[f] = T(0);
+      rfb[f] = T(0);
+      return;
+    }
+    const T lO = lam[O];
+    T phb = -lO;
+    if (LAST) phb += phio[f];
+    T r = T(0);
+    if (face_kind(t, bb, DIFVM_BC_PRESSURE) == DIFVM_FACE_FIXED) {
+      const T pO = pn[O], mO = O == pin ? T(2) : T(1);
+      T afb = lO * pb[bb] - lO * pO * mO;
+      if (LAST) afb -= phio[f] * (pb[bb] - pO);
+      pbb[bb] += lO * af[f];
+      r = afb * ck.x;
+    }
+    if (ku == DIFVM_FACE_FIXED && Ubb) {
+      const V4<T> s = ld4(g.Sw + f);
+      Ubb[bb] += phb * s.x;
+      Ubb[nb + bb] += phb * s.y;
+      Ubb[2 * nb + bb] += phb * s.z;
+    }
+    phiHb[f] = phb;
+    rfb[f] = r;
+  }
+}
+
+// Gather of k_adj_pfaces: HbyA_bar and rAU_bar of corrector s, the adjoint of
+// grad p_s from its non-orthogonal use (overwrites gpn), limiter terms into p_bar_s.
+template <typename T, bool NONORTH>
+__global__ void __launch_bounds__(kPB) k_adj_pcells(Topo t, Geo<T> g, const T* phiHb,
+                                                    const T* rfb, const T* lk, const T* ld, T* HAb,
+                                                    T* rAUb, T* gpn, T* pbar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc;
+  T h[3], gacc[3] = {T(0), T(0), T(0)}, r = T(0), pacc = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) h[c] = HAb[c * nc + i];
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int ent = t.cent[e];
+    const int f = ent >> 1;
+    const V4<T> s = ld4(g.Sw + f);
+    const T ph = phiHb[f];
+    if (f < t.ni) {
+      const bool nside = ent & 1;
+      const T wi = nside ? T(1) - s.w : s.w;
+      h[0] += wi * ph * s.x;
+      h[1] += wi * ph * s.y;
+      h[2] += wi * ph * s.z;
+      r += wi * rfb[f];
+      if (NONORTH) {
+        const V4<T> ck = ld4(g.ck + f);
+        const T l = wi * lk[f];
+        gacc[0] += l * ck.y;
+        gacc[1] += l * ck.z;
+        gacc[2] += l * ck.w;
+        pacc += nside ? ld[f] : -ld[f];
+      }
+    } else {
+      const int bb = f - t.ni;
+      const int ku = face_kind(t, bb, DIFVM_BC_VELOCITY);
+      if (ku == DIFVM_FACE_EMPTY) continue;
+      if (ku == DIFVM_FACE_ZEROGRAD) {
+        h[0] += ph * s.x;
+        h[1] += ph * s.y;
+        h[2] += ph * s.z;
+      }
+      r += rfb[f];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) HAb[c * nc + i] = h[c];
+  rAUb[i] += r;
+  if (NONORTH) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gpn[c * nc + i] = gacc[c];
+    pbar[i] += pacc;
+  }
+}
+
+// HbyA_s = (b - N U_s)/D backwards: D_bar -= h_bar . HbyA, b_bar += h_bar,
+// U_bar_s = -N^T h_bar (overwritten), h_bar = HbyA_bar / D.
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_adj_HbyA(Topo t, const T* D, const T* Lo, const T* Up,
+                                                  const T* b, const T* Us, const T* HAb, T* Db,
+                                                  T* bb, T* Ubar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc;
+  T h[3], u[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) h[c] = b[c * nc + i];
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int ent = t.cent[e];
+    const int f = ent >> 1;
+    if (f >= t.ni) break;
+    const int2 on = t.on[f];
+    const bool nside = ent & 1;
+    const int j = nside ? on.x : on.y;
+    const T a = nside ? Lo[f] : Up[f];     // row i, column j
+    const T aT = nside ? Up[f] : Lo[f];    // row j, column i
+    const T rDj = T(1) / D[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h[c] -= a * Us[c * nc + j];
+      u[c] -= aT * (HAb[c * nc + j] * rDj);
+    }
+  }
+  const T di = D[i];
+  T dacc = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T hb = HAb[c * nc + i] / di;
+    dacc += hb * (h[c] / di);
+    bb[c * nc + i] += hb;
+    Ubar[c * nc + i] = u[c];
+  }
+  Db[i] -= dacc;
+}
+
+// Off-diagonal coefficient adjoints of the HbyA products: Up_bar_f -= h_bar_O . U_s,N,
+// Lo_bar_f -= h_bar_N . U_s,O.
+template <typename T>
+__global__ void k_adj_LU(int ni, int nc, const int2* on, const T* D, const T* HAb, const T* Us,
+                         T* Lob, T* Upb) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= ni) return;
+  const int2 o = on[f];
+  const T rO = T(1) / D[o.x], rN = T(1) / D[o.y];
+  T su = T(0), sl = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    su += HAb[c * nc + o.x] * rO * Us[c * nc + o.y];
+    sl += HAb[c * nc + o.y] * rN * Us[c * nc + o.x];
+  }
+  Upb[f] -= su;
+  Lob[f] -= sl;
+}
+
+// Momentum predictor backwards, per cell: lamU = A^{-T} U_bar_0;  D_bar gets the
+// solve term and rAU = V/D; b_bar += lamU; (grad p^n)_bar -= V lamU; then
+// U_bar^n = V/dt b_bar (overwrites U_bar).
+template <typename T>
+__global__ void k_adj_mom_cells(int nc, Geo<T> g, T rdt, const T* D, const T* lamU,
+                                const T* Ustar, const T* rAUb, T* Db, T* bb, T* gpn, T* Ubar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  const T V = g.V[i], di = D[i];
+  T d = Db[i] - rAUb[i] * V / (di * di);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T l = lamU[c * nc + i];
+    d -= l * Ustar[c * nc + i];
+    const T bv = bb[c * nc + i] + l;
+    bb[c * nc + i] = bv;
+    gpn[c * nc + i] -= V * l;
+    Ubar[c * nc + i] = V * rdt * bv;
+  }
+  Db[i] = d;
+}
+
+// Momentum assembly backwards, per face: the face flux adjoint (upwind switch),
+// the viscosity adjoint contribution (FP64, reduced later in a fixed order), the
+// limited non-orthogonal correction (lkU / ldU per component), U_b_bar.
+template <typename T, bool NONORTH>
+__global__ void k_adj_mom_faces(Topo t, Geo<T> g, T nu, T psi, const T* phi0, const T* Db,
+                                const T* bb, const T* Lob, const T* Upb, const T* lamU,
+                                const T* Ustar, const T* U0, const T* gradU, const T* Ub, T* phib,
+                                double* nuf, T* lkU, T* ldU, T* Ubb) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nf) return;
+  const int nc = t.nc, nb = t.nb, ni = t.ni;
+  const T m = phi0[f];
+  const V4<T> ck = ld4(g.ck + f);
+  if (f < ni) {
+    const int2 on = t.on[f];
+    const int O = on.x, N = on.y;
+    T upt = Upb[f], lot = Lob[f];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      upt -= lamU[c * nc + O] * Ustar[c * nc + N];
+      lot -= lamU[c * nc + N] * Ustar[c * nc + O];
+    }
+    const T dO = Db[O], dN = Db[N];
+    const bool hp = m > T(0), hn = m < T(0);
+    phib[f] = (hp ? dO - lot : T(0)) + (hn ? upt - dN : T(0));
+    double nv = (double)(ck.x * (dO + dN - upt - lot));
+    if (NONORTH) {
+      const T w = ld4(g.Sw + f).w;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T gf[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          gf[k] = w * gradU[(c * 3 + k) * nc + O] + (T(1) - w) * gradU[(c * 3 + k) * nc + N];
+        const T corr = gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w;
+        const T orth = ck.x * (U0[c * nc + N] - U0[c * nc + O]);
+        const T cb = bb[c * nc + O] - bb[c * nc + N];
+        nv += (double)(cb * limit_corr(corr, orth, psi));
+        T dorth;
+        const T dcorr = limit_corr_d(corr, orth, psi, dorth);
+        const T lb = nu * cb;
+        lkU[c * ni + f] = lb * dcorr;
+        ldU[c * ni + f] = lb * dorth * ck.x;
+      }
+    }
+    nuf[f] = nv;
+  } else {
+    const int b = f - ni;
+    const int O = t.bown[b];
+    const int kind = face_kind(t, b, DIFVM_BC_VELOCITY);
+    if (kind == DIFVM_FACE_FIXED) {
+      const T a = nu * ck.x;
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T bo = bb[c * nc + O];
+        s += bo * Ub[c * nb + b];
+        if (Ubb) Ubb[c * nb + b] += (a - m) * bo;
+      }
+      phib[f] = -s;
+      nuf[f] = (double)(ck.x * (Db[O] + s));
+    } else {
+      phib[f] = kind == DIFVM_FACE_ZEROGRAD ? Db[O] : T(0);
+      nuf[f] = 0.0;
+    }
+  }
+}
+
+// Gather of the momentum non-orthogonal terms: (grad U^n)_bar (overwritten) and
+// the limiter's U^n_bar terms.
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_adj_mom_cells2(Topo t, Geo<T> g, const T* lkU,
+                                                        const T* ldU, T* gUb, T* Ubar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc, ni = t.ni;
+  T ga[3][3], ua[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    ua[c] = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ga[c][k] = T(0);
+  }
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int ent = t.cent[e];
+    const int f = ent >> 1;
+    if (f >= ni) break;
+    const bool nside = ent & 1;
+    const T w = ld4(g.Sw + f).w;
+    const T wi = nside ? T(1) - w : w;
+    const V4<T> ck = ld4(g.ck + f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T l = wi * lkU[c * ni + f];
+      ga[c][0] += l * ck.y;
+      ga[c][1] += l * ck.z;
+      ga[c][2] += l * ck.w;
+      const T d = ldU[c * ni + f];
+      ua[c] += nside ? d : -d;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gUb[(c * 3 + k) * nc + i] = ga[c][k];
+    Ubar[c * nc + i] += ua[c];
+  }
+}
+
+// Fixed-order FP64 sum: kRedBlocks blocks stride the array, one block adds the
+// partial sums in block order and accumulates into *out.
+constexpr int kRedBlocks = 296;
+__global__ void __launch_bounds__(kPB) k_sum_partial(int n, const double* a, double* part) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kPB + threadIdx.x; i < n; i += kRedBlocks * kPB) s += a[i];
+  __shared__ double sm[kPB];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kPB / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void k_sum_final(const double* part, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 0; k < kRedBlocks; ++k) s += part[k];
+  *out += s;
+}
+
+template <typename T>
+__global__ void k_axpy1(int n, const T* a, T* b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] += a[i];
+}
+
+// Windkessel backwards, one block per outlet: p_out_bar = sum of the patch's p_b
+// adjoint (the patch's input p_b is overwritten, so its adjoint is zero), RCR
+// step derivatives, then Q_bar is added to every face flux of the patch.
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_adj_windkessel(int ni, const int* pstart, const int* psize,
+                                                        int scheme, double dt, const double* wk,
+                                                        const double* pc_in, const double* Q,
+                                                        T* pbb, T* phib, double* wkb,
+                                                        double* Qbar, double* pobar) {
+  const int o = blockIdx.x;
+  const int s = pstart[o], z = psize[o];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < z; k += blockDim.x) {
+    acc += (double)pbb[s + k - ni];
+    pbb[s + k - ni] = T(0);
+  }
+  __shared__ double sm[kPB / 32];
+  __shared__ double qb_sh;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double pob = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) pob += sm[k];
+    const double Rp = wk[4 * o], C = wk[4 * o + 1], Rd = wk[4 * o + 2], q = Q[o];
+    double dp0, dq, drd, dc;
+    wk_partials(scheme, C, Rd, q, dt, pc_in[o], dp0, dq, drd, dc);
+    const double G = wkb[4 * o + 3] + pob;
+    const double qb = G * dq + pob * Rp;
+    wkb[4 * o] += pob * q;
+    wkb[4 * o + 1] += G * dc;
+    wkb[4 * o + 2] += G * drd;
+    wkb[4 * o + 3] = G * dp0;
+    Qbar[o] = qb;
+    pobar[o] = pob;
+    qb_sh = qb;
+  }
+  __syncthreads();
+  const T qb = (T)qb_sh;
+  for (int k = threadIdx.x; k < z; k += blockDim.x) phib[s + k] += qb;
+}
+
+// p_c before the step, for the tape
+__global__ void k_tape_wk_in(int n_out, const double* wk, double* pc_in) {
+  int o = threadIdx.x;
+  if (o < n_out) pc_in[o] = wk[4 * o + 3];
+}
+
 // ---------------------------------------------------------------- driver
+// Tape of one recorded step (byte offsets, each section 256-byte aligned):
+// U^n [3][nc], U_s [n_corr+1][3][nc] (U_0 = predicted velocity, U_s after
+// corrector s), p_s [n_corr+1][nc] (p_0 = p^n), phi^n [nf], p_b after the
+// Windkessel update [nb], then FP64 p_c before the step [16] and Q [16].
+struct TapeLayout {
+  size_t U0, Us, ps, phi, pb, wk, bytes;
+};
+static TapeLayout tape_layout(const difvm_piso* h) {
+  const difvm_mesh* m = h->m;
+  const size_t e = h->elt, nc = m->nc, K = h->o.n_corr;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  TapeLayout L;
+  size_t off = 0;
+  L.U0 = off; off = al(off + 3 * nc * e);
+  L.Us = off; off = al(off + 3 * nc * e * (K + 1));
+  L.ps = off; off = al(off + nc * e * (K + 1));
+  L.phi = off; off = al(off + (size_t)m->nf * e);
+  L.pb = off; off = al(off + (size_t)std::max(m->nb, 1) * e);
+  L.wk = off; off = al(off + 32 * sizeof(double));
+  L.bytes = off;
+  return L;
+}
+
 template <typename T>
 static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, T* pb, double* wk,
-                                difvm_piso_info* info, cudaStream_t st) {
+                                difvm_piso_info* info, unsigned char* tape, cudaStream_t st) {
   difvm_mesh* m = h->m;
   const int nc = m->nc, ni = m->ni, nf = m->nf;
   const difvm_piso_opts& o = h->o;
@@ -425,6 +932,19 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   double* Qd = (double*)(h->sinfo + 8);
   double* pod = Qd + 16;
   int worst = DIFVM_OK;
+  TapeLayout TL{};
+  const size_t v3 = 3 * (size_t)nc * sizeof(T), v1 = (size_t)nc * sizeof(T);
+  if (o.n_out > 0 && !wk) return set_error(DIFVM_EINVAL, "Windkessel outlets need the wk state array");
+  if (tape) {
+    TL = tape_layout(h);
+    DIFVM_CUDA(cudaMemcpyAsync(tape + TL.U0, U, v3, cudaMemcpyDeviceToDevice, st));
+    DIFVM_CUDA(cudaMemcpyAsync(tape + TL.ps, p, v1, cudaMemcpyDeviceToDevice, st));
+    DIFVM_CUDA(cudaMemcpyAsync(tape + TL.phi, phi, (size_t)nf * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    if (o.n_out > 0) {
+      k_tape_wk_in<<<1, 32, 0, st>>>(o.n_out, wk, (double*)(tape + TL.wk));
+      DIFVM_TRY(check_launch("tape_wk_in"));
+    }
+  }
   // 1. Windkessel outlets
   if (o.n_out > 0) {
     if (!wk) return set_error(DIFVM_EINVAL, "Windkessel outlets need the wk state array");
@@ -433,6 +953,16 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     k_piso_windkessel<T><<<o.n_out, kPB, 0, st>>>(ni, tab, tab + 16, o.wk_scheme, o.dt, phi, pb, wk,
                                                     Qd, pod);
     DIFVM_TRY(check_launch("piso_windkessel"));
+  }
+  if (tape) {
+    const size_t nbb = (size_t)m->nb * sizeof(T);
+    if (pb && nbb)
+      DIFVM_CUDA(cudaMemcpyAsync(tape + TL.pb, pb, nbb, cudaMemcpyDeviceToDevice, st));
+    else if (nbb)
+      DIFVM_CUDA(cudaMemsetAsync(tape + TL.pb, 0, nbb, st));
+    if (o.n_out > 0)
+      DIFVM_CUDA(cudaMemcpyAsync(tape + TL.wk + 16 * sizeof(double), Qd, o.n_out * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
   }
   // 2. momentum predictor
   DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
@@ -456,6 +986,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     if (s == DIFVM_EINVAL || s == DIFVM_ECUDA) return s;
     worst = std::max(worst, (int)s);
   }
+  if (tape) DIFVM_CUDA(cudaMemcpyAsync(tape + TL.Us, U, v3, cudaMemcpyDeviceToDevice, st));
   // 3. pressure correctors
   const int pin = h->has_fixed_p ? -1 : o.pref_cell;
   for (int corr = 0; corr < o.n_corr; ++corr) {
@@ -492,6 +1023,10 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
     k_U_correct<T><<<Bc, kPB, 0, st>>>(nc, HbyA, rAU, gradp, U);
     DIFVM_TRY(check_launch("U_correct"));
+    if (tape) {
+      DIFVM_CUDA(cudaMemcpyAsync(tape + TL.Us + (corr + 1) * v3, U, v3, cudaMemcpyDeviceToDevice, st));
+      DIFVM_CUDA(cudaMemcpyAsync(tape + TL.ps + (corr + 1) * v1, p, v1, cudaMemcpyDeviceToDevice, st));
+    }
   }
   if (info) {
     k_piso_info<<<1, 32, 0, st>>>(h->sinfo, o.n_corr, DIFVM_OK, o.n_out, Qd, pod, info);
@@ -632,7 +1167,262 @@ extern "C" difvm_status difvm_piso_step(difvm_piso_t h, void* U, void* p, void* 
   cudaStream_t st = (cudaStream_t)stream;
   if (h->prec == DIFVM_F64)
     return piso_step_t<double>(h, (double*)U, (double*)p, (double*)phi, (const double*)Ub,
-                               (double*)pb, wk, info, st);
+                               (double*)pb, wk, info, nullptr, st);
   return piso_step_t<float>(h, (float*)U, (float*)p, (float*)phi, (const float*)Ub, (float*)pb, wk,
-                            info, st);
+                            info, nullptr, st);
+}
+
+// ---------------------------------------------------------------- adjoint driver
+static difvm_status adj_alloc(difvm_piso* h) {
+  if (h->adj_ready) return DIFVM_OK;
+  const difvm_mesh* m = h->m;
+  const size_t e = h->elt, nc = m->nc, ni = std::max(m->ni, 1), nf = m->nf;
+  const size_t nb = std::max(m->nb, 1);
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) return false;
+    h->allocs.push_back(*p);
+    return true;
+  };
+  bool ok = alloc(&h->a_HAb, 3 * nc * e) && alloc(&h->a_gpb, 3 * nc * e) &&
+            alloc(&h->a_gpn, 3 * nc * e) && alloc(&h->a_rAUb, nc * e) && alloc(&h->a_Db, nc * e) &&
+            alloc(&h->a_bb, 3 * nc * e) && alloc(&h->a_Lob, ni * e) && alloc(&h->a_Upb, ni * e) &&
+            alloc(&h->a_lam, nc * e) && alloc(&h->a_lamU, 3 * nc * e) &&
+            alloc(&h->a_phiHb, nf * e) && alloc(&h->a_rfb, nf * e) && alloc(&h->a_lk, ni * e) &&
+            alloc(&h->a_ld, ni * e) && alloc(&h->a_phio, nf * e) && alloc(&h->a_pbb, nb * e) &&
+            alloc(&h->a_gUb, 9 * nc * e) && alloc(&h->a_lkU, 3 * ni * e) &&
+            alloc(&h->a_ldU, 3 * ni * e) && alloc(&h->a_gp2, 3 * nc * e) &&
+            alloc((void**)&h->a_nuf, nf * sizeof(double)) &&
+            alloc((void**)&h->a_part, kRedBlocks * sizeof(double));
+  if (!ok) return set_error(DIFVM_ENOMEM, "device allocation for the PISO adjoint workspace failed");
+  h->adj_ready = true;
+  return DIFVM_OK;
+}
+
+// lam = A_p^{-1} rhs with the forward step's pressure matrix and solver
+// settings (zero initial guess; the matrix is symmetric, so A^{-T} = A^{-1}).
+template <typename T>
+static difvm_status adj_psolve(difvm_piso* h, const T* rhs, T* lam, difvm_solve_info* si,
+                               cudaStream_t st) {
+  difvm_mesh* m = h->m;
+  const int nc = m->nc;
+  const unsigned Bc = blocks_for(nc, kPB);
+  if (h->mixed) {
+    k_to64<T><<<Bc, kPB, 0, st>>>(nc, rhs, h->b64);
+    DIFVM_TRY(check_launch("to64"));
+    DIFVM_CUDA(cudaMemsetAsync(h->p64, 0, (size_t)nc * sizeof(double), st));
+    difvm_status s = difvm_krylov_solve_refine(m, &h->o.solve_p, (const float*)h->Dp,
+                                               (const float*)h->Lp, nullptr, h->b64, h->p64, 1,
+                                               h->wsp, h->wsp_bytes, si, st);
+    if (s == DIFVM_EINVAL || s == DIFVM_ECUDA) return s;
+    k_from64<T><<<Bc, kPB, 0, st>>>(nc, h->p64, lam);
+    DIFVM_TRY(check_launch("from64"));
+    return s;
+  }
+  DIFVM_CUDA(cudaMemsetAsync(lam, 0, (size_t)nc * sizeof(T), st));
+  difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
+  return difvm_krylov_solve(m, pr, &h->o.solve_p, h->Dp, h->Lp, nullptr, rhs, lam, 1, h->wsp,
+                            h->wsp_bytes, si, st);
+}
+
+template <typename T>
+static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, const T* Ub,
+                                    const double* wk, T* Ubar, T* pbar, T* phibar, T* pbbar,
+                                    double* wkbar, T* Ubbar, double* nubar, difvm_piso_info* info,
+                                    cudaStream_t st) {
+  difvm_mesh* m = h->m;
+  const int nc = m->nc, ni = m->ni, nf = m->nf, nb = m->nb, K = h->o.n_corr;
+  const difvm_piso_opts& o = h->o;
+  Topo t = m->topo();
+  Geo<T> g = geo<T>(m);
+  const unsigned Bc = blocks_for(nc, kPB), Bf = blocks_for(nf, kPB), Bi = blocks_for(std::max(ni, 1), kPB);
+  const TapeLayout TL = tape_layout(h);
+  const size_t v3 = 3 * (size_t)nc, v1 = nc;
+  const T* U0 = (const T*)(tape + TL.U0);
+  const T* Us = (const T*)(tape + TL.Us);
+  const T* ps = (const T*)(tape + TL.ps);
+  const T* phi0 = (const T*)(tape + TL.phi);
+  const T* pb1 = (const T*)(tape + TL.pb);
+  const double* pc_in = (const double*)(tape + TL.wk);
+  const double* Qrec = pc_in + 16;
+  T *gradp = (T*)h->gradp, *gradU = (T*)h->gradU, *D = (T*)h->D, *Lo = (T*)h->Lo, *Up = (T*)h->Up;
+  T *b = (T*)h->b, *rhs = (T*)h->rhs, *rAU = (T*)h->rAU, *HbyA = (T*)h->HbyA, *Dp = (T*)h->Dp;
+  T *Lp = (T*)h->Lp, *bp = (T*)h->bp, *phiH = (T*)h->phiHbyA, *af = (T*)h->af;
+  T* no = (T*)h->nonorth;
+  T *HAb = (T*)h->a_HAb, *gpb = (T*)h->a_gpb, *gpn = (T*)h->a_gpn, *rAUb = (T*)h->a_rAUb;
+  T *Db = (T*)h->a_Db, *bb = (T*)h->a_bb, *Lob = (T*)h->a_Lob, *Upb = (T*)h->a_Upb;
+  T *lam = (T*)h->a_lam, *lamU = (T*)h->a_lamU, *phiHb = (T*)h->a_phiHb, *rfb = (T*)h->a_rfb;
+  T *lk = (T*)h->a_lk, *ld = (T*)h->a_ld, *phio = (T*)h->a_phio, *pbb = (T*)h->a_pbb;
+  T *gUb = (T*)h->a_gUb, *lkU = (T*)h->a_lkU, *ldU = (T*)h->a_ldU, *gp2 = (T*)h->a_gp2;
+  const bool no_U = (o.nonorth & DIFVM_NONORTH_MOMENTUM) != 0;
+  const bool no_p = (o.nonorth & DIFVM_NONORTH_PRESSURE) != 0;
+  const T psi = (T)o.nonorth_limit;
+  const int pin = h->has_fixed_p ? -1 : o.pref_cell;
+  const difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
+  double* Qb = (double*)(h->sinfo + 8);
+  double* pob = Qb + 16;
+  int worst = DIFVM_OK;
+
+  // recompute the forward step's matrices from the tape
+  DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, ps, pb1, 1, gradp, st));
+  if (no_U) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U0, Ub, 3, gradU, st));
+  if (ni > 0) {
+    k_mom_faces<T><<<Bi, kPB, 0, st>>>(ni, g, (T)o.nu, phi0, Lo, Up);
+    DIFVM_TRY(check_launch("mom_faces"));
+  }
+  if (no_U)
+    k_mom_cells<T, true><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi0, U0, Ub, gradU, gradp, D, b, rhs);
+  else
+    k_mom_cells<T, false><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi0, U0, Ub, gradU, gradp, D, b, rhs);
+  DIFVM_TRY(check_launch("mom_cells"));
+  k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, Us, HbyA, rAU);
+  DIFVM_TRY(check_launch("HbyA"));
+  k_p_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, psi, HbyA, rAU, Ub, gradp, ps, phiH, af, no, Lp);
+  DIFVM_TRY(check_launch("p_faces"));
+  k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb1, pin, Dp, bp);
+  DIFVM_TRY(check_launch("p_cells"));
+
+  // adjoint state
+  DIFVM_CUDA(cudaMemcpyAsync(phio, phibar, (size_t)nf * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  if (nb > 0) {
+    if (pbbar)
+      DIFVM_CUDA(cudaMemcpyAsync(pbb, pbbar, (size_t)nb * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    else
+      DIFVM_CUDA(cudaMemsetAsync(pbb, 0, (size_t)nb * sizeof(T), st));
+  }
+  DIFVM_CUDA(cudaMemsetAsync(gpn, 0, v3 * sizeof(T), st));
+  DIFVM_CUDA(cudaMemsetAsync(rAUb, 0, v1 * sizeof(T), st));
+  DIFVM_CUDA(cudaMemsetAsync(Db, 0, v1 * sizeof(T), st));
+  DIFVM_CUDA(cudaMemsetAsync(bb, 0, v3 * sizeof(T), st));
+  DIFVM_CUDA(cudaMemsetAsync(Lob, 0, (size_t)std::max(ni, 1) * sizeof(T), st));
+  DIFVM_CUDA(cudaMemsetAsync(Upb, 0, (size_t)std::max(ni, 1) * sizeof(T), st));
+
+  // pressure correctors, last first
+  for (int s = K - 1; s >= 0; --s) {
+    const T* Uk = Us + s * v3;
+    const T* pk = ps + s * v1;
+    const T* pn = pk + v1;
+    DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, pn, pb1, 1, gradp, st));
+    k_adj_Ucorr<T><<<Bc, kPB, 0, st>>>(nc, Ubar, gradp, rAU, gpn, HAb, rAUb, gpb);
+    DIFVM_TRY(check_launch("adj_Ucorr"));
+    DIFVM_TRY(difvm_grad_gauss_bwd(m, pr, DIFVM_BC_PRESSURE, gpb, 1, pbar, pbb, st));
+    const bool last = s == K - 1;
+    if (last) {
+      k_adj_flux_cells<T><<<Bc, kPB, 0, st>>>(t, af, phio, pbar, pbb);
+      DIFVM_TRY(check_launch("adj_flux_cells"));
+    }
+    {
+      difvm_status sv = adj_psolve<T>(h, pbar, lam, h->sinfo + 3 + std::min(s, 3), st);
+      if (sv == DIFVM_EINVAL || sv == DIFVM_ECUDA) return sv;
+      worst = std::max(worst, (int)sv);
+    }
+    DIFVM_CUDA(cudaMemsetAsync(pbar, 0, v1 * sizeof(T), st));   // now the adjoint of p_s
+    if (no_p) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, pk, pb1, 1, gp2, st));
+#define DIFVM_PF(NO, LA)                                                                          \
+  k_adj_pfaces<T, NO, LA><<<Bf, kPB, 0, st>>>(t, g, psi, pin, lam, pn, pk, gp2, rAU, af, pb1,    \
+                                              phio, phiHb, rfb, lk, ld, pbb, Ubbar)
+    if (no_p) { if (last) DIFVM_PF(true, true); else DIFVM_PF(true, false); }
+    else { if (last) DIFVM_PF(false, true); else DIFVM_PF(false, false); }
+#undef DIFVM_PF
+    DIFVM_TRY(check_launch("adj_pfaces"));
+    if (no_p)
+      k_adj_pcells<T, true><<<Bc, kPB, 0, st>>>(t, g, phiHb, rfb, lk, ld, HAb, rAUb, gpn, pbar);
+    else
+      k_adj_pcells<T, false><<<Bc, kPB, 0, st>>>(t, g, phiHb, rfb, lk, ld, HAb, rAUb, gpn, pbar);
+    DIFVM_TRY(check_launch("adj_pcells"));
+    k_adj_HbyA<T><<<Bc, kPB, 0, st>>>(t, D, Lo, Up, b, Uk, HAb, Db, bb, Ubar);
+    DIFVM_TRY(check_launch("adj_HbyA"));
+    if (ni > 0) {
+      k_adj_LU<T><<<Bi, kPB, 0, st>>>(ni, nc, t.on, D, HAb, Uk, Lob, Upb);
+      DIFVM_TRY(check_launch("adj_LU"));
+    }
+  }
+
+  // momentum predictor: lamU = A^{-T} U_bar_0 (lower and upper swapped)
+  DIFVM_CUDA(cudaMemsetAsync(lamU, 0, v3 * sizeof(T), st));
+  {
+    difvm_status sv = difvm_krylov_solve(m, pr, &o.solve_U, D, Up, Lo, Ubar, lamU, 3, h->wsU,
+                                         h->wsU_bytes, h->sinfo, st);
+    if (sv == DIFVM_EINVAL || sv == DIFVM_ECUDA) return sv;
+    worst = std::max(worst, (int)sv);
+  }
+  k_adj_mom_cells<T><<<Bc, kPB, 0, st>>>(nc, g, (T)(1.0 / o.dt), D, lamU, Us, rAUb, Db, bb, gpn, Ubar);
+  DIFVM_TRY(check_launch("adj_mom_cells"));
+  DIFVM_TRY(difvm_grad_gauss_bwd(m, pr, DIFVM_BC_PRESSURE, gpn, 1, pbar, pbb, st));
+  if (no_U)
+    k_adj_mom_faces<T, true><<<Bf, kPB, 0, st>>>(t, g, (T)o.nu, psi, phi0, Db, bb, Lob, Upb, lamU, Us,
+                                                  U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, Ubbar);
+  else
+    k_adj_mom_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, (T)o.nu, psi, phi0, Db, bb, Lob, Upb, lamU, Us,
+                                                   U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, Ubbar);
+  DIFVM_TRY(check_launch("adj_mom_faces"));
+  if (no_U) {
+    k_adj_mom_cells2<T><<<Bc, kPB, 0, st>>>(t, g, lkU, ldU, gUb, Ubar);
+    DIFVM_TRY(check_launch("adj_mom_cells2"));
+    DIFVM_TRY(difvm_grad_gauss_bwd(m, pr, DIFVM_BC_VELOCITY, gUb, 3, Ubar, Ubbar, st));
+  }
+  if (nubar) {
+    k_sum_partial<<<kRedBlocks, kPB, 0, st>>>(nf, h->a_nuf, h->a_part);
+    k_sum_final<<<1, 32, 0, st>>>(h->a_part, nubar);
+    DIFVM_TRY(check_launch("sum_nu"));
+  }
+  // Windkessel outlets
+  if (o.n_out > 0) {
+    int* tab = (int*)(pob + 16);
+    k_adj_windkessel<T><<<o.n_out, kPB, 0, st>>>(ni, tab, tab + 16, o.wk_scheme, o.dt, wk, pc_in,
+                                                  Qrec, pbb, phibar, wkbar, Qb, pob);
+    DIFVM_TRY(check_launch("adj_windkessel"));
+  }
+  if (pbbar && nb > 0)
+    DIFVM_CUDA(cudaMemcpyAsync(pbbar, pbb, (size_t)nb * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  if (info) {
+    k_piso_info<<<1, 32, 0, st>>>(h->sinfo, K, DIFVM_OK, o.n_out, Qb, pob, info);
+    DIFVM_TRY(check_launch("piso_info"));
+  }
+  return (difvm_status)worst;
+}
+
+extern "C" size_t difvm_piso_tape_bytes(difvm_piso_t h) { return h ? tape_layout(h).bytes : 0; }
+
+extern "C" difvm_status difvm_piso_step_record(difvm_piso_t h, void* U, void* p, void* phi,
+                                               const void* Ub, void* pb, double* wk,
+                                               difvm_piso_info* info, void* tape,
+                                               size_t tape_bytes, void* stream) {
+  if (!h) return set_error(DIFVM_EINVAL, "null PISO handle");
+  if (!U || !p || !phi) return set_error(DIFVM_EINVAL, "null state field");
+  if (!tape) return set_error(DIFVM_EINVAL, "null tape");
+  if ((uintptr_t)tape % 256 != 0) return set_error(DIFVM_EINVAL, "the tape must be 256-byte aligned");
+  if (tape_bytes < tape_layout(h).bytes)
+    return set_error(DIFVM_EINVAL, "tape of %zu bytes, the step needs %zu", tape_bytes,
+                     tape_layout(h).bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->prec == DIFVM_F64)
+    return piso_step_t<double>(h, (double*)U, (double*)p, (double*)phi, (const double*)Ub,
+                               (double*)pb, wk, info, (unsigned char*)tape, st);
+  return piso_step_t<float>(h, (float*)U, (float*)p, (float*)phi, (const float*)Ub, (float*)pb, wk,
+                            info, (unsigned char*)tape, st);
+}
+
+extern "C" difvm_status difvm_piso_step_bwd(difvm_piso_t h, const void* tape, size_t tape_bytes,
+                                            const void* Ub, const double* wk, void* U_bar,
+                                            void* p_bar, void* phi_bar, void* p_b_bar,
+                                            double* wk_bar, void* U_b_bar, double* nu_bar,
+                                            difvm_piso_info* info, void* stream) {
+  if (!h) return set_error(DIFVM_EINVAL, "null PISO handle");
+  if (!tape || !U_bar || !p_bar || !phi_bar) return set_error(DIFVM_EINVAL, "null argument");
+  if ((uintptr_t)tape % 256 != 0) return set_error(DIFVM_EINVAL, "the tape must be 256-byte aligned");
+  if (tape_bytes < tape_layout(h).bytes)
+    return set_error(DIFVM_EINVAL, "tape of %zu bytes, the step needs %zu", tape_bytes,
+                     tape_layout(h).bytes);
+  if (h->o.n_out > 0 && (!wk || !wk_bar))
+    return set_error(DIFVM_EINVAL, "Windkessel outlets need wk and wk_bar");
+  DIFVM_TRY(adj_alloc(h));
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned char* tp = (const unsigned char*)tape;
+  if (h->prec == DIFVM_F64)
+    return piso_step_bwd_t<double>(h, tp, (const double*)Ub, wk, (double*)U_bar, (double*)p_bar,
+                                   (double*)phi_bar, (double*)p_b_bar, wk_bar, (double*)U_b_bar,
+                                   nu_bar, info, st);
+  return piso_step_bwd_t<float>(h, tp, (const float*)Ub, wk, (float*)U_bar, (float*)p_bar,
+                                (float*)phi_bar, (float*)p_b_bar, wk_bar, (float*)U_b_bar, nu_bar,
+                                info, st);
 }

@@ -103,6 +103,9 @@ _SIGS = {
     "difvm_krylov_refine_workspace_bytes": [_vp, _i, _i],
     "difvm_piso_create": [_vp, _i, _vp, _vp],
     "difvm_piso_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "difvm_piso_step_record": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp],
+    "difvm_piso_step_bwd": [_vp, _vp, C.c_size_t, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                            _vp],
     "difvm_flux_from_U": [_vp, _i, _vp, _vp, _vp, _vp],
     "difvm_laplacian_apply_bwd_noalloc": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
                                           _vp],
@@ -135,6 +138,9 @@ def lib():
         for nm in ("difvm_krylov_workspace_bytes", "difvm_krylov_refine_workspace_bytes"):
             if hasattr(L, nm):
                 getattr(L, nm).restype = C.c_size_t
+        if hasattr(L, "difvm_piso_tape_bytes"):
+            L.difvm_piso_tape_bytes.argtypes = [_vp]
+            L.difvm_piso_tape_bytes.restype = C.c_size_t
         if hasattr(L, "difvm_piso_destroy"):
             L.difvm_piso_destroy.argtypes = [_vp]
             L.difvm_piso_destroy.restype = None
@@ -506,5 +512,52 @@ class Piso:
         return st, info
 
 
+    def tape_bytes(self):
+        return int(lib().difvm_piso_tape_bytes(self.h))
+
+    def new_tape(self, device):
+        """A device tape for one recorded step (torch allocations are 512-byte aligned)."""
+        return torch.empty(self.tape_bytes(), dtype=torch.uint8, device=device)
+
+    def step_record(self, U, p, phi, U_b, p_b, tape, wk=None, info=None, stream=None):
+        """difvm_piso_step that also writes the step's tape.  Returns (status, info)."""
+        if info is None:
+            info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U.device)
+        st = lib().difvm_piso_step_record(self.h, _ptr(U), _ptr(p), _ptr(phi), _ptr(U_b), _ptr(p_b),
+                                          _ptr(wk), _ptr(info), _ptr(tape), tape.numel(),
+                                          _stream(stream))
+        if st in (EINVAL, ECUDA, ENOMEM):
+            _check(st)
+        return st, info
+
+    def step_bwd(self, tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar=None, wk_bar=None,
+                 U_b_bar=None, nu_bar=None, info=None, stream=None):
+        """Adjoint of a recorded step, in place on the adjoint arrays (see the C header).
+        Returns (status, info)."""
+        if info is None:
+            info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U_bar.device)
+        st = lib().difvm_piso_step_bwd(self.h, _ptr(tape), tape.numel(), _ptr(U_b), _ptr(wk),
+                                       _ptr(U_bar), _ptr(p_bar), _ptr(phi_bar), _ptr(p_b_bar),
+                                       _ptr(wk_bar), _ptr(U_b_bar), _ptr(nu_bar), _ptr(info),
+                                       _stream(stream))
+        if st in (EINVAL, ECUDA, ENOMEM):
+            _check(st)
+        return st, info
+
+
 def difvm_piso_step(piso, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
     return piso.step(U, p, phi, U_b, p_b, wk, info, stream)
+
+
+def difvm_piso_tape_bytes(piso):
+    return piso.tape_bytes()
+
+
+def difvm_piso_step_record(piso, U, p, phi, U_b, p_b, tape, wk=None, info=None, stream=None):
+    return piso.step_record(U, p, phi, U_b, p_b, tape, wk, info, stream)
+
+
+def difvm_piso_step_bwd(piso, tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar=None, wk_bar=None,
+                        U_b_bar=None, nu_bar=None, info=None, stream=None):
+    return piso.step_bwd(tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar, wk_bar, U_b_bar, nu_bar,
+                         info, stream)
