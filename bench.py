@@ -51,6 +51,7 @@ NU, DT = 0.01, 0.002
 # these jittered tetrahedra for every setting tried.  dt = 0.002: with two
 # correctors the PISO splitting error grows at dt = 0.004 on this mesh.
 NONORTH = 1
+CKPT = 5          # checkpoint interval of the checkpointed forward + adjoint run
 
 
 def measured_peaks():
@@ -322,6 +323,48 @@ def run_ours(args):
     h2d = (Ub_pin.numel() + pb_pin.numel()) * 4
     d2h = info_pin.numel()
 
+    # forward + adjoint against forward alone, from one state of the same run:
+    # loss = kinetic energy after K steps, its adjoint back to the state K steps
+    # earlier and to U_b and nu (every step recorded; and with the state kept
+    # every CKPT steps and the segments re-run with tapes)
+    V32 = torch.as_tensor(dm.to_cells(m.V), dtype=dt_, device="cuda")
+
+    def ke_grad(U, p, phi, pb, wk):
+        return (V32 * U).contiguous(), torch.zeros_like(p), torch.zeros_like(phi), None, None
+
+    base = [t.clone() for t in s]
+
+    def fresh():
+        return [t.clone() for t in base]
+
+    def ev_time(fn):
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    s1 = fresh()
+    fwd_ms, _ = ev_time(lambda: [h.step(*s1, info=info) for _ in range(K)])
+    s2 = fresh()
+    fa_ms, adj = ev_time(lambda: D.simulate_adjoint(h, s2, K, ke_grad))
+    s3 = fresh()
+    fc_ms, adjc = ev_time(lambda: D.simulate_adjoint(h, s3, K, ke_grad, checkpoint_every=CKPT))
+    same = bool(torch.equal(adj["U"], adjc["U"]) and torch.equal(adj["nu"], adjc["nu"]))
+    fwd_adj = {"value": fa_ms / fwd_ms, "unit": "time ratio", "steps": K,
+               "fwd_ms_per_step": fwd_ms / K, "fwd_adj_ms_per_step": fa_ms / K,
+               "taping": "every step recorded (tapes resident in HBM)",
+               "tape_bytes_per_step": h.tape_bytes(),
+               "checkpointed": {"every": CKPT, "value": fc_ms / fwd_ms,
+                                "fwd_adj_ms_per_step": fc_ms / K, "bitwise_equal": same},
+               "loss": "kinetic energy after the K steps", "status": int(max(adj["status"], adjc["status"])),
+               "dL_dnu": float(adj["nu"][0]),
+               "adjoint_iters_first_step": {k_: D.decode_piso_info(adj["info"])[k_][:n_]
+                                            for k_, n_ in (("itU", 3), ("itp", 2))}}
+
     if rank != 0:
         return 0
     # CPU baseline: one full oracle PISO step of the same cavity (single thread)
@@ -347,7 +390,7 @@ def run_ours(args):
         "f64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64,
                 "pressure_iters_last_step": r64["info"]["itp"][:2],
                 "momentum_iters_last_step": r64["info"]["itU"]},
-        "fwd_adjoint_over_fwd": None,
+        "fwd_adjoint_over_fwd": fwd_adj,
         "roofline": {"kernel": "k_pcg_spmv<float,1> (LDU SpMV + p.q)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,

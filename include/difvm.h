@@ -368,11 +368,17 @@ difvm_status difvm_piso_step_record(difvm_piso_t, void* U, void* p, void* phi, c
  * the handle's forward workspace is reused, so a forward step and a
  * backward step must not run concurrently on one handle.  Every sum has a
  * fixed order: results are bitwise reproducible.  Returns OK or the worst
- * status of the adjoint solves; EINVAL for a short or misaligned tape. */
+ * status of the adjoint solves; EINVAL for a short or misaligned tape.
+ * Each adjoint solve starts from the handle's solution of the same solve in
+ * the previous call (the reverse-time analogue of the forward step starting
+ * from p^n); the result then depends on the call sequence only within the
+ * solver tolerance.  difvm_piso_adjoint_reset zeroes those starting guesses
+ * (the first call after create starts from zero). */
 difvm_status difvm_piso_step_bwd(difvm_piso_t, const void* tape, size_t tape_bytes,
                                  const void* U_b, const double* wk, void* U_bar, void* p_bar,
                                  void* phi_bar, void* p_b_bar, double* wk_bar, void* U_b_bar,
                                  double* nu_bar, difvm_piso_info* info_dev, void* stream);
+difvm_status difvm_piso_adjoint_reset(difvm_piso_t, void* stream);
 /* Initial face flux phi_f = U_f . S_f (linear interpolation; boundary: U_b.S
  * for fixed velocity, U_O.S for zero gradient, 0 for empty). */
 difvm_status difvm_flux_from_U(difvm_mesh_t, difvm_prec, const void* U, const void* U_b,

@@ -42,6 +42,9 @@ struct difvm_piso {
   void *a_phiHb = nullptr, *a_rfb = nullptr, *a_lk = nullptr, *a_ld = nullptr, *a_phio = nullptr;
   void *a_pbb = nullptr, *a_gUb = nullptr, *a_lkU = nullptr, *a_ldU = nullptr, *a_gp2 = nullptr;
   double *a_nuf = nullptr, *a_part = nullptr;
+  // starting guesses of the adjoint pressure solves, one per corrector (FP64 on
+  // mixed-precision handles): the previous reverse step's solutions
+  void* a_lamw = nullptr;
 };
 
 namespace difvm {
@@ -1192,35 +1195,42 @@ static difvm_status adj_alloc(difvm_piso* h) {
             alloc(&h->a_gUb, 9 * nc * e) && alloc(&h->a_lkU, 3 * ni * e) &&
             alloc(&h->a_ldU, 3 * ni * e) && alloc(&h->a_gp2, 3 * nc * e) &&
             alloc((void**)&h->a_nuf, nf * sizeof(double)) &&
-            alloc((void**)&h->a_part, kRedBlocks * sizeof(double));
+            alloc((void**)&h->a_part, kRedBlocks * sizeof(double)) &&
+            alloc(&h->a_lamw, (size_t)h->o.n_corr * nc * (h->mixed ? 8 : e));
   if (!ok) return set_error(DIFVM_ENOMEM, "device allocation for the PISO adjoint workspace failed");
+  DIFVM_CUDA(cudaMemset(h->a_lamw, 0, (size_t)h->o.n_corr * nc * (h->mixed ? 8 : e)));
+  DIFVM_CUDA(cudaMemset(h->a_lamU, 0, 3 * nc * e));
   h->adj_ready = true;
   return DIFVM_OK;
 }
 
 // lam = A_p^{-1} rhs with the forward step's pressure matrix and solver
-// settings (zero initial guess; the matrix is symmetric, so A^{-T} = A^{-1}).
+// settings (the matrix is symmetric, so A^{-T} = A^{-1}).  The solve starts
+// from corrector s's solution of the previous call, like the forward step
+// starts from p^n; *lam points at the result.
 template <typename T>
-static difvm_status adj_psolve(difvm_piso* h, const T* rhs, T* lam, difvm_solve_info* si,
-                               cudaStream_t st) {
+static difvm_status adj_psolve(difvm_piso* h, const T* rhs, int s, T* scratch, T** lam,
+                               difvm_solve_info* si, cudaStream_t st) {
   difvm_mesh* m = h->m;
   const int nc = m->nc;
   const unsigned Bc = blocks_for(nc, kPB);
   if (h->mixed) {
+    double* x = (double*)h->a_lamw + (size_t)s * nc;
     k_to64<T><<<Bc, kPB, 0, st>>>(nc, rhs, h->b64);
     DIFVM_TRY(check_launch("to64"));
-    DIFVM_CUDA(cudaMemsetAsync(h->p64, 0, (size_t)nc * sizeof(double), st));
-    difvm_status s = difvm_krylov_solve_refine(m, &h->o.solve_p, (const float*)h->Dp,
-                                               (const float*)h->Lp, nullptr, h->b64, h->p64, 1,
-                                               h->wsp, h->wsp_bytes, si, st);
-    if (s == DIFVM_EINVAL || s == DIFVM_ECUDA) return s;
-    k_from64<T><<<Bc, kPB, 0, st>>>(nc, h->p64, lam);
+    difvm_status r = difvm_krylov_solve_refine(m, &h->o.solve_p, (const float*)h->Dp,
+                                               (const float*)h->Lp, nullptr, h->b64, x, 1, h->wsp,
+                                               h->wsp_bytes, si, st);
+    if (r == DIFVM_EINVAL || r == DIFVM_ECUDA) return r;
+    k_from64<T><<<Bc, kPB, 0, st>>>(nc, x, scratch);
     DIFVM_TRY(check_launch("from64"));
-    return s;
+    *lam = scratch;
+    return r;
   }
-  DIFVM_CUDA(cudaMemsetAsync(lam, 0, (size_t)nc * sizeof(T), st));
+  T* x = (T*)h->a_lamw + (size_t)s * nc;
   difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
-  return difvm_krylov_solve(m, pr, &h->o.solve_p, h->Dp, h->Lp, nullptr, rhs, lam, 1, h->wsp,
+  *lam = x;
+  return difvm_krylov_solve(m, pr, &h->o.solve_p, h->Dp, h->Lp, nullptr, rhs, x, 1, h->wsp,
                             h->wsp_bytes, si, st);
 }
 
@@ -1250,7 +1260,7 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   T* no = (T*)h->nonorth;
   T *HAb = (T*)h->a_HAb, *gpb = (T*)h->a_gpb, *gpn = (T*)h->a_gpn, *rAUb = (T*)h->a_rAUb;
   T *Db = (T*)h->a_Db, *bb = (T*)h->a_bb, *Lob = (T*)h->a_Lob, *Upb = (T*)h->a_Upb;
-  T *lam = (T*)h->a_lam, *lamU = (T*)h->a_lamU, *phiHb = (T*)h->a_phiHb, *rfb = (T*)h->a_rfb;
+  T *lam_scratch = (T*)h->a_lam, *lamU = (T*)h->a_lamU, *phiHb = (T*)h->a_phiHb, *rfb = (T*)h->a_rfb;
   T *lk = (T*)h->a_lk, *ld = (T*)h->a_ld, *phio = (T*)h->a_phio, *pbb = (T*)h->a_pbb;
   T *gUb = (T*)h->a_gUb, *lkU = (T*)h->a_lkU, *ldU = (T*)h->a_ldU, *gp2 = (T*)h->a_gp2;
   const bool no_U = (o.nonorth & DIFVM_NONORTH_MOMENTUM) != 0;
@@ -1310,8 +1320,9 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
       k_adj_flux_cells<T><<<Bc, kPB, 0, st>>>(t, af, phio, pbar, pbb);
       DIFVM_TRY(check_launch("adj_flux_cells"));
     }
+    T* lam = nullptr;
     {
-      difvm_status sv = adj_psolve<T>(h, pbar, lam, h->sinfo + 3 + std::min(s, 3), st);
+      difvm_status sv = adj_psolve<T>(h, pbar, s, lam_scratch, &lam, h->sinfo + 3 + std::min(s, 3), st);
       if (sv == DIFVM_EINVAL || sv == DIFVM_ECUDA) return sv;
       worst = std::max(worst, (int)sv);
     }
@@ -1337,8 +1348,8 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
     }
   }
 
-  // momentum predictor: lamU = A^{-T} U_bar_0 (lower and upper swapped)
-  DIFVM_CUDA(cudaMemsetAsync(lamU, 0, v3 * sizeof(T), st));
+  // momentum predictor: lamU = A^{-T} U_bar_0 (lower and upper swapped), started
+  // from the previous call's lamU
   {
     difvm_status sv = difvm_krylov_solve(m, pr, &o.solve_U, D, Up, Lo, Ubar, lamU, 3, h->wsU,
                                          h->wsU_bytes, h->sinfo, st);
@@ -1382,6 +1393,16 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
 }
 
 extern "C" size_t difvm_piso_tape_bytes(difvm_piso_t h) { return h ? tape_layout(h).bytes : 0; }
+
+extern "C" difvm_status difvm_piso_adjoint_reset(difvm_piso_t h, void* stream) {
+  if (!h) return set_error(DIFVM_EINVAL, "null PISO handle");
+  if (!h->adj_ready) return DIFVM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = h->m->nc;
+  DIFVM_CUDA(cudaMemsetAsync(h->a_lamw, 0, (size_t)h->o.n_corr * nc * (h->mixed ? 8 : h->elt), st));
+  DIFVM_CUDA(cudaMemsetAsync(h->a_lamU, 0, 3 * nc * h->elt, st));
+  return DIFVM_OK;
+}
 
 extern "C" difvm_status difvm_piso_step_record(difvm_piso_t h, void* U, void* p, void* phi,
                                                const void* Ub, void* pb, double* wk,

@@ -106,6 +106,7 @@ _SIGS = {
     "difvm_piso_step_record": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp],
     "difvm_piso_step_bwd": [_vp, _vp, C.c_size_t, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp],
+    "difvm_piso_adjoint_reset": [_vp, _vp],
     "difvm_flux_from_U": [_vp, _i, _vp, _vp, _vp, _vp],
     "difvm_laplacian_apply_bwd_noalloc": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
                                           _vp],
@@ -545,6 +546,15 @@ class Piso:
         return st, info
 
 
+    def adjoint_reset(self, stream=None):
+        """Zero the starting guesses of the adjoint solves."""
+        _check(lib().difvm_piso_adjoint_reset(self.h, _stream(stream)))
+
+
+def difvm_piso_adjoint_reset(piso, stream=None):
+    piso.adjoint_reset(stream)
+
+
 def difvm_piso_step(piso, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
     return piso.step(U, p, phi, U_b, p_b, wk, info, stream)
 
@@ -561,3 +571,71 @@ def difvm_piso_step_bwd(piso, tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar=None
                         U_b_bar=None, nu_bar=None, info=None, stream=None):
     return piso.step_bwd(tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar, wk_bar, U_b_bar, nu_bar,
                          info, stream)
+
+
+# ------------------------------------------------- forward + adjoint trajectory
+def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=None, stream=None):
+    """n PISO steps forward, then the adjoint of a loss of the final state back
+    to the initial state and the parameters (Sec. 2.5, Eq. vjp).
+
+    state = [U, p, phi, U_b, p_b] (device tensors of the handle's precision;
+    U, p, phi, p_b end at the final state), wk the Windkessel array or None.
+    loss_grad(U, p, phi, p_b, wk) returns the seeds (U_bar, p_bar, phi_bar,
+    p_b_bar or None, pc_bar or None) of the loss at the final state.
+
+    checkpoint_every = k: the forward pass keeps the state every k steps and
+    the reverse pass re-runs each k-step segment with tapes (memory: k tapes
+    plus n/k states; cost: one extra forward step per step).  None: every step
+    is recorded in the forward pass (n tapes, no recomputation).
+
+    Returns dict(U, p, phi, p_b, pc: adjoints of the initial state; U_b, nu,
+    Rp, C, Rd: parameter adjoints; status: worst step status; info: the
+    adjoint solver record of the first step)."""
+    U, p, phi, Ub, pb = state
+    k = nsteps if not checkpoint_every else max(1, min(int(checkpoint_every), nsteps))
+    tapes = [piso.new_tape(U.device) for _ in range(k)]
+    worst = OK
+    n_out = piso.opts.n_out
+    snaps = []
+
+    def snap():
+        return [t.clone() for t in (U, p, phi, pb)] + [wk.clone() if wk is not None else None]
+
+    if k == nsteps:
+        for j in range(nsteps):
+            worst = max(worst, piso.step_record(U, p, phi, Ub, pb, tapes[j], wk=wk, stream=stream)[0])
+    else:
+        for j in range(nsteps):
+            if j % k == 0:
+                snaps.append(snap())
+            worst = max(worst, piso.step(U, p, phi, Ub, pb, wk=wk, stream=stream)[0])
+    Ubar, pbar, phibar, pbbar, pcbar = loss_grad(U, p, phi, pb, wk)
+    Ubar, pbar, phibar = Ubar.clone(), pbar.clone(), phibar.clone()
+    pbbar = torch.zeros_like(pb) if pbbar is None else pbbar.clone()
+    wkbar = None
+    if n_out:
+        wkbar = torch.zeros(4 * n_out, dtype=torch.float64, device=U.device)
+        if pcbar is not None:
+            wkbar[3::4] = pcbar
+    Ubbar = torch.zeros_like(Ub)
+    nubar = torch.zeros(1, dtype=torch.float64, device=U.device)
+    info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U.device)
+    piso.adjoint_reset(stream)
+    nseg = (nsteps + k - 1) // k
+    for seg in reversed(range(nseg)):
+        n0, n1 = seg * k, min(nsteps, seg * k + k)
+        if k != nsteps:      # re-run the segment from its checkpoint, recording tapes
+            sU, sp, sphi, spb, swk = snaps[seg]
+            for j in range(n1 - n0):
+                worst = max(worst, piso.step_record(sU, sp, sphi, Ub, spb, tapes[j], wk=swk,
+                                                    stream=stream)[0])
+        for j in reversed(range(n1 - n0)):
+            st, _ = piso.step_bwd(tapes[j], Ub, wk, Ubar, pbar, phibar, pbbar, wkbar, Ubbar, nubar,
+                                  info=info, stream=stream)
+            worst = max(worst, st)
+    out = dict(U=Ubar, p=pbar, phi=phibar, p_b=pbbar, U_b=Ubbar, nu=nubar, status=worst,
+               info=info)   # info: device record of the first step's adjoint (decode_piso_info)
+    if n_out:
+        w = wkbar.view(n_out, 4)
+        out.update(Rp=w[:, 0], C=w[:, 1], Rd=w[:, 2], pc=w[:, 3])
+    return out

@@ -155,9 +155,12 @@ def test_piso_step_bwd_is_deterministic():
     w = _weights(m, x, 5)
     pg = _gpu_piso(dm, D.F64, kw, 3, 0.5)
     a, _, _ = _gpu_adjoint(dm, pg, x, kw, w)
+    warm, _, _ = _gpu_adjoint(dm, pg, x, kw, w)     # adjoint solves start from a's solutions
+    pg.adjoint_reset()
     b, _, _ = _gpu_adjoint(dm, pg, x, kw, w)
     for key in a:
         assert np.array_equal(np.asarray(a[key]), np.asarray(b[key])), key
+        assert nrel(warm[key], a[key]) < 1e-10, key
 
 
 def test_piso_step_bwd_f32_refine_close_to_oracle():
@@ -231,3 +234,26 @@ def test_multi_step_lid_gradient_matches_oracle_differences():
     fd_nu = (oracle_loss(1.0, nu + h * nu) - oracle_loss(1.0, nu - h * nu)) / (2 * h * nu)
     assert abs(dL_dlid - fd_lid) < 1e-6 * abs(fd_lid), (dL_dlid, fd_lid)
     assert abs(float(nubar[0]) - fd_nu) < 1e-6 * abs(fd_nu), (float(nubar[0]), fd_nu)
+
+
+def test_checkpointed_trajectory_adjoint_equals_fully_taped():
+    """simulate_adjoint with the state kept every 2 steps (segments re-run with
+    tapes) gives bitwise the same adjoint as recording all 5 steps."""
+    m, om, dm, x, kw = _case("wk_exact", 5, 12)
+    pg = _gpu_piso(dm, D.F64, kw, 3, 0.5)
+    V = cuda(dm.to_cells(m.V))
+
+    def loss_grad(U, p, phi, pb, wk):
+        return (V * U).contiguous(), torch.zeros_like(p), torch.zeros_like(phi), None, \
+            torch.ones(1, dtype=torch.float64, device="cuda")
+
+    res = []
+    for ck in (None, 2):
+        g = [cuda(dm.to_cells(x["U"])), cuda(dm.to_cells(x["p"])), cuda(dm.to_faces(x["phi"])),
+             cuda(dm.to_bnd(x["Ub"])), cuda(dm.to_bnd(x["pb"]))]
+        wk = cuda(np.array([0.3, 0.8, 1.2, 0.4]))
+        r = D.simulate_adjoint(pg, g, 5, loss_grad, wk=wk, checkpoint_every=ck)
+        assert r["status"] == D.OK
+        res.append(r)
+    for key in ("U", "p", "phi", "p_b", "U_b", "nu", "Rp", "C", "Rd", "pc"):
+        assert torch.equal(res[0][key], res[1][key]), key
