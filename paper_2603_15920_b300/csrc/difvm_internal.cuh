@@ -139,6 +139,15 @@ struct difvm_mesh {
   double *V64 = nullptr, *rV64 = nullptr, *C64 = nullptr, *Cf64 = nullptr;
   float *V32 = nullptr, *rV32 = nullptr;
   int num_sms = 148;
+  // Segmented (batched) solves: set when the mesh was created with a case
+  // table.  Solver block b works on rows [cs[k] + j*seg_rows, ...) of case
+  // k = seg_case[b], j = b - seg_cb0[k]; a case's blocks are contiguous.
+  bool seg = false;
+  int seg_nblk = 0;
+  int* seg_case = nullptr;   // [seg_nblk]
+  int* seg_cb0 = nullptr;    // [ncases + 1]
+  int* seg_cs = nullptr;     // [ncases + 1] first cell of each case
+  std::vector<int32_t> bown_host;  // boundary-face owners, internal numbering
 
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
@@ -154,6 +163,9 @@ template <> inline Geo<double> geo<double>(const difvm_mesh* m) { return m->geo6
 template <> inline Geo<float> geo<float>(const difvm_mesh* m) { return m->geo32(); }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// rows per block of the segmented (batched) Krylov kernels: 512 threads x 4 rows
+constexpr int kSegRows = 2048;
 difvm_status check_mesh(const difvm_mesh* m);
 difvm_status check_prec(difvm_prec p);
 

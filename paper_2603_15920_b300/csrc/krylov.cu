@@ -740,7 +740,7 @@ __global__ void k_write_info(int ncomp, const KState* st, difvm_solve_info* info
 
 // ------------------------------------------------------------- workspace
 struct WsLayout {
-  size_t vec_bytes, n_vec, val_off, state_off, part_off, ticket_off, total;
+  size_t vec_bytes, n_vec, val_off, state_off, part_off, ticket_off, flag_off, total;
 };
 
 static int grid_for(const difvm_mesh* m) {
@@ -758,8 +758,16 @@ static WsLayout layout(const difvm_mesh* m, size_t elt, int method, int ncomp) {
   L.n_vec = (method == DIFVM_PCG ? 3 : 8) * (size_t)ncomp + 1;
   L.val_off = L.n_vec * L.vec_bytes;
   L.state_off = L.val_off + up256((size_t)std::max<int64_t>(m->ell_nslots, 1) * elt);
+  if (m->seg) {  // per-case states, partials and tickets of the segmented solvers
+    L.part_off = L.state_off + up256((size_t)m->ncases * ncomp * sizeof(KState));
+    L.ticket_off = L.part_off + up256((size_t)m->seg_nblk * kMaxParts * sizeof(double));
+    L.flag_off = L.ticket_off + up256((size_t)m->ncases * sizeof(unsigned));
+    L.total = L.flag_off + 256;
+    return L;
+  }
   L.part_off = L.state_off + 256 * 4;
   L.ticket_off = L.part_off + up256((size_t)grid_for(m) * kMaxParts * sizeof(double));
+  L.flag_off = L.ticket_off;
   L.total = L.ticket_off + 256;
   return L;
 }
@@ -1200,6 +1208,602 @@ __global__ void k_solve_coeff_bwd(Topo t, const T* x, const T* bbar, T* Dbar, T*
   }
 }
 
+// ====================================================== segmented (batched)
+// The same PCG / BiCGStab on a disjoint union of cases: every case keeps its
+// own scalars (alpha, beta, rho, omega, ...), convergence flag and iteration
+// count, as if it were solved alone.  Each solver block works inside one case
+// (a chunk of kSegRows of its rows); each case has its own ticket, and the
+// last of the case's blocks to arrive reduces that case's partials in block
+// order.  A case's block partition depends only on its own size, so a case
+// gives bitwise the same result alone as inside any batch.
+struct SWork {
+  KState* st;          // [ncases * NC]
+  double* part;        // [nblk * kMaxParts]
+  unsigned* ticket;    // [ncases]
+  const int* bcase;    // [nblk]
+  const int* cb0;      // [ncases + 1]
+  const int* cs;       // [ncases + 1]
+  int maxit;
+  double tol_rel, tol_abs;
+};
+
+struct SegBlock {
+  int k, r0, r1;
+};
+__device__ __forceinline__ SegBlock seg_block(const SWork& w) {
+  SegBlock b;
+  b.k = __ldg(w.bcase + blockIdx.x);
+  b.r0 = __ldg(w.cs + b.k) + (blockIdx.x - __ldg(w.cb0 + b.k)) * kSegRows;
+  b.r1 = min(__ldg(w.cs + b.k + 1), b.r0 + kSegRows);
+  return b;
+}
+
+template <int NC>
+__device__ __forceinline__ unsigned seg_active(const SWork& w, int k) {
+  unsigned m = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (!w.st[k * NC + c].done) m |= 1u << c;
+  return m;
+}
+
+// Store this block's partials; true in the last block of case k, with the
+// case totals in `tot` (all threads of that block).
+template <int K>
+__device__ __forceinline__ bool seg_sum(const SWork& w, int k, double (&v)[K], double (&tot)[K]) {
+  block_sum<K>(v);
+  __shared__ int amlast;
+  __shared__ double res[K];
+  const int b0 = __ldg(w.cb0 + k), nb = __ldg(w.cb0 + k + 1) - b0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) w.part[blockIdx.x * kMaxParts + q] = v[q];
+    __threadfence();
+    amlast = atomicAdd(w.ticket + k, 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+  double a[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) a[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] += __ldcg(w.part + (b0 + b) * kMaxParts + q);
+  block_sum<K>(a);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) res[q] = a[q];
+    w.ticket[k] = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) tot[q] = res[q];
+  return true;
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_pcg_init(Topo t, Mat<T> A, int jacobi, const T* b, T* x,
+                                                     T* r, T* p, T* rD, SWork w) {
+  const SegBlock B = seg_block(w);
+  const int nc = t.nc;
+  DotAcc<T> bb[NC], rr[NC], rz[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    const T di = __ldg(A.D + i);
+    const T rd = jacobi ? T(1) / di : T(1);
+    rD[i] = rd;
+    T ax[NC];
+    spmv_row<T, NC, 0>(t, A, i, x, ax, (1u << NC) - 1);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T bi = b[c * nc + i];
+      const T ri = bi - ax[c];
+      const T zi = ri * rd;
+      r[c * nc + i] = ri;
+      p[c * nc + i] = zi;
+      bb[c].add(bi, bi);
+      rr[c].add(ri, ri);
+      rz[c].add(ri, zi);
+    }
+  }
+  double v[3 * NC], tot[3 * NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    v[3 * c] = bb[c].get();
+    v[3 * c + 1] = rr[c].get();
+    v[3 * c + 2] = rz[c].get();
+  }
+  if (!seg_sum<3 * NC>(w, B.k, v, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    KState& s = w.st[B.k * NC + c];
+    s.bb = tot[3 * c];
+    s.rr = tot[3 * c + 1];
+    s.rz = tot[3 * c + 2];
+    s.res0 = sqrt(s.rr);
+    s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+    s.iters = 0;
+    s.status = DIFVM_OK;
+    s.zero_rhs = s.bb == 0.0;
+    s.done = s.zero_rhs || s.rr <= s.tol2;
+    if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
+  }
+}
+
+template <typename T, int NC, int MAXW>
+__global__ void __launch_bounds__(kKB) k_sg_pcg_spmv(Topo t, Mat<T> A, const T* p, T* q, SWork w) {
+  const SegBlock B = seg_block(w);
+  const unsigned act = seg_active<NC>(w, B.k);
+  if (!act) return;
+  const int nc = t.nc;
+  DotAcc<T> pq[NC];
+#pragma unroll 4
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    T y[NC];
+    spmv_row<T, NC, MAXW>(t, A, i, p, y, act);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        q[c * nc + i] = y[c];
+        pq[c].add(p[c * nc + i], y[c]);
+      }
+  }
+  double v[NC], tot[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v[c] = pq[c].get();
+  if (!seg_sum<NC>(w, B.k, v, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (act >> c & 1) w.st[B.k * NC + c].alpha = w.st[B.k * NC + c].rz / tot[c];
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_pcg_update(int nc, const T* p, const T* q, const T* rD,
+                                                       T* x, T* r, SWork w) {
+  const SegBlock B = seg_block(w);
+  const unsigned act = seg_active<NC>(w, B.k);
+  if (!act) return;
+  T al[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) al[c] = (T)w.st[B.k * NC + c].alpha;
+  DotAcc<T> rr[NC], rz[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    const T rd = rD[i];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        const int k = c * nc + i;
+        x[k] += al[c] * p[k];
+        const T ri = r[k] - al[c] * q[k];
+        r[k] = ri;
+        rr[c].add(ri, ri);
+        rz[c].add(ri, ri * rd);
+      }
+  }
+  double v[2 * NC], tot[2 * NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    v[2 * c] = rr[c].get();
+    v[2 * c + 1] = rz[c].get();
+  }
+  if (!seg_sum<2 * NC>(w, B.k, v, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (!(act >> c & 1)) continue;
+    KState& s = w.st[B.k * NC + c];
+    s.iters += 1;
+    s.rr = tot[2 * c];
+    if (!finite_d(s.rr) || !finite_d(s.alpha)) { s.done = 1; s.status = DIFVM_ENONFINITE; continue; }
+    if (s.rr <= s.tol2) { s.done = 1; continue; }
+    if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; continue; }
+    s.beta = tot[2 * c + 1] / s.rz;
+    s.rz = tot[2 * c + 1];
+  }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_pcg_pupdate(int nc, const T* r, const T* rD, T* p, SWork w) {
+  const SegBlock B = seg_block(w);
+  const unsigned act = seg_active<NC>(w, B.k);
+  if (!act) return;
+  T be[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) be[c] = (T)w.st[B.k * NC + c].beta;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    const T rd = rD[i];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        const int k = c * nc + i;
+        p[k] = r[k] * rd + be[c] * p[k];
+      }
+  }
+}
+
+template <typename T, int NC>
+__global__ void k_sg_zero_rhs(int nc, T* x, SWork w) {
+  const SegBlock B = seg_block(w);
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (w.st[B.k * NC + c].zero_rhs) x[c * nc + i] = T(0);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_init(Topo t, Mat<T> A, int jacobi, const T* b, T* x,
+                                                      T* r, T* rh, T* p, T* v, T* rD, SWork w) {
+  const SegBlock B = seg_block(w);
+  const int nc = t.nc;
+  DotAcc<T> bb[NC], rr[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    const T di = __ldg(A.D + i);
+    rD[i] = jacobi ? T(1) / di : T(1);
+    T ax[NC];
+    spmv_row<T, NC, 0>(t, A, i, x, ax, (1u << NC) - 1);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int k = c * nc + i;
+      const T bi = b[k];
+      const T ri = bi - ax[c];
+      r[k] = ri;
+      rh[k] = ri;
+      p[k] = T(0);
+      v[k] = T(0);
+      bb[c].add(bi, bi);
+      rr[c].add(ri, ri);
+    }
+  }
+  double vv[2 * NC], tot[2 * NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    vv[2 * c] = bb[c].get();
+    vv[2 * c + 1] = rr[c].get();
+  }
+  if (!seg_sum<2 * NC>(w, B.k, vv, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    KState& s = w.st[B.k * NC + c];
+    s.bb = tot[2 * c];
+    s.rr = tot[2 * c + 1];
+    s.rz = s.rr;
+    s.res0 = sqrt(s.rr);
+    s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+    s.iters = 0;
+    s.status = DIFVM_OK;
+    s.rho = 1.0; s.alpha = 1.0; s.omega = 1.0;
+    s.sconv = 0;
+    s.zero_rhs = s.bb == 0.0;
+    s.done = s.zero_rhs || s.rr <= s.tol2;
+    if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
+  }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_p(int nc, const T* r, const T* v, T* p, SWork w) {
+  const SegBlock B = seg_block(w);
+  const unsigned act = seg_active<NC>(w, B.k);
+  if (!act) return;
+  T be[NC], om[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const KState& s = w.st[B.k * NC + c];
+    be[c] = (T)((s.rz / s.rho) * (s.alpha / s.omega));
+    om[c] = (T)s.omega;
+  }
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        const int k = c * nc + i;
+        p[k] = r[k] + be[c] * (p[k] - om[c] * v[k]);
+      }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_scale(int nc, const T* a, const T* rD, T* y, SWork w,
+                                                       int second) {
+  const SegBlock B = seg_block(w);
+  unsigned act = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const KState& s = w.st[B.k * NC + c];
+    if (!s.done && !(second && s.sconv)) act |= 1u << c;
+  }
+  if (!act) return;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    const T rd = rD[i];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) y[c * nc + i] = a[c * nc + i] * rd;
+  }
+}
+
+template <typename T, int NC, int MAXW>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_spmv1(Topo t, Mat<T> A, const T* rh, const T* y, T* v,
+                                                       SWork w) {
+  const SegBlock B = seg_block(w);
+  const unsigned act = seg_active<NC>(w, B.k);
+  if (!act) return;
+  const int nc = t.nc;
+  DotAcc<T> rv[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    T a[NC];
+    spmv_row<T, NC, MAXW>(t, A, i, y, a, act);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        v[c * nc + i] = a[c];
+        rv[c].add(rh[c * nc + i], a[c]);
+      }
+  }
+  double vv[NC], tot[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) vv[c] = rv[c].get();
+  if (!seg_sum<NC>(w, B.k, vv, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (!(act >> c & 1)) continue;
+    KState& s = w.st[B.k * NC + c];
+    s.rho = s.rz;
+    if (s.rho == 0.0 || tot[c] == 0.0 || s.omega == 0.0) { s.done = 1; s.status = DIFVM_EBREAKDOWN; continue; }
+    s.alpha = s.rho / tot[c];
+  }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_s(int nc, const T* r, const T* v, T* s_, SWork w) {
+  const SegBlock B = seg_block(w);
+  const unsigned act = seg_active<NC>(w, B.k);
+  if (!act) return;
+  T al[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) al[c] = (T)w.st[B.k * NC + c].alpha;
+  DotAcc<T> ss[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        const int k = c * nc + i;
+        const T si = r[k] - al[c] * v[k];
+        s_[k] = si;
+        ss[c].add(si, si);
+      }
+  double vv[NC], tot[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) vv[c] = ss[c].get();
+  if (!seg_sum<NC>(w, B.k, vv, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (!(act >> c & 1)) continue;
+    KState& s = w.st[B.k * NC + c];
+    s.iters += 1;
+    s.pq = tot[c];
+    s.sconv = tot[c] <= s.tol2;
+    if (s.sconv) s.rr = tot[c];
+  }
+}
+
+template <typename T, int NC>
+__global__ void k_sg_bicg_sfinish(int nc, const T* y, T* x, SWork w) {
+  const SegBlock B = seg_block(w);
+  unsigned fin = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (!w.st[B.k * NC + c].done && w.st[B.k * NC + c].sconv) fin |= 1u << c;
+  if (!fin) return;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (fin >> c & 1) x[c * nc + i] += (T)w.st[B.k * NC + c].alpha * y[c * nc + i];
+}
+
+template <typename T, int NC, int MAXW>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_spmv2(Topo t, Mat<T> A, const T* z, const T* s_, T* tv,
+                                                       SWork w) {
+  const SegBlock B = seg_block(w);
+  unsigned act = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (!w.st[B.k * NC + c].done && !w.st[B.k * NC + c].sconv) act |= 1u << c;
+  if (!act) return;
+  const int nc = t.nc;
+  DotAcc<T> ts[NC], tt[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    T a[NC];
+    spmv_row<T, NC, MAXW>(t, A, i, z, a, act);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        tv[c * nc + i] = a[c];
+        ts[c].add(a[c], s_[c * nc + i]);
+        tt[c].add(a[c], a[c]);
+      }
+  }
+  double vv[2 * NC], tot[2 * NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    vv[2 * c] = ts[c].get();
+    vv[2 * c + 1] = tt[c].get();
+  }
+  if (!seg_sum<2 * NC>(w, B.k, vv, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (act >> c & 1)
+      w.st[B.k * NC + c].omega = tot[2 * c + 1] > 0.0 ? tot[2 * c] / tot[2 * c + 1] : 0.0;
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kKB) k_sg_bicg_update(int nc, const T* y, const T* z, const T* s_,
+                                                        const T* tv, const T* rh, T* x, T* r, SWork w) {
+  const SegBlock B = seg_block(w);
+  unsigned act = 0, fin = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const KState& s = w.st[B.k * NC + c];
+    if (!s.done && !s.sconv) act |= 1u << c;
+    if (!s.done && s.sconv) fin |= 1u << c;
+  }
+  // components that converged on s are closed by the case's first block
+  if (!act) {
+    if (fin && blockIdx.x == __ldg(w.cb0 + B.k) && threadIdx.x == 0)
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (fin >> c & 1) w.st[B.k * NC + c].done = 1;
+    return;
+  }
+  T al[NC], om[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    al[c] = (T)w.st[B.k * NC + c].alpha;
+    om[c] = (T)w.st[B.k * NC + c].omega;
+  }
+  DotAcc<T> rr[NC], rhr[NC];
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (act >> c & 1) {
+        const int k = c * nc + i;
+        x[k] += al[c] * y[k] + om[c] * z[k];
+        const T ri = s_[k] - om[c] * tv[k];
+        r[k] = ri;
+        rr[c].add(ri, ri);
+        rhr[c].add(rh[k], ri);
+      }
+  double vv[2 * NC], tot[2 * NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    vv[2 * c] = rr[c].get();
+    vv[2 * c + 1] = rhr[c].get();
+  }
+  if (!seg_sum<2 * NC>(w, B.k, vv, tot) || threadIdx.x != 0) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    KState& s = w.st[B.k * NC + c];
+    if (!s.done && s.sconv) { s.done = 1; continue; }
+    if (!(act >> c & 1)) continue;
+    s.rr = tot[2 * c];
+    s.rz = tot[2 * c + 1];
+    if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; continue; }
+    if (s.rr <= s.tol2) { s.done = 1; continue; }
+    if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; continue; }
+  }
+}
+
+__global__ void k_sg_write_info(int n, const KState* st, difvm_solve_info* info) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const KState& s = st[c];
+  difvm_solve_info o;
+  o.iters = s.iters;
+  o.refinements = 0;
+  o.status = s.status;
+  o.pad = 0;
+  o.res0 = s.res0;
+  o.res = sqrt(s.rr);
+  o.bnorm = sqrt(s.bb);
+  info[c] = o;
+}
+
+// 1 while any (case, component) is still iterating (host poll)
+__global__ void k_sg_any_active(int n, const KState* st, int* out) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (!st[c].done) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *out = any;
+}
+
+template <typename T, int NC, int MW>
+static difvm_status solve_sg(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A, const T* b, T* x,
+                             char* ws, const WsLayout& L, difvm_solve_info* info, cudaStream_t st) {
+  const int nc = m->nc, G = m->seg_nblk, nst = m->ncases * NC;
+  Topo t = m->topo();
+  auto vec = [&](int k) { return (T*)(ws + (size_t)k * L.vec_bytes); };
+  SWork w;
+  w.st = (KState*)(ws + L.state_off);
+  w.part = (double*)(ws + L.part_off);
+  w.ticket = (unsigned*)(ws + L.ticket_off);
+  w.bcase = m->seg_case;
+  w.cb0 = m->seg_cb0;
+  w.cs = m->seg_cs;
+  w.maxit = o->max_iter > 0 ? o->max_iter : 1000;
+  w.tol_rel = o->tol_rel;
+  w.tol_abs = o->tol_abs;
+  int* flag = (int*)(ws + L.flag_off);
+  const int jac = o->precond != DIFVM_PRECOND_NONE;
+  const int chunk = o->check_every > 0 ? o->check_every : 8;
+  DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned) * m->ncases, st));
+  T* rD = vec(L.n_vec - 1);
+  int host_flag = 1;
+  auto poll = [&]() -> difvm_status {
+    k_sg_any_active<<<1, 256, 0, st>>>(nst, w.st, flag);
+    DIFVM_TRY(check_launch("sg_any_active"));
+    DIFVM_CUDA(cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DIFVM_CUDA(cudaStreamSynchronize(st));
+    return DIFVM_OK;
+  };
+  if (o->method == DIFVM_PCG) {
+    T *r = vec(0), *p = vec(NC), *q = vec(2 * NC);
+    k_sg_pcg_init<T, NC><<<G, kKB, 0, st>>>(t, A, jac, b, x, r, p, rD, w);
+    DIFVM_TRY(check_launch("sg_pcg_init"));
+    k_sg_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
+    DIFVM_TRY(check_launch("sg_zero_rhs"));
+    for (int it = 0; it < w.maxit;) {
+      const int n = std::min(chunk, w.maxit - it);
+      for (int k = 0; k < n; ++k) {
+        k_sg_pcg_spmv<T, NC, MW><<<G, kKB, 0, st>>>(t, A, p, q, w);
+        k_sg_pcg_update<T, NC><<<G, kKB, 0, st>>>(nc, p, q, rD, x, r, w);
+        k_sg_pcg_pupdate<T, NC><<<G, kKB, 0, st>>>(nc, r, rD, p, w);
+        count_launch(); count_launch();
+        DIFVM_TRY(check_launch("sg_pcg_iter"));
+      }
+      it += n;
+      DIFVM_TRY(poll());
+      if (!host_flag) break;
+    }
+  } else if (o->method == DIFVM_BICGSTAB) {
+    T *r = vec(0), *rh = vec(NC), *p = vec(2 * NC), *v = vec(3 * NC), *s_ = vec(4 * NC),
+      *tv = vec(5 * NC), *y = vec(6 * NC), *z = vec(7 * NC);
+    k_sg_bicg_init<T, NC><<<G, kKB, 0, st>>>(t, A, jac, b, x, r, rh, p, v, rD, w);
+    DIFVM_TRY(check_launch("sg_bicg_init"));
+    k_sg_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
+    DIFVM_TRY(check_launch("sg_zero_rhs"));
+    for (int it = 0; it < w.maxit;) {
+      const int n = std::min(chunk, w.maxit - it);
+      for (int k = 0; k < n; ++k) {
+        k_sg_bicg_p<T, NC><<<G, kKB, 0, st>>>(nc, r, v, p, w);
+        k_sg_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, p, rD, y, w, 0);
+        k_sg_bicg_spmv1<T, NC, MW><<<G, kKB, 0, st>>>(t, A, rh, y, v, w);
+        k_sg_bicg_s<T, NC><<<G, kKB, 0, st>>>(nc, r, v, s_, w);
+        k_sg_bicg_sfinish<T, NC><<<G, kKB, 0, st>>>(nc, y, x, w);
+        k_sg_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, s_, rD, z, w, 1);
+        k_sg_bicg_spmv2<T, NC, MW><<<G, kKB, 0, st>>>(t, A, z, s_, tv, w);
+        k_sg_bicg_update<T, NC><<<G, kKB, 0, st>>>(nc, y, z, s_, tv, rh, x, r, w);
+        for (int q = 0; q < 7; ++q) count_launch();
+        DIFVM_TRY(check_launch("sg_bicg_iter"));
+      }
+      it += n;
+      DIFVM_TRY(poll());
+      if (!host_flag) break;
+    }
+  } else {
+    return set_error(DIFVM_EINVAL, "unknown Krylov method %d", o->method);
+  }
+  if (info) {
+    k_sg_write_info<<<blocks_for(nst, 128), 128, 0, st>>>(nst, w.st, info);
+    DIFVM_TRY(check_launch("sg_write_info"));
+  }
+  // worst status over all cases and components
+  std::vector<KState> hs(nst);
+  DIFVM_CUDA(cudaMemcpyAsync(hs.data(), w.st, sizeof(KState) * nst, cudaMemcpyDeviceToHost, st));
+  DIFVM_CUDA(cudaStreamSynchronize(st));
+  int worst = DIFVM_OK;
+  for (const KState& s : hs) worst = std::max(worst, s.status);
+  return (difvm_status)worst;
+}
+
 template <typename T>
 static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const void* D, const void* L,
                             const void* U, const void* b, void* x, int ncomp, void* ws,
@@ -1212,6 +1816,22 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
   Mat<T> A{(const T*)D, m->ell(), val};
   KState hs[3];
   const int mw = maxw_bucket(m);
+  if (m->seg) {
+#define DIFVM_SOLVE(NC, MW) solve_sg<T, NC, MW>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st)
+    switch (ncomp * 16 + mw) {
+      case 16 + 4: return DIFVM_SOLVE(1, 4);
+      case 16 + 8: return DIFVM_SOLVE(1, 8);
+      case 16 + 0: return DIFVM_SOLVE(1, 0);
+      case 32 + 4: return DIFVM_SOLVE(2, 4);
+      case 32 + 8: return DIFVM_SOLVE(2, 8);
+      case 32 + 0: return DIFVM_SOLVE(2, 0);
+      case 48 + 4: return DIFVM_SOLVE(3, 4);
+      case 48 + 8: return DIFVM_SOLVE(3, 8);
+      case 48 + 0: return DIFVM_SOLVE(3, 0);
+    }
+#undef DIFVM_SOLVE
+    return set_error(DIFVM_EINVAL, "ncomp must be 1..3");
+  }
 #define DIFVM_SOLVE(NC, MW) solve_nc<T, NC, MW>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs)
   switch (ncomp * 16 + mw) {
     case 16 + 4: return DIFVM_SOLVE(1, 4);
@@ -1264,6 +1884,7 @@ extern "C" difvm_status difvm_krylov_solve_refine(difvm_mesh_t m, const difvm_so
                                                   const double* b64, double* x64, int ncomp, void* ws,
                                                   size_t wsbytes, difvm_solve_info* info, void* stream) {
   DIFVM_TRY(check_solve(m, DIFVM_F32, o, ncomp, D, L));
+  if (m->seg) return set_error(DIFVM_EINVAL, "difvm_krylov_solve_refine: not available on batched meshes");
   if (ncomp != 1 || o->method != DIFVM_PCG)
     return set_error(DIFVM_EINVAL, "the mixed-precision solve is single-RHS PCG");
   if (U) return set_error(DIFVM_EINVAL, "the mixed-precision PCG needs a symmetric matrix (upper = NULL)");

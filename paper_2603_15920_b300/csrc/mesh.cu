@@ -192,7 +192,8 @@ static void free_mesh(difvm_mesh* m) {
   if (!m) return;
   void* ptrs[] = {m->on,   m->bown, m->cptr, m->cent, m->bkind, m->bpatch, m->Sw64,
                   m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
-                  m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map};
+                  m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map,
+                  m->seg_case, m->seg_cb0, m->seg_cs};
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
@@ -419,6 +420,23 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload(&m->ell_soff, soff.data(), soff.size()));
   DIFVM_TRY(upload(&m->ell_col, ecol.data(), ecol.size()));
   DIFVM_TRY(upload(&m->ell_map, emap.data(), emap.size()));
+  m->bown_host.assign(bown.begin(), bown.begin() + nb);
+  if (d->case_cell_start) {
+    // block tables of the segmented solvers (the case ranges survive the
+    // renumbering: RCM keeps every case's cells contiguous and in case order)
+    m->seg = true;
+    std::vector<int> cb0(ncases + 1, 0), bcase;
+    for (int k = 0; k < ncases; ++k) {
+      const int nk = m->case_start[k + 1] - m->case_start[k];
+      const int nbk = (nk + kSegRows - 1) / kSegRows;
+      cb0[k + 1] = cb0[k] + nbk;
+      for (int j = 0; j < nbk; ++j) bcase.push_back(k);
+    }
+    m->seg_nblk = cb0[ncases];
+    DIFVM_TRY(upload(&m->seg_case, bcase.data(), bcase.size()));
+    DIFVM_TRY(upload(&m->seg_cb0, cb0.data(), cb0.size()));
+    DIFVM_TRY(upload(&m->seg_cs, m->case_start.data(), m->case_start.size()));
+  }
   double* Sf_d = nullptr;
   DIFVM_TRY(upload(&Sf_d, Sf.data(), Sf.size()));
   DIFVM_TRY(upload(&m->Cf64, Cf.data(), Cf.size()));

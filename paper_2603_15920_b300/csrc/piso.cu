@@ -24,6 +24,9 @@ struct difvm_piso {
   difvm_piso_opts o{};
   bool mixed = false;
   int has_fixed_p = 0;
+  int nk = 1;                      // cases (solve-info slots per solve)
+  int pin = -1;                    // pinned cell of a single-case mesh
+  unsigned char* pinflag = nullptr;  // batched mesh: 1 on each case's pinned cell
   size_t elt = 8;
   void *gradp = nullptr, *gradU = nullptr, *D = nullptr, *Lo = nullptr, *Up = nullptr, *b = nullptr;
   void *rhs = nullptr, *rAU = nullptr, *HbyA = nullptr, *Dp = nullptr, *Lp = nullptr, *bp = nullptr;
@@ -33,7 +36,9 @@ struct difvm_piso {
   void* wsp = nullptr;
   size_t wsp_bytes = 0;
   double *p64 = nullptr, *b64 = nullptr;
-  difvm_solve_info* sinfo = nullptr;  // [3 + 4] device
+  // solve infos: momentum [3 nk] (case-major), then 4 pressure slots of [nk];
+  // followed by Q[16], p_out[16] (double) and the outlet table (int start[16], size[16])
+  difvm_solve_info* sinfo = nullptr;
   std::vector<void*> allocs;
   // adjoint workspace, allocated by the first difvm_piso_step_bwd
   bool adj_ready = false;
@@ -319,7 +324,8 @@ __global__ void k_p_faces(Topo t, Geo<T> g, T psi, const T* HbyA, const T* rAU, 
 // per cell: Dp = sum a_f, bp = sum sigma(-phiHbyA + nonorth) + sum_fixed a_f p_b; pinned cell
 template <typename T>
 __global__ void __launch_bounds__(kPB) k_p_cells(Topo t, const T* phiHbyA, const T* af,
-                                                 const T* nonorth, const T* pb, int pin, T* Dp,
+                                                 const T* nonorth, const T* pb, int pin,
+                                                 const unsigned char* pinflag, T* Dp,
                                                  T* bp) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
@@ -342,7 +348,8 @@ __global__ void __launch_bounds__(kPB) k_p_cells(Topo t, const T* phiHbyA, const
       }
     }
   }
-  if (i == pin) d += d;  // p_ref = 0 at the pinned cell (all-Neumann pressure)
+  // p_ref = 0 at the pinned cell (all-Neumann pressure)
+  if (pinflag ? pinflag[i] != 0 : i == pin) d += d;
   Dp[i] = d;
   bp[i] = r;
 }
@@ -408,14 +415,30 @@ template <typename T> __global__ void k_from64(int n, const double* a, T* b) {
   if (i < n) b[i] = (T)a[i];
 }
 
-__global__ void k_piso_info(const difvm_solve_info* si, int ncorr, int status, int n_out,
+// Step record: per solve the largest iteration count over the cases, the
+// worst status over all solves and cases, and the outlet values.
+__global__ void k_piso_info(const difvm_solve_info* si, int nk, int ncorr, int status, int n_out,
                             const double* Q, const double* po, difvm_piso_info* out) {
   if (threadIdx.x != 0) return;
   difvm_piso_info r;
-  for (int c = 0; c < 3; ++c) r.itU[c] = si[c].iters;
-  for (int k = 0; k < 4; ++k) r.itp[k] = k < ncorr ? si[3 + k].iters : 0;
   int st = status;
-  for (int c = 0; c < 3 + (ncorr < 4 ? ncorr : 4); ++c) st = st > si[c].status ? st : si[c].status;
+  for (int c = 0; c < 3; ++c) {
+    int it = 0;
+    for (int k = 0; k < nk; ++k) {
+      it = max(it, si[k * 3 + c].iters);
+      st = max(st, si[k * 3 + c].status);
+    }
+    r.itU[c] = it;
+  }
+  for (int q = 0; q < 4; ++q) {
+    int it = 0;
+    if (q < ncorr)
+      for (int k = 0; k < nk; ++k) {
+        it = max(it, si[(3 + q) * nk + k].iters);
+        st = max(st, si[(3 + q) * nk + k].status);
+      }
+    r.itp[q] = it;
+  }
   r.status = st;
   r.pad = 0;
   for (int k = 0; k < 16; ++k) {
@@ -501,7 +524,8 @@ __global__ void __launch_bounds__(kPB) k_adj_flux_cells(Topo t, const T* af, con
 // fixed-p boundary face), lk / ld (limited non-orthogonal term: weight of the
 // interpolated grad p_s . k_f, and of p_s,N - p_s,O).
 template <typename T, bool NONORTH, bool LAST>
-__global__ void k_adj_pfaces(Topo t, Geo<T> g, T psi, int pin, const T* lam, const T* pn,
+__global__ void k_adj_pfaces(Topo t, Geo<T> g, T psi, int pin, const unsigned char* pinflag,
+                             const T* lam, const T* pn,
                              const T* pk, const T* gk, const T* rAU, const T* af, const T* pb,
                              const T* phio, T* phiHb, T* rfb, T* lk, T* ld, T* pbb, T* Ubb) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -512,7 +536,8 @@ __global__ void k_adj_pfaces(Topo t, Geo<T> g, T psi, int pin, const T* lam, con
     const int2 on = t.on[f];
     const int O = on.x, N = on.y;
     const T lO = lam[O], lN = lam[N], pO = pn[O], pN = pn[N];
-    const T mO = O == pin ? T(2) : T(1), mN = N == pin ? T(2) : T(1);
+    const T mO = (pinflag ? pinflag[O] != 0 : O == pin) ? T(2) : T(1);
+    const T mN = (pinflag ? pinflag[N] != 0 : N == pin) ? T(2) : T(1);
     T afb = lO * pN + lN * pO - lO * pO * mO - lN * pN * mN;
     const T qb = lO - lN;
     T phb = -qb, nob = qb;
@@ -554,7 +579,7 @@ __global__ void k_adj_pfaces(Topo t, Geo<T> g, T psi, int pin, const T* lam, con
     if (LAST) phb += phio[f];
     T r = T(0);
     if (face_kind(t, bb, DIFVM_BC_PRESSURE) == DIFVM_FACE_FIXED) {
-      const T pO = pn[O], mO = O == pin ? T(2) : T(1);
+      const T pO = pn[O], mO = (pinflag ? pinflag[O] != 0 : O == pin) ? T(2) : T(1);
       T afb = lO * pb[bb] - lO * pO * mO;
       if (LAST) afb -= phio[f] * (pb[bb] - pO);
       pbb[bb] += lO * af[f];
@@ -932,7 +957,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   T *Lp = (T*)h->Lp, *bp = (T*)h->bp, *phiH = (T*)h->phiHbyA, *af = (T*)h->af;
   T* no = (T*)h->nonorth;
   // scratch for Windkessel outputs: inside the solve-info buffer tail
-  double* Qd = (double*)(h->sinfo + 8);
+  double* Qd = (double*)(h->sinfo + 7 * h->nk + 1);
   double* pod = Qd + 16;
   int worst = DIFVM_OK;
   TapeLayout TL{};
@@ -991,7 +1016,6 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   }
   if (tape) DIFVM_CUDA(cudaMemcpyAsync(tape + TL.Us, U, v3, cudaMemcpyDeviceToDevice, st));
   // 3. pressure correctors
-  const int pin = h->has_fixed_p ? -1 : o.pref_cell;
   for (int corr = 0; corr < o.n_corr; ++corr) {
     k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, U, HbyA, rAU);
     DIFVM_TRY(check_launch("HbyA"));
@@ -1002,9 +1026,9 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
       k_p_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, psi, HbyA, rAU, Ub, gradp, p, phiH, af, no, Lp);
     }
     DIFVM_TRY(check_launch("p_faces"));
-    k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb, pin, Dp, bp);
+    k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb, h->pin, h->pinflag, Dp, bp);
     DIFVM_TRY(check_launch("p_cells"));
-    difvm_solve_info* si = h->sinfo + 3 + std::min(corr, 3);
+    difvm_solve_info* si = h->sinfo + (3 + std::min(corr, 3)) * h->nk;
     difvm_status s;
     if (h->mixed) {
       k_to64<T><<<Bc, kPB, 0, st>>>(nc, bp, h->b64);
@@ -1032,7 +1056,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     }
   }
   if (info) {
-    k_piso_info<<<1, 32, 0, st>>>(h->sinfo, o.n_corr, DIFVM_OK, o.n_out, Qd, pod, info);
+    k_piso_info<<<1, 32, 0, st>>>(h->sinfo, h->nk, o.n_corr, DIFVM_OK, o.n_out, Qd, pod, info);
     DIFVM_TRY(check_launch("piso_info"));
   }
   return (difvm_status)worst;
@@ -1116,11 +1140,40 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
   h->o = *o;
   h->mixed = prec == DIFVM_F32 && o->solve_p.refine_max > 0;
   h->elt = prec == DIFVM_F64 ? 8 : 4;
-  for (int p = 0; p < m->npatch; ++p) h->has_fixed_p |= m->patch_type[p] == DIFVM_PATCH_OUTLET;
-  if (!h->has_fixed_p && (o->pref_cell < 0 || o->pref_cell >= m->nc)) {
+  h->nk = m->seg ? m->ncases : 1;
+  if (h->mixed && m->seg) {
     delete h;
-    return set_error(DIFVM_EINVAL, "pref_cell %d out of range (no patch fixes p)", o->pref_cell);
+    return set_error(DIFVM_EINVAL, "FP64 refinement of the pressure solve is not available on batched "
+                                   "meshes (use FP32 with FP64 dots, refine_max = 0, or FP64)");
   }
+  // which cases have a fixed-pressure face (their pressure needs no pin)
+  std::vector<char> fixed(h->nk, 0);
+  for (int p = 0; p < m->npatch; ++p) {
+    if (m->patch_type[p] != DIFVM_PATCH_OUTLET) continue;
+    for (int f = m->patch_start[p]; f < m->patch_start[p] + m->patch_size[p]; ++f) {
+      const int own = m->bown_host[f - m->ni];
+      const int k = (int)(std::upper_bound(m->case_start.begin(), m->case_start.end(), own) -
+                          m->case_start.begin()) - 1;
+      fixed[m->seg ? k : 0] = 1;
+    }
+  }
+  std::vector<unsigned char> pf;
+  for (int k = 0; k < h->nk; ++k) {
+    if (fixed[k]) continue;
+    const int n0 = m->seg ? m->case_start[k] : 0, n1 = m->seg ? m->case_start[k + 1] : m->nc;
+    if (o->pref_cell < 0 || o->pref_cell >= n1 - n0) {
+      delete h;
+      return set_error(DIFVM_EINVAL, "pref_cell %d out of range of case %d (no face fixes p there)",
+                       o->pref_cell, k);
+    }
+    if (m->seg) {
+      if (pf.empty()) pf.assign(m->nc, 0);
+      pf[n0 + o->pref_cell] = 1;
+    } else {
+      h->pin = o->pref_cell;
+    }
+  }
+  h->has_fixed_p = fixed[0];
   auto alloc = [&](void** p, size_t bytes) -> bool {
     if (bytes == 0) bytes = 16;
     if (cudaMalloc(p, bytes) != cudaSuccess) return false;
@@ -1142,8 +1195,10 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     h->wsp_bytes = difvm_krylov_workspace_bytes(m, prec, o->solve_p.method, 1);
   }
   ok = ok && alloc(&h->wsp, h->wsp_bytes);
-  // solve infos [8] + Q[16] + p_out[16] + outlet table (start[16], size[16])
-  ok = ok && alloc((void**)&h->sinfo, 8 * sizeof(difvm_solve_info) + 32 * sizeof(double) + 32 * sizeof(int));
+  // solve infos [7 nk + 1] + Q[16] + p_out[16] + outlet table (start[16], size[16])
+  const size_t ninfo = 7 * (size_t)h->nk + 1;
+  ok = ok && alloc((void**)&h->sinfo, ninfo * sizeof(difvm_solve_info) + 32 * sizeof(double) + 32 * sizeof(int));
+  if (!pf.empty()) ok = ok && alloc((void**)&h->pinflag, m->nc);
   if (!ok) {
     difvm_piso_destroy(h);
     return set_error(DIFVM_ENOMEM, "device allocation for the PISO workspace failed");
@@ -1153,9 +1208,10 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     tab[k] = m->patch_start[o->wk_patch[k]];
     tab[16 + k] = m->patch_size[o->wk_patch[k]];
   }
-  double* Qd = (double*)(h->sinfo + 8);
+  double* Qd = (double*)(h->sinfo + ninfo);
   if (cudaMemcpy(Qd + 32, tab, sizeof tab, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(h->sinfo, 0, 8 * sizeof(difvm_solve_info) + 32 * sizeof(double)) != cudaSuccess) {
+      cudaMemset(h->sinfo, 0, ninfo * sizeof(difvm_solve_info) + 32 * sizeof(double)) != cudaSuccess ||
+      (!pf.empty() && cudaMemcpy(h->pinflag, pf.data(), pf.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
     difvm_piso_destroy(h);
     return set_error(DIFVM_ECUDA, "PISO table upload failed");
   }
@@ -1266,9 +1322,8 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   const bool no_U = (o.nonorth & DIFVM_NONORTH_MOMENTUM) != 0;
   const bool no_p = (o.nonorth & DIFVM_NONORTH_PRESSURE) != 0;
   const T psi = (T)o.nonorth_limit;
-  const int pin = h->has_fixed_p ? -1 : o.pref_cell;
   const difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
-  double* Qb = (double*)(h->sinfo + 8);
+  double* Qb = (double*)(h->sinfo + 7 * h->nk + 1);
   double* pob = Qb + 16;
   int worst = DIFVM_OK;
 
@@ -1288,7 +1343,7 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   DIFVM_TRY(check_launch("HbyA"));
   k_p_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, psi, HbyA, rAU, Ub, gradp, ps, phiH, af, no, Lp);
   DIFVM_TRY(check_launch("p_faces"));
-  k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb1, pin, Dp, bp);
+  k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb1, h->pin, h->pinflag, Dp, bp);
   DIFVM_TRY(check_launch("p_cells"));
 
   // adjoint state
@@ -1322,14 +1377,16 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
     }
     T* lam = nullptr;
     {
-      difvm_status sv = adj_psolve<T>(h, pbar, s, lam_scratch, &lam, h->sinfo + 3 + std::min(s, 3), st);
+      difvm_status sv = adj_psolve<T>(h, pbar, s, lam_scratch, &lam,
+                                      h->sinfo + (3 + std::min(s, 3)) * h->nk, st);
       if (sv == DIFVM_EINVAL || sv == DIFVM_ECUDA) return sv;
       worst = std::max(worst, (int)sv);
     }
     DIFVM_CUDA(cudaMemsetAsync(pbar, 0, v1 * sizeof(T), st));   // now the adjoint of p_s
     if (no_p) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, pk, pb1, 1, gp2, st));
 #define DIFVM_PF(NO, LA)                                                                          \
-  k_adj_pfaces<T, NO, LA><<<Bf, kPB, 0, st>>>(t, g, psi, pin, lam, pn, pk, gp2, rAU, af, pb1,    \
+  k_adj_pfaces<T, NO, LA><<<Bf, kPB, 0, st>>>(t, g, psi, h->pin, h->pinflag, lam, pn, pk, gp2,  \
+                                              rAU, af, pb1,                                      \
                                               phio, phiHb, rfb, lk, ld, pbb, Ubbar)
     if (no_p) { if (last) DIFVM_PF(true, true); else DIFVM_PF(true, false); }
     else { if (last) DIFVM_PF(false, true); else DIFVM_PF(false, false); }
@@ -1386,7 +1443,7 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   if (pbbar && nb > 0)
     DIFVM_CUDA(cudaMemcpyAsync(pbbar, pbb, (size_t)nb * sizeof(T), cudaMemcpyDeviceToDevice, st));
   if (info) {
-    k_piso_info<<<1, 32, 0, st>>>(h->sinfo, K, DIFVM_OK, o.n_out, Qb, pob, info);
+    k_piso_info<<<1, 32, 0, st>>>(h->sinfo, h->nk, K, DIFVM_OK, o.n_out, Qb, pob, info);
     DIFVM_TRY(check_launch("piso_info"));
   }
   return (difvm_status)worst;

@@ -235,6 +235,9 @@ class Mesh:
         self.patch_start = np.asarray(m.patch_start, np.int64)
         self.patch_size = np.asarray(m.patch_size, np.int64)
         self.patch_type = np.asarray(m.patch_type, np.int64)
+        # a case table makes the solvers segmented: one set of Krylov scalars per case
+        self.batched = cs is not None
+        self.n_cases = 1 if cs is None else int(cs.shape[0] - 1)
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -391,20 +394,22 @@ def difvm_krylov_workspace_bytes(mesh, prec, method, ncomp):
 
 def difvm_krylov_solve(mesh, diag, lower, upper, b, x, opts=None, workspace=None, stream=None,
                        raise_on_fail=False, **kw):
-    """Solve A x = b in place (x is the initial guess).  Returns (status, [info per comp])."""
+    """Solve A x = b in place (x is the initial guess).  Returns (status, [info per comp]);
+    on a batched mesh the infos are per case and component, case-major."""
     opts = opts or solve_opts(**kw)
     nq = b.shape[0] if b.dim() == 2 else 1
     prec = _prec(b)
     nbytes = difvm_krylov_workspace_bytes(mesh, prec, opts.method, nq)
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=b.device)
-    info = _info_buf(nq, b.device)
+    nk = getattr(mesh, "n_cases", 1) if getattr(mesh, "batched", False) else 1
+    info = _info_buf(nk * nq, b.device)
     st = lib().difvm_krylov_solve(_mh(mesh), prec, C.byref(opts), _ptr(diag), _ptr(lower), _ptr(upper),
                                   _ptr(b), _ptr(x), nq, _ptr(workspace), workspace.numel(), _ptr(info),
                                   _stream(stream))
     if st in (EINVAL, ECUDA, ENOMEM) or (raise_on_fail and st != OK):
         _check(st)
-    return st, decode_solve_info(info, nq)
+    return st, decode_solve_info(info, nk * nq)
 
 
 def difvm_krylov_solve_refine(mesh, diag32, lower32, upper32, b64, x64, opts=None, workspace=None,

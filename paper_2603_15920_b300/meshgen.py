@@ -145,6 +145,33 @@ def shuffle(mesh: Mesh, seed: int) -> Mesh:
     ).check()
 
 
+def batch(meshes):
+    """Disjoint union of independent meshes (the batched input of Sec. 2.4:
+    many cases in one launch).  Cells and internal faces are concatenated in
+    case order; boundary patches are listed case by case and named
+    "c<k>/<name>".  Returns (mesh, case_cell_start[n_cases + 1])."""
+    cs = np.concatenate([[0], np.cumsum([m.n_cells for m in meshes])]).astype(np.int32)
+    owner_i, nei, S_i, X_i = [], [], [], []
+    for k, m in enumerate(meshes):
+        ni = m.n_internal
+        owner_i.append(m.owner[:ni] + cs[k])
+        nei.append(m.neighbour + cs[k])
+        S_i.append(m.Sf[:ni])
+        X_i.append(m.Cf[:ni])
+    groups, names, types = [], [], []
+    for k, m in enumerate(meshes):
+        for p, nm in enumerate(m.patch_names):
+            f = m.patch_faces(nm)
+            groups.append((m.owner[f] + cs[k], m.Sf[f], m.Cf[f]))
+            names.append(f"c{k}/{nm}")
+            types.append(int(m.patch_type[p]))
+    u = _finish(int(cs[-1]), np.concatenate(owner_i), np.concatenate(nei),
+                np.concatenate(S_i), np.concatenate(X_i),
+                np.concatenate([m.V for m in meshes]), np.concatenate([m.C for m in meshes]),
+                groups, names, types)
+    return u, cs
+
+
 # ---------------------------------------------------------------------------
 # uniform hex box
 # ---------------------------------------------------------------------------
