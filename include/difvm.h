@@ -89,7 +89,11 @@ typedef struct difvm_mesh* difvm_mesh_t;
  *   Cf[3*n_faces]: face centroid.  V[n_cells]: volume.  C[3*n_cells]: centroid.
  *   n_cases / case_cell_start[n_cases+1]: a batch of independent meshes laid
  *     out as one disjoint union (cells of case k in [start[k], start[k+1]));
- *     n_cases <= 1 and NULL for a single mesh.
+ *     no face may couple two cases.  A non-NULL case table (also with
+ *     n_cases = 1) makes the mesh BATCHED: its Krylov solves are segmented,
+ *     every case keeping its own scalars, convergence flag and iteration count
+ *     (the result of a case does not depend on the other cases of the batch,
+ *     bit for bit).  NULL for a single mesh (the single-mesh solvers).
  *   flags: DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES (internal faces are always
  *     re-oriented so that owner < neighbour).
  *   device: CUDA device ordinal the handle lives on. */
@@ -238,7 +242,8 @@ size_t difvm_krylov_workspace_bytes(difvm_mesh_t, difvm_prec, int method, int nc
  * BiCGStab (Sec. 2.6.1: CG for the SPD pressure system, BiCGStab for the
  * momentum system).  x is the initial guess on entry and the solution on exit.
  * Inner products and norms are accumulated in FP64.  info_dev[ncomp] is device
- * memory.  The call synchronises `stream` every check_every iterations to read
+ * memory; on a batched mesh info_dev[n_cases * ncomp], case-major, and each
+ * case stops on its own residual.  The call synchronises `stream` every check_every iterations to read
  * the convergence flags (iterations issued past convergence do nothing).
  * Returns OK or the worst solver status (ENOTCONV, EBREAKDOWN, ENONFINITE);
  * x holds the last iterate in every case. */
@@ -254,7 +259,8 @@ size_t difvm_krylov_refine_workspace_bytes(difvm_mesh_t, int method, int ncomp);
  * FP32 to opts->inner_tol (relative, 0 = 1e-4) and adds e to x64 in FP64, until
  * ||r||_2 <= max(tol_rel ||b||_2, tol_abs) or refine_max sweeps (0 = 20); a
  * sweep that fails to cut the residual by 4x stops with ENOTCONV.
- * info.iters = total inner iterations, info.refinements = sweeps. */
+ * info.iters = total inner iterations, info.refinements = sweeps.  EINVAL on
+ * batched meshes. */
 difvm_status difvm_krylov_solve_refine(difvm_mesh_t, const difvm_solve_opts* opts, const float* diag,
                                        const float* lower, const float* upper, const double* b64,
                                        double* x64, int ncomp, void* workspace,
@@ -297,7 +303,9 @@ typedef struct {
                            DIFVM_NONORTH_MOMENTUM (momentum diffusion) and
                            DIFVM_NONORTH_PRESSURE (pressure Laplacian, lagged); 0 = none */
   difvm_solve_opts solve_U, solve_p;
-  int32_t pref_cell;    /* internal id of the pinned cell when no patch fixes p */
+  int32_t pref_cell;    /* internal id of the pinned cell when no patch fixes p; on a
+                           batched mesh relative to each case's first cell, for every
+                           case with no fixed-pressure face */
   int32_t wk_scheme;    /* DIFVM_WK_* */
   int32_t n_out;        /* Windkessel outlets (0..16) */
   int32_t wk_patch[16]; /* patch ids of the outlets */
