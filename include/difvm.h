@@ -387,6 +387,19 @@ difvm_status difvm_piso_step_bwd(difvm_piso_t, const void* tape, size_t tape_byt
                                  void* phi_bar, void* p_b_bar, double* wk_bar, void* U_b_bar,
                                  double* nu_bar, difvm_piso_info* info_dev, void* stream);
 difvm_status difvm_piso_adjoint_reset(difvm_piso_t, void* stream);
+/* The same step as a CUDA graph: on the first call for an argument set
+ * (U, p, phi, U_b, p_b, wk, info_dev) the step is captured on an internal
+ * stream, every Krylov solve as a device-side conditional WHILE loop (a few
+ * iterations per pass, a one-thread kernel setting the loop condition from the
+ * solver state, bounded by max_iter), and instantiated; each call then
+ * launches that graph on `stream` (one launch, no host synchronisation, no
+ * host-side convergence checks).  Results equal difvm_piso_step's bit for bit
+ * (iterations past convergence do nothing).  The outcome is only in info_dev
+ * (required); the return value reports argument and launch errors.  The
+ * handle keeps one graph per argument set until destroyed.  Not with
+ * difvm_prof_start active. */
+difvm_status difvm_piso_step_graph(difvm_piso_t, void* U, void* p, void* phi, const void* U_b,
+                                   void* p_b, double* wk, difvm_piso_info* info_dev, void* stream);
 /* Initial face flux phi_f = U_f . S_f (linear interpolation; boundary: U_b.S
  * for fixed velocity, U_O.S for zero gradient, 0 for empty). */
 difvm_status difvm_flux_from_U(difvm_mesh_t, difvm_prec, const void* U, const void* U_b,

@@ -15,13 +15,15 @@ namespace difvm {
 // ----------------------------------------------------------------- errors
 difvm_status set_error(difvm_status st, const char* fmt, ...);
 void count_launch();
-difvm_status check_launch(const char* what);
+difvm_status check_launch(const char* what);   // counts one launch, then check_error
+difvm_status check_error(const char* what);    // pending launch error -> ECUDA
 
 // --------------------------------------------------- per-kernel event timing
 // When difvm_prof_start(tag) is active, launches wrapped in prof_before /
 // prof_after with the same tag get a pair of CUDA events on their stream.
 void prof_before(int tag, cudaStream_t s);
 void prof_after(int tag, cudaStream_t s);
+bool prof_active();
 
 #define DIFVM_CUDA(call)                                                            \
   do {                                                                              \
@@ -30,10 +32,10 @@ void prof_after(int tag, cudaStream_t s);
       return ::difvm::set_error(DIFVM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-#define DIFVM_TRY(expr)                 \
-  do {                                  \
-    difvm_status s_ = (expr);           \
-    if (s_ != DIFVM_OK) return s_;      \
+#define DIFVM_TRY(expr)                                   \
+  do {                                                    \
+    difvm_status difvm_try_st_ = (expr);                  \
+    if (difvm_try_st_ != DIFVM_OK) return difvm_try_st_;  \
   } while (0)
 
 // ------------------------------------------------------------ vector types
@@ -166,6 +168,25 @@ inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) /
 
 // rows per block of the segmented (batched) Krylov kernels: 512 threads x 4 rows
 constexpr int kSegRows = 2048;
+
+// --------------------------------------------- CUDA-graph device loops (graph.cu)
+bool stream_capturing(cudaStream_t st);
+struct WhileLoop {
+  cudaStream_t side = nullptr;  // stream that captures the loop body
+  cudaGraph_t body = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  bool open = false;
+};
+// Adds a conditional WHILE node at the capture point of `st` and starts
+// capturing its body on L.side; while_close ends the body capture.
+difvm_status while_open(cudaStream_t st, WhileLoop& L);
+difvm_status while_close(WhileLoop& L);
+// loop condition: any of n int flags (stride_ints apart) is 0, and the body has
+// run fewer than `cap` times
+__global__ void k_loop_cond(const int* done_flags, int stride_ints, int n, int* counter, int cap,
+                            cudaGraphConditionalHandle h);
+// iterations per loop-body execution when a solve runs inside a graph
+constexpr int kGraphUnroll = 4;
 difvm_status check_mesh(const difvm_mesh* m);
 difvm_status check_prec(difvm_prec p);
 

@@ -38,6 +38,12 @@ struct KState {
   int zero_rhs, pad0, pad1, pad2;
 };
 
+static_assert(sizeof(KState) % sizeof(int) == 0, "KState must be a whole number of ints");
+constexpr int kStateInts = (int)(sizeof(KState) / sizeof(int));
+inline const int* done_flags(const KState* st) {
+  return reinterpret_cast<const int*>(reinterpret_cast<const char*>(st) + offsetof(KState, done));
+}
+
 struct KWork {
   KState* st;        // [ncomp]
   double* part;      // [grid * kMaxParts]
@@ -825,32 +831,49 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
   DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
   T* rD = vec(L.n_vec - 1);
   bool done = false;
+  const bool graph = stream_capturing(st);
+  int* counter = reinterpret_cast<int*>(w.ticket) + 1;   // loop counter under a graph
+  // the iterations: on the host loop, or as the body of a device WHILE node
+  auto run = [&](auto&& iter) -> difvm_status {
+    if (graph) {
+      DIFVM_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+      WhileLoop Lw;
+      DIFVM_TRY(while_open(st, Lw));
+      for (int k = 0; k < kGraphUnroll; ++k) iter(Lw.side);
+      k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(w.st), kStateInts, NC, counter,
+                                         w.maxit / kGraphUnroll + 2, Lw.h);
+      difvm_status e = check_launch("loop_cond");
+      DIFVM_TRY(while_close(Lw));
+      return e;
+    }
+    for (int it = 0; it < w.maxit;) {
+      const int n = std::min(chunk, w.maxit - it);
+      for (int k = 0; k < n; ++k) iter(st);
+      DIFVM_TRY(check_error("krylov_iter"));
+      it += n;
+      DIFVM_TRY(read_states<NC>(host_state, w, st, done));
+      if (done) break;
+    }
+    return DIFVM_OK;
+  };
   if (o->method == DIFVM_PCG) {
     T *r = vec(0), *p = vec(NC), *q = vec(2 * NC);
     k_pcg_init<T, NC><<<G, kKB, 0, st>>>(t, A, jac, b, x, r, p, rD, w);
     DIFVM_TRY(check_launch("pcg_init"));
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
-    int it = 0;
-    while (it < w.maxit) {
-      int n = std::min(chunk, w.maxit - it);
-      for (int k = 0; k < n; ++k) {
-        prof_before(DIFVM_PROF_PCG_SPMV, st);
-        k_pcg_spmv<T, NC, MW><<<G, kKB, 0, st>>>(t, A, p, q, w);
-        prof_after(DIFVM_PROF_PCG_SPMV, st);
-        prof_before(DIFVM_PROF_PCG_UPDATE, st);
-        k_pcg_update<T, NC><<<G, kKB, 0, st>>>(nc, p, q, rD, x, r, w);
-        prof_after(DIFVM_PROF_PCG_UPDATE, st);
-        prof_before(DIFVM_PROF_PCG_PUPDATE, st);
-        k_pcg_pupdate<T, NC><<<G, kKB, 0, st>>>(nc, r, rD, p, w);
-        prof_after(DIFVM_PROF_PCG_PUPDATE, st);
-        count_launch(); count_launch();
-        DIFVM_TRY(check_launch("pcg_iter"));
-      }
-      it += n;
-      DIFVM_TRY(read_states<NC>(host_state, w, st, done));
-      if (done) break;
-    }
+    DIFVM_TRY(run([&](cudaStream_t s) {
+      prof_before(DIFVM_PROF_PCG_SPMV, s);
+      k_pcg_spmv<T, NC, MW><<<G, kKB, 0, s>>>(t, A, p, q, w);
+      prof_after(DIFVM_PROF_PCG_SPMV, s);
+      prof_before(DIFVM_PROF_PCG_UPDATE, s);
+      k_pcg_update<T, NC><<<G, kKB, 0, s>>>(nc, p, q, rD, x, r, w);
+      prof_after(DIFVM_PROF_PCG_UPDATE, s);
+      prof_before(DIFVM_PROF_PCG_PUPDATE, s);
+      k_pcg_pupdate<T, NC><<<G, kKB, 0, s>>>(nc, r, rD, p, w);
+      prof_after(DIFVM_PROF_PCG_PUPDATE, s);
+      count_launch(); count_launch(); count_launch();
+    }));
   } else if (o->method == DIFVM_BICGSTAB) {
     T *r = vec(0), *rh = vec(NC), *p = vec(2 * NC), *v = vec(3 * NC), *s_ = vec(4 * NC),
       *tv = vec(5 * NC), *y = vec(6 * NC), *z = vec(7 * NC);
@@ -858,25 +881,17 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     DIFVM_TRY(check_launch("bicg_init"));
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
-    int it = 0;
-    while (it < w.maxit) {
-      int n = std::min(chunk, w.maxit - it);
-      for (int k = 0; k < n; ++k) {
-        k_bicg_p<T, NC><<<G, kKB, 0, st>>>(nc, r, v, p, w);
-        k_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, p, rD, y, w);
-        k_bicg_spmv1<T, NC, MW><<<G, kKB, 0, st>>>(t, A, rh, y, v, w);
-        k_bicg_s<T, NC><<<G, kKB, 0, st>>>(nc, r, v, s_, w);
-        k_bicg_sfinish<T, NC><<<G, kKB, 0, st>>>(nc, y, x, w);
-        k_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, s_, rD, z, w);
-        k_bicg_spmv2<T, NC, MW><<<G, kKB, 0, st>>>(t, A, z, s_, tv, w);
-        k_bicg_update<T, NC><<<G, kKB, 0, st>>>(nc, y, z, s_, tv, rh, x, r, w);
-        for (int q = 0; q < 7; ++q) count_launch();
-        DIFVM_TRY(check_launch("bicg_iter"));
-      }
-      it += n;
-      DIFVM_TRY(read_states<NC>(host_state, w, st, done));
-      if (done) break;
-    }
+    DIFVM_TRY(run([&](cudaStream_t s) {
+      k_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, w);
+      k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, p, rD, y, w);
+      k_bicg_spmv1<T, NC, MW><<<G, kKB, 0, s>>>(t, A, rh, y, v, w);
+      k_bicg_s<T, NC><<<G, kKB, 0, s>>>(nc, r, v, s_, w);
+      k_bicg_sfinish<T, NC><<<G, kKB, 0, s>>>(nc, y, x, w);
+      k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, s_, rD, z, w);
+      k_bicg_spmv2<T, NC, MW><<<G, kKB, 0, s>>>(t, A, z, s_, tv, w);
+      k_bicg_update<T, NC><<<G, kKB, 0, s>>>(nc, y, z, s_, tv, rh, x, r, w);
+      for (int q = 0; q < 8; ++q) count_launch();
+    }));
   } else {
     return set_error(DIFVM_EINVAL, "unknown Krylov method %d", o->method);
   }
@@ -884,6 +899,7 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     k_write_info<<<1, 32, 0, st>>>(NC, w.st, info, 0);
     DIFVM_TRY(check_launch("write_info"));
   }
+  if (graph) return DIFVM_OK;   // outcome in info_dev; the host reads nothing under capture
   DIFVM_TRY(read_states<NC>(host_state, w, st, done));
   int worst = DIFVM_OK;
   for (int c = 0; c < NC; ++c) worst = std::max(worst, host_state[c].status);
@@ -1145,25 +1161,38 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
   DIFVM_TRY(check_launch("rr_init"));
   KState hs[1];
   bool done = false;
-  int it = 0;
-  // the iteration cap is enforced on the device; the host loop is bounded as well
-  while (it < w.maxit + chunk) {
-    for (int k = 0; k < chunk; ++k) {
-      prof_before(DIFVM_PROF_PCG_SPMV, st);
-      k_pcg_spmv<float, 1, MW><<<G, kKB, 0, st>>>(t, A, p, q, w);
-      prof_after(DIFVM_PROF_PCG_SPMV, st);
-      prof_before(DIFVM_PROF_PCG_UPDATE, st);
-      k_rr_update<<<G, kKB, 0, st>>>(nc, p, q, rD, hi, lo, r, w);
-      prof_after(DIFVM_PROF_PCG_UPDATE, st);
-      prof_before(DIFVM_PROF_PCG_PUPDATE, st);
-      k_rr_pupdate<<<G, kKB, 0, st>>>(t, A, b64, hi, lo, r, rD, p, w);
-      prof_after(DIFVM_PROF_PCG_PUPDATE, st);
-      count_launch(); count_launch();
-      DIFVM_TRY(check_launch("rr_iter"));
+  auto iter = [&](cudaStream_t s) {
+    prof_before(DIFVM_PROF_PCG_SPMV, s);
+    k_pcg_spmv<float, 1, MW><<<G, kKB, 0, s>>>(t, A, p, q, w);
+    prof_after(DIFVM_PROF_PCG_SPMV, s);
+    prof_before(DIFVM_PROF_PCG_UPDATE, s);
+    k_rr_update<<<G, kKB, 0, s>>>(nc, p, q, rD, hi, lo, r, w);
+    prof_after(DIFVM_PROF_PCG_UPDATE, s);
+    prof_before(DIFVM_PROF_PCG_PUPDATE, s);
+    k_rr_pupdate<<<G, kKB, 0, s>>>(t, A, b64, hi, lo, r, rD, p, w);
+    prof_after(DIFVM_PROF_PCG_PUPDATE, s);
+    count_launch(); count_launch(); count_launch();
+  };
+  const bool graph = stream_capturing(st);
+  if (graph) {
+    int* counter = reinterpret_cast<int*>(w.ticket) + 1;
+    DIFVM_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    WhileLoop Lw;
+    DIFVM_TRY(while_open(st, Lw));
+    for (int k = 0; k < kGraphUnroll; ++k) iter(Lw.side);
+    k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(w.st), kStateInts, 1, counter,
+                                       w.maxit / kGraphUnroll + 2, Lw.h);
+    difvm_status e = check_launch("loop_cond");
+    DIFVM_TRY(while_close(Lw));
+    DIFVM_TRY(e);
+  } else {
+    // the iteration cap is enforced on the device; the host loop is bounded as well
+    for (int it = 0; it < w.maxit + chunk; it += chunk) {
+      for (int k = 0; k < chunk; ++k) iter(st);
+      DIFVM_TRY(check_error("rr_iter"));
+      DIFVM_TRY(read_states<1>(hs, w, st, done));
+      if (done) break;
     }
-    it += chunk;
-    DIFVM_TRY(read_states<1>(hs, w, st, done));
-    if (done) break;
   }
   k_rr_final<<<G, kKB, 0, st>>>(nc, hi, lo, x64, w);
   DIFVM_TRY(check_launch("rr_final"));
@@ -1171,6 +1200,7 @@ static difvm_status rr_pcg(difvm_mesh_t m, const difvm_solve_opts* o, const floa
     k_rr_info<<<1, 32, 0, st>>>(w.st, info);
     DIFVM_TRY(check_launch("rr_info"));
   }
+  if (graph) return DIFVM_OK;   // outcome in info_dev
   DIFVM_TRY(read_states<1>(hs, w, st, done));
   int s = hs[0].status;
   if (s == DIFVM_OK && !hs[0].done) s = DIFVM_ENOTCONV;
@@ -1744,25 +1774,42 @@ static difvm_status solve_sg(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     DIFVM_CUDA(cudaStreamSynchronize(st));
     return DIFVM_OK;
   };
+  const bool graph = stream_capturing(st);
+  int* counter = flag + 1;   // loop counter under a graph
+  auto run = [&](auto&& iter) -> difvm_status {
+    if (graph) {
+      DIFVM_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+      WhileLoop Lw;
+      DIFVM_TRY(while_open(st, Lw));
+      for (int k = 0; k < kGraphUnroll; ++k) iter(Lw.side);
+      k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(w.st), kStateInts, nst, counter,
+                                         w.maxit / kGraphUnroll + 2, Lw.h);
+      difvm_status e = check_launch("loop_cond");
+      DIFVM_TRY(while_close(Lw));
+      return e;
+    }
+    for (int it = 0; it < w.maxit;) {
+      const int n = std::min(chunk, w.maxit - it);
+      for (int k = 0; k < n; ++k) iter(st);
+      DIFVM_TRY(check_error("sg_iter"));
+      it += n;
+      DIFVM_TRY(poll());
+      if (!host_flag) break;
+    }
+    return DIFVM_OK;
+  };
   if (o->method == DIFVM_PCG) {
     T *r = vec(0), *p = vec(NC), *q = vec(2 * NC);
     k_sg_pcg_init<T, NC><<<G, kKB, 0, st>>>(t, A, jac, b, x, r, p, rD, w);
     DIFVM_TRY(check_launch("sg_pcg_init"));
     k_sg_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("sg_zero_rhs"));
-    for (int it = 0; it < w.maxit;) {
-      const int n = std::min(chunk, w.maxit - it);
-      for (int k = 0; k < n; ++k) {
-        k_sg_pcg_spmv<T, NC, MW><<<G, kKB, 0, st>>>(t, A, p, q, w);
-        k_sg_pcg_update<T, NC><<<G, kKB, 0, st>>>(nc, p, q, rD, x, r, w);
-        k_sg_pcg_pupdate<T, NC><<<G, kKB, 0, st>>>(nc, r, rD, p, w);
-        count_launch(); count_launch();
-        DIFVM_TRY(check_launch("sg_pcg_iter"));
-      }
-      it += n;
-      DIFVM_TRY(poll());
-      if (!host_flag) break;
-    }
+    DIFVM_TRY(run([&](cudaStream_t s) {
+      k_sg_pcg_spmv<T, NC, MW><<<G, kKB, 0, s>>>(t, A, p, q, w);
+      k_sg_pcg_update<T, NC><<<G, kKB, 0, s>>>(nc, p, q, rD, x, r, w);
+      k_sg_pcg_pupdate<T, NC><<<G, kKB, 0, s>>>(nc, r, rD, p, w);
+      count_launch(); count_launch(); count_launch();
+    }));
   } else if (o->method == DIFVM_BICGSTAB) {
     T *r = vec(0), *rh = vec(NC), *p = vec(2 * NC), *v = vec(3 * NC), *s_ = vec(4 * NC),
       *tv = vec(5 * NC), *y = vec(6 * NC), *z = vec(7 * NC);
@@ -1770,24 +1817,17 @@ static difvm_status solve_sg(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     DIFVM_TRY(check_launch("sg_bicg_init"));
     k_sg_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("sg_zero_rhs"));
-    for (int it = 0; it < w.maxit;) {
-      const int n = std::min(chunk, w.maxit - it);
-      for (int k = 0; k < n; ++k) {
-        k_sg_bicg_p<T, NC><<<G, kKB, 0, st>>>(nc, r, v, p, w);
-        k_sg_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, p, rD, y, w, 0);
-        k_sg_bicg_spmv1<T, NC, MW><<<G, kKB, 0, st>>>(t, A, rh, y, v, w);
-        k_sg_bicg_s<T, NC><<<G, kKB, 0, st>>>(nc, r, v, s_, w);
-        k_sg_bicg_sfinish<T, NC><<<G, kKB, 0, st>>>(nc, y, x, w);
-        k_sg_bicg_scale<T, NC><<<G, kKB, 0, st>>>(nc, s_, rD, z, w, 1);
-        k_sg_bicg_spmv2<T, NC, MW><<<G, kKB, 0, st>>>(t, A, z, s_, tv, w);
-        k_sg_bicg_update<T, NC><<<G, kKB, 0, st>>>(nc, y, z, s_, tv, rh, x, r, w);
-        for (int q = 0; q < 7; ++q) count_launch();
-        DIFVM_TRY(check_launch("sg_bicg_iter"));
-      }
-      it += n;
-      DIFVM_TRY(poll());
-      if (!host_flag) break;
-    }
+    DIFVM_TRY(run([&](cudaStream_t s) {
+      k_sg_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, w);
+      k_sg_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, p, rD, y, w, 0);
+      k_sg_bicg_spmv1<T, NC, MW><<<G, kKB, 0, s>>>(t, A, rh, y, v, w);
+      k_sg_bicg_s<T, NC><<<G, kKB, 0, s>>>(nc, r, v, s_, w);
+      k_sg_bicg_sfinish<T, NC><<<G, kKB, 0, s>>>(nc, y, x, w);
+      k_sg_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, s_, rD, z, w, 1);
+      k_sg_bicg_spmv2<T, NC, MW><<<G, kKB, 0, s>>>(t, A, z, s_, tv, w);
+      k_sg_bicg_update<T, NC><<<G, kKB, 0, s>>>(nc, y, z, s_, tv, rh, x, r, w);
+      for (int q = 0; q < 8; ++q) count_launch();
+    }));
   } else {
     return set_error(DIFVM_EINVAL, "unknown Krylov method %d", o->method);
   }
@@ -1795,6 +1835,7 @@ static difvm_status solve_sg(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     k_sg_write_info<<<blocks_for(nst, 128), 128, 0, st>>>(nst, w.st, info);
     DIFVM_TRY(check_launch("sg_write_info"));
   }
+  if (graph) return DIFVM_OK;   // outcome in info_dev
   // worst status over all cases and components
   std::vector<KState> hs(nst);
   DIFVM_CUDA(cudaMemcpyAsync(hs.data(), w.st, sizeof(KState) * nst, cudaMemcpyDeviceToHost, st));

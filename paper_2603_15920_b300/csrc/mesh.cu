@@ -41,6 +41,8 @@ struct ProfState {
 };
 static ProfState g_prof;
 
+bool prof_active() { return g_prof.tag != 0; }
+
 void prof_before(int tag, cudaStream_t s) {
   if (g_prof.tag == tag && g_prof.n < g_prof.cap) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
 }
@@ -51,6 +53,10 @@ void prof_after(int tag, cudaStream_t s) {
 
 difvm_status check_launch(const char* what) {
   count_launch();
+  return check_error(what);
+}
+
+difvm_status check_error(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(DIFVM_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
   return DIFVM_OK;

@@ -50,6 +50,13 @@ struct difvm_piso {
   // starting guesses of the adjoint pressure solves, one per corrector (FP64 on
   // mixed-precision handles): the previous reverse step's solutions
   void* a_lamw = nullptr;
+  // CUDA-graph form of the step: one instantiated graph per argument set
+  struct GraphEntry {
+    const void* key[7];
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace difvm {
@@ -1111,6 +1118,9 @@ extern "C" difvm_status difvm_flux_from_U(difvm_mesh_t m, difvm_prec prec, const
 
 extern "C" void difvm_piso_destroy(difvm_piso_t h) {
   if (!h) return;
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -1503,4 +1513,48 @@ extern "C" difvm_status difvm_piso_step_bwd(difvm_piso_t h, const void* tape, si
   return piso_step_bwd_t<float>(h, tp, (const float*)Ub, wk, (float*)U_bar, (float*)p_bar,
                                 (float*)phi_bar, (float*)p_b_bar, wk_bar, (float*)U_b_bar, nu_bar,
                                 info, st);
+}
+
+// The step as a CUDA graph: captured once per argument set on an internal
+// stream (each Krylov solve becomes a device-side WHILE loop), then replayed
+// with one launch on the caller's stream.  No host synchronisation.
+extern "C" difvm_status difvm_piso_step_graph(difvm_piso_t h, void* U, void* p, void* phi,
+                                              const void* Ub, void* pb, double* wk,
+                                              difvm_piso_info* info, void* stream) {
+  if (!h) return set_error(DIFVM_EINVAL, "null PISO handle");
+  if (!U || !p || !phi || !info) return set_error(DIFVM_EINVAL, "null state field or info");
+  if (h->o.n_out > 0 && !wk) return set_error(DIFVM_EINVAL, "Windkessel outlets need the wk state array");
+  if (prof_active())
+    return set_error(DIFVM_EINVAL, "per-kernel profiling is not available inside a graph");
+  const void* key[7] = {U, p, phi, Ub, pb, wk, info};
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : h->graphs)
+    if (std::equal(key, key + 7, g.key)) exec = g.exec;
+  if (!exec) {
+    if (!h->cap_stream) DIFVM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    DIFVM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    difvm_status st = h->prec == DIFVM_F64
+                          ? piso_step_t<double>(h, (double*)U, (double*)p, (double*)phi,
+                                                (const double*)Ub, (double*)pb, wk, info, nullptr, cs)
+                          : piso_step_t<float>(h, (float*)U, (float*)p, (float*)phi,
+                                               (const float*)Ub, (float*)pb, wk, info, nullptr, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (st != DIFVM_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (st != DIFVM_OK) return st;
+      return set_error(DIFVM_ECUDA, "capture of the PISO step: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+      return set_error(DIFVM_ECUDA, "instantiation of the PISO step graph: %s", cudaGetErrorString(e));
+    difvm_piso::GraphEntry ge;
+    std::copy(key, key + 7, ge.key);
+    ge.exec = exec;
+    h->graphs.push_back(ge);
+  }
+  DIFVM_CUDA(cudaGraphLaunch(exec, (cudaStream_t)stream));
+  return DIFVM_OK;
 }

@@ -107,6 +107,7 @@ _SIGS = {
     "difvm_piso_step_bwd": [_vp, _vp, C.c_size_t, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp],
     "difvm_piso_adjoint_reset": [_vp, _vp],
+    "difvm_piso_step_graph": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "difvm_flux_from_U": [_vp, _i, _vp, _vp, _vp, _vp],
     "difvm_laplacian_apply_bwd_noalloc": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
                                           _vp],
@@ -518,6 +519,15 @@ class Piso:
         return st, info
 
 
+    def step_graph(self, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
+        """The step as one CUDA-graph launch (captured on the first call for these
+        tensors).  Returns the info buffer; the status is in it (decode_piso_info)."""
+        if info is None:
+            info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U.device)
+        _check(lib().difvm_piso_step_graph(self.h, _ptr(U), _ptr(p), _ptr(phi), _ptr(U_b), _ptr(p_b),
+                                           _ptr(wk), _ptr(info), _stream(stream)))
+        return info
+
     def tape_bytes(self):
         return int(lib().difvm_piso_tape_bytes(self.h))
 
@@ -564,6 +574,10 @@ def difvm_piso_step(piso, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
     return piso.step(U, p, phi, U_b, p_b, wk, info, stream)
 
 
+def difvm_piso_step_graph(piso, U, p, phi, U_b, p_b, wk=None, info=None, stream=None):
+    return piso.step_graph(U, p, phi, U_b, p_b, wk, info, stream)
+
+
 def difvm_piso_tape_bytes(piso):
     return piso.tape_bytes()
 
@@ -579,7 +593,8 @@ def difvm_piso_step_bwd(piso, tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar=None
 
 
 # ------------------------------------------------- forward + adjoint trajectory
-def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=None, stream=None):
+def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=None, stream=None,
+                     tapes=None):
     """n PISO steps forward, then the adjoint of a loss of the final state back
     to the initial state and the parameters (Sec. 2.5, Eq. vjp).
 
@@ -593,12 +608,15 @@ def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=N
     plus n/k states; cost: one extra forward step per step).  None: every step
     is recorded in the forward pass (n tapes, no recomputation).
 
+    tapes: optional preallocated list of at least k tapes (piso.new_tape).
+
     Returns dict(U, p, phi, p_b, pc: adjoints of the initial state; U_b, nu,
     Rp, C, Rd: parameter adjoints; status: worst step status; info: the
     adjoint solver record of the first step)."""
     U, p, phi, Ub, pb = state
     k = nsteps if not checkpoint_every else max(1, min(int(checkpoint_every), nsteps))
-    tapes = [piso.new_tape(U.device) for _ in range(k)]
+    if tapes is None or len(tapes) < k:
+        tapes = [piso.new_tape(U.device) for _ in range(k)]
     worst = OK
     n_out = piso.opts.n_out
     snaps = []
