@@ -122,6 +122,71 @@ class Clocks:
 
 
 # ---------------------------------------------------------- CPU baseline
+def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4):
+    """Batched form: n_cases independent lid cavities of Kuhn n^3 tetrahedra,
+    n ~ U{8..48}, jitter 0.2h, random lid velocity (speed U(0.5, 1.5), direction
+    in the lid plane), Re = 100 for unit speed, one disjoint-union mesh, F32 with
+    FP64 dots, per-case solver scalars, every step one CUDA graph."""
+    from paper_2603_15920_b300 import meshgen as mg
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(8, 49, size=n_cases)
+    u, cs = mg.batch([mg.kuhn_cube(int(n), JITTER, 100 + k) for k, n in enumerate(ns)])
+    dm = D.Mesh(u, case_cell_start=cs)
+    Ub_h = np.zeros((3, u.n_boundary))
+    for k in range(n_cases):
+        sp, th = rng.uniform(0.5, 1.5), rng.uniform(0.0, 2.0 * np.pi)
+        f = u.patch_faces(f"c{k}/y1") - u.n_internal
+        Ub_h[0, f], Ub_h[2, f] = sp * np.cos(th), sp * np.sin(th)
+    o = D.piso_opts(NU, DT, 2, NONORTH,
+                    solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
+                    solve_p=D.solve_opts(D.PCG, 1e-8, max_iter=20000, check_every=32),
+                    pref_cell=0)
+    h = D.Piso(dm, D.F32, o)
+    U = torch.zeros((3, dm.nc), device="cuda")
+    p = torch.zeros(dm.nc, device="cuda")
+    ub = torch.as_tensor(dm.to_bnd(Ub_h), dtype=torch.float32, device="cuda").contiguous()
+    pb = torch.zeros(dm.nb, device="cuda")
+    phi = D.difvm_flux_from_U(dm, U, ub)
+    info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(W):
+        h.step_graph(U, p, phi, ub, pb, info=info)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        h.step_graph(U, p, phi, ub, pb, info=info)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    gi = D.decode_piso_info(info)
+    # forward + adjoint of the total kinetic energy over K steps (all taped)
+    V = torch.as_tensor(dm.to_cells(u.V), dtype=torch.float32, device="cuda")
+
+    def ke_grad(U_, p_, phi_, pb_, wk_):
+        return (V * U_).contiguous(), torch.zeros_like(p_), torch.zeros_like(phi_), None, None
+    state = [U, p, phi, ub, pb]
+    tapes = [h.new_tape("cuda") for _ in range(K)]
+    D.simulate_adjoint(h, [t.clone() for t in state], 1, ke_grad, tapes=tapes)
+    base = [t.clone() for t in state]
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    adj = D.simulate_adjoint(h, base, K, ke_grad, tapes=tapes)
+    a1.record()
+    torch.cuda.synchronize()
+    fa = a0.elapsed_time(a1) / K
+    return {"workload": f"{n_cases} Kuhn lid cavities, n ~ U{{8..48}}, jitter {JITTER}, "
+                        f"random lid velocity, seed {seed}",
+            "cells": int(dm.nc), "cases": n_cases, "value": 1e3 / ms, "unit": "steps/s",
+            "ms_per_step": ms, "cell_steps_per_s": dm.nc * 1e3 / ms, "steps": K, "warmup": W,
+            "api": "difvm_piso_step_graph on a batched mesh (per-case Krylov scalars)",
+            "precision": "f32 fields, f64 dots, pressure tol 1e-8 per case",
+            "status": int(gi["status"]), "pressure_iters_max_over_cases": gi["itp"][:2],
+            "fwd_adj_ms_per_step": fa, "fwd_adjoint_over_fwd": fa / ms,
+            "fwd_adjoint_note": "forward steps of the adjoint run are recorded host-loop steps",
+            "adjoint_status": int(adj["status"])}
+
+
 def cpu_oracle_step_rate(m, steps=1, warm_steps=0):
     """The FP64 CPU oracle (single thread, as it stands) on the same cavity.
     Returns (steps/s, seconds, sample description)."""
@@ -385,6 +450,8 @@ def run_ours(args):
                "adjoint_iters_first_step": {k_: D.decode_piso_info(adj["info"])[k_][:n_]
                                             for k_, n_ in (("itU", 3), ("itp", 2))}}
 
+    batched = None if args.no_batch else run_batched(D, torch)
+
     if rank != 0:
         return 0
     # CPU baseline: one full oracle PISO step of the same cavity (single thread)
@@ -416,6 +483,7 @@ def run_ours(args):
                 "pressure_iters_last_step": r64["info"]["itp"][:2],
                 "momentum_iters_last_step": r64["info"]["itU"]},
         "fwd_adjoint_over_fwd": fwd_adj,
+        "batched": batched,
         "roofline": {"kernel": "k_pcg_spmv<float,1> (LDU SpMV + p.q)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -439,6 +507,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-case line")
     ap.add_argument("--mesh", type=int, default=N_KUHN, help="Kuhn hex grid size n (n^3 hexes)")
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the F32 form (no F64 or end-to-end legs; for profiling runs)")
