@@ -74,7 +74,16 @@ enum { DIFVM_FACE_FIXED = 0, DIFVM_FACE_ZEROGRAD = 1, DIFVM_FACE_EMPTY = 2 };
 enum { DIFVM_DIV_UPWIND = 0, DIFVM_DIV_LINEAR = 1 };           /* Eq. upwind / central */
 enum { DIFVM_WK_EXACT = 0, DIFVM_WK_FE = 1, DIFVM_WK_BE = 2 };  /* Eq. windkessel_discrete */
 enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
-enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1 };
+/* DIFVM_PRECOND_AMG: one V-cycle of aggregation multigrid per CG iteration
+ * (pairwise aggregation on c_f, two passes per level, down to <= 256 cells;
+ * Galerkin coarse operators summed in a fixed order every solve; two damped
+ * Jacobi sweeps (omega 0.7) before and after the coarse correction, which is
+ * scaled by 1.8; dense inverse on the coarsest level).  A fixed SPD operator:
+ * it changes the iteration count, not the solution.  The paper uses ILU, whose
+ * triangular solves are sequential along the mesh ordering.  Single-RHS CG on
+ * a symmetric matrix of a single mesh only (EINVAL otherwise); the hierarchy
+ * is built on the host on first use and kept by the mesh. */
+enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1, DIFVM_PRECOND_AMG = 2 };
 enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };
 enum { DIFVM_NONORTH_MOMENTUM = 1, DIFVM_NONORTH_PRESSURE = 2, DIFVM_NONORTH_ALL = 3 };
 
@@ -219,7 +228,7 @@ difvm_status difvm_laplacian_apply_bwd_noalloc(difvm_mesh_t, difvm_prec, const v
 /* ------------------------------------------------------------------- Krylov */
 typedef struct {
   int32_t method;      /* DIFVM_PCG (SPD) or DIFVM_BICGSTAB */
-  int32_t precond;     /* DIFVM_PRECOND_NONE or DIFVM_PRECOND_JACOBI */
+  int32_t precond;     /* DIFVM_PRECOND_NONE, DIFVM_PRECOND_JACOBI or DIFVM_PRECOND_AMG */
   int32_t max_iter;
   int32_t check_every; /* iterations between host convergence checks (0 = 8) */
   double tol_rel;      /* stop when ||b - A x||_2 <= max(tol_rel ||b||_2, tol_abs) */
@@ -235,7 +244,15 @@ typedef struct {
   double res0, res, bnorm;
 } difvm_solve_info;
 
-/* Bytes of workspace difvm_krylov_solve needs for (prec, method, ncomp). */
+/* Bytes of workspace a solve with these options needs: difvm_krylov_solve and
+ * difvm_krylov_solve_bwd, and also difvm_krylov_solve_refine when prec is F32
+ * and opts->refine_max > 0; covers
+ * the multigrid preconditioner (whose hierarchy this call builds on first use).
+ * 0 for an invalid combination. */
+size_t difvm_krylov_opts_workspace_bytes(difvm_mesh_t, difvm_prec, const difvm_solve_opts* opts,
+                                         int ncomp);
+/* Bytes of workspace difvm_krylov_solve needs for (prec, method, ncomp) with
+ * Jacobi or no preconditioning. */
 size_t difvm_krylov_workspace_bytes(difvm_mesh_t, difvm_prec, int method, int ncomp);
 /* Solve A x_c = b_c for each of ncomp right-hand sides with the LDU matrix
  * (diag, lower, upper; upper NULL = symmetric) by Jacobi-preconditioned CG or

@@ -1,0 +1,907 @@
+// Aggregation multigrid preconditioner for the symmetric pressure system
+// (the CG of Sec. 2.6.1).
+//
+// The paper preconditions CG with ILU; an incomplete factorisation is applied
+// by two triangular solves whose dependency chains run through every RCM level
+// of the mesh, which leaves a 148-SM GPU idle.  Here the preconditioner is one
+// V-cycle of aggregation multigrid, whose every step is a data-parallel sweep:
+//
+//   hierarchy (once per mesh, host): cells are paired along their strongest
+//     face (largest c_f = |S|^2/(S.d)), a cell left alone joins its strongest
+//     neighbour's pair; two such passes make one level (about 4-5 cells per
+//     aggregate), down to at most kAmgCoarsest cells;
+//   operators (every solve, device): Galerkin products with piecewise-constant
+//     prolongation, i.e. sums of the finer level's coefficients (a coarse
+//     diagonal is the sum of its cells' diagonals plus twice the coefficients
+//     of the faces inside it; a coarse face coefficient is the sum of the fine
+//     faces between its two aggregates), each sum in a fixed order;
+//   V-cycle: two damped-Jacobi sweeps before and after the coarse correction,
+//     the coarse correction scaled by kAmgScale, the coarsest level solved
+//     with a dense inverse (Gauss-Jordan in one block, FP64).
+//
+// The V-cycle is a fixed symmetric positive-definite linear operator, so CG
+// keeps its guarantees; it changes the iteration count, not the solution.
+#include <algorithm>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "krylov_common.cuh"
+
+namespace difvm {
+
+constexpr double kAmgOmega = 0.7;   // Jacobi damping
+constexpr double kAmgScale = 1.8;   // over-correction of the coarse-grid correction
+constexpr int kAmgCoarsest = 256;   // coarsen until at most this many cells
+constexpr int kAmgMaxLevels = 16;
+constexpr int kAB = 256;            // threads per block of the AMG kernels
+
+// One level as the kernels see it.  Level 0 is the mesh (its SpMV uses the
+// sliced ELL); on coarser levels `on` / `cptr` / `cent` hold the level's own
+// faces.  The restriction fields describe the map to the next level.
+struct AmgLev {
+  int n, nf;
+  const int2* on;
+  const int* cptr;
+  const int* cent;
+  const int* agg;                     // [n] cell -> next-level cell
+  const int *ch_ptr, *ch_idx;         // next-level cell -> its cells
+  const int *ci_ptr, *ci_idx;         // next-level cell -> faces inside it
+  const int *cf_ptr, *cf_idx;         // next-level face -> faces mapped to it
+};
+
+struct AmgHier {
+  int nlev = 0;
+  std::vector<AmgLev> lev;
+  std::vector<void*> allocs;
+};
+
+void amg_free(AmgHier* h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+// ------------------------------------------------------------ hierarchy (host)
+namespace {
+
+struct Graph {
+  int n = 0;
+  std::vector<int2> on;     // faces, (I, J) with I < J, ascending
+  std::vector<double> w;    // face weights
+};
+
+// one pairwise pass: agg[i] in [0, na)
+void pair_pass(const Graph& g, std::vector<int>& agg, int& na) {
+  const int nf = (int)g.on.size();
+  std::vector<int> ord(nf);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return g.w[a] > g.w[b]; });
+  agg.assign(g.n, -1);
+  na = 0;
+  for (int f : ord) {
+    const int I = g.on[f].x, J = g.on[f].y;
+    if (agg[I] < 0 && agg[J] < 0) agg[I] = agg[J] = na++;
+  }
+  std::vector<int> best(g.n, -1);  // strongest neighbour
+  for (int f : ord) {
+    const int I = g.on[f].x, J = g.on[f].y;
+    if (best[I] < 0) best[I] = J;
+    if (best[J] < 0) best[J] = I;
+  }
+  for (int i = 0; i < g.n; ++i) {
+    if (agg[i] >= 0) continue;
+    const int j = best[i];
+    agg[i] = (j >= 0 && agg[j] >= 0) ? agg[j] : na++;
+  }
+}
+
+// coarse graph of an aggregation; fmap[f] = coarse face, or -1 inside an aggregate
+void coarse_graph(const Graph& g, const std::vector<int>& agg, int na, Graph& c, std::vector<int>& fmap) {
+  const int nf = (int)g.on.size();
+  std::vector<int64_t> key(nf, -1);
+  std::vector<int64_t> keys;
+  keys.reserve(nf);
+  for (int f = 0; f < nf; ++f) {
+    int a = agg[g.on[f].x], b = agg[g.on[f].y];
+    if (a == b) continue;
+    if (a > b) std::swap(a, b);
+    key[f] = (int64_t)a * na + b;
+    keys.push_back(key[f]);
+  }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  c.n = na;
+  c.on.resize(keys.size());
+  c.w.assign(keys.size(), 0.0);
+  for (size_t k = 0; k < keys.size(); ++k) c.on[k] = make_int2((int)(keys[k] / na), (int)(keys[k] % na));
+  fmap.assign(nf, -1);
+  for (int f = 0; f < nf; ++f) {
+    if (key[f] < 0) continue;
+    const int F = (int)(std::lower_bound(keys.begin(), keys.end(), key[f]) - keys.begin());
+    fmap[f] = F;
+    c.w[F] += g.w[f];
+  }
+}
+
+template <typename T>
+difvm_status upload_vec(AmgHier* H, const T** dst, const std::vector<T>& v) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+  DIFVM_CUDA(cudaMalloc(&p, bytes));
+  H->allocs.push_back(p);
+  if (!v.empty()) DIFVM_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = (const T*)p;
+  return DIFVM_OK;
+}
+
+// CSR of `key[i]` (values in [0, nk)) listing i ascending
+void group_by(const std::vector<int>& key, int nk, std::vector<int>& ptr, std::vector<int>& idx,
+              const std::vector<char>* keep = nullptr) {
+  ptr.assign(nk + 1, 0);
+  for (size_t i = 0; i < key.size(); ++i)
+    if (key[i] >= 0 && (!keep || (*keep)[i])) ptr[key[i] + 1]++;
+  for (int k = 0; k < nk; ++k) ptr[k + 1] += ptr[k];
+  idx.assign(ptr[nk], 0);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (size_t i = 0; i < key.size(); ++i)
+    if (key[i] >= 0 && (!keep || (*keep)[i])) idx[fill[key[i]]++] = (int)i;
+}
+
+difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
+  // level-0 graph: the mesh's internal faces weighted by c_f
+  Graph g;
+  g.n = m->nc;
+  g.on.resize(m->ni);
+  if (m->ni > 0) DIFVM_CUDA(cudaMemcpy(g.on.data(), m->on, sizeof(int2) * m->ni, cudaMemcpyDeviceToHost));
+  std::vector<V4<double>> ck(m->ni);
+  if (m->ni > 0) DIFVM_CUDA(cudaMemcpy(ck.data(), m->ck64, sizeof(V4<double>) * m->ni, cudaMemcpyDeviceToHost));
+  g.w.resize(m->ni);
+  for (int f = 0; f < m->ni; ++f) g.w[f] = ck[f].x;
+
+  while (true) {
+    AmgLev L{};
+    L.n = g.n;
+    L.nf = (int)g.on.size();
+    const int lvl = (int)H->lev.size();
+    if (lvl == 0) {
+      L.on = m->on;
+      L.cptr = m->cptr;
+      L.cent = m->cent;
+    } else {
+      DIFVM_TRY(upload_vec(H, &L.on, g.on));
+      std::vector<int> cptr(g.n + 1, 0), cent(2 * g.on.size());
+      for (const int2& o : g.on) { cptr[o.x + 1]++; cptr[o.y + 1]++; }
+      for (int i = 0; i < g.n; ++i) cptr[i + 1] += cptr[i];
+      std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+      for (int f = 0; f < (int)g.on.size(); ++f) {   // ascending face id per cell
+        cent[fill[g.on[f].x]++] = f << 1;
+        cent[fill[g.on[f].y]++] = (f << 1) | 1;
+      }
+      DIFVM_TRY(upload_vec(H, &L.cptr, cptr));
+      DIFVM_TRY(upload_vec(H, &L.cent, cent));
+    }
+    const bool last = g.n <= kAmgCoarsest || lvl + 1 >= kAmgMaxLevels;
+    if (!last) {
+      // two pairwise passes make the next level
+      std::vector<int> a1, a2, f1, f2;
+      int n1, n2;
+      Graph g1, g2;
+      pair_pass(g, a1, n1);
+      coarse_graph(g, a1, n1, g1, f1);
+      pair_pass(g1, a2, n2);
+      coarse_graph(g1, a2, n2, g2, f2);
+      if (n2 > 0.85 * g.n) {   // coarsening stalled: this is the coarsest level
+        H->lev.push_back(L);
+        break;
+      }
+      std::vector<int> agg(g.n), fmap(g.on.size()), inside(g.on.size(), -1);
+      for (int i = 0; i < g.n; ++i) agg[i] = a2[a1[i]];
+      for (size_t f = 0; f < g.on.size(); ++f) {
+        const int F1 = f1[f];
+        fmap[f] = F1 < 0 ? -1 : f2[F1];
+        if (fmap[f] < 0) inside[f] = agg[g.on[f].x];
+      }
+      std::vector<int> chp, chi, cip, cii, cfp, cfi;
+      group_by(agg, n2, chp, chi);
+      group_by(inside, n2, cip, cii);
+      group_by(fmap, (int)g2.on.size(), cfp, cfi);
+      DIFVM_TRY(upload_vec(H, &L.agg, agg));
+      DIFVM_TRY(upload_vec(H, &L.ch_ptr, chp));
+      DIFVM_TRY(upload_vec(H, &L.ch_idx, chi));
+      DIFVM_TRY(upload_vec(H, &L.ci_ptr, cip));
+      DIFVM_TRY(upload_vec(H, &L.ci_idx, cii));
+      DIFVM_TRY(upload_vec(H, &L.cf_ptr, cfp));
+      DIFVM_TRY(upload_vec(H, &L.cf_idx, cfi));
+      H->lev.push_back(L);
+      g = std::move(g2);
+      continue;
+    }
+    H->lev.push_back(L);
+    break;
+  }
+  H->nlev = (int)H->lev.size();
+  return DIFVM_OK;
+}
+
+std::mutex g_amg_mu;
+
+}  // namespace
+
+difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
+  std::lock_guard<std::mutex> lk(g_amg_mu);
+  if (!m->amg) {
+    AmgHier* H = new (std::nothrow) AmgHier();
+    if (!H) return set_error(DIFVM_ENOMEM, "host allocation failed");
+    difvm_status s = build_hier(m, H);
+    if (s != DIFVM_OK) {
+      amg_free(H);
+      return s;
+    }
+    m->amg = H;
+  }
+  *out = m->amg;
+  return DIFVM_OK;
+}
+
+// ---------------------------------------------------------- workspace layout
+// [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials | ticket]
+struct AmgLayout {
+  size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], r[kAmgMaxLevels],
+      a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, rhs32, e32, total;
+};
+
+static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
+
+static int amg_grid(const difvm_mesh* m) {
+  return std::max(1, std::min((int)blocks_for(m->nc, kKB), m->num_sms * 4));
+}
+
+static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
+  AmgLayout A{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += up256a(std::max<size_t>(bytes, 1)); return r; };
+  A.val = take((size_t)std::max<int64_t>(m->ell_nslots, 1) * e);
+  for (int k = 0; k < 4; ++k) A.vec[k] = take((size_t)m->nc * e);
+  for (int l = 0; l < H->nlev; ++l) {
+    const AmgLev& L = H->lev[l];
+    A.D[l] = take((size_t)L.n * e);
+    A.rD[l] = take((size_t)L.n * e);
+    A.L[l] = take((size_t)L.nf * e);
+    A.r[l] = take((size_t)L.n * e);
+    A.a[l] = take((size_t)L.n * e);
+    A.b[l] = take((size_t)L.n * e);
+  }
+  const int nco = H->lev[H->nlev - 1].n;
+  A.inv = take((size_t)nco * nco * sizeof(double));
+  A.st = take(4 * sizeof(KState));
+  // partials: the CG kernels use amg_grid blocks, the fine-level smoothing one block per kAB cells
+  const size_t nblk = std::max<size_t>(amg_grid(m), blocks_for(m->nc, kAB));
+  A.part = take(nblk * kMaxParts * sizeof(double));
+  A.ticket = take(256);
+  A.rhs32 = take((size_t)m->nc * 4);
+  A.e32 = take((size_t)m->nc * 4);
+  A.total = o;
+  return A;
+}
+
+size_t amg_workspace_bytes(difvm_mesh* m, size_t elt) {
+  AmgHier* H = nullptr;
+  if (amg_hier(m, &H) != DIFVM_OK) return 0;
+  return amg_layout(m, H, elt).total;
+}
+
+// ------------------------------------------------------------------ kernels
+template <typename T>
+__global__ void k_amg_rd(int n, const T* D, T* rD) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rD[i] = T(1) / D[i];
+}
+
+// coarse diagonal: sum of the cells' diagonals + twice the faces inside
+template <typename T>
+__global__ void k_amg_diag(int n1, AmgLev L, const T* D, const T* Lv, T* D1, T* rD1) {
+  int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= n1) return;
+  T d = T(0);
+  for (int c = L.ch_ptr[K]; c < L.ch_ptr[K + 1]; ++c) d += D[L.ch_idx[c]];
+  for (int c = L.ci_ptr[K]; c < L.ci_ptr[K + 1]; ++c) d += T(2) * Lv[L.ci_idx[c]];
+  D1[K] = d;
+  rD1[K] = T(1) / d;
+}
+
+// coarse face coefficient: sum of the fine faces between the two aggregates
+template <typename T>
+__global__ void k_amg_faces(int nf1, AmgLev L, const T* Lv, T* L1) {
+  int F = blockIdx.x * blockDim.x + threadIdx.x;
+  if (F >= nf1) return;
+  T s = T(0);
+  for (int c = L.cf_ptr[F]; c < L.cf_ptr[F + 1]; ++c) s += Lv[L.cf_idx[c]];
+  L1[F] = s;
+}
+
+// dense inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), one block
+template <typename T>
+__global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, const T* Lv, double* A) {
+  const int n = L.n;
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[i * n + i] = (double)D[i];
+  for (int f = threadIdx.x; f < L.nf; f += blockDim.x) {
+    const int2 o = L.on[f];
+    A[o.x * n + o.y] = (double)Lv[f];
+    A[o.y * n + o.x] = (double)Lv[f];
+  }
+  __syncthreads();
+  __shared__ double col[kAmgCoarsest];
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) piv = 1.0 / A[k * n + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = (i == k) ? 0.0 : A[i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] = (j == k ? 1.0 : A[k * n + j]) * piv;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, j = t - i * n;
+      if (i == k) continue;
+      const double a = (j == k) ? 0.0 : A[i * n + j];
+      A[i * n + j] = a - col[i] * A[k * n + j];
+    }
+    __syncthreads();
+  }
+}
+
+// y_i = (A x)_i on level 0 (sliced ELL) or a coarser level (face CSR); x given
+// by a functor so that smoothed / prolongated values can be formed on the fly
+template <typename T, bool FINE, class XF>
+__device__ __forceinline__ T amg_row(const Mat<T>& A, const AmgLev& L, const T* D, const T* Lv, int i,
+                                     XF x) {
+  if (FINE) {
+    T y = __ldg(A.D + i) * x(i);
+    if (A.E.W == 4) {
+      const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      T a[4];
+      Vec4Load<T>::get(A.val, i, a);
+      y += a[0] * x(j4.x);
+      y += a[1] * x(j4.y);
+      y += a[2] * x(j4.z);
+      y += a[3] * x(j4.w);
+      return y;
+    }
+    int base, step, w;
+    ell_row(A.E, i, base, step, w);
+    for (int k = 0; k < w; ++k) y += __ldg(A.val + base + step * k) * x(__ldg(A.E.col + base + step * k));
+    return y;
+  }
+  T y = D[i] * x(i);
+  for (int e = L.cptr[i]; e < L.cptr[i + 1]; ++e) {
+    const int ent = L.cent[e];
+    const int2 o = L.on[ent >> 1];
+    y += Lv[ent >> 1] * x((ent & 1) ? o.x : o.y);
+  }
+  return y;
+}
+
+// pre-smoothing from zero, two sweeps: x1 = w rD r, y = x1 + w rD (r - A x1)
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
+                                                 const T* r, T* y, const int* done) {
+  if (*done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  const T w = (T)kAmgOmega;
+  auto x1 = [&](int j) { return w * rD[j] * r[j]; };
+  y[i] = x1(i) + w * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, x1));
+}
+
+// restriction of the residual after pre-smoothing: rc_K = sum over the cells of K of (r - A y)
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, Mat<T> A, const T* D, const T* Lv,
+                                                      const T* r, const T* y, T* rc, const int* done) {
+  if (*done) return;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= n1) return;
+  auto xy = [&](int j) { return y[j]; };
+  T s = T(0);
+  for (int c = L.ch_ptr[K]; c < L.ch_ptr[K + 1]; ++c) {
+    const int i = L.ch_idx[c];
+    s += r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xy);
+  }
+  rc[K] = s;
+}
+
+// coarse correction and the first post-smoothing sweep: z = y + s P xc (formed
+// on the fly), out = z + w rD (r - A z)
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
+                                                   const T* r, const T* y, const T* xc, T* out,
+                                                   const int* done) {
+  if (*done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  const T w = (T)kAmgOmega, sc = (T)kAmgScale;
+  auto z = [&](int j) { return y[j] + sc * xc[L.agg[j]]; };
+  out[i] = z(i) + w * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, z));
+}
+
+// second post-smoothing sweep: v = u + w rD (r - A u).  On level 0 of a CG
+// iteration it also forms r.z: the last block sets beta (first = 1: rz only).
+template <typename T, bool FINE, bool DOT>
+__global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
+                                                   const T* r, const T* u, T* v, KWork w, int first) {
+  if (w.st[0].done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const T om = (T)kAmgOmega;
+  DotAcc<T> rz;
+  if (i < L.n) {
+    auto xu = [&](int j) { return u[j]; };
+    const T vi = u[i] + om * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xu));
+    v[i] = vi;
+    if (DOT) rz.add(r[i], vi);
+  }
+  if (!DOT) return;
+  double tv[1] = {rz.get()}, tot[1];
+  if (!grid_sum<1>(w, tv, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  if (first) {
+    s.beta = 0.0;
+  } else {
+    s.beta = tot[0] / s.rz;
+  }
+  s.rz = tot[0];
+}
+
+// r.z and beta when the hierarchy has a single level (no smoothing kernel to fuse it into)
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_apcg_rz(int nc, const T* r, const T* z, KWork w, int first) {
+  if (w.st[0].done) return;
+  DotAcc<T> rz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) rz.add(r[i], z[i]);
+  double v[1] = {rz.get()}, tot[1];
+  if (!grid_sum<1>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.beta = first ? 0.0 : tot[0] / s.rz;
+  s.rz = tot[0];
+}
+
+// coarsest level: x = A^{-1} r (dense inverse, one block)
+template <typename T>
+__global__ void __launch_bounds__(256) k_amg_coarse(int n, const double* Ainv, const T* r, T* x, const int* done) {
+  if (*done) return;
+  __shared__ double rs[kAmgCoarsest];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (double)r[j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += Ainv[i * n + j] * rs[j];
+    x[i] = (T)s;
+  }
+}
+
+// --------------------------------------------------------------- CG kernels
+// r = b - A x; bb, rr; convergence at the start; `gate` (may be null): when
+// *gate != 0 the solve is closed at once (the outer refinement loop is done)
+template <typename T, int MW>
+__global__ void __launch_bounds__(kKB) k_apcg_init(Topo t, Mat<T> A, const T* b, T* x, T* r, KWork w,
+                                                   const int* gate, int zero_x) {
+  const int nc = t.nc;
+  DotAcc<T> bb, rr;
+  const bool skip = gate && *gate;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    if (skip) break;
+    if (zero_x) x[i] = T(0);
+    T ax[1];
+    if (zero_x) ax[0] = T(0);
+    else spmv_row<T, 1, MW>(t, A, i, x, ax, 1u);
+    const T bi = b[i], ri = bi - ax[0];
+    r[i] = ri;
+    bb.add(bi, bi);
+    rr.add(ri, ri);
+  }
+  double v[2] = {bb.get(), rr.get()}, tot[2];
+  if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.bb = tot[0];
+  s.rr = tot[1];
+  s.res0 = sqrt(s.rr);
+  s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+  s.iters = 0;
+  s.status = DIFVM_OK;
+  s.zero_rhs = s.bb == 0.0;
+  s.done = skip || s.zero_rhs || s.rr <= s.tol2;
+  if (!skip && !isfinite(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
+}
+
+template <typename T>
+__global__ void k_apcg_zero(int nc, T* x, KWork w) {
+  if (!w.st[0].zero_rhs) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x[i] = T(0);
+}
+
+// p = z + beta p (first: p = z)
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_apcg_p(int nc, const T* z, T* p, KWork w, int first) {
+  if (w.st[0].done) return;
+  const T be = (T)w.st[0].beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : z[i] + be * p[i];
+}
+
+// x += alpha p; r -= alpha q; rr and the convergence test
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_apcg_update(int nc, const T* p, const T* q, T* x, T* r, KWork w) {
+  if (w.st[0].done) return;
+  const T al = (T)w.st[0].alpha;
+  DotAcc<T> rr;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    const T ri = r[i] - al * q[i];
+    r[i] = ri;
+    rr.add(ri, ri);
+  }
+  double v[1] = {rr.get()}, tot[1];
+  if (!grid_sum<1>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.iters += 1;
+  s.rr = tot[0];
+  if (!isfinite(s.rr) || !isfinite(s.alpha)) { s.done = 1; s.status = DIFVM_ENONFINITE; return; }
+  if (s.rr <= s.tol2) { s.done = 1; return; }
+  if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; }
+}
+
+// ------------------------------------------------------------ host drivers
+template <typename T>
+struct AmgRun {
+  difvm_mesh* m;
+  const AmgHier* H;
+  Topo t;
+  Mat<T> A;
+  char* ws;
+  AmgLayout Ly;
+  int G;
+  int MW;
+  T* vec(int k) const { return (T*)(ws + Ly.vec[k]); }
+  T* at(size_t off) const { return (T*)(ws + off); }
+};
+
+// coarse operators of every level from the level-0 matrix (D, L symmetric)
+template <typename T>
+static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cudaStream_t st) {
+  const AmgHier* H = R.H;
+  k_amg_rd<T><<<blocks_for(R.m->nc, kAB), kAB, 0, st>>>(R.m->nc, D0, R.at(R.Ly.rD[0]));
+  DIFVM_TRY(check_launch("amg_rd"));
+  const T* D = D0;
+  const T* Lv = L0;
+  for (int l = 0; l + 1 < H->nlev; ++l) {
+    const AmgLev& L = H->lev[l];
+    const AmgLev& L1 = H->lev[l + 1];
+    T *D1 = R.at(R.Ly.D[l + 1]), *rD1 = R.at(R.Ly.rD[l + 1]), *Lv1 = R.at(R.Ly.L[l + 1]);
+    k_amg_diag<T><<<blocks_for(L1.n, kAB), kAB, 0, st>>>(L1.n, L, D, Lv, D1, rD1);
+    if (L1.nf > 0) k_amg_faces<T><<<blocks_for(L1.nf, kAB), kAB, 0, st>>>(L1.nf, L, Lv, Lv1);
+    DIFVM_TRY(check_launch("amg_coarse_ops"));
+    D = D1;
+    Lv = Lv1;
+  }
+  const AmgLev& Lc = H->lev[H->nlev - 1];
+  if (Lc.n > kAmgCoarsest) return set_error(DIFVM_EINVAL, "AMG: coarsest level has %d cells", Lc.n);
+  k_amg_dense_inv<T><<<1, 1024, 0, st>>>(Lc, D, Lv, (double*)(R.ws + R.Ly.inv));
+  return check_launch("amg_dense_inv");
+}
+
+// z = V-cycle(r) on level l; level 0 ends with the r.z reduction of the CG
+template <typename T>
+static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWork& w, int first,
+                       cudaStream_t s) {
+  const AmgHier* H = R.H;
+  const AmgLev& L = H->lev[l];
+  const int* done = &w.st[0].done;
+  const bool fine = l == 0;
+  const T* D = fine ? R.A.D : R.at(R.Ly.D[l]);
+  const T* rD = R.at(R.Ly.rD[l]);
+  const T* Lv = fine ? nullptr : R.at(R.Ly.L[l]);
+  if (l == H->nlev - 1) {
+    k_amg_coarse<T><<<1, 256, 0, s>>>(L.n, (const double*)(R.ws + R.Ly.inv), r, out, done);
+    count_launch();
+    if (l == 0) {   // a single level: the CG's r.z reduction runs on its own
+      k_apcg_rz<T><<<R.G, kKB, 0, s>>>(L.n, r, out, w, first);
+      count_launch();
+    }
+    return;
+  }
+  const unsigned B = blocks_for(L.n, kAB);
+  T *y = R.at(R.Ly.a[l]), *u = R.at(R.Ly.b[l]);
+  const AmgLev& L1 = H->lev[l + 1];
+  T* rc = R.at(R.Ly.r[l + 1]);
+  T* xc = R.at(R.Ly.a[l + 1]);   // written by the next level's last sweep
+  if (fine) {
+    k_amg_pre<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
+    k_amg_restrict<T, true><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, R.A, D, Lv, r, y, rc, done);
+  } else {
+    k_amg_pre<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
+    k_amg_restrict<T, false><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, R.A, D, Lv, r, y, rc, done);
+  }
+  count_launch(); count_launch();
+  amg_vcycle(R, l + 1, rc, xc, w, first, s);
+  if (fine) {
+    k_amg_post1<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
+    k_amg_post2<T, true, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
+  } else {
+    k_amg_post1<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
+    k_amg_post2<T, false, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
+  }
+  count_launch(); count_launch();
+}
+
+// one AMG-preconditioned CG solve of A x = b (x is the initial guess unless
+// zero_x); state in w.st[0]; `gate` closes the solve at once when set
+template <typename T, int MW>
+static difvm_status amg_cg(const AmgRun<T>& R, const T* b, T* x, const KWork& w, const int* gate,
+                           int zero_x, int chunk, cudaStream_t st) {
+  const int nc = R.m->nc, G = R.G;
+  T *r = R.vec(0), *p = R.vec(1), *q = R.vec(2), *z = R.vec(3);
+  k_apcg_init<T, MW><<<G, kKB, 0, st>>>(R.t, R.A, b, x, r, w, gate, zero_x);
+  DIFVM_TRY(check_launch("apcg_init"));
+  k_apcg_zero<T><<<G, kKB, 0, st>>>(nc, x, w);
+  DIFVM_TRY(check_launch("apcg_zero"));
+  amg_vcycle(R, 0, r, z, w, 1, st);
+  k_apcg_p<T><<<G, kKB, 0, st>>>(nc, z, p, w, 1);
+  DIFVM_TRY(check_launch("apcg_p"));
+  auto iter = [&](cudaStream_t s) {
+    prof_before(DIFVM_PROF_PCG_SPMV, s);
+    k_pcg_spmv<T, 1, MW><<<G, kKB, 0, s>>>(R.t, R.A, p, q, w);
+    prof_after(DIFVM_PROF_PCG_SPMV, s);
+    k_apcg_update<T><<<G, kKB, 0, s>>>(nc, p, q, x, r, w);
+    amg_vcycle(R, 0, r, z, w, 0, s);
+    k_apcg_p<T><<<G, kKB, 0, s>>>(nc, z, p, w, 0);
+    count_launch(); count_launch(); count_launch();
+  };
+  int* counter = reinterpret_cast<int*>(w.ticket) + 1;
+  if (stream_capturing(st)) {
+    DIFVM_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    WhileLoop Lw;
+    DIFVM_TRY(while_open(st, Lw));
+    iter(Lw.side);
+    k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(w.st), kStateInts, 1, counter, w.maxit + 2, Lw.h);
+    difvm_status e = check_launch("loop_cond");
+    DIFVM_TRY(while_close(Lw));
+    return e;
+  }
+  KState hs;
+  for (int it = 0; it < w.maxit + chunk; it += chunk) {
+    for (int k = 0; k < chunk; ++k) iter(st);
+    DIFVM_TRY(check_error("apcg_iter"));
+    DIFVM_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    DIFVM_CUDA(cudaStreamSynchronize(st));
+    if (hs.done) break;
+  }
+  return DIFVM_OK;
+}
+
+__global__ void k_amg_info(const KState* st, difvm_solve_info* info, int refinements, int iters) {
+  if (threadIdx.x != 0) return;
+  difvm_solve_info o;
+  o.iters = iters >= 0 ? iters : st->iters;
+  o.refinements = refinements;
+  o.status = st->status;
+  o.pad = 0;
+  o.res0 = st->res0;
+  o.res = sqrt(st->rr);
+  o.bnorm = sqrt(st->bb);
+  *info = o;
+}
+
+template <typename T>
+static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws, size_t wsbytes,
+                                AmgRun<T>& R, cudaStream_t st) {
+  AmgHier* H = nullptr;
+  DIFVM_TRY(amg_hier(m, &H));
+  R.m = m;
+  R.H = H;
+  R.t = m->topo();
+  R.ws = (char*)ws;
+  R.Ly = amg_layout(m, H, sizeof(T));
+  if (!ws || wsbytes < R.Ly.total)
+    return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes, R.Ly.total);
+  R.G = amg_grid(m);
+  T* val = R.at(R.Ly.val);
+  if (m->ell_nslots > 0) {
+    k_ell_fill<T><<<blocks_for(m->ell_nslots, 256), 256, 0, st>>>((int)m->ell_nslots, m->ell_map, Lo, Lo, val);
+    DIFVM_TRY(check_launch("ell_fill"));
+  }
+  R.A = Mat<T>{D, m->ell(), val};
+  return amg_setup(R, D, Lo, st);
+}
+
+template <typename T>
+static KWork amg_work_t(const AmgRun<T>& R, int k, int maxit, double tol_rel, double tol_abs) {
+  KWork w;
+  w.st = (KState*)(R.ws + R.Ly.st) + k;
+  w.part = (double*)(R.ws + R.Ly.part);
+  w.ticket = (unsigned*)(R.ws + R.Ly.ticket);
+  w.maxit = maxit;
+  w.tol_rel = tol_rel;
+  w.tol_abs = tol_abs;
+  return w;
+}
+
+template <typename T, int MW>
+static difvm_status amg_solve_mw(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo,
+                                 const T* b, T* x, void* ws, size_t wsbytes, difvm_solve_info* info,
+                                 cudaStream_t st) {
+  AmgRun<T> R;
+  DIFVM_TRY(amg_prepare<T>(m, D, Lo, ws, wsbytes, R, st));
+  KWork w = amg_work_t(R, 0, o->max_iter > 0 ? o->max_iter : 1000, o->tol_rel, o->tol_abs);
+  DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
+  const int chunk = o->check_every > 0 ? o->check_every : 8;
+  DIFVM_TRY((amg_cg<T, MW>(R, b, x, w, nullptr, 0, chunk, st)));
+  if (info) {
+    k_amg_info<<<1, 32, 0, st>>>(w.st, info, 0, -1);
+    DIFVM_TRY(check_launch("amg_info"));
+  }
+  if (stream_capturing(st)) return DIFVM_OK;
+  KState hs;
+  DIFVM_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  DIFVM_CUDA(cudaStreamSynchronize(st));
+  return (difvm_status)hs.status;
+}
+
+template <typename T>
+difvm_status amg_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,
+                       T* x, void* ws, size_t wsbytes, difvm_solve_info* info, cudaStream_t st) {
+  if (m->ell_wmax <= 4) return amg_solve_mw<T, 4>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
+  if (m->ell_wmax <= 8) return amg_solve_mw<T, 8>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
+  return amg_solve_mw<T, 0>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
+}
+template difvm_status amg_solve<float>(difvm_mesh*, const difvm_solve_opts*, const float*, const float*,
+                                       const float*, float*, void*, size_t, difvm_solve_info*, cudaStream_t);
+template difvm_status amg_solve<double>(difvm_mesh*, const difvm_solve_opts*, const double*, const double*,
+                                        const double*, double*, void*, size_t, difvm_solve_info*,
+                                        cudaStream_t);
+
+// ------------------------------------------------- mixed precision refinement
+// Outer loop in FP64: r = b - A x (FP32 coefficients are exact in FP64); stop
+// when ||r|| <= max(tol_rel ||b||, tol_abs) or after refine_max sweeps; else
+// solve A e = r with the FP32 AMG-preconditioned CG to inner_tol and add e to x.
+__global__ void __launch_bounds__(kKB) k_ref_residual(Topo t, Mat<float> A, const double* b64,
+                                                      const double* x64, float* r32, KWork w,
+                                                      int refine_max) {
+  const int nc = t.nc;
+  double bb = 0.0, rr = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    double ax = (double)A.D[i] * x64[i];
+    if (A.E.W == 4) {
+      const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      const float4 a4 = __ldg(reinterpret_cast<const float4*>(A.val) + i);
+      ax += (double)a4.x * x64[j4.x];
+      ax += (double)a4.y * x64[j4.y];
+      ax += (double)a4.z * x64[j4.z];
+      ax += (double)a4.w * x64[j4.w];
+    } else {
+      int base, step, wd;
+      ell_row(A.E, i, base, step, wd);
+      for (int k = 0; k < wd; ++k) ax += (double)A.val[base + step * k] * x64[A.E.col[base + step * k]];
+    }
+    const double ri = b64[i] - ax;
+    r32[i] = (float)ri;
+    bb += b64[i] * b64[i];
+    rr += ri * ri;
+  }
+  double v[2] = {bb, rr}, tot[2];
+  if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  if (s.done) return;
+  if (s.iters == 0) {   // first sweep
+    s.bb = tot[0];
+    s.res0 = sqrt(tot[1]);
+    s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+    s.status = DIFVM_OK;
+    s.rho = tot[1];
+    if (s.bb == 0.0) { s.zero_rhs = 1; s.rr = 0.0; s.done = 1; return; }
+  } else if (tot[1] > s.rho / 16.0) {   // a sweep must cut the residual by 4x
+    s.rr = tot[1];
+    s.done = 1;
+    s.status = DIFVM_ENOTCONV;
+    return;
+  }
+  s.rho = tot[1];
+  s.rr = tot[1];
+  if (!isfinite(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; return; }
+  if (s.rr <= s.tol2) { s.done = 1; return; }
+  if (s.iters >= refine_max) { s.done = 1; s.status = DIFVM_ENOTCONV; return; }
+  s.iters += 1;
+}
+
+// x += e after an inner solve; nothing when this sweep's residual closed the
+// loop (the inner solve was skipped); x = 0 for a zero right-hand side
+__global__ void k_ref_add(int nc, const float* e, double* x64, const KState* outer, const KState* inner,
+                          int* total_iters) {
+  if (outer->zero_rhs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x64[i] = 0.0;
+    return;
+  }
+  if (outer->done) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x64[i] += (double)e[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *total_iters += inner->iters;
+}
+
+__global__ void k_amg_ref_info(const KState* outer, const int* total, difvm_solve_info* info) {
+  if (threadIdx.x != 0) return;
+  difvm_solve_info o;
+  o.iters = *total;
+  o.refinements = outer->iters;
+  o.status = outer->status;
+  o.pad = 0;
+  o.res0 = outer->res0;
+  o.res = sqrt(outer->rr);
+  o.bnorm = sqrt(outer->bb);
+  *info = o;
+}
+
+template <int MW>
+static difvm_status amg_refine_mw(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
+                                  const double* b64, double* x64, void* ws, size_t wsbytes,
+                                  difvm_solve_info* info, cudaStream_t st) {
+  AmgRun<float> R;
+  DIFVM_TRY(amg_prepare<float>(m, D, Lo, ws, wsbytes, R, st));
+  const int refine_max = o->refine_max > 0 ? o->refine_max : 20;
+  const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+  KWork wo = amg_work_t(R, 1, refine_max, o->tol_rel, o->tol_abs);           // outer
+  KWork wi = amg_work_t(R, 0, o->max_iter > 0 ? o->max_iter : 1000, inner_tol, 0.0);  // inner
+  float* r32 = (float*)(R.ws + R.Ly.rhs32);
+  float* e32 = (float*)(R.ws + R.Ly.e32);
+  int* total = reinterpret_cast<int*>(wo.ticket) + 2;
+  int* ocounter = reinterpret_cast<int*>(wo.ticket) + 3;
+  DIFVM_CUDA(cudaMemsetAsync(wo.ticket, 0, 16, st));
+  DIFVM_CUDA(cudaMemsetAsync(wo.st, 0, sizeof(KState), st));
+  const int chunk = o->check_every > 0 ? o->check_every : 8;
+  KState* outer = wo.st;
+  auto sweep = [&](cudaStream_t s) -> difvm_status {
+    k_ref_residual<<<R.G, kKB, 0, s>>>(R.t, R.A, b64, x64, r32, wo, refine_max);
+    DIFVM_TRY(check_launch("ref_residual"));
+    DIFVM_TRY((amg_cg<float, MW>(R, r32, e32, wi, &outer->done, 1, chunk, s)));
+    k_ref_add<<<R.G, kKB, 0, s>>>(m->nc, e32, x64, outer, wi.st, total);
+    return check_launch("ref_add");
+  };
+  if (stream_capturing(st)) {
+    DIFVM_CUDA(cudaMemsetAsync(ocounter, 0, sizeof(int), st));
+    WhileLoop Lw;
+    DIFVM_TRY(while_open(st, Lw));
+    difvm_status e = sweep(Lw.side);
+    if (e == DIFVM_OK) {
+      k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(wo.st), kStateInts, 1, ocounter, refine_max + 2, Lw.h);
+      e = check_launch("loop_cond");
+    }
+    DIFVM_TRY(while_close(Lw));
+    DIFVM_TRY(e);
+  } else {
+    KState hs;
+    for (int k = 0; k <= refine_max; ++k) {
+      DIFVM_TRY(sweep(st));
+      DIFVM_CUDA(cudaMemcpyAsync(&hs, outer, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      DIFVM_CUDA(cudaStreamSynchronize(st));
+      if (hs.done) break;
+    }
+  }
+  if (info) {
+    k_amg_ref_info<<<1, 32, 0, st>>>(outer, total, info);
+    DIFVM_TRY(check_launch("amg_ref_info"));
+  }
+  if (stream_capturing(st)) return DIFVM_OK;
+  KState hs;
+  DIFVM_CUDA(cudaMemcpyAsync(&hs, outer, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  DIFVM_CUDA(cudaStreamSynchronize(st));
+  int s = hs.status;
+  if (s == DIFVM_OK && !hs.done) s = DIFVM_ENOTCONV;
+  return (difvm_status)s;
+}
+
+difvm_status amg_refine(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
+                        const double* b64, double* x64, void* ws, size_t wsbytes, difvm_solve_info* info,
+                        cudaStream_t st) {
+  if (m->ell_wmax <= 4) return amg_refine_mw<4>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
+  if (m->ell_wmax <= 8) return amg_refine_mw<8>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
+  return amg_refine_mw<0>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
+}
+
+}  // namespace difvm

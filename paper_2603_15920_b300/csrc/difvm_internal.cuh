@@ -109,6 +109,8 @@ __device__ __forceinline__ int face_kind(const Topo& t, int b, int cls) {
 }
 
 struct difvm_mesh_impl;
+struct AmgHier;
+void amg_free(AmgHier* h);
 }  // namespace difvm
 
 // The opaque handle of the C ABI.
@@ -150,6 +152,7 @@ struct difvm_mesh {
   int* seg_cb0 = nullptr;    // [ncases + 1]
   int* seg_cs = nullptr;     // [ncases + 1] first cell of each case
   std::vector<int32_t> bown_host;  // boundary-face owners, internal numbering
+  difvm::AmgHier* amg = nullptr;   // multigrid hierarchy, built on first use
 
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
@@ -187,6 +190,16 @@ __global__ void k_loop_cond(const int* done_flags, int stride_ints, int n, int* 
                             cudaGraphConditionalHandle h);
 // iterations per loop-body execution when a solve runs inside a graph
 constexpr int kGraphUnroll = 4;
+
+// ------------------------------------- multigrid-preconditioned CG (amg.cu)
+difvm_status amg_hier(difvm_mesh* m, AmgHier** out);
+size_t amg_workspace_bytes(difvm_mesh* m, size_t elt);
+template <typename T>
+difvm_status amg_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,
+                       T* x, void* ws, size_t wsbytes, difvm_solve_info* info, cudaStream_t st);
+difvm_status amg_refine(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
+                        const double* b64, double* x64, void* ws, size_t wsbytes, difvm_solve_info* info,
+                        cudaStream_t st);
 difvm_status check_mesh(const difvm_mesh* m);
 difvm_status check_prec(difvm_prec p);
 

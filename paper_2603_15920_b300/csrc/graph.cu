@@ -6,8 +6,6 @@
 // WHILE node: its body graph holds a few iterations plus a one-thread kernel
 // that sets the loop condition from the device-side solver state.  The whole
 // PISO step then runs as one graph launch with no host round trip.
-#include <mutex>
-
 #include "difvm_internal.cuh"
 
 namespace difvm {
@@ -17,21 +15,23 @@ bool stream_capturing(cudaStream_t st) {
   return cudaStreamIsCapturing(st, &s) == cudaSuccess && s == cudaStreamCaptureStatusActive;
 }
 
-// one non-blocking stream per device, used only to capture loop bodies
-static std::mutex g_side_mu;
-static cudaStream_t g_side[64] = {nullptr};
+// sets a loop's condition to 1 just before the loop node runs
+__global__ void k_loop_start(cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
+}
 
-static difvm_status side_stream(cudaStream_t* out) {
+// Non-blocking streams used only to capture loop bodies: one per device and
+// nesting depth (a loop inside a loop body captures on the next one), per host
+// thread, so concurrent captures on different threads never share one.
+constexpr int kMaxLoopDepth = 4;
+static thread_local cudaStream_t t_side[64][kMaxLoopDepth] = {};
+static thread_local int t_depth = 0;
+
+difvm_status while_open(cudaStream_t st, WhileLoop& L) {
   int dev = 0;
   DIFVM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_error(DIFVM_EINVAL, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lk(g_side_mu);
-  if (!g_side[dev]) DIFVM_CUDA(cudaStreamCreateWithFlags(&g_side[dev], cudaStreamNonBlocking));
-  *out = g_side[dev];
-  return DIFVM_OK;
-}
-
-difvm_status while_open(cudaStream_t st, WhileLoop& L) {
+  if (t_depth >= kMaxLoopDepth) return set_error(DIFVM_EINVAL, "device loops nested too deeply");
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -39,6 +39,12 @@ difvm_status while_open(cudaStream_t st, WhileLoop& L) {
   DIFVM_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
   if (cs != cudaStreamCaptureStatusActive) return set_error(DIFVM_EINVAL, "stream is not capturing");
   DIFVM_CUDA(cudaGraphConditionalHandleCreate(&L.h, g, 1u, cudaGraphCondAssignDefault));
+  // The default value is applied when the top-level graph is launched, not each
+  // time a loop nested in another loop's body starts: set it from the graph
+  // itself, with a kernel that runs just before the loop node.
+  k_loop_start<<<1, 32, 0, st>>>(L.h);
+  DIFVM_TRY(check_error("loop_start"));
+  DIFVM_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
   cudaGraphNodeParams np = {};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = L.h;
@@ -48,14 +54,12 @@ difvm_status while_open(cudaStream_t st, WhileLoop& L) {
   DIFVM_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
   L.body = np.conditional.phGraph_out[0];
   DIFVM_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-  DIFVM_TRY(side_stream(&L.side));
-  g_side_mu.lock();   // one body capture at a time on the side stream
-  cudaError_t e = cudaStreamBeginCaptureToGraph(L.side, L.body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) {
-    g_side_mu.unlock();
-    return set_error(DIFVM_ECUDA, "capture of a loop body: %s", cudaGetErrorString(e));
-  }
+  cudaStream_t& side = t_side[dev][t_depth];
+  if (!side) DIFVM_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  L.side = side;
+  DIFVM_CUDA(cudaStreamBeginCaptureToGraph(L.side, L.body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+  ++t_depth;
   L.open = true;
   return DIFVM_OK;
 }
@@ -65,7 +69,7 @@ difvm_status while_close(WhileLoop& L) {
   cudaGraph_t g = L.body;
   cudaError_t e = cudaStreamEndCapture(L.side, &g);
   L.open = false;
-  g_side_mu.unlock();
+  --t_depth;
   if (e != cudaSuccess) return set_error(DIFVM_ECUDA, "end of a loop-body capture: %s", cudaGetErrorString(e));
   return DIFVM_OK;
 }

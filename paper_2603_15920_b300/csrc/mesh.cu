@@ -205,6 +205,7 @@ static void free_mesh(difvm_mesh* m) {
   cudaSetDevice(m->device);
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  amg_free(m->amg);
   if (cur >= 0) cudaSetDevice(cur);
   delete m;
 }

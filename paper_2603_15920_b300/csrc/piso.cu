@@ -1138,6 +1138,10 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     return set_error(DIFVM_EINVAL, "bad momentum solver");
   if (o->solve_p.method != DIFVM_PCG && o->solve_p.method != DIFVM_BICGSTAB)
     return set_error(DIFVM_EINVAL, "bad pressure solver");
+  if (o->solve_U.precond == DIFVM_PRECOND_AMG)
+    return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves the pressure CG only");
+  if (o->solve_p.precond == DIFVM_PRECOND_AMG && (o->solve_p.method != DIFVM_PCG || m->seg))
+    return set_error(DIFVM_EINVAL, "the multigrid preconditioner needs CG on a single (not batched) mesh");
   for (int k = 0; k < o->n_out; ++k) {
     int p = o->wk_patch[k];
     if (p < 0 || p >= m->npatch || m->patch_type[p] != DIFVM_PATCH_OUTLET)
@@ -1196,15 +1200,11 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
             alloc(&h->rhs, 3 * nc * e) && alloc(&h->rAU, nc * e) && alloc(&h->HbyA, 3 * nc * e) &&
             alloc(&h->Dp, nc * e) && alloc(&h->Lp, ni * e) && alloc(&h->bp, nc * e) &&
             alloc(&h->phiHbyA, nf * e) && alloc(&h->af, nf * e) && alloc(&h->nonorth, ni * e);
-  h->wsU_bytes = difvm_krylov_workspace_bytes(m, prec, o->solve_U.method, 3);
-  ok = ok && alloc(&h->wsU, h->wsU_bytes);
-  if (h->mixed) {
-    h->wsp_bytes = difvm_krylov_refine_workspace_bytes(m, o->solve_p.method, 1);
-    ok = ok && alloc((void**)&h->p64, nc * 8) && alloc((void**)&h->b64, nc * 8);
-  } else {
-    h->wsp_bytes = difvm_krylov_workspace_bytes(m, prec, o->solve_p.method, 1);
-  }
-  ok = ok && alloc(&h->wsp, h->wsp_bytes);
+  h->wsU_bytes = difvm_krylov_opts_workspace_bytes(m, prec, &o->solve_U, 3);
+  ok = ok && h->wsU_bytes > 0 && alloc(&h->wsU, h->wsU_bytes);
+  h->wsp_bytes = difvm_krylov_opts_workspace_bytes(m, prec, &o->solve_p, 1);
+  if (h->mixed) ok = ok && alloc((void**)&h->p64, nc * 8) && alloc((void**)&h->b64, nc * 8);
+  ok = ok && h->wsp_bytes > 0 && alloc(&h->wsp, h->wsp_bytes);
   // solve infos [7 nk + 1] + Q[16] + p_out[16] + outlet table (start[16], size[16])
   const size_t ninfo = 7 * (size_t)h->nk + 1;
   ok = ok && alloc((void**)&h->sinfo, ninfo * sizeof(difvm_solve_info) + 32 * sizeof(double) + 32 * sizeof(int));

@@ -26,7 +26,7 @@ BC_VELOCITY, BC_PRESSURE, BC_ALL_FIXED, BC_ALL_ZEROGRAD = 0, 1, 2, 3
 DIV_UPWIND, DIV_LINEAR = 0, 1
 WK_EXACT, WK_FE, WK_BE = 0, 1, 2
 PCG, BICGSTAB = 0, 1
-PRECOND_NONE, PRECOND_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_AMG = 0, 1, 2
 RENUMBER_RCM, SORT_FACES = 1, 2
 NONORTH_MOMENTUM, NONORTH_PRESSURE, NONORTH_ALL = 1, 2, 3
 
@@ -101,6 +101,7 @@ _SIGS = {
     "difvm_windkessel_update_bwd": [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp,
                                     _vp, _vp, _vp],
     "difvm_krylov_refine_workspace_bytes": [_vp, _i, _i],
+    "difvm_krylov_opts_workspace_bytes": [_vp, _i, _vp, _i],
     "difvm_piso_create": [_vp, _i, _vp, _vp],
     "difvm_piso_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "difvm_piso_step_record": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp],
@@ -137,7 +138,8 @@ def lib():
         L.difvm_launch_count.restype = C.c_uint64
         L.difvm_mesh_destroy.argtypes = [_vp]
         L.difvm_mesh_destroy.restype = None
-        for nm in ("difvm_krylov_workspace_bytes", "difvm_krylov_refine_workspace_bytes"):
+        for nm in ("difvm_krylov_workspace_bytes", "difvm_krylov_refine_workspace_bytes",
+                   "difvm_krylov_opts_workspace_bytes"):
             if hasattr(L, nm):
                 getattr(L, nm).restype = C.c_size_t
         if hasattr(L, "difvm_piso_tape_bytes"):
@@ -400,7 +402,7 @@ def difvm_krylov_solve(mesh, diag, lower, upper, b, x, opts=None, workspace=None
     opts = opts or solve_opts(**kw)
     nq = b.shape[0] if b.dim() == 2 else 1
     prec = _prec(b)
-    nbytes = difvm_krylov_workspace_bytes(mesh, prec, opts.method, nq)
+    nbytes = int(lib().difvm_krylov_opts_workspace_bytes(_mh(mesh), prec, C.byref(opts), nq))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=b.device)
     nk = getattr(mesh, "n_cases", 1) if getattr(mesh, "batched", False) else 1
@@ -417,7 +419,8 @@ def difvm_krylov_solve_refine(mesh, diag32, lower32, upper32, b64, x64, opts=Non
                               stream=None, **kw):
     opts = opts or solve_opts(**kw)
     nq = b64.shape[0] if b64.dim() == 2 else 1
-    nbytes = int(lib().difvm_krylov_refine_workspace_bytes(_mh(mesh), opts.method, nq))
+    nbytes = max(int(lib().difvm_krylov_opts_workspace_bytes(_mh(mesh), F32, C.byref(opts), nq)),
+                 int(lib().difvm_krylov_refine_workspace_bytes(_mh(mesh), opts.method, nq)))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=b64.device)
     info = _info_buf(nq, b64.device)
@@ -434,7 +437,7 @@ def difvm_krylov_solve_bwd(mesh, diag, lower, upper, x, x_bar, b_bar, diag_bar=N
     opts = opts or solve_opts(**kw)
     nq = x.shape[0] if x.dim() == 2 else 1
     prec = _prec(x)
-    nbytes = difvm_krylov_workspace_bytes(mesh, prec, opts.method, nq)
+    nbytes = int(lib().difvm_krylov_opts_workspace_bytes(_mh(mesh), prec, C.byref(opts), nq))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
     info = _info_buf(nq, x.device)
