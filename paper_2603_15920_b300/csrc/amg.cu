@@ -43,7 +43,8 @@ struct AmgLev {
   int n, nf;
   const int2* on;
   const int* cptr;
-  const int* cent;
+  const int* cent;                    // entries F<<1|side, ascending F per cell
+  const int* col;                     // [cptr[n]] neighbour cell of each entry (levels >= 1)
   const int* agg;                     // [n] cell -> next-level cell
   const int *ch_ptr, *ch_idx;         // next-level cell -> its cells
   const int *ci_ptr, *ci_idx;         // next-level cell -> faces inside it
@@ -178,8 +179,14 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
         cent[fill[g.on[f].x]++] = f << 1;
         cent[fill[g.on[f].y]++] = (f << 1) | 1;
       }
+      std::vector<int> col(cent.size());
+      for (size_t e = 0; e < cent.size(); ++e) {
+        const int2 o = g.on[cent[e] >> 1];
+        col[e] = (cent[e] & 1) ? o.x : o.y;
+      }
       DIFVM_TRY(upload_vec(H, &L.cptr, cptr));
       DIFVM_TRY(upload_vec(H, &L.cent, cent));
+      DIFVM_TRY(upload_vec(H, &L.col, col));
     }
     const bool last = g.n <= kAmgCoarsest || lvl + 1 >= kAmgMaxLevels;
     if (!last) {
@@ -247,8 +254,8 @@ difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
 // ---------------------------------------------------------- workspace layout
 // [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials | ticket]
 struct AmgLayout {
-  size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], r[kAmgMaxLevels],
-      a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, rhs32, e32, total;
+  size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], E[kAmgMaxLevels],
+      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, rhs32, e32, total;
 };
 
 static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
@@ -268,12 +275,13 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
     A.D[l] = take((size_t)L.n * e);
     A.rD[l] = take((size_t)L.n * e);
     A.L[l] = take((size_t)L.nf * e);
+    A.E[l] = take((size_t)(l > 0 ? 2 * L.nf : 1) * e);   // row-entry values (levels >= 1)
     A.r[l] = take((size_t)L.n * e);
     A.a[l] = take((size_t)L.n * e);
     A.b[l] = take((size_t)L.n * e);
   }
   const int nco = H->lev[H->nlev - 1].n;
-  A.inv = take((size_t)nco * nco * sizeof(double));
+  A.inv = take((size_t)nco * nco * sizeof(float));
   A.st = take(4 * sizeof(KState));
   // partials: the CG kernels use amg_grid blocks, the fine-level smoothing one block per kAB cells
   const size_t nblk = std::max<size_t>(amg_grid(m), blocks_for(m->nc, kAB));
@@ -320,35 +328,57 @@ __global__ void k_amg_faces(int nf1, AmgLev L, const T* Lv, T* L1) {
   L1[F] = s;
 }
 
-// dense inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), one block
+// row-entry values of a coarse level from its face coefficients
 template <typename T>
-__global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, const T* Lv, double* A) {
+__global__ void k_amg_entries(int nnz, const int* cent, const T* Lv, T* E) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnz) E[e] = Lv[cent[e] >> 1];
+}
+
+// dense inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), one
+// block, in FP32 (the B300's FP64 rate is about 1/64 of FP32 and this runs on one
+// SM), then symmetrised; it serves only as the preconditioner's coarsest solve
+template <typename T>
+__global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, const T* Lv, float* A) {
   const int n = L.n;
-  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.0;
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.f;
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) A[i * n + i] = (double)D[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[i * n + i] = (float)D[i];
   for (int f = threadIdx.x; f < L.nf; f += blockDim.x) {
     const int2 o = L.on[f];
-    A[o.x * n + o.y] = (double)Lv[f];
-    A[o.y * n + o.x] = (double)Lv[f];
+    A[o.x * n + o.y] = (float)Lv[f];
+    A[o.y * n + o.x] = (float)Lv[f];
   }
   __syncthreads();
-  __shared__ double col[kAmgCoarsest];
-  __shared__ double piv;
+  __shared__ float col[kAmgCoarsest];
+  __shared__ float piv;
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) piv = 1.0 / A[k * n + k];
+    if (threadIdx.x == 0) piv = 1.f / A[k * n + k];
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = (i == k) ? 0.0 : A[i * n + k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = (i == k) ? 0.f : A[i * n + k];
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] = (j == k ? 1.0 : A[k * n + j]) * piv;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] = (j == k ? 1.f : A[k * n + j]) * piv;
     __syncthreads();
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const int i = t / n, j = t - i * n;
+    // rows i != k: A[i][j] -= col[i] A[k][j]; 32 x 32 threads tile the (i, j) plane
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < n; i += 32) {
       if (i == k) continue;
-      const double a = (j == k) ? 0.0 : A[i * n + j];
-      A[i * n + j] = a - col[i] * A[k * n + j];
+      const float ci = col[i];
+      for (int j = tx; j < n; j += 32) {
+        const float a = (j == k) ? 0.f : A[i * n + j];
+        A[i * n + j] = a - ci * A[k * n + j];
+      }
     }
     __syncthreads();
+  }
+  // symmetrise: the exact inverse is symmetric
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t - i * n;
+    if (i < j) {
+      const float v = 0.5f * (A[i * n + j] + A[j * n + i]);
+      A[i * n + j] = v;
+      A[j * n + i] = v;
+    }
   }
 }
 
@@ -375,11 +405,8 @@ __device__ __forceinline__ T amg_row(const Mat<T>& A, const AmgLev& L, const T* 
     return y;
   }
   T y = D[i] * x(i);
-  for (int e = L.cptr[i]; e < L.cptr[i + 1]; ++e) {
-    const int ent = L.cent[e];
-    const int2 o = L.on[ent >> 1];
-    y += Lv[ent >> 1] * x((ent & 1) ? o.x : o.y);
-  }
+  const int e1 = L.cptr[i + 1];
+  for (int e = L.cptr[i]; e < e1; ++e) y += Lv[e] * x(L.col[e]);   // Lv: row-entry values here
   return y;
 }
 
@@ -395,19 +422,25 @@ __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D,
   y[i] = x1(i) + w * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, x1));
 }
 
-// restriction of the residual after pre-smoothing: rc_K = sum over the cells of K of (r - A y)
+// residual after pre-smoothing: res = r - A y
 template <typename T, bool FINE>
-__global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, Mat<T> A, const T* D, const T* Lv,
-                                                      const T* r, const T* y, T* rc, const int* done) {
+__global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* D, const T* Lv, const T* r,
+                                                   const T* y, T* res, const int* done) {
+  if (*done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  auto xy = [&](int j) { return y[j]; };
+  res[i] = r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xy);
+}
+
+// restriction: rc_K = sum of res over the cells of K, in ascending cell order
+template <typename T>
+__global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T* res, T* rc, const int* done) {
   if (*done) return;
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= n1) return;
-  auto xy = [&](int j) { return y[j]; };
   T s = T(0);
-  for (int c = L.ch_ptr[K]; c < L.ch_ptr[K + 1]; ++c) {
-    const int i = L.ch_idx[c];
-    s += r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xy);
-  }
+  for (int c = L.ch_ptr[K]; c < L.ch_ptr[K + 1]; ++c) s += res[L.ch_idx[c]];
   rc[K] = s;
 }
 
@@ -467,13 +500,13 @@ __global__ void __launch_bounds__(kKB) k_apcg_rz(int nc, const T* r, const T* z,
 
 // coarsest level: x = A^{-1} r (dense inverse, one block)
 template <typename T>
-__global__ void __launch_bounds__(256) k_amg_coarse(int n, const double* Ainv, const T* r, T* x, const int* done) {
+__global__ void __launch_bounds__(256) k_amg_coarse(int n, const float* Ainv, const T* r, T* x, const int* done) {
   if (*done) return;
-  __shared__ double rs[kAmgCoarsest];
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (double)r[j];
+  __shared__ float rs[kAmgCoarsest];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (float)r[j];
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double s = 0.0;
+    float s = 0.f;
     for (int j = 0; j < n; ++j) s += Ainv[i * n + j] * rs[j];
     x[i] = (T)s;
   }
@@ -578,14 +611,18 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
     const AmgLev& L1 = H->lev[l + 1];
     T *D1 = R.at(R.Ly.D[l + 1]), *rD1 = R.at(R.Ly.rD[l + 1]), *Lv1 = R.at(R.Ly.L[l + 1]);
     k_amg_diag<T><<<blocks_for(L1.n, kAB), kAB, 0, st>>>(L1.n, L, D, Lv, D1, rD1);
-    if (L1.nf > 0) k_amg_faces<T><<<blocks_for(L1.nf, kAB), kAB, 0, st>>>(L1.nf, L, Lv, Lv1);
+    if (L1.nf > 0) {
+      k_amg_faces<T><<<blocks_for(L1.nf, kAB), kAB, 0, st>>>(L1.nf, L, Lv, Lv1);
+      k_amg_entries<T><<<blocks_for(2 * L1.nf, kAB), kAB, 0, st>>>(2 * L1.nf, L1.cent, Lv1,
+                                                                 R.at(R.Ly.E[l + 1]));
+    }
     DIFVM_TRY(check_launch("amg_coarse_ops"));
     D = D1;
     Lv = Lv1;
   }
   const AmgLev& Lc = H->lev[H->nlev - 1];
   if (Lc.n > kAmgCoarsest) return set_error(DIFVM_EINVAL, "AMG: coarsest level has %d cells", Lc.n);
-  k_amg_dense_inv<T><<<1, 1024, 0, st>>>(Lc, D, Lv, (double*)(R.ws + R.Ly.inv));
+  k_amg_dense_inv<T><<<1, 1024, 0, st>>>(Lc, D, Lv, (float*)(R.ws + R.Ly.inv));
   return check_launch("amg_dense_inv");
 }
 
@@ -599,9 +636,9 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const bool fine = l == 0;
   const T* D = fine ? R.A.D : R.at(R.Ly.D[l]);
   const T* rD = R.at(R.Ly.rD[l]);
-  const T* Lv = fine ? nullptr : R.at(R.Ly.L[l]);
+  const T* Lv = fine ? nullptr : R.at(R.Ly.E[l]);   // row-entry values of a coarse level
   if (l == H->nlev - 1) {
-    k_amg_coarse<T><<<1, 256, 0, s>>>(L.n, (const double*)(R.ws + R.Ly.inv), r, out, done);
+    k_amg_coarse<T><<<1, 256, 0, s>>>(L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
     count_launch();
     if (l == 0) {   // a single level: the CG's r.z reduction runs on its own
       k_apcg_rz<T><<<R.G, kKB, 0, s>>>(L.n, r, out, w, first);
@@ -616,12 +653,13 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   T* xc = R.at(R.Ly.a[l + 1]);   // written by the next level's last sweep
   if (fine) {
     k_amg_pre<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
-    k_amg_restrict<T, true><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, R.A, D, Lv, r, y, rc, done);
+    k_amg_resid<T, true><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
   } else {
     k_amg_pre<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
-    k_amg_restrict<T, false><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, R.A, D, Lv, r, y, rc, done);
+    k_amg_resid<T, false><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
   }
-  count_launch(); count_launch();
+  k_amg_restrict<T><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, u, rc, done);
+  count_launch(); count_launch(); count_launch();
   amg_vcycle(R, l + 1, rc, xc, w, first, s);
   if (fine) {
     k_amg_post1<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
