@@ -142,7 +142,8 @@ uint64_t difvm_launch_count(void);
  * difvm_prof_stop synchronises on the recorded events and returns the summed
  * kernel time and the number of timed launches.  Process-wide, one tag at a
  * time, not thread-safe; start/stop allocate and free the events. */
-enum { DIFVM_PROF_PCG_SPMV = 1, DIFVM_PROF_PCG_UPDATE = 2, DIFVM_PROF_PCG_PUPDATE = 3 };
+enum { DIFVM_PROF_PCG_SPMV = 1, DIFVM_PROF_PCG_UPDATE = 2, DIFVM_PROF_PCG_PUPDATE = 3,
+       DIFVM_PROF_AMG_RESID = 4 /* fine-level multigrid residual r - A y */ };
 difvm_status difvm_prof_start(int tag, int max_launches);
 difvm_status difvm_prof_stop(double* total_ms, int64_t* launches);
 
@@ -276,8 +277,11 @@ size_t difvm_krylov_refine_workspace_bytes(difvm_mesh_t, int method, int ncomp);
  * FP32 to opts->inner_tol (relative, 0 = 1e-4) and adds e to x64 in FP64, until
  * ||r||_2 <= max(tol_rel ||b||_2, tol_abs) or refine_max sweeps (0 = 20); a
  * sweep that fails to cut the residual by 4x stops with ENOTCONV.
- * info.iters = total inner iterations, info.refinements = sweeps.  EINVAL on
- * batched meshes. */
+ * info.iters = total inner iterations, info.refinements = sweeps.  With
+ * DIFVM_PRECOND_AMG the solve is instead one CG in FP64 (x, r, p, q, inner
+ * products; FP32 coefficients) preconditioned by the FP32 V-cycle: it reaches
+ * the FP64 tolerance without sweeps (refine_max and inner_tol are not used,
+ * info.refinements = 0).  EINVAL on batched meshes. */
 difvm_status difvm_krylov_solve_refine(difvm_mesh_t, const difvm_solve_opts* opts, const float* diag,
                                        const float* lower, const float* upper, const double* b64,
                                        double* x64, int ncomp, void* workspace,

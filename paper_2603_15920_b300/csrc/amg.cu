@@ -17,7 +17,8 @@
 //     faces between its two aggregates), each sum in a fixed order;
 //   V-cycle: two damped-Jacobi sweeps before and after the coarse correction,
 //     the coarse correction scaled by kAmgScale, the coarsest level solved
-//     with a dense inverse (Gauss-Jordan in one block, FP64).
+//     with a dense inverse (Gauss-Jordan in one block, FP32, symmetrised);
+//   mixed precision: CG in FP64 around the FP32 V-cycle (no refinement sweeps).
 //
 // The V-cycle is a fixed symmetric positive-definite linear operator, so CG
 // keeps its guarantees; it changes the iteration count, not the solution.
@@ -32,7 +33,7 @@ namespace difvm {
 
 constexpr double kAmgOmega = 0.7;   // Jacobi damping
 constexpr double kAmgScale = 1.8;   // over-correction of the coarse-grid correction
-constexpr int kAmgCoarsest = 256;   // coarsen until at most this many cells
+constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 x 32)
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAB = 256;            // threads per block of the AMG kernels
 
@@ -44,7 +45,12 @@ struct AmgLev {
   const int2* on;
   const int* cptr;
   const int* cent;                    // entries F<<1|side, ascending F per cell
-  const int* col;                     // [cptr[n]] neighbour cell of each entry (levels >= 1)
+  // levels >= 1: sliced ELL of the off-diagonal entries (slices of 32 rows,
+  // slot = soff[i/32] + 32 k + i%32, k in CSR order; padding: column i, face -1)
+  const int* soff;
+  const int* ecol;
+  const int* eface;
+  int nslots;
   const int* agg;                     // [n] cell -> next-level cell
   const int *ch_ptr, *ch_idx;         // next-level cell -> its cells
   const int *ci_ptr, *ci_idx;         // next-level cell -> faces inside it
@@ -179,14 +185,34 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
         cent[fill[g.on[f].x]++] = f << 1;
         cent[fill[g.on[f].y]++] = (f << 1) | 1;
       }
-      std::vector<int> col(cent.size());
-      for (size_t e = 0; e < cent.size(); ++e) {
-        const int2 o = g.on[cent[e] >> 1];
-        col[e] = (cent[e] & 1) ? o.x : o.y;
+      const int nsl = (g.n + 31) / 32;
+      std::vector<int> soff(nsl + 1, 0);
+      for (int sl = 0; sl < nsl; ++sl) {
+        int w = 0;
+        for (int i = 32 * sl; i < std::min(g.n, 32 * sl + 32); ++i) w = std::max(w, cptr[i + 1] - cptr[i]);
+        soff[sl + 1] = soff[sl] + 32 * w;
       }
+      std::vector<int> ecol(std::max(soff[nsl], 1)), eface(std::max(soff[nsl], 1), -1);
+      for (int i = 0; i < g.n; ++i) {
+        const int sl = i >> 5, w = (soff[sl + 1] - soff[sl]) / 32;
+        for (int k = 0; k < w; ++k) {
+          const int slot = soff[sl] + 32 * k + (i & 31);
+          const int e = cptr[i] + k;
+          if (e < cptr[i + 1]) {
+            const int2 o = g.on[cent[e] >> 1];
+            ecol[slot] = (cent[e] & 1) ? o.x : o.y;
+            eface[slot] = cent[e] >> 1;
+          } else {
+            ecol[slot] = i;
+          }
+        }
+      }
+      L.nslots = soff[nsl];
       DIFVM_TRY(upload_vec(H, &L.cptr, cptr));
       DIFVM_TRY(upload_vec(H, &L.cent, cent));
-      DIFVM_TRY(upload_vec(H, &L.col, col));
+      DIFVM_TRY(upload_vec(H, &L.soff, soff));
+      DIFVM_TRY(upload_vec(H, &L.ecol, ecol));
+      DIFVM_TRY(upload_vec(H, &L.eface, eface));
     }
     const bool last = g.n <= kAmgCoarsest || lvl + 1 >= kAmgMaxLevels;
     if (!last) {
@@ -255,7 +281,7 @@ difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
 // [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials | ticket]
 struct AmgLayout {
   size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], E[kAmgMaxLevels],
-      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, rhs32, e32, total;
+      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, total;
 };
 
 static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
@@ -275,7 +301,7 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
     A.D[l] = take((size_t)L.n * e);
     A.rD[l] = take((size_t)L.n * e);
     A.L[l] = take((size_t)L.nf * e);
-    A.E[l] = take((size_t)(l > 0 ? 2 * L.nf : 1) * e);   // row-entry values (levels >= 1)
+    A.E[l] = take((size_t)(l > 0 ? L.nslots : 1) * e);   // sliced-ELL values (levels >= 1)
     A.r[l] = take((size_t)L.n * e);
     A.a[l] = take((size_t)L.n * e);
     A.b[l] = take((size_t)L.n * e);
@@ -287,8 +313,6 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
   const size_t nblk = std::max<size_t>(amg_grid(m), blocks_for(m->nc, kAB));
   A.part = take(nblk * kMaxParts * sizeof(double));
   A.ticket = take(256);
-  A.rhs32 = take((size_t)m->nc * 4);
-  A.e32 = take((size_t)m->nc * 4);
   A.total = o;
   return A;
 }
@@ -296,7 +320,8 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
 size_t amg_workspace_bytes(difvm_mesh* m, size_t elt) {
   AmgHier* H = nullptr;
   if (amg_hier(m, &H) != DIFVM_OK) return 0;
-  return amg_layout(m, H, elt).total;
+  // + FP64 r, p, q of the mixed-precision form (FP64 CG, FP32 V-cycle)
+  return amg_layout(m, H, elt).total + 3 * up256a((size_t)m->nc * 8);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -328,11 +353,13 @@ __global__ void k_amg_faces(int nf1, AmgLev L, const T* Lv, T* L1) {
   L1[F] = s;
 }
 
-// row-entry values of a coarse level from its face coefficients
+// sliced-ELL values of a coarse level from its face coefficients (0 on padding)
 template <typename T>
-__global__ void k_amg_entries(int nnz, const int* cent, const T* Lv, T* E) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nnz) E[e] = Lv[cent[e] >> 1];
+__global__ void k_amg_entries(int nslots, const int* eface, const T* Lv, T* E) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nslots) return;
+  const int f = eface[k];
+  E[k] = f < 0 ? T(0) : Lv[f];
 }
 
 // dense inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), one
@@ -340,7 +367,10 @@ __global__ void k_amg_entries(int nnz, const int* cent, const T* Lv, T* E) {
 // SM), then symmetrised; it serves only as the preconditioner's coarsest solve
 template <typename T>
 __global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, const T* Lv, float* A) {
+  // thread (ty, tx) of a 32 x 32 grid owns the elements (ty + 32a, tx + 32b), a, b < 6
+  constexpr int NB = kAmgCoarsest / 32;
   const int n = L.n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.f;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) A[i * n + i] = (float)D[i];
@@ -350,28 +380,65 @@ __global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, co
     A[o.y * n + o.x] = (float)Lv[f];
   }
   __syncthreads();
-  __shared__ float col[kAmgCoarsest];
-  __shared__ float piv;
+  float a[NB][NB];
+#pragma unroll
+  for (int p = 0; p < NB; ++p)
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int i = ty + 32 * p, j = tx + 32 * q;
+      a[p][q] = (i < n && j < n) ? A[i * n + j] : 0.f;
+    }
+  __shared__ float row[kAmgCoarsest], col[kAmgCoarsest];
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) piv = 1.f / A[k * n + k];
+    // row k and column k (before the step) to shared memory; register indices
+    // stay compile-time constants (no local-memory copy of the tile)
+    if (ty == (k & 31)) {
+#pragma unroll
+      for (int p = 0; p < NB; ++p)
+        if (p == (k >> 5)) {
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const int j = tx + 32 * q;
+            if (j < n) row[j] = a[p][q];
+          }
+        }
+    }
+    if (tx == (k & 31)) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q == (k >> 5)) {
+#pragma unroll
+          for (int p = 0; p < NB; ++p) {
+            const int i = ty + 32 * p;
+            if (i < n) col[i] = a[p][q];
+          }
+        }
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = (i == k) ? 0.f : A[i * n + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] = (j == k ? 1.f : A[k * n + j]) * piv;
-    __syncthreads();
-    // rows i != k: A[i][j] -= col[i] A[k][j]; 32 x 32 threads tile the (i, j) plane
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int i = ty; i < n; i += 32) {
-      if (i == k) continue;
-      const float ci = col[i];
-      for (int j = tx; j < n; j += 32) {
-        const float a = (j == k) ? 0.f : A[i * n + j];
-        A[i * n + j] = a - ci * A[k * n + j];
+    const float rp = 1.f / row[k];
+#pragma unroll
+    for (int p = 0; p < NB; ++p) {
+      const int i = ty + 32 * p;
+      const float ci = col[i < n ? i : 0];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const int j = tx + 32 * q;
+        const float rj = (j == k) ? rp : row[j < n ? j : 0] * rp;
+        if (i == k) a[p][q] = rj;
+        else a[p][q] = (j == k ? 0.f : a[p][q]) - ci * rj;
       }
     }
     __syncthreads();
   }
-  // symmetrise: the exact inverse is symmetric
+  // write back symmetrised: the exact inverse is symmetric
+#pragma unroll
+  for (int p = 0; p < NB; ++p)
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int i = ty + 32 * p, j = tx + 32 * q;
+      if (i < n && j < n) A[i * n + j] = a[p][q];
+    }
+  __syncthreads();
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, j = t - i * n;
     if (i < j) {
@@ -405,8 +472,22 @@ __device__ __forceinline__ T amg_row(const Mat<T>& A, const AmgLev& L, const T* 
     return y;
   }
   T y = D[i] * x(i);
-  const int e1 = L.cptr[i + 1];
-  for (int e = L.cptr[i]; e < e1; ++e) y += Lv[e] * x(L.col[e]);   // Lv: row-entry values here
+  int o = __ldg(L.soff + (i >> 5)) + (i & 31);
+  const int w = (__ldg(L.soff + (i >> 5) + 1) - __ldg(L.soff + (i >> 5))) >> 5;
+  // four entries per pass: their column, value and gathered loads are all in
+  // flight together (a coarse row has ~10-25 entries); sums stay in slot order
+  int k = 0;
+  for (; k + 4 <= w; k += 4, o += 128) {
+    const int c0 = __ldg(L.ecol + o), c1 = __ldg(L.ecol + o + 32), c2 = __ldg(L.ecol + o + 64),
+              c3 = __ldg(L.ecol + o + 96);
+    const T v0 = Lv[o], v1 = Lv[o + 32], v2 = Lv[o + 64], v3 = Lv[o + 96];   // Lv: ELL values
+    const T x0 = x(c0), x1 = x(c1), x2 = x(c2), x3 = x(c3);
+    y += v0 * x0;
+    y += v1 * x1;
+    y += v2 * x2;
+    y += v3 * x3;
+  }
+  for (; k < w; ++k, o += 32) y += Lv[o] * x(__ldg(L.ecol + o));
   return y;
 }
 
@@ -440,7 +521,17 @@ __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T*
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= n1) return;
   T s = T(0);
-  for (int c = L.ch_ptr[K]; c < L.ch_ptr[K + 1]; ++c) s += res[L.ch_idx[c]];
+  int c = L.ch_ptr[K];
+  const int c1 = L.ch_ptr[K + 1];
+  for (; c + 4 <= c1; c += 4) {   // children in flight together, summed in order
+    const int i0 = L.ch_idx[c], i1 = L.ch_idx[c + 1], i2 = L.ch_idx[c + 2], i3 = L.ch_idx[c + 3];
+    const T r0 = res[i0], r1 = res[i1], r2 = res[i2], r3 = res[i3];
+    s += r0;
+    s += r1;
+    s += r2;
+    s += r3;
+  }
+  for (; c < c1; ++c) s += res[L.ch_idx[c]];
   rc[K] = s;
 }
 
@@ -461,14 +552,13 @@ __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* 
 // second post-smoothing sweep: v = u + w rD (r - A u).  On level 0 of a CG
 // iteration it also forms r.z: the last block sets beta (first = 1: rz only).
 template <typename T, bool FINE, bool DOT>
-__global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
+__global__ void __launch_bounds__(kKB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                    const T* r, const T* u, T* v, KWork w, int first) {
   if (w.st[0].done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const T om = (T)kAmgOmega;
   DotAcc<T> rz;
-  if (i < L.n) {
-    auto xu = [&](int j) { return u[j]; };
+  auto xu = [&](int j) { return u[j]; };
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
     const T vi = u[i] + om * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xu));
     v[i] = vi;
     if (DOT) rz.add(r[i], vi);
@@ -507,7 +597,7 @@ __global__ void __launch_bounds__(256) k_amg_coarse(int n, const float* Ainv, co
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     float s = 0.f;
-    for (int j = 0; j < n; ++j) s += Ainv[i * n + j] * rs[j];
+    for (int j = 0; j < n; ++j) s += Ainv[j * n + i] * rs[j];   // symmetric: column j = row j
     x[i] = (T)s;
   }
 }
@@ -613,7 +703,7 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
     k_amg_diag<T><<<blocks_for(L1.n, kAB), kAB, 0, st>>>(L1.n, L, D, Lv, D1, rD1);
     if (L1.nf > 0) {
       k_amg_faces<T><<<blocks_for(L1.nf, kAB), kAB, 0, st>>>(L1.nf, L, Lv, Lv1);
-      k_amg_entries<T><<<blocks_for(2 * L1.nf, kAB), kAB, 0, st>>>(2 * L1.nf, L1.cent, Lv1,
+      k_amg_entries<T><<<blocks_for(L1.nslots, kAB), kAB, 0, st>>>(L1.nslots, L1.eface, Lv1,
                                                                  R.at(R.Ly.E[l + 1]));
     }
     DIFVM_TRY(check_launch("amg_coarse_ops"));
@@ -653,7 +743,9 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   T* xc = R.at(R.Ly.a[l + 1]);   // written by the next level's last sweep
   if (fine) {
     k_amg_pre<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
+    prof_before(DIFVM_PROF_AMG_RESID, s);
     k_amg_resid<T, true><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
+    prof_after(DIFVM_PROF_AMG_RESID, s);
   } else {
     k_amg_pre<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
     k_amg_resid<T, false><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
@@ -663,7 +755,7 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   amg_vcycle(R, l + 1, rc, xc, w, first, s);
   if (fine) {
     k_amg_post1<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
-    k_amg_post2<T, true, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
+    k_amg_post2<T, true, true><<<R.G, kKB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
   } else {
     k_amg_post1<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
     k_amg_post2<T, false, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
@@ -797,149 +889,186 @@ template difvm_status amg_solve<double>(difvm_mesh*, const difvm_solve_opts*, co
                                         const double*, double*, void*, size_t, difvm_solve_info*,
                                         cudaStream_t);
 
-// ------------------------------------------------- mixed precision refinement
-// Outer loop in FP64: r = b - A x (FP32 coefficients are exact in FP64); stop
-// when ||r|| <= max(tol_rel ||b||, tol_abs) or after refine_max sweeps; else
-// solve A e = r with the FP32 AMG-preconditioned CG to inner_tol and add e to x.
-__global__ void __launch_bounds__(kKB) k_ref_residual(Topo t, Mat<float> A, const double* b64,
-                                                      const double* x64, float* r32, KWork w,
-                                                      int refine_max) {
+// ------------------------------------------------------ mixed precision
+// CG in FP64 (x, r, p, q, inner products; the SpMV reads the FP32 coefficients,
+// which are exact in FP64) preconditioned by the FP32 V-cycle: the update
+// kernel hands the V-cycle an FP32 copy of r, and p = z + beta p takes the FP32
+// z.  The preconditioner's precision only affects the convergence rate, so the
+// solve reaches FP64 tolerances without refinement sweeps or restarts.
+template <int MW>
+__global__ void __launch_bounds__(kKB) k_mcg_init(Topo t, Mat<float> A, const double* b, const double* x,
+                                                  double* r, float* r32, KWork w) {
   const int nc = t.nc;
   double bb = 0.0, rr = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    double ax = (double)A.D[i] * x64[i];
-    if (A.E.W == 4) {
+    double y = (double)A.D[i] * x[i];
+    if (MW == 4 && A.E.W == 4) {
       const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(A.val) + i);
-      ax += (double)a4.x * x64[j4.x];
-      ax += (double)a4.y * x64[j4.y];
-      ax += (double)a4.z * x64[j4.z];
-      ax += (double)a4.w * x64[j4.w];
+      y = fma((double)a4.x, x[j4.x], y);
+      y = fma((double)a4.y, x[j4.y], y);
+      y = fma((double)a4.z, x[j4.z], y);
+      y = fma((double)a4.w, x[j4.w], y);
     } else {
       int base, step, wd;
       ell_row(A.E, i, base, step, wd);
-      for (int k = 0; k < wd; ++k) ax += (double)A.val[base + step * k] * x64[A.E.col[base + step * k]];
+      for (int k = 0; k < wd; ++k) y = fma((double)A.val[base + step * k], x[A.E.col[base + step * k]], y);
     }
-    const double ri = b64[i] - ax;
+    const double ri = b[i] - y;
+    r[i] = ri;
     r32[i] = (float)ri;
-    bb += b64[i] * b64[i];
-    rr += ri * ri;
+    bb = fma(b[i], b[i], bb);
+    rr = fma(ri, ri, rr);
   }
   double v[2] = {bb, rr}, tot[2];
   if (!grid_sum<2>(w, v, tot) || threadIdx.x != 0) return;
   KState& s = w.st[0];
-  if (s.done) return;
-  if (s.iters == 0) {   // first sweep
-    s.bb = tot[0];
-    s.res0 = sqrt(tot[1]);
-    s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
-    s.status = DIFVM_OK;
-    s.rho = tot[1];
-    if (s.bb == 0.0) { s.zero_rhs = 1; s.rr = 0.0; s.done = 1; return; }
-  } else if (tot[1] > s.rho / 16.0) {   // a sweep must cut the residual by 4x
-    s.rr = tot[1];
-    s.done = 1;
-    s.status = DIFVM_ENOTCONV;
-    return;
-  }
-  s.rho = tot[1];
+  s.bb = tot[0];
   s.rr = tot[1];
-  if (!isfinite(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; return; }
-  if (s.rr <= s.tol2) { s.done = 1; return; }
-  if (s.iters >= refine_max) { s.done = 1; s.status = DIFVM_ENOTCONV; return; }
-  s.iters += 1;
+  s.res0 = sqrt(s.rr);
+  s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+  s.iters = 0;
+  s.status = DIFVM_OK;
+  s.zero_rhs = s.bb == 0.0;
+  s.done = s.zero_rhs || s.rr <= s.tol2;
+  if (!isfinite(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
 }
 
-// x += e after an inner solve; nothing when this sweep's residual closed the
-// loop (the inner solve was skipped); x = 0 for a zero right-hand side
-__global__ void k_ref_add(int nc, const float* e, double* x64, const KState* outer, const KState* inner,
-                          int* total_iters) {
-  if (outer->zero_rhs) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x64[i] = 0.0;
+// q = A p (FP64 arithmetic, FP32 coefficients); alpha = rz / (p.q)
+template <int MW>
+__global__ void __launch_bounds__(kKB) k_mcg_spmv(Topo t, Mat<float> A, const double* p, double* q, KWork w) {
+  if (w.st[0].done) return;
+  const int nc = t.nc;
+  double pq = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    double y = (double)__ldg(A.D + i) * p[i];
+    if (MW == 4 && A.E.W == 4) {
+      const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      const float4 a4 = __ldg(reinterpret_cast<const float4*>(A.val) + i);
+      y = fma((double)a4.x, p[j4.x], y);
+      y = fma((double)a4.y, p[j4.y], y);
+      y = fma((double)a4.z, p[j4.z], y);
+      y = fma((double)a4.w, p[j4.w], y);
+    } else {
+      int base, step, wd;
+      ell_row(A.E, i, base, step, wd);
+      for (int k = 0; k < wd; ++k)
+        y = fma((double)__ldg(A.val + base + step * k), p[__ldg(A.E.col + base + step * k)], y);
+    }
+    q[i] = y;
+    pq = fma(p[i], y, pq);
+  }
+  double v[1] = {pq}, tot[1];
+  if (!grid_sum<1>(w, v, tot) || threadIdx.x != 0) return;
+  w.st[0].alpha = w.st[0].rz / tot[0];
+}
+
+// x += alpha p; r -= alpha q; r32 = (float) r; rr; convergence
+__global__ void __launch_bounds__(kKB) k_mcg_update(int nc, const double* p, const double* q, double* x,
+                                                    double* r, float* r32, KWork w) {
+  if (w.st[0].done) return;
+  const double al = w.st[0].alpha;
+  double rr = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    x[i] = fma(al, p[i], x[i]);
+    const double ri = fma(-al, q[i], r[i]);
+    r[i] = ri;
+    r32[i] = (float)ri;
+    rr = fma(ri, ri, rr);
+  }
+  double v[1] = {rr}, tot[1];
+  if (!grid_sum<1>(w, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[0];
+  s.iters += 1;
+  s.rr = tot[0];
+  if (!isfinite(s.rr) || !isfinite(s.alpha)) { s.done = 1; s.status = DIFVM_ENONFINITE; return; }
+  if (s.rr <= s.tol2) { s.done = 1; return; }
+  if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; }
+}
+
+// p = z + beta p (first: p = z); x = 0 for a zero right-hand side
+__global__ void __launch_bounds__(kKB) k_mcg_p(int nc, const float* z, double* p, double* x, KWork w,
+                                               int first) {
+  if (w.st[0].zero_rhs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x[i] = 0.0;
     return;
   }
-  if (outer->done) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x64[i] += (double)e[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *total_iters += inner->iters;
-}
-
-__global__ void k_amg_ref_info(const KState* outer, const int* total, difvm_solve_info* info) {
-  if (threadIdx.x != 0) return;
-  difvm_solve_info o;
-  o.iters = *total;
-  o.refinements = outer->iters;
-  o.status = outer->status;
-  o.pad = 0;
-  o.res0 = outer->res0;
-  o.res = sqrt(outer->rr);
-  o.bnorm = sqrt(outer->bb);
-  *info = o;
+  if (w.st[0].done) return;
+  const double be = w.st[0].beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+    p[i] = first ? (double)z[i] : fma(be, p[i], (double)z[i]);
 }
 
 template <int MW>
-static difvm_status amg_refine_mw(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
-                                  const double* b64, double* x64, void* ws, size_t wsbytes,
-                                  difvm_solve_info* info, cudaStream_t st) {
+static difvm_status amg_mixed_mw(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
+                                 const double* b64, double* x64, void* ws, size_t wsbytes,
+                                 difvm_solve_info* info, cudaStream_t st) {
   AmgRun<float> R;
   DIFVM_TRY(amg_prepare<float>(m, D, Lo, ws, wsbytes, R, st));
-  const int refine_max = o->refine_max > 0 ? o->refine_max : 20;
-  const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
-  KWork wo = amg_work_t(R, 1, refine_max, o->tol_rel, o->tol_abs);           // outer
-  KWork wi = amg_work_t(R, 0, o->max_iter > 0 ? o->max_iter : 1000, inner_tol, 0.0);  // inner
-  float* r32 = (float*)(R.ws + R.Ly.rhs32);
-  float* e32 = (float*)(R.ws + R.Ly.e32);
-  int* total = reinterpret_cast<int*>(wo.ticket) + 2;
-  int* ocounter = reinterpret_cast<int*>(wo.ticket) + 3;
-  DIFVM_CUDA(cudaMemsetAsync(wo.ticket, 0, 16, st));
-  DIFVM_CUDA(cudaMemsetAsync(wo.st, 0, sizeof(KState), st));
-  const int chunk = o->check_every > 0 ? o->check_every : 8;
-  KState* outer = wo.st;
-  auto sweep = [&](cudaStream_t s) -> difvm_status {
-    k_ref_residual<<<R.G, kKB, 0, s>>>(R.t, R.A, b64, x64, r32, wo, refine_max);
-    DIFVM_TRY(check_launch("ref_residual"));
-    DIFVM_TRY((amg_cg<float, MW>(R, r32, e32, wi, &outer->done, 1, chunk, s)));
-    k_ref_add<<<R.G, kKB, 0, s>>>(m->nc, e32, x64, outer, wi.st, total);
-    return check_launch("ref_add");
+  if (R.Ly.total + 3 * up256a((size_t)m->nc * 8) > wsbytes)
+    return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes,
+                     R.Ly.total + 3 * up256a((size_t)m->nc * 8));
+  double* r = (double*)(R.ws + R.Ly.total);
+  double* p = r + up256a((size_t)m->nc * 8) / 8;
+  double* q = p + up256a((size_t)m->nc * 8) / 8;
+  float* r32 = R.vec(0);
+  float* z32 = R.vec(3);
+  KWork w = amg_work_t(R, 0, o->max_iter > 0 ? o->max_iter : 1000, o->tol_rel, o->tol_abs);
+  DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, 16, st));
+  const int nc = m->nc, G = R.G;
+  k_mcg_init<MW><<<G, kKB, 0, st>>>(R.t, R.A, b64, x64, r, r32, w);
+  DIFVM_TRY(check_launch("mcg_init"));
+  amg_vcycle(R, 0, r32, z32, w, 1, st);
+  k_mcg_p<<<G, kKB, 0, st>>>(nc, z32, p, x64, w, 1);
+  DIFVM_TRY(check_launch("mcg_p"));
+  auto iter = [&](cudaStream_t s) {
+    prof_before(DIFVM_PROF_PCG_SPMV, s);
+    k_mcg_spmv<MW><<<G, kKB, 0, s>>>(R.t, R.A, p, q, w);
+    prof_after(DIFVM_PROF_PCG_SPMV, s);
+    k_mcg_update<<<G, kKB, 0, s>>>(nc, p, q, x64, r, r32, w);
+    amg_vcycle(R, 0, r32, z32, w, 0, s);
+    k_mcg_p<<<G, kKB, 0, s>>>(nc, z32, p, x64, w, 0);
+    count_launch(); count_launch(); count_launch();
   };
-  if (stream_capturing(st)) {
-    DIFVM_CUDA(cudaMemsetAsync(ocounter, 0, sizeof(int), st));
+  int* counter = reinterpret_cast<int*>(w.ticket) + 1;
+  const bool graph = stream_capturing(st);
+  if (graph) {
+    DIFVM_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
     WhileLoop Lw;
     DIFVM_TRY(while_open(st, Lw));
-    difvm_status e = sweep(Lw.side);
-    if (e == DIFVM_OK) {
-      k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(wo.st), kStateInts, 1, ocounter, refine_max + 2, Lw.h);
-      e = check_launch("loop_cond");
-    }
+    iter(Lw.side);
+    k_loop_cond<<<1, 32, 0, Lw.side>>>(done_flags(w.st), kStateInts, 1, counter, w.maxit + 2, Lw.h);
+    difvm_status e = check_launch("loop_cond");
     DIFVM_TRY(while_close(Lw));
     DIFVM_TRY(e);
   } else {
+    const int chunk = o->check_every > 0 ? o->check_every : 8;
     KState hs;
-    for (int k = 0; k <= refine_max; ++k) {
-      DIFVM_TRY(sweep(st));
-      DIFVM_CUDA(cudaMemcpyAsync(&hs, outer, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    for (int it = 0; it < w.maxit + chunk; it += chunk) {
+      for (int k = 0; k < chunk; ++k) iter(st);
+      DIFVM_TRY(check_error("mcg_iter"));
+      DIFVM_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
       DIFVM_CUDA(cudaStreamSynchronize(st));
       if (hs.done) break;
     }
   }
   if (info) {
-    k_amg_ref_info<<<1, 32, 0, st>>>(outer, total, info);
-    DIFVM_TRY(check_launch("amg_ref_info"));
+    k_amg_info<<<1, 32, 0, st>>>(w.st, info, 0, -1);
+    DIFVM_TRY(check_launch("amg_info"));
   }
-  if (stream_capturing(st)) return DIFVM_OK;
+  if (graph) return DIFVM_OK;
   KState hs;
-  DIFVM_CUDA(cudaMemcpyAsync(&hs, outer, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  DIFVM_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
   DIFVM_CUDA(cudaStreamSynchronize(st));
-  int s = hs.status;
-  if (s == DIFVM_OK && !hs.done) s = DIFVM_ENOTCONV;
-  return (difvm_status)s;
+  return (difvm_status)hs.status;
 }
 
 difvm_status amg_refine(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
                         const double* b64, double* x64, void* ws, size_t wsbytes, difvm_solve_info* info,
                         cudaStream_t st) {
-  if (m->ell_wmax <= 4) return amg_refine_mw<4>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
-  if (m->ell_wmax <= 8) return amg_refine_mw<8>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
-  return amg_refine_mw<0>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
+  if (m->ell_wmax <= 4) return amg_mixed_mw<4>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
+  if (m->ell_wmax <= 8) return amg_mixed_mw<8>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
+  return amg_mixed_mw<0>(m, o, D, Lo, b64, x64, ws, wsbytes, info, st);
 }
 
 }  // namespace difvm

@@ -161,7 +161,7 @@ def launch_count() -> int:
     return int(lib().difvm_launch_count())
 
 
-PROF_PCG_SPMV, PROF_PCG_UPDATE, PROF_PCG_PUPDATE = 1, 2, 3
+PROF_PCG_SPMV, PROF_PCG_UPDATE, PROF_PCG_PUPDATE, PROF_AMG_RESID = 1, 2, 3, 4
 
 
 def difvm_prof_start(tag, max_launches=100000):

@@ -86,7 +86,7 @@ def test_amg_cg_solves_the_pressure_system(n, pin):
         assert ia["iters"] * 5 < ij["iters"], (ia["iters"], ij["iters"])
 
 
-def test_amg_f32_refined_reaches_fp64_tolerance():
+def test_amg_mixed_precision_reaches_fp64_tolerance():
     m = mg.shuffle(mg.kuhn_cube(12, 0.2, 5), 6)
     dm = D.Mesh(m)
     om, Dg, Lg = _pressure_matrix(m, 3, pin=11)
@@ -96,7 +96,8 @@ def test_amg_f32_refined_reaches_fp64_tolerance():
     Lg32 = Lg.astype(np.float32).astype(np.float64)
     st, info, x = _solve(dm, m, Dg, Lg, b, D.PRECOND_AMG, prec=D.F32, refine=1, tol=1e-10)
     assert st == D.OK, info
-    assert info["refinements"] >= 2
+    # one FP64 CG around the FP32 V-cycle: no refinement sweeps, few iterations
+    assert info["refinements"] == 0 and info["iters"] < 60
     r = b - O.ldu_apply(om, Dg32, Lg32, None, x[None])[0]
     assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
 
