@@ -478,7 +478,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "mesh": f"kuhn{N_KUHN}^3 jitter {JITTER} seed {SEED} RCM",
                    "cells": dm.nc, "faces": dm.nf, "nu": NU, "dt": DT, "n_corr": 2,
                    "nonorth": "momentum (the lagged pressure correction diverges on these tets)",
-                   "precision": "f32 fields/operators, f64 dots + f64 pressure refinement to 1e-10",
+                   "precision": "f32 fields/operators, f64 dots; pressure: f64 CG to 1e-10 around an "
+                                "f32 multigrid V-cycle",
                    "pressure_solver": "CG + one aggregation-multigrid V-cycle per iteration",
                    "parallelism": f"replicas x{world}",
                    "api": "difvm_piso_step_graph (one CUDA graph per step, solver loops on the device)",

@@ -366,9 +366,10 @@ __global__ void k_amg_entries(int nslots, const int* eface, const T* Lv, T* E) {
 // block, in FP32 (the B300's FP64 rate is about 1/64 of FP32 and this runs on one
 // SM), then symmetrised; it serves only as the preconditioner's coarsest solve
 template <typename T>
-__global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, const T* Lv, float* A) {
-  // thread (ty, tx) of a 32 x 32 grid owns the elements (ty + 32a, tx + 32b), a, b < 6
-  constexpr int NB = kAmgCoarsest / 32;
+__global__ void __launch_bounds__(512) k_amg_dense_inv(AmgLev L, const T* D, const T* Lv, float* A) {
+  // thread (ty, tx) of a 16 x 32 grid owns the elements (ty + 16a, tx + 32b),
+  // a < 12, b < 6: a 12 x 6 register tile (512 threads leave 128 registers each)
+  constexpr int NR = kAmgCoarsest / 16, NC = kAmgCoarsest / 32;
   const int n = L.n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.f;
@@ -380,62 +381,57 @@ __global__ void __launch_bounds__(1024) k_amg_dense_inv(AmgLev L, const T* D, co
     A[o.y * n + o.x] = (float)Lv[f];
   }
   __syncthreads();
-  float a[NB][NB];
+  float a[NR][NC];
 #pragma unroll
-  for (int p = 0; p < NB; ++p)
+  for (int p = 0; p < NR; ++p)
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int i = ty + 32 * p, j = tx + 32 * q;
+    for (int q = 0; q < NC; ++q) {
+      const int i = ty + 16 * p, j = tx + 32 * q;
       a[p][q] = (i < n && j < n) ? A[i * n + j] : 0.f;
     }
   __shared__ float row[kAmgCoarsest], col[kAmgCoarsest];
   for (int k = 0; k < n; ++k) {
-    // row k and column k (before the step) to shared memory; register indices
-    // stay compile-time constants (no local-memory copy of the tile)
-    if (ty == (k & 31)) {
+    // row k and column k (before the step) to shared memory: every tile element
+    // is visited with a compile-time index, predicated on being in row/column k
 #pragma unroll
-      for (int p = 0; p < NB; ++p)
-        if (p == (k >> 5)) {
+    for (int p = 0; p < NR; ++p)
 #pragma unroll
-          for (int q = 0; q < NB; ++q) {
-            const int j = tx + 32 * q;
-            if (j < n) row[j] = a[p][q];
-          }
-        }
-    }
-    if (tx == (k & 31)) {
-#pragma unroll
-      for (int q = 0; q < NB; ++q)
-        if (q == (k >> 5)) {
-#pragma unroll
-          for (int p = 0; p < NB; ++p) {
-            const int i = ty + 32 * p;
-            if (i < n) col[i] = a[p][q];
-          }
-        }
-    }
+      for (int q = 0; q < NC; ++q) {
+        const int i = ty + 16 * p, j = tx + 32 * q;
+        if (i == k && j < n) row[j] = a[p][q];
+        if (j == k && i < n) col[i] = a[p][q];
+      }
     __syncthreads();
     const float rp = 1.f / row[k];
+    float rj[NC], ci[NR];
 #pragma unroll
-    for (int p = 0; p < NB; ++p) {
-      const int i = ty + 32 * p;
-      const float ci = col[i < n ? i : 0];
+    for (int q = 0; q < NC; ++q) {
+      const int j = tx + 32 * q;
+      rj[q] = (j == k) ? rp : row[j < n ? j : 0] * rp;
+    }
 #pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        const int j = tx + 32 * q;
-        const float rj = (j == k) ? rp : row[j < n ? j : 0] * rp;
-        if (i == k) a[p][q] = rj;
-        else a[p][q] = (j == k ? 0.f : a[p][q]) - ci * rj;
+    for (int p = 0; p < NR; ++p) {
+      const int i = ty + 16 * p;
+      ci[p] = col[i < n ? i : 0];
+    }
+#pragma unroll
+    for (int p = 0; p < NR; ++p) {
+      const bool rowk = ty + 16 * p == k;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const bool colk = tx + 32 * q == k;
+        const float old = colk ? 0.f : a[p][q];
+        a[p][q] = rowk ? rj[q] : old - ci[p] * rj[q];
       }
     }
     __syncthreads();
   }
   // write back symmetrised: the exact inverse is symmetric
 #pragma unroll
-  for (int p = 0; p < NB; ++p)
+  for (int p = 0; p < NR; ++p)
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int i = ty + 32 * p, j = tx + 32 * q;
+    for (int q = 0; q < NC; ++q) {
+      const int i = ty + 16 * p, j = tx + 32 * q;
       if (i < n && j < n) A[i * n + j] = a[p][q];
     }
   __syncthreads();
@@ -712,7 +708,7 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
   }
   const AmgLev& Lc = H->lev[H->nlev - 1];
   if (Lc.n > kAmgCoarsest) return set_error(DIFVM_EINVAL, "AMG: coarsest level has %d cells", Lc.n);
-  k_amg_dense_inv<T><<<1, 1024, 0, st>>>(Lc, D, Lv, (float*)(R.ws + R.Ly.inv));
+  k_amg_dense_inv<T><<<1, 512, 0, st>>>(Lc, D, Lv, (float*)(R.ws + R.Ly.inv));
   return check_launch("amg_dense_inv");
 }
 
