@@ -187,6 +187,67 @@ def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4):
             "adjoint_status": int(adj["status"])}
 
 
+def run_face_ops(D, torch, dm, peak, reps=20):
+    """The face operators on the bench mesh in FP32 and FP64 (Sec. 2.3-2.4: Gauss
+    gradient, convective divergence, diffusive flux, LDU apply): median device time
+    of `reps` launches, each after writing a 512 MB buffer, so that none of the
+    inputs is L2-resident.  Algorithmic bytes: each face array read once
+    (int32 owner/neighbour + the geometry the operator needs), each input cell
+    array read once, each output written once; gathers hit cache."""
+    nc, ni, nf, nb = dm.nc, dm.ni, dm.nf, dm.nb
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    res = {}
+    for prec, dt, v in ((D.F32, torch.float32, 4), (D.F64, torch.float64, 8)):
+        def rn(*shape):
+            return torch.randn(*shape, generator=gen, device="cuda", dtype=dt)
+        phi, phib, U, Ub, mf = rn(1, nc), rn(1, nb), rn(3, nc), rn(3, nb), rn(nf)
+        Dg, L, Uu, x1, x3 = rn(nc).abs() + 10.0, rn(ni), rn(ni), rn(1, nc), rn(3, nc)
+        g1 = torch.empty(1, 3, nc, dtype=dt, device="cuda")
+        g3 = torch.empty(3, 3, nc, dtype=dt, device="cuda")
+        o1, o3 = torch.empty(1, nc, dtype=dt, device="cuda"), torch.empty(3, nc, dtype=dt, device="cuda")
+        gp = D.difvm_grad_gauss(dm, D.BC_ALL_FIXED, phi, phib)
+        ops = {
+            "grad_gauss_scalar": (lambda: D.difvm_grad_gauss(dm, D.BC_PRESSURE, phi, phib, grad=g1),
+                                  nf * (8 + 4 * v) + nc * 5 * v),
+            "grad_gauss_vector": (lambda: D.difvm_grad_gauss(dm, D.BC_VELOCITY, U, Ub, grad=g3),
+                                  nf * (8 + 4 * v) + nc * 13 * v),
+            "div_flux_upwind_3": (lambda: D.difvm_div_flux(dm, D.DIV_UPWIND, D.BC_VELOCITY, mf, U, Ub, out=o3),
+                                  nf * (8 + v) + nc * 6 * v),
+            "div_flux_linear_3": (lambda: D.difvm_div_flux(dm, D.DIV_LINEAR, D.BC_VELOCITY, mf, U, Ub, out=o3),
+                                  nf * (8 + 2 * v) + nc * 6 * v),
+            "laplacian_apply_sym_1": (lambda: D.difvm_laplacian_apply(dm, Dg, L, None, x1, y=o1),
+                                      nf * (8 + v) + nc * 3 * v),
+            "laplacian_apply_asym_3": (lambda: D.difvm_laplacian_apply(dm, Dg, L, Uu, x3, y=o3),
+                                       nf * (8 + 2 * v) + nc * 7 * v),
+            "laplacian_nonorth_1": (lambda: D.difvm_laplacian(dm, D.BC_ALL_FIXED, 1.0, phi, phib, grad=gp, out=o1),
+                                    nf * (8 + 5 * v) + nc * 5 * v),
+        }
+        key = "f32" if prec == D.F32 else "f64"
+        for name, (fn, nbytes) in ops.items():
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            t = float(np.median(ts))
+            gbs = nbytes / (t * 1e-3) / 1e9
+            res.setdefault(name, {})[key] = {"us": round(t * 1e3, 2), "alg_MB": round(nbytes / 1e6, 1),
+                                             "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3),
+                                             "frac_of_8TBs": round(gbs / 8000.0, 3)}
+    fr = [res[k]["f32"]["frac"] for k in res]
+    return {"unit": "GB/s (algorithmic)", "peak": peak, "reps": reps, "ops": res,
+            "f32_frac_median": float(np.median(fr)), "f32_frac_min": float(min(fr)),
+            "method": "median of 20 launches, 512 MB written before each (L2 cold), CUDA events"}
+
+
 def cpu_oracle_step_rate(m, steps=1, warm_steps=0):
     """The FP64 CPU oracle (single thread, as it stands) on the same cavity.
     Returns (steps/s, seconds, sample description)."""
@@ -460,6 +521,7 @@ def run_ours(args):
                "adjoint_iters_first_step": {k_: D.decode_piso_info(adj["info"])[k_][:n_]
                                             for k_, n_ in (("itU", 3), ("itp", 2))}}
 
+    face_ops = run_face_ops(D, torch, dm, peak)
     batched = None if args.no_batch else run_batched(D, torch)
 
     if rank != 0:
@@ -496,6 +558,7 @@ def run_ours(args):
                 "pressure_iters_last_step": r64["info"]["itp"][:2],
                 "momentum_iters_last_step": r64["info"]["itU"]},
         "fwd_adjoint_over_fwd": fwd_adj,
+        "face_ops": face_ops,
         "batched": batched,
         "roofline": {"kernel": "k_amg_resid<float,FINE> (fine-level multigrid residual r - A y)",
                      "bound": "hbm",

@@ -90,6 +90,35 @@ struct Ell {
   const int* map;   // [nslots]
 };
 
+// Half-face layout of the cell-CSR rows (every face of a cell, internal and
+// boundary, in ascending face order), for the face operators: sliced ELL with
+// slice height 32, column-major in a slice (slot k of row i at
+// soff[i/32] + 32 k + i%32; with a uniform width W > 0 soff is not read).
+// nb[slot] = 2 j + side for an internal face (j the other cell, side 1 = row is
+// the neighbour), -2 - b for boundary face ni + b, -1 on padding; fid[slot] =
+// face id.  The face records Sw, ck are copied into slot order, so a row's
+// faces come in with coalesced loads and only the neighbour values are gathered.
+struct Hf {
+  int W;
+  const int* soff;
+  const int* nb;
+  const int* fid;
+};
+template <typename T> struct HfGeo {
+  const V4<T>* sw;  // [nslots] Sw of the slot's face
+  const V4<T>* ck;  // [nslots] ck of the slot's face
+};
+__device__ __forceinline__ void hf_row(const Hf& H, int i, int& base, int& w) {
+  if (H.W > 0) {
+    base = (i >> 5) * 32 * H.W + (i & 31);
+    w = H.W;
+  } else {
+    const int o = __ldg(H.soff + (i >> 5));
+    base = o + (i & 31);
+    w = (__ldg(H.soff + (i >> 5) + 1) - o) >> 5;
+  }
+}
+
 // first slot and slot stride of row i
 __device__ __forceinline__ void ell_row(const Ell& E, int i, int& base, int& step, int& w) {
   if (E.W > 0) {
@@ -153,11 +182,24 @@ struct difvm_mesh {
   int* seg_cs = nullptr;     // [ncases + 1] first cell of each case
   std::vector<int32_t> bown_host;  // boundary-face owners, internal numbering
   difvm::AmgHier* amg = nullptr;   // multigrid hierarchy, built on first use
+  // half-face layout of the CSR rows (see difvm::Hf)
+  int hf_w = 0;
+  int64_t hf_nslots = 0;
+  int* hf_soff = nullptr;
+  int* hf_nb = nullptr;
+  int* hf_fid = nullptr;
+  difvm::V4<double>* hf_sw64 = nullptr;
+  difvm::V4<double>* hf_ck64 = nullptr;
+  difvm::V4<float>* hf_sw32 = nullptr;
+  difvm::V4<float>* hf_ck32 = nullptr;
 
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
   }
   difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_w, ell_soff, ell_col, ell_map}; }
+  difvm::Hf hf() const { return difvm::Hf{hf_w, hf_soff, hf_nb, hf_fid}; }
+  difvm::HfGeo<double> hfgeo64() const { return {hf_sw64, hf_ck64}; }
+  difvm::HfGeo<float> hfgeo32() const { return {hf_sw32, hf_ck32}; }
   difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }
   difvm::Geo<float> geo32() const { return {Sw32, ck32, V32, rV32}; }
 };
@@ -166,6 +208,9 @@ namespace difvm {
 template <typename T> inline Geo<T> geo(const difvm_mesh* m);
 template <> inline Geo<double> geo<double>(const difvm_mesh* m) { return m->geo64(); }
 template <> inline Geo<float> geo<float>(const difvm_mesh* m) { return m->geo32(); }
+template <typename T> inline HfGeo<T> hfgeo(const difvm_mesh* m);
+template <> inline HfGeo<double> hfgeo<double>(const difvm_mesh* m) { return m->hfgeo64(); }
+template <> inline HfGeo<float> hfgeo<float>(const difvm_mesh* m) { return m->hfgeo32(); }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 

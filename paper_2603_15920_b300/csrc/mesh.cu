@@ -194,12 +194,33 @@ __global__ void k_cell_coeffs(int nc, const double* V, double* rV64, float* V32,
   rV32[i] = (float)(1.0 / v);
 }
 
+// face records in half-face slot order (zero on padding)
+__global__ void k_hf_fill(int ns, const int* fid, const V4<double>* Sw64, const V4<double>* ck64,
+                          const V4<float>* Sw32, const V4<float>* ck32, V4<double>* hsw64,
+                          V4<double>* hck64, V4<float>* hsw32, V4<float>* hck32) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  const int f = fid[k];
+  if (f < 0) {
+    hsw64[k] = V4<double>{0, 0, 0, 0};
+    hck64[k] = V4<double>{0, 0, 0, 0};
+    hsw32[k] = V4<float>{0, 0, 0, 0};
+    hck32[k] = V4<float>{0, 0, 0, 0};
+    return;
+  }
+  hsw64[k] = Sw64[f];
+  hck64[k] = ck64[f];
+  hsw32[k] = Sw32[f];
+  hck32[k] = ck32[f];
+}
+
 static void free_mesh(difvm_mesh* m) {
   if (!m) return;
   void* ptrs[] = {m->on,   m->bown, m->cptr, m->cent, m->bkind, m->bpatch, m->Sw64,
                   m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
                   m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map,
-                  m->seg_case, m->seg_cb0, m->seg_cs};
+                  m->seg_case, m->seg_cb0, m->seg_cs, m->hf_soff, m->hf_nb, m->hf_fid,
+                  m->hf_sw64, m->hf_ck64, m->hf_sw32, m->hf_ck32};
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
@@ -396,6 +417,29 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   }
   m->ell_nsl = nsl;
   m->ell_nslots = soff[nsl];
+  // half-face layout: every CSR entry of a row, sliced ELL, column-major per slice
+  std::vector<int> hsoff(nsl + 1, 0);
+  int hwmax = 0;
+  for (int sl = 0; sl < nsl; ++sl) {
+    int w = 0;
+    for (int i = 32 * sl; i < std::min(nc, 32 * sl + 32); ++i) w = std::max(w, cptr[i + 1] - cptr[i]);
+    hsoff[sl + 1] = hsoff[sl] + 32 * w;
+    hwmax = std::max(hwmax, w);
+  }
+  if ((int64_t)32 * hwmax * nsl <= (int64_t)hsoff[nsl] + hsoff[nsl] / 20) {
+    for (int sl = 0; sl <= nsl; ++sl) hsoff[sl] = 32 * hwmax * sl;
+    m->hf_w = hwmax;
+  }
+  m->hf_nslots = hsoff[nsl];
+  std::vector<int> hnb((size_t)std::max<int64_t>(m->hf_nslots, 1), -1), hfid(hnb.size(), -1);
+  for (int i = 0; i < nc; ++i) {
+    for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
+      const int slot = hsoff[i >> 5] + 32 * (e - cptr[i]) + (i & 31);
+      const int ent = cent[e], f = ent >> 1;
+      hfid[slot] = f;
+      hnb[slot] = f < ni ? 2 * ((ent & 1) ? on[f].x : on[f].y) + (ent & 1) : -2 - (f - ni);
+    }
+  }
   // boundary kinds per bc class (2 bits each)
   std::vector<uint8_t> bkind(nb > 0 ? nb : 1);
   std::vector<uint16_t> bpatch(nb > 0 ? nb : 1);
@@ -427,6 +471,9 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload(&m->ell_soff, soff.data(), soff.size()));
   DIFVM_TRY(upload(&m->ell_col, ecol.data(), ecol.size()));
   DIFVM_TRY(upload(&m->ell_map, emap.data(), emap.size()));
+  DIFVM_TRY(upload(&m->hf_soff, hsoff.data(), hsoff.size()));
+  DIFVM_TRY(upload(&m->hf_nb, hnb.data(), hnb.size()));
+  DIFVM_TRY(upload(&m->hf_fid, hfid.data(), hfid.size()));
   m->bown_host.assign(bown.begin(), bown.begin() + nb);
   if (d->case_cell_start) {
     // block tables of the segmented solvers (the case ranges survive the
@@ -461,6 +508,17 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(check_launch("face_coeffs"));
   k_cell_coeffs<<<blocks_for(nc, 256), 256>>>(nc, m->V64, m->rV64, m->V32, m->rV32);
   DIFVM_TRY(check_launch("cell_coeffs"));
+  {
+    const size_t ns = (size_t)std::max<int64_t>(m->hf_nslots, 1);
+    DIFVM_TRY(upload<V4<double>>(&m->hf_sw64, nullptr, ns));
+    DIFVM_TRY(upload<V4<double>>(&m->hf_ck64, nullptr, ns));
+    DIFVM_TRY(upload<V4<float>>(&m->hf_sw32, nullptr, ns));
+    DIFVM_TRY(upload<V4<float>>(&m->hf_ck32, nullptr, ns));
+    k_hf_fill<<<blocks_for((int64_t)ns, 256), 256>>>((int)ns, m->hf_fid, m->Sw64, m->ck64, m->Sw32,
+                                                     m->ck32, m->hf_sw64, m->hf_ck64, m->hf_sw32,
+                                                     m->hf_ck32);
+    DIFVM_TRY(check_launch("hf_fill"));
+  }
   DIFVM_CUDA(cudaDeviceSynchronize());
   cudaFree(Sf_d);
   return DIFVM_OK;

@@ -1,7 +1,8 @@
 // Face operators of the message-passing form (Sec. 2.4.1) and their adjoints.
 //
-// Every operator is one cell-centric kernel: thread i walks the cell-CSR row of
-// cell i (faces in ascending id), recomputes the face message of each face
+// Every operator is one cell-centric kernel: thread i walks the row of cell i
+// (faces in ascending id; the forward operators read the half-face layout, in
+// which a row's face records arrive with coalesced loads), recomputes the face message of each face
 // exactly as the owner side does (same operands, same instruction order, so
 // the owner and the neighbour see bitwise the same message), and accumulates
 // sigma * message in registers.  This is the aggregation of Eq. aggregate as a
@@ -20,10 +21,35 @@ constexpr int kBlock = 256;
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Four consecutive half-face slots of a row: their neighbour words and face
+// records arrive with coalesced loads issued before any is used, so each face
+// costs one dependent gather (the neighbour's value).  Slots are consumed in
+// row order (ascending face id), so every sum keeps the CSR order.
+template <typename T, bool SW, bool CK>
+struct HfChunk {
+  int v[4];       // half-face word (see Hf), -1 past the row end or on padding
+  int slot[4];
+  V4<T> sw[4], ck[4];
+};
+template <typename T, bool SW, bool CK>
+__device__ __forceinline__ void hf_chunk(const Hf& H, const HfGeo<T>& G, int base, int k0, int w,
+                                         HfChunk<T, SW, CK>& c) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    c.slot[k] = base + 32 * (k0 + k);
+    c.v[k] = (k0 + k < w) ? ldg(H.nb + c.slot[k]) : -1;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (SW && k0 + k < w) c.sw[k] = ld4(G.sw + c.slot[k]);
+    if (CK && k0 + k < w) c.ck[k] = ld4(G.ck + c.slot[k]);
+  }
+}
+
 // ----------------------------------------------------------- Gauss gradient
 // grad_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green)
 template <typename T, int NC>
-__global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Geo<T> g, int cls,
+__global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg, Geo<T> g, int cls,
                                                        const T* __restrict__ phi,
                                                        const T* __restrict__ phib,
                                                        T* __restrict__ grad) {
@@ -36,37 +62,45 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Geo<T> g, int cls
     pi[c] = ldg(phi + c * nc + i);
     acc[c][0] = acc[c][1] = acc[c][2] = T(0);
   }
-  const int e1 = ldg(t.cptr + i + 1);
-  for (int e = ldg(t.cptr + i); e < e1; ++e) {
-    const int ent = ldg(t.cent + e);
-    const int f = ent >> 1;
-    const V4<T> s = ld4(g.Sw + f);
-    T pf[NC];
-    T sg = T(1);
-    if (f < t.ni) {
-      const int2 on = ldg(t.on + f);
-      const bool nside = ent & 1;
-      const int j = nside ? on.x : on.y;
+  int base, w;
+  hf_row(H, i, base, w);
+  for (int k0 = 0; k0 < w; k0 += 4) {
+    HfChunk<T, true, false> q;
+    hf_chunk<T, true, false>(H, hg, base, k0, w, q);
+    T pj[4][NC];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pj[k][c] = q.v[k] >= 0 ? ldg(phi + c * nc + (q.v[k] >> 1)) : T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int v = q.v[k];
+      if (v == -1) continue;
+      const V4<T> s = q.sw[k];
+      T pf[NC];
+      T sg = T(1);
+      if (v >= 0) {
+        const bool nside = v & 1;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
+          pf[c] = s.w * pO + (T(1) - s.w) * pN;
+        }
+        if (nside) sg = T(-1);
+      } else {
+        const int b = -2 - v;
+        const int kind = face_kind(t, b, cls);
+        if (kind == DIFVM_FACE_EMPTY) continue;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) pf[c] = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
+      }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const T pj = ldg(phi + c * nc + j);
-        const T pO = nside ? pj : pi[c], pN = nside ? pi[c] : pj;
-        pf[c] = s.w * pO + (T(1) - s.w) * pN;
+        const T qv = sg * pf[c];
+        acc[c][0] += qv * s.x;
+        acc[c][1] += qv * s.y;
+        acc[c][2] += qv * s.z;
       }
-      if (nside) sg = T(-1);
-    } else {
-      const int b = f - t.ni;
-      const int kind = face_kind(t, b, cls);
-      if (kind == DIFVM_FACE_EMPTY) continue;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) pf[c] = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const T q = sg * pf[c];
-      acc[c][0] += q * s.x;
-      acc[c][1] += q * s.y;
-      acc[c][2] += q * s.z;
     }
   }
   const T r = ldg(g.rV + i);
@@ -138,7 +172,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss_bwd(Topo t, Geo<T> g, int
 // ------------------------------------------------------------ convection
 // out_i = sum_f sigma m_f phi_f   (Eqs. conv_face_flux, upwind; tie m=0 -> owner)
 template <typename T, int NC, bool UPWIND>
-__global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Geo<T> g, int cls,
+__global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls,
                                                      const T* __restrict__ mf,
                                                      const T* __restrict__ phi,
                                                      const T* __restrict__ phib,
@@ -152,33 +186,45 @@ __global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Geo<T> g, int cls,
     pi[c] = ldg(phi + c * nc + i);
     acc[c] = T(0);
   }
-  const int e1 = ldg(t.cptr + i + 1);
-  for (int e = ldg(t.cptr + i); e < e1; ++e) {
-    const int ent = ldg(t.cent + e);
-    const int f = ent >> 1;
-    const T m = ldg(mf + f);
-    if (f < t.ni) {
-      const int2 on = ldg(t.on + f);
-      const bool nside = ent & 1;
-      const int j = nside ? on.x : on.y;
-      T w = T(0);
-      if (!UPWIND) w = ld4(g.Sw + f).w;
+  int base, w;
+  hf_row(H, i, base, w);
+  for (int k0 = 0; k0 < w; k0 += 4) {
+    HfChunk<T, !UPWIND, false> q;
+    hf_chunk<T, !UPWIND, false>(H, hg, base, k0, w, q);
+    int fk[4];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const T pj = ldg(phi + c * nc + j);
-        const T pO = nside ? pj : pi[c], pN = nside ? pi[c] : pj;
-        const T pf = UPWIND ? (m >= T(0) ? pO : pN) : w * pO + (T(1) - w) * pN;
-        const T F = m * pf;
-        acc[c] += nside ? -F : F;
-      }
-    } else {
-      const int b = f - t.ni;
-      const int kind = face_kind(t, b, cls);
-      if (kind == DIFVM_FACE_EMPTY) continue;
+    for (int k = 0; k < 4; ++k) fk[k] = q.v[k] != -1 ? ldg(H.fid + q.slot[k]) : 0;
+    T mk[4], pj[4][NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const T pf = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
-        acc[c] += m * pf;
+    for (int k = 0; k < 4; ++k) {
+      mk[k] = q.v[k] != -1 ? ldg(mf + fk[k]) : T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pj[k][c] = q.v[k] >= 0 ? ldg(phi + c * nc + (q.v[k] >> 1)) : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int v = q.v[k];
+      if (v == -1) continue;
+      const T m = mk[k];
+      if (v >= 0) {
+        const bool nside = v & 1;
+        const T wf = UPWIND ? T(0) : q.sw[k].w;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
+          const T pf = UPWIND ? (m >= T(0) ? pO : pN) : wf * pO + (T(1) - wf) * pN;
+          const T F = m * pf;
+          acc[c] += nside ? -F : F;
+        }
+      } else {
+        const int b = -2 - v;
+        const int kind = face_kind(t, b, cls);
+        if (kind == DIFVM_FACE_EMPTY) continue;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T pf = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
+          acc[c] += m * pf;
+        }
       }
     }
   }
@@ -262,7 +308,7 @@ __global__ void __launch_bounds__(kBlock) k_div_flux_bwd(Topo t, Geo<T> g, int c
 // --------------------------------------------------------------- diffusion
 // out_i = sum_f sigma gamma [c_f (phi_N - phi_O) + (grad phi)_f . k_f]   (Eq. nonortho_flux)
 template <typename T, int NC, bool NONORTH>
-__global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Geo<T> g, int cls, T gamma,
+__global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Hf H, HfGeo<T> hg, int cls, T gamma,
                                                       const T* __restrict__ phi,
                                                       const T* __restrict__ phib,
                                                       const T* __restrict__ grad,
@@ -279,41 +325,49 @@ __global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Geo<T> g, int cls,
 #pragma unroll
       for (int d = 0; d < 3; ++d) gi[c][d] = ldg(grad + (c * 3 + d) * nc + i);
   }
-  const int e1 = ldg(t.cptr + i + 1);
-  for (int e = ldg(t.cptr + i); e < e1; ++e) {
-    const int ent = ldg(t.cent + e);
-    const int f = ent >> 1;
-    const V4<T> ck = ld4(g.ck + f);
-    if (f < t.ni) {
-      const int2 on = ldg(t.on + f);
-      const bool nside = ent & 1;
-      const int j = nside ? on.x : on.y;
-      T w = T(0);
-      if (NONORTH) w = ld4(g.Sw + f).w;
+  int base, w;
+  hf_row(H, i, base, w);
+  for (int k0 = 0; k0 < w; k0 += 4) {
+    HfChunk<T, NONORTH, true> q;
+    hf_chunk<T, NONORTH, true>(H, hg, base, k0, w, q);
+    T pj[4][NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const T pj = ldg(phi + c * nc + j);
-        const T pO = nside ? pj : pi[c], pN = nside ? pi[c] : pj;
-        T F = ck.x * (pN - pO);
-        if (NONORTH) {
-          T gk = T(0);
-          const T kk[3] = {ck.y, ck.z, ck.w};
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const T gj = ldg(grad + (c * 3 + d) * nc + j);
-            const T gO = nside ? gj : gi[c][d], gN = nside ? gi[c][d] : gj;
-            gk += (w * gO + (T(1) - w) * gN) * kk[d];
+      for (int c = 0; c < NC; ++c) pj[k][c] = q.v[k] >= 0 ? ldg(phi + c * nc + (q.v[k] >> 1)) : T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int v = q.v[k];
+      if (v == -1) continue;
+      const V4<T> ck = q.ck[k];
+      if (v >= 0) {
+        const bool nside = v & 1;
+        const int j = v >> 1;
+        const T wf = NONORTH ? q.sw[k].w : T(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
+          T F = ck.x * (pN - pO);
+          if (NONORTH) {
+            T gk = T(0);
+            const T kk[3] = {ck.y, ck.z, ck.w};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const T gj = ldg(grad + (c * 3 + d) * nc + j);
+              const T gO = nside ? gj : gi[c][d], gN = nside ? gi[c][d] : gj;
+              gk += (wf * gO + (T(1) - wf) * gN) * kk[d];
+            }
+            F += gk;
           }
-          F += gk;
+          F *= gamma;
+          acc[c] += nside ? -F : F;
         }
-        F *= gamma;
-        acc[c] += nside ? -F : F;
-      }
-    } else {
-      const int b = f - t.ni;
-      if (face_kind(t, b, cls) != DIFVM_FACE_FIXED) continue;
+      } else {
+        const int b = -2 - v;
+        if (face_kind(t, b, cls) != DIFVM_FACE_FIXED) continue;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += gamma * (ck.x * (ldg(phib + c * nb + b) - pi[c]));
+        for (int c = 0; c < NC; ++c) acc[c] += gamma * (ck.x * (ldg(phib + c * nb + b) - pi[c]));
+      }
     }
   }
 #pragma unroll
@@ -381,7 +435,7 @@ __global__ void __launch_bounds__(kBlock) k_laplacian_bwd(Topo t, Geo<T> g, int 
 // ---------------------------------------------------------------- LDU apply
 // y_i = D_i x_i + sum_{O(f)=i} U_f x_N + sum_{N(f)=i} L_f x_O   (Eq. Ap_H)
 template <typename T, int NC>
-__global__ void __launch_bounds__(kBlock) k_ldu_apply(Topo t, const T* __restrict__ D,
+__global__ void __launch_bounds__(kBlock) k_ldu_apply(Topo t, Hf H, const T* __restrict__ D,
                                                       const T* __restrict__ L,
                                                       const T* __restrict__ U,
                                                       const T* __restrict__ x,
@@ -393,17 +447,29 @@ __global__ void __launch_bounds__(kBlock) k_ldu_apply(Topo t, const T* __restric
   T acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = d * ldg(x + c * nc + i);
-  const int e1 = ldg(t.cptr + i + 1);
-  for (int e = ldg(t.cptr + i); e < e1; ++e) {
-    const int ent = ldg(t.cent + e);
-    const int f = ent >> 1;
-    if (f >= t.ni) break;  // boundary entries come last
-    const int2 on = ldg(t.on + f);
-    const bool nside = ent & 1;
-    const int j = nside ? on.x : on.y;
-    const T a = nside ? ldg(L + f) : ldg(U + f);
+  int base, w;
+  hf_row(H, i, base, w);
+  for (int k0 = 0; k0 < w; k0 += 4) {
+    int v[4], fk[4];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] += a * ldg(x + c * nc + j);
+    for (int k = 0; k < 4; ++k) {
+      const int slot = base + 32 * (k0 + k);
+      v[k] = (k0 + k < w) ? ldg(H.nb + slot) : -1;
+      fk[k] = (k0 + k < w) ? ldg(H.fid + slot) : 0;
+    }
+    T ak[4], xk[4][NC];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ak[k] = v[k] >= 0 ? ((v[k] & 1) ? ldg(L + fk[k]) : ldg(U + fk[k])) : T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xk[k][c] = v[k] >= 0 ? ldg(x + c * nc + (v[k] >> 1)) : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (v[k] < 0) continue;   // boundary faces and padding carry no off-diagonal entry
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += ak[k] * xk[k][c];
+    }
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) y[c * nc + i] = acc[c];
@@ -469,7 +535,8 @@ template <typename T>
 difvm_status grad_gauss_t(difvm_mesh_t m, int cls, const void* phi, const void* phib,
                           int ncomp, void* grad, cudaStream_t s) {
   DIFVM_NC_SWITCH(ncomp, k_grad_gauss<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                             m->topo(), geo<T>(m), cls, (const T*)phi, (const T*)phib, (T*)grad));
+                             m->topo(), m->hf(), hfgeo<T>(m), geo<T>(m), cls, (const T*)phi,
+                             (const T*)phib, (T*)grad));
   return check_launch("grad_gauss");
 }
 template difvm_status grad_gauss_t<float>(difvm_mesh_t, int, const void*, const void*, int, void*,
@@ -491,11 +558,11 @@ static difvm_status div_flux_t(difvm_mesh_t m, int scheme, int cls, const void* 
                                cudaStream_t s) {
   if (scheme == DIFVM_DIV_UPWIND) {
     DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), geo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               m->topo(), m->hf(), hfgeo<T>(m), cls, (const T*)mf, (const T*)phi,
                                (const T*)phib, (T*)out));
   } else {
     DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), geo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               m->topo(), m->hf(), hfgeo<T>(m), cls, (const T*)mf, (const T*)phi,
                                (const T*)phib, (T*)out));
   }
   return check_launch("div_flux");
@@ -523,12 +590,12 @@ static difvm_status laplacian_t(difvm_mesh_t m, int cls, double gamma, const voi
                                 cudaStream_t s) {
   if (grad) {
     DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), geo<T>(m), cls, (T)gamma, (const T*)phi, (const T*)phib,
-                               (const T*)grad, (T*)out));
+                               m->topo(), m->hf(), hfgeo<T>(m), cls, (T)gamma, (const T*)phi,
+                               (const T*)phib, (const T*)grad, (T*)out));
   } else {
     DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), geo<T>(m), cls, (T)gamma, (const T*)phi, (const T*)phib,
-                               (const T*)nullptr, (T*)out));
+                               m->topo(), m->hf(), hfgeo<T>(m), cls, (T)gamma, (const T*)phi,
+                               (const T*)phib, (const T*)nullptr, (T*)out));
   }
   return check_launch("laplacian");
 }
@@ -550,7 +617,7 @@ difvm_status ldu_apply_t(difvm_mesh_t m, const void* D, const void* L, const voi
   const T* Up = U ? (const T*)U : Lp;
   if (transpose) std::swap(Lp, Up);
   DIFVM_NC_SWITCH(ncomp, k_ldu_apply<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                             m->topo(), (const T*)D, Lp, Up, (const T*)x, (T*)y));
+                             m->topo(), m->hf(), (const T*)D, Lp, Up, (const T*)x, (T*)y));
   return check_launch("ldu_apply");
 }
 template difvm_status ldu_apply_t<float>(difvm_mesh_t, const void*, const void*, const void*,
