@@ -83,7 +83,12 @@ enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
  * triangular solves are sequential along the mesh ordering.  Single-RHS CG on
  * a symmetric matrix of a single mesh only (EINVAL otherwise); the hierarchy
  * is built on the host on first use and kept by the mesh. */
-enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1, DIFVM_PRECOND_AMG = 2 };
+/* DIFVM_PRECOND_AMG_REUSE: as AMG, reusing the coefficient copy and multigrid
+ * operators that the previous AMG solve with the same workspace built; the
+ * caller guarantees the matrix is unchanged (e.g. the pressure matrix of the
+ * second PISO corrector, which depends only on V/D). */
+enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1, DIFVM_PRECOND_AMG = 2,
+       DIFVM_PRECOND_AMG_REUSE = 3 };
 enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };
 enum { DIFVM_NONORTH_MOMENTUM = 1, DIFVM_NONORTH_PRESSURE = 2, DIFVM_NONORTH_ALL = 3 };
 

@@ -585,16 +585,32 @@ __global__ void __launch_bounds__(kKB) k_apcg_rz(int nc, const T* r, const T* z,
 }
 
 // coarsest level: x = A^{-1} r (dense inverse, one block)
+// one warp per row (32 warps): each lane's at most kAmgCoarsest/32 entries of
+// the row are loaded together, then a shuffle tree sums the lanes in a fixed order
 template <typename T>
-__global__ void __launch_bounds__(256) k_amg_coarse(int n, const float* Ainv, const T* r, T* x, const int* done) {
+__global__ void __launch_bounds__(1024) k_amg_coarse(int n, const float* Ainv, const T* r, T* x, const int* done) {
   if (*done) return;
+  constexpr int NJ = kAmgCoarsest / 32;
   __shared__ float rs[kAmgCoarsest];
   for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (float)r[j];
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw) {
+    float a[NJ];
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+      const int j = lane + 32 * q;
+      a[q] = j < n ? Ainv[i * n + j] : 0.f;
+    }
     float s = 0.f;
-    for (int j = 0; j < n; ++j) s += Ainv[j * n + i] * rs[j];   // symmetric: column j = row j
-    x[i] = (T)s;
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+      const int j = lane + 32 * q;
+      s += a[q] * (j < n ? rs[j] : 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[i] = (T)s;
   }
 }
 
@@ -724,7 +740,7 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const T* rD = R.at(R.Ly.rD[l]);
   const T* Lv = fine ? nullptr : R.at(R.Ly.E[l]);   // row-entry values of a coarse level
   if (l == H->nlev - 1) {
-    k_amg_coarse<T><<<1, 256, 0, s>>>(L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
+    k_amg_coarse<T><<<1, 1024, 0, s>>>(L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
     count_launch();
     if (l == 0) {   // a single level: the CG's r.z reduction runs on its own
       k_apcg_rz<T><<<R.G, kKB, 0, s>>>(L.n, r, out, w, first);
@@ -817,9 +833,11 @@ __global__ void k_amg_info(const KState* st, difvm_solve_info* info, int refinem
   *info = o;
 }
 
+// reuse: the ELL values and multigrid operators already in the workspace belong to
+// this same matrix (DIFVM_PRECOND_AMG_REUSE); only the views are set up
 template <typename T>
 static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws, size_t wsbytes,
-                                AmgRun<T>& R, cudaStream_t st) {
+                                AmgRun<T>& R, cudaStream_t st, bool reuse = false) {
   AmgHier* H = nullptr;
   DIFVM_TRY(amg_hier(m, &H));
   R.m = m;
@@ -831,6 +849,10 @@ static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes, R.Ly.total);
   R.G = amg_grid(m);
   T* val = R.at(R.Ly.val);
+  if (reuse) {
+    R.A = Mat<T>{D, m->ell(), val};
+    return DIFVM_OK;
+  }
   if (m->ell_nslots > 0) {
     k_ell_fill<T><<<blocks_for(m->ell_nslots, 256), 256, 0, st>>>((int)m->ell_nslots, m->ell_map, Lo, Lo, val);
     DIFVM_TRY(check_launch("ell_fill"));
@@ -856,7 +878,7 @@ static difvm_status amg_solve_mw(difvm_mesh* m, const difvm_solve_opts* o, const
                                  const T* b, T* x, void* ws, size_t wsbytes, difvm_solve_info* info,
                                  cudaStream_t st) {
   AmgRun<T> R;
-  DIFVM_TRY(amg_prepare<T>(m, D, Lo, ws, wsbytes, R, st));
+  DIFVM_TRY(amg_prepare<T>(m, D, Lo, ws, wsbytes, R, st, o->precond == DIFVM_PRECOND_AMG_REUSE));
   KWork w = amg_work_t(R, 0, o->max_iter > 0 ? o->max_iter : 1000, o->tol_rel, o->tol_abs);
   DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
   const int chunk = o->check_every > 0 ? o->check_every : 8;
@@ -1000,7 +1022,7 @@ static difvm_status amg_mixed_mw(difvm_mesh* m, const difvm_solve_opts* o, const
                                  const double* b64, double* x64, void* ws, size_t wsbytes,
                                  difvm_solve_info* info, cudaStream_t st) {
   AmgRun<float> R;
-  DIFVM_TRY(amg_prepare<float>(m, D, Lo, ws, wsbytes, R, st));
+  DIFVM_TRY(amg_prepare<float>(m, D, Lo, ws, wsbytes, R, st, o->precond == DIFVM_PRECOND_AMG_REUSE));
   if (R.Ly.total + 3 * up256a((size_t)m->nc * 8) > wsbytes)
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes,
                      R.Ly.total + 3 * up256a((size_t)m->nc * 8));

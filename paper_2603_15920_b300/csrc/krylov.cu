@@ -1529,7 +1529,7 @@ template <typename T>
 static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const void* D, const void* L,
                             const void* U, const void* b, void* x, int ncomp, void* ws,
                             size_t wsbytes, difvm_solve_info* info, cudaStream_t st) {
-  if (o->precond == DIFVM_PRECOND_AMG) {
+  if (o->precond == DIFVM_PRECOND_AMG || o->precond == DIFVM_PRECOND_AMG_REUSE) {
     if (o->method != DIFVM_PCG || ncomp != 1 || U || m->seg)
       return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves single-RHS CG on a "
                                      "symmetric matrix of a single (not batched) mesh");
@@ -1605,7 +1605,7 @@ extern "C" size_t difvm_krylov_opts_workspace_bytes(difvm_mesh_t m, difvm_prec p
                                                     const difvm_solve_opts* o, int ncomp) {
   if (!m || !o || ncomp < 1 || ncomp > 3) return 0;
   const bool refine = prec == DIFVM_F32 && o->refine_max > 0;
-  if (o->precond == DIFVM_PRECOND_AMG) {
+  if (o->precond == DIFVM_PRECOND_AMG || o->precond == DIFVM_PRECOND_AMG_REUSE) {
     if (o->method != DIFVM_PCG || ncomp != 1 || m->seg) return 0;
     return amg_workspace_bytes(m, refine ? 4 : (prec == DIFVM_F64 ? 8 : 4));
   }
@@ -1624,7 +1624,7 @@ extern "C" difvm_status difvm_krylov_solve_refine(difvm_mesh_t m, const difvm_so
                                                   size_t wsbytes, difvm_solve_info* info, void* stream) {
   DIFVM_TRY(check_solve(m, DIFVM_F32, o, ncomp, D, L));
   if (m->seg) return set_error(DIFVM_EINVAL, "difvm_krylov_solve_refine: not available on batched meshes");
-  if (o->precond == DIFVM_PRECOND_AMG) {
+  if (o->precond == DIFVM_PRECOND_AMG || o->precond == DIFVM_PRECOND_AMG_REUSE) {
     if (o->method != DIFVM_PCG || ncomp != 1 || U)
       return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves single-RHS CG on a symmetric matrix");
     if (!b64 || !x64) return set_error(DIFVM_EINVAL, "null vector");

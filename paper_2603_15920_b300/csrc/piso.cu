@@ -927,6 +927,10 @@ __global__ void k_tape_wk_in(int n_out, const double* wk, double* pc_in) {
 }
 
 // ---------------------------------------------------------------- driver
+static inline bool amg_opts(const difvm_solve_opts& o) {
+  return o.precond == DIFVM_PRECOND_AMG || o.precond == DIFVM_PRECOND_AMG_REUSE;
+}
+
 // Tape of one recorded step (byte offsets, each section 256-byte aligned):
 // U^n [3][nc], U_s [n_corr+1][3][nc] (U_0 = predicted velocity, U_s after
 // corrector s), p_s [n_corr+1][nc] (p_0 = p^n), phi^n [nf], p_b after the
@@ -1036,19 +1040,23 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     k_p_cells<T><<<Bc, kPB, 0, st>>>(t, phiH, af, no, pb, h->pin, h->pinflag, Dp, bp);
     DIFVM_TRY(check_launch("p_cells"));
     difvm_solve_info* si = h->sinfo + (3 + std::min(corr, 3)) * h->nk;
+    // the pressure matrix depends only on V/D: correctors after the first reuse the
+    // multigrid operators the first one built
+    difvm_solve_opts sp = o.solve_p;
+    if (corr > 0 && amg_opts(sp)) sp.precond = DIFVM_PRECOND_AMG_REUSE;
     difvm_status s;
     if (h->mixed) {
       k_to64<T><<<Bc, kPB, 0, st>>>(nc, bp, h->b64);
       k_to64<T><<<Bc, kPB, 0, st>>>(nc, p, h->p64);
       DIFVM_TRY(check_launch("to64"));
       count_launch();
-      s = difvm_krylov_solve_refine(m, &o.solve_p, (const float*)Dp, (const float*)Lp, nullptr,
+      s = difvm_krylov_solve_refine(m, &sp, (const float*)Dp, (const float*)Lp, nullptr,
                                     h->b64, h->p64, 1, h->wsp, h->wsp_bytes, si, st);
       k_from64<T><<<Bc, kPB, 0, st>>>(nc, h->p64, p);
       DIFVM_TRY(check_launch("from64"));
     } else {
       difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
-      s = difvm_krylov_solve(m, pr, &o.solve_p, Dp, Lp, nullptr, bp, p, 1, h->wsp, h->wsp_bytes, si, st);
+      s = difvm_krylov_solve(m, pr, &sp, Dp, Lp, nullptr, bp, p, 1, h->wsp, h->wsp_bytes, si, st);
     }
     if (s == DIFVM_EINVAL || s == DIFVM_ECUDA) return s;
     worst = std::max(worst, (int)s);
@@ -1138,9 +1146,9 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     return set_error(DIFVM_EINVAL, "bad momentum solver");
   if (o->solve_p.method != DIFVM_PCG && o->solve_p.method != DIFVM_BICGSTAB)
     return set_error(DIFVM_EINVAL, "bad pressure solver");
-  if (o->solve_U.precond == DIFVM_PRECOND_AMG)
+  if (amg_opts(o->solve_U))
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves the pressure CG only");
-  if (o->solve_p.precond == DIFVM_PRECOND_AMG && (o->solve_p.method != DIFVM_PCG || m->seg))
+  if (amg_opts(o->solve_p) && (o->solve_p.method != DIFVM_PCG || m->seg))
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner needs CG on a single (not batched) mesh");
   for (int k = 0; k < o->n_out; ++k) {
     int p = o->wk_patch[k];
@@ -1280,11 +1288,15 @@ static difvm_status adj_psolve(difvm_piso* h, const T* rhs, int s, T* scratch, T
   difvm_mesh* m = h->m;
   const int nc = m->nc;
   const unsigned Bc = blocks_for(nc, kPB);
+  // the reverse sweep recomputed the step's pressure matrix: its first adjoint
+  // solve (the last corrector's) builds the multigrid operators, the others reuse them
+  difvm_solve_opts sp = h->o.solve_p;
+  if (s < h->o.n_corr - 1 && amg_opts(sp)) sp.precond = DIFVM_PRECOND_AMG_REUSE;
   if (h->mixed) {
     double* x = (double*)h->a_lamw + (size_t)s * nc;
     k_to64<T><<<Bc, kPB, 0, st>>>(nc, rhs, h->b64);
     DIFVM_TRY(check_launch("to64"));
-    difvm_status r = difvm_krylov_solve_refine(m, &h->o.solve_p, (const float*)h->Dp,
+    difvm_status r = difvm_krylov_solve_refine(m, &sp, (const float*)h->Dp,
                                                (const float*)h->Lp, nullptr, h->b64, x, 1, h->wsp,
                                                h->wsp_bytes, si, st);
     if (r == DIFVM_EINVAL || r == DIFVM_ECUDA) return r;
@@ -1296,7 +1308,7 @@ static difvm_status adj_psolve(difvm_piso* h, const T* rhs, int s, T* scratch, T
   T* x = (T*)h->a_lamw + (size_t)s * nc;
   difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
   *lam = x;
-  return difvm_krylov_solve(m, pr, &h->o.solve_p, h->Dp, h->Lp, nullptr, rhs, x, 1, h->wsp,
+  return difvm_krylov_solve(m, pr, &sp, h->Dp, h->Lp, nullptr, rhs, x, 1, h->wsp,
                             h->wsp_bytes, si, st);
 }
 
