@@ -18,7 +18,8 @@
 //   V-cycle: two damped-Jacobi sweeps before and after the coarse correction,
 //     the coarse correction scaled by kAmgScale, the coarsest level solved
 //     with a dense inverse (Gauss-Jordan in one block, FP32, symmetrised);
-//   mixed precision: CG in FP64 around the FP32 V-cycle (no refinement sweeps).
+//   mixed precision: CG with FP64 accuracy (float-float vectors) around the FP32
+//     V-cycle (no refinement sweeps).
 //
 // The V-cycle is a fixed symmetric positive-definite linear operator, so CG
 // keeps its guarantees; it changes the iteration count, not the solution.
@@ -320,8 +321,8 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
 size_t amg_workspace_bytes(difvm_mesh* m, size_t elt) {
   AmgHier* H = nullptr;
   if (amg_hier(m, &H) != DIFVM_OK) return 0;
-  // + FP64 r, p, q of the mixed-precision form (FP64 CG, FP32 V-cycle)
-  return amg_layout(m, H, elt).total + 3 * up256a((size_t)m->nc * 8);
+  // + the float-float x, r (low part), p, q of the mixed-precision form
+  return amg_layout(m, H, elt).total + 7 * up256a((size_t)m->nc * 4);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -908,14 +909,52 @@ template difvm_status amg_solve<double>(difvm_mesh*, const difvm_solve_opts*, co
                                         cudaStream_t);
 
 // ------------------------------------------------------ mixed precision
-// CG in FP64 (x, r, p, q, inner products; the SpMV reads the FP32 coefficients,
-// which are exact in FP64) preconditioned by the FP32 V-cycle: the update
-// kernel hands the V-cycle an FP32 copy of r, and p = z + beta p takes the FP32
-// z.  The preconditioner's precision only affects the convergence rate, so the
-// solve reaches FP64 tolerances without refinement sweeps or restarts.
+// CG with FP64 accuracy around the FP32 V-cycle.  The preconditioner's
+// precision only affects the convergence rate, so the solve reaches FP64
+// tolerances without refinement sweeps or restarts.  The CG vectors x, r, p, q
+// are float-float pairs (hi, lo: about 48 significant bits) updated with
+// error-free transformations (TwoSum: Knuth; TwoProduct by fma), so the B300's
+// FP32 pipes carry what FP64 arithmetic would (its FP64 rate is ~1/64 of
+// FP32); inner products are reduced in FP64.  The initial residual b - A x and
+// the returned x are FP64; the FP32 coefficients are exact in either form.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.h, y.h);
+  return ff_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ FF ff_mul_f(FF x, float a) {            // x * a
+  const float p = __fmul_rn(x.h, a);
+  const float e = __fmaf_rn(x.h, a, -p);
+  return ff_fast_two_sum(p, __fmaf_rn(x.l, a, e));
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_of(double d) {
+  const float h = (float)d;
+  return FF{h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double ff_dbl(FF x) { return (double)x.h + (double)x.l; }
+
+// r = b - A x in FP64 (stored as pairs), x as pairs; bb, rr
 template <int MW>
-__global__ void __launch_bounds__(kKB) k_mcg_init(Topo t, Mat<float> A, const double* b, const double* x,
-                                                  double* r, float* r32, KWork w) {
+__global__ void __launch_bounds__(kKB) k_fcg_init(Topo t, Mat<float> A, const double* b, const double* x,
+                                                  float* xh, float* xl, float* rh, float* rl, KWork w) {
   const int nc = t.nc;
   double bb = 0.0, rr = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
@@ -933,8 +972,11 @@ __global__ void __launch_bounds__(kKB) k_mcg_init(Topo t, Mat<float> A, const do
       for (int k = 0; k < wd; ++k) y = fma((double)A.val[base + step * k], x[A.E.col[base + step * k]], y);
     }
     const double ri = b[i] - y;
-    r[i] = ri;
-    r32[i] = (float)ri;
+    const FF rf = ff_of(ri), xf = ff_of(x[i]);
+    rh[i] = rf.h;
+    rl[i] = rf.l;
+    xh[i] = xf.h;
+    xl[i] = xf.l;
     bb = fma(b[i], b[i], bb);
     rr = fma(ri, ri, rr);
   }
@@ -952,49 +994,58 @@ __global__ void __launch_bounds__(kKB) k_mcg_init(Topo t, Mat<float> A, const do
   if (!isfinite(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
 }
 
-// q = A p (FP64 arithmetic, FP32 coefficients); alpha = rz / (p.q)
+// q = A p (pairs; FP32 coefficients); alpha = rz / (p.q)
 template <int MW>
-__global__ void __launch_bounds__(kKB) k_mcg_spmv(Topo t, Mat<float> A, const double* p, double* q, KWork w) {
+__global__ void __launch_bounds__(kKB) k_fcg_spmv(Topo t, Mat<float> A, const float* ph, const float* pl,
+                                                  float* qh, float* ql, KWork w) {
   if (w.st[0].done) return;
   const int nc = t.nc;
-  double pq = 0.0;
+  FF pq{0.f, 0.f};
+  auto pv = [&](int j) { return FF{__ldg(ph + j), __ldg(pl + j)}; };
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    double y = (double)__ldg(A.D + i) * p[i];
+    const FF pi = pv(i);
+    FF y = ff_mul_f(pi, __ldg(A.D + i));
     if (MW == 4 && A.E.W == 4) {
       const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(A.val) + i);
-      y = fma((double)a4.x, p[j4.x], y);
-      y = fma((double)a4.y, p[j4.y], y);
-      y = fma((double)a4.z, p[j4.z], y);
-      y = fma((double)a4.w, p[j4.w], y);
+      const FF p0 = pv(j4.x), p1 = pv(j4.y), p2 = pv(j4.z), p3 = pv(j4.w);
+      y = ff_add(y, ff_mul_f(p0, a4.x));
+      y = ff_add(y, ff_mul_f(p1, a4.y));
+      y = ff_add(y, ff_mul_f(p2, a4.z));
+      y = ff_add(y, ff_mul_f(p3, a4.w));
     } else {
       int base, step, wd;
       ell_row(A.E, i, base, step, wd);
       for (int k = 0; k < wd; ++k)
-        y = fma((double)__ldg(A.val + base + step * k), p[__ldg(A.E.col + base + step * k)], y);
+        y = ff_add(y, ff_mul_f(pv(__ldg(A.E.col + base + step * k)), __ldg(A.val + base + step * k)));
     }
-    q[i] = y;
-    pq = fma(p[i], y, pq);
+    qh[i] = y.h;
+    ql[i] = y.l;
+    pq = ff_add(pq, ff_mul(pi, y));
   }
-  double v[1] = {pq}, tot[1];
+  double v[1] = {ff_dbl(pq)}, tot[1];
   if (!grid_sum<1>(w, v, tot) || threadIdx.x != 0) return;
   w.st[0].alpha = w.st[0].rz / tot[0];
 }
 
-// x += alpha p; r -= alpha q; r32 = (float) r; rr; convergence
-__global__ void __launch_bounds__(kKB) k_mcg_update(int nc, const double* p, const double* q, double* x,
-                                                    double* r, float* r32, KWork w) {
+// x += alpha p; r -= alpha q (pairs); rr; convergence
+__global__ void __launch_bounds__(kKB) k_fcg_update(int nc, const float* ph, const float* pl, const float* qh,
+                                                    const float* ql, float* xh, float* xl, float* rh, float* rl,
+                                                    KWork w) {
   if (w.st[0].done) return;
-  const double al = w.st[0].alpha;
-  double rr = 0.0;
+  const FF al = ff_of(w.st[0].alpha), nal = ff_of(-w.st[0].alpha);
+  FF rr{0.f, 0.f};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    x[i] = fma(al, p[i], x[i]);
-    const double ri = fma(-al, q[i], r[i]);
-    r[i] = ri;
-    r32[i] = (float)ri;
-    rr = fma(ri, ri, rr);
+    const FF p{ph[i], pl[i]}, q{qh[i], ql[i]};
+    const FF x = ff_add(FF{xh[i], xl[i]}, ff_mul(p, al));
+    const FF r = ff_add(FF{rh[i], rl[i]}, ff_mul(q, nal));
+    xh[i] = x.h;
+    xl[i] = x.l;
+    rh[i] = r.h;
+    rl[i] = r.l;
+    rr = ff_add(rr, ff_mul(r, r));
   }
-  double v[1] = {rr}, tot[1];
+  double v[1] = {ff_dbl(rr)}, tot[1];
   if (!grid_sum<1>(w, v, tot) || threadIdx.x != 0) return;
   KState& s = w.st[0];
   s.iters += 1;
@@ -1004,17 +1055,22 @@ __global__ void __launch_bounds__(kKB) k_mcg_update(int nc, const double* p, con
   if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; }
 }
 
-// p = z + beta p (first: p = z); x = 0 for a zero right-hand side
-__global__ void __launch_bounds__(kKB) k_mcg_p(int nc, const float* z, double* p, double* x, KWork w,
-                                               int first) {
-  if (w.st[0].zero_rhs) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) x[i] = 0.0;
-    return;
-  }
+// p = z + beta p (first: p = z)
+__global__ void __launch_bounds__(kKB) k_fcg_p(int nc, const float* z, float* ph, float* pl, KWork w, int first) {
   if (w.st[0].done) return;
-  const double be = w.st[0].beta;
+  const FF be = ff_of(w.st[0].beta);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const FF p = first ? FF{z[i], 0.f} : ff_add(ff_mul(FF{ph[i], pl[i]}, be), FF{z[i], 0.f});
+    ph[i] = p.h;
+    pl[i] = p.l;
+  }
+}
+
+// x64 = xh + xl (0 for a zero right-hand side)
+__global__ void k_fcg_final(int nc, const float* xh, const float* xl, double* x, KWork w) {
+  const bool z = w.st[0].zero_rhs;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-    p[i] = first ? (double)z[i] : fma(be, p[i], (double)z[i]);
+    x[i] = z ? 0.0 : (double)xh[i] + (double)xl[i];
 }
 
 template <int MW>
@@ -1023,29 +1079,29 @@ static difvm_status amg_mixed_mw(difvm_mesh* m, const difvm_solve_opts* o, const
                                  difvm_solve_info* info, cudaStream_t st) {
   AmgRun<float> R;
   DIFVM_TRY(amg_prepare<float>(m, D, Lo, ws, wsbytes, R, st, o->precond == DIFVM_PRECOND_AMG_REUSE));
-  if (R.Ly.total + 3 * up256a((size_t)m->nc * 8) > wsbytes)
-    return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes,
-                     R.Ly.total + 3 * up256a((size_t)m->nc * 8));
-  double* r = (double*)(R.ws + R.Ly.total);
-  double* p = r + up256a((size_t)m->nc * 8) / 8;
-  double* q = p + up256a((size_t)m->nc * 8) / 8;
-  float* r32 = R.vec(0);
+  const size_t vb = up256a((size_t)m->nc * 4);
+  if (R.Ly.total + 7 * vb > wsbytes)
+    return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes, R.Ly.total + 7 * vb);
+  float* base = (float*)(R.ws + R.Ly.total);
+  float *xh = base, *xl = base + vb / 4, *rl = base + 2 * vb / 4, *ph = base + 3 * vb / 4;
+  float *pl = base + 4 * vb / 4, *qh = base + 5 * vb / 4, *ql = base + 6 * vb / 4;
+  float* rh = R.vec(0);    // the V-cycle's input
   float* z32 = R.vec(3);
   KWork w = amg_work_t(R, 0, o->max_iter > 0 ? o->max_iter : 1000, o->tol_rel, o->tol_abs);
   DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, 16, st));
   const int nc = m->nc, G = R.G;
-  k_mcg_init<MW><<<G, kKB, 0, st>>>(R.t, R.A, b64, x64, r, r32, w);
-  DIFVM_TRY(check_launch("mcg_init"));
-  amg_vcycle(R, 0, r32, z32, w, 1, st);
-  k_mcg_p<<<G, kKB, 0, st>>>(nc, z32, p, x64, w, 1);
-  DIFVM_TRY(check_launch("mcg_p"));
+  k_fcg_init<MW><<<G, kKB, 0, st>>>(R.t, R.A, b64, x64, xh, xl, rh, rl, w);
+  DIFVM_TRY(check_launch("fcg_init"));
+  amg_vcycle(R, 0, rh, z32, w, 1, st);
+  k_fcg_p<<<G, kKB, 0, st>>>(nc, z32, ph, pl, w, 1);
+  DIFVM_TRY(check_launch("fcg_p"));
   auto iter = [&](cudaStream_t s) {
     prof_before(DIFVM_PROF_PCG_SPMV, s);
-    k_mcg_spmv<MW><<<G, kKB, 0, s>>>(R.t, R.A, p, q, w);
+    k_fcg_spmv<MW><<<G, kKB, 0, s>>>(R.t, R.A, ph, pl, qh, ql, w);
     prof_after(DIFVM_PROF_PCG_SPMV, s);
-    k_mcg_update<<<G, kKB, 0, s>>>(nc, p, q, x64, r, r32, w);
-    amg_vcycle(R, 0, r32, z32, w, 0, s);
-    k_mcg_p<<<G, kKB, 0, s>>>(nc, z32, p, x64, w, 0);
+    k_fcg_update<<<G, kKB, 0, s>>>(nc, ph, pl, qh, ql, xh, xl, rh, rl, w);
+    amg_vcycle(R, 0, rh, z32, w, 0, s);
+    k_fcg_p<<<G, kKB, 0, s>>>(nc, z32, ph, pl, w, 0);
     count_launch(); count_launch(); count_launch();
   };
   int* counter = reinterpret_cast<int*>(w.ticket) + 1;
@@ -1064,12 +1120,14 @@ static difvm_status amg_mixed_mw(difvm_mesh* m, const difvm_solve_opts* o, const
     KState hs;
     for (int it = 0; it < w.maxit + chunk; it += chunk) {
       for (int k = 0; k < chunk; ++k) iter(st);
-      DIFVM_TRY(check_error("mcg_iter"));
+      DIFVM_TRY(check_error("fcg_iter"));
       DIFVM_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
       DIFVM_CUDA(cudaStreamSynchronize(st));
       if (hs.done) break;
     }
   }
+  k_fcg_final<<<G, kKB, 0, st>>>(nc, xh, xl, x64, w);
+  DIFVM_TRY(check_launch("fcg_final"));
   if (info) {
     k_amg_info<<<1, 32, 0, st>>>(w.st, info, 0, -1);
     DIFVM_TRY(check_launch("amg_info"));
