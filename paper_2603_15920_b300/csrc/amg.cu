@@ -37,6 +37,7 @@ constexpr double kAmgScale = 1.8;   // over-correction of the coarse-grid correc
 constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 x 32)
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAB = 256;            // threads per block of the AMG kernels
+constexpr int kAmgBigLevel = 100000;   // from this size a level's sweeps are bandwidth-bound
 
 // One level as the kernels see it.  Level 0 is the mesh (its SpMV uses the
 // sliced ELL); on coarser levels `on` / `cptr` / `cent` hold the level's own
@@ -287,6 +288,8 @@ struct AmgLayout {
 
 static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
 
+// the CG kernels and the level-0 sweep with r.z: grid-stride, one wave (their
+// grid reductions finish once instead of once per wave of blocks)
 static int amg_grid(const difvm_mesh* m) {
   return std::max(1, std::min((int)blocks_for(m->nc, kKB), m->num_sms * 4));
 }
@@ -310,8 +313,8 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
   const int nco = H->lev[H->nlev - 1].n;
   A.inv = take((size_t)nco * nco * sizeof(float));
   A.st = take(4 * sizeof(KState));
-  // partials: the CG kernels use amg_grid blocks, the fine-level smoothing one block per kAB cells
-  const size_t nblk = std::max<size_t>(amg_grid(m), blocks_for(m->nc, kAB));
+  // partials: one per block of the CG kernels and of the level-0 smoothing with r.z
+  const size_t nblk = amg_grid(m);
   A.part = take(nblk * kMaxParts * sizeof(double));
   A.ticket = take(256);
   A.total = o;
@@ -446,12 +449,18 @@ __global__ void __launch_bounds__(512) k_amg_dense_inv(AmgLev L, const T* D, con
   }
 }
 
-// y_i = (A x)_i on level 0 (sliced ELL) or a coarser level (face CSR); x given
-// by a functor so that smoothed / prolongated values can be formed on the fly
-template <typename T, bool FINE, class XF>
-__device__ __forceinline__ T amg_row(const Mat<T>& A, const AmgLev& L, const T* D, const T* Lv, int i,
-                                     XF x) {
-  if (FINE) {
+// (A x)_i of row i.  TPR == 1: level 0, one thread per row, the mesh's ELL.
+// TPR > 1: a coarser level's sliced ELL, TPR lanes per row (lane t takes
+// slots t, t + TPR, ..., two in flight per pass), so the dependent loads of a
+// row (slice offset, column, gathered value) take a few round trips whatever
+// its width; the lanes are summed by a fixed xor tree and every lane gets the
+// total.  x is a functor so that smoothed values can be formed on the fly.
+// `ok` = the row exists; all lanes of a warp must call it (shuffles).
+template <typename T, int TPR, class XF>
+__device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* D, const T* Lv, int i, int t,
+                                     bool ok, XF x) {
+  if constexpr (TPR == 1) {
+    if (!ok) return T(0);
     T y = __ldg(A.D + i) * x(i);
     if (A.E.W == 4) {
       const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
@@ -467,108 +476,128 @@ __device__ __forceinline__ T amg_row(const Mat<T>& A, const AmgLev& L, const T* 
     ell_row(A.E, i, base, step, w);
     for (int k = 0; k < w; ++k) y += __ldg(A.val + base + step * k) * x(__ldg(A.E.col + base + step * k));
     return y;
+  } else {
+    T y = T(0);
+    if (ok) {
+      const int o0 = __ldg(L.soff + (i >> 5));
+      const int w = (__ldg(L.soff + (i >> 5) + 1) - o0) >> 5;
+      int o = o0 + (i & 31) + 32 * t;
+      if (t == 0) y = D[i] * x(i);
+      int k = t;
+      for (; k + TPR < w; k += 2 * TPR, o += 64 * TPR) {
+        const int c0 = __ldg(L.ecol + o), c1 = __ldg(L.ecol + o + 32 * TPR);
+        const T v0 = Lv[o], v1 = Lv[o + 32 * TPR];   // Lv: ELL values
+        const T x0 = x(c0), x1 = x(c1);
+        y += v0 * x0;
+        y += v1 * x1;
+      }
+      if (k < w) y += Lv[o] * x(__ldg(L.ecol + o));
+    }
+#pragma unroll
+    for (int d = TPR / 2; d > 0; d >>= 1) y += __shfl_xor_sync(0xffffffffu, y, d);
+    return y;
   }
-  T y = D[i] * x(i);
-  int o = __ldg(L.soff + (i >> 5)) + (i & 31);
-  const int w = (__ldg(L.soff + (i >> 5) + 1) - __ldg(L.soff + (i >> 5))) >> 5;
-  // four entries per pass: their column, value and gathered loads are all in
-  // flight together (a coarse row has ~10-25 entries); sums stay in slot order
-  int k = 0;
-  for (; k + 4 <= w; k += 4, o += 128) {
-    const int c0 = __ldg(L.ecol + o), c1 = __ldg(L.ecol + o + 32), c2 = __ldg(L.ecol + o + 64),
-              c3 = __ldg(L.ecol + o + 96);
-    const T v0 = Lv[o], v1 = Lv[o + 32], v2 = Lv[o + 64], v3 = Lv[o + 96];   // Lv: ELL values
-    const T x0 = x(c0), x1 = x(c1), x2 = x(c2), x3 = x(c3);
-    y += v0 * x0;
-    y += v1 * x1;
-    y += v2 * x2;
-    y += v3 * x3;
-  }
-  for (; k < w; ++k, o += 32) y += Lv[o] * x(__ldg(L.ecol + o));
-  return y;
 }
 
 // pre-smoothing from zero, two sweeps: x1 = w rD r, y = x1 + w rD (r - A x1)
-template <typename T, bool FINE>
+template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                  const T* r, T* y, const int* done) {
   if (*done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
+  const bool ok = i < L.n;
   const T w = (T)kAmgOmega;
   auto x1 = [&](int j) { return w * rD[j] * r[j]; };
-  y[i] = x1(i) + w * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, x1));
+  const T ax = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, x1);
+  if (ok && t == 0) y[i] = x1(i) + w * rD[i] * (r[i] - ax);
 }
 
 // residual after pre-smoothing: res = r - A y
-template <typename T, bool FINE>
+template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* D, const T* Lv, const T* r,
                                                    const T* y, T* res, const int* done) {
   if (*done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
+  const bool ok = i < L.n;
   auto xy = [&](int j) { return y[j]; };
-  res[i] = r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xy);
+  const T ay = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, xy);
+  if (ok && t == 0) res[i] = r[i] - ay;
 }
 
-// restriction: rc_K = sum of res over the cells of K, in ascending cell order
-template <typename T>
+// restriction: rc_K = sum of res over the cells of K.  RL == 1: one thread
+// per K, four children in flight; RL > 1: RL lanes per K, each summing its
+// children in ascending order, then a fixed xor tree.
+template <typename T, int RL>
 __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T* res, T* rc, const int* done) {
   if (*done) return;
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K >= n1) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, K = g / RL, t = g % RL;
   T s = T(0);
-  int c = L.ch_ptr[K];
-  const int c1 = L.ch_ptr[K + 1];
-  for (; c + 4 <= c1; c += 4) {   // children in flight together, summed in order
-    const int i0 = L.ch_idx[c], i1 = L.ch_idx[c + 1], i2 = L.ch_idx[c + 2], i3 = L.ch_idx[c + 3];
-    const T r0 = res[i0], r1 = res[i1], r2 = res[i2], r3 = res[i3];
-    s += r0;
-    s += r1;
-    s += r2;
-    s += r3;
+  if (K < n1) {
+    const int c1 = L.ch_ptr[K + 1];
+    int c = L.ch_ptr[K] + t;
+    if (RL == 1) {
+      for (; c + 4 <= c1; c += 4) {
+        const int i0 = L.ch_idx[c], i1 = L.ch_idx[c + 1], i2 = L.ch_idx[c + 2], i3 = L.ch_idx[c + 3];
+        const T r0 = res[i0], r1 = res[i1], r2 = res[i2], r3 = res[i3];
+        s += r0;
+        s += r1;
+        s += r2;
+        s += r3;
+      }
+    }
+    for (; c < c1; c += RL) s += res[L.ch_idx[c]];
   }
-  for (; c < c1; ++c) s += res[L.ch_idx[c]];
-  rc[K] = s;
+#pragma unroll
+  for (int d = RL / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (K < n1 && t == 0) rc[K] = s;
 }
 
 // coarse correction and the first post-smoothing sweep: z = y + s P xc (formed
 // on the fly), out = z + w rD (r - A z)
-template <typename T, bool FINE>
+template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                    const T* r, const T* y, const T* xc, T* out,
                                                    const int* done) {
   if (*done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
+  const bool ok = i < L.n;
   const T w = (T)kAmgOmega, sc = (T)kAmgScale;
   auto z = [&](int j) { return y[j] + sc * xc[L.agg[j]]; };
-  out[i] = z(i) + w * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, z));
+  const T az = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, z);
+  if (ok && t == 0) out[i] = z(i) + w * rD[i] * (r[i] - az);
 }
 
-// second post-smoothing sweep: v = u + w rD (r - A u).  On level 0 of a CG
-// iteration it also forms r.z: the last block sets beta (first = 1: rz only).
-template <typename T, bool FINE, bool DOT>
-__global__ void __launch_bounds__(kKB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
-                                                   const T* r, const T* u, T* v, KWork w, int first) {
+// second post-smoothing sweep: v = u + w rD (r - A u)
+template <typename T, int TPR>
+__global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
+                                                   const T* r, const T* u, T* v, const int* done) {
+  if (*done) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
+  const bool ok = i < L.n;
+  const T om = (T)kAmgOmega;
+  auto xu = [&](int j) { return u[j]; };
+  const T au = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, xu);
+  if (ok && t == 0) v[i] = u[i] + om * rD[i] * (r[i] - au);
+}
+
+// the same sweep on level 0 of a CG iteration (grid-stride), also forming
+// r.v: the last block sets beta (first = 1: rz only)
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_amg_post2_dot(AmgLev L, Mat<T> A, const T* rD, const T* r, const T* u,
+                                                       T* v, KWork w, int first) {
   if (w.st[0].done) return;
   const T om = (T)kAmgOmega;
   DotAcc<T> rz;
   auto xu = [&](int j) { return u[j]; };
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
-    const T vi = u[i] + om * rD[i] * (r[i] - amg_row<T, FINE>(A, L, D, Lv, i, xu));
+    const T vi = u[i] + om * rD[i] * (r[i] - lev_row<T, 1>(A, L, nullptr, nullptr, i, 0, true, xu));
     v[i] = vi;
-    if (DOT) rz.add(r[i], vi);
+    rz.add(r[i], vi);
   }
-  if (!DOT) return;
   double tv[1] = {rz.get()}, tot[1];
   if (!grid_sum<1>(w, tv, tot) || threadIdx.x != 0) return;
   KState& s = w.st[0];
-  if (first) {
-    s.beta = 0.0;
-  } else {
-    s.beta = tot[0] / s.rz;
-  }
+  s.beta = first ? 0.0 : tot[0] / s.rz;
   s.rz = tot[0];
 }
 
@@ -729,6 +758,43 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
   return check_launch("amg_dense_inv");
 }
 
+// lanes per row of a level's sweeps: one on level 0 (the mesh's ELL); on a
+// coarser level (never one lane: lev_row<T, 1> reads the mesh's ELL) two for
+// large levels, 4-8 for small levels, whose sweeps are latency-bound chains of
+// dependent loads (measured on the 1.6M-cell Kuhn mesh: 2 lanes on its
+// 327k-row level 1 beat 4 and 8 by 2-7% of the step)
+static int amg_tpr(const AmgLev& L, int l) {
+  if (l == 0) return 1;
+  if (L.n >= kAmgBigLevel) return 2;
+  return L.nslots > 8 * L.n ? 8 : 4;
+}
+
+template <typename T, int TPR>
+static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, const T* D, const T* rD,
+                       const T* Lv, const T* r, T* y, T* u, T* rc, T* xc, T* out, const KWork& w, int first,
+                       int down, cudaStream_t s) {
+  const int* done = &w.st[0].done;
+  const unsigned B = blocks_for((int64_t)L.n * TPR, kAB);
+  if (down) {
+    k_amg_pre<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
+    if (TPR == 1) prof_before(DIFVM_PROF_AMG_RESID, s);
+    k_amg_resid<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
+    if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
+    if (L1.n >= kAmgBigLevel / 4)
+      k_amg_restrict<T, 1><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, u, rc, done);
+    else
+      k_amg_restrict<T, 8><<<blocks_for((int64_t)L1.n * 8, kAB), kAB, 0, s>>>(L1.n, L, u, rc, done);
+    count_launch(); count_launch(); count_launch();
+    return;
+  }
+  k_amg_post1<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
+  if (TPR == 1)
+    k_amg_post2_dot<T><<<R.G, kKB, 0, s>>>(L, R.A, rD, r, u, out, w, first);
+  else
+    k_amg_post2<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, done);
+  count_launch(); count_launch();
+}
+
 // z = V-cycle(r) on level l; level 0 ends with the r.z reduction of the CG
 template <typename T>
 static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWork& w, int first,
@@ -749,31 +815,18 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
     }
     return;
   }
-  const unsigned B = blocks_for(L.n, kAB);
   T *y = R.at(R.Ly.a[l]), *u = R.at(R.Ly.b[l]);
   const AmgLev& L1 = H->lev[l + 1];
   T* rc = R.at(R.Ly.r[l + 1]);
   T* xc = R.at(R.Ly.a[l + 1]);   // written by the next level's last sweep
-  if (fine) {
-    k_amg_pre<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
-    prof_before(DIFVM_PROF_AMG_RESID, s);
-    k_amg_resid<T, true><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
-    prof_after(DIFVM_PROF_AMG_RESID, s);
-  } else {
-    k_amg_pre<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
-    k_amg_resid<T, false><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
+  const int tpr = amg_tpr(L, l);
+  for (int down = 1; down >= 0; --down) {
+    if (tpr == 1) amg_sweeps<T, 1>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
+    else if (tpr == 2) amg_sweeps<T, 2>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
+    else if (tpr == 4) amg_sweeps<T, 4>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
+    else amg_sweeps<T, 8>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
+    if (down) amg_vcycle(R, l + 1, rc, xc, w, first, s);
   }
-  k_amg_restrict<T><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, u, rc, done);
-  count_launch(); count_launch(); count_launch();
-  amg_vcycle(R, l + 1, rc, xc, w, first, s);
-  if (fine) {
-    k_amg_post1<T, true><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
-    k_amg_post2<T, true, true><<<R.G, kKB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
-  } else {
-    k_amg_post1<T, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
-    k_amg_post2<T, false, false><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, w, first);
-  }
-  count_launch(); count_launch();
 }
 
 // one AMG-preconditioned CG solve of A x = b (x is the initial guess unless
