@@ -96,17 +96,19 @@ struct Ell {
 // soff[i/32] + 32 k + i%32; with a uniform width W > 0 soff is not read).
 // nb[slot] = 2 j + side for an internal face (j the other cell, side 1 = row is
 // the neighbour), -2 - b for boundary face ni + b, -1 on padding; fid[slot] =
-// face id.  The face records Sw, ck are copied into slot order, so a row's
-// faces come in with coalesced loads and only the neighbour values are gathered.
+// face id.  The Sw face records are also copied into slot order (a row's
+// records then come in with coalesced loads, without the face id).
 struct Hf {
   int W;
   const int* soff;
   const int* nb;
   const int* fid;
 };
+// face records as a face kernel reads them: by slot (sw = the slot copies,
+// ck unused) or by face id (sw, ck = the face arrays)
 template <typename T> struct HfGeo {
-  const V4<T>* sw;  // [nslots] Sw of the slot's face
-  const V4<T>* ck;  // [nslots] ck of the slot's face
+  const V4<T>* sw;
+  const V4<T>* ck;
 };
 __device__ __forceinline__ void hf_row(const Hf& H, int i, int& base, int& w) {
   if (H.W > 0) {
@@ -189,17 +191,15 @@ struct difvm_mesh {
   int* hf_nb = nullptr;
   int* hf_fid = nullptr;
   difvm::V4<double>* hf_sw64 = nullptr;
-  difvm::V4<double>* hf_ck64 = nullptr;
   difvm::V4<float>* hf_sw32 = nullptr;
-  difvm::V4<float>* hf_ck32 = nullptr;
 
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
   }
   difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_w, ell_soff, ell_col, ell_map}; }
   difvm::Hf hf() const { return difvm::Hf{hf_w, hf_soff, hf_nb, hf_fid}; }
-  difvm::HfGeo<double> hfgeo64() const { return {hf_sw64, hf_ck64}; }
-  difvm::HfGeo<float> hfgeo32() const { return {hf_sw32, hf_ck32}; }
+  difvm::HfGeo<double> hfgeo64() const { return {hf_sw64, nullptr}; }
+  difvm::HfGeo<float> hfgeo32() const { return {hf_sw32, nullptr}; }
   difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }
   difvm::Geo<float> geo32() const { return {Sw32, ck32, V32, rV32}; }
 };

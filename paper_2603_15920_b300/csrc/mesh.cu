@@ -194,24 +194,19 @@ __global__ void k_cell_coeffs(int nc, const double* V, double* rV64, float* V32,
   rV32[i] = (float)(1.0 / v);
 }
 
-// face records in half-face slot order (zero on padding)
-__global__ void k_hf_fill(int ns, const int* fid, const V4<double>* Sw64, const V4<double>* ck64,
-                          const V4<float>* Sw32, const V4<float>* ck32, V4<double>* hsw64,
-                          V4<double>* hck64, V4<float>* hsw32, V4<float>* hck32) {
+// Sw face records in half-face slot order (zero on padding)
+__global__ void k_hf_fill(int ns, const int* fid, const V4<double>* Sw64, const V4<float>* Sw32,
+                          V4<double>* hsw64, V4<float>* hsw32) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ns) return;
   const int f = fid[k];
   if (f < 0) {
     hsw64[k] = V4<double>{0, 0, 0, 0};
-    hck64[k] = V4<double>{0, 0, 0, 0};
     hsw32[k] = V4<float>{0, 0, 0, 0};
-    hck32[k] = V4<float>{0, 0, 0, 0};
     return;
   }
   hsw64[k] = Sw64[f];
-  hck64[k] = ck64[f];
   hsw32[k] = Sw32[f];
-  hck32[k] = ck32[f];
 }
 
 static void free_mesh(difvm_mesh* m) {
@@ -220,7 +215,7 @@ static void free_mesh(difvm_mesh* m) {
                   m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
                   m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map,
                   m->seg_case, m->seg_cb0, m->seg_cs, m->hf_soff, m->hf_nb, m->hf_fid,
-                  m->hf_sw64, m->hf_ck64, m->hf_sw32, m->hf_ck32};
+                  m->hf_sw64, m->hf_sw32};
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
@@ -511,12 +506,9 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   {
     const size_t ns = (size_t)std::max<int64_t>(m->hf_nslots, 1);
     DIFVM_TRY(upload<V4<double>>(&m->hf_sw64, nullptr, ns));
-    DIFVM_TRY(upload<V4<double>>(&m->hf_ck64, nullptr, ns));
     DIFVM_TRY(upload<V4<float>>(&m->hf_sw32, nullptr, ns));
-    DIFVM_TRY(upload<V4<float>>(&m->hf_ck32, nullptr, ns));
-    k_hf_fill<<<blocks_for((int64_t)ns, 256), 256>>>((int)ns, m->hf_fid, m->Sw64, m->ck64, m->Sw32,
-                                                     m->ck32, m->hf_sw64, m->hf_ck64, m->hf_sw32,
-                                                     m->hf_ck32);
+    k_hf_fill<<<blocks_for((int64_t)ns, 256), 256>>>((int)ns, m->hf_fid, m->Sw64, m->Sw32, m->hf_sw64,
+                                                     m->hf_sw32);
     DIFVM_TRY(check_launch("hf_fill"));
   }
   DIFVM_CUDA(cudaDeviceSynchronize());

@@ -29,26 +29,29 @@ template <typename T, bool SW, bool CK>
 struct HfChunk {
   int v[4];       // half-face word (see Hf), -1 past the row end or on padding
   int slot[4];
+  int f[4];       // face id (FG)
   V4<T> sw[4], ck[4];
 };
-template <typename T, bool SW, bool CK>
+template <bool FG, typename T, bool SW, bool CK>
 __device__ __forceinline__ void hf_chunk(const Hf& H, const HfGeo<T>& G, int base, int k0, int w,
                                          HfChunk<T, SW, CK>& c) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     c.slot[k] = base + 32 * (k0 + k);
     c.v[k] = (k0 + k < w) ? ldg(H.nb + c.slot[k]) : -1;
+    if (FG) c.f[k] = (k0 + k < w) ? max(ldg(H.fid + c.slot[k]), 0) : 0;   // padding: fid -1
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (SW && k0 + k < w) c.sw[k] = ld4(G.sw + c.slot[k]);
-    if (CK && k0 + k < w) c.ck[k] = ld4(G.ck + c.slot[k]);
+    const int o = FG ? c.f[k] : c.slot[k];
+    if (SW && k0 + k < w) c.sw[k] = ld4(G.sw + o);
+    if (CK && k0 + k < w) c.ck[k] = ld4(G.ck + o);
   }
 }
 
 // ----------------------------------------------------------- Gauss gradient
 // grad_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green)
-template <typename T, int NC>
+template <typename T, int NC, bool FG>
 __global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg, Geo<T> g, int cls,
                                                        const T* __restrict__ phi,
                                                        const T* __restrict__ phib,
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg
   hf_row(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
     HfChunk<T, true, false> q;
-    hf_chunk<T, true, false>(H, hg, base, k0, w, q);
+    hf_chunk<FG>(H, hg, base, k0, w, q);
     T pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -171,12 +174,10 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss_bwd(Topo t, Geo<T> g, int
 
 // ------------------------------------------------------------ convection
 // out_i = sum_f sigma m_f phi_f   (Eqs. conv_face_flux, upwind; tie m=0 -> owner)
-template <typename T, int NC, bool UPWIND>
-__global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls,
-                                                     const T* __restrict__ mf,
-                                                     const T* __restrict__ phi,
-                                                     const T* __restrict__ phib,
-                                                     T* __restrict__ out) {
+template <typename T, int NC, bool UPWIND, bool FG>
+__device__ __forceinline__ void div_flux_row(const Topo& t, const Hf& H, const HfGeo<T>& hg, int cls,
+                                             const T* __restrict__ mf, const T* __restrict__ phi,
+                                             const T* __restrict__ phib, T* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc, nb = t.nb;
@@ -190,10 +191,10 @@ __global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Hf H, HfGeo<T> hg, 
   hf_row(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
     HfChunk<T, !UPWIND, false> q;
-    hf_chunk<T, !UPWIND, false>(H, hg, base, k0, w, q);
+    hf_chunk<FG>(H, hg, base, k0, w, q);
     int fk[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) fk[k] = q.v[k] != -1 ? ldg(H.fid + q.slot[k]) : 0;
+    for (int k = 0; k < 4; ++k) fk[k] = FG ? q.f[k] : (q.v[k] != -1 ? ldg(H.fid + q.slot[k]) : 0);
     T mk[4], pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -230,6 +231,20 @@ __global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Hf H, HfGeo<T> hg, 
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) out[c * nc + i] = acc[c];
+}
+template <typename T, int NC, bool UPWIND, bool FG>
+__global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls, const T* __restrict__ mf,
+                                                     const T* __restrict__ phi, const T* __restrict__ phib,
+                                                     T* __restrict__ out) {
+  div_flux_row<T, NC, UPWIND, FG>(t, H, hg, cls, mf, phi, phib, out);
+}
+// the same with registers capped for six blocks per SM: measured faster for the
+// FP32 upwind form on the 1.6M-cell Kuhn mesh (29 vs 36 us, 3 components)
+template <typename T, int NC, bool UPWIND, bool FG>
+__global__ void __launch_bounds__(kBlock, 6) k_div_flux_occ(Topo t, Hf H, HfGeo<T> hg, int cls,
+                                                            const T* __restrict__ mf, const T* __restrict__ phi,
+                                                            const T* __restrict__ phib, T* __restrict__ out) {
+  div_flux_row<T, NC, UPWIND, FG>(t, H, hg, cls, mf, phi, phib, out);
 }
 
 // Adjoint.  delta_f = obar_O - obar_N (internal) or obar_O (boundary):
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_div_flux_bwd(Topo t, Geo<T> g, int c
 
 // --------------------------------------------------------------- diffusion
 // out_i = sum_f sigma gamma [c_f (phi_N - phi_O) + (grad phi)_f . k_f]   (Eq. nonortho_flux)
-template <typename T, int NC, bool NONORTH>
+template <typename T, int NC, bool NONORTH, bool FG>
 __global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Hf H, HfGeo<T> hg, int cls, T gamma,
                                                       const T* __restrict__ phi,
                                                       const T* __restrict__ phib,
@@ -329,7 +344,7 @@ __global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Hf H, HfGeo<T> hg,
   hf_row(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
     HfChunk<T, NONORTH, true> q;
-    hf_chunk<T, NONORTH, true>(H, hg, base, k0, w, q);
+    hf_chunk<FG>(H, hg, base, k0, w, q);
     T pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -531,10 +546,20 @@ static difvm_status check_cls(int cls) {
   return DIFVM_OK;
 }
 
+// Face records by slot (the Sw copies of the half-face layout: coalesced, no
+// face-id load; the Gauss gradient) or by face id from the face arrays (each
+// record read from DRAM once, its second visit an L2 hit within the RCM
+// bandwidth; the kernels that load the face id anyway).  Chosen per kernel by
+// measurement on the 1.6M-cell Kuhn mesh.
+template <typename T> static HfGeo<T> fgeo(const difvm_mesh* m) {
+  const Geo<T> g = geo<T>(m);
+  return HfGeo<T>{g.Sw, g.ck};
+}
+
 template <typename T>
 difvm_status grad_gauss_t(difvm_mesh_t m, int cls, const void* phi, const void* phib,
                           int ncomp, void* grad, cudaStream_t s) {
-  DIFVM_NC_SWITCH(ncomp, k_grad_gauss<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+  DIFVM_NC_SWITCH(ncomp, k_grad_gauss<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
                              m->topo(), m->hf(), hfgeo<T>(m), geo<T>(m), cls, (const T*)phi,
                              (const T*)phib, (T*)grad));
   return check_launch("grad_gauss");
@@ -556,13 +581,18 @@ template <typename T>
 static difvm_status div_flux_t(difvm_mesh_t m, int scheme, int cls, const void* mf,
                                const void* phi, const void* phib, int ncomp, void* out,
                                cudaStream_t s) {
-  if (scheme == DIFVM_DIV_UPWIND) {
-    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), m->hf(), hfgeo<T>(m), cls, (const T*)mf, (const T*)phi,
+  const unsigned B = blocks_for(m->nc, kBlock);
+  if (scheme == DIFVM_DIV_UPWIND && sizeof(T) == 4) {
+    DIFVM_NC_SWITCH(ncomp, k_div_flux_occ<T, NCc, true, true><<<B, kBlock, 0, s>>>(
+                               m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi,
+                               (const T*)phib, (T*)out));
+  } else if (scheme == DIFVM_DIV_UPWIND) {
+    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, true, true><<<B, kBlock, 0, s>>>(
+                               m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi,
                                (const T*)phib, (T*)out));
   } else {
-    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), m->hf(), hfgeo<T>(m), cls, (const T*)mf, (const T*)phi,
+    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, false, true><<<B, kBlock, 0, s>>>(
+                               m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi,
                                (const T*)phib, (T*)out));
   }
   return check_launch("div_flux");
@@ -589,12 +619,12 @@ static difvm_status laplacian_t(difvm_mesh_t m, int cls, double gamma, const voi
                                 const void* phib, const void* grad, int ncomp, void* out,
                                 cudaStream_t s) {
   if (grad) {
-    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), m->hf(), hfgeo<T>(m), cls, (T)gamma, (const T*)phi,
+    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, true, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), m->hf(), fgeo<T>(m), cls, (T)gamma, (const T*)phi,
                                (const T*)phib, (const T*)grad, (T*)out));
   } else {
-    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), m->hf(), hfgeo<T>(m), cls, (T)gamma, (const T*)phi,
+    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, false, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
+                               m->topo(), m->hf(), fgeo<T>(m), cls, (T)gamma, (const T*)phi,
                                (const T*)phib, (const T*)nullptr, (T*)out));
   }
   return check_launch("laplacian");
