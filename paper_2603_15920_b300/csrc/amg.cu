@@ -503,6 +503,7 @@ __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* 
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                  const T* r, T* y, const int* done) {
+  pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
@@ -516,6 +517,7 @@ __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D,
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* D, const T* Lv, const T* r,
                                                    const T* y, T* res, const int* done) {
+  pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
@@ -529,6 +531,7 @@ __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* 
 // children in ascending order, then a fixed xor tree.
 template <typename T, int RL>
 __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T* res, T* rc, const int* done) {
+  pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, K = g / RL, t = g % RL;
   T s = T(0);
@@ -558,6 +561,7 @@ template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                    const T* r, const T* y, const T* xc, T* out,
                                                    const int* done) {
+  pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
@@ -571,6 +575,7 @@ __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* 
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                    const T* r, const T* u, T* v, const int* done) {
+  pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
@@ -585,6 +590,7 @@ __global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* 
 template <typename T>
 __global__ void __launch_bounds__(kKB) k_amg_post2_dot(AmgLev L, Mat<T> A, const T* rD, const T* r, const T* u,
                                                        T* v, KWork w, int first) {
+  pdl_chain();
   if (w.st[0].done) return;
   const T om = (T)kAmgOmega;
   DotAcc<T> rz;
@@ -619,6 +625,7 @@ __global__ void __launch_bounds__(kKB) k_apcg_rz(int nc, const T* r, const T* z,
 // the row are loaded together, then a shuffle tree sums the lanes in a fixed order
 template <typename T>
 __global__ void __launch_bounds__(1024) k_amg_coarse(int n, const float* Ainv, const T* r, T* x, const int* done) {
+  pdl_chain();
   if (*done) return;
   constexpr int NJ = kAmgCoarsest / 32;
   __shared__ float rs[kAmgCoarsest];
@@ -687,6 +694,7 @@ __global__ void k_apcg_zero(int nc, T* x, KWork w) {
 // p = z + beta p (first: p = z)
 template <typename T>
 __global__ void __launch_bounds__(kKB) k_apcg_p(int nc, const T* z, T* p, KWork w, int first) {
+  pdl_chain();
   if (w.st[0].done) return;
   const T be = (T)w.st[0].beta;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
@@ -696,6 +704,7 @@ __global__ void __launch_bounds__(kKB) k_apcg_p(int nc, const T* z, T* p, KWork 
 // x += alpha p; r -= alpha q; rr and the convergence test
 template <typename T>
 __global__ void __launch_bounds__(kKB) k_apcg_update(int nc, const T* p, const T* q, T* x, T* r, KWork w) {
+  pdl_chain();
   if (w.st[0].done) return;
   const T al = (T)w.st[0].alpha;
   DotAcc<T> rr;
@@ -776,22 +785,22 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
   const int* done = &w.st[0].done;
   const unsigned B = blocks_for((int64_t)L.n * TPR, kAB);
   if (down) {
-    k_amg_pre<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, done);
+    launch_pdl(k_amg_pre<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, done);
     if (TPR == 1) prof_before(DIFVM_PROF_AMG_RESID, s);
-    k_amg_resid<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, Lv, r, y, u, done);
+    launch_pdl(k_amg_resid<T, TPR>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
     if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
     if (L1.n >= kAmgBigLevel / 4)
-      k_amg_restrict<T, 1><<<blocks_for(L1.n, kAB), kAB, 0, s>>>(L1.n, L, u, rc, done);
+      launch_pdl(k_amg_restrict<T, 1>, blocks_for(L1.n, kAB), kAB, s, L1.n, L, u, rc, done);
     else
-      k_amg_restrict<T, 8><<<blocks_for((int64_t)L1.n * 8, kAB), kAB, 0, s>>>(L1.n, L, u, rc, done);
+      launch_pdl(k_amg_restrict<T, 8>, blocks_for((int64_t)L1.n * 8, kAB), kAB, s, L1.n, L, u, rc, done);
     count_launch(); count_launch(); count_launch();
     return;
   }
-  k_amg_post1<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, y, xc, u, done);
+  launch_pdl(k_amg_post1<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, xc, u, done);
   if (TPR == 1)
-    k_amg_post2_dot<T><<<R.G, kKB, 0, s>>>(L, R.A, rD, r, u, out, w, first);
+    launch_pdl(k_amg_post2_dot<T>, R.G, kKB, s, L, R.A, rD, r, u, out, w, first);
   else
-    k_amg_post2<T, TPR><<<B, kAB, 0, s>>>(L, R.A, D, rD, Lv, r, u, out, done);
+    launch_pdl(k_amg_post2<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, u, out, done);
   count_launch(); count_launch();
 }
 
@@ -807,7 +816,7 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const T* rD = R.at(R.Ly.rD[l]);
   const T* Lv = fine ? nullptr : R.at(R.Ly.E[l]);   // row-entry values of a coarse level
   if (l == H->nlev - 1) {
-    k_amg_coarse<T><<<1, 1024, 0, s>>>(L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
+    launch_pdl(k_amg_coarse<T>, 1, 1024, s, L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
     count_launch();
     if (l == 0) {   // a single level: the CG's r.z reduction runs on its own
       k_apcg_rz<T><<<R.G, kKB, 0, s>>>(L.n, r, out, w, first);
@@ -847,9 +856,9 @@ static difvm_status amg_cg(const AmgRun<T>& R, const T* b, T* x, const KWork& w,
     prof_before(DIFVM_PROF_PCG_SPMV, s);
     k_pcg_spmv<T, 1, MW><<<G, kKB, 0, s>>>(R.t, R.A, p, q, w);
     prof_after(DIFVM_PROF_PCG_SPMV, s);
-    k_apcg_update<T><<<G, kKB, 0, s>>>(nc, p, q, x, r, w);
+    launch_pdl(k_apcg_update<T>, G, kKB, s, nc, p, q, x, r, w);
     amg_vcycle(R, 0, r, z, w, 0, s);
-    k_apcg_p<T><<<G, kKB, 0, s>>>(nc, z, p, w, 0);
+    launch_pdl(k_apcg_p<T>, G, kKB, s, nc, z, p, w, 0);
     count_launch(); count_launch(); count_launch();
   };
   int* counter = reinterpret_cast<int*>(w.ticket) + 1;
@@ -1051,6 +1060,7 @@ __global__ void __launch_bounds__(kKB) k_fcg_init(Topo t, Mat<float> A, const do
 template <int MW>
 __global__ void __launch_bounds__(kKB) k_fcg_spmv(Topo t, Mat<float> A, const float* ph, const float* pl,
                                                   float* qh, float* ql, KWork w) {
+  pdl_chain();
   if (w.st[0].done) return;
   const int nc = t.nc;
   FF pq{0.f, 0.f};
@@ -1085,6 +1095,7 @@ __global__ void __launch_bounds__(kKB) k_fcg_spmv(Topo t, Mat<float> A, const fl
 __global__ void __launch_bounds__(kKB) k_fcg_update(int nc, const float* ph, const float* pl, const float* qh,
                                                     const float* ql, float* xh, float* xl, float* rh, float* rl,
                                                     KWork w) {
+  pdl_chain();
   if (w.st[0].done) return;
   const FF al = ff_of(w.st[0].alpha), nal = ff_of(-w.st[0].alpha);
   FF rr{0.f, 0.f};
@@ -1110,6 +1121,7 @@ __global__ void __launch_bounds__(kKB) k_fcg_update(int nc, const float* ph, con
 
 // p = z + beta p (first: p = z)
 __global__ void __launch_bounds__(kKB) k_fcg_p(int nc, const float* z, float* ph, float* pl, KWork w, int first) {
+  pdl_chain();
   if (w.st[0].done) return;
   const FF be = ff_of(w.st[0].beta);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
@@ -1150,11 +1162,11 @@ static difvm_status amg_mixed_mw(difvm_mesh* m, const difvm_solve_opts* o, const
   DIFVM_TRY(check_launch("fcg_p"));
   auto iter = [&](cudaStream_t s) {
     prof_before(DIFVM_PROF_PCG_SPMV, s);
-    k_fcg_spmv<MW><<<G, kKB, 0, s>>>(R.t, R.A, ph, pl, qh, ql, w);
+    launch_pdl(k_fcg_spmv<MW>, G, kKB, s, R.t, R.A, ph, pl, qh, ql, w);
     prof_after(DIFVM_PROF_PCG_SPMV, s);
-    k_fcg_update<<<G, kKB, 0, s>>>(nc, ph, pl, qh, ql, xh, xl, rh, rl, w);
+    launch_pdl(k_fcg_update, G, kKB, s, nc, ph, pl, qh, ql, xh, xl, rh, rl, w);
     amg_vcycle(R, 0, rh, z32, w, 0, s);
-    k_fcg_p<<<G, kKB, 0, s>>>(nc, z32, ph, pl, w, 0);
+    launch_pdl(k_fcg_p, G, kKB, s, nc, z32, ph, pl, w, 0);
     count_launch(); count_launch(); count_launch();
   };
   int* counter = reinterpret_cast<int*>(w.ticket) + 1;

@@ -38,6 +38,32 @@ bool prof_active();
     if (difvm_try_st_ != DIFVM_OK) return difvm_try_st_;  \
   } while (0)
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel started with launch_pdl may begin while the kernel before it in the
+// stream is still finishing (its blocks are scheduled once every block of the
+// predecessor is resident).  Such a kernel calls pdl_chain() first, in every
+// thread and before any exit: griddepcontrol.wait returns once the predecessor
+// has completed and its writes are visible, so completion still chains through
+// every kernel; launch_dependents then lets the next kernel be scheduled.
+__device__ __forceinline__ void pdl_chain() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... P, typename... A>
+inline void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, ((P)args)...);   // an error is left for check_error
+}
+
 // ------------------------------------------------------------ vector types
 template <typename T> struct V4;
 template <> struct __align__(16) V4<float> { float x, y, z, w; };
