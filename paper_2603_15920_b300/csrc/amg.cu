@@ -477,16 +477,33 @@ __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* 
     for (int k = 0; k < w; ++k) y += __ldg(A.val + base + step * k) * x(__ldg(A.E.col + base + step * k));
     return y;
   } else {
+    // a lane's first Q slots: all column and value loads, then all gathers,
+    // then the sums in slot order (three dependent round trips for rows of up
+    // to Q * TPR slots); longer rows continue two slots per pass
+    constexpr int Q = (TPR >= 8 ? 32 : 16) / TPR;
     T y = T(0);
     if (ok) {
       const int o0 = __ldg(L.soff + (i >> 5));
       const int w = (__ldg(L.soff + (i >> 5) + 1) - o0) >> 5;
-      int o = o0 + (i & 31) + 32 * t;
-      if (t == 0) y = D[i] * x(i);
-      int k = t;
+      const int ob = o0 + (i & 31) + 32 * t;
+      const T xi = t == 0 ? x(i) : T(0);
+      int c[Q];
+      T v[Q], xv[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const bool in = t + q * TPR < w;
+        c[q] = in ? __ldg(L.ecol + ob + 32 * q * TPR) : -1;
+        v[q] = in ? Lv[ob + 32 * q * TPR] : T(0);   // Lv: ELL values
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) xv[q] = c[q] >= 0 ? x(c[q]) : T(0);
+      if (t == 0) y = D[i] * xi;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) y += v[q] * xv[q];
+      int k = t + Q * TPR, o = ob + 32 * Q * TPR;
       for (; k + TPR < w; k += 2 * TPR, o += 64 * TPR) {
         const int c0 = __ldg(L.ecol + o), c1 = __ldg(L.ecol + o + 32 * TPR);
-        const T v0 = Lv[o], v1 = Lv[o + 32 * TPR];   // Lv: ELL values
+        const T v0 = Lv[o], v1 = Lv[o + 32 * TPR];
         const T x0 = x(c0), x1 = x(c1);
         y += v0 * x0;
         y += v1 * x1;
