@@ -54,6 +54,7 @@ struct AmgLev {
   const int* eface;
   int nslots;
   const int* agg;                     // [n] cell -> next-level cell
+  const int* eagg;                    // [slots of the level's ELL] agg of the slot's column
   const int *ch_ptr, *ch_idx;         // next-level cell -> its cells
   const int *ci_ptr, *ci_idx;         // next-level cell -> faces inside it
   const int *cf_ptr, *cf_idx;         // next-level face -> faces mapped to it
@@ -168,6 +169,10 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
   g.w.resize(m->ni);
   for (int f = 0; f < m->ni; ++f) g.w[f] = ck[f].x;
 
+  std::vector<int> ecol_host;   // the current level's ELL columns (level 0: the mesh's ELL)
+  ecol_host.resize(std::max<int64_t>(m->ell_nslots, 0));
+  if (m->ell_nslots > 0)
+    DIFVM_CUDA(cudaMemcpy(ecol_host.data(), m->ell_col, sizeof(int) * m->ell_nslots, cudaMemcpyDeviceToHost));
   while (true) {
     AmgLev L{};
     L.n = g.n;
@@ -210,6 +215,7 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
         }
       }
       L.nslots = soff[nsl];
+      ecol_host = ecol;
       DIFVM_TRY(upload_vec(H, &L.cptr, cptr));
       DIFVM_TRY(upload_vec(H, &L.cent, cent));
       DIFVM_TRY(upload_vec(H, &L.soff, soff));
@@ -242,6 +248,9 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
       group_by(inside, n2, cip, cii);
       group_by(fmap, (int)g2.on.size(), cfp, cfi);
       DIFVM_TRY(upload_vec(H, &L.agg, agg));
+      std::vector<int> eagg(ecol_host.size());
+      for (size_t k = 0; k < ecol_host.size(); ++k) eagg[k] = agg[ecol_host[k]];
+      DIFVM_TRY(upload_vec(H, &L.eagg, eagg));
       DIFVM_TRY(upload_vec(H, &L.ch_ptr, chp));
       DIFVM_TRY(upload_vec(H, &L.ch_idx, chi));
       DIFVM_TRY(upload_vec(H, &L.ci_ptr, cip));
@@ -456,25 +465,36 @@ __global__ void __launch_bounds__(512) k_amg_dense_inv(AmgLev L, const T* D, con
 // its width; the lanes are summed by a fixed xor tree and every lane gets the
 // total.  x is a functor so that smoothed values can be formed on the fly.
 // `ok` = the row exists; all lanes of a warp must call it (shuffles).
-template <typename T, int TPR, class XF>
+// PROL: x takes (column, its aggregate), the aggregates coming from L.eagg
+// in the same slot order, so that a prolongated value needs no dependent load.
+template <bool PROL, class XF>
+__device__ __forceinline__ auto xat(XF& x, int c, int a) {
+  if constexpr (PROL) return x(c, a);
+  else return x(c);
+}
+template <typename T, int TPR, bool PROL = false, class XF>
 __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* D, const T* Lv, int i, int t,
                                      bool ok, XF x) {
   if constexpr (TPR == 1) {
     if (!ok) return T(0);
-    T y = __ldg(A.D + i) * x(i);
+    T y = __ldg(A.D + i) * xat<PROL>(x, i, PROL ? __ldg(L.agg + i) : 0);
     if (A.E.W == 4) {
       const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      const int4 g4 = PROL ? __ldg(reinterpret_cast<const int4*>(L.eagg) + i) : make_int4(0, 0, 0, 0);
       T a[4];
       Vec4Load<T>::get(A.val, i, a);
-      y += a[0] * x(j4.x);
-      y += a[1] * x(j4.y);
-      y += a[2] * x(j4.z);
-      y += a[3] * x(j4.w);
+      y += a[0] * xat<PROL>(x, j4.x, g4.x);
+      y += a[1] * xat<PROL>(x, j4.y, g4.y);
+      y += a[2] * xat<PROL>(x, j4.z, g4.z);
+      y += a[3] * xat<PROL>(x, j4.w, g4.w);
       return y;
     }
     int base, step, w;
     ell_row(A.E, i, base, step, w);
-    for (int k = 0; k < w; ++k) y += __ldg(A.val + base + step * k) * x(__ldg(A.E.col + base + step * k));
+    for (int k = 0; k < w; ++k) {
+      const int o = base + step * k;
+      y += __ldg(A.val + o) * xat<PROL>(x, __ldg(A.E.col + o), PROL ? __ldg(L.eagg + o) : 0);
+    }
     return y;
   } else {
     // a lane's first Q slots: all column and value loads, then all gathers,
@@ -486,29 +506,31 @@ __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* 
       const int o0 = __ldg(L.soff + (i >> 5));
       const int w = (__ldg(L.soff + (i >> 5) + 1) - o0) >> 5;
       const int ob = o0 + (i & 31) + 32 * t;
-      const T xi = t == 0 ? x(i) : T(0);
-      int c[Q];
+      const T xi = t == 0 ? xat<PROL>(x, i, PROL ? __ldg(L.agg + i) : 0) : T(0);
+      int c[Q], ag[Q];
       T v[Q], xv[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const bool in = t + q * TPR < w;
         c[q] = in ? __ldg(L.ecol + ob + 32 * q * TPR) : -1;
+        ag[q] = in && PROL ? __ldg(L.eagg + ob + 32 * q * TPR) : 0;
         v[q] = in ? Lv[ob + 32 * q * TPR] : T(0);   // Lv: ELL values
       }
 #pragma unroll
-      for (int q = 0; q < Q; ++q) xv[q] = c[q] >= 0 ? x(c[q]) : T(0);
+      for (int q = 0; q < Q; ++q) xv[q] = c[q] >= 0 ? xat<PROL>(x, c[q], ag[q]) : T(0);
       if (t == 0) y = D[i] * xi;
 #pragma unroll
       for (int q = 0; q < Q; ++q) y += v[q] * xv[q];
       int k = t + Q * TPR, o = ob + 32 * Q * TPR;
       for (; k + TPR < w; k += 2 * TPR, o += 64 * TPR) {
         const int c0 = __ldg(L.ecol + o), c1 = __ldg(L.ecol + o + 32 * TPR);
+        const int a0 = PROL ? __ldg(L.eagg + o) : 0, a1 = PROL ? __ldg(L.eagg + o + 32 * TPR) : 0;
         const T v0 = Lv[o], v1 = Lv[o + 32 * TPR];
-        const T x0 = x(c0), x1 = x(c1);
+        const T x0 = xat<PROL>(x, c0, a0), x1 = xat<PROL>(x, c1, a1);
         y += v0 * x0;
         y += v1 * x1;
       }
-      if (k < w) y += Lv[o] * x(__ldg(L.ecol + o));
+      if (k < w) y += Lv[o] * xat<PROL>(x, __ldg(L.ecol + o), PROL ? __ldg(L.eagg + o) : 0);
     }
 #pragma unroll
     for (int d = TPR / 2; d > 0; d >>= 1) y += __shfl_xor_sync(0xffffffffu, y, d);
@@ -583,9 +605,9 @@ __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* 
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
   const T w = (T)kAmgOmega, sc = (T)kAmgScale;
-  auto z = [&](int j) { return y[j] + sc * xc[L.agg[j]]; };
-  const T az = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, z);
-  if (ok && t == 0) out[i] = z(i) + w * rD[i] * (r[i] - az);
+  auto z = [&](int j, int a) { return y[j] + sc * xc[a]; };
+  const T az = lev_row<T, TPR, true>(A, L, D, Lv, i, t, ok, z);
+  if (ok && t == 0) out[i] = z(i, L.agg[i]) + w * rD[i] * (r[i] - az);
 }
 
 // second post-smoothing sweep: v = u + w rD (r - A u)
