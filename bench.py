@@ -573,7 +573,7 @@ def run_ours(args):
         "fwd_adjoint_over_fwd": fwd_adj,
         "face_ops": face_ops,
         "batched": batched,
-        "roofline": {"kernel": "k_amg_resid<float,FINE> (fine-level multigrid residual r - A y)",
+        "roofline": {"kernel": "k_amg_resid<float, 1> (mesh-level multigrid residual r - A y)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
