@@ -90,6 +90,17 @@ enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
 enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1, DIFVM_PRECOND_AMG = 2,
        DIFVM_PRECOND_AMG_REUSE = 3 };
 enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };
+/* Split S_f = Delta_f + k_f of the diffusive flux (Eq. nonortho_flux, Sec. 2.3.2),
+ * Delta_f along the cell-to-cell vector d, in bits 2-3 of the mesh flags:
+ *   OVERRELAXED (0, the paper's default)  Delta = (|S| / |S^.d^|) d^
+ *   MINIMUM                               Delta = (S.d^) d^
+ *   ORTHOGONAL                            Delta = |S| d^
+ *   NONE                                  the two-point flux |S| (phi_N - phi_O) / |d|, k = 0
+ * It sets c_f = |Delta|/|d| and k_f = S - Delta for every operator, solver and
+ * PISO step on the mesh.  Boundary faces (no d_ij) use |S|^2 / (S.d) with
+ * d = x_f - C_O and no correction, for every split. */
+enum { DIFVM_NONORTH_OVERRELAXED = 0u, DIFVM_NONORTH_MINIMUM = 4u, DIFVM_NONORTH_ORTHOGONAL = 8u,
+       DIFVM_NONORTH_NONE = 12u, DIFVM_NONORTH_MASK = 12u };
 enum { DIFVM_NONORTH_MOMENTUM = 1, DIFVM_NONORTH_PRESSURE = 2, DIFVM_NONORTH_ALL = 3 };
 
 typedef struct difvm_mesh* difvm_mesh_t;
@@ -109,7 +120,7 @@ typedef struct difvm_mesh* difvm_mesh_t;
  *     (the result of a case does not depend on the other cases of the batch,
  *     bit for bit).  NULL for a single mesh (the single-mesh solvers).
  *   flags: DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES (internal faces are always
- *     re-oriented so that owner < neighbour).
+ *     re-oriented so that owner < neighbour) | one DIFVM_NONORTH_* split.
  *   device: CUDA device ordinal the handle lives on. */
 typedef struct {
   int32_t n_cells, n_internal, n_faces, n_patches;
@@ -123,7 +134,8 @@ typedef struct {
 } difvm_mesh_desc;
 
 /* Validate, renumber, build the cell-CSR and the derived face coefficients
- * (w_f, c_f = |S|^2/(S.d), k_f = S - c_f d, 1/V; Sec. 2.3.2) and upload them.
+ * (w_f, c_f = |Delta_f|/|d| (|S|^2/(S.d) for the default split), k_f = S - c_f d,
+ * 1/V; Sec. 2.3.2) and upload them.
  * Errors: EINVAL with a message for index out of range, owner == neighbour,
  * patches not covering the boundary faces contiguously, V <= 0 or S.d <= 0;
  * ENOMEM / ECUDA on allocation or copy failure.  Synchronous. */

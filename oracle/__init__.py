@@ -26,6 +26,8 @@ BC_FIXED, BC_ZEROGRAD, BC_EMPTY = 0, 1, 2
 PT_WALL, PT_INLET, PT_OUTLET, PT_EMPTY = 0, 1, 2, 3
 DIV_UPWIND, DIV_LINEAR = 0, 1
 WK_EXACT, WK_FE, WK_BE = 0, 1, 2
+# split of S_f = Delta_f + k_f in Eq. nonortho_flux
+NONORTH_OVERRELAXED, NONORTH_MINIMUM, NONORTH_ORTHOGONAL, NONORTH_NONE = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +55,7 @@ class _Mesh(C.Structure):
                 ("owner", C.c_void_p), ("neighbour", C.c_void_p),
                 ("Sf", C.c_void_p), ("Cf", C.c_void_p), ("V", C.c_void_p), ("C", C.c_void_p),
                 ("patch_start", C.c_void_p), ("patch_size", C.c_void_p),
-                ("patch_type", C.c_void_p)]
+                ("patch_type", C.c_void_p), ("nonorth", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -90,7 +92,7 @@ class OMesh:
     """Holds the oracle's view of a mesh (plain arrays, input numbering)."""
 
     def __init__(self, n_cells, n_internal, owner, neighbour, Sf, Cf, V, Cc,
-                 patch_start, patch_size, patch_type):
+                 patch_start, patch_size, patch_type, nonorth=0):
         self.keep = [_i32(owner), _i32(neighbour), _f64(Sf), _f64(Cf), _f64(V), _f64(Cc),
                      _i32(patch_start), _i32(patch_size), _i32(patch_type)]
         o, n, S, X, Vv, Cv, ps, pz, pt = self.keep
@@ -98,13 +100,16 @@ class OMesh:
         self.nb = self.nf - self.nint
         self.npatch = int(ps.shape[0])
         self.patch_start, self.patch_size, self.patch_type = ps, pz, pt
+        self.nonorth = int(nonorth)
         self.s = _Mesh(self.nc, self.nint, self.nf, self.npatch, _p(o), _p(n), _p(S), _p(X),
-                       _p(Vv), _p(Cv), _p(ps), _p(pz), _p(pt))
+                       _p(Vv), _p(Cv), _p(ps), _p(pz), _p(pt), self.nonorth)
 
     @classmethod
-    def from_mesh(cls, m):
+    def from_mesh(cls, m, nonorth=0):
+        """nonorth: the split of S_f in Eq. nonortho_flux, NONORTH_OVERRELAXED (the
+        paper's default), NONORTH_MINIMUM, NONORTH_ORTHOGONAL or NONORTH_NONE."""
         return cls(m.n_cells, m.n_internal, m.owner, m.neighbour, m.Sf, m.Cf, m.V, m.C,
-                   m.patch_start, m.patch_size, m.patch_type)
+                   m.patch_start, m.patch_size, m.patch_type, nonorth)
 
     def ref(self):
         return C.byref(self.s)

@@ -25,7 +25,9 @@
  * Readings where the paper is silent (each one is listed in the design notes):
  *   w_f  = S.(C_N - x_f) / S.(C_N - C_O)   owner weight of linear interpolation
  *   c_f  = |S|^2 / (S.d)                   |Delta_f|/|d| for the over-relaxed
- *                                          split Delta = (|S|/|S^.d^|) d^ (Eq. nonortho_flux)
+ *                                          split Delta = (|S|/|S^.d^|) d^ (Eq. nonortho_flux;
+ *                                          the minimum / orthogonal / no-correction
+ *                                          splits of the same paragraph by om_mesh.nonorth)
  *   k_f  = S - c_f d                        non-orthogonal remainder
  *   boundary diffusion is orthogonal only, d = x_f - C_O.
  *   a boundary face carries its boundary-condition value for every scheme.
@@ -45,12 +47,14 @@ typedef struct {
   const int *owner, *neighbour;
   const double *Sf, *Cf, *V, *C;
   const int *patch_start, *patch_size, *patch_type;
+  int nonorth;   /* split of S_f in Eq. nonortho_flux: NO_OVERRELAXED .. NO_NONE */
 } om_mesh;
 
 enum { BC_FIXED = 0, BC_ZEROGRAD = 1, BC_EMPTY = 2 };
 enum { PT_WALL = 0, PT_INLET = 1, PT_OUTLET = 2, PT_EMPTY = 3 };
 enum { DIV_UPWIND = 0, DIV_LINEAR = 1 };
 enum { WK_EXACT = 0, WK_FE = 1, WK_BE = 2 };
+enum { NO_OVERRELAXED = 0, NO_MINIMUM = 1, NO_ORTHOGONAL = 2, NO_NONE = 3 };
 
 static double dot3(const double *a, const double *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -78,7 +82,25 @@ static double limit_corr(double corr, double orth, double psi) {
 }
 
 /* ---------------------------------------------------------------- geometry */
-/* Derived face coefficients (Sec. 2.3.2): w[nint], c[nf], k[nint*3]. */
+/* |Delta_f| / |d| for the split S = Delta + k of Eq. nonortho_flux, Delta
+ * along d (Sec. 2.3.2, the paragraph on non-orthogonality correction):
+ *   over-relaxed  Delta = (|S| / |S^.d^|) d^   ->  |S|^2 / (S.d)
+ *   minimum       Delta = (S.d^) d^            ->  (S.d) / |d|^2
+ *   orthogonal    Delta = |S| d^               ->  |S| / |d|
+ *   none          the two-point flux of Eq. diff_ortho: |S| / |d|, k = 0 */
+static double split_coeff(int scheme, const double *S, const double *d) {
+  switch (scheme) {
+    case NO_MINIMUM: return dot3(S, d) / dot3(d, d);
+    case NO_ORTHOGONAL:
+    case NO_NONE: return sqrt(dot3(S, S)) / sqrt(dot3(d, d));
+    default: return dot3(S, S) / dot3(S, d);
+  }
+}
+
+/* Derived face coefficients (Sec. 2.3.2): w[nint], c[nf], k[nint*3] with
+ * k = S - Delta = S - c d (0 for the scheme without correction).  The splits
+ * are defined along the cell-to-cell vector d_ij; a boundary face has none and
+ * keeps the orthogonal-only boundary flux of the readings above. */
 void om_face_coeffs(const om_mesh *m, double *w, double *c, double *k) {
   for (int f = 0; f < m->nf; ++f) {
     const double *S = m->Sf + 3 * f, *xf = m->Cf + 3 * f, *CO = m->C + 3 * m->owner[f];
@@ -88,11 +110,11 @@ void om_face_coeffs(const om_mesh *m, double *w, double *c, double *k) {
       double dN[3] = {CN[0] - xf[0], CN[1] - xf[1], CN[2] - xf[2]};
       for (int a = 0; a < 3; ++a) d[a] = CN[a] - CO[a];
       w[f] = dot3(S, dN) / dot3(S, d);
-      c[f] = dot3(S, S) / dot3(S, d);
-      for (int a = 0; a < 3; ++a) k[3 * f + a] = S[a] - c[f] * d[a];
-    } else {
+      c[f] = split_coeff(m->nonorth, S, d);
+      for (int a = 0; a < 3; ++a) k[3 * f + a] = m->nonorth == NO_NONE ? 0.0 : S[a] - c[f] * d[a];
+    } else {   /* no cell on the other side: every scheme keeps |S|^2 / (S.d), d = x_f - C_O */
       for (int a = 0; a < 3; ++a) d[a] = xf[a] - CO[a];
-      c[f] = dot3(S, S) / dot3(S, d);
+      c[f] = split_coeff(NO_OVERRELAXED, S, d);
     }
   }
 }

@@ -154,9 +154,11 @@ static std::vector<int32_t> rcm(int nc, const std::vector<int>& ap, const std::v
 // Derived face coefficients (Sec. 2.3.2), FP64:
 //   d   = C_N - C_O (internal), x_f - C_O (boundary)
 //   w_f = S.(C_N - x_f) / S.d                 owner weight of linear interpolation
-//   c_f = |S|^2 / S.d                         over-relaxed |Delta|/|d|
-//   k_f = S - c_f d                           non-orthogonal remainder (internal only)
-__global__ void k_face_coeffs(int ni, int nf, const int2* on, const int* bown, const double* Sf,
+//   c_f = |Delta_f| / |d|                     for the split S = Delta + k of Eq. nonortho_flux:
+//         over-relaxed |S|^2 / S.d, minimum S.d / |d|^2, orthogonal and none |S| / |d|;
+//         boundary faces (no cell-to-cell vector) |S|^2 / S.d for every split
+//   k_f = S - c_f d                           non-orthogonal remainder (internal only; 0 for none)
+__global__ void k_face_coeffs(int ni, int nf, int split, const int2* on, const int* bown, const double* Sf,
                               const double* Cf, const double* C, V4<double>* Sw64,
                               V4<double>* ck64, V4<float>* Sw32, V4<float>* ck32) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -173,8 +175,12 @@ __global__ void k_face_coeffs(int ni, int nf, const int2* on, const int* bown, c
     double d[3] = {CN[0] - CO[0], CN[1] - CO[1], CN[2] - CO[2]};
     double Sd = S[0] * d[0] + S[1] * d[1] + S[2] * d[2];
     w = (S[0] * (CN[0] - xf[0]) + S[1] * (CN[1] - xf[1]) + S[2] * (CN[2] - xf[2])) / Sd;
-    c = SS / Sd;
-    for (int a = 0; a < 3; ++a) k[a] = S[a] - c * d[a];
+    const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (split == DIFVM_NONORTH_MINIMUM) c = Sd / dd;
+    else if (split == DIFVM_NONORTH_ORTHOGONAL || split == DIFVM_NONORTH_NONE) c = sqrt(SS) / sqrt(dd);
+    else c = SS / Sd;
+    if (split != DIFVM_NONORTH_NONE)
+      for (int a = 0; a < 3; ++a) k[a] = S[a] - c * d[a];
   } else {
     double d[3] = {xf[0] - CO[0], xf[1] - CO[1], xf[2] - CO[2]};
     c = SS / (S[0] * d[0] + S[1] * d[1] + S[2] * d[2]);
@@ -242,6 +248,8 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
     return set_error(DIFVM_EINVAL, "bad sizes nc=%d ni=%d nf=%d npatch=%d", nc, ni, nf, np);
   if (!d->owner || (ni > 0 && !d->neighbour) || !d->Sf || !d->Cf || !d->V || !d->C)
     return set_error(DIFVM_EINVAL, "null mesh array");
+  if (d->flags & ~(uint32_t)(DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES | DIFVM_NONORTH_MASK))
+    return set_error(DIFVM_EINVAL, "unknown mesh flags 0x%x", d->flags);
   if (nb > 0 && (!d->patch_start || !d->patch_size || !d->patch_type))
     return set_error(DIFVM_EINVAL, "boundary faces without patches");
   for (int f = 0; f < nf; ++f)
@@ -498,7 +506,8 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload<double>(&m->rV64, nullptr, nc));
   DIFVM_TRY(upload<float>(&m->V32, nullptr, nc));
   DIFVM_TRY(upload<float>(&m->rV32, nullptr, nc));
-  k_face_coeffs<<<blocks_for(nf, 256), 256>>>(ni, nf, m->on, m->bown, Sf_d, m->Cf64, m->C64,
+  k_face_coeffs<<<blocks_for(nf, 256), 256>>>(ni, nf, (int)(d->flags & DIFVM_NONORTH_MASK), m->on, m->bown,
+                                               Sf_d, m->Cf64, m->C64,
                                                m->Sw64, m->ck64, m->Sw32, m->ck32);
   DIFVM_TRY(check_launch("face_coeffs"));
   k_cell_coeffs<<<blocks_for(nc, 256), 256>>>(nc, m->V64, m->rV64, m->V32, m->rV32);

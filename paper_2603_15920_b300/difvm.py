@@ -28,6 +28,8 @@ WK_EXACT, WK_FE, WK_BE = 0, 1, 2
 PCG, BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_AMG, PRECOND_AMG_REUSE = 0, 1, 2, 3
 RENUMBER_RCM, SORT_FACES = 1, 2
+# split of S_f in Eq. nonortho_flux (mesh flags bits 2-3)
+NONORTH_OVERRELAXED, NONORTH_MINIMUM, NONORTH_ORTHOGONAL, NONORTH_NONE = 0, 4, 8, 12
 NONORTH_MOMENTUM, NONORTH_PRESSURE, NONORTH_ALL = 1, 2, 3
 
 _STATUS = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOTCONV: "ENOTCONV",
@@ -207,8 +209,10 @@ class Mesh:
     data between the input numbering and the internal (RCM + sorted) one.
     """
 
-    def __init__(self, m, device=0, flags=RENUMBER_RCM | SORT_FACES, case_cell_start=None):
+    def __init__(self, m, device=0, flags=RENUMBER_RCM | SORT_FACES, case_cell_start=None,
+                 nonorth=NONORTH_OVERRELAXED):
         self.src = m
+        flags = (flags & ~NONORTH_NONE) | nonorth
         self.device = device
         keep = [np.ascontiguousarray(a, dt) for a, dt in (
             (m.owner, np.int32), (m.neighbour, np.int32), (m.Sf, np.float64), (m.Cf, np.float64),

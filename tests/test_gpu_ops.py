@@ -120,6 +120,27 @@ def test_laplacian(name, nonorth, dt):
             assert nrel(got, ref) < TOL[dt] * 4, (cls, nq, nrel(got, ref))
 
 
+SPLITS = [(D.NONORTH_MINIMUM, O.NONORTH_MINIMUM), (D.NONORTH_ORTHOGONAL, O.NONORTH_ORTHOGONAL),
+          (D.NONORTH_NONE, O.NONORTH_NONE)]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("name", ["kuhn10", "dbox"])
+@pytest.mark.parametrize("split", SPLITS, ids=["minimum", "orthogonal", "none"])
+def test_laplacian_nonorth_splits(name, split, dt):
+    # the other splits of Eq. nonortho_flux (mesh flag) against the oracle's
+    m = get(name)[0]
+    om, dm = O.OMesh.from_mesh(m, split[1]), D.Mesh(m, nonorth=split[0])
+    f = mg.random_fields(m, 4)
+    g = np.random.default_rng(6).standard_normal((3, 3, m.n_cells))
+    for cls in (D.BC_VELOCITY, D.BC_ALL_FIXED):
+        ref = O.laplacian(om, bc_table(om, cls), 0.37, f["U"], f["U_b"], g)
+        out = D.difvm_laplacian(dm, cls, 0.37, cuda(dm.to_cells(f["U"]), dt), cuda(dm.to_bnd(f["U_b"]), dt),
+                                cuda(dm.to_cells(g), dt))
+        got = dm.from_cells(out.double().cpu().numpy())
+        assert nrel(got, ref) < TOL[dt] * 4, (cls, nrel(got, ref))
+
+
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("name", list(MESHES))
 def test_laplacian_apply(name, dt):
@@ -177,6 +198,12 @@ def test_bad_arguments_raise():
         D._check(D.lib().difvm_grad_gauss(dm.h, 1, 0, phi.data_ptr(), None, 4, phi.data_ptr(), None))
     with pytest.raises(D.DifvmError):          # bad precision
         D._check(D.lib().difvm_grad_gauss(dm.h, 7, 0, phi.data_ptr(), None, 1, phi.data_ptr(), None))
+
+
+def test_mesh_create_rejects_unknown_flags():
+    m = get("kuhn10")[0]
+    with pytest.raises(D.DifvmError):
+        D.Mesh(m, flags=D.RENUMBER_RCM | 16)
 
 
 def test_mesh_create_rejects_bad_meshes():

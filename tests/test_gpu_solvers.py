@@ -293,6 +293,27 @@ def test_piso_lid_cavity_f64_pinned_pressure(psi, mask):
     assert worst < 1e-9, worst
 
 
+@pytest.mark.parametrize("split", [(D.NONORTH_MINIMUM, O.NONORTH_MINIMUM),
+                                   (D.NONORTH_ORTHOGONAL, O.NONORTH_ORTHOGONAL)], ids=["minimum", "orthogonal"])
+def test_piso_lid_cavity_f64_other_splits(split):
+    # the PISO step on a mesh created with another split of Eq. nonortho_flux
+    m, Ub = _cavity()
+    om, dm = O.OMesh.from_mesh(m, split[1]), D.Mesh(m, nonorth=split[0])
+    pref = 17
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    phi = O.flux_from_U(om, U, Ub)
+    pg = _piso(dm, D.F64, 0.01, 0.05, pref=pref, nonorth=3)
+    worst = 0.0
+    for _ in range(3):
+        g = _state_to_gpu(dm, U, p, phi, Ub, pb)
+        assert pg.step(*g)[0] == D.OK
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12,
+                                          tolp=1e-12, pref_cell=pref, nonorth=3)
+        worst = max(worst, nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p),
+                    nrel(dm.from_faces(host(g[2])), phi))
+    assert worst < 1e-9, worst
+
+
 def test_piso_free_stream_on_gpu():
     m = mg.kuhn_cube(5, 0.2, 5, patch_types=dict(x0=mg.INLET, x1=mg.OUTLET))
     dm = D.Mesh(m)

@@ -61,6 +61,52 @@ def test_overrelaxed_split():
     np.testing.assert_allclose(k, S - Delta, atol=1e-15)
 
 
+@pytest.mark.parametrize("scheme", [O.NONORTH_OVERRELAXED, O.NONORTH_MINIMUM, O.NONORTH_ORTHOGONAL,
+                                    O.NONORTH_NONE])
+def test_nonorth_split_defining_property(scheme):
+    # Each split S = Delta + k of Eq. nonortho_flux (Delta along d) is fixed by one
+    # geometric property: over-relaxed k . S = 0, minimum k . d = 0 (Delta the
+    # projection of S on d), orthogonal |Delta| = |S|; no correction: k = 0 with
+    # the two-point coefficient |S|/|d| of Eq. diff_ortho.
+    m = _kuhn(4, 0.25, 11)
+    w, c, k = O.face_coeffs(O.OMesh.from_mesh(m, scheme))
+    ni = m.n_internal
+    d = m.C[m.neighbour] - m.C[m.owner[:ni]]
+    S = m.Sf[:ni]
+    Sn, dn = np.linalg.norm(S, axis=1), np.linalg.norm(d, axis=1)
+    Delta = c[:ni, None] * d
+    if scheme == O.NONORTH_NONE:
+        assert np.all(k == 0)
+        np.testing.assert_allclose(c[:ni] * dn, Sn, rtol=1e-14)
+    else:
+        np.testing.assert_allclose(Delta + k, S, atol=1e-15)
+        if scheme == O.NONORTH_OVERRELAXED:
+            res = np.einsum("ij,ij->i", k, S) / Sn ** 2
+        elif scheme == O.NONORTH_MINIMUM:
+            res = np.einsum("ij,ij->i", k, d) / (Sn * dn)
+        else:
+            res = (np.linalg.norm(Delta, axis=1) - Sn) / Sn
+        assert np.abs(res).max() < 1e-13
+        # the correction is small but present on these jittered tetrahedra
+        assert np.abs(k).max() > 1e-3 * Sn.max()
+    # boundary faces have no cell-to-cell vector: the same coefficient for every scheme
+    c0 = O.face_coeffs(O.OMesh.from_mesh(m))[1]
+    np.testing.assert_array_equal(c[ni:], c0[ni:])
+
+
+def test_nonorth_splits_agree_on_an_orthogonal_mesh():
+    m = mg.hex_box(3, 4, 5, (1.0, 0.7, 0.3))
+    ref = O.face_coeffs(O.OMesh.from_mesh(m))
+    for scheme in (O.NONORTH_MINIMUM, O.NONORTH_ORTHOGONAL, O.NONORTH_NONE):
+        w, c, k = O.face_coeffs(O.OMesh.from_mesh(m, scheme))
+        np.testing.assert_allclose(c, ref[1], rtol=1e-14)
+        assert np.abs(k).max() < 1e-15
+    # c = |S| / h per direction: areas 0.7/4 * 0.3/5 with spacing 1/3 along x, ...
+    np.testing.assert_allclose(sorted(set(np.round(ref[1][:m.n_internal], 12))),
+                               sorted({round(0.7 / 4 * 0.3 / 5 * 3, 12), round(1 / 3 * 0.3 / 5 * 4 / 0.7, 12),
+                                       round(1 / 3 * 0.7 / 4 * 5 / 0.3, 12)}), rtol=1e-12)
+
+
 # ------------------------------------------------------------------ gradient
 def test_grad_constant_is_zero_on_jittered_tets():
     m = _kuhn(6, 0.2, 1)

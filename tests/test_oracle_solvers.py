@@ -32,8 +32,8 @@ def _f(X):
     return -10 * np.pi ** 2 * s * (y ** 4 - y) + 24 * s * y ** 2
 
 
-def _poisson(m, nonorth=True):
-    om = _om(m)
+def _poisson(m, nonorth=True, scheme=O.NONORTH_OVERRELAXED):
+    om = O.OMesh.from_mesh(m, scheme)
     w, c, k = O.face_coeffs(om)
     D = np.bincount(m.owner, c, m.n_cells) + np.bincount(m.neighbour, c[:m.n_internal], m.n_cells)
     L = -c[:m.n_internal]
@@ -72,6 +72,20 @@ def test_poisson_second_order_with_overrelaxed_correction():
     assert np.all(orders > 1.9), orders
     mx = [b for a, b in e]
     assert np.log2(mx[1] / mx[2]) > 1.5
+
+
+@pytest.mark.parametrize("scheme", [O.NONORTH_MINIMUM, O.NONORTH_ORTHOGONAL])
+def test_poisson_second_order_with_minimum_and_orthogonal_corrections(scheme):
+    # the other two corrected splits of Eq. nonortho_flux are second order too
+    l2 = [_poisson(mg.distorted_box(n, 0.05), scheme=scheme)[0] for n in (8, 16, 32)]
+    orders = np.log2(np.array(l2[:-1]) / np.array(l2[1:]))
+    assert np.all(orders > 1.9), orders
+
+
+def test_poisson_two_point_flux_does_not_converge():
+    # Eq. diff_ortho alone (no correction) on the distorted mesh stalls
+    l2 = [_poisson(mg.distorted_box(n, 0.05), nonorth=False, scheme=O.NONORTH_NONE)[0] for n in (8, 16, 32)]
+    assert np.log2(l2[1] / l2[2]) < 0.5
 
 
 def test_poisson_without_correction_does_not_converge():
