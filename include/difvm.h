@@ -149,6 +149,26 @@ difvm_status difvm_mesh_permutation(difvm_mesh_t, int32_t* cell_new_of_old,
 /* Sizes: n_cells, n_internal, n_faces, n_boundary, n_patches, csr_entries. */
 difvm_status difvm_mesh_info(difvm_mesh_t, int64_t out[6]);
 void difvm_mesh_destroy(difvm_mesh_t);
+
+/* Geometry of a polyhedral mesh given by its vertices (the form of an OpenFOAM
+ * polyMesh), producing the Sf, Cf, V, C of difvm_mesh_desc (Sec. 2.4.1 static
+ * graph arrays; every element type: tetrahedra, hexahedra, prisms, pyramids,
+ * general polyhedra).  All HOST pointers, caller-owned; no device work.
+ *   points[3*n_points] (xyz); face f has the vertices
+ *   face_pts[face_ptr[f] .. face_ptr[f+1]-1] (n_faces+1 pointers, >= 3 vertices
+ *   per face) ordered so that their right-hand normal points out of owner[f];
+ *   faces [0, n_internal) are internal with neighbour[f].
+ * Faces are split into triangles around their vertex average, cells into
+ * pyramids around the average of their face centroids (exact for planar faces).
+ * Outputs Sf[3*n_faces], Cf[3*n_faces], V[n_cells], C[3*n_cells].
+ * Errors: EINVAL with a message for out-of-range indices, faces with fewer than
+ * three vertices or zero area, cells with fewer than four faces, and cells of
+ * non-positive volume (faces not oriented out of their owner). */
+difvm_status difvm_polymesh_geometry(int32_t n_points, const double* points, int32_t n_faces,
+                                     const int32_t* face_ptr, const int32_t* face_pts,
+                                     int32_t n_cells, const int32_t* owner, int32_t n_internal,
+                                     const int32_t* neighbour, double* Sf, double* Cf, double* V,
+                                     double* C);
 const char* difvm_last_error(void);
 /* Number of kernels this library has launched on the calling process (all
  * devices).  For launch accounting in benchmarks. */

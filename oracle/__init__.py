@@ -291,3 +291,49 @@ def piso_step_bwd(m: OMesh, U, p, phi, Ub, pb, Ubar, pbar, phibar, pbbar=None, p
                                 _p(Ubbar), C.byref(nubar), _p(Rpb), _p(Cb), _p(Rdb))
     return dict(U=Ub_, p=pb_, phi=phib_, pb=pbb_, pc=pcb_[:n_out], Ub=Ubbar, nu=nubar.value,
                 Rp=Rpb[:n_out], Cw=Cb[:n_out], Rd=Rdb[:n_out], status=st)
+
+
+# ------------------------------------------------------- polyhedral geometry
+def polymesh_geometry(points, face_ptr, face_pts, owner, neighbour, n_cells):
+    """Geometry of a polyhedral mesh from its vertices (the static graph
+    arrays of Sec. 2.4.1 for a mesh given as points and face vertex loops, the
+    form of an OpenFOAM polyMesh).  Face f has vertices
+    face_pts[face_ptr[f]:face_ptr[f+1]] whose right-hand normal points out of
+    owner[f].  Plain definitions, exact for planar faces:
+      S_f = 1/2 sum_k p_k x p_{k+1}                     (vector area of the loop)
+      x_f = centroid of the polygon: a fan from p_0, triangle centroids
+            weighted by their signed areas along S_f
+      V_i = 1/3 sum_f x_f . S_f^out                     (divergence theorem, div x = 3)
+      C_i = 1/(4 V_i) sum_f (x_f . S_f^out) x_f          (div(x_a x) = 4 x_a; x . n is
+                                                         constant on a planar face)
+    with S_f^out = +S_f for the owner, -S_f for the neighbour.
+    Returns Sf [nf, 3], Cf [nf, 3], V [nc], C [nc, 3]."""
+    P = np.asarray(points, np.float64)
+    fp = np.asarray(face_ptr, np.int64)
+    fv = np.asarray(face_pts, np.int64)
+    nf = fp.shape[0] - 1
+    Sf = np.zeros((nf, 3))
+    Cf = np.zeros((nf, 3))
+    for f in range(nf):
+        v = P[fv[fp[f]:fp[f + 1]]]
+        S = 0.5 * np.cross(v, np.roll(v, -1, axis=0)).sum(axis=0)
+        n = S / np.linalg.norm(S)
+        a_sum, c_sum = 0.0, np.zeros(3)
+        for k in range(1, v.shape[0] - 1):
+            a = 0.5 * np.dot(np.cross(v[k] - v[0], v[k + 1] - v[0]), n)
+            a_sum += a
+            c_sum += a * (v[0] + v[k] + v[k + 1]) / 3.0
+        Sf[f], Cf[f] = S, c_sum / a_sum
+    own = np.asarray(owner, np.int64)
+    nei = np.asarray(neighbour, np.int64)
+    ni = nei.shape[0]
+    xs = np.einsum("ij,ij->i", Cf, Sf)
+    vol = np.zeros(n_cells)
+    mom = np.zeros((n_cells, 3))
+    for f in range(nf):
+        vol[own[f]] += xs[f] / 3.0
+        mom[own[f]] += xs[f] * Cf[f] / 4.0
+        if f < ni:
+            vol[nei[f]] -= xs[f] / 3.0
+            mom[nei[f]] -= xs[f] * Cf[f] / 4.0
+    return Sf, Cf, vol, mom / vol[:, None]

@@ -114,6 +114,7 @@ _SIGS = {
     "difvm_flux_from_U": [_vp, _i, _vp, _vp, _vp, _vp],
     "difvm_laplacian_apply_bwd_noalloc": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
                                           _vp],
+    "difvm_polymesh_geometry": [_i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp],
     "difvm_prof_start": [_i, _i],
     "difvm_prof_stop": [_vp, _vp],
 }
@@ -157,6 +158,24 @@ def lib():
 def _check(st):
     if st != OK:
         raise DifvmError(st, lib().difvm_last_error().decode())
+
+
+def difvm_polymesh_geometry(points, face_ptr, face_pts, owner, neighbour, n_cells):
+    """Face area vectors and centroids, cell volumes and centroids of a
+    polyhedral mesh given by vertices and face vertex loops (host arrays, input
+    numbering; see include/difvm.h).  Returns (Sf [nf,3], Cf [nf,3], V [nc], C [nc,3])."""
+    P = np.ascontiguousarray(points, np.float64)
+    fp = np.ascontiguousarray(face_ptr, np.int32)
+    fv = np.ascontiguousarray(face_pts, np.int32)
+    own = np.ascontiguousarray(owner, np.int32)
+    nei = np.ascontiguousarray(neighbour, np.int32)
+    nf, nc = int(fp.shape[0] - 1), int(n_cells)
+    Sf, Cf = np.empty((nf, 3)), np.empty((nf, 3))
+    V, Cc = np.empty(nc), np.empty((nc, 3))
+    _check(lib().difvm_polymesh_geometry(int(P.shape[0]), P.ctypes.data, nf, fp.ctypes.data, fv.ctypes.data,
+                                         nc, own.ctypes.data, int(nei.shape[0]), nei.ctypes.data,
+                                         Sf.ctypes.data, Cf.ctypes.data, V.ctypes.data, Cc.ctypes.data))
+    return Sf, Cf, V, Cc
 
 
 def launch_count() -> int:

@@ -48,6 +48,12 @@ class Mesh:
     patch_start: np.ndarray = None   # int32 [np], absolute face index
     patch_size: np.ndarray = None    # int32 [np]
     patch_type: np.ndarray = None    # int32 [np]
+    # vertex topology (polyMesh form), when the generator keeps it: points [np, 3];
+    # the vertices of face f are face_pts[face_ptr[f]:face_ptr[f + 1]], ordered so that
+    # their right-hand normal points out of the owner
+    points: np.ndarray = None
+    face_ptr: np.ndarray = None
+    face_pts: np.ndarray = None
 
     @property
     def n_faces(self) -> int:
@@ -93,8 +99,9 @@ class Mesh:
         return self
 
 
-def _finish(nc, owner, neighbour, Sf, Cf, V, C, bnd_groups, names, types):
-    """Assemble a Mesh from internal faces plus boundary face groups."""
+def _finish(nc, owner, neighbour, Sf, Cf, V, C, bnd_groups, names, types, topo=None):
+    """Assemble a Mesh from internal faces plus boundary face groups.  topo:
+    (points, internal face vertices [ni, k], [group face vertices [n_g, k]])."""
     o_i, S_i, X_i = owner, Sf, Cf
     o_b = [g[0] for g in bnd_groups]
     S_b = [g[1] for g in bnd_groups]
@@ -113,6 +120,14 @@ def _finish(nc, owner, neighbour, Sf, Cf, V, C, bnd_groups, names, types):
         patch_names=list(names), patch_start=starts, patch_size=sizes,
         patch_type=np.array(types, np.int32),
     )
+    if topo is not None:
+        pts, fv_i, fv_b = topo
+        fv = [np.asarray(a, np.int64) for a in [fv_i] + list(fv_b)]
+        counts = np.concatenate([np.full(a.shape[0], a.shape[1]) for a in fv])
+        m.points = np.ascontiguousarray(pts, np.float64)
+        m.face_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        m.face_pts = np.ascontiguousarray(np.concatenate([a.ravel() for a in fv]).astype(np.int32))
+        assert m.face_ptr[-1] == m.face_pts.shape[0] and m.face_ptr.shape[0] == m.n_faces + 1
     return m.check()
 
 
@@ -122,7 +137,7 @@ def shuffle(mesh: Mesh, seed: int) -> Mesh:
     Face orientation is kept (S_f still points out of the same physical cell),
     so an internal face may end up with owner id > neighbour id.  This is the
     'cell ids randomly permuted by seed' input of the channel run; the loader
-    must undo the locality loss.
+    must undo the locality loss.  The vertex topology is not carried over.
     """
     rng = np.random.default_rng(seed)
     nc, ni, nf = mesh.n_cells, mesh.n_internal, mesh.n_faces
@@ -299,22 +314,24 @@ def kuhn_cube(n: int, jitter: float = 0.0, seed: int = 0, patch_types=None) -> M
         Xf = (A + B + Cc) / 3.0
         sgn = np.sign(np.einsum("ij,ij->i", S, Xf - C[own]))
         assert np.all(sgn != 0)
-        return S * sgn[:, None], Xf
+        oriented = np.where(sgn[:, None] > 0, fverts, fverts[:, ::-1])
+        return S * sgn[:, None], Xf, oriented
 
-    S_i, X_i = geom(fvi, own_i)
-    S_b, X_b = geom(fvb, own_b)
+    S_i, X_i, fvi_o = geom(fvi, own_i)
+    S_b, X_b, fvb_o = geom(fvb, own_b)
     types = dict(x0=WALL, x1=WALL, y0=WALL, y1=WALL, z0=WALL, z1=WALL)
     if patch_types:
         types.update(patch_types)
-    groups, names = [], []
+    groups, names, gfv = [], [], []
     tol = 1e-9
     for ax, (lo, hi) in enumerate([("x0", "x1"), ("y0", "y1"), ("z0", "z1")]):
         for name, val in ((lo, 0.0), (hi, 1.0)):
             sel = np.abs(X_b[:, ax] - val) < tol
             groups.append((own_b[sel], S_b[sel], X_b[sel])); names.append(name)
+            gfv.append(fvb_o[sel])
     assert sum(g[0].shape[0] for g in groups) == own_b.shape[0] == 12 * n * n
     return _finish(nc, own_i, nei_i, S_i, X_i, V, C, groups, names,
-                   [types[nm] for nm in names])
+                   [types[nm] for nm in names], topo=(P, fvi_o, gfv))
 
 
 # ---------------------------------------------------------------------------
@@ -358,6 +375,13 @@ def extrude_quads(xy, quads, n_layers, Lz, edge_patch, edge_patch_names, edge_pa
     C = np.stack([np.tile(cxq, n_layers), np.tile(cyq, n_layers), (lay + 0.5) * dz], 1)
     V = np.tile(A2, n_layers) * dz
 
+    P3 = np.concatenate([np.concatenate([xy, np.full((nv2, 1), l * dz)], 1) for l in range(n_layers + 1)])
+    vtx = lambda v, l: v + nv2 * l    # vertex v of the 2D mesh on plane z = l dz
+
+    def side_v(slot, l):                 # (a, l) (b, l) (b, l+1) (a, l+1): normal out of the first quad
+        e = ed[order[slot]]
+        return np.stack([vtx(e[:, 0], l), vtx(e[:, 1], l), vtx(e[:, 1], l + 1), vtx(e[:, 0], l + 1)], 1)
+
     def side(slot, l):
         e = ed[order[slot]]              # directed edge as seen from its first quad
         pa, pb = xy[e[:, 0]], xy[e[:, 1]]
@@ -367,40 +391,46 @@ def extrude_quads(xy, quads, n_layers, Lz, edge_patch, edge_patch_names, edge_pa
                       np.full(len(e), (l + 0.5) * dz)], 1)
         return S, X
 
-    own, nei, S, X = [], [], [], []
+    own, nei, S, X, FV = [], [], [], [], []
     qa, qb = eq[order[pair]], eq[order[pair + 1]]
     for l in range(n_layers):
         Sl, Xl = side(pair, l)
         own.append(cell(qa, l)); nei.append(cell(qb, l)); S.append(Sl); X.append(Xl)
+        FV.append(side_v(pair, l))
     zero = np.zeros(nq2)
     for l in range(n_layers - 1):
         own.append(cell(np.arange(nq2), l)); nei.append(cell(np.arange(nq2), l + 1))
         S.append(np.stack([zero, zero, A2], 1))
         X.append(np.stack([cxq, cyq, np.full(nq2, (l + 1) * dz)], 1))
+        FV.append(vtx(quads, l + 1))     # counter-clockwise: normal +z, out of the lower cell
     own_i, nei_i = np.concatenate(own), np.concatenate(nei)
     S_i, X_i = np.concatenate(S), np.concatenate(X)
+    FV_i = np.concatenate(FV)
     flip = own_i > nei_i
     own_i, nei_i = np.where(flip, nei_i, own_i), np.where(flip, own_i, nei_i)
     S_i[flip] *= -1
+    FV_i[flip] = FV_i[flip][:, ::-1]
     wq = eq[order[single]]
     e_single = ed[order[single]]
     mids = 0.5 * (xy[e_single[:, 0]] + xy[e_single[:, 1]])
     pid = np.array([edge_patch(mid) for mid in mids], np.int64)
-    groups, names, types = [], [], []
+    groups, names, types, gfv = [], [], [], []
     for p, (nm, tp) in enumerate(zip(edge_patch_names, edge_patch_types)):
         sel = pid == p
-        wo, wS, wX = [], [], []
+        wo, wS, wX, wv = [], [], [], []
         for l in range(n_layers):
             Sl, Xl = side(single[sel], l)
-            wo.append(cell(wq[sel], l)); wS.append(Sl); wX.append(Xl)
+            wo.append(cell(wq[sel], l)); wS.append(Sl); wX.append(Xl); wv.append(side_v(single[sel], l))
         groups.append((np.concatenate(wo), np.concatenate(wS), np.concatenate(wX)))
         names.append(nm); types.append(tp)
+        gfv.append(np.concatenate(wv) if wv else np.zeros((0, 4), np.int64))
     groups.append((cell(np.arange(nq2), 0), np.stack([zero, zero, -A2], 1),
                    np.stack([cxq, cyq, np.zeros(nq2)], 1)))
     groups.append((cell(np.arange(nq2), n_layers - 1), np.stack([zero, zero, A2], 1),
                    np.stack([cxq, cyq, np.full(nq2, Lz)], 1)))
+    gfv += [vtx(quads, 0)[:, ::-1], vtx(quads, n_layers)]
     names += [bottom[0], top[0]]; types += [bottom[1], top[1]]
-    return _finish(nc, own_i, nei_i, S_i, X_i, V, C, groups, names, types)
+    return _finish(nc, own_i, nei_i, S_i, X_i, V, C, groups, names, types, topo=(P3, FV_i, gfv))
 
 
 def pipe_ohgrid(n_core=16, n_outer=8, n_layers=200, R=1.0, L=10.0, core_frac=0.5,
