@@ -55,6 +55,7 @@ enum { PT_WALL = 0, PT_INLET = 1, PT_OUTLET = 2, PT_EMPTY = 3 };
 enum { DIV_UPWIND = 0, DIV_LINEAR = 1 };
 enum { WK_EXACT = 0, WK_FE = 1, WK_BE = 2 };
 enum { NO_OVERRELAXED = 0, NO_MINIMUM = 1, NO_ORTHOGONAL = 2, NO_NONE = 3 };
+enum { CONV_UPWIND = 0, CONV_SOU = 1 };
 
 static double dot3(const double *a, const double *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -429,11 +430,16 @@ void om_windkessel_update(int n, int scheme, const double *Rp, const double *Cc,
  *   Up_f = min(m,0) - nu c   (row O, column N)
  *   Lo_f = -max(m,0) - nu c  (row N, column O)
  *   b_i  = V_i/dt U^n_i + sigma nu (gradU)_f . k_f + bnd   (correction limited by psi)
- * boundary fixed U: D += nu c, b += (nu c - m) U_b;  zero gradient: D += m. */
+ * boundary fixed U: D += nu c, b += (nu c - m) U_b;  zero gradient: D += m.
+ * gradS (may be NULL): second-order upwind by deferred correction (Eqs.
+ * deferred_correction, sou): on every internal face the explicit part
+ *   t_f = m (gradS)_C . (x_f - x_C),  C = O if m >= 0 else N   (Eq. upwind)
+ * leaves the upwind cell's row: b_O -= t_f, b_N += t_f.  Boundary faces keep
+ * their boundary-condition face value. */
 void om_momentum_assemble(const om_mesh *m, const int *bcU, double nu, double dt,
                           const double *mf, const double *Uold, const double *Ub,
-                          const double *gradU, double psi, double *D, double *Lo, double *Up,
-                          double *b) {
+                          const double *gradU, const double *gradS, double psi, double *D,
+                          double *Lo, double *Up, double *b) {
   int nc = m->nc, nb = m->nf - m->nint;
   double *w = malloc(sizeof(double) * (m->nint + 1));
   double *c = malloc(sizeof(double) * (m->nf + 1));
@@ -462,6 +468,18 @@ void om_momentum_assemble(const om_mesh *m, const int *bcU, double nu, double dt
           double corr = nu * limit_corr(dot3(gf, k + 3 * f), orth, psi);
           b[q * nc + O] += corr;
           b[q * nc + N] -= corr;
+        }
+      }
+      if (gradS) {
+        int Cu = mm >= 0.0 ? O : N;
+        double dC[3];
+        for (int a = 0; a < 3; ++a) dC[a] = m->Cf[3 * f + a] - m->C[3 * Cu + a];
+        for (int q = 0; q < 3; ++q) {
+          const double *g = gradS + (size_t)q * 3 * nc;
+          double gC[3] = {g[Cu], g[nc + Cu], g[2 * nc + Cu]};
+          double t = mm * dot3(gC, dC);
+          b[q * nc + O] -= t;
+          b[q * nc + N] += t;
         }
       }
     } else {
@@ -570,6 +588,7 @@ typedef struct {
   const int *wk_patch;          /* [n_out] patch ids */
   const double *Rp, *Cw, *Rd;   /* [n_out] */
   double psi;                   /* non-orthogonal limiter coefficient (1 = unlimited) */
+  int conv;                     /* momentum convection: CONV_UPWIND or CONV_SOU (deferred correction) */
 } om_piso_opts;
 
 typedef struct { int itU[3], itp[4], status; double Q[8], po[8]; } om_piso_info;
@@ -612,9 +631,9 @@ int om_piso_step(const om_mesh *m, const om_piso_opts *o, double *U, double *p, 
   om_info si;
   /* 2. momentum predictor: A U* = b - V grad p^n */
   om_grad_gauss(m, bcp, 1, p, pb, gradp);
-  if (o->nonorth & 1) om_grad_gauss(m, bcU, 3, U, Ub, gradU);
-  om_momentum_assemble(m, bcU, o->nu, o->dt, phi, U, Ub, (o->nonorth & 1) ? gradU : NULL, o->psi,
-                       D, Lo, Up, b);
+  if ((o->nonorth & 1) || o->conv == CONV_SOU) om_grad_gauss(m, bcU, 3, U, Ub, gradU);
+  om_momentum_assemble(m, bcU, o->nu, o->dt, phi, U, Ub, (o->nonorth & 1) ? gradU : NULL,
+                       o->conv == CONV_SOU ? gradU : NULL, o->psi, D, Lo, Up, b);
   for (int q = 0; q < 3; ++q) {
     for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gradp[q * nc + i];
     int st = om_bicgstab(m, D, Lo, Up, rhs, U + (size_t)q * nc, o->tolU, o->tol_abs, o->maxitU, &si);
@@ -739,7 +758,7 @@ int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in
                      double *phibar, double *pbbar, double *pcbar, double *Ubbar, double *nubar,
                      double *Rpbar, double *Cbar, double *Rdbar) {
   const int nc = m->nc, nf = m->nf, ni = m->nint, nb = nf - ni, K = o->ncorr;
-  const int nonU = (o->nonorth & 1) != 0, nonP = (o->nonorth & 2) != 0;
+  const int nonU = (o->nonorth & 1) != 0, nonP = (o->nonorth & 2) != 0, sou = o->conv == CONV_SOU;
   int status = 0;
   int *bcU = malloc(sizeof(int) * m->npatch), *bcp = malloc(sizeof(int) * m->npatch);
   int has_fixed_p = 0;
@@ -779,9 +798,9 @@ int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in
   double *H = malloc(sizeof(double) * 3 * nc);
   memcpy(ps, p_in, sizeof(double) * nc);
   om_grad_gauss(m, bcp, 1, p_in, pb, gp);
-  if (nonU) om_grad_gauss(m, bcU, 3, U_in, Ub, gradU);
-  om_momentum_assemble(m, bcU, o->nu, o->dt, phi_in, U_in, Ub, nonU ? gradU : NULL, o->psi, D, Lo,
-                       Up, b);
+  if (nonU || sou) om_grad_gauss(m, bcU, 3, U_in, Ub, gradU);
+  om_momentum_assemble(m, bcU, o->nu, o->dt, phi_in, U_in, Ub, nonU ? gradU : NULL,
+                       sou ? gradU : NULL, o->psi, D, Lo, Up, b);
   memcpy(Us, U_in, sizeof(double) * 3 * nc);
   for (int q = 0; q < 3; ++q) {
     for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gp[q * nc + i];
@@ -1002,6 +1021,19 @@ int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in
           Un_b[q * nc + O] -= lb * dorth * c[f];
         }
       }
+      if (sou) {   /* t_f = m (gradU)_C . d_Cf enters b_O with -1, b_N with +1 */
+        int Cu = mm >= 0.0 ? O : N;
+        double dC[3];
+        for (int a = 0; a < 3; ++a) dC[a] = m->Cf[3 * f + a] - m->C[3 * Cu + a];
+        for (int q = 0; q < 3; ++q) {
+          const double *g = gradU + (size_t)q * 3 * nc;
+          double gC[3] = {g[Cu], g[nc + Cu], g[2 * nc + Cu]};
+          double tb = bb[q * nc + N] - bb[q * nc + O];
+          phin_b[f] += tb * dot3(gC, dC);
+          double *gq = gUb + (size_t)q * 3 * nc;
+          for (int d = 0; d < 3; ++d) gq[d * nc + Cu] += tb * mm * dC[d];
+        }
+      }
     } else {
       int kind = bcU[patch_of_face(m, f)], bf = f - ni;
       if (kind == BC_FIXED) {
@@ -1017,7 +1049,7 @@ int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in
       }
     }
   }
-  if (nonU)
+  if (nonU || sou)
     for (int q = 0; q < 3; ++q)
       grad_gauss_T(m, w, bcU, gUb + (size_t)q * 3 * nc, Un_b + (size_t)q * nc, Ubbar + (size_t)q * nb);
   /* Windkessel: pb on an outlet patch is p_o, both inside the step and in its output */

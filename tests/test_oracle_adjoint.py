@@ -44,21 +44,25 @@ def _fwd(om, x, kw):
     return dict(U=U, p=p, phi=phi, pb=pb, pc=pc)
 
 
-CASES = [  # (mesh / outlet kind, non-orthogonal mask, limiter psi, correctors)
-    ("wk_exact", 3, 1.0, 2),
-    ("wk_exact", 3, 0.5, 2),
-    ("wk_fe", 1, 0.3, 2),
-    ("wk_be", 0, 1.0, 1),
-    ("outlet", 3, 0.5, 3),
-    ("cavity", 3, 0.5, 2),
-    ("cavity", 2, 1.0, 3),
+UP, SOU = O.CONV_UPWIND, O.CONV_SOU
+CASES = [  # (mesh / outlet kind, non-orthogonal mask, limiter psi, correctors, convection)
+    ("wk_exact", 3, 1.0, 2, UP),
+    ("wk_exact", 3, 0.5, 2, UP),
+    ("wk_fe", 1, 0.3, 2, UP),
+    ("wk_be", 0, 1.0, 1, UP),
+    ("outlet", 3, 0.5, 3, UP),
+    ("cavity", 3, 0.5, 2, UP),
+    ("cavity", 2, 1.0, 3, UP),
+    ("outlet", 0, 1.0, 2, SOU),
+    ("cavity", 3, 0.5, 2, SOU),
+    ("wk_exact", 1, 1.0, 2, SOU),
 ]
 
 
-@pytest.mark.parametrize("kind,mask,psi,ncorr", CASES)
-def test_piso_step_adjoint_matches_central_differences(kind, mask, psi, ncorr):
+@pytest.mark.parametrize("kind,mask,psi,ncorr,conv", CASES)
+def test_piso_step_adjoint_matches_central_differences(kind, mask, psi, ncorr, conv):
     om, x, kw = _case(kind, seed=len(kind) + mask)
-    kw.update(nonorth=mask, psi=psi, ncorr=ncorr)
+    kw.update(nonorth=mask, psi=psi, ncorr=ncorr, conv=conv)
     y = _fwd(om, x, kw)
     rng = np.random.default_rng(11)
     w = {k: rng.normal(size=np.shape(v)) for k, v in y.items()}
