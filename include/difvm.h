@@ -370,7 +370,14 @@ typedef struct {
   double nonorth_limit; /* psi in (0,1): cap each explicit non-orthogonal correction at
                            psi/(1-psi) x the face's orthogonal part (the "limited" form of
                            Eq. nonortho_flux); 0 or >= 1: unlimited over-relaxed correction */
+  int32_t conv;         /* momentum convection: DIFVM_CONV_UPWIND (Eq. upwind, implicit) or
+                           DIFVM_CONV_SOU, second-order upwind by deferred correction (Eqs.
+                           deferred_correction, sou): the matrix stays upwind and each internal
+                           face adds m_f (grad U^n)_C . (x_f - x_C) of its upwind cell C to the
+                           explicit part (boundary faces keep their condition's face value) */
+  int32_t pad;
 } difvm_piso_opts;
+enum { DIFVM_CONV_UPWIND = 0, DIFVM_CONV_SOU = 1 };
 
 typedef struct difvm_piso* difvm_piso_t;
 /* Create a PISO driver for one mesh and precision; owns all step workspace. */

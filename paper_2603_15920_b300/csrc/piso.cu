@@ -31,6 +31,7 @@ struct difvm_piso {
   void *gradp = nullptr, *gradU = nullptr, *D = nullptr, *Lo = nullptr, *Up = nullptr, *b = nullptr;
   void *rhs = nullptr, *rAU = nullptr, *HbyA = nullptr, *Dp = nullptr, *Lp = nullptr, *bp = nullptr;
   void *phiHbyA = nullptr, *af = nullptr, *nonorth = nullptr;
+  void* sou_d = nullptr;           // second-order upwind: V4<T> x_f - x_O [ni], then x_f - x_N [ni]
   void* wsU = nullptr;
   size_t wsU_bytes = 0;
   void* wsp = nullptr;
@@ -46,6 +47,7 @@ struct difvm_piso {
   void *a_bb = nullptr, *a_Lob = nullptr, *a_Upb = nullptr, *a_lam = nullptr, *a_lamU = nullptr;
   void *a_phiHb = nullptr, *a_rfb = nullptr, *a_lk = nullptr, *a_ld = nullptr, *a_phio = nullptr;
   void *a_pbb = nullptr, *a_gUb = nullptr, *a_lkU = nullptr, *a_ldU = nullptr, *a_gp2 = nullptr;
+  void* a_lsU = nullptr;           // second-order upwind: per face and component, t_bar m
   double *a_nuf = nullptr, *a_part = nullptr;
   // starting guesses of the adjoint pressure solves, one per corrector (FP64 on
   // mixed-precision handles): the previous reverse step's solutions
@@ -184,12 +186,26 @@ __global__ void k_mom_faces(int ni, Geo<T> g, T nu, const T* phi, T* Lo, T* Up) 
   Lo[f] = -fmax(m, T(0)) - a;
 }
 
+// x_f - x_O and x_f - x_N of every internal face (second-order upwind reconstruction)
+template <typename T>
+__global__ void k_sou_d(int ni, const int2* on, const double* Cf, const double* C, V4<T>* d) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= ni) return;
+  const int O = on[f].x, N = on[f].y;
+  d[f] = V4<T>{(T)(Cf[3 * f] - C[3 * O]), (T)(Cf[3 * f + 1] - C[3 * O + 1]), (T)(Cf[3 * f + 2] - C[3 * O + 2]), T(0)};
+  d[ni + f] = V4<T>{(T)(Cf[3 * f] - C[3 * N]), (T)(Cf[3 * f + 1] - C[3 * N + 1]),
+                    (T)(Cf[3 * f + 2] - C[3 * N + 2]), T(0)};
+}
+
 // cells: D = V/dt + sum over faces; b = V/dt U^n + sigma nu (gradU)_f.k + boundary;
-// rhs = b - V grad p
-template <typename T, bool NONORTH>
+// rhs = b - V grad p.  SOU: second-order upwind by deferred correction (Eqs.
+// deferred_correction, sou): each internal face moves t_f = m (gradU)_C . (x_f - x_C)
+// of its upwind cell C (the owner when m >= 0) out of the owner's row into the
+// neighbour's: b_O -= t_f, b_N += t_f.
+template <typename T, bool NONORTH, bool SOU>
 __global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt, T psi, const T* phi,
                                                    const T* U, const T* Ub, const T* gradU,
-                                                   const T* gradp, T* D, T* b, T* rhs) {
+                                                   const V4<T>* sd, const T* gradp, T* D, T* b, T* rhs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc, nb = t.nb;
@@ -199,7 +215,7 @@ __global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt
 #pragma unroll
   for (int c = 0; c < 3; ++c) bc[c] = V * rdt * U[c * nc + i];
   T gi[3][3];
-  if (NONORTH)
+  if (NONORTH || SOU)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -214,23 +230,41 @@ __global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt
     if (f < t.ni) {
       const bool nside = ent & 1;
       d += (nside ? fmax(-m, T(0)) : fmax(m, T(0))) + a;
-      if (NONORTH) {
+      if (NONORTH || SOU) {
         const int2 on = t.on[f];
         const int j = nside ? on.x : on.y;
-        const T w = ld4(g.Sw + f).w;
+        const bool upO = m >= T(0);             // the owner is the upwind cell
+        const bool up_self = upO != nside;      // this cell is the upwind cell
+        T gj[3][3];
+        if (NONORTH || !up_self)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          T gf[3];
+          for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const T gj = gradU[(c * 3 + k) * nc + j];
-            const T gO = nside ? gj : gi[c][k], gN = nside ? gi[c][k] : gj;
-            gf[k] = w * gO + (T(1) - w) * gN;
+            for (int k = 0; k < 3; ++k) gj[c][k] = gradU[(c * 3 + k) * nc + j];
+        if (NONORTH) {
+          const T w = ld4(g.Sw + f).w;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            T gf[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const T gO = nside ? gj[c][k] : gi[c][k], gN = nside ? gi[c][k] : gj[c][k];
+              gf[k] = w * gO + (T(1) - w) * gN;
+            }
+            const T uj = U[c * nc + j], ui = U[c * nc + i];
+            const T orth = ck.x * (nside ? ui - uj : uj - ui);
+            const T corr = nu * limit_corr(gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w, orth, psi);
+            bc[c] += nside ? -corr : corr;
           }
-          const T uj = U[c * nc + j], ui = U[c * nc + i];
-          const T orth = ck.x * (nside ? ui - uj : uj - ui);
-          const T corr = nu * limit_corr(gf[0] * ck.y + gf[1] * ck.z + gf[2] * ck.w, orth, psi);
-          bc[c] += nside ? -corr : corr;
+        }
+        if (SOU) {
+          const V4<T> dc = ld4(sd + (upO ? f : t.ni + f));
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T* gC = up_self ? gi[c] : gj[c];
+            const T tf = m * (gC[0] * dc.x + gC[1] * dc.y + gC[2] * dc.z);
+            bc[c] += nside ? tf : -tf;
+          }
         }
       }
     } else {
@@ -743,11 +777,11 @@ __global__ void k_adj_mom_cells(int nc, Geo<T> g, T rdt, const T* D, const T* la
 // Momentum assembly backwards, per face: the face flux adjoint (upwind switch),
 // the viscosity adjoint contribution (FP64, reduced later in a fixed order), the
 // limited non-orthogonal correction (lkU / ldU per component), U_b_bar.
-template <typename T, bool NONORTH>
+template <typename T, bool NONORTH, bool SOU>
 __global__ void k_adj_mom_faces(Topo t, Geo<T> g, T nu, T psi, const T* phi0, const T* Db,
                                 const T* bb, const T* Lob, const T* Upb, const T* lamU,
                                 const T* Ustar, const T* U0, const T* gradU, const T* Ub, T* phib,
-                                double* nuf, T* lkU, T* ldU, T* Ubb) {
+                                double* nuf, T* lkU, T* ldU, const V4<T>* sd, T* lsU, T* Ubb) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nf) return;
   const int nc = t.nc, nb = t.nb, ni = t.ni;
@@ -785,6 +819,20 @@ __global__ void k_adj_mom_faces(Topo t, Geo<T> g, T nu, T psi, const T* phi0, co
         ldU[c * ni + f] = lb * dorth * ck.x;
       }
     }
+    if (SOU) {   // t_f = m (gradU)_C . d_Cf enters b_O with -1 and b_N with +1
+      const bool upO = m >= T(0);
+      const int Cu = upO ? O : N;
+      const V4<T> dc = ld4(sd + (upO ? f : ni + f));
+      T mb = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T tb = bb[c * nc + N] - bb[c * nc + O];
+        mb += tb * (gradU[(c * 3) * nc + Cu] * dc.x + gradU[(c * 3 + 1) * nc + Cu] * dc.y +
+                    gradU[(c * 3 + 2) * nc + Cu] * dc.z);
+        lsU[c * ni + f] = tb * m;
+      }
+      phib[f] += mb;
+    }
     nuf[f] = nv;
   } else {
     const int b = f - ni;
@@ -809,10 +857,11 @@ __global__ void k_adj_mom_faces(Topo t, Geo<T> g, T nu, T psi, const T* phi0, co
 }
 
 // Gather of the momentum non-orthogonal terms: (grad U^n)_bar (overwritten) and
-// the limiter's U^n_bar terms.
-template <typename T>
+// the limiter's U^n_bar terms; SOU: the upwind cell's share t_bar m (x_f - x_C).
+template <typename T, bool NONORTH, bool SOU>
 __global__ void __launch_bounds__(kPB) k_adj_mom_cells2(Topo t, Geo<T> g, const T* lkU,
-                                                        const T* ldU, T* gUb, T* Ubar) {
+                                                        const T* ldU, const T* phi0, const V4<T>* sd,
+                                                        const T* lsU, T* gUb, T* Ubar) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc, ni = t.ni;
@@ -829,17 +878,29 @@ __global__ void __launch_bounds__(kPB) k_adj_mom_cells2(Topo t, Geo<T> g, const 
     const int f = ent >> 1;
     if (f >= ni) break;
     const bool nside = ent & 1;
-    const T w = ld4(g.Sw + f).w;
-    const T wi = nside ? T(1) - w : w;
-    const V4<T> ck = ld4(g.ck + f);
+    if (NONORTH) {
+      const T w = ld4(g.Sw + f).w;
+      const T wi = nside ? T(1) - w : w;
+      const V4<T> ck = ld4(g.ck + f);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T l = wi * lkU[c * ni + f];
-      ga[c][0] += l * ck.y;
-      ga[c][1] += l * ck.z;
-      ga[c][2] += l * ck.w;
-      const T d = ldU[c * ni + f];
-      ua[c] += nside ? d : -d;
+      for (int c = 0; c < 3; ++c) {
+        const T l = wi * lkU[c * ni + f];
+        ga[c][0] += l * ck.y;
+        ga[c][1] += l * ck.z;
+        ga[c][2] += l * ck.w;
+        const T d = ldU[c * ni + f];
+        ua[c] += nside ? d : -d;
+      }
+    }
+    if (SOU && ((phi0[f] >= T(0)) != nside)) {   // this cell is the face's upwind cell
+      const V4<T> dc = ld4(sd + (nside ? ni + f : f));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T l = lsU[c * ni + f];
+        ga[c][0] += l * dc.x;
+        ga[c][1] += l * dc.y;
+        ga[c][2] += l * dc.z;
+      }
     }
   }
 #pragma unroll
@@ -954,6 +1015,14 @@ static TapeLayout tape_layout(const difvm_piso* h) {
   return L;
 }
 
+template <typename T, typename... A>
+static void launch_mom_cells(bool no_U, bool sou, unsigned Bc, cudaStream_t st, A... a) {
+  if (no_U && sou) k_mom_cells<T, true, true><<<Bc, kPB, 0, st>>>(a...);
+  else if (no_U) k_mom_cells<T, true, false><<<Bc, kPB, 0, st>>>(a...);
+  else if (sou) k_mom_cells<T, false, true><<<Bc, kPB, 0, st>>>(a...);
+  else k_mom_cells<T, false, false><<<Bc, kPB, 0, st>>>(a...);
+}
+
 template <typename T>
 static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, T* pb, double* wk,
                                 difvm_piso_info* info, unsigned char* tape, cudaStream_t st) {
@@ -1007,16 +1076,15 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
   const bool no_U = (o.nonorth & DIFVM_NONORTH_MOMENTUM) != 0;
   const bool no_p = (o.nonorth & DIFVM_NONORTH_PRESSURE) != 0;
-  if (no_U) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U, Ub, 3, gradU, st));
+  const bool sou = o.conv == DIFVM_CONV_SOU;
+  if (no_U || sou) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U, Ub, 3, gradU, st));
   if (ni > 0) {
     k_mom_faces<T><<<Bi, kPB, 0, st>>>(ni, g, (T)o.nu, phi, Lo, Up);
     DIFVM_TRY(check_launch("mom_faces"));
   }
   const T psi = (T)o.nonorth_limit;
-  if (no_U)
-    k_mom_cells<T, true><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi, U, Ub, gradU, gradp, D, b, rhs);
-  else
-    k_mom_cells<T, false><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi, U, Ub, gradU, gradp, D, b, rhs);
+  launch_mom_cells<T>(no_U, sou, Bc, st, t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi, U, Ub, gradU,
+                      (const V4<T>*)h->sou_d, gradp, D, b, rhs);
   DIFVM_TRY(check_launch("mom_cells"));
   {
     difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
@@ -1142,6 +1210,8 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
   if (!(o->dt > 0) || !(o->nu >= 0)) return set_error(DIFVM_EINVAL, "need dt > 0 and nu >= 0");
   if (o->n_corr < 1 || o->n_corr > 8) return set_error(DIFVM_EINVAL, "n_corr must be 1..8");
   if (o->n_out < 0 || o->n_out > 16) return set_error(DIFVM_EINVAL, "n_out must be 0..16");
+  if (o->conv != DIFVM_CONV_UPWIND && o->conv != DIFVM_CONV_SOU)
+    return set_error(DIFVM_EINVAL, "unknown convection scheme %d", o->conv);
   if (o->solve_U.method != DIFVM_BICGSTAB && o->solve_U.method != DIFVM_PCG)
     return set_error(DIFVM_EINVAL, "bad momentum solver");
   if (o->solve_p.method != DIFVM_PCG && o->solve_p.method != DIFVM_BICGSTAB)
@@ -1207,7 +1277,8 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
             alloc(&h->Lo, ni * e) && alloc(&h->Up, ni * e) && alloc(&h->b, 3 * nc * e) &&
             alloc(&h->rhs, 3 * nc * e) && alloc(&h->rAU, nc * e) && alloc(&h->HbyA, 3 * nc * e) &&
             alloc(&h->Dp, nc * e) && alloc(&h->Lp, ni * e) && alloc(&h->bp, nc * e) &&
-            alloc(&h->phiHbyA, nf * e) && alloc(&h->af, nf * e) && alloc(&h->nonorth, ni * e);
+            alloc(&h->phiHbyA, nf * e) && alloc(&h->af, nf * e) && alloc(&h->nonorth, ni * e) &&
+            (o->conv != DIFVM_CONV_SOU || alloc(&h->sou_d, 2 * ni * (e == 8 ? sizeof(V4<double>) : sizeof(V4<float>))));
   h->wsU_bytes = difvm_krylov_opts_workspace_bytes(m, prec, &o->solve_U, 3);
   ok = ok && h->wsU_bytes > 0 && alloc(&h->wsU, h->wsU_bytes);
   h->wsp_bytes = difvm_krylov_opts_workspace_bytes(m, prec, &o->solve_p, 1);
@@ -1225,6 +1296,16 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
   for (int k = 0; k < o->n_out; ++k) {
     tab[k] = m->patch_start[o->wk_patch[k]];
     tab[16 + k] = m->patch_size[o->wk_patch[k]];
+  }
+  if (o->conv == DIFVM_CONV_SOU && m->ni > 0) {
+    if (e == 8)
+      k_sou_d<double><<<blocks_for(m->ni, kPB), kPB>>>(m->ni, m->on, m->Cf64, m->C64, (V4<double>*)h->sou_d);
+    else
+      k_sou_d<float><<<blocks_for(m->ni, kPB), kPB>>>(m->ni, m->on, m->Cf64, m->C64, (V4<float>*)h->sou_d);
+    if (check_launch("sou_d") != DIFVM_OK || cudaDeviceSynchronize() != cudaSuccess) {
+      difvm_piso_destroy(h);
+      return set_error(DIFVM_ECUDA, "second-order upwind setup failed");
+    }
   }
   double* Qd = (double*)(h->sinfo + ninfo);
   if (cudaMemcpy(Qd + 32, tab, sizeof tab, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1268,6 +1349,7 @@ static difvm_status adj_alloc(difvm_piso* h) {
             alloc(&h->a_ld, ni * e) && alloc(&h->a_phio, nf * e) && alloc(&h->a_pbb, nb * e) &&
             alloc(&h->a_gUb, 9 * nc * e) && alloc(&h->a_lkU, 3 * ni * e) &&
             alloc(&h->a_ldU, 3 * ni * e) && alloc(&h->a_gp2, 3 * nc * e) &&
+            (h->o.conv != DIFVM_CONV_SOU || alloc(&h->a_lsU, 3 * ni * e)) &&
             alloc((void**)&h->a_nuf, nf * sizeof(double)) &&
             alloc((void**)&h->a_part, kRedBlocks * sizeof(double)) &&
             alloc(&h->a_lamw, (size_t)h->o.n_corr * nc * (h->mixed ? 8 : e));
@@ -1351,15 +1433,15 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
 
   // recompute the forward step's matrices from the tape
   DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, ps, pb1, 1, gradp, st));
-  if (no_U) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U0, Ub, 3, gradU, st));
+  const bool sou = o.conv == DIFVM_CONV_SOU;
+  const V4<T>* sd = (const V4<T>*)h->sou_d;
+  if (no_U || sou) DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_VELOCITY, U0, Ub, 3, gradU, st));
   if (ni > 0) {
     k_mom_faces<T><<<Bi, kPB, 0, st>>>(ni, g, (T)o.nu, phi0, Lo, Up);
     DIFVM_TRY(check_launch("mom_faces"));
   }
-  if (no_U)
-    k_mom_cells<T, true><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi0, U0, Ub, gradU, gradp, D, b, rhs);
-  else
-    k_mom_cells<T, false><<<Bc, kPB, 0, st>>>(t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi0, U0, Ub, gradU, gradp, D, b, rhs);
+  launch_mom_cells<T>(no_U, sou, Bc, st, t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi0, U0, Ub, gradU, sd,
+                      gradp, D, b, rhs);
   DIFVM_TRY(check_launch("mom_cells"));
   k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, Us, HbyA, rAU);
   DIFVM_TRY(check_launch("HbyA"));
@@ -1438,15 +1520,18 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   k_adj_mom_cells<T><<<Bc, kPB, 0, st>>>(nc, g, (T)(1.0 / o.dt), D, lamU, Us, rAUb, Db, bb, gpn, Ubar);
   DIFVM_TRY(check_launch("adj_mom_cells"));
   DIFVM_TRY(difvm_grad_gauss_bwd(m, pr, DIFVM_BC_PRESSURE, gpn, 1, pbar, pbb, st));
-  if (no_U)
-    k_adj_mom_faces<T, true><<<Bf, kPB, 0, st>>>(t, g, (T)o.nu, psi, phi0, Db, bb, Lob, Upb, lamU, Us,
-                                                  U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, Ubbar);
-  else
-    k_adj_mom_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, (T)o.nu, psi, phi0, Db, bb, Lob, Upb, lamU, Us,
-                                                   U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, Ubbar);
+  T* lsU = (T*)h->a_lsU;
+#define DIFVM_AMF(NO, SO)                                                                          \
+  k_adj_mom_faces<T, NO, SO><<<Bf, kPB, 0, st>>>(t, g, (T)o.nu, psi, phi0, Db, bb, Lob, Upb, lamU, Us, \
+                                                 U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, sd, lsU, Ubbar)
+  if (no_U) { if (sou) DIFVM_AMF(true, true); else DIFVM_AMF(true, false); }
+  else { if (sou) DIFVM_AMF(false, true); else DIFVM_AMF(false, false); }
+#undef DIFVM_AMF
   DIFVM_TRY(check_launch("adj_mom_faces"));
-  if (no_U) {
-    k_adj_mom_cells2<T><<<Bc, kPB, 0, st>>>(t, g, lkU, ldU, gUb, Ubar);
+  if (no_U || sou) {
+    if (no_U && sou) k_adj_mom_cells2<T, true, true><<<Bc, kPB, 0, st>>>(t, g, lkU, ldU, phi0, sd, lsU, gUb, Ubar);
+    else if (no_U) k_adj_mom_cells2<T, true, false><<<Bc, kPB, 0, st>>>(t, g, lkU, ldU, phi0, sd, lsU, gUb, Ubar);
+    else k_adj_mom_cells2<T, false, true><<<Bc, kPB, 0, st>>>(t, g, lkU, ldU, phi0, sd, lsU, gUb, Ubar);
     DIFVM_TRY(check_launch("adj_mom_cells2"));
     DIFVM_TRY(difvm_grad_gauss_bwd(m, pr, DIFVM_BC_VELOCITY, gUb, 3, Ubar, Ubbar, st));
   }

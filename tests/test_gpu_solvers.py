@@ -314,6 +314,44 @@ def test_piso_lid_cavity_f64_other_splits(split):
     assert worst < 1e-9, worst
 
 
+@pytest.mark.parametrize("mask", [0, 3])
+def test_piso_sou_deferred_correction_f64(mask):
+    # second-order upwind momentum convection by deferred correction, against the
+    # oracle per step: a lid cavity (all walls) and an inlet/outlet Kuhn box
+    for kind in ("cavity", "channel"):
+        if kind == "cavity":
+            m, Ub = _cavity()
+            pref = 17
+        else:
+            m = mg.shuffle(mg.kuhn_cube(6, 0.2, 4, patch_types=dict(x0=mg.INLET, x1=mg.OUTLET)), 5)
+            Ub = np.zeros((3, m.n_boundary))
+            Ub[0, m.patch_faces("x0") - m.n_internal] = 1.0
+            pref = 0
+        om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
+        U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+        phi = O.flux_from_U(om, U, Ub)
+        o = D.piso_opts(0.01, 0.05, 2, mask, conv=D.CONV_SOU,
+                        solve_U=D.solve_opts(D.BICGSTAB, 1e-12, max_iter=2000),
+                        solve_p=D.solve_opts(D.PCG, 1e-12, max_iter=20000),
+                        pref_cell=int(dm.cell_new_of_old[pref]))
+        pg = D.Piso(dm, D.F64, o)
+        worst = 0.0
+        for _ in range(4):
+            g = _state_to_gpu(dm, U, p, phi, Ub, pb)
+            assert pg.step(*g)[0] == D.OK
+            U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12,
+                                              tolp=1e-12, pref_cell=pref, nonorth=mask, conv=O.CONV_SOU)
+            worst = max(worst, nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p),
+                        nrel(dm.from_faces(host(g[2])), phi))
+        assert worst < 1e-9, (kind, worst)
+        # the scheme matters: the upwind step from the same state differs
+        Uu = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12, tolp=1e-12, pref_cell=pref,
+                         nonorth=mask)[0]
+        Us = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12, tolp=1e-12, pref_cell=pref,
+                         nonorth=mask, conv=O.CONV_SOU)[0]
+        assert nrel(Us, Uu) > 1e-4
+
+
 def test_piso_free_stream_on_gpu():
     m = mg.kuhn_cube(5, 0.2, 5, patch_types=dict(x0=mg.INLET, x1=mg.OUTLET))
     dm = D.Mesh(m)
