@@ -30,6 +30,8 @@ WK_EXACT, WK_FE, WK_BE = 0, 1, 2
 NONORTH_OVERRELAXED, NONORTH_MINIMUM, NONORTH_ORTHOGONAL, NONORTH_NONE = 0, 1, 2, 3
 # momentum convection: upwind, or second-order upwind by deferred correction (Eqs. deferred_correction, sou)
 CONV_UPWIND, CONV_SOU = 0, 1
+# momentum time scheme: backward Euler or Crank-Nicolson
+TIME_BE, TIME_CN = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -71,7 +73,7 @@ class _PisoOpts(C.Structure):
                 ("maxitU", C.c_int), ("maxitp", C.c_int), ("pref_cell", C.c_int),
                 ("wk_scheme", C.c_int), ("n_out", C.c_int), ("wk_patch", C.c_void_p),
                 ("Rp", C.c_void_p), ("Cw", C.c_void_p), ("Rd", C.c_void_p), ("psi", C.c_double),
-                ("conv", C.c_int)]
+                ("conv", C.c_int), ("time", C.c_int)]
 
 
 class _PisoInfo(C.Structure):
@@ -204,9 +206,11 @@ def windkessel_update(scheme, Rp, Cw, Rd, Q, dt, pc):
     return pc, po
 
 
-def momentum_assemble(m: OMesh, nu, dt, mf, Uold, Ub, gradU=None, psi=1.0, gradS=None):
+def momentum_assemble(m: OMesh, nu, dt, mf, Uold, Ub, gradU=None, psi=1.0, gradS=None,
+                      time=TIME_BE):
     """gradU: the non-orthogonal correction's velocity gradient; gradS: the
-    gradient of the second-order upwind deferred correction (None: upwind)."""
+    gradient of the second-order upwind deferred correction (None: upwind);
+    time: TIME_BE or TIME_CN (the Crank-Nicolson form of the rows)."""
     D = np.zeros(m.nc); Lo = np.zeros(m.nint + 1); Up = np.zeros(m.nint + 1)
     b = np.zeros((3, m.nc))
     lib().om_momentum_assemble(m.ref(), _p(m.bc_U()), C.c_double(nu), C.c_double(dt),
@@ -214,6 +218,8 @@ def momentum_assemble(m: OMesh, nu, dt, mf, Uold, Ub, gradU=None, psi=1.0, gradS
                                _p(None if gradU is None else _f64(gradU)),
                                _p(None if gradS is None else _f64(gradS)), C.c_double(psi), _p(D),
                                _p(Lo), _p(Up), _p(b))
+    if time == TIME_CN:
+        lib().om_momentum_cn(m.ref(), C.c_double(dt), _p(_f64(Uold)), _p(D), _p(Lo), _p(Up), _p(b))
     return D, Lo[:m.nint], Up[:m.nint], b
 
 
@@ -243,7 +249,8 @@ def flux_from_U(m: OMesh, U, Ub):
 
 def piso_step(m: OMesh, U, p, phi, Ub, pb, *, nu, dt, ncorr=2, nonorth=True, tolU=1e-10,
               tolp=1e-10, tol_abs=0.0, maxitU=1000, maxitp=20000, pref_cell=0,
-              wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(), wk_scheme=WK_EXACT, psi=1.0, conv=CONV_UPWIND):
+              wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(), wk_scheme=WK_EXACT, psi=1.0, conv=CONV_UPWIND,
+              time=TIME_BE):
     """One PISO step in place on copies; returns (U, p, phi, pb, pc, info).
 
     nonorth: True (both), False (none), or a mask: 1 momentum, 2 pressure."""
@@ -255,7 +262,7 @@ def piso_step(m: OMesh, U, p, phi, Ub, pb, *, nu, dt, ncorr=2, nonorth=True, tol
     pc = _f64(np.array(np.atleast_1d(np.asarray(pc, np.float64))))
     nonorth = 3 if nonorth is True else (0 if nonorth is False else int(nonorth))
     opts = _PisoOpts(nu, dt, ncorr, nonorth, tolU, tolp, tol_abs, maxitU, maxitp, pref_cell,
-                     wk_scheme, int(wk_patch.shape[0]), _p(wk_patch), _p(Rp), _p(Cw), _p(Rd), psi, conv)
+                     wk_scheme, int(wk_patch.shape[0]), _p(wk_patch), _p(Rp), _p(Cw), _p(Rd), psi, conv, time)
     info = _PisoInfo()
     lib().om_piso_step(m.ref(), C.byref(opts), _p(U), _p(p), _p(phi), _p(Ub), _p(pb), _p(pc),
                        C.byref(info))
@@ -268,7 +275,7 @@ def piso_step(m: OMesh, U, p, phi, Ub, pb, *, nu, dt, ncorr=2, nonorth=True, tol
 def piso_step_bwd(m: OMesh, U, p, phi, Ub, pb, Ubar, pbar, phibar, pbbar=None, pcbar=(), *, nu,
                   dt, ncorr=2, nonorth=True, tolU=1e-10, tolp=1e-10, tol_abs=0.0, maxitU=1000,
                   maxitp=20000, pref_cell=0, wk_patch=(), Rp=(), Cw=(), Rd=(), pc=(),
-                  wk_scheme=WK_EXACT, psi=1.0, conv=CONV_UPWIND):
+                  wk_scheme=WK_EXACT, psi=1.0, conv=CONV_UPWIND, time=TIME_BE):
     """Adjoint of ``piso_step`` at the inputs (U, p, phi, Ub, pb, pc).
 
     (Ubar, pbar, phibar, pbbar, pcbar) are the adjoints of the step's outputs
@@ -291,7 +298,7 @@ def piso_step_bwd(m: OMesh, U, p, phi, Ub, pb, Ubar, pbar, phibar, pbbar=None, p
     Rpb, Cb, Rdb = np.zeros(max(n_out, 1)), np.zeros(max(n_out, 1)), np.zeros(max(n_out, 1))
     nonorth = 3 if nonorth is True else (0 if nonorth is False else int(nonorth))
     opts = _PisoOpts(nu, dt, ncorr, nonorth, tolU, tolp, tol_abs, maxitU, maxitp, pref_cell,
-                     wk_scheme, n_out, _p(wk_patch), _p(Rp), _p(Cw), _p(Rd), psi, conv)
+                     wk_scheme, n_out, _p(wk_patch), _p(Rp), _p(Cw), _p(Rd), psi, conv, time)
     st = lib().om_piso_step_bwd(m.ref(), C.byref(opts), _p(U), _p(p), _p(phi), _p(Ub), _p(pb),
                                 _p(pc), _p(Ub_), _p(pb_), _p(phib_), _p(pbb_), _p(pcb_),
                                 _p(Ubbar), C.byref(nubar), _p(Rpb), _p(Cb), _p(Rdb))

@@ -56,6 +56,7 @@ enum { DIV_UPWIND = 0, DIV_LINEAR = 1 };
 enum { WK_EXACT = 0, WK_FE = 1, WK_BE = 2 };
 enum { NO_OVERRELAXED = 0, NO_MINIMUM = 1, NO_ORTHOGONAL = 2, NO_NONE = 3 };
 enum { CONV_UPWIND = 0, CONV_SOU = 1 };
+enum { TIME_BE = 0, TIME_CN = 1 };
 
 static double dot3(const double *a, const double *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -497,6 +498,29 @@ void om_momentum_assemble(const om_mesh *m, const int *bcU, double nu, double dt
   free(w); free(c); free(k);
 }
 
+/* Crank-Nicolson form of the momentum rows (Sec. 3 time schemes, second order):
+ * with the backward-Euler rows D = V/dt + D_cd, off-diagonals Lo/Up and b = V/dt U^n + b_cd
+ * of om_momentum_assemble, the spatial operator A_cd U - b_cd is averaged between the two
+ * time levels: (V/dt + A_cd/2) U* = V/dt U^n + b_cd - A_cd U^n / 2.  Transforms D, Lo, Up,
+ * b in place (A_cd U^n with the backward-Euler coefficients). */
+void om_momentum_cn(const om_mesh *m, double dt, const double *Uold, double *D, double *Lo,
+                    double *Up, double *b) {
+  int nc = m->nc;
+  for (int q = 0; q < 3; ++q) {
+    const double *u = Uold + (size_t)q * nc;
+    double *a = calloc((size_t)nc, sizeof(double));
+    for (int i = 0; i < nc; ++i) a[i] = (D[i] - m->V[i] / dt) * u[i];
+    for (int f = 0; f < m->nint; ++f) {
+      a[m->owner[f]] += Up[f] * u[m->neighbour[f]];
+      a[m->neighbour[f]] += Lo[f] * u[m->owner[f]];
+    }
+    for (int i = 0; i < nc; ++i) b[q * nc + i] -= 0.5 * a[i];
+    free(a);
+  }
+  for (int i = 0; i < nc; ++i) D[i] = m->V[i] / dt + 0.5 * (D[i] - m->V[i] / dt);
+  for (int f = 0; f < m->nint; ++f) { Lo[f] *= 0.5; Up[f] *= 0.5; }
+}
+
 /* H_i = b_i - sum_{f:O=i} Up_f U_N - sum_{f:N=i} Lo_f U_O  (Eq. Ap_H off-diagonal part) */
 void om_H(const om_mesh *m, const double *Lo, const double *Up, const double *b,
           const double *U, double *H) {
@@ -589,6 +613,7 @@ typedef struct {
   const double *Rp, *Cw, *Rd;   /* [n_out] */
   double psi;                   /* non-orthogonal limiter coefficient (1 = unlimited) */
   int conv;                     /* momentum convection: CONV_UPWIND or CONV_SOU (deferred correction) */
+  int time;                     /* momentum time scheme: TIME_BE or TIME_CN */
 } om_piso_opts;
 
 typedef struct { int itU[3], itp[4], status; double Q[8], po[8]; } om_piso_info;
@@ -634,6 +659,7 @@ int om_piso_step(const om_mesh *m, const om_piso_opts *o, double *U, double *p, 
   if ((o->nonorth & 1) || o->conv == CONV_SOU) om_grad_gauss(m, bcU, 3, U, Ub, gradU);
   om_momentum_assemble(m, bcU, o->nu, o->dt, phi, U, Ub, (o->nonorth & 1) ? gradU : NULL,
                        o->conv == CONV_SOU ? gradU : NULL, o->psi, D, Lo, Up, b);
+  if (o->time == TIME_CN) om_momentum_cn(m, o->dt, U, D, Lo, Up, b);
   for (int q = 0; q < 3; ++q) {
     for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gradp[q * nc + i];
     int st = om_bicgstab(m, D, Lo, Up, rhs, U + (size_t)q * nc, o->tolU, o->tol_abs, o->maxitU, &si);
@@ -801,6 +827,7 @@ int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in
   if (nonU || sou) om_grad_gauss(m, bcU, 3, U_in, Ub, gradU);
   om_momentum_assemble(m, bcU, o->nu, o->dt, phi_in, U_in, Ub, nonU ? gradU : NULL,
                        sou ? gradU : NULL, o->psi, D, Lo, Up, b);
+  if (o->time == TIME_CN) om_momentum_cn(m, o->dt, U_in, D, Lo, Up, b);
   memcpy(Us, U_in, sizeof(double) * 3 * nc);
   for (int q = 0; q < 3; ++q) {
     for (int i = 0; i < nc; ++i) rhs[i] = b[q * nc + i] - m->V[i] * gp[q * nc + i];
@@ -993,6 +1020,30 @@ int om_piso_step_bwd(const om_mesh *m, const om_piso_opts *o, const double *U_in
   double nub = 0.0;
   for (int q = 0; q < 3; ++q)
     for (int i = 0; i < nc; ++i) Un_b[q * nc + i] = m->V[i] / o->dt * bb[q * nc + i];
+  if (o->time == TIME_CN) {
+    /* Crank-Nicolson transform backwards: D, Lo, Up hold the halved rows; the
+     * backward-Euler coefficients are twice their off-time parts */
+    for (int i = 0; i < nc; ++i) {
+      double Dcd = 2.0 * (D[i] - m->V[i] / o->dt), s = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        s += bb[q * nc + i] * U_in[q * nc + i];
+        Un_b[q * nc + i] -= 0.5 * Dcd * bb[q * nc + i];
+      }
+      Db[i] = 0.5 * Db[i] - 0.5 * s;
+    }
+    for (int f = 0; f < ni; ++f) {
+      int O = m->owner[f], N = m->neighbour[f];
+      double sl = 0.0, su = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        sl += bb[q * nc + N] * U_in[q * nc + O];
+        su += bb[q * nc + O] * U_in[q * nc + N];
+        Un_b[q * nc + O] -= 0.5 * (2.0 * Lo[f]) * bb[q * nc + N];
+        Un_b[q * nc + N] -= 0.5 * (2.0 * Up[f]) * bb[q * nc + O];
+      }
+      Lob[f] = 0.5 * Lob[f] - 0.5 * sl;
+      Upb[f] = 0.5 * Upb[f] - 0.5 * su;
+    }
+  }
   for (int f = 0; f < nf; ++f) {
     int O = m->owner[f];
     double mm = phi_in[f];

@@ -45,24 +45,27 @@ def _fwd(om, x, kw):
 
 
 UP, SOU = O.CONV_UPWIND, O.CONV_SOU
-CASES = [  # (mesh / outlet kind, non-orthogonal mask, limiter psi, correctors, convection)
-    ("wk_exact", 3, 1.0, 2, UP),
-    ("wk_exact", 3, 0.5, 2, UP),
-    ("wk_fe", 1, 0.3, 2, UP),
-    ("wk_be", 0, 1.0, 1, UP),
-    ("outlet", 3, 0.5, 3, UP),
-    ("cavity", 3, 0.5, 2, UP),
-    ("cavity", 2, 1.0, 3, UP),
-    ("outlet", 0, 1.0, 2, SOU),
-    ("cavity", 3, 0.5, 2, SOU),
-    ("wk_exact", 1, 1.0, 2, SOU),
+BE, CN = O.TIME_BE, O.TIME_CN
+CASES = [  # (mesh / outlet kind, non-orthogonal mask, limiter psi, correctors, convection, time)
+    ("wk_exact", 3, 1.0, 2, UP, BE),
+    ("wk_exact", 3, 0.5, 2, UP, BE),
+    ("wk_fe", 1, 0.3, 2, UP, BE),
+    ("wk_be", 0, 1.0, 1, UP, BE),
+    ("outlet", 3, 0.5, 3, UP, BE),
+    ("cavity", 3, 0.5, 2, UP, BE),
+    ("cavity", 2, 1.0, 3, UP, BE),
+    ("outlet", 0, 1.0, 2, SOU, BE),
+    ("cavity", 3, 0.5, 2, SOU, BE),
+    ("wk_exact", 1, 1.0, 2, SOU, BE),
+    ("outlet", 3, 1.0, 2, UP, CN),
+    ("cavity", 1, 0.5, 2, SOU, CN),
 ]
 
 
-@pytest.mark.parametrize("kind,mask,psi,ncorr,conv", CASES)
-def test_piso_step_adjoint_matches_central_differences(kind, mask, psi, ncorr, conv):
+@pytest.mark.parametrize("kind,mask,psi,ncorr,conv,time", CASES)
+def test_piso_step_adjoint_matches_central_differences(kind, mask, psi, ncorr, conv, time):
     om, x, kw = _case(kind, seed=len(kind) + mask)
-    kw.update(nonorth=mask, psi=psi, ncorr=ncorr, conv=conv)
+    kw.update(nonorth=mask, psi=psi, ncorr=ncorr, conv=conv, time=time)
     y = _fwd(om, x, kw)
     rng = np.random.default_rng(11)
     w = {k: rng.normal(size=np.shape(v)) for k, v in y.items()}

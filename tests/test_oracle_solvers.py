@@ -309,3 +309,45 @@ def test_limiter_caps_the_explicit_correction():
     assert np.abs(b_full - b_plain).max() > 2 * np.abs(b_lim - b_plain).max()
     # psi = 1 is the unlimited over-relaxed correction
     np.testing.assert_array_equal(O.momentum_assemble(om, nu, dt, mf, U, zero, g, psi=1.0)[3], b_full)
+
+
+def test_crank_nicolson_momentum_rows_are_second_order_in_time():
+    # The momentum rows as a linear ODE V dU/dt = -(A U - b) (fixed face flux, no
+    # pressure): backward Euler is first order in dt, the Crank-Nicolson form of
+    # the rows second order, against the matrix exponential of the same system.
+    from scipy.linalg import expm
+    m = mg.kuhn_cube(2, 0.2, 4)
+    om = _om(m)
+    rng = np.random.default_rng(8)
+    mf = O.flux_from_U(om, np.tile([[0.6], [-0.3], [0.2]], (1, m.n_cells)), np.tile([[0.6], [-0.3], [0.2]],
+                                                                                        (1, m.n_boundary)))
+    Ub = rng.standard_normal((3, m.n_boundary))
+    U0 = rng.standard_normal((3, m.n_cells))
+    nu, T = 0.05, 0.2
+    nc, ni = m.n_cells, m.n_internal
+
+    def dense(D, Lo, Up):
+        A = np.diag(D)
+        A[m.owner[:ni], m.neighbour] += Up
+        A[m.neighbour, m.owner[:ni]] += Lo
+        return A
+
+    D, Lo, Up, b = O.momentum_assemble(om, nu, 1.0, mf, U0, Ub)
+    Acd = dense(D - m.V, Lo, Up)                    # dt = 1: D = V + D_cd
+    bcd = b - m.V * U0
+    Uinf = np.linalg.solve(Acd, bcd.T).T
+    E = expm(-np.diag(1.0 / m.V) @ Acd * T)
+    exact = Uinf + (E @ (U0 - Uinf).T).T
+    err = {}
+    for time in (O.TIME_BE, O.TIME_CN):
+        err[time] = []
+        for n in (8, 16, 32):
+            dt, U = T / n, U0.copy()
+            for _ in range(n):
+                D, Lo, Up, b = O.momentum_assemble(om, nu, dt, mf, U, Ub, time=time)
+                U = np.linalg.solve(dense(D, Lo, Up), b.T).T
+            err[time].append(np.abs(U - exact).max())
+    be = np.log2(np.array(err[O.TIME_BE][:-1]) / np.array(err[O.TIME_BE][1:]))
+    cn = np.log2(np.array(err[O.TIME_CN][:-1]) / np.array(err[O.TIME_CN][1:]))
+    assert np.all(np.abs(be - 1) < 0.15), be
+    assert np.all(np.abs(cn - 2) < 0.1), cn
