@@ -346,7 +346,7 @@ def run_ours(args):
         phi = D.difvm_flux_from_U(dm, U, Ub)
         return [U, p, phi, Ub, pb]
 
-    def piso(prec, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND):
+    def piso(prec, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND, time_scheme=D.TIME_BE):
         # pressure: CG preconditioned by one multigrid V-cycle (or Jacobi); the
         # Jacobi form polls less often since it runs ~50x more iterations
         ce = 32 if precond == D.PRECOND_JACOBI else 4
@@ -355,7 +355,7 @@ def run_ours(args):
                 NU, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
                 solve_p=D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=ce, refine_max=20,
                                      inner_tol=1e-4, precond=precond),
-                pref_cell=pref, conv=conv))
+                pref_cell=pref, conv=conv, time_scheme=time_scheme))
         return D.Piso(dm, D.F64, D.piso_opts(
             NU, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-10, max_iter=1000, check_every=4),
             solve_p=D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=ce, precond=precond),
@@ -363,9 +363,10 @@ def run_ours(args):
 
     info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
 
-    def timed(prec, W, K, prof_tag=None, graph=False, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND):
+    def timed(prec, W, K, prof_tag=None, graph=False, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND,
+              time_scheme=D.TIME_BE):
         dt_ = torch.float32 if prec == D.F32 else torch.float64
-        h = piso(prec, precond, conv)
+        h = piso(prec, precond, conv, time_scheme)
         s = new_state(dt_)
 
         def one():
@@ -460,6 +461,11 @@ def run_ours(args):
            "status": int(rs["status"]), "pressure_iters_last_step": rs["info"]["itp"][:2],
            "momentum_iters_last_step": rs["info"]["itU"],
            "api": "difvm_piso_step_graph, momentum convection by second-order upwind deferred correction"}
+    rc = timed(D.F32, W, K, graph=True, time_scheme=D.TIME_CN)
+    cn = {"value": 1e3 * K / rc["ms"], "unit": "steps/s", "ms_per_step": rc["ms"] / K,
+          "status": int(rc["status"]), "pressure_iters_last_step": rc["info"]["itp"][:2],
+          "momentum_iters_last_step": rc["info"]["itU"],
+          "api": "difvm_piso_step_graph, Crank-Nicolson momentum predictor"}
     host_loop = {"value": 1e3 * K / r32["ms"], "unit": "steps/s", "ms_per_step": r32["ms"] / K,
                  "status": int(r32["status"]), "pressure_iters_last_step": r32["info"]["itp"][:2],
                  "api": "difvm_piso_step (host polls the solver flags every check_every iterations)"}
@@ -573,6 +579,7 @@ def run_ours(args):
         "host_loop": host_loop,
         "jacobi_pressure": jacobi,
         "sou_convection": sou,
+        "crank_nicolson": cn,
         "f64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64,
                 "pressure_iters_last_step": r64["info"]["itp"][:2],
                 "momentum_iters_last_step": r64["info"]["itU"]},

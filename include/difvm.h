@@ -375,9 +375,13 @@ typedef struct {
                            deferred_correction, sou): the matrix stays upwind and each internal
                            face adds m_f (grad U^n)_C . (x_f - x_C) of its upwind cell C to the
                            explicit part (boundary faces keep their condition's face value) */
-  int32_t pad;
+  int32_t time_scheme;  /* momentum predictor: DIFVM_TIME_BE (backward Euler) or DIFVM_TIME_CN
+                           (Crank-Nicolson: the convection-diffusion operator A and its source b
+                           averaged over the two time levels, (V/dt + A/2) U* = V/dt U^n + b -
+                           A U^n / 2, the face flux and the explicit corrections from step n) */
 } difvm_piso_opts;
 enum { DIFVM_CONV_UPWIND = 0, DIFVM_CONV_SOU = 1 };
+enum { DIFVM_TIME_BE = 0, DIFVM_TIME_CN = 1 };
 
 typedef struct difvm_piso* difvm_piso_t;
 /* Create a PISO driver for one mesh and precision; owns all step workspace. */

@@ -287,6 +287,47 @@ __global__ void __launch_bounds__(kPB) k_mom_cells(Topo t, Geo<T> g, T nu, T rdt
   }
 }
 
+// Crank-Nicolson form of the momentum rows: with the backward-Euler rows
+// D = V/dt + D_cd, Lo/Up and b = V/dt U^n + b_cd, average the spatial operator
+// over the two time levels: D <- V/dt + D_cd/2, b and rhs -= (A_cd U^n)/2 (the
+// off-diagonals are halved afterwards by k_cn_faces, so they are read whole here).
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_cn_cells(Topo t, Geo<T> g, T rdt, const T* Lo, const T* Up,
+                                                  const T* U, T* D, T* b, T* rhs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc;
+  const T Vdt = g.V[i] * rdt, Dcd = D[i] - Vdt;
+  T a[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) a[c] = Dcd * U[c * nc + i];
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int ent = t.cent[e];
+    const int f = ent >> 1;
+    if (f >= t.ni) break;
+    const int2 on = t.on[f];
+    const bool nside = ent & 1;
+    const T coef = nside ? Lo[f] : Up[f];   // row N holds Lo_f U_O, row O holds Up_f U_N
+    const int j = nside ? on.x : on.y;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] += coef * U[c * nc + j];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    b[c * nc + i] -= T(0.5) * a[c];
+    rhs[c * nc + i] -= T(0.5) * a[c];
+  }
+  D[i] = Vdt + T(0.5) * Dcd;
+}
+template <typename T>
+__global__ void k_cn_faces(int ni, T* Lo, T* Up) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= ni) return;
+  Lo[f] *= T(0.5);
+  Up[f] *= T(0.5);
+}
+
 // HbyA = (b - sum offdiag U)/D,  rAU = V/D   (Eq. Ap_H)
 template <typename T>
 __global__ void __launch_bounds__(kPB) k_HbyA(Topo t, Geo<T> g, const T* D, const T* Lo,
@@ -774,6 +815,42 @@ __global__ void k_adj_mom_cells(int nc, Geo<T> g, T rdt, const T* D, const T* la
   Db[i] = d;
 }
 
+// Crank-Nicolson rows backwards, per cell (D, Lo, Up hold the halved rows; the
+// backward-Euler coefficients are D_cd = 2 (D - V/dt), 2 Lo, 2 Up):
+//   D_bar <- D_bar/2 - sum_c b_bar U^n / 2,  U^n_bar -= (A_cd^T b_bar)/2.
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_adj_cn_cells(Topo t, Geo<T> g, T rdt, const T* D, const T* Lo,
+                                                      const T* Up, const T* U0, const T* bb, T* Db,
+                                                      T* Ubar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  const int nc = t.nc;
+  const T Dcd = T(2) * (D[i] - g.V[i] * rdt);
+  T s = T(0), a[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T bi = bb[c * nc + i];
+    s += bi * U0[c * nc + i];
+    a[c] = Dcd * bi;
+  }
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int ent = t.cent[e];
+    const int f = ent >> 1;
+    if (f >= t.ni) break;
+    const int2 on = t.on[f];
+    const bool nside = ent & 1;
+    // U_i enters row N through Lo_f when i is the owner, row O through Up_f when i is the neighbour
+    const T coef = T(2) * (nside ? Up[f] : Lo[f]);
+    const int j = nside ? on.x : on.y;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] += coef * bb[c * nc + j];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) Ubar[c * nc + i] -= T(0.5) * a[c];
+  Db[i] = T(0.5) * Db[i] - T(0.5) * s;
+}
+
 // Momentum assembly backwards, per face: the face flux adjoint (upwind switch),
 // the viscosity adjoint contribution (FP64, reduced later in a fixed order), the
 // limited non-orthogonal correction (lkU / ldU per component), U_b_bar.
@@ -781,7 +858,7 @@ template <typename T, bool NONORTH, bool SOU>
 __global__ void k_adj_mom_faces(Topo t, Geo<T> g, T nu, T psi, const T* phi0, const T* Db,
                                 const T* bb, const T* Lob, const T* Upb, const T* lamU,
                                 const T* Ustar, const T* U0, const T* gradU, const T* Ub, T* phib,
-                                double* nuf, T* lkU, T* ldU, const V4<T>* sd, T* lsU, T* Ubb) {
+                                double* nuf, T* lkU, T* ldU, const V4<T>* sd, T* lsU, T* Ubb, int cn) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nf) return;
   const int nc = t.nc, nb = t.nb, ni = t.ni;
@@ -795,6 +872,16 @@ __global__ void k_adj_mom_faces(Topo t, Geo<T> g, T nu, T psi, const T* phi0, co
     for (int c = 0; c < 3; ++c) {
       upt -= lamU[c * nc + O] * Ustar[c * nc + N];
       lot -= lamU[c * nc + N] * Ustar[c * nc + O];
+    }
+    if (cn) {   // Crank-Nicolson rows: halved coefficients and -A_cd U^n / 2 in b
+      T su = T(0), sl = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        su += bb[c * nc + O] * U0[c * nc + N];
+        sl += bb[c * nc + N] * U0[c * nc + O];
+      }
+      upt = T(0.5) * upt - T(0.5) * su;
+      lot = T(0.5) * lot - T(0.5) * sl;
     }
     const T dO = Db[O], dN = Db[N];
     const bool hp = m > T(0), hn = m < T(0);
@@ -1015,6 +1102,21 @@ static TapeLayout tape_layout(const difvm_piso* h) {
   return L;
 }
 
+// the Crank-Nicolson transform of the assembled backward-Euler rows (U = U^n)
+template <typename T>
+static difvm_status momentum_cn(difvm_piso* h, const T* U, cudaStream_t st) {
+  const difvm_mesh* m = h->m;
+  k_cn_cells<T><<<blocks_for(m->nc, kPB), kPB, 0, st>>>(m->topo(), geo<T>(m), (T)(1.0 / h->o.dt),
+                                                        (const T*)h->Lo, (const T*)h->Up, U, (T*)h->D,
+                                                        (T*)h->b, (T*)h->rhs);
+  DIFVM_TRY(check_launch("cn_cells"));
+  if (m->ni > 0) {
+    k_cn_faces<T><<<blocks_for(m->ni, kPB), kPB, 0, st>>>(m->ni, (T*)h->Lo, (T*)h->Up);
+    DIFVM_TRY(check_launch("cn_faces"));
+  }
+  return DIFVM_OK;
+}
+
 template <typename T, typename... A>
 static void launch_mom_cells(bool no_U, bool sou, unsigned Bc, cudaStream_t st, A... a) {
   if (no_U && sou) k_mom_cells<T, true, true><<<Bc, kPB, 0, st>>>(a...);
@@ -1086,6 +1188,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   launch_mom_cells<T>(no_U, sou, Bc, st, t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi, U, Ub, gradU,
                       (const V4<T>*)h->sou_d, gradp, D, b, rhs);
   DIFVM_TRY(check_launch("mom_cells"));
+  if (o.time_scheme == DIFVM_TIME_CN) DIFVM_TRY(momentum_cn<T>(h, U, st));
   {
     difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
     difvm_status s = difvm_krylov_solve(m, pr, &o.solve_U, D, Lo, Up, rhs, U, 3, h->wsU, h->wsU_bytes,
@@ -1212,6 +1315,8 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
   if (o->n_out < 0 || o->n_out > 16) return set_error(DIFVM_EINVAL, "n_out must be 0..16");
   if (o->conv != DIFVM_CONV_UPWIND && o->conv != DIFVM_CONV_SOU)
     return set_error(DIFVM_EINVAL, "unknown convection scheme %d", o->conv);
+  if (o->time_scheme != DIFVM_TIME_BE && o->time_scheme != DIFVM_TIME_CN)
+    return set_error(DIFVM_EINVAL, "unknown time scheme %d", o->time_scheme);
   if (o->solve_U.method != DIFVM_BICGSTAB && o->solve_U.method != DIFVM_PCG)
     return set_error(DIFVM_EINVAL, "bad momentum solver");
   if (o->solve_p.method != DIFVM_PCG && o->solve_p.method != DIFVM_BICGSTAB)
@@ -1443,6 +1548,7 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   launch_mom_cells<T>(no_U, sou, Bc, st, t, g, (T)o.nu, (T)(1.0 / o.dt), psi, phi0, U0, Ub, gradU, sd,
                       gradp, D, b, rhs);
   DIFVM_TRY(check_launch("mom_cells"));
+  if (o.time_scheme == DIFVM_TIME_CN) DIFVM_TRY(momentum_cn<T>(h, U0, st));
   k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, Us, HbyA, rAU);
   DIFVM_TRY(check_launch("HbyA"));
   k_p_faces<T, false><<<Bf, kPB, 0, st>>>(t, g, psi, HbyA, rAU, Ub, gradp, ps, phiH, af, no, Lp);
@@ -1519,11 +1625,16 @@ static difvm_status piso_step_bwd_t(difvm_piso* h, const unsigned char* tape, co
   }
   k_adj_mom_cells<T><<<Bc, kPB, 0, st>>>(nc, g, (T)(1.0 / o.dt), D, lamU, Us, rAUb, Db, bb, gpn, Ubar);
   DIFVM_TRY(check_launch("adj_mom_cells"));
+  const int cn = o.time_scheme == DIFVM_TIME_CN;
+  if (cn) {
+    k_adj_cn_cells<T><<<Bc, kPB, 0, st>>>(t, g, (T)(1.0 / o.dt), D, Lo, Up, U0, bb, Db, Ubar);
+    DIFVM_TRY(check_launch("adj_cn_cells"));
+  }
   DIFVM_TRY(difvm_grad_gauss_bwd(m, pr, DIFVM_BC_PRESSURE, gpn, 1, pbar, pbb, st));
   T* lsU = (T*)h->a_lsU;
 #define DIFVM_AMF(NO, SO)                                                                          \
   k_adj_mom_faces<T, NO, SO><<<Bf, kPB, 0, st>>>(t, g, (T)o.nu, psi, phi0, Db, bb, Lob, Upb, lamU, Us, \
-                                                 U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, sd, lsU, Ubbar)
+                                                 U0, gradU, Ub, phibar, h->a_nuf, lkU, ldU, sd, lsU, Ubbar, cn)
   if (no_U) { if (sou) DIFVM_AMF(true, true); else DIFVM_AMF(true, false); }
   else { if (sou) DIFVM_AMF(false, true); else DIFVM_AMF(false, false); }
 #undef DIFVM_AMF

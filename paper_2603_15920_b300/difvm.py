@@ -30,6 +30,8 @@ PRECOND_NONE, PRECOND_JACOBI, PRECOND_AMG, PRECOND_AMG_REUSE = 0, 1, 2, 3
 RENUMBER_RCM, SORT_FACES = 1, 2
 # momentum convection of the PISO step: upwind, or second-order upwind by deferred correction
 CONV_UPWIND, CONV_SOU = 0, 1
+# momentum time scheme of the PISO step: backward Euler or Crank-Nicolson
+TIME_BE, TIME_CN = 0, 1
 # split of S_f in Eq. nonortho_flux (mesh flags bits 2-3)
 NONORTH_OVERRELAXED, NONORTH_MINIMUM, NONORTH_ORTHOGONAL, NONORTH_NONE = 0, 4, 8, 12
 NONORTH_MOMENTUM, NONORTH_PRESSURE, NONORTH_ALL = 1, 2, 3
@@ -70,7 +72,7 @@ class PisoOpts(C.Structure):
                 ("nonorth", C.c_int32), ("solve_U", SolveOpts), ("solve_p", SolveOpts),
                 ("pref_cell", C.c_int32), ("wk_scheme", C.c_int32), ("n_out", C.c_int32),
                 ("wk_patch", C.c_int32 * 16), ("nonorth_limit", C.c_double), ("conv", C.c_int32),
-                ("pad", C.c_int32)]
+                ("time_scheme", C.c_int32)]
 
 
 class PisoInfo(C.Structure):
@@ -503,7 +505,7 @@ def difvm_flux_from_U(mesh, U, U_b, phi=None, stream=None):
 
 
 def piso_opts(nu, dt, n_corr=2, nonorth=True, solve_U=None, solve_p=None, pref_cell=0,
-              wk_scheme=WK_EXACT, wk_patch=(), nonorth_limit=1.0, conv=None):
+              wk_scheme=WK_EXACT, wk_patch=(), nonorth_limit=1.0, conv=None, time_scheme=None):
     o = PisoOpts()
     # nonorth: True = momentum and pressure corrections, False = none, or a bitmask
     mask = NONORTH_ALL if nonorth is True else (0 if nonorth is False else int(nonorth))
@@ -515,6 +517,7 @@ def piso_opts(nu, dt, n_corr=2, nonorth=True, solve_U=None, solve_p=None, pref_c
         o.wk_patch[k] = int(p)
     o.nonorth_limit = float(nonorth_limit)
     o.conv = CONV_UPWIND if conv is None else int(conv)
+    o.time_scheme = TIME_BE if time_scheme is None else int(time_scheme)
     return o
 
 

@@ -59,8 +59,8 @@ def _case(kind, n, seed):
     return m, om, dm, x, kw
 
 
-def _gpu_piso(dm, prec, kw, mask, psi, refine=0, conv=None):
-    o = D.piso_opts(kw["nu"], kw["dt"], kw["ncorr"], mask, conv=conv,
+def _gpu_piso(dm, prec, kw, mask, psi, refine=0, conv=None, time=None):
+    o = D.piso_opts(kw["nu"], kw["dt"], kw["ncorr"], mask, conv=conv, time_scheme=time,
                     solve_U=D.solve_opts(D.BICGSTAB, TOL if prec == D.F64 else 1e-7, max_iter=5000),
                     solve_p=D.solve_opts(D.PCG, TOL if prec == D.F64 else 1e-12, max_iter=20000,
                                          refine_max=refine),
@@ -103,30 +103,33 @@ def _weights(m, x, seed):
 
 
 UP, SOU = O.CONV_UPWIND, O.CONV_SOU
-CASES = [  # (outlet kind, mesh n, non-orthogonal mask, limiter psi, correctors, convection)
-    ("wk_exact", 6, 3, 1.0, 2, UP),
-    ("wk_exact", 6, 3, 0.5, 2, UP),
-    ("wk_fe", 5, 1, 0.3, 2, UP),
-    ("wk_be", 5, 0, 1.0, 1, UP),
-    ("outlet", 6, 3, 0.5, 3, UP),
-    ("cavity", 6, 3, 0.5, 2, UP),
-    ("cavity", 7, 2, 1.0, 3, UP),
-    ("outlet", 6, 0, 1.0, 2, SOU),
-    ("cavity", 6, 3, 0.5, 2, SOU),
-    ("wk_exact", 5, 1, 1.0, 2, SOU),
+BE, CN = O.TIME_BE, O.TIME_CN
+CASES = [  # (outlet kind, mesh n, non-orthogonal mask, limiter psi, correctors, convection, time)
+    ("wk_exact", 6, 3, 1.0, 2, UP, BE),
+    ("wk_exact", 6, 3, 0.5, 2, UP, BE),
+    ("wk_fe", 5, 1, 0.3, 2, UP, BE),
+    ("wk_be", 5, 0, 1.0, 1, UP, BE),
+    ("outlet", 6, 3, 0.5, 3, UP, BE),
+    ("cavity", 6, 3, 0.5, 2, UP, BE),
+    ("cavity", 7, 2, 1.0, 3, UP, BE),
+    ("outlet", 6, 0, 1.0, 2, SOU, BE),
+    ("cavity", 6, 3, 0.5, 2, SOU, BE),
+    ("wk_exact", 5, 1, 1.0, 2, SOU, BE),
+    ("outlet", 6, 3, 1.0, 2, UP, CN),
+    ("cavity", 6, 1, 0.5, 2, SOU, CN),
 ]
 
 
-@pytest.mark.parametrize("kind,n,mask,psi,ncorr,conv", CASES)
-def test_piso_step_bwd_matches_oracle_f64(kind, n, mask, psi, ncorr, conv):
+@pytest.mark.parametrize("kind,n,mask,psi,ncorr,conv,time", CASES)
+def test_piso_step_bwd_matches_oracle_f64(kind, n, mask, psi, ncorr, conv, time):
     m, om, dm, x, kw = _case(kind, n, seed=n + mask)
     kw["ncorr"] = ncorr
     w = _weights(m, x, 3)
-    pg = _gpu_piso(dm, D.F64, kw, mask, psi, conv=conv)
+    pg = _gpu_piso(dm, D.F64, kw, mask, psi, conv=conv, time=time)
     got, _, _ = _gpu_adjoint(dm, pg, x, kw, w)
     ref = O.piso_step_bwd(om, x["U"], x["p"], x["phi"], x["Ub"], x["pb"], w["U"], w["p"], w["phi"],
                           w["pb"], w["pc"], pc=x["pc"], nonorth=mask, psi=psi, tolU=TOL, tolp=TOL,
-                          maxitU=5000, maxitp=20000, conv=conv, **kw)
+                          maxitU=5000, maxitp=20000, conv=conv, time=time, **kw)
     assert ref["status"] == 0
     for key in ("U", "p", "phi", "pb", "Ub"):
         assert nrel(got[key], ref[key]) < 1e-9, (key, nrel(got[key], ref[key]))

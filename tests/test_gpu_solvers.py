@@ -314,10 +314,13 @@ def test_piso_lid_cavity_f64_other_splits(split):
     assert worst < 1e-9, worst
 
 
-@pytest.mark.parametrize("mask", [0, 3])
-def test_piso_sou_deferred_correction_f64(mask):
-    # second-order upwind momentum convection by deferred correction, against the
-    # oracle per step: a lid cavity (all walls) and an inlet/outlet Kuhn box
+@pytest.mark.parametrize("mask,conv,time", [(0, O.CONV_SOU, O.TIME_BE), (3, O.CONV_SOU, O.TIME_BE),
+                                            (3, O.CONV_UPWIND, O.TIME_CN), (1, O.CONV_SOU, O.TIME_CN)],
+                         ids=["sou", "sou-nonorth", "cn", "sou-cn"])
+def test_piso_sou_and_crank_nicolson_f64(mask, conv, time):
+    # second-order upwind convection by deferred correction and the Crank-Nicolson
+    # momentum rows, against the oracle per step: a lid cavity (all walls) and an
+    # inlet/outlet Kuhn box
     for kind in ("cavity", "channel"):
         if kind == "cavity":
             m, Ub = _cavity()
@@ -330,7 +333,7 @@ def test_piso_sou_deferred_correction_f64(mask):
         om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
         U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
         phi = O.flux_from_U(om, U, Ub)
-        o = D.piso_opts(0.01, 0.05, 2, mask, conv=D.CONV_SOU,
+        o = D.piso_opts(0.01, 0.05, 2, mask, conv=conv, time_scheme=time,
                         solve_U=D.solve_opts(D.BICGSTAB, 1e-12, max_iter=2000),
                         solve_p=D.solve_opts(D.PCG, 1e-12, max_iter=20000),
                         pref_cell=int(dm.cell_new_of_old[pref]))
@@ -340,15 +343,15 @@ def test_piso_sou_deferred_correction_f64(mask):
             g = _state_to_gpu(dm, U, p, phi, Ub, pb)
             assert pg.step(*g)[0] == D.OK
             U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12,
-                                              tolp=1e-12, pref_cell=pref, nonorth=mask, conv=O.CONV_SOU)
+                                              tolp=1e-12, pref_cell=pref, nonorth=mask, conv=conv, time=time)
             worst = max(worst, nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p),
                         nrel(dm.from_faces(host(g[2])), phi))
         assert worst < 1e-9, (kind, worst)
-        # the scheme matters: the upwind step from the same state differs
+        # the scheme matters: the upwind backward-Euler step from the same state differs
         Uu = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12, tolp=1e-12, pref_cell=pref,
                          nonorth=mask)[0]
         Us = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12, tolp=1e-12, pref_cell=pref,
-                         nonorth=mask, conv=O.CONV_SOU)[0]
+                         nonorth=mask, conv=conv, time=time)[0]
         assert nrel(Us, Uu) > 1e-4
 
 
