@@ -626,8 +626,56 @@ def difvm_piso_step_bwd(piso, tape, U_b, wk, U_bar, p_bar, phi_bar, p_b_bar=None
 
 
 # ------------------------------------------------- forward + adjoint trajectory
+def binomial_cost(n, s):
+    """Fewest plain forward steps that reverse n steps from a stored initial
+    state with s further state slots (one tape): r n - beta(s + 2, r - 1), r the
+    least integer with beta(s + 1, r) >= n, beta(c, r) = C(c + r, c) (Griewank's
+    binomial bound; the initial state is one of the s + 1 checkpoints)."""
+    from math import comb
+    if n <= 1:
+        return 0
+    c, r = s + 1, 0
+    while comb(c + r, c) < n:
+        r += 1
+    return r * n - (comb(c + 1 + r - 1, c + 1) if r >= 1 else 0)
+
+
+def binomial_schedule(n, s):
+    """Optimal (binomial) checkpoint schedule reversing steps 0..n-1 with the
+    initial state in slot 0 and s further slots (Sec. 2.5, Eq. checkpointing).
+    Actions on one working state: ("load", slot), ("advance", m) plain steps,
+    ("save", slot), ("record", t) the taped step t (the working state is at t),
+    ("bwd", t) its adjoint, ("free", slot).  A segment of length L with c free
+    slots is split after the k that minimises k + cost(L - k, c - 1) + cost(k, c):
+    advance k, save, reverse the right part, free, reverse the left part."""
+    acts = []
+
+    def rev(i, j, c, slot):
+        if j - i == 1:
+            acts.extend([("load", slot), ("record", i), ("bwd", i)])
+            return
+        if c == 0:
+            for t in range(j - 1, i - 1, -1):
+                acts.append(("load", slot))
+                if t > i:
+                    acts.append(("advance", t - i))
+                acts.extend([("record", t), ("bwd", t)])
+            return
+        L = j - i
+        k = min(range(1, L), key=lambda q: (q + binomial_cost(L - q, c - 1) + binomial_cost(q, c), q))
+        new = s - c + 1
+        acts.extend([("load", slot), ("advance", k), ("save", new)])
+        rev(i + k, j, c - 1, new)
+        acts.append(("free", new))
+        rev(i, i + k, c, slot)
+
+    if n > 0:
+        rev(0, n, s, 0)
+    return acts
+
+
 def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=None, stream=None,
-                     tapes=None):
+                     tapes=None, checkpoints=None):
     """n PISO steps forward, then the adjoint of a loss of the final state back
     to the initial state and the parameters (Sec. 2.5, Eq. vjp).
 
@@ -643,9 +691,17 @@ def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=N
 
     tapes: optional preallocated list of at least k tapes (piso.new_tape).
 
+    checkpoints = s (instead of checkpoint_every): the optimal binomial schedule
+    (binomial_schedule) with s stored states besides the initial one and a
+    single tape: memory s + 1 states and one tape; plain forward steps
+    binomial_cost(n, s) + 1 (the last one gives the final state for the loss).
+
     Returns dict(U, p, phi, p_b, pc: adjoints of the initial state; U_b, nu,
     Rp, C, Rd: parameter adjoints; status: worst step status; info: the
     adjoint solver record of the first step)."""
+    if checkpoints is not None:
+        return _simulate_adjoint_binomial(piso, state, nsteps, loss_grad, wk, int(checkpoints), stream,
+                                          tapes)
     U, p, phi, Ub, pb = state
     k = nsteps if not checkpoint_every else max(1, min(int(checkpoint_every), nsteps))
     if tapes is None or len(tapes) < k:
@@ -691,6 +747,76 @@ def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=N
             worst = max(worst, st)
     out = dict(U=Ubar, p=pbar, phi=phibar, p_b=pbbar, U_b=Ubbar, nu=nubar, status=worst,
                info=info)   # info: device record of the first step's adjoint (decode_piso_info)
+    if n_out:
+        w = wkbar.view(n_out, 4)
+        out.update(Rp=w[:, 0], C=w[:, 1], Rd=w[:, 2], pc=w[:, 3])
+    return out
+
+
+def _simulate_adjoint_binomial(piso, state, nsteps, loss_grad, wk, s, stream, tapes):
+    U, p, phi, Ub, pb = state
+    acts = binomial_schedule(nsteps, s)
+    tape = tapes[0] if tapes else piso.new_tape(U.device)
+    n_out = piso.opts.n_out
+    worst = OK
+
+    def snap(src):
+        return [t.clone() for t in src[:4]] + [src[4].clone() if src[4] is not None else None]
+
+    def put(dst, src):
+        for a, b in zip(dst, src):
+            if a is not None:
+                a.copy_(b)
+
+    cur = [U, p, phi, pb, wk]                 # the working state (the caller's tensors)
+    slots = {0: snap(cur)}
+    # forward: the schedule's first descent (loads, advances and saves before its first
+    # record) doubles as the forward pass; one more step gives the final state
+    first = next(q for q, a in enumerate(acts) if a[0] == "record")
+    for a in acts[:first]:
+        if a[0] == "load":
+            put(cur, slots[a[1]])
+        elif a[0] == "advance":
+            for _ in range(a[1]):
+                worst = max(worst, piso.step(cur[0], cur[1], cur[2], Ub, cur[3], wk=cur[4], stream=stream)[0])
+        elif a[0] == "save":
+            slots[a[1]] = snap(cur)
+    at_last = snap(cur)                       # state n - 1
+    worst = max(worst, piso.step(cur[0], cur[1], cur[2], Ub, cur[3], wk=cur[4], stream=stream)[0])
+    Ubar, pbar, phibar, pbbar, pcbar = loss_grad(cur[0], cur[1], cur[2], cur[3], cur[4])
+    final = snap(cur)
+    Ubar, pbar, phibar = Ubar.clone(), pbar.clone(), phibar.clone()
+    pbbar = torch.zeros_like(pb) if pbbar is None else pbbar.clone()
+    wkbar = None
+    if n_out:
+        wkbar = torch.zeros(4 * n_out, dtype=torch.float64, device=U.device)
+        if pcbar is not None:
+            wkbar[3::4] = pcbar
+    Ubbar = torch.zeros_like(Ub)
+    nubar = torch.zeros(1, dtype=torch.float64, device=U.device)
+    info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U.device)
+    piso.adjoint_reset(stream)
+    put(cur, at_last)
+    for a in acts[first:]:
+        kind = a[0]
+        if kind == "load":
+            put(cur, slots[a[1]])
+        elif kind == "advance":
+            for _ in range(a[1]):
+                worst = max(worst, piso.step(cur[0], cur[1], cur[2], Ub, cur[3], wk=cur[4], stream=stream)[0])
+        elif kind == "save":
+            slots[a[1]] = snap(cur)
+        elif kind == "free":
+            del slots[a[1]]
+        elif kind == "record":
+            worst = max(worst, piso.step_record(cur[0], cur[1], cur[2], Ub, cur[3], tape, wk=cur[4],
+                                                stream=stream)[0])
+        elif kind == "bwd":
+            st, _ = piso.step_bwd(tape, Ub, wk, Ubar, pbar, phibar, pbbar, wkbar, Ubbar, nubar, info=info,
+                                  stream=stream)
+            worst = max(worst, st)
+    put(cur, final)                           # the caller's state ends at step n
+    out = dict(U=Ubar, p=pbar, phi=phibar, p_b=pbbar, U_b=Ubbar, nu=nubar, status=worst, info=info)
     if n_out:
         w = wkbar.view(n_out, 4)
         out.update(Rp=w[:, 0], C=w[:, 1], Rd=w[:, 2], pc=w[:, 3])

@@ -245,7 +245,8 @@ def test_multi_step_lid_gradient_matches_oracle_differences():
 
 def test_checkpointed_trajectory_adjoint_equals_fully_taped():
     """simulate_adjoint with the state kept every 2 steps (segments re-run with
-    tapes) gives bitwise the same adjoint as recording all 5 steps."""
+    tapes), or with the binomial schedule (one tape, 0 or 2 extra states), gives
+    bitwise the same adjoint as recording all 5 steps."""
     m, om, dm, x, kw = _case("wk_exact", 5, 12)
     pg = _gpu_piso(dm, D.F64, kw, 3, 0.5)
     V = cuda(dm.to_cells(m.V))
@@ -254,13 +255,18 @@ def test_checkpointed_trajectory_adjoint_equals_fully_taped():
         return (V * U).contiguous(), torch.zeros_like(p), torch.zeros_like(phi), None, \
             torch.ones(1, dtype=torch.float64, device="cuda")
 
-    res = []
-    for ck in (None, 2):
+    res, finals = [], []
+    for ck in (dict(), dict(checkpoint_every=2), dict(checkpoints=0), dict(checkpoints=2)):
         g = [cuda(dm.to_cells(x["U"])), cuda(dm.to_cells(x["p"])), cuda(dm.to_faces(x["phi"])),
              cuda(dm.to_bnd(x["Ub"])), cuda(dm.to_bnd(x["pb"]))]
         wk = cuda(np.array([0.3, 0.8, 1.2, 0.4]))
-        r = D.simulate_adjoint(pg, g, 5, loss_grad, wk=wk, checkpoint_every=ck)
+        r = D.simulate_adjoint(pg, g, 5, loss_grad, wk=wk, **ck)
         assert r["status"] == D.OK
         res.append(r)
-    for key in ("U", "p", "phi", "p_b", "U_b", "nu", "Rp", "C", "Rd", "pc"):
-        assert torch.equal(res[0][key], res[1][key]), key
+        finals.append([t.clone() for t in g] + [wk.clone()])
+    # uniform segments and the binomial schedule (no extra slot, two slots): bitwise equal
+    for r, fin in zip(res[1:], finals[1:]):
+        for key in ("U", "p", "phi", "p_b", "U_b", "nu", "Rp", "C", "Rd", "pc"):
+            assert torch.equal(res[0][key], r[key]), key
+        for a, b in zip(finals[0], fin):      # the caller's state ends at the final step
+            assert torch.equal(a, b)
