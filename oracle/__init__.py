@@ -193,6 +193,23 @@ def pcg(m, D, L, U, b, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
     return _solve("om_pcg", m, D, L, U, b, x0, tol_rel, tol_abs, maxit)
 
 
+def dic_factor(m, D, L, rank):
+    """The diagonal d of the DIC factorisation in the elimination order rank[i]."""
+    d = np.zeros(m.nc)
+    lib().om_dic_factor(m.ref(), _p(_f64(D)), _p(_f64(np.concatenate([L, [0.0]]))), _p(_i32(rank)), _p(d))
+    return d
+
+
+def pcg_dic(m, D, L, b, rank, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
+    """CG preconditioned by diagonal incomplete Cholesky, cells eliminated in the
+    order rank[i] (symmetric matrix: D, L)."""
+    x = np.zeros(m.nc) if x0 is None else np.array(x0, np.float64)
+    info = _Info()
+    lib().om_pcg_dic(m.ref(), _p(_f64(D)), _p(_f64(np.concatenate([L, [0.0]]))), _p(_i32(rank)),
+                     _p(_f64(b)), _p(x), C.c_double(tol_rel), C.c_double(tol_abs), int(maxit), C.byref(info))
+    return x, dict(iters=info.iters, res0=info.res0, res=info.res, bnorm=info.bnorm, status=info.status)
+
+
 def bicgstab(m, D, L, U, b, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
     return _solve("om_bicgstab", m, D, L, U, b, x0, tol_rel, tol_abs, maxit)
 

@@ -347,6 +347,123 @@ int om_pcg(const om_mesh *m, const double *D, const double *L, const double *U, 
   return info->status;
 }
 
+/* Diagonal incomplete Cholesky (the CG preconditioner the paper names, Sec. 2.6.1,
+ * in its DIC form for a symmetric LDU matrix: D diagonal, L[f] the off-diagonal of
+ * internal face f).  Cells are eliminated in the order rank[i] (the library uses its
+ * RCM numbering); for face f, lo(f) / hi(f) are its cells of lower / higher rank.
+ *   d_i = D_i - sum_{f: hi(f)=i} L_f^2 / d_lo(f)          in increasing rank
+ * M = (Dd + Lo) Dd^-1 (Dd + Lo^T) with Dd = diag(d), Lo the strictly lower part:
+ * diag(M) = diag(A) and M = A on the matrix's sparsity pattern (fill-in dropped).
+ * d[nc] out. */
+static void dic_sides(const om_mesh *m, const int *rank, int f, int *lo, int *hi) {
+  int O = m->owner[f], N = m->neighbour[f];
+  if (rank[O] < rank[N]) { *lo = O; *hi = N; } else { *lo = N; *hi = O; }
+}
+
+/* faces of each cell (CSR over cells) and the cells in rank order */
+static void dic_tables(const om_mesh *m, const int *rank, int **fptr, int **fidx, int **byrank) {
+  int nc = m->nc, ni = m->nint;
+  int *ptr = calloc((size_t)nc + 1, sizeof(int)), *idx = malloc(sizeof(int) * 2 * (ni + 1));
+  for (int f = 0; f < ni; ++f) { ptr[m->owner[f] + 1]++; ptr[m->neighbour[f] + 1]++; }
+  for (int i = 0; i < nc; ++i) ptr[i + 1] += ptr[i];
+  int *fill = malloc(sizeof(int) * nc);
+  for (int i = 0; i < nc; ++i) fill[i] = ptr[i];
+  for (int f = 0; f < ni; ++f) { idx[fill[m->owner[f]]++] = f; idx[fill[m->neighbour[f]]++] = f; }
+  int *br = malloc(sizeof(int) * nc);
+  for (int i = 0; i < nc; ++i) br[rank[i]] = i;
+  free(fill);
+  *fptr = ptr; *fidx = idx; *byrank = br;
+}
+
+void om_dic_factor(const om_mesh *m, const double *D, const double *L, const int *rank, double *d) {
+  int *ptr, *idx, *br;
+  dic_tables(m, rank, &ptr, &idx, &br);
+  for (int k = 0; k < m->nc; ++k) {
+    int i = br[k];
+    double s = D[i];
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int f = idx[e], lo, hi;
+      dic_sides(m, rank, f, &lo, &hi);
+      if (hi == i) s -= L[f] * L[f] / d[lo];
+    }
+    d[i] = s;
+  }
+  free(ptr); free(idx); free(br);
+}
+
+/* z = M^-1 r: forward (Dd + Lo) y = r, then backward (I + Dd^-1 Lo^T) z = y */
+static void dic_apply(const om_mesh *m, const int *rank, const int *ptr, const int *idx,
+                      const int *br, const double *d, const double *L, const double *r, double *z) {
+  int nc = m->nc;
+  for (int k = 0; k < nc; ++k) {
+    int i = br[k];
+    double s = r[i];
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int f = idx[e], lo, hi;
+      dic_sides(m, rank, f, &lo, &hi);
+      if (hi == i) s -= L[f] * z[lo];
+    }
+    z[i] = s / d[i];
+  }
+  for (int k = nc - 1; k >= 0; --k) {
+    int i = br[k];
+    double s = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int f = idx[e], lo, hi;
+      dic_sides(m, rank, f, &lo, &hi);
+      if (lo == i) s += L[f] * z[hi];
+    }
+    z[i] -= s / d[i];
+  }
+}
+
+/* CG preconditioned by DIC in the elimination order rank; same stopping rule as om_pcg */
+int om_pcg_dic(const om_mesh *m, const double *D, const double *L, const int *rank, const double *b,
+               double *x, double tol_rel, double tol_abs, int maxit, om_info *info) {
+  int n = m->nc;
+  double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+  double *p = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
+  double *d = malloc(sizeof(double) * n);
+  int *ptr, *idx, *br;
+  dic_tables(m, rank, &ptr, &idx, &br);
+  om_dic_factor(m, D, L, rank, d);
+  double bn = sqrt(vdot(n, b, b));
+  info->bnorm = bn; info->iters = 0; info->status = 0;
+  int it = 0;
+  double rn = 0.0;
+  if (bn == 0.0) {
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    info->res0 = 0.0;
+  } else {
+    double tol = fmax(tol_rel * bn, tol_abs);
+    om_ldu_apply(m, 1, D, L, NULL, x, q);
+    for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    rn = sqrt(vdot(n, r, r));
+    info->res0 = rn;
+    dic_apply(m, rank, ptr, idx, br, d, L, r, z);
+    for (int i = 0; i < n; ++i) p[i] = z[i];
+    double rz = vdot(n, r, z);
+    while (rn > tol && it < maxit) {
+      om_ldu_apply(m, 1, D, L, NULL, p, q);
+      double alpha = rz / vdot(n, p, q);
+      for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+      ++it;
+      rn = sqrt(vdot(n, r, r));
+      if (!isfinite(rn)) { info->status = 5; break; }
+      if (rn <= tol) break;
+      dic_apply(m, rank, ptr, idx, br, d, L, r, z);
+      double rz1 = vdot(n, r, z);
+      double beta = rz1 / rz;
+      rz = rz1;
+      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (info->status == 0 && rn > tol) info->status = 3;
+  }
+  info->iters = it; info->res = rn;
+  free(r); free(z); free(p); free(q); free(d); free(ptr); free(idx); free(br);
+  return info->status;
+}
+
 /* Right-Jacobi-preconditioned BiCGStab (van der Vorst 1992) for the
  * non-symmetric momentum system (Sec. 2.6.1).  Same stopping rule as om_pcg. */
 int om_bicgstab(const om_mesh *m, const double *D, const double *L, const double *U,
