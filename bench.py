@@ -457,6 +457,11 @@ def run_ours(args):
     jacobi = {"value": 1e3 * K / rj["ms"], "unit": "steps/s", "ms_per_step": rj["ms"] / K,
               "status": int(rj["status"]), "pressure_iters_last_step": rj["info"]["itp"][:2],
               "api": "difvm_piso_step_graph, pressure CG with Jacobi preconditioning"}
+    # the paper's preconditioner (diagonal incomplete Cholesky, level-scheduled): FP64, one step
+    rd = timed(D.F64, 1, 1, graph=True, precond=D.PRECOND_DIC)
+    dic = {"value": 1e3 / rd["ms"], "unit": "steps/s", "ms_per_step": rd["ms"], "steps": 1,
+           "status": int(rd["status"]), "pressure_iters_last_step": rd["info"]["itp"][:2],
+           "api": "difvm_piso_step_graph, FP64, pressure CG with DIC (one launch per dependency level)"}
     rs = timed(D.F32, W, K, graph=True, conv=D.CONV_SOU)
     sou = {"value": 1e3 * K / rs["ms"], "unit": "steps/s", "ms_per_step": rs["ms"] / K,
            "status": int(rs["status"]), "pressure_iters_last_step": rs["info"]["itp"][:2],
@@ -587,6 +592,7 @@ def run_ours(args):
         "pressure_iters_last_step": gi["itp"][:2], "momentum_iters_last_step": gi["itU"],
         "host_loop": host_loop,
         "jacobi_pressure": jacobi,
+        "dic_pressure": dic,
         "sou_convection": sou,
         "crank_nicolson": cn,
         "f64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64,

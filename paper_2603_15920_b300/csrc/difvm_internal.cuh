@@ -168,6 +168,8 @@ __device__ __forceinline__ int face_kind(const Topo& t, int b, int cls) {
 struct difvm_mesh_impl;
 struct AmgHier;
 void amg_free(AmgHier* h);
+struct DicLevels;
+void dic_free(DicLevels* d);
 }  // namespace difvm
 
 // The opaque handle of the C ABI.
@@ -210,6 +212,7 @@ struct difvm_mesh {
   int* seg_cs = nullptr;     // [ncases + 1] first cell of each case
   std::vector<int32_t> bown_host;  // boundary-face owners, internal numbering
   difvm::AmgHier* amg = nullptr;   // multigrid hierarchy, built on first use
+  difvm::DicLevels* dic = nullptr; // incomplete-Cholesky dependency levels, built on first use
   // half-face layout of the CSR rows (see difvm::Hf)
   int hf_w = 0;
   int64_t hf_nslots = 0;
@@ -271,6 +274,11 @@ difvm_status amg_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, con
 difvm_status amg_refine(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
                         const double* b64, double* x64, void* ws, size_t wsbytes, difvm_solve_info* info,
                         cudaStream_t st);
+// ---------------------------- incomplete-Cholesky-preconditioned CG (dic.cu)
+size_t dic_workspace_bytes(difvm_mesh* m, size_t elt);
+template <typename T>
+difvm_status dic_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,
+                       T* x, void* ws, size_t wsbytes, difvm_solve_info* info, cudaStream_t st);
 difvm_status check_mesh(const difvm_mesh* m);
 difvm_status check_prec(difvm_prec p);
 

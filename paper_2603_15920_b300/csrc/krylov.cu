@@ -1535,6 +1535,12 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
                                      "symmetric matrix of a single (not batched) mesh");
     return amg_solve<T>(m, o, (const T*)D, (const T*)L, (const T*)b, (T*)x, ws, wsbytes, info, st);
   }
+  if (o->precond == DIFVM_PRECOND_DIC) {
+    if (o->method != DIFVM_PCG || ncomp != 1 || U || m->seg)
+      return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner serves single-RHS CG on a "
+                                     "symmetric matrix of a single (not batched) mesh");
+    return dic_solve<T>(m, o, (const T*)D, (const T*)L, (const T*)b, (T*)x, ws, wsbytes, info, st);
+  }
   WsLayout Ly = layout(m, sizeof(T), o->method, ncomp);
   if (!ws || wsbytes < Ly.total)
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed", wsbytes, Ly.total);
@@ -1608,6 +1614,10 @@ extern "C" size_t difvm_krylov_opts_workspace_bytes(difvm_mesh_t m, difvm_prec p
   if (o->precond == DIFVM_PRECOND_AMG || o->precond == DIFVM_PRECOND_AMG_REUSE) {
     if (o->method != DIFVM_PCG || ncomp != 1 || m->seg) return 0;
     return amg_workspace_bytes(m, refine ? 4 : (prec == DIFVM_F64 ? 8 : 4));
+  }
+  if (o->precond == DIFVM_PRECOND_DIC) {
+    if (o->method != DIFVM_PCG || ncomp != 1 || m->seg || refine) return 0;
+    return dic_workspace_bytes(m, prec == DIFVM_F64 ? 8 : 4);
   }
   const size_t plain = difvm_krylov_workspace_bytes(m, prec, o->method, ncomp);
   return refine ? std::max(plain, difvm_krylov_refine_workspace_bytes(m, o->method, ncomp)) : plain;

@@ -228,6 +228,7 @@ static void free_mesh(difvm_mesh* m) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   amg_free(m->amg);
+  dic_free(m->dic);
   if (cur >= 0) cudaSetDevice(cur);
   delete m;
 }

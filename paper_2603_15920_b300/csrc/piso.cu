@@ -1325,6 +1325,12 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves the pressure CG only");
   if (amg_opts(o->solve_p) && (o->solve_p.method != DIFVM_PCG || m->seg))
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner needs CG on a single (not batched) mesh");
+  if (o->solve_U.precond == DIFVM_PRECOND_DIC)
+    return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner serves the pressure CG only");
+  if (o->solve_p.precond == DIFVM_PRECOND_DIC &&
+      (o->solve_p.method != DIFVM_PCG || m->seg || (prec == DIFVM_F32 && o->solve_p.refine_max > 0)))
+    return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner needs CG without refinement on a "
+                                   "single (not batched) mesh");
   for (int k = 0; k < o->n_out; ++k) {
     int p = o->wk_patch[k];
     if (p < 0 || p >= m->npatch || m->patch_type[p] != DIFVM_PATCH_OUTLET)

@@ -26,7 +26,7 @@ BC_VELOCITY, BC_PRESSURE, BC_ALL_FIXED, BC_ALL_ZEROGRAD = 0, 1, 2, 3
 DIV_UPWIND, DIV_LINEAR = 0, 1
 WK_EXACT, WK_FE, WK_BE = 0, 1, 2
 PCG, BICGSTAB = 0, 1
-PRECOND_NONE, PRECOND_JACOBI, PRECOND_AMG, PRECOND_AMG_REUSE = 0, 1, 2, 3
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_AMG, PRECOND_AMG_REUSE, PRECOND_DIC = 0, 1, 2, 3, 4
 RENUMBER_RCM, SORT_FACES = 1, 2
 # momentum convection of the PISO step: upwind, or second-order upwind by deferred correction
 CONV_UPWIND, CONV_SOU = 0, 1
