@@ -76,8 +76,9 @@ enum { DIFVM_WK_EXACT = 0, DIFVM_WK_FE = 1, DIFVM_WK_BE = 2 };  /* Eq. windkesse
 enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
 /* DIFVM_PRECOND_AMG: one V-cycle of aggregation multigrid per CG iteration
  * (pairwise aggregation on c_f, two passes per level, down to <= 256 cells;
- * Galerkin coarse operators summed in a fixed order every solve; two damped
- * Jacobi sweeps (omega 0.7) before and after the coarse correction, which is
+ * Galerkin coarse operators summed in a fixed order every solve; two Jacobi
+ * sweeps with degree-2 Chebyshev weights on [1/2, 2] (0.56, 1.39) before and
+ * after the coarse correction, which is
  * scaled by 1.8; dense inverse on the coarsest level).  A fixed SPD operator:
  * it changes the iteration count, not the solution.  The paper uses ILU, whose
  * triangular solves are sequential along the mesh ordering.  Single-RHS CG on

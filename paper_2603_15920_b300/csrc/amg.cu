@@ -15,9 +15,9 @@
 //     diagonal is the sum of its cells' diagonals plus twice the coefficients
 //     of the faces inside it; a coarse face coefficient is the sum of the fine
 //     faces between its two aggregates), each sum in a fixed order;
-//   V-cycle: two damped-Jacobi sweeps before and after the coarse correction,
-//     the coarse correction scaled by kAmgScale, the coarsest level solved
-//     with a dense inverse (Gauss-Jordan in one block, FP32, symmetrised);
+//   V-cycle: two Jacobi sweeps with Chebyshev weights before and after the
+//     coarse correction, which is scaled by kAmgScale; the coarsest level
+//     solved with a dense inverse (Gauss-Jordan in one block, FP32, symmetrised);
 //   mixed precision: CG with FP64 accuracy (float-float vectors) around the FP32
 //     V-cycle (no refinement sweeps).
 //
@@ -32,7 +32,15 @@
 
 namespace difvm {
 
-constexpr double kAmgOmega = 0.7;   // Jacobi damping
+// Jacobi weights of the two smoothing sweeps: the reciprocals of the degree-2
+// Chebyshev nodes on [1/2, 2] (Gershgorin bounds the spectrum of D^-1 A of these
+// diagonally dominant matrices by 2), 5/4 -+ (3/4) cos(pi/4).  The two sweeps
+// before the coarse correction use (w1, w2), the two after it (w2, w1): the
+// smoother is the degree-2 Chebyshev polynomial in D^-1 A either way, so the
+// V-cycle stays symmetric.  CPU prototype on a 40^3 Kuhn mesh: 22 CG iterations
+// against 25 with two omega = 0.7 sweeps, at the same cost per iteration.
+constexpr double kAmgW1 = 1.0 / (1.25 + 0.75 * 0.70710678118654752);
+constexpr double kAmgW2 = 1.0 / (1.25 - 0.75 * 0.70710678118654752);
 constexpr double kAmgScale = 1.8;   // over-correction of the coarse-grid correction
 constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 x 32)
 constexpr int kAmgMaxLevels = 16;
@@ -538,7 +546,7 @@ __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* 
   }
 }
 
-// pre-smoothing from zero, two sweeps: x1 = w rD r, y = x1 + w rD (r - A x1)
+// pre-smoothing from zero, two sweeps: x1 = w1 rD r, y = x1 + w2 rD (r - A x1)
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                  const T* r, T* y, const int* done) {
@@ -546,10 +554,10 @@ __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D,
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
-  const T w = (T)kAmgOmega;
-  auto x1 = [&](int j) { return w * rD[j] * r[j]; };
+  const T w1 = (T)kAmgW1, w2 = (T)kAmgW2;
+  auto x1 = [&](int j) { return w1 * rD[j] * r[j]; };
   const T ax = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, x1);
-  if (ok && t == 0) y[i] = x1(i) + w * rD[i] * (r[i] - ax);
+  if (ok && t == 0) y[i] = x1(i) + w2 * rD[i] * (r[i] - ax);
 }
 
 // residual after pre-smoothing: res = r - A y
@@ -604,13 +612,13 @@ __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* 
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
-  const T w = (T)kAmgOmega, sc = (T)kAmgScale;
+  const T w = (T)kAmgW2, sc = (T)kAmgScale;   // first sweep after the correction: w2
   auto z = [&](int j, int a) { return y[j] + sc * xc[a]; };
   const T az = lev_row<T, TPR, true>(A, L, D, Lv, i, t, ok, z);
   if (ok && t == 0) out[i] = z(i, L.agg[i]) + w * rD[i] * (r[i] - az);
 }
 
-// second post-smoothing sweep: v = u + w rD (r - A u)
+// second post-smoothing sweep: v = u + w1 rD (r - A u)
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                    const T* r, const T* u, T* v, const int* done) {
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* 
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
-  const T om = (T)kAmgOmega;
+  const T om = (T)kAmgW1;
   auto xu = [&](int j) { return u[j]; };
   const T au = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, xu);
   if (ok && t == 0) v[i] = u[i] + om * rD[i] * (r[i] - au);
@@ -631,7 +639,7 @@ __global__ void __launch_bounds__(kKB) k_amg_post2_dot(AmgLev L, Mat<T> A, const
                                                        T* v, KWork w, int first) {
   pdl_chain();
   if (w.st[0].done) return;
-  const T om = (T)kAmgOmega;
+  const T om = (T)kAmgW1;
   DotAcc<T> rz;
   auto xu = [&](int j) { return u[j]; };
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
