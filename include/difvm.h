@@ -79,7 +79,7 @@ enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
  * Galerkin coarse operators summed in a fixed order every solve; two Jacobi
  * sweeps with degree-2 Chebyshev weights on [1/2, 2] (0.56, 1.39) before and
  * after the coarse correction, which is
- * scaled by 1.8; dense inverse on the coarsest level).  A fixed SPD operator:
+ * scaled by 1.9; dense inverse on the coarsest level).  A fixed SPD operator:
  * it changes the iteration count, not the solution.  The paper uses ILU, whose
  * triangular solves are sequential along the mesh ordering.  Single-RHS CG on
  * a symmetric matrix of a single mesh only (EINVAL otherwise); the hierarchy
