@@ -168,6 +168,47 @@ void group_by(const std::vector<int>& key, int nk, std::vector<int>& ptr, std::v
     if (key[i] >= 0 && (!keep || (*keep)[i])) idx[fill[key[i]]++] = (int)i;
 }
 
+// Relabel the cells of a new level so that, inside windows of 256 ids, they come
+// in decreasing number of faces: the 32-row slices of the level's sliced ELL
+// then hold rows of similar length (padding ~45% -> ~8% on Kuhn meshes), while
+// ids stay within their window (locality kept).  agg (finer cell -> new cell)
+// and fmap (finer face -> new face) follow; the new level's faces are re-sorted.
+void relabel_by_degree(Graph& g, std::vector<int>& agg, std::vector<int>& fmap) {
+  const int n = g.n, nf = (int)g.on.size();
+  std::vector<int> deg(n, 0);
+  for (const int2& o : g.on) { deg[o.x]++; deg[o.y]++; }
+  std::vector<int> order(n), newid(n);
+  std::iota(order.begin(), order.end(), 0);
+  for (int w0 = 0; w0 < n; w0 += 256) {
+    const int w1 = std::min(n, w0 + 256);
+    std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) { return deg[a] > deg[b]; });
+  }
+  for (int k = 0; k < n; ++k) newid[order[k]] = k;
+  for (int& a : agg) a = newid[a];
+  std::vector<int64_t> key(nf);
+  for (int F = 0; F < nf; ++F) {
+    int a = newid[g.on[F].x], b = newid[g.on[F].y];
+    if (a > b) std::swap(a, b);
+    key[F] = (int64_t)a * n + b;
+  }
+  std::vector<int> fo(nf), fnew(nf);
+  std::iota(fo.begin(), fo.end(), 0);
+  std::sort(fo.begin(), fo.end(), [&](int a, int b) { return key[a] < key[b]; });
+  Graph h;
+  h.n = n;
+  h.on.resize(nf);
+  h.w.resize(nf);
+  for (int k = 0; k < nf; ++k) {
+    const int F = fo[k];
+    fnew[F] = k;
+    h.on[k] = make_int2((int)(key[F] / n), (int)(key[F] % n));
+    h.w[k] = g.w[F];
+  }
+  for (int& F : fmap)
+    if (F >= 0) F = fnew[F];
+  g = std::move(h);
+}
+
 difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
   // level-0 graph: the mesh's internal faces weighted by c_f
   Graph g;
@@ -251,8 +292,10 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
       for (size_t f = 0; f < g.on.size(); ++f) {
         const int F1 = f1[f];
         fmap[f] = F1 < 0 ? -1 : f2[F1];
-        if (fmap[f] < 0) inside[f] = agg[g.on[f].x];
       }
+      relabel_by_degree(g2, agg, fmap);
+      for (size_t f = 0; f < g.on.size(); ++f)
+        if (fmap[f] < 0) inside[f] = agg[g.on[f].x];
       std::vector<int> chp, chi, cip, cii, cfp, cfi;
       group_by(agg, n2, chp, chi);
       group_by(inside, n2, cip, cii);
