@@ -1028,6 +1028,20 @@ static KWork amg_work_t(const AmgRun<T>& R, int k, int maxit, double tol_rel, do
   return w;
 }
 
+// Build the ELL values and multigrid operators of the matrix (D, Lo) in the
+// workspace, so that a following AMG_REUSE solve with this workspace starts at
+// once (the PISO step builds them beside its momentum solve).  elt = 4: FP32
+// operators (FP32 solves and the mixed-precision solve), 8: FP64.
+difvm_status amg_prebuild(difvm_mesh* m, size_t elt, const void* D, const void* Lo, void* ws, size_t wsbytes,
+                          cudaStream_t st) {
+  if (elt == 8) {
+    AmgRun<double> R;
+    return amg_prepare<double>(m, (const double*)D, (const double*)Lo, ws, wsbytes, R, st, false);
+  }
+  AmgRun<float> R;
+  return amg_prepare<float>(m, (const float*)D, (const float*)Lo, ws, wsbytes, R, st, false);
+}
+
 template <typename T, int MW>
 static difvm_status amg_solve_mw(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo,
                                  const T* b, T* x, void* ws, size_t wsbytes, difvm_solve_info* info,

@@ -271,6 +271,8 @@ size_t amg_workspace_bytes(difvm_mesh* m, size_t elt);
 template <typename T>
 difvm_status amg_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,
                        T* x, void* ws, size_t wsbytes, difvm_solve_info* info, cudaStream_t st);
+difvm_status amg_prebuild(difvm_mesh* m, size_t elt, const void* D, const void* Lo, void* ws, size_t wsbytes,
+                          cudaStream_t st);
 difvm_status amg_refine(difvm_mesh* m, const difvm_solve_opts* o, const float* D, const float* Lo,
                         const double* b64, double* x64, void* ws, size_t wsbytes, difvm_solve_info* info,
                         cudaStream_t st);

@@ -32,6 +32,12 @@ struct difvm_piso {
   void *rhs = nullptr, *rAU = nullptr, *HbyA = nullptr, *Dp = nullptr, *Lp = nullptr, *bp = nullptr;
   void *phiHbyA = nullptr, *af = nullptr, *nonorth = nullptr;
   void* sou_d = nullptr;           // second-order upwind: V4<T> x_f - x_O [ni], then x_f - x_N [ni]
+  // multigrid pressure solves: the operators of corrector 0 are built on a side
+  // stream while the momentum predictor is solved (the pressure matrix needs only
+  // V/D); rAU_e is that stream's copy of V/D
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void* rAU_e = nullptr;
   void* wsU = nullptr;
   size_t wsU_bytes = 0;
   void* wsp = nullptr;
@@ -434,6 +440,55 @@ __global__ void __launch_bounds__(kPB) k_p_cells(Topo t, const T* phiHbyA, const
   if (pinflag ? pinflag[i] != 0 : i == pin) d += d;
   Dp[i] = d;
   bp[i] = r;
+}
+
+// The pressure matrix alone (the same arithmetic as k_HbyA's rAU, k_p_faces' a_f,
+// Lp and k_p_cells' Dp, so the values are identical): rAU = V/D, a_f, Lp = -a_f
+template <typename T>
+__global__ void k_p_rau(int nc, Geo<T> g, const T* D, T* rAU) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  rAU[i] = g.V[i] / D[i];
+}
+template <typename T>
+__global__ void k_p_matrix(Topo t, Geo<T> g, const T* rAU, T* af, T* Lp) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nf) return;
+  const V4<T> ck = ld4(g.ck + f);
+  if (f < t.ni) {
+    const int2 on = t.on[f];
+    const T w = ld4(g.Sw + f).w;
+    const T rf = w * rAU[on.x] + (T(1) - w) * rAU[on.y];
+    const T a = rf * ck.x;
+    af[f] = a;
+    Lp[f] = -a;
+  } else {
+    const int bb = f - t.ni;
+    const int ku = face_kind(t, bb, DIFVM_BC_VELOCITY);
+    const int kp = face_kind(t, bb, DIFVM_BC_PRESSURE);
+    af[f] = (ku != DIFVM_FACE_EMPTY && kp == DIFVM_FACE_FIXED) ? rAU[t.bown[bb]] * ck.x : T(0);
+  }
+}
+template <typename T>
+__global__ void __launch_bounds__(kPB) k_p_diag(Topo t, const T* af, int pin, const unsigned char* pinflag,
+                                                T* Dp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.nc) return;
+  T d = T(0);
+  const int e1 = t.cptr[i + 1];
+  for (int e = t.cptr[i]; e < e1; ++e) {
+    const int f = t.cent[e] >> 1;
+    if (f < t.ni) {
+      d += af[f];
+    } else {
+      const int bb = f - t.ni;
+      if (face_kind(t, bb, DIFVM_BC_PRESSURE) == DIFVM_FACE_FIXED &&
+          face_kind(t, bb, DIFVM_BC_VELOCITY) != DIFVM_FACE_EMPTY)
+        d += af[f];
+    }
+  }
+  if (pinflag ? pinflag[i] != 0 : i == pin) d += d;
+  Dp[i] = d;
 }
 
 // Rhie-Chow flux correction: phi = phiHbyA - a_f dp - nonorth
@@ -1189,6 +1244,20 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
                       (const V4<T>*)h->sou_d, gradp, D, b, rhs);
   DIFVM_TRY(check_launch("mom_cells"));
   if (o.time_scheme == DIFVM_TIME_CN) DIFVM_TRY(momentum_cn<T>(h, U, st));
+  // multigrid pressure solves: build corrector 0's operators beside the momentum solve
+  const bool prebuilt = h->side != nullptr;
+  if (prebuilt) {
+    DIFVM_CUDA(cudaEventRecord(h->ev_fork, st));
+    DIFVM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    T* rAUe = (T*)h->rAU_e;
+    k_p_rau<T><<<Bc, kPB, 0, h->side>>>(nc, g, D, rAUe);
+    k_p_matrix<T><<<Bf, kPB, 0, h->side>>>(t, g, rAUe, af, Lp);
+    k_p_diag<T><<<Bc, kPB, 0, h->side>>>(t, af, h->pin, h->pinflag, Dp);
+    DIFVM_TRY(check_launch("p_matrix"));
+    count_launch(); count_launch();
+    DIFVM_TRY(amg_prebuild(m, h->mixed ? 4 : sizeof(T), Dp, Lp, h->wsp, h->wsp_bytes, h->side));
+    DIFVM_CUDA(cudaEventRecord(h->ev_join, h->side));
+  }
   {
     difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
     difvm_status s = difvm_krylov_solve(m, pr, &o.solve_U, D, Lo, Up, rhs, U, 3, h->wsU, h->wsU_bytes,
@@ -1197,6 +1266,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     worst = std::max(worst, (int)s);
   }
   if (tape) DIFVM_CUDA(cudaMemcpyAsync(tape + TL.Us, U, v3, cudaMemcpyDeviceToDevice, st));
+  if (prebuilt) DIFVM_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
   // 3. pressure correctors
   for (int corr = 0; corr < o.n_corr; ++corr) {
     k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, U, HbyA, rAU);
@@ -1214,7 +1284,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     // the pressure matrix depends only on V/D: correctors after the first reuse the
     // multigrid operators the first one built
     difvm_solve_opts sp = o.solve_p;
-    if (corr > 0 && amg_opts(sp)) sp.precond = DIFVM_PRECOND_AMG_REUSE;
+    if ((corr > 0 || prebuilt) && amg_opts(sp)) sp.precond = DIFVM_PRECOND_AMG_REUSE;
     difvm_status s;
     if (h->mixed) {
       k_to64<T><<<Bc, kPB, 0, st>>>(nc, bp, h->b64);
@@ -1300,6 +1370,9 @@ extern "C" void difvm_piso_destroy(difvm_piso_t h) {
   for (auto& g : h->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -1407,6 +1480,15 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
   for (int k = 0; k < o->n_out; ++k) {
     tab[k] = m->patch_start[o->wk_patch[k]];
     tab[16 + k] = m->patch_size[o->wk_patch[k]];
+  }
+  if (amg_opts(o->solve_p) && !m->seg) {
+    if (!alloc(&h->rAU_e, nc * e) ||
+        cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      difvm_piso_destroy(h);
+      return set_error(DIFVM_ECUDA, "side stream for the multigrid setup could not be created");
+    }
   }
   if (o->conv == DIFVM_CONV_SOU && m->ni > 0) {
     if (e == 8)
