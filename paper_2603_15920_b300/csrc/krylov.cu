@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kKB) k_bicg_init(Topo t, Mat<T> A, int jacobi,
     s.iters = 0;
     s.status = DIFVM_OK;
     s.rho = 1.0; s.alpha = 1.0; s.omega = 1.0;
+    s.beta = (s.rz / s.rho) * (s.alpha / s.omega);   // the p-update's scalar (p = v = 0 here)
     s.sconv = 0;
     s.zero_rhs = s.bb == 0.0;
     s.done = s.zero_rhs || s.rr <= s.tol2;
@@ -207,11 +208,11 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(kKB) k_bicg_p(int nc, const T* r, const T* v, T* p, KWork w) {
   const unsigned act = active_mask<NC>(w);
   if (!act) return;
-  T be[NC], om[NC];
+  T be[NC], om[NC];   // beta = (rho_new / rho)(alpha / omega), formed once by the last block before
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const KState& s = w.st[c];
-    be[c] = (T)((s.rz / s.rho) * (s.alpha / s.omega));
+    be[c] = (T)s.beta;
     om[c] = (T)s.omega;
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
@@ -402,6 +403,7 @@ __global__ void __launch_bounds__(kKB) k_bicg_update(int nc, const T* y, const T
     if (!(act >> c & 1)) continue;
     s.rr = tot[2 * c];
     s.rz = tot[2 * c + 1];
+    s.beta = (s.rz / s.rho) * (s.alpha / s.omega);
     if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; continue; }
     if (s.rr <= s.tol2) { s.done = 1; continue; }
     if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; continue; }
@@ -1181,6 +1183,7 @@ __global__ void __launch_bounds__(kKB) k_sg_bicg_init(Topo t, Mat<T> A, int jaco
     s.iters = 0;
     s.status = DIFVM_OK;
     s.rho = 1.0; s.alpha = 1.0; s.omega = 1.0;
+    s.beta = (s.rz / s.rho) * (s.alpha / s.omega);
     s.sconv = 0;
     s.zero_rhs = s.bb == 0.0;
     s.done = s.zero_rhs || s.rr <= s.tol2;
@@ -1197,7 +1200,7 @@ __global__ void __launch_bounds__(kKB) k_sg_bicg_p(int nc, const T* r, const T* 
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const KState& s = w.st[B.k * NC + c];
-    be[c] = (T)((s.rz / s.rho) * (s.alpha / s.omega));
+    be[c] = (T)s.beta;   // formed once by the last block of the update
     om[c] = (T)s.omega;
   }
   for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x)
@@ -1393,6 +1396,7 @@ __global__ void __launch_bounds__(kKB) k_sg_bicg_update(int nc, const T* y, cons
     if (!(act >> c & 1)) continue;
     s.rr = tot[2 * c];
     s.rz = tot[2 * c + 1];
+    s.beta = (s.rz / s.rho) * (s.alpha / s.omega);
     if (!finite_d(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; continue; }
     if (s.rr <= s.tol2) { s.done = 1; continue; }
     if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; continue; }
