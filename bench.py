@@ -123,11 +123,14 @@ class Clocks:
 
 
 # ---------------------------------------------------------- CPU baseline
-def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4):
+def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4, precond=None):
     """Batched form: n_cases independent lid cavities of Kuhn n^3 tetrahedra,
     n ~ U{8..48}, jitter 0.2h, random lid velocity (speed U(0.5, 1.5), direction
     in the lid plane), Re = 100 for unit speed, one disjoint-union mesh, F32 with
-    FP64 dots, per-case solver scalars, every step one CUDA graph."""
+    FP64 dots, per-case solver scalars, every step one CUDA graph.  Pressure:
+    CG with one multigrid V-cycle over the union per iteration (default) or
+    Jacobi."""
+    precond = D.PRECOND_AMG if precond is None else precond
     from paper_2603_15920_b300 import meshgen as mg
     rng = np.random.default_rng(seed)
     ns = rng.integers(8, 49, size=n_cases)
@@ -140,7 +143,7 @@ def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4):
         Ub_h[0, f], Ub_h[2, f] = sp * np.cos(th), sp * np.sin(th)
     o = D.piso_opts(NU, DT, 2, NONORTH,
                     solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
-                    solve_p=D.solve_opts(D.PCG, 1e-8, max_iter=20000, check_every=32),
+                    solve_p=D.solve_opts(D.PCG, 1e-8, max_iter=20000, check_every=32, precond=precond),
                     pref_cell=0)
     h = D.Piso(dm, D.F32, o)
     U = torch.zeros((3, dm.nc), device="cuda")
@@ -181,6 +184,8 @@ def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4):
             "cells": int(dm.nc), "cases": n_cases, "value": 1e3 / ms, "unit": "steps/s",
             "ms_per_step": ms, "cell_steps_per_s": dm.nc * 1e3 / ms, "steps": K, "warmup": W,
             "api": "difvm_piso_step_graph on a batched mesh (per-case Krylov scalars)",
+            "pressure_solver": ("CG + one multigrid V-cycle over the union per iteration"
+                                if precond == D.PRECOND_AMG else "CG + Jacobi"),
             "precision": "f32 fields, f64 dots, pressure tol 1e-8 per case",
             "status": int(gi["status"]), "pressure_iters_max_over_cases": gi["itp"][:2],
             "fwd_adj_ms_per_step": fa, "fwd_adjoint_over_fwd": fa / ms,
@@ -335,6 +340,10 @@ def run_ours(args):
     dm = D.Mesh(m, device=local)
     if args.face_ops_only:   # profiling runs of the face operators alone
         print(json.dumps(run_face_ops(D, torch, m, dm, measured_peaks()[0])), flush=True)
+        return 0
+    if args.batch_only:      # the batched 64-case form alone
+        print(json.dumps(run_batched(D, torch, precond=D.PRECOND_JACOBI if args.batch_jacobi else None)),
+              flush=True)
         return 0
     Ub_h = lid_bc(m)
     pref = int(dm.cell_new_of_old[0])
@@ -560,7 +569,13 @@ def run_ours(args):
                                             for k_, n_ in (("itU", 3), ("itp", 2))}}
 
     face_ops = run_face_ops(D, torch, m, dm, peak)
-    batched = None if args.no_batch else run_batched(D, torch)
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(D, torch)
+        bj = run_batched(D, torch, precond=D.PRECOND_JACOBI)
+        batched["jacobi_pressure"] = {k: bj[k] for k in ("value", "unit", "ms_per_step", "status",
+                                                         "pressure_iters_max_over_cases",
+                                                         "fwd_adjoint_over_fwd")}
 
     if rank != 0:
         return 0
@@ -626,6 +641,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-case line")
+    ap.add_argument("--batch-only", action="store_true", help="time only the batched 64-case form")
+    ap.add_argument("--batch-jacobi", action="store_true",
+                    help="with --batch-only: Jacobi instead of multigrid for the pressure CG")
     ap.add_argument("--mesh", type=int, default=N_KUHN, help="Kuhn hex grid size n (n^3 hexes)")
     ap.add_argument("--face-ops-only", action="store_true",
                     help="run only the face-operator timings (for profiling runs)")

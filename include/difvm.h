@@ -75,15 +75,19 @@ enum { DIFVM_DIV_UPWIND = 0, DIFVM_DIV_LINEAR = 1 };           /* Eq. upwind / c
 enum { DIFVM_WK_EXACT = 0, DIFVM_WK_FE = 1, DIFVM_WK_BE = 2 };  /* Eq. windkessel_discrete */
 enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
 /* DIFVM_PRECOND_AMG: one V-cycle of aggregation multigrid per CG iteration
- * (pairwise aggregation on c_f, two passes per level, down to <= 256 cells;
+ * (pairwise aggregation on c_f, two passes per level, down to <= 192 cells;
  * Galerkin coarse operators summed in a fixed order every solve; two Jacobi
  * sweeps with degree-2 Chebyshev weights on [1/2, 2] (0.56, 1.39) before and
  * after the coarse correction, which is
  * scaled by 1.9; dense inverse on the coarsest level).  A fixed SPD operator:
  * it changes the iteration count, not the solution.  The paper uses ILU, whose
  * triangular solves are sequential along the mesh ordering.  Single-RHS CG on
- * a symmetric matrix of a single mesh only (EINVAL otherwise); the hierarchy
- * is built on the host on first use and kept by the mesh. */
+ * a symmetric matrix only (EINVAL otherwise); the hierarchy is built on the
+ * host on first use and kept by the mesh.  On a batched mesh the hierarchy is
+ * built on the disjoint union (an aggregate never spans two cases, so each
+ * case gets its own V-cycle) and every case keeps its own CG scalars and
+ * stopping test; FP64 refinement is not available there (EINVAL), and EINVAL
+ * too if the union does not coarsen to <= 192 cells (e.g. more than 192 cases). */
 /* DIFVM_PRECOND_AMG_REUSE: as AMG, reusing the coefficient copy and multigrid
  * operators that the previous AMG solve with the same workspace built; the
  * caller guarantees the matrix is unchanged (e.g. the pressure matrix of the

@@ -342,10 +342,11 @@ difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
 }
 
 // ---------------------------------------------------------- workspace layout
-// [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials | ticket]
+// [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials |
+//  tickets | flags]; a batched mesh has one state and one ticket per case
 struct AmgLayout {
   size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], E[kAmgMaxLevels],
-      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, total;
+      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, flag, total;
 };
 
 static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
@@ -374,11 +375,13 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
   }
   const int nco = H->lev[H->nlev - 1].n;
   A.inv = take((size_t)nco * nco * sizeof(float));
-  A.st = take(4 * sizeof(KState));
-  // partials: one per block of the CG kernels and of the level-0 smoothing with r.z
-  const size_t nblk = amg_grid(m);
+  A.st = take((size_t)(m->seg ? m->ncases : 4) * sizeof(KState));
+  // partials: one per block of the CG kernels and of the level-0 smoothing with
+  // r.z (batched: one per block of the segmented CG kernels)
+  const size_t nblk = m->seg ? std::max(amg_grid(m), m->seg_nblk) : amg_grid(m);
   A.part = take(nblk * kMaxParts * sizeof(double));
-  A.ticket = take(256);
+  A.ticket = take((size_t)(m->seg ? m->ncases : 2) * sizeof(unsigned));
+  A.flag = take(4 * sizeof(int));
   A.total = o;
   return A;
 }
@@ -827,6 +830,9 @@ struct AmgRun {
   AmgLayout Ly;
   int G;
   int MW;
+  // batched solves: the V-cycle's early exit reads this flag (1 once every case
+  // has converged) and level 0 ends with a plain sweep (the per-case r.z follows)
+  const int* seg_done = nullptr;
   T* vec(int k) const { return (T*)(ws + Ly.vec[k]); }
   T* at(size_t off) const { return (T*)(ws + off); }
 };
@@ -874,7 +880,7 @@ template <typename T, int TPR>
 static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, const T* D, const T* rD,
                        const T* Lv, const T* r, T* y, T* u, T* rc, T* xc, T* out, const KWork& w, int first,
                        int down, cudaStream_t s) {
-  const int* done = &w.st[0].done;
+  const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
   const unsigned B = blocks_for((int64_t)L.n * TPR, kAB);
   if (down) {
     launch_pdl(k_amg_pre<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, done);
@@ -889,7 +895,7 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
     return;
   }
   launch_pdl(k_amg_post1<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, xc, u, done);
-  if (TPR == 1)
+  if (TPR == 1 && !R.seg_done)
     launch_pdl(k_amg_post2_dot<T>, R.G, kKB, s, L, R.A, rD, r, u, out, w, first);
   else
     launch_pdl(k_amg_post2<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, u, out, done);
@@ -902,7 +908,7 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
                        cudaStream_t s) {
   const AmgHier* H = R.H;
   const AmgLev& L = H->lev[l];
-  const int* done = &w.st[0].done;
+  const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
   const bool fine = l == 0;
   const T* D = fine ? R.A.D : R.at(R.Ly.D[l]);
   const T* rD = R.at(R.Ly.rD[l]);
@@ -910,7 +916,7 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   if (l == H->nlev - 1) {
     launch_pdl(k_amg_coarse<T>, 1, 1024, s, L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
     count_launch();
-    if (l == 0) {   // a single level: the CG's r.z reduction runs on its own
+    if (l == 0 && !R.seg_done) {   // a single level: the CG's r.z reduction runs on its own
       k_apcg_rz<T><<<R.G, kKB, 0, s>>>(L.n, r, out, w, first);
       count_launch();
     }
@@ -1063,9 +1069,217 @@ static difvm_status amg_solve_mw(difvm_mesh* m, const difvm_solve_opts* o, const
   return (difvm_status)hs.status;
 }
 
+// ------------------------------------------------- batched (segmented) CG
+// The multigrid-preconditioned CG on a disjoint union of cases.  Every case keeps
+// its own CG scalars, convergence flag and iteration count, with the per-case
+// reductions of the segmented Krylov solvers (seg_sum).  The hierarchy is built
+// on the union: an aggregate only joins cells linked by a face, so it never
+// spans two cases, every coarse operator is block diagonal by case and one
+// V-cycle over the union applies each case's own V-cycle.  flag[0] counts the
+// converged cases and flag[1] turns 1 once all have converged: the V-cycle
+// kernels then return at once.
+__device__ __forceinline__ void sg_case_done(int* flag, int ncases) {
+  if (atomicAdd(flag, 1) + 1 == ncases) atomicExch(flag + 1, 1);
+}
+
+// r = b - A x; bb, rr per case; convergence at the start
+template <typename T, int MW>
+__global__ void __launch_bounds__(kKB) k_sgapcg_init(Topo t, Mat<T> A, const T* b, const T* x, T* r,
+                                                      SWork w, int* flag, int ncases) {
+  const SegBlock B = seg_block(w);
+  DotAcc<T> bb, rr;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    T ax[1];
+    spmv_row<T, 1, MW>(t, A, i, x, ax, 1u);
+    const T bi = b[i], ri = bi - ax[0];
+    r[i] = ri;
+    bb.add(bi, bi);
+    rr.add(ri, ri);
+  }
+  double v[2] = {bb.get(), rr.get()}, tot[2];
+  if (!seg_sum<2>(w, B.k, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[B.k];
+  s.bb = tot[0];
+  s.rr = tot[1];
+  s.res0 = sqrt(s.rr);
+  s.tol2 = fmax(w.tol_rel * w.tol_rel * s.bb, w.tol_abs * w.tol_abs);
+  s.iters = 0;
+  s.status = DIFVM_OK;
+  s.zero_rhs = s.bb == 0.0;
+  s.done = s.zero_rhs || s.rr <= s.tol2;
+  if (!isfinite(s.rr)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
+  if (s.done) sg_case_done(flag, ncases);
+}
+
+// a case with b = 0 gets x = 0
+template <typename T>
+__global__ void k_sgapcg_zero(T* x, SWork w) {
+  const SegBlock B = seg_block(w);
+  if (!w.st[B.k].zero_rhs) return;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) x[i] = T(0);
+}
+
+// r.z of each active case and its beta (first: beta = 0)
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_sgapcg_rz(const T* r, const T* z, SWork w, int first) {
+  pdl_chain();
+  const SegBlock B = seg_block(w);
+  if (w.st[B.k].done) return;
+  DotAcc<T> rz;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) rz.add(r[i], z[i]);
+  double v[1] = {rz.get()}, tot[1];
+  if (!seg_sum<1>(w, B.k, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[B.k];
+  s.beta = first ? 0.0 : tot[0] / s.rz;
+  s.rz = tot[0];
+}
+
+// p = z + beta p in each active case (first: p = z)
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_sgapcg_p(const T* z, T* p, SWork w, int first) {
+  pdl_chain();
+  const SegBlock B = seg_block(w);
+  if (w.st[B.k].done) return;
+  const T be = (T)w.st[B.k].beta;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) p[i] = first ? z[i] : z[i] + be * p[i];
+}
+
+// q = A p in each active case; alpha = rz / (p.q)
+template <typename T, int MW>
+__global__ void __launch_bounds__(kKB) k_sgapcg_spmv(Topo t, Mat<T> A, const T* p, T* q, SWork w) {
+  pdl_chain();
+  const SegBlock B = seg_block(w);
+  if (w.st[B.k].done) return;
+  DotAcc<T> pq;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    T y[1];
+    spmv_row<T, 1, MW>(t, A, i, p, y, 1u);
+    q[i] = y[0];
+    pq.add(p[i], y[0]);
+  }
+  double v[1] = {pq.get()}, tot[1];
+  if (!seg_sum<1>(w, B.k, v, tot) || threadIdx.x != 0) return;
+  w.st[B.k].alpha = w.st[B.k].rz / tot[0];
+}
+
+// x += alpha p; r -= alpha q; rr and the convergence test of each active case
+template <typename T>
+__global__ void __launch_bounds__(kKB) k_sgapcg_update(const T* p, const T* q, T* x, T* r, SWork w,
+                                                        int* flag, int ncases) {
+  pdl_chain();
+  const SegBlock B = seg_block(w);
+  if (w.st[B.k].done) return;
+  const T al = (T)w.st[B.k].alpha;
+  DotAcc<T> rr;
+  for (int i = B.r0 + threadIdx.x; i < B.r1; i += blockDim.x) {
+    x[i] += al * p[i];
+    const T ri = r[i] - al * q[i];
+    r[i] = ri;
+    rr.add(ri, ri);
+  }
+  double v[1] = {rr.get()}, tot[1];
+  if (!seg_sum<1>(w, B.k, v, tot) || threadIdx.x != 0) return;
+  KState& s = w.st[B.k];
+  s.iters += 1;
+  s.rr = tot[0];
+  if (!isfinite(s.rr) || !isfinite(s.alpha)) { s.done = 1; s.status = DIFVM_ENONFINITE; }
+  else if (s.rr <= s.tol2) s.done = 1;
+  else if (s.iters >= w.maxit) { s.done = 1; s.status = DIFVM_ENOTCONV; }
+  if (s.done) sg_case_done(flag, ncases);
+}
+
+__global__ void k_sgapcg_info(int n, const KState* st, difvm_solve_info* info) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const KState& s = st[c];
+  difvm_solve_info o;
+  o.iters = s.iters;
+  o.refinements = 0;
+  o.status = s.status;
+  o.pad = 0;
+  o.res0 = s.res0;
+  o.res = sqrt(s.rr);
+  o.bnorm = sqrt(s.bb);
+  info[c] = o;
+}
+
+template <typename T, int MW>
+static difvm_status amg_solve_seg(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo,
+                                  const T* b, T* x, void* ws, size_t wsbytes, difvm_solve_info* info,
+                                  cudaStream_t st) {
+  AmgRun<T> R;
+  DIFVM_TRY(amg_prepare<T>(m, D, Lo, ws, wsbytes, R, st, o->precond == DIFVM_PRECOND_AMG_REUSE));
+  const int nk = m->ncases, G = m->seg_nblk;
+  SWork w;
+  w.st = (KState*)(R.ws + R.Ly.st);
+  w.part = (double*)(R.ws + R.Ly.part);
+  w.ticket = (unsigned*)(R.ws + R.Ly.ticket);
+  w.bcase = m->seg_case;
+  w.cb0 = m->seg_cb0;
+  w.cs = m->seg_cs;
+  w.maxit = o->max_iter > 0 ? o->max_iter : 1000;
+  w.tol_rel = o->tol_rel;
+  w.tol_abs = o->tol_abs;
+  int* flag = (int*)(R.ws + R.Ly.flag);   // converged cases, all converged, loop counter, poll
+  R.seg_done = flag + 1;
+  KWork kw = amg_work_t(R, 0, w.maxit, w.tol_rel, w.tol_abs);   // (unused by a batched V-cycle)
+  DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned) * nk, st));
+  DIFVM_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int), st));
+  T *r = R.vec(0), *p = R.vec(1), *q = R.vec(2), *z = R.vec(3);
+  k_sgapcg_init<T, MW><<<G, kKB, 0, st>>>(R.t, R.A, b, x, r, w, flag, nk);
+  k_sgapcg_zero<T><<<G, kKB, 0, st>>>(x, w);
+  DIFVM_TRY(check_launch("sgapcg_init"));
+  amg_vcycle(R, 0, r, z, kw, 1, st);
+  launch_pdl(k_sgapcg_rz<T>, G, kKB, st, (const T*)r, (const T*)z, w, 1);
+  launch_pdl(k_sgapcg_p<T>, G, kKB, st, (const T*)z, p, w, 1);
+  DIFVM_TRY(check_launch("sgapcg_first"));
+  auto iter = [&](cudaStream_t s) {
+    launch_pdl(k_sgapcg_spmv<T, MW>, G, kKB, s, R.t, R.A, (const T*)p, q, w);
+    launch_pdl(k_sgapcg_update<T>, G, kKB, s, (const T*)p, (const T*)q, x, r, w, flag, nk);
+    amg_vcycle(R, 0, r, z, kw, 0, s);
+    launch_pdl(k_sgapcg_rz<T>, G, kKB, s, (const T*)r, (const T*)z, w, 0);
+    launch_pdl(k_sgapcg_p<T>, G, kKB, s, (const T*)z, p, w, 0);
+    for (int k = 0; k < 4; ++k) count_launch();
+  };
+  if (stream_capturing(st)) {
+    WhileLoop Lw;
+    DIFVM_TRY(while_open(st, Lw));
+    iter(Lw.side);
+    // continue while flag[1] == 0, at most maxit + 2 passes
+    k_loop_cond<<<1, 32, 0, Lw.side>>>(flag + 1, 0, 1, flag + 2, w.maxit + 2, Lw.h);
+    DIFVM_TRY(check_launch("loop_cond"));
+    DIFVM_TRY(while_close(Lw));
+  } else {
+    const int chunk = o->check_every > 0 ? o->check_every : 8;
+    int all = 0;
+    for (int it = 0; it < w.maxit && !all; it += chunk) {
+      for (int k = 0; k < chunk; ++k) iter(st);
+      DIFVM_TRY(check_error("sgapcg_iter"));
+      DIFVM_CUDA(cudaMemcpyAsync(&all, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+      DIFVM_CUDA(cudaStreamSynchronize(st));
+    }
+  }
+  if (info) {
+    k_sgapcg_info<<<blocks_for(nk, 128), 128, 0, st>>>(nk, w.st, info);
+    DIFVM_TRY(check_launch("sgapcg_info"));
+  }
+  if (stream_capturing(st)) return DIFVM_OK;   // outcome in info_dev
+  std::vector<KState> hs(nk);
+  DIFVM_CUDA(cudaMemcpyAsync(hs.data(), w.st, sizeof(KState) * nk, cudaMemcpyDeviceToHost, st));
+  DIFVM_CUDA(cudaStreamSynchronize(st));
+  int worst = DIFVM_OK;
+  for (const KState& k : hs) worst = std::max(worst, k.status);
+  return (difvm_status)worst;
+}
+
 template <typename T>
 difvm_status amg_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,
                        T* x, void* ws, size_t wsbytes, difvm_solve_info* info, cudaStream_t st) {
+  if (m->seg) {
+    if (m->ell_wmax <= 4) return amg_solve_seg<T, 4>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
+    if (m->ell_wmax <= 8) return amg_solve_seg<T, 8>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
+    return amg_solve_seg<T, 0>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
+  }
   if (m->ell_wmax <= 4) return amg_solve_mw<T, 4>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
   if (m->ell_wmax <= 8) return amg_solve_mw<T, 8>(m, o, D, Lo, b, x, ws, wsbytes, info, st);
   return amg_solve_mw<T, 0>(m, o, D, Lo, b, x, ws, wsbytes, info, st);

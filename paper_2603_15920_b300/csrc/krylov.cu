@@ -921,78 +921,7 @@ __global__ void k_solve_coeff_bwd(Topo t, const T* x, const T* bbar, T* Dbar, T*
 }
 
 // ====================================================== segmented (batched)
-// The same PCG / BiCGStab on a disjoint union of cases: every case keeps its
-// own scalars (alpha, beta, rho, omega, ...), convergence flag and iteration
-// count, as if it were solved alone.  Each solver block works inside one case
-// (a chunk of kSegRows of its rows); each case has its own ticket, and the
-// last of the case's blocks to arrive reduces that case's partials in block
-// order.  A case's block partition depends only on its own size, so a case
-// gives bitwise the same result alone as inside any batch.
-struct SWork {
-  KState* st;          // [ncases * NC]
-  double* part;        // [nblk * kMaxParts]
-  unsigned* ticket;    // [ncases]
-  const int* bcase;    // [nblk]
-  const int* cb0;      // [ncases + 1]
-  const int* cs;       // [ncases + 1]
-  int maxit;
-  double tol_rel, tol_abs;
-};
-
-struct SegBlock {
-  int k, r0, r1;
-};
-__device__ __forceinline__ SegBlock seg_block(const SWork& w) {
-  SegBlock b;
-  b.k = __ldg(w.bcase + blockIdx.x);
-  b.r0 = __ldg(w.cs + b.k) + (blockIdx.x - __ldg(w.cb0 + b.k)) * kSegRows;
-  b.r1 = min(__ldg(w.cs + b.k + 1), b.r0 + kSegRows);
-  return b;
-}
-
-template <int NC>
-__device__ __forceinline__ unsigned seg_active(const SWork& w, int k) {
-  unsigned m = 0;
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-    if (!w.st[k * NC + c].done) m |= 1u << c;
-  return m;
-}
-
-// Store this block's partials; true in the last block of case k, with the
-// case totals in `tot` (all threads of that block).
-template <int K>
-__device__ __forceinline__ bool seg_sum(const SWork& w, int k, double (&v)[K], double (&tot)[K]) {
-  block_sum<K>(v);
-  __shared__ int amlast;
-  __shared__ double res[K];
-  const int b0 = __ldg(w.cb0 + k), nb = __ldg(w.cb0 + k + 1) - b0;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) w.part[blockIdx.x * kMaxParts + q] = v[q];
-    __threadfence();
-    amlast = atomicAdd(w.ticket + k, 1u) == (unsigned)(nb - 1);
-  }
-  __syncthreads();
-  if (!amlast) return false;
-  __threadfence();
-  double a[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) a[q] = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
-#pragma unroll
-    for (int q = 0; q < K; ++q) a[q] += __ldcg(w.part + (b0 + b) * kMaxParts + q);
-  block_sum<K>(a);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) res[q] = a[q];
-    w.ticket[k] = 0u;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < K; ++q) tot[q] = res[q];
-  return true;
-}
+// (SWork, seg_block and seg_sum: krylov_common.cuh)
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(kKB) k_sg_pcg_init(Topo t, Mat<T> A, int jacobi, const T* b, T* x,
@@ -1534,9 +1463,9 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
                             const void* U, const void* b, void* x, int ncomp, void* ws,
                             size_t wsbytes, difvm_solve_info* info, cudaStream_t st) {
   if (o->precond == DIFVM_PRECOND_AMG || o->precond == DIFVM_PRECOND_AMG_REUSE) {
-    if (o->method != DIFVM_PCG || ncomp != 1 || U || m->seg)
+    if (o->method != DIFVM_PCG || ncomp != 1 || U)
       return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves single-RHS CG on a "
-                                     "symmetric matrix of a single (not batched) mesh");
+                                     "symmetric matrix");
     return amg_solve<T>(m, o, (const T*)D, (const T*)L, (const T*)b, (T*)x, ws, wsbytes, info, st);
   }
   if (o->precond == DIFVM_PRECOND_DIC) {
@@ -1616,7 +1545,7 @@ extern "C" size_t difvm_krylov_opts_workspace_bytes(difvm_mesh_t m, difvm_prec p
   if (!m || !o || ncomp < 1 || ncomp > 3) return 0;
   const bool refine = prec == DIFVM_F32 && o->refine_max > 0;
   if (o->precond == DIFVM_PRECOND_AMG || o->precond == DIFVM_PRECOND_AMG_REUSE) {
-    if (o->method != DIFVM_PCG || ncomp != 1 || m->seg) return 0;
+    if (o->method != DIFVM_PCG || ncomp != 1 || (m->seg && refine)) return 0;
     return amg_workspace_bytes(m, refine ? 4 : (prec == DIFVM_F64 ? 8 : 4));
   }
   if (o->precond == DIFVM_PRECOND_DIC) {

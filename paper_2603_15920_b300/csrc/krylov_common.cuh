@@ -331,4 +331,78 @@ __global__ void __launch_bounds__(kKB) k_pcg_spmv(Topo t, Mat<T> A, const T* p, 
     if (act >> c & 1) w.st[c].alpha = w.st[c].rz / tot[c];
 }
 
+// ---------------------------------------------------- segmented (batched)
+// The same PCG / BiCGStab on a disjoint union of cases: every case keeps its
+// own scalars (alpha, beta, rho, omega, ...), convergence flag and iteration
+// count, as if it were solved alone.  Each solver block works inside one case
+// (a chunk of kSegRows of its rows); each case has its own ticket, and the
+// last of the case's blocks to arrive reduces that case's partials in block
+// order.  A case's block partition depends only on its own size, so a case
+// gives bitwise the same result alone as inside any batch.
+struct SWork {
+  KState* st;          // [ncases * NC]
+  double* part;        // [nblk * kMaxParts]
+  unsigned* ticket;    // [ncases]
+  const int* bcase;    // [nblk]
+  const int* cb0;      // [ncases + 1]
+  const int* cs;       // [ncases + 1]
+  int maxit;
+  double tol_rel, tol_abs;
+};
+
+struct SegBlock {
+  int k, r0, r1;
+};
+__device__ __forceinline__ SegBlock seg_block(const SWork& w) {
+  SegBlock b;
+  b.k = __ldg(w.bcase + blockIdx.x);
+  b.r0 = __ldg(w.cs + b.k) + (blockIdx.x - __ldg(w.cb0 + b.k)) * kSegRows;
+  b.r1 = min(__ldg(w.cs + b.k + 1), b.r0 + kSegRows);
+  return b;
+}
+
+template <int NC>
+__device__ __forceinline__ unsigned seg_active(const SWork& w, int k) {
+  unsigned m = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (!w.st[k * NC + c].done) m |= 1u << c;
+  return m;
+}
+
+// Store this block's partials; true in the last block of case k, with the
+// case totals in `tot` (all threads of that block).
+template <int K>
+__device__ __forceinline__ bool seg_sum(const SWork& w, int k, double (&v)[K], double (&tot)[K]) {
+  block_sum<K>(v);
+  __shared__ int amlast;
+  __shared__ double res[K];
+  const int b0 = __ldg(w.cb0 + k), nb = __ldg(w.cb0 + k + 1) - b0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) w.part[blockIdx.x * kMaxParts + q] = v[q];
+    __threadfence();
+    amlast = atomicAdd(w.ticket + k, 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+  double a[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) a[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] += __ldcg(w.part + (b0 + b) * kMaxParts + q);
+  block_sum<K>(a);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) res[q] = a[q];
+    w.ticket[k] = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) tot[q] = res[q];
+  return true;
+}
+
 }  // namespace difvm

@@ -1396,8 +1396,8 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     return set_error(DIFVM_EINVAL, "bad pressure solver");
   if (amg_opts(o->solve_U))
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves the pressure CG only");
-  if (amg_opts(o->solve_p) && (o->solve_p.method != DIFVM_PCG || m->seg))
-    return set_error(DIFVM_EINVAL, "the multigrid preconditioner needs CG on a single (not batched) mesh");
+  if (amg_opts(o->solve_p) && o->solve_p.method != DIFVM_PCG)
+    return set_error(DIFVM_EINVAL, "the multigrid preconditioner needs CG");
   if (o->solve_U.precond == DIFVM_PRECOND_DIC)
     return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner serves the pressure CG only");
   if (o->solve_p.precond == DIFVM_PRECOND_DIC &&

@@ -202,10 +202,15 @@ def test_graph_step_with_amg_equals_plain(prec, refine):
         assert np.array_equal(a, b)
 
 
-def test_amg_rejected_on_batched_meshes():
+def test_batched_multigrid_limits():
+    """On a batched mesh the multigrid CG is accepted (per-case scalars; parity in
+    the batched tests) but its FP64-refinement form and BiCGStab are not."""
     ms = [mg.kuhn_cube(3, 0.2, 1), mg.kuhn_cube(4, 0.2, 2)]
     u, cs = mg.batch(ms)
     dm = D.Mesh(u, case_cell_start=cs)
-    o = D.piso_opts(0.02, 0.05, 2, 3, solve_p=D.solve_opts(D.PCG, 1e-10, precond=D.PRECOND_AMG))
-    with pytest.raises(D.DifvmError):
-        D.Piso(dm, D.F64, o)
+    D.Piso(dm, D.F64, D.piso_opts(0.02, 0.05, 2, 3,
+                                  solve_p=D.solve_opts(D.PCG, 1e-10, precond=D.PRECOND_AMG)))
+    for prec, sp in ((D.F32, D.solve_opts(D.PCG, 1e-10, precond=D.PRECOND_AMG, refine_max=20)),
+                     (D.F64, D.solve_opts(D.BICGSTAB, 1e-10, precond=D.PRECOND_AMG))):
+        with pytest.raises(D.DifvmError):
+            D.Piso(dm, prec, D.piso_opts(0.02, 0.05, 2, 3, solve_p=sp))

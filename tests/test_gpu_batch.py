@@ -53,14 +53,15 @@ def test_batched_numbering_keeps_cases_contiguous(batch):
         assert np.array_equal(got, dm.cell_new_of_old)
 
 
-def _spd(m, seed):
-    """Pressure-like SPD LDU matrix of one case: D = sum c_f + shift, L = -c_f."""
+def _spd(m, seed, diag_frac=None):
+    """Pressure-like SPD LDU matrix of one case: D = sum c_f + shift, L = -c_f
+    (shift 0.01 V, or diag_frac * sum c_f: condition number ~2 / diag_frac)."""
     om = O.OMesh.from_mesh(m)
     w, c, k = O.face_coeffs(om)
     rng = np.random.default_rng(seed)
     a = c[:m.n_internal] * rng.uniform(0.5, 2.0, m.n_internal)
-    Dg = np.bincount(m.owner[:m.n_internal], a, m.n_cells) + \
-        np.bincount(m.neighbour, a, m.n_cells) + 0.01 * m.V
+    rs = np.bincount(m.owner[:m.n_internal], a, m.n_cells) + np.bincount(m.neighbour, a, m.n_cells)
+    Dg = rs + (0.01 * m.V if diag_frac is None else diag_frac * rs)
     return om, Dg, -a
 
 
@@ -193,6 +194,101 @@ def test_batched_piso_step_and_adjoint(batch):
         for tp in reversed(tapes):
             assert h.step_bwd(tp, s_[3], None, ub, pb_, fb, None, None, ubb, nb_)[0] == D.OK
         assert np.array_equal(dm.from_cells(host(ub)), Ubar_u[:, cs[k]:cs[k + 1]])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batched_multigrid_cg_matches_oracle(batch, prec):
+    """Multigrid-preconditioned CG on the union: each case converges on its own
+    (its own CG scalars and stopping test) to the oracle's solution of that case
+    alone; a case with b = 0 returns x = 0 after no iteration; the iteration
+    counts stay far below Jacobi's."""
+    ms, u, cs, dmu, dms = batch
+    rng = np.random.default_rng(5)
+    # FP32: a matrix of condition ~100, so that the FP32 floor of the true
+    # residual (u32 cond(A) ~ 6e-6) sits near the 1e-6 stopping tolerance
+    mats = [_spd(m, 20 + k, None if prec == "f64" else 0.02) for k, m in enumerate(ms)]
+    bs = [rng.normal(size=m.n_cells) for m in ms]
+    bs[1][:] = 0.0                        # the middle case: zero right-hand side
+    Du = np.concatenate([mt[1] for mt in mats])
+    Lu = _to_union_faces(dmu, [mt[2] for mt in mats], u, cs, ms)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    tol = 1e-12 if prec == "f64" else 1e-6
+    x = torch.full((dmu.nc,), 0.5, dtype=dt, device="cuda")   # nonzero guess
+    st, info = D.difvm_krylov_solve(dmu, cuda(dmu.to_cells(Du), dt), cuda(Lu, dt), None,
+                                    cuda(dmu.to_cells(np.concatenate(bs)), dt), x,
+                                    method=D.PCG, precond=D.PRECOND_AMG, tol_rel=tol, max_iter=500)
+    assert st == D.OK and len(info) == len(ms)
+    _, jac = D.difvm_krylov_solve(dmu, cuda(dmu.to_cells(Du)), cuda(Lu), None,
+                                  cuda(dmu.to_cells(np.concatenate(bs))),
+                                  torch.zeros(dmu.nc, dtype=torch.float64, device="cuda"),
+                                  method=D.PCG, tol_rel=tol, max_iter=5000)
+    xu = dmu.from_cells(host(x))
+    for k, m in enumerate(ms):
+        om, Dg, Lg = mats[k]
+        xc = xu[cs[k]:cs[k + 1]]
+        if k == 1:
+            assert info[k]["iters"] == 0 and np.all(xc == 0.0)
+            continue
+        assert info[k]["status"] == D.OK and 0 < info[k]["iters"] <= 40
+        assert info[k]["iters"] * 2 < jac[k]["iters"]
+        r = bs[k] - O.ldu_apply(om, Dg, Lg, None, xc[None])[0]
+        ref, _ = O.pcg(om, Dg, Lg, None, bs[k], tol_rel=1e-13)
+        if prec == "f64":
+            assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(bs[k])
+            assert nrel(xc, ref) < 1e-8
+        else:
+            # FP32 vectors and matrix: the recursive residual reaches 1e-6, the
+            # true one stays within a few times the floor u32 cond(A); the
+            # solution error within cond(A) times that
+            assert np.linalg.norm(r) <= 5e-5 * np.linalg.norm(bs[k])
+            assert nrel(xc, ref) < 5e-3
+
+
+def test_batched_piso_step_multigrid_pressure(batch):
+    """The batched PISO step with the multigrid pressure CG: each case against
+    the oracle (which solves its pressure with Jacobi CG to the same tight
+    tolerance) at 1e-9, over two steps; then the adjoint of the second step
+    (its pressure solves transposed through the same multigrid CG) against the
+    oracle's adjoint of that step, case by case."""
+    ms, u, cs, dmu, dms = batch
+    lids = [1.0, 0.7, 1.3]
+    Ubs = [_cavity_state(m, l) for m, l in zip(ms, lids)]
+    pref = 0
+    o = D.piso_opts(0.02, 0.05, 2, 3,
+                    solve_U=D.solve_opts(D.BICGSTAB, 1e-13, max_iter=2000),
+                    solve_p=D.solve_opts(D.PCG, 1e-13, max_iter=500, precond=D.PRECOND_AMG),
+                    pref_cell=pref, nonorth_limit=0.5)
+    hu = D.Piso(dmu, D.F64, o)
+    st_u = [torch.zeros((3, dmu.nc), dtype=torch.float64, device="cuda"),
+            torch.zeros(dmu.nc, dtype=torch.float64, device="cuda"), None,
+            cuda(dmu.to_bnd(np.concatenate(Ubs, axis=1))),
+            torch.zeros(dmu.nb, dtype=torch.float64, device="cuda")]
+    st_u[2] = D.difvm_flux_from_U(dmu, st_u[0], st_u[3])
+    s, info = hu.step(*st_u)
+    assert s == D.OK, D.decode_piso_info(info)
+    tape = hu.new_tape("cuda")
+    s, info = hu.step_record(*st_u, tape)
+    assert s == D.OK, D.decode_piso_info(info)
+    Ubar = (cuda(dmu.to_cells(u.V)) * st_u[0]).contiguous()     # d(KE)/dU of the step's output
+    pbar, phibar = torch.zeros_like(st_u[1]), torch.zeros_like(st_u[2])
+    Ubbar = torch.zeros_like(st_u[3])
+    nubar = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert hu.step_bwd(tape, st_u[3], None, Ubar, pbar, phibar, None, None, Ubbar, nubar)[0] == D.OK
+    Ubar_u = dmu.from_cells(host(Ubar))
+    for k, (m, dm) in enumerate(zip(ms, dms)):
+        om = O.OMesh.from_mesh(m)
+        pin_old = int(np.where(dm.cell_new_of_old == pref)[0][0])
+        kw = dict(nu=0.02, dt=0.05, tolU=1e-13, tolp=1e-13, pref_cell=pin_old, psi=0.5, nonorth=3)
+        U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+        phi = O.flux_from_U(om, U, Ubs[k])
+        U1, p1, phi1, pb1, _, _ = O.piso_step(om, U, p, phi, Ubs[k], pb, **kw)
+        U2, p2, _, _, _, _ = O.piso_step(om, U1, p1, phi1, Ubs[k], pb1, **kw)
+        assert nrel(dmu.from_cells(host(st_u[0]))[:, cs[k]:cs[k + 1]], U2) < 1e-9
+        assert nrel(dmu.from_cells(host(st_u[1]))[cs[k]:cs[k + 1]], p2) < 1e-9
+        ref = O.piso_step_bwd(om, U1, p1, phi1, Ubs[k], pb1, m.V * U2, np.zeros(m.n_cells),
+                              np.zeros(m.n_faces), **kw)
+        assert ref["status"] == 0
+        assert nrel(Ubar_u[:, cs[k]:cs[k + 1]], ref["U"]) < 1e-8
 
 
 def test_refinement_is_rejected_on_batched_meshes(batch):
