@@ -681,9 +681,11 @@ __global__ void __launch_bounds__(kAB) k_amg_post2(AmgLev L, Mat<T> A, const T* 
 }
 
 // the same sweep on level 0 of a CG iteration (grid-stride), also forming
-// r.v: the last block sets beta (first = 1: rz only)
+// r.v: the last block sets beta (first = 1: rz only).  FP32: four blocks per SM
+// (32 registers; 40 without the bound) so that the grid of 4 x SMs blocks runs
+// in one wave.
 template <typename T>
-__global__ void __launch_bounds__(kKB) k_amg_post2_dot(AmgLev L, Mat<T> A, const T* rD, const T* r, const T* u,
+__global__ void __launch_bounds__(kKB, sizeof(T) == 4 ? 4 : 0) k_amg_post2_dot(AmgLev L, Mat<T> A, const T* rD, const T* r, const T* u,
                                                        T* v, KWork w, int first) {
   pdl_chain();
   if (w.st[0].done) return;

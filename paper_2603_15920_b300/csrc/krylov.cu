@@ -438,6 +438,25 @@ static int grid_for(const difvm_mesh* m) {
 
 static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Grid of a grid-stride solver kernel: the blocks that are resident on the SMs
+// at once (1-4 per SM, by the kernel's register use; 40 or more registers fit
+// fewer than four 512-thread blocks), so that it runs in one wave and its
+// reduction finishes once; never more than the rows need or than grid_for(m),
+// for which the partials are sized.
+template <typename K>
+static int wave_grid(K kernel, const difvm_mesh* m) {
+  static int per = 0;   // per kernel instantiation
+  if (per == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kKB, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      b = 4;
+    }
+    per = std::max(1, std::min(b, 4));
+  }
+  return std::max(1, std::min(grid_for(m), per * m->num_sms));
+}
+
 // [vectors | ELL values | solver states | block partials | ticket]
 static WsLayout layout(const difvm_mesh* m, size_t elt, int method, int ncomp) {
   WsLayout L;
@@ -559,19 +578,21 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
   } else if (o->method == DIFVM_BICGSTAB) {
     T *r = vec(0), *rh = vec(NC), *p = vec(2 * NC), *v = vec(3 * NC), *s_ = vec(4 * NC),
       *tv = vec(5 * NC), *y = vec(6 * NC), *z = vec(7 * NC);
-    k_bicg_init<T, NC><<<G, kKB, 0, st>>>(t, A, jac, b, x, r, rh, p, v, rD, w);
+    const int Gi = wave_grid(k_bicg_init<T, NC>, m), G1 = wave_grid(k_bicg_spmv1<T, NC, MW>, m),
+              G2 = wave_grid(k_bicg_spmv2<T, NC, MW>, m), Gu = wave_grid(k_bicg_update<T, NC>, m);
+    k_bicg_init<T, NC><<<Gi, kKB, 0, st>>>(t, A, jac, b, x, r, rh, p, v, rD, w);
     DIFVM_TRY(check_launch("bicg_init"));
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
     DIFVM_TRY(run([&](cudaStream_t s) {
       k_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, w);
       k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, p, rD, y, w);
-      k_bicg_spmv1<T, NC, MW><<<G, kKB, 0, s>>>(t, A, rh, y, v, w);
+      k_bicg_spmv1<T, NC, MW><<<G1, kKB, 0, s>>>(t, A, rh, y, v, w);
       k_bicg_s<T, NC><<<G, kKB, 0, s>>>(nc, r, v, s_, w);
       k_bicg_sfinish<T, NC><<<G, kKB, 0, s>>>(nc, y, x, w);
       k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, s_, rD, z, w);
-      k_bicg_spmv2<T, NC, MW><<<G, kKB, 0, s>>>(t, A, z, s_, tv, w);
-      k_bicg_update<T, NC><<<G, kKB, 0, s>>>(nc, y, z, s_, tv, rh, x, r, w);
+      k_bicg_spmv2<T, NC, MW><<<G2, kKB, 0, s>>>(t, A, z, s_, tv, w);
+      k_bicg_update<T, NC><<<Gu, kKB, 0, s>>>(nc, y, z, s_, tv, rh, x, r, w);
       for (int q = 0; q < 8; ++q) count_launch();
     }));
   } else {
