@@ -46,6 +46,13 @@ METRIC = "PISO steps/s & fwd+adjoint/fwd time at 1.6M-cell tet mesh; face-op HBM
 WORKLOAD = "kuhn64_cavity_re100"
 N_KUHN, JITTER, SEED = 64, 0.2, 0
 NU, DT = 0.01, 0.002
+# the batched cavities (64 cases, n ~ U{8..48}) keep these whatever --mesh is
+BATCH_JITTER, BATCH_NU = JITTER, NU
+# --mesh 128: the large mixed-precision cavity (12.6M cells, jitter 0.15h, Re 400).
+# At jitter 0.2h and Re 100 the 128^3 cavity diverges within a few steps in FP32 and
+# FP64 alike (nu dt / h^2 = 0.33 against 0.08 at 64^3: the explicit non-orthogonal
+# momentum correction is unstable there); at Re 400 nu dt / h^2 is 0.08 again.
+LARGE = {128: ("kuhn128_cavity_re400", 0.15, 0.0025)}
 # Explicit over-relaxed non-orthogonal correction in the momentum equation only
 # (bit 0); the lagged correction of the pressure Laplacian (bit 1) diverges on
 # these jittered tetrahedra for every setting tried.  dt = 0.002: with two
@@ -134,14 +141,14 @@ def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4, precond=None):
     from paper_2603_15920_b300 import meshgen as mg
     rng = np.random.default_rng(seed)
     ns = rng.integers(8, 49, size=n_cases)
-    u, cs = mg.batch([mg.kuhn_cube(int(n), JITTER, 100 + k) for k, n in enumerate(ns)])
+    u, cs = mg.batch([mg.kuhn_cube(int(n), BATCH_JITTER, 100 + k) for k, n in enumerate(ns)])
     dm = D.Mesh(u, case_cell_start=cs)
     Ub_h = np.zeros((3, u.n_boundary))
     for k in range(n_cases):
         sp, th = rng.uniform(0.5, 1.5), rng.uniform(0.0, 2.0 * np.pi)
         f = u.patch_faces(f"c{k}/y1") - u.n_internal
         Ub_h[0, f], Ub_h[2, f] = sp * np.cos(th), sp * np.sin(th)
-    o = D.piso_opts(NU, DT, 2, NONORTH,
+    o = D.piso_opts(BATCH_NU, DT, 2, NONORTH,
                     solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
                     solve_p=D.solve_opts(D.PCG, 1e-8, max_iter=20000, check_every=32, precond=precond),
                     pref_cell=0)
@@ -179,7 +186,7 @@ def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4, precond=None):
     a1.record()
     torch.cuda.synchronize()
     fa = a0.elapsed_time(a1) / K
-    return {"workload": f"{n_cases} Kuhn lid cavities, n ~ U{{8..48}}, jitter {JITTER}, "
+    return {"workload": f"{n_cases} Kuhn lid cavities, n ~ U{{8..48}}, jitter {BATCH_JITTER}, "
                         f"random lid velocity, seed {seed}",
             "cells": int(dm.nc), "cases": n_cases, "value": 1e3 / ms, "unit": "steps/s",
             "ms_per_step": ms, "cell_steps_per_s": dm.nc * 1e3 / ms, "steps": K, "warmup": W,
@@ -324,6 +331,9 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2603_15920_b300 import difvm as D
+    global WORKLOAD, JITTER, NU
+    if args.mesh in LARGE:
+        WORKLOAD, JITTER, NU = LARGE[args.mesh]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -450,7 +460,7 @@ def run_ours(args):
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if spmv_n else None
     traffic = None
     tf_path = os.path.join(ROOT, "profiles", "traffic_amg_resid_f32_kuhn64.json")
-    if os.path.exists(tf_path):
+    if os.path.exists(tf_path) and args.mesh == N_KUHN:   # captured on the 64^3 mesh
         try:
             traffic = json.load(open(tf_path)).get("dram_bytes_per_launch")
         except Exception:
@@ -466,11 +476,15 @@ def run_ours(args):
     jacobi = {"value": 1e3 * K / rj["ms"], "unit": "steps/s", "ms_per_step": rj["ms"] / K,
               "status": int(rj["status"]), "pressure_iters_last_step": rj["info"]["itp"][:2],
               "api": "difvm_piso_step_graph, pressure CG with Jacobi preconditioning"}
-    # the paper's preconditioner (diagonal incomplete Cholesky, level-scheduled): FP64, one step
-    rd = timed(D.F64, 1, 1, graph=True, precond=D.PRECOND_DIC)
-    dic = {"value": 1e3 / rd["ms"], "unit": "steps/s", "ms_per_step": rd["ms"], "steps": 1,
-           "status": int(rd["status"]), "pressure_iters_last_step": rd["info"]["itp"][:2],
-           "api": "difvm_piso_step_graph, FP64, pressure CG with DIC (one launch per dependency level)"}
+    # the paper's preconditioner (diagonal incomplete Cholesky, level-scheduled): FP64, one
+    # step (its sweeps advance one dependency level per launch: minutes per step above 64^3)
+    if args.mesh <= N_KUHN:
+        rd = timed(D.F64, 1, 1, graph=True, precond=D.PRECOND_DIC)
+        dic = {"value": 1e3 / rd["ms"], "unit": "steps/s", "ms_per_step": rd["ms"], "steps": 1,
+               "status": int(rd["status"]), "pressure_iters_last_step": rd["info"]["itp"][:2],
+               "api": "difvm_piso_step_graph, FP64, pressure CG with DIC (one launch per dependency level)"}
+    else:
+        dic = {"skipped": f"not timed above {N_KUHN}^3 (one launch per dependency level)"}
     rs = timed(D.F32, W, K, graph=True, conv=D.CONV_SOU)
     sou = {"value": 1e3 * K / rs["ms"], "unit": "steps/s", "ms_per_step": rs["ms"] / K,
            "status": int(rs["status"]), "pressure_iters_last_step": rs["info"]["itp"][:2],
@@ -487,6 +501,20 @@ def run_ours(args):
     # plain FP64 form, same workload (fewer steps: it is the slow form)
     r64 = timed(D.F64, 3, max(2, min(K, 5)))
     ms64 = r64["ms"] / max(2, min(K, 5))
+    # accuracy of the mixed-precision step: the F32 form (graph) stepped from rest
+    # as many times as the FP64 run, fields compared (normwise max relative)
+    n64 = 3 + max(2, min(K, 5))
+    hq, sq = piso(D.F32), new_state(torch.float32)
+    for _ in range(n64):
+        hq.step_graph(*sq, info=info)
+    torch.cuda.synchronize()
+
+    def nrel(a, b):
+        a, b = a.double(), b.double()
+        return float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+    f32_err = {"steps": n64, "U": nrel(sq[0], r64["state"][0]), "p": nrel(sq[1], r64["state"][1]),
+               "phi": nrel(sq[2], r64["state"][2])}
+    del hq, sq
 
     # end to end through the public API: per step the lid boundary values go
     # host -> device from pinned memory and the step's info record comes back
@@ -590,7 +618,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mesh": f"kuhn{N_KUHN}^3 jitter {JITTER} seed {SEED} RCM",
+        "config": {"workload": WORKLOAD if args.mesh in (N_KUHN, *LARGE) else f"kuhn{args.mesh}_cavity_re100",
+                   "mesh": f"kuhn{args.mesh}^3 jitter {JITTER} seed {SEED} RCM",
                    "cells": dm.nc, "faces": dm.nf, "nu": NU, "dt": DT, "n_corr": 2,
                    "nonorth": "momentum (the lagged pressure correction diverges on these tets)",
                    "precision": "f32 fields/operators, f64 dots; pressure: f64 CG to 1e-10 around an "
@@ -598,7 +627,7 @@ def run_ours(args):
                    "pressure_solver": "CG + one aggregation-multigrid V-cycle per iteration",
                    "parallelism": f"replicas x{world}",
                    "api": "difvm_piso_step_graph (one CUDA graph per step, solver loops on the device)",
-                   "l2": "working set (~0.9 GB) > 126 MB L2; no flush needed"},
+                   "l2": f"working set (~{0.9 * (args.mesh / 64) ** 3:.1f} GB) > 126 MB L2; no flush needed"},
         "gpu_launches": int(r32["launches"]),
         "gpu_launches_note": "counted on the host-loop run of the same K steps; the graph replays "
                              "the same kernels plus at most 3 early-exit iterations and one "
@@ -612,7 +641,8 @@ def run_ours(args):
         "crank_nicolson": cn,
         "f64": {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64,
                 "pressure_iters_last_step": r64["info"]["itp"][:2],
-                "momentum_iters_last_step": r64["info"]["itU"]},
+                "momentum_iters_last_step": r64["info"]["itU"],
+                "f32_field_err_vs_f64": f32_err},
         "fwd_adjoint_over_fwd": fwd_adj,
         "face_ops": face_ops,
         "batched": batched,
