@@ -442,13 +442,14 @@ static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 // at once (1-4 per SM, by the kernel's register use; 40 or more registers fit
 // fewer than four 512-thread blocks), so that it runs in one wave and its
 // reduction finishes once; never more than the rows need or than grid_for(m),
-// for which the partials are sized.
-template <typename K>
-static int wave_grid(K kernel, const difvm_mesh* m) {
-  static int per = 0;   // per kernel instantiation
+// for which the partials are sized.  The kernel is a template argument, so each
+// kernel keeps its own count (kernels of one signature do not share it).
+template <auto K>
+static int wave_grid(const difvm_mesh* m) {
+  static int per = 0;
   if (per == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kKB, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kKB, 0) != cudaSuccess) {
       (void)cudaGetLastError();
       b = 4;
     }
@@ -578,8 +579,8 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
   } else if (o->method == DIFVM_BICGSTAB) {
     T *r = vec(0), *rh = vec(NC), *p = vec(2 * NC), *v = vec(3 * NC), *s_ = vec(4 * NC),
       *tv = vec(5 * NC), *y = vec(6 * NC), *z = vec(7 * NC);
-    const int Gi = wave_grid(k_bicg_init<T, NC>, m), G1 = wave_grid(k_bicg_spmv1<T, NC, MW>, m),
-              G2 = wave_grid(k_bicg_spmv2<T, NC, MW>, m), Gu = wave_grid(k_bicg_update<T, NC>, m);
+    const int Gi = wave_grid<k_bicg_init<T, NC>>(m), G1 = wave_grid<k_bicg_spmv1<T, NC, MW>>(m),
+              G2 = wave_grid<k_bicg_spmv2<T, NC, MW>>(m), Gu = wave_grid<k_bicg_update<T, NC>>(m);
     k_bicg_init<T, NC><<<Gi, kKB, 0, st>>>(t, A, jac, b, x, r, rh, p, v, rD, w);
     DIFVM_TRY(check_launch("bicg_init"));
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
