@@ -120,3 +120,71 @@ def test_adjoint_of_windkessel_outlet_pressure_is_the_flux_adjoint():
     np.testing.assert_allclose(g, dpo_dQ, rtol=1e-14)
     assert np.all(adj["pb"][f0:f0 + nq] == 0.0)       # the input p_b there is overwritten
     np.testing.assert_allclose(adj["pc"], e, rtol=1e-14)
+
+
+# ------------------------------------- pulsatile pipe with an RCR outlet (trajectory)
+def _pipe_run(om, m, theta, steps, dt, probes, target=None, keep=False):
+    """Forward trajectory of the pulsatile pipe; returns the probe-pressure MSE
+    (or the probe pressures when target is None) and, with keep, every step's
+    inputs (for the reverse sweep)."""
+    Rp, Cw, Rd = theta
+    out = m.patch_index("outlet")
+    fin = m.patch_faces("inlet")
+    r2 = (m.Cf[fin, 0] ** 2 + m.Cf[fin, 1] ** 2)
+    shape = 1.0 - r2 / r2.max() * 0.999          # parabolic, positive on every face
+    area = np.linalg.norm(m.Sf[fin], axis=1)
+    kw = dict(nu=0.035, dt=dt, tolU=1e-14, tolp=1e-14, maxitU=5000, maxitp=5000, pref_cell=0,
+              wk_patch=[out], Rp=[Rp], Cw=[Cw], Rd=[Rd])
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    pc = np.array([0.0])
+    Ub = np.zeros((3, m.n_boundary))
+    phi = O.flux_from_U(om, U, Ub)
+    probe_p, inputs = [], []
+    for k in range(steps):
+        t = (k + 1) * dt                           # boundary values at t^{n+1}
+        Q = 1.0 + 0.5 * np.sin(2 * np.pi * t) + 0.2 * np.sin(4 * np.pi * t)
+        Ub = np.zeros((3, m.n_boundary))
+        Ub[2, fin - m.n_internal] = shape * Q / (shape * area).sum()   # inflow along +z, sum u|S| = Q
+        if keep:
+            inputs.append((U, p, phi, Ub, pb, pc))
+        U, p, phi, pb, pc, info = O.piso_step(om, U, p, phi, Ub, pb, pc=pc, **kw)
+        assert info["status"] == 0
+        probe_p.append(p[probes])
+    P = np.array(probe_p)
+    if target is None:
+        return P
+    loss = ((P - target) ** 2).mean()
+    return (loss, P, inputs, kw) if keep else loss
+
+
+def test_pulsatile_pipe_windkessel_gradient_matches_central_differences():
+    """A small version of the differentiable pulsatile pipe: d(loss)/d(R_p, C, R_d)
+    from the per-step adjoints chained over the trajectory (Sec. 2.5) equals central
+    differences of the forward loss."""
+    m = mg.pipe_ohgrid(4, 2, 6, L=3.0)
+    om = O.OMesh.from_mesh(m)
+    steps, dt = 6, 0.0025 * 8
+    probes = np.random.default_rng(11).choice(m.n_cells, size=4, replace=False)
+    target = _pipe_run(om, m, (0.15, 0.7, 1.3), steps, dt, probes)
+    theta = np.array([0.1, 1.0, 1.0])
+    loss, P, inputs, kw = _pipe_run(om, m, theta, steps, dt, probes, target, keep=True)
+    # reverse sweep: dL/dp at the probes of each step's output, chained through the steps
+    Ubar, pbar = np.zeros((3, m.n_cells)), np.zeros(m.n_cells)
+    phibar, pbbar, pcbar = np.zeros(m.n_faces), np.zeros(m.n_boundary), np.zeros(1)
+    g = np.zeros(3)
+    for k in reversed(range(steps)):
+        pbar = pbar.copy()
+        pbar[probes] += 2.0 * (P[k] - target[k]) / P.size
+        U, p, phi, Ub, pb, pc = inputs[k]
+        r = O.piso_step_bwd(om, U, p, phi, Ub, pb, Ubar, pbar, phibar, pbbar, pcbar, pc=pc, **kw)
+        assert r["status"] == 0
+        g += [r["Rp"][0], r["Cw"][0], r["Rd"][0]]
+        Ubar, pbar, phibar, pbbar, pcbar = r["U"], r["p"], r["phi"], r["pb"], r["pc"]
+    for i in range(3):
+        h = 1e-5 * theta[i]
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (_pipe_run(om, m, tp, steps, dt, probes, target) -
+              _pipe_run(om, m, tm, steps, dt, probes, target)) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-5 * abs(fd) + 1e-12, (i, g[i], fd)
