@@ -338,7 +338,9 @@ __global__ void __launch_bounds__(kKB) k_pcg_spmv(Topo t, Mat<T> A, const T* p, 
 // (a chunk of kSegRows of its rows); each case has its own ticket, and the
 // last of the case's blocks to arrive reduces that case's partials in block
 // order.  A case's block partition depends only on its own size, so a case
-// gives bitwise the same result alone as inside any batch.
+// gives bitwise the same result alone as inside any batch (Jacobi or no
+// preconditioning; the multigrid form in amg.cu shares its hierarchy across
+// the cases and is equal to the case alone only up to rounding).
 struct SWork {
   KState* st;          // [ncases * NC]
   double* part;        // [nblk * kMaxParts]
