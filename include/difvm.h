@@ -269,6 +269,7 @@ difvm_status difvm_laplacian_apply_bwd(difvm_mesh_t, difvm_prec, const void* dia
  *    clearing); each GPU has its own copy, and calls on the same GPU that
  *    can overlap (for example on two streams with no ordering between them)
  *    race on it;
+ *  - the mesh's device must be the current device (EINVAL otherwise);
  *  - no cudaMalloc, cudaFree or allocating library routine is called. */
 difvm_status difvm_laplacian_apply_bwd_noalloc(difvm_mesh_t, difvm_prec, const void* diag,
                                                const void* lower, const void* upper, const void* x,

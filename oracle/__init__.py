@@ -34,24 +34,60 @@ CONV_UPWIND, CONV_SOU = 0, 1
 TIME_BE, TIME_CN = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (gcc -O2 -ffp-contract=off, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def _compile(out, extra):
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", *extra,
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc -O2 -ffp-contract=off, no FMA contraction), and
+    its multi-core build (the same source with -fopenmp) used only by the
+    all-cores CPU baseline."""
+    if force:
+        for f in (_LIB, _LIB_OMP):
+            if os.path.exists(f):
+                os.remove(f)
+    _compile(_LIB_OMP, ["-fopenmp"])
+    return _compile(_LIB, [])
 
 
 _lib = None
+_use_omp = False
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        build()
+        _lib = C.CDLL(_LIB_OMP if _use_omp else _LIB)
     return _lib
+
+
+def use_multicore(on: bool = True):
+    """Switch every following oracle call to the multi-core build (True) or
+    back to the single-thread oracle (False).  Returns the thread count."""
+    global _lib, _use_omp
+    if on != _use_omp:
+        _use_omp, _lib = on, None
+    return threads()
+
+
+def threads() -> int:
+    """Threads the selected build runs on (1 for the single-thread oracle)."""
+    return int(lib().om_threads())
+
+
+def set_threads(n: int) -> int:
+    """Thread count of the multi-core build (no effect on the single-thread one)."""
+    lib().om_set_threads(int(n))
+    return threads()
 
 
 class _Mesh(C.Structure):

@@ -37,10 +37,22 @@
  * PISO step against central differences of the forward step).
  * Parity unpinned: the interpolation weight on non-uniform meshes (w_f above
  * is a reading; every choice gives 0.5 on the uniform hex meshes that pin it).
+ *
+ * Multi-core build (compiled with -fopenmp; only the all-cores CPU baseline
+ * uses it): the Krylov vector loops run on all threads, the LDU apply visits
+ * each cell's faces in ascending face id through a cell-to-face table (the
+ * same additions in the same order as the face loop, so bitwise the same y),
+ * and inner products add fixed blocks of OM_DOT_BLOCK entries and then the
+ * block sums in order (the result does not depend on the thread count; it
+ * differs from the single-thread sum by rounding only).  Everything else is
+ * the code above, unchanged.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int nc, nint, nf, npatch;
@@ -278,10 +290,49 @@ void om_laplacian(const om_mesh *m, const int *bc, int ncomp, double gamma, cons
 /* ------------------------------------------------------------- LDU apply */
 /* y_i = D_i x_i + sum_{f: O=i} U_f x_N + sum_{f: N=i} L_f x_O   (Eq. Ap_H).
  * U == NULL means symmetric (U = L).  Swapping L and U gives A^T. */
+#ifdef _OPENMP
+/* cell -> internal-face table of the last mesh seen, faces ascending per cell */
+static struct { const int *owner; int nc, nint; int *ptr, *ent; } om_csr;
+static void om_csr_build(const om_mesh *m) {
+  if (om_csr.owner == m->owner && om_csr.nc == m->nc && om_csr.nint == m->nint) return;
+  free(om_csr.ptr); free(om_csr.ent);
+  int *ptr = calloc((size_t)m->nc + 1, sizeof(int)), *ent = malloc(sizeof(int) * (2 * (size_t)m->nint + 1));
+  for (int f = 0; f < m->nint; ++f) { ptr[m->owner[f] + 1]++; ptr[m->neighbour[f] + 1]++; }
+  for (int i = 0; i < m->nc; ++i) ptr[i + 1] += ptr[i];
+  int *fill = malloc(sizeof(int) * ((size_t)m->nc + 1));
+  memcpy(fill, ptr, sizeof(int) * (size_t)m->nc);
+  for (int f = 0; f < m->nint; ++f) {        /* entry = face << 1 | (1 if the cell is the neighbour) */
+    ent[fill[m->owner[f]]++] = f << 1;
+    ent[fill[m->neighbour[f]]++] = (f << 1) | 1;
+  }
+  free(fill);
+  om_csr.owner = m->owner; om_csr.nc = m->nc; om_csr.nint = m->nint;
+  om_csr.ptr = ptr; om_csr.ent = ent;
+}
+#endif
+
 void om_ldu_apply(const om_mesh *m, int ncomp, const double *D, const double *L,
                   const double *U, const double *x, double *y) {
   int nc = m->nc;
   if (!U) U = L;
+#ifdef _OPENMP
+  om_csr_build(m);
+  for (int q = 0; q < ncomp; ++q) {
+    const double *xq = x + (size_t)q * nc;
+    double *yq = y + (size_t)q * nc;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < nc; ++i) {
+      double acc = D[i] * xq[i];
+      for (int e = om_csr.ptr[i]; e < om_csr.ptr[i + 1]; ++e) {
+        int f = om_csr.ent[e] >> 1;
+        if (om_csr.ent[e] & 1) acc += L[f] * xq[m->owner[f]];
+        else acc += U[f] * xq[m->neighbour[f]];
+      }
+      yq[i] = acc;
+    }
+  }
+  return;
+#endif
   for (int q = 0; q < ncomp; ++q) {
     const double *xq = x + (size_t)q * nc;
     double *yq = y + (size_t)q * nc;
@@ -295,10 +346,45 @@ void om_ldu_apply(const om_mesh *m, int ncomp, const double *D, const double *L,
 }
 
 /* ---------------------------------------------------------------- Krylov */
+#ifdef _OPENMP
+#define OM_DOT_BLOCK 4096
+static double vdot(int n, const double *a, const double *b) {
+  int nblk = (n + OM_DOT_BLOCK - 1) / OM_DOT_BLOCK;
+  double *part = malloc(sizeof(double) * (nblk > 0 ? nblk : 1));
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nblk; ++k) {
+    double s = 0.0;
+    int e = (k + 1) * OM_DOT_BLOCK < n ? (k + 1) * OM_DOT_BLOCK : n;
+    for (int i = k * OM_DOT_BLOCK; i < e; ++i) s += a[i] * b[i];
+    part[k] = s;
+  }
+  double s = 0.0;
+  for (int k = 0; k < nblk; ++k) s += part[k];
+  free(part);
+  return s;
+}
+#else
 static double vdot(int n, const double *a, const double *b) {
   double s = 0.0;
   for (int i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
+}
+#endif
+
+/* number of threads the multi-core build uses (1 in the single-thread build) */
+int om_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+void om_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
 
 typedef struct { int iters; double res0, res, bnorm; int status; } om_info;
@@ -321,24 +407,29 @@ int om_pcg(const om_mesh *m, const double *D, const double *L, const double *U, 
   }
   double tol = fmax(tol_rel * bn, tol_abs);
   om_ldu_apply(m, 1, D, L, U, x, q);
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
   double rn = sqrt(vdot(n, r, r));
   info->res0 = rn;
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) { z[i] = r[i] / D[i]; p[i] = z[i]; }
   double rz = vdot(n, r, z);
   int it = 0;
   while (rn > tol && it < maxit) {
     om_ldu_apply(m, 1, D, L, U, p, q);
     double alpha = rz / vdot(n, p, q);
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
     ++it;
     rn = sqrt(vdot(n, r, r));
     if (!isfinite(rn)) { info->status = 5; break; }
     if (rn <= tol) break;
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) z[i] = r[i] / D[i];
     double rz1 = vdot(n, r, z);
     double beta = rz1 / rz;
     rz = rz1;
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
   }
   info->iters = it; info->res = rn;
@@ -482,6 +573,7 @@ int om_bicgstab(const om_mesh *m, const double *D, const double *L, const double
   }
   double tol = fmax(tol_rel * bn, tol_abs);
   om_ldu_apply(m, 1, D, L, U, x, t);
+  #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; }
   double rn = sqrt(vdot(n, r, r));
   info->res0 = rn;
@@ -492,22 +584,28 @@ int om_bicgstab(const om_mesh *m, const double *D, const double *L, const double
     if (rho1 == 0.0 || omega == 0.0) { info->status = 4; break; }
     double beta = (rho1 / rho) * (alpha / omega);
     rho = rho1;
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) y[i] = p[i] / D[i];
     om_ldu_apply(m, 1, D, L, U, y, v);
     alpha = rho / vdot(n, rh, v);
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
     ++it;
     double sn = sqrt(vdot(n, s, s));
     if (sn <= tol) {
+      #pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) x[i] += alpha * y[i];
       rn = sn;
       break;
     }
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) z[i] = s[i] / D[i];
     om_ldu_apply(m, 1, D, L, U, z, t);
     double tt = vdot(n, t, t);
     omega = tt > 0.0 ? vdot(n, t, s) / tt : 0.0;
+    #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) { x[i] += alpha * y[i] + omega * z[i]; r[i] = s[i] - omega * t[i]; }
     rn = sqrt(vdot(n, r, r));
     if (!isfinite(rn)) { info->status = 5; break; }

@@ -66,6 +66,14 @@ extern "C" difvm_status difvm_laplacian_apply_bwd_noalloc(difvm_mesh_t m, difvm_
                      "difvm_laplacian_apply_bwd_noalloc: %d x %d cells need %zu bytes of scratch, "
                      "the built-in maximum is %zu bytes",
                      ncomp, m->nc, need, kNoAllocScratchBytes);
+  // the kernels launch on the current device, and the scratch and the mesh
+  // arrays belong to the mesh's device: the two must be the same
+  int cur = -1;
+  DIFVM_CUDA(cudaGetDevice(&cur));
+  if (cur != m->device)
+    return set_error(DIFVM_EINVAL,
+                     "difvm_laplacian_apply_bwd_noalloc: current device %d is not the mesh's device %d",
+                     cur, m->device);
   cudaStream_t st = (cudaStream_t)stream;
   if (xbar) {
     void* scratch = nullptr;

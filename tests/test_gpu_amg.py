@@ -128,7 +128,7 @@ def _cavity(n, seed):
     return m, Ub
 
 
-@pytest.mark.parametrize("prec,refine,bar", [(D.F64, 0, 1e-9), (D.F32, 20, 2e-4)])
+@pytest.mark.parametrize("prec,refine,bar", [(D.F64, 0, 1e-9), (D.F32, 20, 1e-4)])
 def test_piso_with_amg_pressure_matches_oracle(prec, refine, bar):
     m, Ub = _cavity(8, 21)
     om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
@@ -144,8 +144,8 @@ def test_piso_with_amg_pressure_matches_oracle(prec, refine, bar):
         assert st == D.OK, D.decode_piso_info(info)
         U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.02, dt=0.05, tolU=1e-12,
                                           tolp=1e-12, pref_cell=pref, psi=0.5, nonorth=3)
-    assert nrel(dm.from_cells(host(g[0])), U) < bar
-    assert nrel(dm.from_cells(host(g[1])), p) < bar * 10
+    errs = nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p)
+    assert max(errs) < bar, errs
     assert max(D.decode_piso_info(info)["itp"][:2]) < 60
 
 
