@@ -228,6 +228,13 @@ def run_face_ops(D, torch, m, dm, peak, reps=20, copies=4):
     geometry the operator needs), each input cell array read once, each output
     written once; gathers hit cache."""
     nc, ni, nf, nb = dm.nc, dm.ni, dm.nf, dm.nb
+    nhf = 2 * ni + nb          # half-faces: every internal face seen from both cells
+    # FP64 work per launch: FP64 add / mul / fma instructions of each kernel, per
+    # internal half-face (boundary half-faces are ~1% of the total and counted
+    # alike) and per cell, read off the kernels' arithmetic
+    fp64_ops = {"grad_gauss_scalar": (7, 3), "grad_gauss_vector": (19, 9), "div_flux_upwind_3": (6, 0),
+                "div_flux_linear_3": (13, 0), "laplacian_apply_sym_1": (1, 1),
+                "laplacian_apply_asym_3": (3, 3), "laplacian_nonorth_1": (15, 0)}
     dms = [dm] + [D.Mesh(m, device=torch.cuda.current_device()) for _ in range(copies - 1)]
     gen = torch.Generator(device="cuda")
     gen.manual_seed(7)
@@ -262,9 +269,8 @@ def run_face_ops(D, torch, m, dm, peak, reps=20, copies=4):
             }
         per_copy = [ops_of(d) for d in dms]
         key = "f32" if prec == D.F32 else "f64"
-        for name in per_copy[0]:
-            fns = [oc[name][0] for oc in per_copy]
-            nbytes = per_copy[0][name][1]
+
+        def time_op(fns):
             for f in fns:
                 f()
             torch.cuda.synchronize()
@@ -274,14 +280,42 @@ def run_face_ops(D, torch, m, dm, peak, reps=20, copies=4):
                 fns[r % copies]()
             b.record()
             torch.cuda.synchronize()
-            t = a.elapsed_time(b) / reps
+            return a.elapsed_time(b) / reps
+
+        for name in per_copy[0]:
+            fns = [oc[name][0] for oc in per_copy]
+            nbytes = per_copy[0][name][1]
+            t_default = None
+            if prec == D.F32:
+                # the default launch variant, then the one first-use timing keeps
+                for d in dms:
+                    D.difvm_mesh_autotune(d, 0)
+                t_default = time_op(fns)
+                for d in dms:
+                    D.difvm_mesh_autotune(d, 1)
+            t = time_op(fns)
             gbs = nbytes / (t * 1e-3) / 1e9
-            res.setdefault(name, {})[key] = {"us": round(t * 1e3, 2), "alg_MB": round(nbytes / 1e6, 1),
-                                             "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3),
-                                             "frac_of_8TBs": round(gbs / 8000.0, 3)}
+            e = {"us": round(t * 1e3, 2), "alg_MB": round(nbytes / 1e6, 1),
+                 "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3),
+                 "frac_of_8TBs": round(gbs / 8000.0, 3)}
+            if t_default is not None:
+                e["us_default_variant"] = round(t_default * 1e3, 2)
+            else:
+                # FP64: the roofline is the slower of HBM and the FP64 pipe
+                # (1.25 TFLOP/s dense = 0.625e12 fma instructions/s, every FP64
+                # add / mul / fma taking one issue slot)
+                ph, pc = fp64_ops[name]
+                ops = ph * nhf + pc * nc
+                t_alu, t_hbm = ops / 0.625e12, nbytes / (peak * 1e9)
+                e.update({"fp64_ops": int(ops), "t_alu_us": round(t_alu * 1e6, 2),
+                          "t_hbm_us": round(t_hbm * 1e6, 2), "bound": "alu" if t_alu > t_hbm else "hbm",
+                          "frac_of_bound": round(max(t_alu, t_hbm) / (t * 1e-3), 3)})
+            res.setdefault(name, {})[key] = e
+        if prec == D.F32:
+            res["_tuned_variants"] = {f"{k[0]}.{k[1]}.{k[2]}": v for k, v in D.difvm_mesh_tuning(dms[0]).items()}
         del per_copy
     del dms[1:]
-    fr = [res[k]["f32"]["frac"] for k in res]
+    fr = [res[k]["f32"]["frac"] for k in res if not k.startswith("_")]
     return {"unit": "GB/s (algorithmic)", "peak": peak, "reps": reps, "ops": res,
             "f32_frac_median": float(np.median(fr)), "f32_frac_min": float(min(fr)),
             "method": f"{reps} back-to-back launches rotating over {copies} device copies of the mesh and "

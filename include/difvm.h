@@ -150,9 +150,28 @@ typedef struct {
  * (w_f, c_f = |Delta_f|/|d| (|S|^2/(S.d) for the default split), k_f = S - c_f d,
  * 1/V; Sec. 2.3.2) and upload them.
  * Errors: EINVAL with a message for index out of range, owner == neighbour,
- * patches not covering the boundary faces contiguously, V <= 0 or S.d <= 0;
- * ENOMEM / ECUDA on allocation or copy failure.  Synchronous. */
+ * patches not covering the boundary faces contiguously, V <= 0 or S.d <= 0,
+ * more than 2^29 - 1 boundary faces; ENOMEM / ECUDA on allocation or copy
+ * failure.  Synchronous. */
 difvm_status difvm_mesh_create(const difvm_mesh_desc* desc, difvm_mesh_t* out);
+/* Launch variants of the face operators (difvm_grad_gauss, difvm_div_flux,
+ * difvm_laplacian, difvm_laplacian_apply) in FP32 on meshes whose rows all have
+ * four faces (tetrahedra): the first call of each (operator, scheme or
+ * correction, components) on a mesh times the variants -- register budgets
+ * for 1, 6 and 8 resident 256-thread blocks per SM -- on that call's own
+ * arguments and keeps the fastest for the mesh.  That first call synchronises
+ * with the host; a first call under stream capture launches the default
+ * variant and records nothing.  No device memory is allocated.
+ * mode 0: no timing, every call launches the default variant; 1: timing on
+ * (the default); 2: forget the kept choices and time again.  EINVAL on a bad
+ * mode. */
+difvm_status difvm_mesh_autotune(difvm_mesh_t, int mode);
+/* The kept choices, HOST outputs: keys[k] = operator << 8 | option << 4 |
+ * components (operator 1 Gauss gradient, 2 divergence (option 1 upwind),
+ * 3 Laplacian (option 1 with the non-orthogonal term), 4 LDU apply) and
+ * variants[k] in 0..2; at most cap entries are written, *count gets the
+ * number kept. */
+difvm_status difvm_mesh_tuning(difvm_mesh_t, uint32_t* keys, int32_t* variants, int cap, int32_t* count);
 /* Maps between input and internal numbering, HOST outputs (any may be NULL):
  *   cell_new_of_old[n_cells], face_old_of_new[n_faces],
  *   face_flip[n_faces] (1 where the internal face was re-oriented: its S, and

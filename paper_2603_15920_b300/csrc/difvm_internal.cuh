@@ -116,20 +116,46 @@ struct Ell {
   const int* map;   // [nslots]
 };
 
+// Boundary faces as the face operators see them: a patch is "empty" (the face
+// drops out of every sum), an outlet (fixed pressure, zero-gradient velocity)
+// or anything else (fixed velocity, zero-gradient pressure).  The kind of a
+// face for a boundary-condition class follows from that category alone.
+enum { kCatOther = 0, kCatOutlet = 1, kCatEmpty = 2 };
+__host__ __device__ __forceinline__ int patch_cat(int patch_type) {
+  return patch_type == DIFVM_PATCH_EMPTY ? kCatEmpty : (patch_type == DIFVM_PATCH_OUTLET ? kCatOutlet : kCatOther);
+}
+__host__ __device__ __forceinline__ int bc_kind(int cls, int cat) {
+  if (cat == kCatEmpty) return DIFVM_FACE_EMPTY;
+  switch (cls) {
+    case DIFVM_BC_VELOCITY: return cat == kCatOutlet ? DIFVM_FACE_ZEROGRAD : DIFVM_FACE_FIXED;
+    case DIFVM_BC_PRESSURE: return cat == kCatOutlet ? DIFVM_FACE_FIXED : DIFVM_FACE_ZEROGRAD;
+    case DIFVM_BC_ALL_FIXED: return DIFVM_FACE_FIXED;
+    default: return DIFVM_FACE_ZEROGRAD;
+  }
+}
+
 // Half-face layout of the cell-CSR rows (every face of a cell, internal and
 // boundary, in ascending face order), for the face operators: sliced ELL with
 // slice height 32, column-major in a slice (slot k of row i at
 // soff[i/32] + 32 k + i%32; with a uniform width W > 0 soff is not read).
 // nb[slot] = 2 j + side for an internal face (j the other cell, side 1 = row is
-// the neighbour), -2 - b for boundary face ni + b, -1 on padding; fid[slot] =
-// face id.  The Sw face records are also copied into slot order (a row's
-// records then come in with coalesced loads, without the face id).
+// the neighbour), -2 - (4 b + cat) for boundary face ni + b of patch category
+// cat (so a kernel knows the face's boundary kind without another load), -1 on
+// padding; fid[slot] = face id; nf[slot] = (nb, fid) in one 8-byte word.  The
+// Sw face records are also copied into slot order (a row's records then come
+// in with coalesced loads, without the face id).
 struct Hf {
   int W;
   const int* soff;
   const int* nb;
   const int* fid;
+  const int2* nf;
 };
+// boundary face index and patch category of a boundary slot word (v <= -2)
+__device__ __forceinline__ int hf_bface(int v) { return (-2 - v) >> 2; }
+__device__ __forceinline__ int hf_bcat(int v) { return (-2 - v) & 3; }
+// largest boundary-face count the slot words can encode
+constexpr int kMaxBoundaryFaces = (1 << 29) - 1;
 // face records as a face kernel reads them: by slot (sw = the slot copies,
 // ck unused) or by face id (sw, ck = the face arrays)
 template <typename T> struct HfGeo {
@@ -219,6 +245,11 @@ struct difvm_mesh {
   int* hf_soff = nullptr;
   int* hf_nb = nullptr;
   int* hf_fid = nullptr;
+  int2* hf_nf = nullptr;
+  // face-operator launch variants picked by first-use timing (see ops.cu):
+  // key -> variant, and whether timing is allowed
+  std::vector<std::pair<uint32_t, int>> tuned;
+  int autotune = 1;
   difvm::V4<double>* hf_sw64 = nullptr;
   difvm::V4<float>* hf_sw32 = nullptr;
 
@@ -226,7 +257,7 @@ struct difvm_mesh {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
   }
   difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_w, ell_soff, ell_col, ell_map}; }
-  difvm::Hf hf() const { return difvm::Hf{hf_w, hf_soff, hf_nb, hf_fid}; }
+  difvm::Hf hf() const { return difvm::Hf{hf_w, hf_soff, hf_nb, hf_fid, hf_nf}; }
   difvm::HfGeo<double> hfgeo64() const { return {hf_sw64, nullptr}; }
   difvm::HfGeo<float> hfgeo32() const { return {hf_sw32, nullptr}; }
   difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }

@@ -221,7 +221,7 @@ static void free_mesh(difvm_mesh* m) {
                   m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
                   m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map,
                   m->seg_case, m->seg_cb0, m->seg_cs, m->hf_soff, m->hf_nb, m->hf_fid,
-                  m->hf_sw64, m->hf_sw32};
+                  m->hf_nf, m->hf_sw64, m->hf_sw32};
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
@@ -253,6 +253,8 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
     return set_error(DIFVM_EINVAL, "unknown mesh flags 0x%x", d->flags);
   if (nb > 0 && (!d->patch_start || !d->patch_size || !d->patch_type))
     return set_error(DIFVM_EINVAL, "boundary faces without patches");
+  if (nb > kMaxBoundaryFaces)
+    return set_error(DIFVM_EINVAL, "%d boundary faces: at most %d are supported", nb, kMaxBoundaryFaces);
   for (int f = 0; f < nf; ++f)
     if (d->owner[f] < 0 || d->owner[f] >= nc)
       return set_error(DIFVM_EINVAL, "owner[%d]=%d out of range", f, d->owner[f]);
@@ -421,6 +423,10 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   }
   m->ell_nsl = nsl;
   m->ell_nslots = soff[nsl];
+  // patch of every boundary face (the slot words carry its category)
+  std::vector<int> bpatch_of(nb > 0 ? nb : 1, 0);
+  for (int p = 0; p < np; ++p)
+    for (int f = d->patch_start[p]; f < d->patch_start[p] + d->patch_size[p]; ++f) bpatch_of[f - ni] = p;
   // half-face layout: every CSR entry of a row, sliced ELL, column-major per slice
   std::vector<int> hsoff(nsl + 1, 0);
   int hwmax = 0;
@@ -441,21 +447,17 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
       const int slot = hsoff[i >> 5] + 32 * (e - cptr[i]) + (i & 31);
       const int ent = cent[e], f = ent >> 1;
       hfid[slot] = f;
-      hnb[slot] = f < ni ? 2 * ((ent & 1) ? on[f].x : on[f].y) + (ent & 1) : -2 - (f - ni);
+      hnb[slot] = f < ni ? 2 * ((ent & 1) ? on[f].x : on[f].y) + (ent & 1)
+                         : -2 - (4 * (f - ni) + patch_cat(d->patch_type[bpatch_of[f - ni]]));
     }
   }
   // boundary kinds per bc class (2 bits each)
   std::vector<uint8_t> bkind(nb > 0 ? nb : 1);
   std::vector<uint16_t> bpatch(nb > 0 ? nb : 1);
   for (int p = 0; p < np; ++p) {
-    int t = d->patch_type[p];
-    int kU = t == DIFVM_PATCH_EMPTY ? DIFVM_FACE_EMPTY
-             : (t == DIFVM_PATCH_OUTLET ? DIFVM_FACE_ZEROGRAD : DIFVM_FACE_FIXED);
-    int kp = t == DIFVM_PATCH_EMPTY ? DIFVM_FACE_EMPTY
-             : (t == DIFVM_PATCH_OUTLET ? DIFVM_FACE_FIXED : DIFVM_FACE_ZEROGRAD);
-    int kF = t == DIFVM_PATCH_EMPTY ? DIFVM_FACE_EMPTY : DIFVM_FACE_FIXED;
-    int kZ = t == DIFVM_PATCH_EMPTY ? DIFVM_FACE_EMPTY : DIFVM_FACE_ZEROGRAD;
-    uint8_t code = (uint8_t)(kU | (kp << 2) | (kF << 4) | (kZ << 6));
+    const int cat = patch_cat(d->patch_type[p]);
+    uint8_t code = 0;
+    for (int cls = 0; cls < 4; ++cls) code |= (uint8_t)(bc_kind(cls, cat) << (2 * cls));
     for (int f = d->patch_start[p]; f < d->patch_start[p] + d->patch_size[p]; ++f) {
       bkind[f - ni] = code;
       bpatch[f - ni] = (uint16_t)p;
@@ -478,6 +480,11 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload(&m->hf_soff, hsoff.data(), hsoff.size()));
   DIFVM_TRY(upload(&m->hf_nb, hnb.data(), hnb.size()));
   DIFVM_TRY(upload(&m->hf_fid, hfid.data(), hfid.size()));
+  {
+    std::vector<int2> hnf(hnb.size());
+    for (size_t k = 0; k < hnb.size(); ++k) hnf[k] = make_int2(hnb[k], hfid[k]);
+    DIFVM_TRY(upload(&m->hf_nf, hnf.data(), hnf.size()));
+  }
   m->bown_host.assign(bown.begin(), bown.begin() + nb);
   if (d->case_cell_start) {
     // block tables of the segmented solvers (the case ranges survive the

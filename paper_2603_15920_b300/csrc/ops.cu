@@ -21,41 +21,73 @@ constexpr int kBlock = 256;
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
-// Four consecutive half-face slots of a row: their neighbour words and face
-// records arrive with coalesced loads issued before any is used, so each face
-// costs one dependent gather (the neighbour's value).  Slots are consumed in
-// row order (ascending face id), so every sum keeps the CSR order.
-template <typename T, bool SW, bool CK>
-struct HfChunk {
-  int v[4];       // half-face word (see Hf), -1 past the row end or on padding
-  int slot[4];
-  int f[4];       // face id (FG)
-  V4<T> sw[4], ck[4];
-};
-template <bool FG, typename T, bool SW, bool CK>
-__device__ __forceinline__ void hf_chunk(const Hf& H, const HfGeo<T>& G, int base, int k0, int w,
-                                         HfChunk<T, SW, CK>& c) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    c.slot[k] = base + 32 * (k0 + k);
-    c.v[k] = (k0 + k < w) ? ldg(H.nb + c.slot[k]) : -1;
-    if (FG) c.f[k] = (k0 + k < w) ? max(ldg(H.fid + c.slot[k]), 0) : 0;   // padding: fid -1
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int o = FG ? c.f[k] : c.slot[k];
-    if (SW && k0 + k < w) c.sw[k] = ld4(G.sw + o);
-    if (CK && k0 + k < w) c.ck[k] = ld4(G.ck + o);
+// A row's half-face slots, four at a time: their words (and face ids, or the
+// slot copies of the face records) arrive with coalesced loads issued before
+// any is used.  The neighbour values and the boundary values are gathered in
+// one second round: a boundary slot's word carries its patch category, so the
+// face's kind for the requested boundary-condition class needs no load.  Slots
+// are consumed in row order (ascending face id), so every sum keeps the CSR
+// order.  WK > 0: every row has exactly WK slots, known at compile time (the
+// uniform layout of tetrahedral meshes, WK = 4); WK = 0: the row width is read
+// from the layout.
+template <int WK>
+__device__ __forceinline__ void hf_row_w(const Hf& H, int i, int& base, int& w) {
+  if (WK > 0) {
+    base = (i >> 5) * 32 * WK + (i & 31);
+    w = WK;
+  } else {
+    hf_row(H, i, base, w);
   }
 }
 
+// words (and, with FID, face ids) of slots k0..k0+3 of a row; -1 past its end
+template <bool FID>
+__device__ __forceinline__ void hf_words(const Hf& H, int base, int k0, int w, int (&v)[4], int (&f)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int slot = base + 32 * (k0 + k);
+    v[k] = -1;
+    f[k] = 0;
+    if (k0 + k < w) {
+      if (FID) {
+        const int2 q = __ldg(H.nf + slot);
+        v[k] = q.x;
+        f[k] = max(q.y, 0);   // padding carries face id -1
+      } else {
+        v[k] = ldg(H.nb + slot);
+      }
+    }
+  }
+}
+
+// boundary kind of slot word v (v <= -2) for class cls
+__device__ __forceinline__ int hf_kind(int v, int cls) { return bc_kind(cls, hf_bcat(v)); }
+
+// component c of the value across slot word v: the other cell's (internal
+// face), the boundary value (fixed boundary face), the row's own value
+// (zero-gradient boundary face) or 0 (empty face, padding)
+template <typename T>
+__device__ __forceinline__ T hf_other(int v, int cls, const T* __restrict__ phi, const T* __restrict__ phib,
+                                      int nc, int nb, int c, T own) {
+  if (v >= 0) return ldg(phi + c * nc + (v >> 1));
+  if (v == -1) return T(0);
+  const int kind = hf_kind(v, cls);
+  return kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + hf_bface(v)) : (kind == DIFVM_FACE_ZEROGRAD ? own : T(0));
+}
+
+// slot k0+k takes no part in a sum: padding, or an empty boundary face
+__device__ __forceinline__ bool hf_skip(int v, int cls) {
+  return v == -1 || (v <= -2 && hf_kind(v, cls) == DIFVM_FACE_EMPTY);
+}
+
 // ----------------------------------------------------------- Gauss gradient
-// grad_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green)
-template <typename T, int NC, bool FG>
-__global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg, Geo<T> g, int cls,
-                                                       const T* __restrict__ phi,
-                                                       const T* __restrict__ phib,
-                                                       T* __restrict__ grad) {
+// grad_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green).  Face records are
+// read from their slot copies (coalesced, no face id).
+template <typename T, int NC, int WK, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg, Geo<T> g, int cls,
+                                                             const T* __restrict__ phi,
+                                                             const T* __restrict__ phib,
+                                                             T* __restrict__ grad) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc, nb = t.nb;
@@ -65,48 +97,49 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg
     pi[c] = ldg(phi + c * nc + i);
     acc[c][0] = acc[c][1] = acc[c][2] = T(0);
   }
+  const T r = ldg(g.rV + i);
   int base, w;
-  hf_row(H, i, base, w);
+  hf_row_w<WK>(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
-    HfChunk<T, true, false> q;
-    hf_chunk<FG>(H, hg, base, k0, w, q);
+    int v[4], f[4];
+    hf_words<false>(H, base, k0, w, v, f);
+    V4<T> s[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      s[k] = k0 + k < w ? ld4(hg.sw + base + 32 * (k0 + k)) : V4<T>{T(0), T(0), T(0), T(0)};
     T pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) pj[k][c] = q.v[k] >= 0 ? ldg(phi + c * nc + (q.v[k] >> 1)) : T(0);
+      for (int c = 0; c < NC; ++c) pj[k][c] = hf_other(v[k], cls, phi, phib, nc, nb, c, pi[c]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int v = q.v[k];
-      if (v == -1) continue;
-      const V4<T> s = q.sw[k];
+      const int vk = v[k];
+      if (hf_skip(vk, cls)) continue;
+      const V4<T> sk = s[k];
       T pf[NC];
       T sg = T(1);
-      if (v >= 0) {
-        const bool nside = v & 1;
+      if (vk >= 0) {
+        const bool nside = vk & 1;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
-          pf[c] = s.w * pO + (T(1) - s.w) * pN;
+          pf[c] = sk.w * pO + (T(1) - sk.w) * pN;
         }
         if (nside) sg = T(-1);
       } else {
-        const int b = -2 - v;
-        const int kind = face_kind(t, b, cls);
-        if (kind == DIFVM_FACE_EMPTY) continue;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) pf[c] = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
+        for (int c = 0; c < NC; ++c) pf[c] = pj[k][c];
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const T qv = sg * pf[c];
-        acc[c][0] += qv * s.x;
-        acc[c][1] += qv * s.y;
-        acc[c][2] += qv * s.z;
+        acc[c][0] += qv * sk.x;
+        acc[c][1] += qv * sk.y;
+        acc[c][2] += qv * sk.z;
       }
     }
   }
-  const T r = ldg(g.rV + i);
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -173,11 +206,14 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss_bwd(Topo t, Geo<T> g, int
 }
 
 // ------------------------------------------------------------ convection
-// out_i = sum_f sigma m_f phi_f   (Eqs. conv_face_flux, upwind; tie m=0 -> owner)
-template <typename T, int NC, bool UPWIND, bool FG>
-__device__ __forceinline__ void div_flux_row(const Topo& t, const Hf& H, const HfGeo<T>& hg, int cls,
-                                             const T* __restrict__ mf, const T* __restrict__ phi,
-                                             const T* __restrict__ phib, T* __restrict__ out) {
+// out_i = sum_f sigma m_f phi_f   (Eqs. conv_face_flux, upwind; tie m=0 -> owner).
+// The face flux (and, for the linear scheme, w_f) is read by face id.
+template <typename T, int NC, bool UPWIND, int WK, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls,
+                                                           const T* __restrict__ mf,
+                                                           const T* __restrict__ phi,
+                                                           const T* __restrict__ phib,
+                                                           T* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc, nb = t.nb;
@@ -188,63 +224,40 @@ __device__ __forceinline__ void div_flux_row(const Topo& t, const Hf& H, const H
     acc[c] = T(0);
   }
   int base, w;
-  hf_row(H, i, base, w);
+  hf_row_w<WK>(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
-    HfChunk<T, !UPWIND, false> q;
-    hf_chunk<FG>(H, hg, base, k0, w, q);
-    int fk[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) fk[k] = FG ? q.f[k] : (q.v[k] != -1 ? ldg(H.fid + q.slot[k]) : 0);
-    T mk[4], pj[4][NC];
+    int v[4], f[4];
+    hf_words<true>(H, base, k0, w, v, f);
+    T mk[4], wk[4], pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      mk[k] = q.v[k] != -1 ? ldg(mf + fk[k]) : T(0);
+      mk[k] = v[k] != -1 ? ldg(mf + f[k]) : T(0);
+      wk[k] = (!UPWIND && v[k] >= 0) ? ld4(hg.sw + f[k]).w : T(0);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) pj[k][c] = q.v[k] >= 0 ? ldg(phi + c * nc + (q.v[k] >> 1)) : T(0);
+      for (int c = 0; c < NC; ++c) pj[k][c] = hf_other(v[k], cls, phi, phib, nc, nb, c, pi[c]);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int v = q.v[k];
-      if (v == -1) continue;
+      const int vk = v[k];
+      if (hf_skip(vk, cls)) continue;
       const T m = mk[k];
-      if (v >= 0) {
-        const bool nside = v & 1;
-        const T wf = UPWIND ? T(0) : q.sw[k].w;
+      if (vk >= 0) {
+        const bool nside = vk & 1;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
-          const T pf = UPWIND ? (m >= T(0) ? pO : pN) : wf * pO + (T(1) - wf) * pN;
+          const T pf = UPWIND ? (m >= T(0) ? pO : pN) : wk[k] * pO + (T(1) - wk[k]) * pN;
           const T F = m * pf;
           acc[c] += nside ? -F : F;
         }
       } else {
-        const int b = -2 - v;
-        const int kind = face_kind(t, b, cls);
-        if (kind == DIFVM_FACE_EMPTY) continue;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const T pf = kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + b) : pi[c];
-          acc[c] += m * pf;
-        }
+        for (int c = 0; c < NC; ++c) acc[c] += m * pj[k][c];
       }
     }
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) out[c * nc + i] = acc[c];
-}
-template <typename T, int NC, bool UPWIND, bool FG>
-__global__ void __launch_bounds__(kBlock) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls, const T* __restrict__ mf,
-                                                     const T* __restrict__ phi, const T* __restrict__ phib,
-                                                     T* __restrict__ out) {
-  div_flux_row<T, NC, UPWIND, FG>(t, H, hg, cls, mf, phi, phib, out);
-}
-// the same with registers capped for six blocks per SM: measured faster for the
-// FP32 upwind form on the 1.6M-cell Kuhn mesh (29 vs 36 us, 3 components)
-template <typename T, int NC, bool UPWIND, bool FG>
-__global__ void __launch_bounds__(kBlock, 6) k_div_flux_occ(Topo t, Hf H, HfGeo<T> hg, int cls,
-                                                            const T* __restrict__ mf, const T* __restrict__ phi,
-                                                            const T* __restrict__ phib, T* __restrict__ out) {
-  div_flux_row<T, NC, UPWIND, FG>(t, H, hg, cls, mf, phi, phib, out);
 }
 
 // Adjoint.  delta_f = obar_O - obar_N (internal) or obar_O (boundary):
@@ -321,13 +334,14 @@ __global__ void __launch_bounds__(kBlock) k_div_flux_bwd(Topo t, Geo<T> g, int c
 }
 
 // --------------------------------------------------------------- diffusion
-// out_i = sum_f sigma gamma [c_f (phi_N - phi_O) + (grad phi)_f . k_f]   (Eq. nonortho_flux)
-template <typename T, int NC, bool NONORTH, bool FG>
-__global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Hf H, HfGeo<T> hg, int cls, T gamma,
-                                                      const T* __restrict__ phi,
-                                                      const T* __restrict__ phib,
-                                                      const T* __restrict__ grad,
-                                                      T* __restrict__ out) {
+// out_i = sum_f sigma gamma [c_f (phi_N - phi_O) + (grad phi)_f . k_f]   (Eq. nonortho_flux).
+// (c, k) and w_f are read by face id.
+template <typename T, int NC, bool NONORTH, int WK, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_laplacian(Topo t, Hf H, HfGeo<T> hg, int cls, T gamma,
+                                                            const T* __restrict__ phi,
+                                                            const T* __restrict__ phib,
+                                                            const T* __restrict__ grad,
+                                                            T* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc, nb = t.nb;
@@ -341,36 +355,39 @@ __global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Hf H, HfGeo<T> hg,
       for (int d = 0; d < 3; ++d) gi[c][d] = ldg(grad + (c * 3 + d) * nc + i);
   }
   int base, w;
-  hf_row(H, i, base, w);
+  hf_row_w<WK>(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
-    HfChunk<T, NONORTH, true> q;
-    hf_chunk<FG>(H, hg, base, k0, w, q);
-    T pj[4][NC];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) pj[k][c] = q.v[k] >= 0 ? ldg(phi + c * nc + (q.v[k] >> 1)) : T(0);
+    int v[4], f[4];
+    hf_words<true>(H, base, k0, w, v, f);
+    V4<T> ck[4];
+    T wk[4], pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int v = q.v[k];
-      if (v == -1) continue;
-      const V4<T> ck = q.ck[k];
-      if (v >= 0) {
-        const bool nside = v & 1;
-        const int j = v >> 1;
-        const T wf = NONORTH ? q.sw[k].w : T(0);
+      ck[k] = v[k] != -1 ? ld4(hg.ck + f[k]) : V4<T>{T(0), T(0), T(0), T(0)};
+      wk[k] = (NONORTH && v[k] >= 0) ? ld4(hg.sw + f[k]).w : T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pj[k][c] = hf_other(v[k], cls, phi, phib, nc, nb, c, pi[c]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int vk = v[k];
+      if (vk == -1) continue;
+      const V4<T> c4 = ck[k];
+      if (vk >= 0) {
+        const bool nside = vk & 1;
+        const int j = vk >> 1;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
-          T F = ck.x * (pN - pO);
+          T F = c4.x * (pN - pO);
           if (NONORTH) {
             T gk = T(0);
-            const T kk[3] = {ck.y, ck.z, ck.w};
+            const T kk[3] = {c4.y, c4.z, c4.w};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
               const T gj = ldg(grad + (c * 3 + d) * nc + j);
               const T gO = nside ? gj : gi[c][d], gN = nside ? gi[c][d] : gj;
-              gk += (wf * gO + (T(1) - wf) * gN) * kk[d];
+              gk += (wk[k] * gO + (T(1) - wk[k]) * gN) * kk[d];
             }
             F += gk;
           }
@@ -378,10 +395,9 @@ __global__ void __launch_bounds__(kBlock) k_laplacian(Topo t, Hf H, HfGeo<T> hg,
           acc[c] += nside ? -F : F;
         }
       } else {
-        const int b = -2 - v;
-        if (face_kind(t, b, cls) != DIFVM_FACE_FIXED) continue;
+        if (hf_kind(vk, cls) != DIFVM_FACE_FIXED) continue;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += gamma * (ck.x * (ldg(phib + c * nb + b) - pi[c]));
+        for (int c = 0; c < NC; ++c) acc[c] += gamma * (c4.x * (pj[k][c] - pi[c]));
       }
     }
   }
@@ -449,12 +465,12 @@ __global__ void __launch_bounds__(kBlock) k_laplacian_bwd(Topo t, Geo<T> g, int 
 
 // ---------------------------------------------------------------- LDU apply
 // y_i = D_i x_i + sum_{O(f)=i} U_f x_N + sum_{N(f)=i} L_f x_O   (Eq. Ap_H)
-template <typename T, int NC>
-__global__ void __launch_bounds__(kBlock) k_ldu_apply(Topo t, Hf H, const T* __restrict__ D,
-                                                      const T* __restrict__ L,
-                                                      const T* __restrict__ U,
-                                                      const T* __restrict__ x,
-                                                      T* __restrict__ y) {
+template <typename T, int NC, int WK, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_ldu_apply(Topo t, Hf H, const T* __restrict__ D,
+                                                            const T* __restrict__ L,
+                                                            const T* __restrict__ U,
+                                                            const T* __restrict__ x,
+                                                            T* __restrict__ y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.nc) return;
   const int nc = t.nc;
@@ -463,15 +479,10 @@ __global__ void __launch_bounds__(kBlock) k_ldu_apply(Topo t, Hf H, const T* __r
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = d * ldg(x + c * nc + i);
   int base, w;
-  hf_row(H, i, base, w);
+  hf_row_w<WK>(H, i, base, w);
   for (int k0 = 0; k0 < w; k0 += 4) {
     int v[4], fk[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int slot = base + 32 * (k0 + k);
-      v[k] = (k0 + k < w) ? ldg(H.nb + slot) : -1;
-      fk[k] = (k0 + k < w) ? ldg(H.fid + slot) : 0;
-    }
+    hf_words<true>(H, base, k0, w, v, fk);
     T ak[4], xk[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -556,12 +567,88 @@ template <typename T> static HfGeo<T> fgeo(const difvm_mesh* m) {
   return HfGeo<T>{g.Sw, g.ck};
 }
 
+// ------------------------------------------------------------- autotuning
+// The F32 kernels of the uniform tetrahedral layout (four slots per row) come
+// in launch variants that differ in the register budget the compiler must meet:
+// variant 0 lets it choose (one block per SM guaranteed), 1 and 2 force six and
+// eight resident 256-thread blocks per SM.  More resident warps hide more of the
+// gather latency but may spill; which variant wins depends on the operator,
+// the component count and the mesh.  So the first call of each (operator,
+// components, scheme) on a mesh times every variant on that call's own
+// arguments (a forward operator only writes its output, so running it again
+// changes nothing) and the mesh keeps the fastest; later calls launch it.  A
+// first call under stream capture (no timing possible) launches the default
+// variant without recording a choice.  difvm_mesh_autotune switches timing off
+// (every call then launches the default) or clears the kept choices.
+constexpr int kVariants = 3;
+enum { kOpGrad = 1, kOpDiv = 2, kOpLap = 3, kOpLdu = 4 };
+static uint32_t tune_key(int op, int extra, int nc) { return (uint32_t)(op << 8 | extra << 4 | nc); }
+
+static int tuned_variant(const difvm_mesh* m, uint32_t key) {
+  for (const auto& kv : m->tuned)
+    if (kv.first == key) return kv.second;
+  return -1;
+}
+
+template <typename F>
+static difvm_status tuned_launch(difvm_mesh* m, uint32_t key, int dflt, cudaStream_t s, F&& launch) {
+  int var = tuned_variant(m, key);
+  if (var < 0 && m->autotune && !stream_capturing(s)) {
+    constexpr int kReps = 3;
+    cudaEvent_t ev[kVariants][2];
+    for (int v = 0; v < kVariants; ++v)
+      for (int e = 0; e < 2; ++e) DIFVM_CUDA(cudaEventCreate(&ev[v][e]));
+    difvm_status st = DIFVM_OK;
+    for (int v = 0; v < kVariants && st == DIFVM_OK; ++v) {
+      launch(v);                       // first launch of the variant: not timed
+      cudaEventRecord(ev[v][0], s);
+      for (int r = 0; r < kReps; ++r) launch(v);
+      cudaEventRecord(ev[v][1], s);
+      st = check_error("autotune");
+    }
+    float best = 0.f;
+    for (int v = 0; v < kVariants && st == DIFVM_OK; ++v) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(ev[v][1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, ev[v][0], ev[v][1]) != cudaSuccess) {
+        st = set_error(DIFVM_ECUDA, "autotune timing failed");
+        break;
+      }
+      if (var < 0 || ms < best) {
+        best = ms;
+        var = v;
+      }
+    }
+    for (int v = 0; v < kVariants; ++v)
+      for (int e = 0; e < 2; ++e) cudaEventDestroy(ev[v][e]);
+    DIFVM_TRY(st);
+    m->tuned.emplace_back(key, var);
+  }
+  launch(var < 0 ? dflt : var);
+  return DIFVM_OK;
+}
+
 template <typename T>
 difvm_status grad_gauss_t(difvm_mesh_t m, int cls, const void* phi, const void* phib,
                           int ncomp, void* grad, cudaStream_t s) {
-  DIFVM_NC_SWITCH(ncomp, k_grad_gauss<T, NCc, false><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                             m->topo(), m->hf(), hfgeo<T>(m), geo<T>(m), cls, (const T*)phi,
-                             (const T*)phib, (T*)grad));
+  const unsigned B = blocks_for(m->nc, kBlock);
+  const auto args = [&](auto k) {
+    k<<<B, kBlock, 0, s>>>(m->topo(), m->hf(), hfgeo<T>(m), geo<T>(m), cls, (const T*)phi, (const T*)phib,
+                           (T*)grad);
+  };
+  if (sizeof(T) == 4 && m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, DIFVM_TRY(tuned_launch(m, tune_key(kOpGrad, 0, NCc), 0, s, [&](int var) {
+      switch (var) {
+        case 0: args(k_grad_gauss<T, NCc, 4, 1>); break;
+        case 1: args(k_grad_gauss<T, NCc, 4, 6>); break;
+        default: args(k_grad_gauss<T, NCc, 4, 8>); break;
+      }
+    })));
+  } else if (m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, args(k_grad_gauss<T, NCc, 4, 1>));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, args(k_grad_gauss<T, NCc, 0, 1>));
+  }
   return check_launch("grad_gauss");
 }
 template difvm_status grad_gauss_t<float>(difvm_mesh_t, int, const void*, const void*, int, void*,
@@ -577,25 +664,36 @@ static difvm_status grad_gauss_bwd_t(difvm_mesh_t m, int cls, const void* gbar, 
   return check_launch("grad_gauss_bwd");
 }
 
+template <typename T, bool UPWIND>
+static difvm_status div_flux_s(difvm_mesh_t m, int cls, const void* mf, const void* phi, const void* phib,
+                               int ncomp, void* out, cudaStream_t s) {
+  const unsigned B = blocks_for(m->nc, kBlock);
+  const auto args = [&](auto k) {
+    k<<<B, kBlock, 0, s>>>(m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi, (const T*)phib,
+                           (T*)out);
+  };
+  if (sizeof(T) == 4 && m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, DIFVM_TRY(tuned_launch(m, tune_key(kOpDiv, UPWIND, NCc), UPWIND ? 1 : 0, s,
+                                                  [&](int var) {
+      switch (var) {
+        case 0: args(k_div_flux<T, NCc, UPWIND, 4, 1>); break;
+        case 1: args(k_div_flux<T, NCc, UPWIND, 4, 6>); break;
+        default: args(k_div_flux<T, NCc, UPWIND, 4, 8>); break;
+      }
+    })));
+  } else if (m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, args(k_div_flux<T, NCc, UPWIND, 4, 1>));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, args(k_div_flux<T, NCc, UPWIND, 0, 1>));
+  }
+  return check_launch("div_flux");
+}
 template <typename T>
 static difvm_status div_flux_t(difvm_mesh_t m, int scheme, int cls, const void* mf,
                                const void* phi, const void* phib, int ncomp, void* out,
                                cudaStream_t s) {
-  const unsigned B = blocks_for(m->nc, kBlock);
-  if (scheme == DIFVM_DIV_UPWIND && sizeof(T) == 4) {
-    DIFVM_NC_SWITCH(ncomp, k_div_flux_occ<T, NCc, true, true><<<B, kBlock, 0, s>>>(
-                               m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi,
-                               (const T*)phib, (T*)out));
-  } else if (scheme == DIFVM_DIV_UPWIND) {
-    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, true, true><<<B, kBlock, 0, s>>>(
-                               m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi,
-                               (const T*)phib, (T*)out));
-  } else {
-    DIFVM_NC_SWITCH(ncomp, k_div_flux<T, NCc, false, true><<<B, kBlock, 0, s>>>(
-                               m->topo(), m->hf(), fgeo<T>(m), cls, (const T*)mf, (const T*)phi,
-                               (const T*)phib, (T*)out));
-  }
-  return check_launch("div_flux");
+  return scheme == DIFVM_DIV_UPWIND ? div_flux_s<T, true>(m, cls, mf, phi, phib, ncomp, out, s)
+                                    : div_flux_s<T, false>(m, cls, mf, phi, phib, ncomp, out, s);
 }
 
 template <typename T>
@@ -614,20 +712,35 @@ static difvm_status div_flux_bwd_t(difvm_mesh_t m, int scheme, int cls, const vo
   return check_launch("div_flux_bwd");
 }
 
+template <typename T, bool NONORTH>
+static difvm_status laplacian_s(difvm_mesh_t m, int cls, double gamma, const void* phi, const void* phib,
+                                const void* grad, int ncomp, void* out, cudaStream_t s) {
+  const unsigned B = blocks_for(m->nc, kBlock);
+  const auto args = [&](auto k) {
+    k<<<B, kBlock, 0, s>>>(m->topo(), m->hf(), fgeo<T>(m), cls, (T)gamma, (const T*)phi, (const T*)phib,
+                           (const T*)grad, (T*)out);
+  };
+  if (sizeof(T) == 4 && m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, DIFVM_TRY(tuned_launch(m, tune_key(kOpLap, NONORTH, NCc), 0, s, [&](int var) {
+      switch (var) {
+        case 0: args(k_laplacian<T, NCc, NONORTH, 4, 1>); break;
+        case 1: args(k_laplacian<T, NCc, NONORTH, 4, 6>); break;
+        default: args(k_laplacian<T, NCc, NONORTH, 4, 8>); break;
+      }
+    })));
+  } else if (m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, args(k_laplacian<T, NCc, NONORTH, 4, 1>));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, args(k_laplacian<T, NCc, NONORTH, 0, 1>));
+  }
+  return check_launch("laplacian");
+}
 template <typename T>
 static difvm_status laplacian_t(difvm_mesh_t m, int cls, double gamma, const void* phi,
                                 const void* phib, const void* grad, int ncomp, void* out,
                                 cudaStream_t s) {
-  if (grad) {
-    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, true, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), m->hf(), fgeo<T>(m), cls, (T)gamma, (const T*)phi,
-                               (const T*)phib, (const T*)grad, (T*)out));
-  } else {
-    DIFVM_NC_SWITCH(ncomp, k_laplacian<T, NCc, false, true><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                               m->topo(), m->hf(), fgeo<T>(m), cls, (T)gamma, (const T*)phi,
-                               (const T*)phib, (const T*)nullptr, (T*)out));
-  }
-  return check_launch("laplacian");
+  return grad ? laplacian_s<T, true>(m, cls, gamma, phi, phib, grad, ncomp, out, s)
+              : laplacian_s<T, false>(m, cls, gamma, phi, phib, nullptr, ncomp, out, s);
 }
 
 template <typename T>
@@ -646,8 +759,21 @@ difvm_status ldu_apply_t(difvm_mesh_t m, const void* D, const void* L, const voi
   const T* Lp = (const T*)L;
   const T* Up = U ? (const T*)U : Lp;
   if (transpose) std::swap(Lp, Up);
-  DIFVM_NC_SWITCH(ncomp, k_ldu_apply<T, NCc><<<blocks_for(m->nc, kBlock), kBlock, 0, s>>>(
-                             m->topo(), m->hf(), (const T*)D, Lp, Up, (const T*)x, (T*)y));
+  const unsigned B = blocks_for(m->nc, kBlock);
+  const auto args = [&](auto k) { k<<<B, kBlock, 0, s>>>(m->topo(), m->hf(), (const T*)D, Lp, Up, (const T*)x, (T*)y); };
+  if (sizeof(T) == 4 && m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, DIFVM_TRY(tuned_launch(m, tune_key(kOpLdu, 0, NCc), 0, s, [&](int var) {
+      switch (var) {
+        case 0: args(k_ldu_apply<T, NCc, 4, 1>); break;
+        case 1: args(k_ldu_apply<T, NCc, 4, 6>); break;
+        default: args(k_ldu_apply<T, NCc, 4, 8>); break;
+      }
+    })));
+  } else if (m->hf_w == 4) {
+    DIFVM_NC_SWITCH(ncomp, args(k_ldu_apply<T, NCc, 4, 1>));
+  } else {
+    DIFVM_NC_SWITCH(ncomp, args(k_ldu_apply<T, NCc, 0, 1>));
+  }
   return check_launch("ldu_apply");
 }
 template difvm_status ldu_apply_t<float>(difvm_mesh_t, const void*, const void*, const void*,
@@ -769,4 +895,25 @@ extern "C" difvm_status difvm_laplacian_apply_bwd(difvm_mesh_t m, difvm_prec pre
   if (xbar && !tmp) return set_error(DIFVM_EINVAL, "x_bar needs a [ncomp][nc] scratch buffer");
   return DIFVM_PREC_DISPATCH(prec, ldu_apply_bwd_t, m, D, L, U, x, ybar, ncomp, xbar, Dbar, Lbar,
                              Ubar, tmp, (cudaStream_t)stream);
+}
+
+extern "C" difvm_status difvm_mesh_autotune(difvm_mesh_t m, int mode) {
+  DIFVM_TRY(check_mesh(m));
+  if (mode < 0 || mode > 2) return set_error(DIFVM_EINVAL, "autotune mode must be 0, 1 or 2 (got %d)", mode);
+  if (mode == 2) m->tuned.clear();
+  m->autotune = mode != 0;
+  return DIFVM_OK;
+}
+
+extern "C" difvm_status difvm_mesh_tuning(difvm_mesh_t m, uint32_t* keys, int32_t* variants, int cap,
+                                          int32_t* count) {
+  DIFVM_TRY(check_mesh(m));
+  if (!count || cap < 0 || (cap > 0 && (!keys || !variants))) return set_error(DIFVM_EINVAL, "bad output arrays");
+  const int n = (int)m->tuned.size();
+  for (int k = 0; k < n && k < cap; ++k) {
+    keys[k] = m->tuned[k].first;
+    variants[k] = m->tuned[k].second;
+  }
+  *count = n;
+  return DIFVM_OK;
 }

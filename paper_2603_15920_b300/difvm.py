@@ -91,6 +91,8 @@ _SIGS = {
     "difvm_mesh_create": [_vp, _vp],
     "difvm_mesh_permutation": [_vp, _vp, _vp, _vp],
     "difvm_mesh_info": [_vp, _vp],
+    "difvm_mesh_autotune": [_vp, _i],
+    "difvm_mesh_tuning": [_vp, _vp, _vp, _i, _vp],
     "difvm_grad_gauss": [_vp, _i, _i, _vp, _vp, _i, _vp, _vp],
     "difvm_grad_gauss_bwd": [_vp, _i, _i, _vp, _i, _vp, _vp, _vp],
     "difvm_div_flux": [_vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp],
@@ -313,6 +315,21 @@ class Mesh:
         out = np.empty_like(b) if isinstance(b, np.ndarray) else torch.empty_like(b)
         out[..., self.bnd_old_of_new] = b
         return out
+
+
+def difvm_mesh_autotune(mesh, mode):
+    """0: face operators launch their default variant; 1: first-use timing on
+    (the default); 2: forget the kept choices."""
+    _check(lib().difvm_mesh_autotune(_mh(mesh), int(mode)))
+
+
+def difvm_mesh_tuning(mesh):
+    """The kept face-operator variants: {(operator, option, components): variant}."""
+    cap = 64
+    keys, var, n = (C.c_uint32 * cap)(), (C.c_int32 * cap)(), C.c_int32()
+    _check(lib().difvm_mesh_tuning(_mh(mesh), keys, var, cap, C.byref(n)))
+    return {(int(keys[k]) >> 8, (int(keys[k]) >> 4) & 15, int(keys[k]) & 15): int(var[k])
+            for k in range(min(n.value, cap))}
 
 
 def _mh(mesh):

@@ -426,3 +426,39 @@ def test_full_size_operators(kuhn64, dt):
         dm, cuda(dm.to_cells(Dg), dt), cuda(np.where(flip, U[fo], L[fo]), dt),
         cuda(np.where(flip, L[fo], U[fo]), dt), cuda(dm.to_cells(x), dt)).double().cpu().numpy()), ref)
     assert max(errs.values()) < TOL[dt], errs
+
+
+# ------------------------------------------------------------- autotuning
+def test_autotuned_variants_agree_and_are_kept():
+    # the F32 face operators of a tetrahedral mesh time their launch variants on
+    # first use; every variant computes the same sums in the same order
+    m = get("kuhn10")[0]
+    dm = D.Mesh(m)
+    D.difvm_mesh_autotune(dm, 0)
+    f = mg.random_fields(m, 9)
+    dt = torch.float32
+    phi, U = cuda(dm.to_cells(f["U"][:1]), dt), cuda(dm.to_cells(f["U"]), dt)
+    phib, Ub = cuda(dm.to_bnd(f["U_b"][:1]), dt), cuda(dm.to_bnd(f["U_b"]), dt)
+    mf = cuda(dm.to_faces(f["m"]), dt)
+    g = D.difvm_grad_gauss(dm, D.BC_ALL_FIXED, phi, phib)
+    rng = np.random.default_rng(3)
+    Dg, L = cuda(rng.standard_normal(dm.nc) + 5.0, dt), cuda(rng.standard_normal(dm.ni), dt)
+    ops = {
+        (1, 0, 1): lambda: D.difvm_grad_gauss(dm, D.BC_VELOCITY, phi, phib),
+        (1, 0, 3): lambda: D.difvm_grad_gauss(dm, D.BC_VELOCITY, U, Ub),
+        (2, 1, 3): lambda: D.difvm_div_flux(dm, D.DIV_UPWIND, D.BC_VELOCITY, mf, U, Ub),
+        (2, 0, 3): lambda: D.difvm_div_flux(dm, D.DIV_LINEAR, D.BC_PRESSURE, mf, U, Ub),
+        (3, 1, 1): lambda: D.difvm_laplacian(dm, D.BC_ALL_FIXED, 0.3, phi, phib, g),
+        (3, 0, 3): lambda: D.difvm_laplacian(dm, D.BC_VELOCITY, 0.3, U, Ub),
+        (4, 0, 3): lambda: D.difvm_laplacian_apply(dm, Dg, L, None, U),
+    }
+    ref = {k: fn().clone() for k, fn in ops.items()}
+    assert D.difvm_mesh_tuning(dm) == {}
+    D.difvm_mesh_autotune(dm, 2)
+    for k, fn in ops.items():
+        first, second = fn().clone(), fn().clone()
+        assert torch.equal(first, ref[k]) and torch.equal(second, ref[k]), k
+    kept = D.difvm_mesh_tuning(dm)
+    assert set(kept) >= set(ops) and all(0 <= v <= 2 for v in kept.values()), kept
+    with pytest.raises(D.DifvmError):
+        D.difvm_mesh_autotune(dm, 3)
