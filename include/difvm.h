@@ -172,6 +172,17 @@ difvm_status difvm_mesh_autotune(difvm_mesh_t, int mode);
  * variants[k] in 0..2; at most cap entries are written, *count gets the
  * number kept. */
 difvm_status difvm_mesh_tuning(difvm_mesh_t, uint32_t* keys, int32_t* variants, int cap, int32_t* count);
+/* Multigrid V-cycle launch shape (DIFVM_PRECOND_AMG): levels of fewer than
+ * tail_rows rows, and the coarsest dense solve, run as one cooperative kernel
+ * (phases separated by grid barriers whose waits are bounded; a wait that runs
+ * out ends the solve with DIFVM_ETIMEOUT) of tail_bps blocks per SM, instead
+ * of five kernels per level; 0 rows: every level its own kernels.  -1 keeps
+ * the library's choice (0 rows: on the B300 the per-level kernels, chained by
+ * programmatic dependent launch, were faster; 2 blocks per SM).  Both forms
+ * compute the same sums in the same order.  Takes effect at the next solve
+ * that builds the multigrid operators.  EINVAL on tail_rows < -1 or tail_bps
+ * 0 / < -1. */
+difvm_status difvm_mesh_amg_config(difvm_mesh_t, int tail_rows, int tail_bps);
 /* Maps between input and internal numbering, HOST outputs (any may be NULL):
  *   cell_new_of_old[n_cells], face_old_of_new[n_faces],
  *   face_flip[n_faces] (1 where the internal face was re-oriented: its S, and

@@ -343,13 +343,15 @@ difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
 
 // ---------------------------------------------------------- workspace layout
 // [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials |
-//  tickets | flags]; a batched mesh has one state and one ticket per case
+//  tickets | flags | fused-level descriptors | barrier]; a batched mesh has one state and
+//  one ticket per case
 struct AmgLayout {
   size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], E[kAmgMaxLevels],
-      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, flag, total;
+      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, flag, tail, bar, total;
 };
 
 static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
+constexpr int kBarGroupsL = 16;   // counters of the fused kernel's grid barrier (kBarGroups)
 
 // the CG kernels and the level-0 sweep with r.z: grid-stride, one wave (their
 // grid reductions finish once instead of once per wave of blocks)
@@ -382,6 +384,8 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
   A.part = take(nblk * kMaxParts * sizeof(double));
   A.ticket = take((size_t)(m->seg ? m->ncases : 2) * sizeof(unsigned));
   A.flag = take(4 * sizeof(int));
+  A.tail = take(kAmgMaxLevels * 256);   // level descriptors of the fused coarse-level kernel
+  A.bar = take((2 + kBarGroupsL) * 128); // its grid barrier (one 128-byte line per counter)
   A.total = o;
   return A;
 }
@@ -748,6 +752,244 @@ __global__ void __launch_bounds__(1024) k_amg_coarse(int n, const float* Ainv, c
   }
 }
 
+// -------------------------------------------- fused coarse levels (one launch)
+// On request (difvm_mesh_amg_config), levels of fewer than a given number of
+// rows, and the coarsest dense solve, run in one cooperative kernel: every
+// pre-smoothing, residual, restriction, dense solve and post-smoothing sweep
+// of those levels is a phase of the whole grid, phases separated by a grid
+// barrier, instead of one launch per sweep.  The phases compute exactly what
+// the per-level kernels compute, in the same order per row.  (Measured slower
+// than the per-level kernels on the B300, hence off by default: see
+// amg_tail_plan.)
+constexpr int kTB = 512;            // threads per block of the fused kernel
+constexpr int kTailMaxLev = kAmgMaxLevels;
+
+// one level as the fused kernel sees it (a copy lives in the workspace)
+template <typename T> struct TailLev {
+  AmgLev L;
+  const T *D, *rD, *Lv;   // diagonal, its reciprocal, sliced-ELL values
+  T *r, *y, *u;           // right-hand side; work vectors (y ends as the output)
+  int tpr, rl;            // lanes per row of the sweeps; per aggregate of the restriction
+};
+static_assert(sizeof(TailLev<double>) <= 256 && sizeof(TailLev<float>) <= 256 &&
+                  sizeof(TailLev<double>) % sizeof(int) == 0 && sizeof(TailLev<float>) % sizeof(int) == 0,
+              "a level descriptor must fit its 256-byte workspace slot, in whole ints");
+template <typename T> struct TailArgs {
+  const TailLev<T>* lev;  // [nlev]: the first fused level .. the coarsest
+  int nlev;
+  const float* Ainv;      // coarsest dense inverse
+  const int* done;        // the CG (or every case of a batch) has converged
+  unsigned* bar;          // the grid barrier's words (see tail_barrier)
+  KState* st;             // solver states, marked ETIMEOUT if a barrier wait runs out
+  int nst;
+  int* all_done;          // batched solves: the all-cases-converged flag, or null
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier of a cooperative launch (every block resident), two-level so that
+// no counter takes more than ~32 arrivals: block b arrives on group counter
+// b % kBarGroups; the last of a group arrives on the root counter; the last at
+// the root resets the root and bumps the generation (group counters are reset
+// by their last arriver).  Waiters spin on the generation, at most ~4M polls
+// (about a second).  bar: [0] generation, [1] root count, [2..] group counts,
+// each on its own 128-byte line.  Returns false in every thread of a block
+// whose wait ran out.
+constexpr int kBarGroups = kBarGroupsL;
+constexpr int kBarStride = 32;   // unsigned per 128-byte line
+__device__ __forceinline__ bool tail_barrier(unsigned* bar, unsigned& gen) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = gen;
+    const unsigned nb = gridDim.x, grp = blockIdx.x % kBarGroups;
+    const unsigned ngrp = nb < kBarGroups ? nb : kBarGroups;
+    const unsigned in_grp = nb / kBarGroups + (grp < nb % kBarGroups ? 1u : 0u);
+    __threadfence();
+    unsigned* gc = bar + (2 + grp) * kBarStride;
+    bool last = false;
+    if (atomicAdd(gc, 1u) == in_grp - 1) {
+      *gc = 0u;
+      __threadfence();
+      last = atomicAdd(bar + kBarStride, 1u) == ngrp - 1;
+    }
+    if (last) {
+      bar[kBarStride] = 0u;
+      __threadfence();
+      atomicExch(bar, g + 1);
+    } else {
+      int spins = 0;
+      while (ld_acquire_u32(bar) == g) {
+        if (++spins > (1 << 22)) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    gen = g + 1;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Phases: grid-stride loops over whole warps of TPR-lane rows.  Vectors the
+// kernel itself writes (r, y, u of the fused levels) are read through L2
+// (__ldcg), since another block may have written them in the previous phase.
+template <typename T, int TPR, class F>
+__device__ __forceinline__ void tail_rows(int n, F&& body) {
+  const int nvt = (int)(((int64_t)n * TPR + 31) & ~(int64_t)31);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nvt; g += gridDim.x * blockDim.x)
+    body(g / TPR, g % TPR);
+}
+
+template <typename T, int TPR>
+__device__ void tail_pre(const TailLev<T>& P) {
+  const T w1 = (T)kAmgW1, w2 = (T)kAmgW2;
+  const Mat<T> A{};
+  tail_rows<T, TPR>(P.L.n, [&](int i, int t) {
+    const bool ok = i < P.L.n;
+    auto x1 = [&](int j) { return w1 * P.rD[j] * __ldcg(P.r + j); };
+    const T ax = lev_row<T, TPR>(A, P.L, P.D, P.Lv, i, t, ok, x1);
+    if (ok && t == 0) P.y[i] = x1(i) + w2 * P.rD[i] * (__ldcg(P.r + i) - ax);
+  });
+}
+template <typename T, int TPR>
+__device__ void tail_resid(const TailLev<T>& P) {
+  const Mat<T> A{};
+  tail_rows<T, TPR>(P.L.n, [&](int i, int t) {
+    const bool ok = i < P.L.n;
+    auto xy = [&](int j) { return __ldcg(P.y + j); };
+    const T ay = lev_row<T, TPR>(A, P.L, P.D, P.Lv, i, t, ok, xy);
+    if (ok && t == 0) P.u[i] = __ldcg(P.r + i) - ay;
+  });
+}
+template <typename T, int RL>
+__device__ void tail_restrict(const TailLev<T>& P, int n1, T* rc) {
+  tail_rows<T, RL>(n1, [&](int K, int t) {
+    T s = T(0);
+    if (K < n1) {
+      const int c1 = P.L.ch_ptr[K + 1];
+      for (int c = P.L.ch_ptr[K] + t; c < c1; c += RL) s += __ldcg(P.u + P.L.ch_idx[c]);
+    }
+#pragma unroll
+    for (int d = RL / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (K < n1 && t == 0) rc[K] = s;
+  });
+}
+template <typename T, int TPR>
+__device__ void tail_post1(const TailLev<T>& P, const T* xc) {
+  const T w = (T)kAmgW2, sc = (T)kAmgScale;
+  const Mat<T> A{};
+  tail_rows<T, TPR>(P.L.n, [&](int i, int t) {
+    const bool ok = i < P.L.n;
+    auto z = [&](int j, int a) { return __ldcg(P.y + j) + sc * __ldcg(xc + a); };
+    const T az = lev_row<T, TPR, true>(A, P.L, P.D, P.Lv, i, t, ok, z);
+    if (ok && t == 0) P.u[i] = z(i, P.L.agg[i]) + w * P.rD[i] * (__ldcg(P.r + i) - az);
+  });
+}
+template <typename T, int TPR>
+__device__ void tail_post2(const TailLev<T>& P) {
+  const T om = (T)kAmgW1;
+  const Mat<T> A{};
+  tail_rows<T, TPR>(P.L.n, [&](int i, int t) {
+    const bool ok = i < P.L.n;
+    auto xu = [&](int j) { return __ldcg(P.u + j); };
+    const T au = lev_row<T, TPR>(A, P.L, P.D, P.Lv, i, t, ok, xu);
+    if (ok && t == 0) P.y[i] = __ldcg(P.u + i) + om * P.rD[i] * (__ldcg(P.r + i) - au);
+  });
+}
+// coarsest level: y = A^{-1} r, one warp per row, lanes summed by a fixed tree
+template <typename T>
+__device__ void tail_coarse(const TailLev<T>& P, const float* Ainv) {
+  constexpr int NJ = kAmgCoarsest / 32;
+  const int n = P.L.n, lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = wg; i < n; i += nw) {
+    float a[NJ], x[NJ];
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+      const int j = lane + 32 * q;
+      a[q] = j < n ? Ainv[i * n + j] : 0.f;
+      x[q] = j < n ? (float)__ldcg(P.r + j) : 0.f;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) s += a[q] * x[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) P.y[i] = (T)s;
+  }
+}
+
+#define DIFVM_TAIL_TPR(tpr, F, ...) \
+  do {                              \
+    if ((tpr) == 2) F<T, 2>(__VA_ARGS__); \
+    else if ((tpr) == 4) F<T, 4>(__VA_ARGS__); \
+    else F<T, 8>(__VA_ARGS__);      \
+  } while (0)
+
+template <typename T>
+__global__ void __launch_bounds__(kTB, 2) k_amg_tail(TailArgs<T> P) {
+  if (*P.done) return;
+  // the level descriptors, staged once in shared memory
+  __shared__ __align__(16) TailLev<T> lev[kTailMaxLev];
+  {
+    const int nw = P.nlev * (int)(sizeof(TailLev<T>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(P.lev);
+    int* dst = reinterpret_cast<int*>(lev);
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
+  unsigned gen = 0;
+  if (threadIdx.x == 0) gen = ld_acquire_u32(P.bar);
+  const int nl = P.nlev;
+  bool ok = true;
+  for (int k = 0; k + 1 < nl && ok; ++k) {   // down: smooth, residual, restrict
+    const TailLev<T>& L = lev[k];
+    DIFVM_TAIL_TPR(L.tpr, tail_pre, L);
+    if (!(ok = tail_barrier(P.bar, gen))) break;
+    DIFVM_TAIL_TPR(L.tpr, tail_resid, L);
+    if (!(ok = tail_barrier(P.bar, gen))) break;
+    if (L.rl == 1) tail_restrict<T, 1>(L, lev[k + 1].L.n, lev[k + 1].r);
+    else tail_restrict<T, 8>(L, lev[k + 1].L.n, lev[k + 1].r);
+    ok = tail_barrier(P.bar, gen);
+  }
+  if (ok) {
+    tail_coarse<T>(lev[nl - 1], P.Ainv);
+    ok = nl == 1 || tail_barrier(P.bar, gen);
+  }
+  for (int k = nl - 2; k >= 0 && ok; --k) {  // up: corrected sweep, second sweep
+    const TailLev<T>& L = lev[k];
+    DIFVM_TAIL_TPR(L.tpr, tail_post1, L, (const T*)lev[k + 1].y);
+    if (!(ok = tail_barrier(P.bar, gen))) break;
+    DIFVM_TAIL_TPR(L.tpr, tail_post2, L);
+    if (k > 0) ok = tail_barrier(P.bar, gen);
+  }
+  if (!ok && threadIdx.x == 0) {
+    for (int k = 0; k < P.nst; ++k) {
+      P.st[k].status = DIFVM_ETIMEOUT;
+      P.st[k].done = 1;
+    }
+    if (P.all_done) *P.all_done = 1;
+  }
+}
+#undef DIFVM_TAIL_TPR
+
+// copies the level descriptors into the workspace (a kernel, so that it also
+// works under stream capture)
+template <typename T> struct TailLevs { TailLev<T> lev[kTailMaxLev]; };
+template <typename T>
+__global__ void k_amg_tail_desc(TailLevs<T> d, int n, TailLev<T>* out) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) out[k] = d.lev[k];
+}
+
 // --------------------------------------------------------------- CG kernels
 // r = b - A x; bb, rr; convergence at the start; `gate` (may be null): when
 // *gate != 0 the solve is closed at once (the outer refinement loop is done)
@@ -835,9 +1077,24 @@ struct AmgRun {
   // batched solves: the V-cycle's early exit reads this flag (1 once every case
   // has converged) and level 0 ends with a plain sweep (the per-case r.z follows)
   const int* seg_done = nullptr;
+  // levels tail_from .. nlev-1 run in one cooperative launch of tail_grid
+  // blocks (tail_from == 0: none)
+  int tail_from = 0;
+  int tail_grid = 0;
   T* vec(int k) const { return (T*)(ws + Ly.vec[k]); }
   T* at(size_t off) const { return (T*)(ws + off); }
 };
+
+// lanes per row of a level's sweeps: one on level 0 (the mesh's ELL); on a
+// coarser level (never one lane: lev_row<T, 1> reads the mesh's ELL) two for
+// large levels, 4-8 for small levels, whose sweeps are latency-bound chains of
+// dependent loads (measured on the 1.6M-cell Kuhn mesh: 2 lanes on its
+// 327k-row level 1 beat 4 and 8 by 2-7% of the step)
+static int amg_tpr(const AmgLev& L, int l) {
+  if (l == 0) return 1;
+  if (L.n >= kAmgBigLevel) return 2;
+  return L.nslots > 8 * L.n ? 8 : 4;
+}
 
 // coarse operators of every level from the level-0 matrix (D, L symmetric)
 template <typename T>
@@ -864,18 +1121,83 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
   const AmgLev& Lc = H->lev[H->nlev - 1];
   if (Lc.n > kAmgCoarsest) return set_error(DIFVM_EINVAL, "AMG: coarsest level has %d cells", Lc.n);
   k_amg_dense_inv<T><<<1, 512, 0, st>>>(Lc, D, Lv, (float*)(R.ws + R.Ly.inv));
-  return check_launch("amg_dense_inv");
+  DIFVM_TRY(check_launch("amg_dense_inv"));
+  if (R.tail_from > 0) {
+    TailLevs<T> d;
+    const int nl = H->nlev - R.tail_from;
+    for (int k = 0; k < nl; ++k) {
+      const int l = R.tail_from + k;
+      const AmgLev& L = H->lev[l];
+      TailLev<T>& t = d.lev[k];
+      t.L = L;
+      t.D = R.at(R.Ly.D[l]);
+      t.rD = R.at(R.Ly.rD[l]);
+      t.Lv = R.at(R.Ly.E[l]);
+      t.r = R.at(R.Ly.r[l]);
+      t.y = R.at(R.Ly.a[l]);
+      t.u = R.at(R.Ly.b[l]);
+      t.tpr = amg_tpr(L, l);
+      t.rl = l + 1 < H->nlev && H->lev[l + 1].n >= kAmgBigLevel / 4 ? 1 : 8;
+    }
+    k_amg_tail_desc<T><<<1, 32, 0, st>>>(d, nl, (TailLev<T>*)(R.ws + R.Ly.tail));
+    DIFVM_TRY(check_launch("amg_tail_desc"));
+    DIFVM_CUDA(cudaMemsetAsync(R.ws + R.Ly.bar, 0, (2 + kBarGroups) * 128, st));
+  }
+  return DIFVM_OK;
 }
 
-// lanes per row of a level's sweeps: one on level 0 (the mesh's ELL); on a
-// coarser level (never one lane: lev_row<T, 1> reads the mesh's ELL) two for
-// large levels, 4-8 for small levels, whose sweeps are latency-bound chains of
-// dependent loads (measured on the 1.6M-cell Kuhn mesh: 2 lanes on its
-// 327k-row level 1 beat 4 and 8 by 2-7% of the step)
-static int amg_tpr(const AmgLev& L, int l) {
-  if (l == 0) return 1;
-  if (L.n >= kAmgBigLevel) return 2;
-  return L.nslots > 8 * L.n ? 8 : 4;
+// Levels below m->amg_tail_rows rows (and the coarsest solve) run in the fused
+// kernel, with at most m->amg_tail_bps blocks per SM (default 2, at most its
+// occupancy).  Off by default: on the 1.6M-cell Kuhn cavity the per-level
+// kernels, chained by programmatic dependent launch, take 16.0 ms per PISO
+// step against 17.0-19.2 ms with any range of levels fused (barrier and
+// cooperative-launch costs exceed the launch latency they save).
+static void amg_tail_plan(const difvm_mesh* m, const AmgHier* H, int elt, int& from, int& grid) {
+  from = 0;
+  grid = 0;
+  const int mrows = m->amg_tail_rows >= 0 ? m->amg_tail_rows : 0;
+  const int mbps = m->amg_tail_bps > 0 ? m->amg_tail_bps : 2;
+  if (H->nlev < 2 || mrows <= 0) return;
+  for (int l = 1; l < H->nlev; ++l)
+    if (H->lev[l].n < mrows) {
+      from = l;
+      break;
+    }
+  if (from == 0) return;
+  int bps = 0;
+  const cudaError_t e = elt == 8
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_amg_tail<double>, kTB, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_amg_tail<float>, kTB, 0);
+  if (e != cudaSuccess || bps < 1) {
+    from = 0;   // cannot be co-resident: keep the per-level kernels
+    return;
+  }
+  grid = std::min(bps, mbps) * m->num_sms;
+}
+
+template <typename T>
+static void amg_tail_launch(const AmgRun<T>& R, const int* done, KState* st, int nst, int* all_done,
+                            cudaStream_t s) {
+  TailArgs<T> a;
+  a.lev = (const TailLev<T>*)(R.ws + R.Ly.tail);
+  a.nlev = R.H->nlev - R.tail_from;
+  a.Ainv = (const float*)(R.ws + R.Ly.inv);
+  a.done = done;
+  a.bar = (unsigned*)(R.ws + R.Ly.bar);
+  a.st = st;
+  a.nst = nst;
+  a.all_done = all_done;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(R.tail_grid);
+  cfg.blockDim = dim3(kTB);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;   // every block resident: the barriers complete
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_amg_tail<T>, a);   // an error is left for check_error
+  count_launch();
 }
 
 template <typename T, int TPR>
@@ -911,6 +1233,12 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const AmgHier* H = R.H;
   const AmgLev& L = H->lev[l];
   const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
+  if (R.tail_from > 0 && l == R.tail_from) {
+    KState* st = (KState*)(R.ws + R.Ly.st);
+    amg_tail_launch(R, done, R.seg_done ? st : w.st, R.seg_done ? R.m->ncases : 1,
+                    R.seg_done ? const_cast<int*>(R.seg_done) : nullptr, s);
+    return;
+  }
   const bool fine = l == 0;
   const T* D = fine ? R.A.D : R.at(R.Ly.D[l]);
   const T* rD = R.at(R.Ly.rD[l]);
@@ -1011,6 +1339,7 @@ static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws
   if (!ws || wsbytes < R.Ly.total)
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes, R.Ly.total);
   R.G = amg_grid(m);
+  amg_tail_plan(m, H, (int)sizeof(T), R.tail_from, R.tail_grid);
   T* val = R.at(R.Ly.val);
   if (reuse) {
     R.A = Mat<T>{D, m->ell(), val};
@@ -1535,3 +1864,14 @@ difvm_status amg_refine(difvm_mesh* m, const difvm_solve_opts* o, const float* D
 }
 
 }  // namespace difvm
+
+using namespace difvm;
+
+extern "C" difvm_status difvm_mesh_amg_config(difvm_mesh_t m, int tail_rows, int tail_bps) {
+  DIFVM_TRY(check_mesh(m));
+  if (tail_rows < -1 || tail_bps < -1 || tail_bps == 0)
+    return set_error(DIFVM_EINVAL, "bad multigrid configuration (%d, %d)", tail_rows, tail_bps);
+  m->amg_tail_rows = tail_rows;
+  m->amg_tail_bps = tail_bps;
+  return DIFVM_OK;
+}

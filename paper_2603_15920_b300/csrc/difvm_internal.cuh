@@ -250,6 +250,9 @@ struct difvm_mesh {
   // key -> variant, and whether timing is allowed
   std::vector<std::pair<uint32_t, int>> tuned;
   int autotune = 1;
+  // multigrid: levels below amg_tail_rows rows run in one fused launch of
+  // amg_tail_bps blocks per SM (-1: the library's choice)
+  int amg_tail_rows = -1, amg_tail_bps = -1;
   difvm::V4<double>* hf_sw64 = nullptr;
   difvm::V4<float>* hf_sw32 = nullptr;
 

@@ -92,6 +92,7 @@ _SIGS = {
     "difvm_mesh_permutation": [_vp, _vp, _vp, _vp],
     "difvm_mesh_info": [_vp, _vp],
     "difvm_mesh_autotune": [_vp, _i],
+    "difvm_mesh_amg_config": [_vp, _i, _i],
     "difvm_mesh_tuning": [_vp, _vp, _vp, _i, _vp],
     "difvm_grad_gauss": [_vp, _i, _i, _vp, _vp, _i, _vp, _vp],
     "difvm_grad_gauss_bwd": [_vp, _i, _i, _vp, _i, _vp, _vp, _vp],
@@ -330,6 +331,12 @@ def difvm_mesh_tuning(mesh):
     _check(lib().difvm_mesh_tuning(_mh(mesh), keys, var, cap, C.byref(n)))
     return {(int(keys[k]) >> 8, (int(keys[k]) >> 4) & 15, int(keys[k]) & 15): int(var[k])
             for k in range(min(n.value, cap))}
+
+
+def difvm_mesh_amg_config(mesh, tail_rows=-1, tail_bps=-1):
+    """Levels below tail_rows rows run as one fused cooperative kernel of
+    tail_bps blocks per SM (0 rows: none; -1: the library's choice)."""
+    _check(lib().difvm_mesh_amg_config(_mh(mesh), int(tail_rows), int(tail_bps)))
 
 
 def _mh(mesh):

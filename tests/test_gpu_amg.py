@@ -214,3 +214,40 @@ def test_batched_multigrid_limits():
                      (D.F64, D.solve_opts(D.BICGSTAB, 1e-10, precond=D.PRECOND_AMG))):
         with pytest.raises(D.DifvmError):
             D.Piso(dm, prec, D.piso_opts(0.02, 0.05, 2, 3, solve_p=sp))
+
+
+@pytest.mark.parametrize("prec,refine", [(D.F64, 0), (D.F32, 1)])
+def test_fused_coarse_levels_match_per_level_kernels(prec, refine):
+    # the levels below the fused-kernel threshold run as phases of one cooperative
+    # launch; each phase computes what its per-level kernel computes, in the same order
+    m = mg.shuffle(mg.kuhn_cube(16, 0.2, 12), 13)
+    dm = D.Mesh(m)
+    om, Dg, Lg = _pressure_matrix(m, 7, pin=5)
+    b = np.random.default_rng(8).normal(size=m.n_cells)
+    b -= b.mean()
+    out = {}
+    for rows in (0, 100000, 2000):       # per-level kernels; every coarse level fused; only the smallest
+        D.difvm_mesh_amg_config(dm, rows, -1)
+        st, info, x = _solve(dm, m, Dg, Lg, b, D.PRECOND_AMG, prec=prec, refine=refine,
+                             tol=1e-12 if prec == D.F64 else 1e-10)
+        assert st == D.OK, info
+        out[rows] = (info["iters"], x)
+    assert out[0][0] == out[100000][0] == out[2000][0]
+    assert np.array_equal(out[0][1], out[100000][1]) and np.array_equal(out[0][1], out[2000][1])
+    with pytest.raises(D.DifvmError):
+        D.difvm_mesh_amg_config(dm, 100, 0)
+
+
+def test_fused_coarse_levels_batched_match_per_level_kernels():
+    ms = [mg.kuhn_cube(n, 0.2, 30 + n) for n in (5, 9, 7)]
+    u, cs = mg.batch(ms)
+    dmu = D.Mesh(u, case_cell_start=cs)
+    om, Dg, Lg = _pressure_matrix(u, 9)
+    b = np.random.default_rng(10).normal(size=u.n_cells)
+    xs = []
+    for rows in (0, 100000):
+        D.difvm_mesh_amg_config(dmu, rows, -1)
+        st, info, x = _solve(dmu, u, Dg, Lg, b, D.PRECOND_AMG)
+        assert st == D.OK
+        xs.append((info["iters"], x))
+    assert xs[0][0] == xs[1][0] and np.array_equal(xs[0][1], xs[1][1])
