@@ -147,74 +147,184 @@ class Clocks:
 
 
 # ---------------------------------------------------------- CPU baseline
-def run_batched(D, torch, K=3, W=3, n_cases=64, seed=4, precond=None):
-    """Batched form: n_cases independent lid cavities of Kuhn n^3 tetrahedra,
-    n ~ U{8..48}, jitter 0.2h, random lid velocity (speed U(0.5, 1.5), direction
-    in the lid plane), Re = 100 for unit speed, one disjoint-union mesh, F32 with
-    FP64 dots, per-case solver scalars, every step one CUDA graph.  Pressure:
-    CG with one multigrid V-cycle over the union per iteration (default) or
-    Jacobi."""
-    precond = D.PRECOND_AMG if precond is None else precond
+def run_batched(D, torch, K=20, W=3, n_cases=64, seed=4, precond=None, f64=True, adjoint=True):
+    """Batched form: the meshgen.cavity_batch cavities as one disjoint-union mesh, Re =
+    100 (nu = 0.01), dt = 0.002 for every case, FP32 fields with FP64 dots
+    (pressure CG per case to 1e-8), per-case solver scalars, every step one CUDA
+    graph; beside it the same batch in plain FP64 (pressure to 1e-10) and the
+    FP32 fields' difference from it after the same steps; and forward + adjoint
+    of the total kinetic energy over the K steps.  Pressure: CG with one
+    multigrid V-cycle over the union per iteration (default) or Jacobi."""
     from paper_2603_15920_b300 import meshgen as mg
-    rng = np.random.default_rng(seed)
-    ns = rng.integers(8, 49, size=n_cases)
-    u, cs = mg.batch([mg.kuhn_cube(int(n), BATCH_JITTER, 100 + k) for k, n in enumerate(ns)])
+    precond = D.PRECOND_AMG if precond is None else precond
+    ms, u, cs, Ub_h, opens = mg.cavity_batch(n_cases, seed, BATCH_JITTER)
     dm = D.Mesh(u, case_cell_start=cs)
-    Ub_h = np.zeros((3, u.n_boundary))
-    for k in range(n_cases):
-        sp, th = rng.uniform(0.5, 1.5), rng.uniform(0.0, 2.0 * np.pi)
-        f = u.patch_faces(f"c{k}/y1") - u.n_internal
-        Ub_h[0, f], Ub_h[2, f] = sp * np.cos(th), sp * np.sin(th)
-    o = D.piso_opts(BATCH_NU, DT, 2, NONORTH,
-                    solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
-                    solve_p=D.solve_opts(D.PCG, 1e-8, max_iter=20000, check_every=32, precond=precond),
-                    pref_cell=0)
-    h = D.Piso(dm, D.F32, o)
-    U = torch.zeros((3, dm.nc), device="cuda")
-    p = torch.zeros(dm.nc, device="cuda")
-    ub = torch.as_tensor(dm.to_bnd(Ub_h), dtype=torch.float32, device="cuda").contiguous()
-    pb = torch.zeros(dm.nb, device="cuda")
-    phi = D.difvm_flux_from_U(dm, U, ub)
-    info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
-    for _ in range(W):
-        h.step_graph(U, p, phi, ub, pb, info=info)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(K):
-        h.step_graph(U, p, phi, ub, pb, info=info)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / K
-    gi = D.decode_piso_info(info)
-    # forward + adjoint of the total kinetic energy over K steps (all taped)
-    V = torch.as_tensor(dm.to_cells(u.V), dtype=torch.float32, device="cuda")
+    ce = 32 if precond == D.PRECOND_JACOBI else 4
 
-    def ke_grad(U_, p_, phi_, pb_, wk_):
-        return (V * U_).contiguous(), torch.zeros_like(p_), torch.zeros_like(phi_), None, None
-    state = [U, p, phi, ub, pb]
-    tapes = [h.new_tape("cuda") for _ in range(K)]
-    D.simulate_adjoint(h, [t.clone() for t in state], 1, ke_grad, tapes=tapes)
-    base = [t.clone() for t in state]
+    def handle(prec):
+        tolp = 1e-8 if prec == D.F32 else 1e-10
+        o = D.piso_opts(BATCH_NU, DT, 2, NONORTH,
+                        solve_U=D.solve_opts(D.BICGSTAB, 1e-6 if prec == D.F32 else 1e-10, max_iter=1000,
+                                             check_every=4),
+                        solve_p=D.solve_opts(D.PCG, tolp, max_iter=20000, check_every=ce, precond=precond),
+                        pref_cell=0)
+        return D.Piso(dm, prec, o)
+
+    def state(dt_):
+        U = torch.zeros((3, dm.nc), dtype=dt_, device="cuda")
+        p = torch.zeros(dm.nc, dtype=dt_, device="cuda")
+        ub = torch.as_tensor(dm.to_bnd(Ub_h), dtype=dt_, device="cuda").contiguous()
+        pb = torch.zeros(dm.nb, dtype=dt_, device="cuda")
+        return [U, p, D.difvm_flux_from_U(dm, U, ub), ub, pb]
+
+    info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(prec):
+        h, st = handle(prec), state(torch.float32 if prec == D.F32 else torch.float64)
+        for _ in range(W):
+            h.step_graph(*st, info=info)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            h.step_graph(*st, info=info)
+        e1.record()
+        torch.cuda.synchronize()
+        return h, st, e0.elapsed_time(e1) / K, D.decode_piso_info(info)
+
+    h, s32, ms32, gi = timed(D.F32)
+    out = {"workload": f"{n_cases} Kuhn lid cavities (lid U = (1,0,0)), n ~ U{{8..48}}, jitter {BATCH_JITTER}, "
+                       f"each other side a wall with probability 0.8, else an opening (p = 0), seed {seed}",
+           "cells": int(dm.nc), "cases": n_cases, "cases_with_opening": int(opens.any(axis=1).sum()),
+           "value": 1e3 / ms32, "unit": "steps/s", "ms_per_step": ms32, "cell_steps_per_s": dm.nc * 1e3 / ms32,
+           "steps": K, "warmup": W,
+           "api": "difvm_piso_step_graph on a batched mesh (per-case Krylov scalars)",
+           "pressure_solver": ("CG + one multigrid V-cycle over the union per iteration"
+                               if precond == D.PRECOND_AMG else "CG + Jacobi"),
+           "precision": "f32 fields, f64 dots, pressure tol 1e-8 per case",
+           "status": int(gi["status"]), "pressure_iters_max_over_cases": gi["itp"][:2]}
+    if f64:
+        h64, s64, ms64, gi64 = timed(D.F64)
+
+        def nrel(a, b):
+            a, b = a.double(), b.double()
+            return float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+        out["f64"] = {"value": 1e3 / ms64, "unit": "steps/s", "ms_per_step": ms64, "status": int(gi64["status"]),
+                      "pressure_iters_max_over_cases": gi64["itp"][:2],
+                      "f32_field_err_vs_f64": {"steps": W + K, "U": nrel(s32[0], s64[0]),
+                                               "p": nrel(s32[1], s64[1]), "phi": nrel(s32[2], s64[2])},
+                      "f32_over_f64_speed": ms64 / ms32}
+        del h64, s64
+    if adjoint:
+        # forward + adjoint of the total kinetic energy after K steps (every step taped)
+        V = torch.as_tensor(dm.to_cells(u.V), dtype=torch.float32, device="cuda")
+
+        def ke_grad(U_, p_, phi_, pb_, wk_):
+            return (V * U_).contiguous(), torch.zeros_like(p_), torch.zeros_like(phi_), None, None
+        tapes = [h.new_tape("cuda") for _ in range(K)]
+        base = [t.clone() for t in s32]
+        D.simulate_adjoint(h, [t.clone() for t in base], 1, ke_grad, tapes=tapes)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        adj = D.simulate_adjoint(h, [t.clone() for t in base], K, ke_grad, tapes=tapes)
+        a1.record()
+        torch.cuda.synchronize()
+        fa = a0.elapsed_time(a1) / K
+        out.update({"fwd_adj_ms_per_step": fa, "fwd_adjoint_over_fwd": fa / ms32,
+                    "fwd_adjoint_note": "forward steps of the adjoint run are recorded host-loop steps; "
+                                        f"{K} steps taped", "adjoint_status": int(adj["status"])})
+        del tapes
+    return out
+
+
+def run_large(D, torch, K=10, W=3, n=128):
+    """The large mixed-precision case: lid-driven cavity on Kuhn tetrahedra of a
+    128^3 hex grid (12,582,912 cells), jitter 0.15h, Re 400 (nu = 0.0025), dt
+    0.002, two correctors; the FP32 step (FP64 dots, float-float pressure CG to
+    1e-10 around the FP32 V-cycle) and the plain FP64 step, each K graph steps
+    after W from rest; the FP32 fields against the FP64 ones after the same
+    steps; and forward + adjoint of the kinetic energy over K steps with the
+    state kept every 5 steps (segments re-run with tapes)."""
+    name, jitter, nu = LARGE[n]
+    from paper_2603_15920_b300 import meshgen as mg
+    m = mg.kuhn_cube(n, jitter, SEED)
+    dm = D.Mesh(m)
+    Ub_h = lid_bc(m)
+    pref = int(dm.cell_new_of_old[0])
+    info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
+
+    def handle(prec):
+        if prec == D.F32:
+            sp = D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=4, refine_max=20, inner_tol=1e-4,
+                              precond=D.PRECOND_AMG)
+        else:
+            sp = D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=4, precond=D.PRECOND_AMG)
+        return D.Piso(dm, prec, D.piso_opts(
+            nu, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-6 if prec == D.F32 else 1e-10,
+                                                     max_iter=1000, check_every=4),
+            solve_p=sp, pref_cell=pref))
+
+    def state(dt_):
+        U = torch.zeros(3, dm.nc, dtype=dt_, device="cuda")
+        p = torch.zeros(dm.nc, dtype=dt_, device="cuda")
+        Ub = torch.as_tensor(dm.to_bnd(Ub_h), dtype=dt_, device="cuda").contiguous()
+        pb = torch.zeros(dm.nb, dtype=dt_, device="cuda")
+        return [U, p, D.difvm_flux_from_U(dm, U, Ub), Ub, pb]
+
+    def run(prec):
+        h, st = handle(prec), state(torch.float32 if prec == D.F32 else torch.float64)
+        for _ in range(W):
+            h.step_graph(*st, info=info)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            h.step_graph(*st, info=info)
+        e1.record()
+        torch.cuda.synchronize()
+        return h, st, e0.elapsed_time(e1) / K, D.decode_piso_info(info)
+
+    h32, s32, ms32, gi32 = run(D.F32)
+    h64, s64, ms64, gi64 = run(D.F64)
+
+    def nrel(a, b):
+        a, b = a.double(), b.double()
+        return float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+    err = {"steps": W + K, "U": nrel(s32[0], s64[0]), "p": nrel(s32[1], s64[1]), "phi": nrel(s32[2], s64[2])}
+    del h64, s64
+    V = torch.as_tensor(dm.to_cells(m.V), dtype=torch.float32, device="cuda")
+
+    def ke_grad(U, p, phi, pb, wk):
+        return (V * U).contiguous(), torch.zeros_like(p), torch.zeros_like(phi), None, None
+    ck = 5
+    tapes = [h32.new_tape("cuda") for _ in range(ck)]
+    base = [t.clone() for t in s32]
+    D.simulate_adjoint(h32, [t.clone() for t in base], 1, ke_grad, tapes=tapes)
+    s1 = [t.clone() for t in base]
     torch.cuda.synchronize()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record()
-    adj = D.simulate_adjoint(h, base, K, ke_grad, tapes=tapes)
-    a1.record()
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record()
+    for _ in range(K):
+        h32.step(*s1, info=info)
+    b.record()
+    adj = D.simulate_adjoint(h32, [t.clone() for t in base], K, ke_grad, checkpoint_every=ck, tapes=tapes)
+    c.record()
     torch.cuda.synchronize()
-    fa = a0.elapsed_time(a1) / K
-    return {"workload": f"{n_cases} Kuhn lid cavities, n ~ U{{8..48}}, jitter {BATCH_JITTER}, "
-                        f"random lid velocity, seed {seed}",
-            "cells": int(dm.nc), "cases": n_cases, "value": 1e3 / ms, "unit": "steps/s",
-            "ms_per_step": ms, "cell_steps_per_s": dm.nc * 1e3 / ms, "steps": K, "warmup": W,
-            "api": "difvm_piso_step_graph on a batched mesh (per-case Krylov scalars)",
-            "pressure_solver": ("CG + one multigrid V-cycle over the union per iteration"
-                                if precond == D.PRECOND_AMG else "CG + Jacobi"),
-            "precision": "f32 fields, f64 dots, pressure tol 1e-8 per case",
-            "status": int(gi["status"]), "pressure_iters_max_over_cases": gi["itp"][:2],
-            "fwd_adj_ms_per_step": fa, "fwd_adjoint_over_fwd": fa / ms,
-            "fwd_adjoint_note": "forward steps of the adjoint run are recorded host-loop steps",
-            "adjoint_status": int(adj["status"])}
+    free, total = torch.cuda.mem_get_info()
+    fwd, fa = a.elapsed_time(b), b.elapsed_time(c)
+    return {"workload": name, "mesh": f"kuhn{n}^3 jitter {jitter} seed {SEED} RCM", "cells": dm.nc,
+            "faces": dm.nf, "nu": nu, "dt": DT,
+            "value": 1e3 / ms32, "unit": "steps/s", "ms_per_step": ms32, "steps": K, "warmup": W,
+            "status": int(gi32["status"]), "pressure_iters_last_step": gi32["itp"][:2],
+            "f64": {"value": 1e3 / ms64, "ms_per_step": ms64, "status": int(gi64["status"]),
+                    "pressure_iters_last_step": gi64["itp"][:2]},
+            "f32_field_err_vs_f64": err, "f32_over_f64_speed": ms64 / ms32,
+            "fwd_adjoint_over_fwd": {"value": fa / fwd, "steps": K, "checkpoint_every": ck,
+                                     "fwd_ms_per_step": fwd / K, "fwd_adj_ms_per_step": fa / K,
+                                     "status": int(adj["status"]),
+                                     "forward": "host-loop steps (difvm_piso_step) in both"},
+            "device_memory_in_use_GB": round((total - free) / 1e9, 1)}
 
 
 def run_face_ops(D, torch, m, dm, peak, reps=20, copies=4):
@@ -403,8 +513,8 @@ def run_ours(args):
         print(json.dumps(run_face_ops(D, torch, m, dm, measured_peaks()[0])), flush=True)
         return 0
     if args.batch_only:      # the batched 64-case form alone
-        print(json.dumps(run_batched(D, torch, precond=D.PRECOND_JACOBI if args.batch_jacobi else None)),
-              flush=True)
+        print(json.dumps(run_batched(D, torch, K=args.steps,
+                                     precond=D.PRECOND_JACOBI if args.batch_jacobi else None)), flush=True)
         return 0
     Ub_h = lid_bc(m)
     pref = int(dm.cell_new_of_old[0])
@@ -417,13 +527,14 @@ def run_ours(args):
         phi = D.difvm_flux_from_U(dm, U, Ub)
         return [U, p, phi, Ub, pb]
 
-    def piso(prec, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND, time_scheme=D.TIME_BE):
+    def piso(prec, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND, time_scheme=D.TIME_BE, check_every=None):
         # pressure: CG preconditioned by one multigrid V-cycle (or Jacobi); the
         # Jacobi form polls less often since it runs ~50x more iterations
-        ce = 32 if precond == D.PRECOND_JACOBI else 4
+        ce = check_every or (32 if precond == D.PRECOND_JACOBI else 4)
         if prec == D.F32:
             return D.Piso(dm, D.F32, D.piso_opts(
-                NU, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000, check_every=4),
+                NU, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-6, max_iter=1000,
+                                                         check_every=check_every or 4),
                 solve_p=D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=ce, refine_max=20,
                                      inner_tol=1e-4, precond=precond),
                 pref_cell=pref, conv=conv, time_scheme=time_scheme))
@@ -481,42 +592,66 @@ def run_ours(args):
     # the same step through difvm_piso_step (host-driven solver loops): secondary
     # line, launch count, and the state the roofline pass continues from
     r32 = timed(D.F32, W, K) if graph else rg
-    # roofline pass: the same handle and state continue for K more steps with
-    # CUDA events recorded around every launch of the fine-level multigrid
-    # residual kernel (kept out of the headline timed region, whose launches
-    # they would slow)
+    # roofline passes: the same handle and state continue for K more steps, with
+    # CUDA events recorded around every launch of one kernel (kept out of the
+    # headline timed region, whose launches they would slow): the kernel with the
+    # largest share of the step's time, the coarse-level corrected smoothing
+    # sweep k_amg_post1<float, 8> (levels 2-5), and the mesh-level residual
     h32, s32 = r32["handle"], r32["state"]
-    torch.cuda.synchronize()
-    D.difvm_prof_start(D.PROF_AMG_RESID, 200000)
-    for _ in range(K):
-        h32.step(*s32, info=info)
-    torch.cuda.synchronize()
-    r32["prof"] = D.difvm_prof_stop()
+    prof = {}
+    for tag in (D.PROF_AMG_POST1C, D.PROF_AMG_RESID):
+        torch.cuda.synchronize()
+        D.difvm_prof_start(tag, 200000)
+        for _ in range(K):
+            h32.step(*s32, info=info)
+        torch.cuda.synchronize()
+        nbytes = D.prof_bytes()
+        ms_tot, n_l = D.difvm_prof_stop()
+        prof[tag] = (ms_tot, n_l, nbytes)
     ms_local = rg["ms"] / K
     ms_step = max_over_ranks(ms_local, dist if world > 1 else None, "cuda")
     value = job_rate(ms_step, world)
 
-    # roofline of the dominant kernel: the fine-level multigrid residual res = r - A y
-    # (symmetric LDU, F32); algorithmic bytes per launch = internal faces x (owner +
-    # neighbour + coefficient) + cells x (D, r, y, res)
+    # algorithmic bytes of one step: the same settings with the solvers' convergence
+    # checked after every iteration (no iterations past convergence), W steps from
+    # rest, then the bytes of K steps counted (the Krylov and multigrid kernels)
+    hb, sb = piso(D.F32, check_every=1), new_state(torch.float32)
+    for _ in range(W):
+        hb.step(*sb, info=info)
+    torch.cuda.synchronize()
+    b0 = D.alg_bytes()
+    for _ in range(K):
+        hb.step(*sb, info=info)
+    torch.cuda.synchronize()
+    step_bytes = (D.alg_bytes() - b0) / K
+    del hb, sb
+
     peak, peak_kind = measured_peaks()
-    spmv_ms, spmv_n = r32["prof"]
-    alg_bytes = dm.ni * (4 + 4 + 4) + dm.nc * (4 + 4 + 4 + 4)
-    avg_ms = spmv_ms / max(spmv_n, 1)
-    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if spmv_n else None
-    traffic = None
-    tf_path = os.path.join(ROOT, "profiles", "traffic_amg_resid_f32_kuhn64.json")
-    if os.path.exists(tf_path) and args.mesh == N_KUHN:   # captured on the 64^3 mesh
+
+    def kernel_roofline(tag):
+        ms_tot, n_l, nbytes = prof[tag]
+        avg_ms = ms_tot / max(n_l, 1)
+        per_launch = nbytes / max(n_l, 1)
+        ach = per_launch / (avg_ms * 1e-3) / 1e9 if n_l else None
+        return ach, per_launch, avg_ms, n_l
+    achieved, alg_bytes, avg_ms, n_post1 = kernel_roofline(D.PROF_AMG_POST1C)
+    ach_res, alg_res, avg_res, n_res = kernel_roofline(D.PROF_AMG_RESID)
+
+    def traffic_of(name):
+        path = os.path.join(ROOT, "profiles", name)
+        if not (os.path.exists(path) and args.mesh == N_KUHN):   # captured on the 64^3 mesh
+            return None
         try:
-            traffic = json.load(open(tf_path)).get("dram_bytes_per_launch")
+            return json.load(open(path)).get("dram_bytes_per_launch")
         except Exception:
-            traffic = None
+            return None
 
     if args.only_f32:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "steps/s", "ms_per_step": ms_step,
                               "mesh": args.mesh, "status": int(r32["status"]),
-                              "amg_resid_avg_us": avg_ms * 1e3, "info": r32["info"]}), flush=True)
+                              "amg_post1c_avg_us": avg_ms * 1e3, "amg_resid_avg_us": avg_res * 1e3,
+                              "step_alg_bytes": step_bytes, "info": r32["info"]}), flush=True)
         return 0
     rj = timed(D.F32, W, K, graph=True, precond=D.PRECOND_JACOBI)
     jacobi = {"value": 1e3 * K / rj["ms"], "unit": "steps/s", "ms_per_step": rj["ms"] / K,
@@ -562,30 +697,39 @@ def run_ours(args):
                "phi": nrel(sq[2], r64["state"][2])}
     del hq, sq
 
-    # end to end through the public API: per step the lid boundary values go
-    # host -> device from pinned memory and the step's info record comes back
+    # end to end through the public API, like the headline from rest (W warm-up
+    # steps, then K timed steps): per step the boundary values go host -> device
+    # from pinned memory, the step runs (difvm_piso_step_graph), and its result
+    # (U, p, phi) comes back to pinned host buffers before the next step starts
     dt_ = torch.float32
-    h, s = rg["handle"], rg["state"]
+    he, se = piso(D.F32), new_state(dt_)
     Ub_pin = torch.as_tensor(dm.to_bnd(Ub_h), dtype=dt_).contiguous().pin_memory()
     pb_pin = torch.zeros(dm.nb, dtype=dt_).pin_memory()
-    info_pin = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8).pin_memory()
+    out_pin = [torch.empty(se[k].shape, dtype=dt_).pin_memory() for k in range(3)]
+
+    def e2e_step():
+        se[3].copy_(Ub_pin, non_blocking=True)
+        se[4].copy_(pb_pin, non_blocking=True)
+        he.step_graph(*se, info=info)
+        for k in range(3):
+            out_pin[k].copy_(se[k], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    for _ in range(W):
+        e2e_step()
     torch.cuda.synchronize()
     barrier()
-    t0 = time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(K):
-        s[3].copy_(Ub_pin, non_blocking=True)
-        s[4].copy_(pb_pin, non_blocking=True)
-        h.step_graph(*s, info=info)
-        info_pin.copy_(info, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        e2e_step()
     e1.record()
     torch.cuda.synchronize()
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / K, dist if world > 1 else None, "cuda")
     h2d = (Ub_pin.numel() + pb_pin.numel()) * 4
-    d2h = info_pin.numel()
+    d2h = sum(t.numel() for t in out_pin) * 4
+    e2e_same = bool(torch.equal(out_pin[0], se[0].cpu()) and torch.equal(out_pin[0], rg["state"][0].cpu()))
+    del he, se
 
     h, s = r32["handle"], r32["state"]
     # forward + adjoint against forward alone, from one state of the same run:
@@ -643,22 +787,36 @@ def run_ours(args):
                                             for k_, n_ in (("itU", 3), ("itp", 2))}}
 
     face_ops = run_face_ops(D, torch, m, dm, peak)
+    large = None
+    if args.mesh == N_KUHN and not args.no_large:
+        large = run_large(D, torch)
     batched = None
     if not args.no_batch:
         batched = run_batched(D, torch)
-        bj = run_batched(D, torch, precond=D.PRECOND_JACOBI)
+        bj = run_batched(D, torch, K=3, precond=D.PRECOND_JACOBI, f64=False, adjoint=False)
         batched["jacobi_pressure"] = {k: bj[k] for k in ("value", "unit", "ms_per_step", "status",
-                                                         "pressure_iters_max_over_cases",
-                                                         "fwd_adjoint_over_fwd")}
+                                                         "pressure_iters_max_over_cases", "steps")}
 
     if rank != 0:
         return 0
     # CPU baseline: one full oracle PISO step of the same cavity (single thread)
     cpu = None
     if not args.no_cpu:
+        import oracle as O
         rate, secs = cpu_oracle_step_rate(m, steps=1)
         cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": f"1 full FP64 oracle PISO step of the same cavity from rest ({secs:.1f} s)"}
+        # the same oracle built with OpenMP over cells (cell-CSR LDU apply, fixed-block
+        # dot products: deterministic) on every host core
+        try:
+            threads = O.use_multicore(True)
+            rate_mc, secs_mc = cpu_oracle_step_rate(m, steps=1)
+        finally:
+            O.use_multicore(False)
+        cpu["all_cores"] = {"value": rate_mc, "unit": "steps/s", "cores": threads, "nproc": os.cpu_count(),
+                            "kind": "oracle, OpenMP build",
+                            "sample": f"1 full FP64 oracle PISO step of the same cavity from rest "
+                                      f"({secs_mc:.1f} s)"}
     gi = rg["info"]
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -692,14 +850,30 @@ def run_ours(args):
         "fwd_adjoint_over_fwd": fwd_adj,
         "face_ops": face_ops,
         "batched": batched,
-        "roofline": {"kernel": "k_amg_resid<float, 1> (mesh-level multigrid residual r - A y)",
+        "large": large,
+        "roofline": {"kernel": "k_amg_post1<float, 8> (coarse-level multigrid corrected smoothing "
+                               "sweep, levels 2-5; the largest share of the step's kernel time)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic_of("traffic_amg_post1c_f32_kuhn64.json"),
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,
-                     "launches_timed": spmv_n, "peak_kind": peak_kind},
+                     "launches_timed": n_post1, "peak_kind": peak_kind,
+                     "step_alg_bytes": step_bytes,
+                     "step_frac": step_bytes / (ms_step * 1e-3) / (peak * 1e9),
+                     "step_frac_note": "algorithmic bytes of the Krylov and multigrid kernels of one step "
+                                       "(about 93% of the step's kernel time) / ms_per_step / peak; the "
+                                       "assembly, gradient and flux kernels are not counted, so this is a "
+                                       "lower bound",
+                     "mesh_level_residual": {"kernel": "k_amg_resid<float, 1>", "achieved": ach_res,
+                                             "frac": (ach_res / peak) if ach_res else None,
+                                             "alg_bytes_per_launch": alg_res,
+                                             "avg_launch_us": avg_res * 1e3, "launches_timed": n_res,
+                                             "traffic": traffic_of("traffic_amg_resid_f32_kuhn64.json")}},
         "e2e": {"value": job_rate(e2e_ms, world), "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "returned": "U, p, phi to pinned host memory every step",
+                "same_final_U_as_headline": e2e_same},
         "clocks": ck,
         "cpu_baseline": cpu,
     }
@@ -717,6 +891,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-case line")
+    ap.add_argument("--no-large", action="store_true", help="skip the 128^3 Re 400 line")
     ap.add_argument("--batch-only", action="store_true", help="time only the batched 64-case form")
     ap.add_argument("--batch-jacobi", action="store_true",
                     help="with --batch-only: Jacobi instead of multigrid for the pressure CG")

@@ -216,16 +216,29 @@ const char* difvm_last_error(void);
 /* Number of kernels this library has launched on the calling process (all
  * devices).  For launch accounting in benchmarks. */
 uint64_t difvm_launch_count(void);
+/* Algorithmic bytes of the Krylov and multigrid kernels launched so far
+ * (momentum BiCGStab, pressure CG, V-cycles and their set-up): every array a
+ * kernel must read or write counted once at its logical size -- a matrix as its
+ * faces (owner, neighbour, coefficient(s)) plus its diagonal -- regardless of
+ * layout, padding, re-reads or caching.  Counted at launch, so kernels that
+ * exit early after convergence still count; launches inside a CUDA graph count
+ * once, when captured.  For roofline accounting in benchmarks. */
+uint64_t difvm_alg_bytes(void);
 /* Per-kernel device timing for benchmarks: while active, every launch of the
  * kernel named by `tag` is bracketed by a pair of CUDA events on its own
  * stream (at most max_launches pairs; later launches are not timed).
  * difvm_prof_stop synchronises on the recorded events and returns the summed
- * kernel time and the number of timed launches.  Process-wide, one tag at a
- * time, not thread-safe; start/stop allocate and free the events. */
+ * kernel time and the number of timed launches; difvm_prof_bytes (before
+ * difvm_prof_stop) the summed algorithmic bytes of the timed launches (as
+ * difvm_alg_bytes counts them; multigrid tags only, 0 otherwise).
+ * Process-wide, one tag at a time, not thread-safe; start/stop allocate and
+ * free the events. */
 enum { DIFVM_PROF_PCG_SPMV = 1, DIFVM_PROF_PCG_UPDATE = 2, DIFVM_PROF_PCG_PUPDATE = 3,
-       DIFVM_PROF_AMG_RESID = 4 /* fine-level multigrid residual r - A y */ };
+       DIFVM_PROF_AMG_RESID = 4,  /* fine-level multigrid residual r - A y */
+       DIFVM_PROF_AMG_POST1C = 5  /* coarse-level corrected smoothing sweeps of eight lanes per row */ };
 difvm_status difvm_prof_start(int tag, int max_launches);
 difvm_status difvm_prof_stop(double* total_ms, int64_t* launches);
+uint64_t difvm_prof_bytes(void);
 
 /* ---------------------------------------------------------------- operators */
 /* Gauss gradient (Eq. gauss_green): grad_i = (1/V_i) sum_f sigma phi_f S_f,

@@ -1096,12 +1096,29 @@ static int amg_tpr(const AmgLev& L, int l) {
   return L.nslots > 8 * L.n ? 8 : 4;
 }
 
+// Algorithmic bytes of the V-cycle kernels on level L (n rows, nf faces; next
+// level n1 rows), element size v: the level's symmetric matrix is its faces'
+// (owner, neighbour, coefficient) plus the diagonal; every vector a kernel
+// reads or writes counts once.
+static uint64_t lev_mat_bytes(const AmgLev& L, uint64_t v) { return (uint64_t)L.nf * (8 + v); }
+static uint64_t lev_pre_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 4 * v; }
+static uint64_t lev_resid_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 4 * v; }
+static uint64_t lev_restrict_bytes(const AmgLev& L, int n1, uint64_t v) {
+  return (uint64_t)L.n * (4 + v) + (uint64_t)n1 * v;
+}
+static uint64_t lev_post1_bytes(const AmgLev& L, int n1, uint64_t v) {
+  return lev_mat_bytes(L, v) + (uint64_t)L.n * (5 * v + 4) + (uint64_t)n1 * v;
+}
+static uint64_t lev_post2_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 5 * v; }
+
 // coarse operators of every level from the level-0 matrix (D, L symmetric)
 template <typename T>
 static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cudaStream_t st) {
   const AmgHier* H = R.H;
+  const uint64_t v = sizeof(T);
   k_amg_rd<T><<<blocks_for(R.m->nc, kAB), kAB, 0, st>>>(R.m->nc, D0, R.at(R.Ly.rD[0]));
   DIFVM_TRY(check_launch("amg_rd"));
+  count_bytes(2 * (uint64_t)R.m->nc * v);
   const T* D = D0;
   const T* Lv = L0;
   for (int l = 0; l + 1 < H->nlev; ++l) {
@@ -1109,6 +1126,11 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
     const AmgLev& L1 = H->lev[l + 1];
     T *D1 = R.at(R.Ly.D[l + 1]), *rD1 = R.at(R.Ly.rD[l + 1]), *Lv1 = R.at(R.Ly.L[l + 1]);
     k_amg_diag<T><<<blocks_for(L1.n, kAB), kAB, 0, st>>>(L1.n, L, D, Lv, D1, rD1);
+    // diagonal: the level's D, L and aggregate map in, D1 and 1/D1 out; faces: L in
+    // with its map, L1 out; entries: L1 into the next level's ELL slots
+    count_bytes((uint64_t)L.n * (v + 4) + (uint64_t)L.nf * (v + 4) + 2 * (uint64_t)L1.n * v);
+    if (L1.nf > 0) count_bytes((uint64_t)L.nf * (v + 4) + (uint64_t)L1.nf * v +
+                               (uint64_t)L1.nslots * (4 + v) + (uint64_t)L1.nf * v);
     if (L1.nf > 0) {
       k_amg_faces<T><<<blocks_for(L1.nf, kAB), kAB, 0, st>>>(L1.nf, L, Lv, Lv1);
       k_amg_entries<T><<<blocks_for(L1.nslots, kAB), kAB, 0, st>>>(L1.nslots, L1.eface, Lv1,
@@ -1122,6 +1144,7 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
   if (Lc.n > kAmgCoarsest) return set_error(DIFVM_EINVAL, "AMG: coarsest level has %d cells", Lc.n);
   k_amg_dense_inv<T><<<1, 512, 0, st>>>(Lc, D, Lv, (float*)(R.ws + R.Ly.inv));
   DIFVM_TRY(check_launch("amg_dense_inv"));
+  count_bytes((uint64_t)Lc.n * Lc.n * 4 + (uint64_t)Lc.n * v + (uint64_t)Lc.nf * (8 + v));
   if (R.tail_from > 0) {
     TailLevs<T> d;
     const int nl = H->nlev - R.tail_from;
@@ -1206,9 +1229,14 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
                        int down, cudaStream_t s) {
   const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
   const unsigned B = blocks_for((int64_t)L.n * TPR, kAB);
+  const uint64_t v = sizeof(T);
   if (down) {
+    count_bytes(lev_pre_bytes(L, v) + lev_resid_bytes(L, v) + lev_restrict_bytes(L, L1.n, v));
     launch_pdl(k_amg_pre<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, done);
-    if (TPR == 1) prof_before(DIFVM_PROF_AMG_RESID, s);
+    if (TPR == 1) {
+      prof_bytes(DIFVM_PROF_AMG_RESID, lev_resid_bytes(L, v));
+      prof_before(DIFVM_PROF_AMG_RESID, s);
+    }
     launch_pdl(k_amg_resid<T, TPR>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
     if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
     if (L1.n >= kAmgBigLevel / 4)
@@ -1218,7 +1246,13 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
     count_launch(); count_launch(); count_launch();
     return;
   }
+  count_bytes(lev_post1_bytes(L, L1.n, v) + lev_post2_bytes(L, v));
+  if (TPR == 8) {
+    prof_bytes(DIFVM_PROF_AMG_POST1C, lev_post1_bytes(L, L1.n, v));
+    prof_before(DIFVM_PROF_AMG_POST1C, s);
+  }
   launch_pdl(k_amg_post1<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, xc, u, done);
+  if (TPR == 8) prof_after(DIFVM_PROF_AMG_POST1C, s);
   if (TPR == 1 && !R.seg_done)
     launch_pdl(k_amg_post2_dot<T>, R.G, kKB, s, L, R.A, rD, r, u, out, w, first);
   else
@@ -1234,6 +1268,15 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const AmgLev& L = H->lev[l];
   const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
   if (R.tail_from > 0 && l == R.tail_from) {
+    const uint64_t v = sizeof(T);
+    for (int k = l; k + 1 < H->nlev; ++k) {
+      const AmgLev& Lk = H->lev[k];
+      const int n1 = H->lev[k + 1].n;
+      count_bytes(lev_pre_bytes(Lk, v) + lev_resid_bytes(Lk, v) + lev_restrict_bytes(Lk, n1, v) +
+                  lev_post1_bytes(Lk, n1, v) + lev_post2_bytes(Lk, v));
+    }
+    const int nco = H->lev[H->nlev - 1].n;
+    count_bytes((uint64_t)nco * nco * 4 + 2 * (uint64_t)nco * v);
     KState* st = (KState*)(R.ws + R.Ly.st);
     amg_tail_launch(R, done, R.seg_done ? st : w.st, R.seg_done ? R.m->ncases : 1,
                     R.seg_done ? const_cast<int*>(R.seg_done) : nullptr, s);
@@ -1244,6 +1287,7 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const T* rD = R.at(R.Ly.rD[l]);
   const T* Lv = fine ? nullptr : R.at(R.Ly.E[l]);   // row-entry values of a coarse level
   if (l == H->nlev - 1) {
+    count_bytes((uint64_t)L.n * L.n * 4 + 2 * (uint64_t)L.n * sizeof(T));
     launch_pdl(k_amg_coarse<T>, 1, 1024, s, L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
     count_launch();
     if (l == 0 && !R.seg_done) {   // a single level: the CG's r.z reduction runs on its own
@@ -1280,7 +1324,10 @@ static difvm_status amg_cg(const AmgRun<T>& R, const T* b, T* x, const KWork& w,
   amg_vcycle(R, 0, r, z, w, 1, st);
   k_apcg_p<T><<<G, kKB, 0, st>>>(nc, z, p, w, 1);
   DIFVM_TRY(check_launch("apcg_p"));
+  const uint64_t v = sizeof(T), n64 = (uint64_t)nc;
+  const uint64_t cg_bytes = lev_mat_bytes(R.H->lev[0], v) + 3 * n64 * v + 6 * n64 * v + 3 * n64 * v;
   auto iter = [&](cudaStream_t s) {
+    count_bytes(cg_bytes);   // q = A p; x, r update; p update
     prof_before(DIFVM_PROF_PCG_SPMV, s);
     k_pcg_spmv<T, 1, MW><<<G, kKB, 0, s>>>(R.t, R.A, p, q, w);
     prof_after(DIFVM_PROF_PCG_SPMV, s);
@@ -1348,6 +1395,7 @@ static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws
   if (m->ell_nslots > 0) {
     k_ell_fill<T><<<blocks_for(m->ell_nslots, 256), 256, 0, st>>>((int)m->ell_nslots, m->ell_map, Lo, Lo, val);
     DIFVM_TRY(check_launch("ell_fill"));
+    count_bytes((uint64_t)m->ni * sizeof(T) + 2 * (uint64_t)m->ni * (4 + sizeof(T)));
   }
   R.A = Mat<T>{D, m->ell(), val};
   return amg_setup(R, D, Lo, st);
@@ -1811,7 +1859,12 @@ static difvm_status amg_mixed_mw(difvm_mesh* m, const difvm_solve_opts* o, const
   amg_vcycle(R, 0, rh, z32, w, 1, st);
   k_fcg_p<<<G, kKB, 0, st>>>(nc, z32, ph, pl, w, 1);
   DIFVM_TRY(check_launch("fcg_p"));
+  // q = A p (matrix, D, p and q as float pairs); x, r, p, q pairs; p pair and z
+  const uint64_t n64 = (uint64_t)nc;
+  const uint64_t fcg_bytes = lev_mat_bytes(R.H->lev[0], 4) + 20 * n64 + 48 * n64 + 20 * n64;
+  count_bytes(lev_mat_bytes(R.H->lev[0], 4) + 36 * n64);   // the FP64 initial residual
   auto iter = [&](cudaStream_t s) {
+    count_bytes(fcg_bytes);
     prof_before(DIFVM_PROF_PCG_SPMV, s);
     launch_pdl(k_fcg_spmv<MW>, G, kKB, s, R.t, R.A, ph, pl, qh, ql, w);
     prof_after(DIFVM_PROF_PCG_SPMV, s);

@@ -15,6 +15,10 @@ namespace difvm {
 // ----------------------------------------------------------------- errors
 difvm_status set_error(difvm_status st, const char* fmt, ...);
 void count_launch();
+// algorithmic bytes of the kernels launched (each array a kernel must read or
+// write counted once at its logical size: no padding, re-reads or caching);
+// the solver kernels (Krylov, multigrid) add theirs at launch time
+void count_bytes(uint64_t bytes);
 difvm_status check_launch(const char* what);   // counts one launch, then check_error
 difvm_status check_error(const char* what);    // pending launch error -> ECUDA
 
@@ -23,6 +27,7 @@ difvm_status check_error(const char* what);    // pending launch error -> ECUDA
 // prof_after with the same tag get a pair of CUDA events on their stream.
 void prof_before(int tag, cudaStream_t s);
 void prof_after(int tag, cudaStream_t s);
+void prof_bytes(int tag, uint64_t bytes);   // algorithmic bytes of the launch prof_before bracketed
 bool prof_active();
 
 #define DIFVM_CUDA(call)                                                            \

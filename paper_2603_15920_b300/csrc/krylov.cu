@@ -585,7 +585,14 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     DIFVM_TRY(check_launch("bicg_init"));
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
+    // algorithmic bytes of one iteration: the LDU matrix (owner, neighbour, L, U per
+    // internal face; D) in each of the two products, NC-component vectors once per kernel
+    const uint64_t vb = sizeof(T), ncu = (uint64_t)nc, nq = NC;
+    const uint64_t mat = (uint64_t)m->ni * (8 + 2 * vb) + ncu * vb;
+    const uint64_t it_bytes = 4 * nq * ncu * vb + 2 * (ncu * vb + 2 * nq * ncu * vb) +
+                              2 * (mat + 3 * nq * ncu * vb) + 3 * nq * ncu * vb + 8 * nq * ncu * vb;
     DIFVM_TRY(run([&](cudaStream_t s) {
+      count_bytes(it_bytes);
       k_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, w);
       k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, p, rD, y, w);
       k_bicg_spmv1<T, NC, MW><<<G1, kKB, 0, s>>>(t, A, rh, y, v, w);

@@ -32,11 +32,14 @@ difvm_status set_error(difvm_status st, const char* fmt, ...) {
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static std::atomic<uint64_t> g_alg_bytes{0};
+void count_bytes(uint64_t bytes) { g_alg_bytes.fetch_add(bytes, std::memory_order_relaxed); }
 
 struct ProfState {
   int tag = 0;
   int cap = 0;
   int n = 0;
+  uint64_t bytes = 0;
   std::vector<cudaEvent_t> ev;
 };
 static ProfState g_prof;
@@ -45,6 +48,10 @@ bool prof_active() { return g_prof.tag != 0; }
 
 void prof_before(int tag, cudaStream_t s) {
   if (g_prof.tag == tag && g_prof.n < g_prof.cap) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
+}
+
+void prof_bytes(int tag, uint64_t bytes) {
+  if (g_prof.tag == tag && g_prof.n < g_prof.cap) g_prof.bytes += bytes;
 }
 
 void prof_after(int tag, cudaStream_t s) {
@@ -575,6 +582,10 @@ extern "C" const char* difvm_last_error(void) { return g_err.c_str(); }
 
 extern "C" uint64_t difvm_launch_count(void) { return g_launches.load(); }
 
+extern "C" uint64_t difvm_alg_bytes(void) { return g_alg_bytes.load(); }
+
+extern "C" uint64_t difvm_prof_bytes(void) { return g_prof.bytes; }
+
 extern "C" difvm_status difvm_prof_start(int tag, int max_launches) {
   if (tag <= 0 || max_launches <= 0) return set_error(DIFVM_EINVAL, "bad profiling request");
   if (g_prof.tag != 0) return set_error(DIFVM_EINVAL, "profiling already active");
@@ -582,6 +593,7 @@ extern "C" difvm_status difvm_prof_start(int tag, int max_launches) {
   for (auto& e : g_prof.ev) DIFVM_CUDA(cudaEventCreate(&e));
   g_prof.cap = max_launches;
   g_prof.n = 0;
+  g_prof.bytes = 0;
   g_prof.tag = tag;
   return DIFVM_OK;
 }

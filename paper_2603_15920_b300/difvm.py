@@ -147,6 +147,8 @@ def lib():
                 fn.restype = C.c_int
         L.difvm_last_error.restype = C.c_char_p
         L.difvm_launch_count.restype = C.c_uint64
+        L.difvm_alg_bytes.restype = C.c_uint64
+        L.difvm_prof_bytes.restype = C.c_uint64
         L.difvm_mesh_destroy.argtypes = [_vp]
         L.difvm_mesh_destroy.restype = None
         for nm in ("difvm_krylov_workspace_bytes", "difvm_krylov_refine_workspace_bytes",
@@ -190,7 +192,17 @@ def launch_count() -> int:
     return int(lib().difvm_launch_count())
 
 
-PROF_PCG_SPMV, PROF_PCG_UPDATE, PROF_PCG_PUPDATE, PROF_AMG_RESID = 1, 2, 3, 4
+PROF_PCG_SPMV, PROF_PCG_UPDATE, PROF_PCG_PUPDATE, PROF_AMG_RESID, PROF_AMG_POST1C = 1, 2, 3, 4, 5
+
+
+def alg_bytes() -> int:
+    """Algorithmic bytes of the Krylov and multigrid kernels launched so far."""
+    return int(lib().difvm_alg_bytes())
+
+
+def prof_bytes() -> int:
+    """Algorithmic bytes of the launches timed since difvm_prof_start."""
+    return int(lib().difvm_prof_bytes())
 
 
 def difvm_prof_start(tag, max_launches=100000):

@@ -187,6 +187,28 @@ def batch(meshes):
     return u, cs
 
 
+def cavity_batch(n_cases: int = 64, seed: int = 4, jitter: float = 0.2):
+    """The batched benchmark input: n_cases lid-driven cavities, each a Kuhn
+    cube of n^3 hexes with n ~ U{8..48} and the given jitter (case k seeded
+    100 + k).  The lid (patch y1) is a wall moving with U = (1, 0, 0); each of
+    the other five sides is a fixed wall with probability 0.8, else an opening
+    (OUTLET: zero-gradient velocity, fixed pressure), drawn by seed.  Returns
+    (cases, union mesh, case_cell_start, lid boundary values of the union
+    [3, n_boundary], opening table [n_cases, 5] for x0, x1, y0, z0, z1)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(8, 49, size=n_cases)
+    sides = ("x0", "x1", "y0", "z0", "z1")
+    opens = rng.uniform(size=(n_cases, len(sides))) >= 0.8
+    ms = [kuhn_cube(int(n), jitter, 100 + k,
+                    patch_types={sd: (OUTLET if opens[k, q] else WALL) for q, sd in enumerate(sides)})
+          for k, n in enumerate(ns)]
+    u, cs = batch(ms)
+    Ub = np.zeros((3, u.n_boundary))
+    for k in range(n_cases):
+        Ub[0, u.patch_faces(f"c{k}/y1") - u.n_internal] = 1.0
+    return ms, u, cs, Ub, opens
+
+
 # ---------------------------------------------------------------------------
 # uniform hex box
 # ---------------------------------------------------------------------------
