@@ -327,6 +327,79 @@ def run_large(D, torch, K=10, W=3, n=128):
             "device_memory_in_use_GB": round((total - free) / 1e9, 1)}
 
 
+def run_pipe(D, torch, steps=400, ckpt=20):
+    """The differentiable pulsatile pipe (the survey's config 3): O-H pipe R = 1,
+    L = 10, 153,600 cells; parabolic inflow Q(t) = 1 + 0.5 sin 2 pi t + 0.2 sin
+    4 pi t; RCR Windkessel outlet (R_p, C, R_d) = (0.1, 1, 1), exact update; nu
+    0.035, dt 0.0025, FP64, 400 steps.  Loss: pressure misfit at 8 probes over
+    all steps against the (0.15, 0.7, 1.3) trajectory; its gradient by the
+    step adjoints chained over the trajectory, the state kept every 20 steps
+    (tests/test_gpu_pipe.py checks it against central differences at 1e-4)."""
+    from paper_2603_15920_b300 import meshgen as mg
+    dt, nu = 0.0025, 0.035
+    m = mg.pipe_ohgrid(16, 8, 200, L=10.0)
+    dm = D.Mesh(m)
+    shape = torch.as_tensor(dm.to_bnd(mg.pipe_inflow(m)), dtype=torch.float64, device="cuda").contiguous()
+    probes = np.random.default_rng(11).choice(m.n_cells, size=8, replace=False)
+    probes = torch.as_tensor(dm.cell_new_of_old[probes], dtype=torch.long, device="cuda")
+    h = D.Piso(dm, D.F64, D.piso_opts(
+        nu, dt, 2, 1, solve_U=D.solve_opts(D.BICGSTAB, 1e-12, max_iter=2000, check_every=4),
+        solve_p=D.solve_opts(D.PCG, 1e-12, max_iter=5000, check_every=4, precond=D.PRECOND_AMG),
+        wk_scheme=D.WK_EXACT, wk_patch=[m.patch_index("outlet")]))
+    info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
+
+    def boundary(j, Ub):
+        torch.mul(shape, mg.pulsatile_flow((j + 1) * dt), out=Ub)
+
+    def state(theta):
+        U = torch.zeros(3, dm.nc, dtype=torch.float64, device="cuda")
+        p = torch.zeros(dm.nc, dtype=torch.float64, device="cuda")
+        Ub = shape.clone()
+        boundary(-1, Ub)
+        pb = torch.zeros(dm.nb, dtype=torch.float64, device="cuda")
+        wk = torch.tensor(list(theta) + [0.0], dtype=torch.float64, device="cuda")
+        return [U, p, D.difvm_flux_from_U(dm, U, Ub), Ub, pb], wk
+
+    def forward(theta):
+        (U, p, phi, Ub, pb), wk = state(theta)
+        P = torch.empty(steps, 8, dtype=torch.float64, device="cuda")
+        for j in range(steps):
+            boundary(j, Ub)
+            h.step_graph(U, p, phi, Ub, pb, wk, info=info)
+            P[j] = p[probes]
+        return P
+
+    target = forward((0.15, 0.7, 1.3))
+    torch.cuda.synchronize()
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record()
+    P = forward((0.1, 1.0, 1.0))
+    b.record()
+    torch.cuda.synchronize()
+    loss = float(((P - target) ** 2).mean())
+    st, wk = state((0.1, 1.0, 1.0))
+    N = float(target.numel())
+
+    def seeds(j, U, p, phi, pb, w):
+        g = torch.zeros_like(p)
+        g[probes] = 2.0 * (p[probes] - target[j]) / N
+        return None, g, None, None, None
+    torch.cuda.synchronize()
+    b2 = torch.cuda.Event(enable_timing=True)
+    b2.record()
+    r = D.trajectory_adjoint(h, st, steps, boundary, seeds, wk=wk, checkpoint_every=ckpt)
+    c.record()
+    torch.cuda.synchronize()
+    fwd, fa = a.elapsed_time(b), b2.elapsed_time(c)
+    return {"workload": "pulsatile O-H pipe with an RCR Windkessel outlet, 400 steps", "cells": dm.nc,
+            "precision": "f64", "value": steps * 1e3 / fwd, "unit": "steps/s", "ms_per_step": fwd / steps,
+            "api": "difvm_piso_step_graph per step, inlet values updated in place",
+            "loss": loss, "dL_dRp_C_Rd": [float(r["Rp"][0]), float(r["C"][0]), float(r["Rd"][0])],
+            "fwd_adjoint_over_fwd": {"value": fa / fwd, "checkpoint_every": ckpt, "fwd_adj_ms": fa,
+                                     "forward": "host-loop steps in the adjoint run"},
+            "status": int(r["status"])}
+
+
 def run_face_ops(D, torch, m, dm, peak, reps=20, copies=4):
     """The face operators on the bench mesh in FP32 and FP64 (Sec. 2.3-2.4: Gauss
     gradient, convective divergence, diffusive flux, LDU apply).  `copies`
@@ -787,9 +860,10 @@ def run_ours(args):
                                             for k_, n_ in (("itU", 3), ("itp", 2))}}
 
     face_ops = run_face_ops(D, torch, m, dm, peak)
-    large = None
+    large = pipe = None
     if args.mesh == N_KUHN and not args.no_large:
         large = run_large(D, torch)
+        pipe = run_pipe(D, torch)
     batched = None
     if not args.no_batch:
         batched = run_batched(D, torch)
@@ -851,6 +925,7 @@ def run_ours(args):
         "face_ops": face_ops,
         "batched": batched,
         "large": large,
+        "pulsatile_pipe": pipe,
         "roofline": {"kernel": "k_amg_post1<float, 8> (coarse-level multigrid corrected smoothing "
                                "sweep, levels 2-5; the largest share of the step's kernel time)",
                      "bound": "hbm",
@@ -891,7 +966,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-case line")
-    ap.add_argument("--no-large", action="store_true", help="skip the 128^3 Re 400 line")
+    ap.add_argument("--no-large", action="store_true", help="skip the 128^3 Re 400 and pulsatile-pipe lines")
     ap.add_argument("--batch-only", action="store_true", help="time only the batched 64-case form")
     ap.add_argument("--batch-jacobi", action="store_true",
                     help="with --batch-only: Jacobi instead of multigrid for the pressure CG")

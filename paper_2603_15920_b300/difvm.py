@@ -789,6 +789,90 @@ def simulate_adjoint(piso, state, nsteps, loss_grad, wk=None, checkpoint_every=N
     return out
 
 
+def trajectory_adjoint(piso, state, nsteps, boundary, step_loss_grad, wk=None, checkpoint_every=None,
+                       stream=None, tapes=None):
+    """n PISO steps with boundary values that change from step to step, then
+    the adjoint of a loss summed over the steps' outputs,
+    L = sum_j l_j(state after step j), back to the initial state and the
+    parameters (Sec. 2.5, Eq. vjp, applied step by step in reverse).
+
+    state = [U, p, phi, U_b, p_b] as for simulate_adjoint (U, p, phi, p_b end at
+    the final state); boundary(j, U_b) writes the boundary values of step j into
+    U_b in place (it is called again for the same j when a segment is re-run);
+    step_loss_grad(j, U, p, phi, p_b, wk) returns the seeds (U_bar, p_bar,
+    phi_bar, p_b_bar, pc_bar) of l_j at the output of step j, any of them None
+    (no seed).  checkpoint_every = k keeps the state every k steps and re-runs
+    each segment with tapes (k tapes); None tapes every step.
+
+    Returns dict(U, p, phi, p_b, U_b, nu, status, and Rp, C, Rd, pc per outlet
+    when the handle has Windkessel outlets); U_b is the adjoint summed over the
+    steps' boundary values."""
+    U, p, phi, Ub, pb = state
+    k = nsteps if not checkpoint_every else max(1, min(int(checkpoint_every), nsteps))
+    if tapes is None or len(tapes) < k:
+        tapes = [piso.new_tape(U.device) for _ in range(k)]
+    n_out = piso.opts.n_out
+    worst = OK
+
+    def snap(src):
+        return [t.clone() for t in src[:4]] + [src[4].clone() if src[4] is not None else None]
+
+    cur = [U, p, phi, pb, wk]
+    snaps, outs = [], {}
+    for j in range(nsteps):
+        boundary(j, Ub)
+        if k == nsteps:
+            worst = max(worst, piso.step_record(U, p, phi, Ub, pb, tapes[j], wk=wk, stream=stream)[0])
+            outs[j] = snap(cur)
+        else:
+            if j % k == 0:
+                snaps.append(snap(cur))
+            worst = max(worst, piso.step(U, p, phi, Ub, pb, wk=wk, stream=stream)[0])
+    Ubar, pbar, phibar = torch.zeros_like(U), torch.zeros_like(p), torch.zeros_like(phi)
+    pbbar, Ubbar = torch.zeros_like(pb), torch.zeros_like(Ub)
+    nubar = torch.zeros(1, dtype=torch.float64, device=U.device)
+    wkbar = torch.zeros(4 * n_out, dtype=torch.float64, device=U.device) if n_out else None
+    info = torch.zeros(PISO_INFO_NBYTES, dtype=torch.uint8, device=U.device)
+
+    def seed(j, st):
+        g = step_loss_grad(j, *st)
+        if g is None:
+            return
+        for bar, v in zip((Ubar, pbar, phibar, pbbar), g[:4]):
+            if v is not None:
+                bar += v
+        if len(g) > 4 and g[4] is not None and n_out:
+            wkbar[3::4] += g[4]
+
+    seed(nsteps - 1, [U, p, phi, pb, wk])
+    piso.adjoint_reset(stream)
+    nseg = (nsteps + k - 1) // k
+    for sg in reversed(range(nseg)):
+        n0, n1 = sg * k, min(nsteps, sg * k + k)
+        if k != nsteps:      # re-run the segment from its checkpoint, recording tapes and outputs
+            seg = snaps[sg]
+            if n0 > 0:
+                outs[n0 - 1] = snap(seg)      # the checkpoint is step n0 - 1's output
+            for j in range(n0, n1):
+                boundary(j, Ub)
+                worst = max(worst, piso.step_record(seg[0], seg[1], seg[2], Ub, seg[3], tapes[j - n0],
+                                                    wk=seg[4], stream=stream)[0])
+                outs[j] = snap(seg)
+        for j in reversed(range(n0, n1)):
+            boundary(j, Ub)
+            st, _ = piso.step_bwd(tapes[j - n0], Ub, wk, Ubar, pbar, phibar, pbbar, wkbar, Ubbar, nubar,
+                                  info=info, stream=stream)
+            worst = max(worst, st)
+            if j > 0:
+                seed(j - 1, outs[j - 1])
+            outs.pop(j, None)
+    out = dict(U=Ubar, p=pbar, phi=phibar, p_b=pbbar, U_b=Ubbar, nu=nubar, status=worst, info=info)
+    if n_out:
+        w = wkbar.view(n_out, 4)
+        out.update(Rp=w[:, 0], C=w[:, 1], Rd=w[:, 2], pc=w[:, 3])
+    return out
+
+
 def _simulate_adjoint_binomial(piso, state, nsteps, loss_grad, wk, s, stream, tapes):
     U, p, phi, Ub, pb = state
     acts = binomial_schedule(nsteps, s)

@@ -489,6 +489,25 @@ def pipe_ohgrid(n_core=16, n_outer=8, n_layers=200, R=1.0, L=10.0, core_frac=0.5
                          bottom=("inlet", INLET), top=("outlet", outlet_type))
 
 
+def pipe_inflow(mesh: Mesh):
+    """Inlet boundary velocities of unit flux for an O-H pipe: a parabolic
+    profile in the face-centre radius (kept positive on every inlet face),
+    along +z, scaled so that sum_f u_f |S_f| = 1 over the inlet.  Returns
+    [3, n_boundary] (zero off the inlet); multiply by Q(t) for the flow Q."""
+    fin = mesh.patch_faces("inlet")
+    r2 = mesh.Cf[fin, 0] ** 2 + mesh.Cf[fin, 1] ** 2
+    shape = 1.0 - r2 / r2.max() * 0.999
+    area = np.linalg.norm(mesh.Sf[fin], axis=1)
+    ub = np.zeros((3, mesh.n_boundary))
+    ub[2, fin - mesh.n_internal] = shape / (shape * area).sum()
+    return ub
+
+
+def pulsatile_flow(t: float) -> float:
+    """Inlet flow of the pulsatile pipe: Q(t) = 1 + 0.5 sin 2 pi t + 0.2 sin 4 pi t."""
+    return 1.0 + 0.5 * np.sin(2 * np.pi * t) + 0.2 * np.sin(4 * np.pi * t)
+
+
 def distorted_box(n: int, eps: float = 0.05, nz: int = None, patch_types=None) -> Mesh:
     """Unit cube of n x n x nz prisms whose x-y grid is smoothly distorted.
 
