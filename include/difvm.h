@@ -239,6 +239,22 @@ enum { DIFVM_PROF_PCG_SPMV = 1, DIFVM_PROF_PCG_UPDATE = 2, DIFVM_PROF_PCG_PUPDAT
 difvm_status difvm_prof_start(int tag, int max_launches);
 difvm_status difvm_prof_stop(double* total_ms, int64_t* launches);
 uint64_t difvm_prof_bytes(void);
+/* Phases of the PISO step (Sec. 2.4.2): the Windkessel update and boundary
+ * values; the momentum assembly (gradients, face and cell coefficients); the
+ * momentum solve; per corrector the pressure assembly (HbyA, face fluxes,
+ * pressure matrix), the pressure solve and the flux and velocity correction.
+ * difvm_piso_step marks each phase with an NVTX range named "difvm:<phase>"
+ * (visible to tools that record NVTX).  While difvm_phase_prof_start is active
+ * it also records a CUDA event at every phase boundary on the step's stream (at
+ * most max_marks, 6 + 3 n_corr per step); difvm_phase_prof_stop synchronises
+ * and returns the summed milliseconds per phase in ms[DIFVM_PHASE_COUNT] and
+ * the number of steps.  Host-loop steps only: steps under stream capture
+ * (difvm_piso_step_graph) record nothing.  Process-wide, not thread-safe. */
+enum { DIFVM_PHASE_WINDKESSEL = 0, DIFVM_PHASE_MOMENTUM_ASSEMBLY = 1, DIFVM_PHASE_MOMENTUM_SOLVE = 2,
+       DIFVM_PHASE_PRESSURE_ASSEMBLY = 3, DIFVM_PHASE_PRESSURE_SOLVE = 4, DIFVM_PHASE_CORRECTION = 5,
+       DIFVM_PHASE_COUNT = 6 };
+difvm_status difvm_phase_prof_start(int max_marks);
+difvm_status difvm_phase_prof_stop(double* ms, int64_t* steps);
 
 /* ---------------------------------------------------------------- operators */
 /* Gauss gradient (Eq. gauss_green): grad_i = (1/V_i) sum_f sigma phi_f S_f,

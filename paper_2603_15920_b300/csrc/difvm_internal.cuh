@@ -28,6 +28,10 @@ difvm_status check_error(const char* what);    // pending launch error -> ECUDA
 void prof_before(int tag, cudaStream_t s);
 void prof_after(int tag, cudaStream_t s);
 void prof_bytes(int tag, uint64_t bytes);   // algorithmic bytes of the launch prof_before bracketed
+// PISO phase timing (difvm_phase_prof_start): phase_mark records an event on s
+// that starts `phase` (DIFVM_PHASE_*, or -1: the step ended) and opens the
+// matching NVTX range (the previous one closes); a no-op under stream capture.
+void phase_mark(int phase, cudaStream_t s);
 bool prof_active();
 
 #define DIFVM_CUDA(call)                                                            \

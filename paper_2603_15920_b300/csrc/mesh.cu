@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <numeric>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "difvm_internal.cuh"
 
 namespace difvm {
@@ -45,6 +47,32 @@ struct ProfState {
 static ProfState g_prof;
 
 bool prof_active() { return g_prof.tag != 0; }
+
+// phase timing of the PISO step
+struct PhaseState {
+  bool on = false;
+  int cap = 0;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ph;
+  int64_t steps = 0;
+};
+static PhaseState g_phase;
+static bool g_nvtx_open = false;
+static const char* const kPhaseNames[DIFVM_PHASE_COUNT] = {
+    "difvm:windkessel", "difvm:momentum_assembly", "difvm:momentum_solve", "difvm:pressure_assembly",
+    "difvm:pressure_solve", "difvm:correction"};
+
+void phase_mark(int phase, cudaStream_t s) {
+  if (stream_capturing(s)) return;
+  if (g_nvtx_open) nvtxRangePop();
+  g_nvtx_open = phase >= 0;
+  if (phase >= 0) nvtxRangePushA(kPhaseNames[phase]);
+  if (!g_phase.on || (int)g_phase.ph.size() >= g_phase.cap) return;
+  const size_t k = g_phase.ph.size();
+  cudaEventRecord(g_phase.ev[k], s);
+  g_phase.ph.push_back(phase);
+  if (phase < 0) ++g_phase.steps;
+}
 
 void prof_before(int tag, cudaStream_t s) {
   if (g_prof.tag == tag && g_prof.n < g_prof.cap) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
@@ -585,6 +613,42 @@ extern "C" uint64_t difvm_launch_count(void) { return g_launches.load(); }
 extern "C" uint64_t difvm_alg_bytes(void) { return g_alg_bytes.load(); }
 
 extern "C" uint64_t difvm_prof_bytes(void) { return g_prof.bytes; }
+
+extern "C" difvm_status difvm_phase_prof_start(int max_marks) {
+  if (max_marks <= 0) return set_error(DIFVM_EINVAL, "bad phase-profiling request");
+  if (g_phase.on) return set_error(DIFVM_EINVAL, "phase profiling already active");
+  g_phase.ev.resize((size_t)max_marks);
+  for (auto& e : g_phase.ev) DIFVM_CUDA(cudaEventCreate(&e));
+  g_phase.ph.clear();
+  g_phase.cap = max_marks;
+  g_phase.steps = 0;
+  g_phase.on = true;
+  return DIFVM_OK;
+}
+
+extern "C" difvm_status difvm_phase_prof_stop(double* ms, int64_t* steps) {
+  if (!g_phase.on) return set_error(DIFVM_EINVAL, "phase profiling not active");
+  difvm_status st = DIFVM_OK;
+  double tot[DIFVM_PHASE_COUNT] = {0};
+  for (size_t k = 0; k + 1 < g_phase.ph.size(); ++k) {
+    if (g_phase.ph[k] < 0) continue;   // between steps
+    float t = 0.f;
+    if (cudaEventSynchronize(g_phase.ev[k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, g_phase.ev[k], g_phase.ev[k + 1]) != cudaSuccess) {
+      st = set_error(DIFVM_ECUDA, "phase timing failed");
+      break;
+    }
+    tot[g_phase.ph[k]] += t;
+  }
+  if (ms)
+    for (int p = 0; p < DIFVM_PHASE_COUNT; ++p) ms[p] = tot[p];
+  if (steps) *steps = g_phase.steps;
+  for (auto& e : g_phase.ev) cudaEventDestroy(e);
+  g_phase.ev.clear();
+  g_phase.ph.clear();
+  g_phase.on = false;
+  return st;
+}
 
 extern "C" difvm_status difvm_prof_start(int tag, int max_launches) {
   if (tag <= 0 || max_launches <= 0) return set_error(DIFVM_EINVAL, "bad profiling request");

@@ -1211,6 +1211,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     }
   }
   // 1. Windkessel outlets
+  phase_mark(DIFVM_PHASE_WINDKESSEL, st);
   if (o.n_out > 0) {
     if (!wk) return set_error(DIFVM_EINVAL, "Windkessel outlets need the wk state array");
     // patch starts/sizes of the outlets live in a small device table after Qd/pod
@@ -1230,6 +1231,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
                                  cudaMemcpyDeviceToDevice, st));
   }
   // 2. momentum predictor
+  phase_mark(DIFVM_PHASE_MOMENTUM_ASSEMBLY, st);
   DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
   const bool no_U = (o.nonorth & DIFVM_NONORTH_MOMENTUM) != 0;
   const bool no_p = (o.nonorth & DIFVM_NONORTH_PRESSURE) != 0;
@@ -1258,6 +1260,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     DIFVM_TRY(amg_prebuild(m, h->mixed ? 4 : sizeof(T), Dp, Lp, h->wsp, h->wsp_bytes, h->side));
     DIFVM_CUDA(cudaEventRecord(h->ev_join, h->side));
   }
+  phase_mark(DIFVM_PHASE_MOMENTUM_SOLVE, st);
   {
     difvm_prec pr = sizeof(T) == 8 ? DIFVM_F64 : DIFVM_F32;
     difvm_status s = difvm_krylov_solve(m, pr, &o.solve_U, D, Lo, Up, rhs, U, 3, h->wsU, h->wsU_bytes,
@@ -1269,6 +1272,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
   if (prebuilt) DIFVM_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
   // 3. pressure correctors
   for (int corr = 0; corr < o.n_corr; ++corr) {
+    phase_mark(DIFVM_PHASE_PRESSURE_ASSEMBLY, st);
     k_HbyA<T><<<Bc, kPB, 0, st>>>(t, g, D, Lo, Up, b, U, HbyA, rAU);
     DIFVM_TRY(check_launch("HbyA"));
     if (no_p) {
@@ -1285,6 +1289,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     // multigrid operators the first one built
     difvm_solve_opts sp = o.solve_p;
     if ((corr > 0 || prebuilt) && amg_opts(sp)) sp.precond = DIFVM_PRECOND_AMG_REUSE;
+    phase_mark(DIFVM_PHASE_PRESSURE_SOLVE, st);
     difvm_status s;
     if (h->mixed) {
       k_to64<T><<<Bc, kPB, 0, st>>>(nc, bp, h->b64);
@@ -1301,6 +1306,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     }
     if (s == DIFVM_EINVAL || s == DIFVM_ECUDA) return s;
     worst = std::max(worst, (int)s);
+    phase_mark(DIFVM_PHASE_CORRECTION, st);
     k_flux_correct<T><<<Bf, kPB, 0, st>>>(t, phiH, af, no, p, pb, phi);
     DIFVM_TRY(check_launch("flux_correct"));
     DIFVM_TRY(grad_gauss_t<T>(m, DIFVM_BC_PRESSURE, p, pb, 1, gradp, st));
@@ -1315,6 +1321,7 @@ static difvm_status piso_step_t(difvm_piso* h, T* U, T* p, T* phi, const T* Ub, 
     k_piso_info<<<1, 32, 0, st>>>(h->sinfo, h->nk, o.n_corr, DIFVM_OK, o.n_out, Qd, pod, info);
     DIFVM_TRY(check_launch("piso_info"));
   }
+  phase_mark(-1, st);
   return (difvm_status)worst;
 }
 

@@ -195,6 +195,21 @@ def launch_count() -> int:
 PROF_PCG_SPMV, PROF_PCG_UPDATE, PROF_PCG_PUPDATE, PROF_AMG_RESID, PROF_AMG_POST1C = 1, 2, 3, 4, 5
 
 
+PHASES = ("windkessel", "momentum_assembly", "momentum_solve", "pressure_assembly", "pressure_solve",
+          "correction")
+
+
+def difvm_phase_prof_start(max_marks=100000):
+    _check(lib().difvm_phase_prof_start(int(max_marks)))
+
+
+def difvm_phase_prof_stop():
+    """Returns ({phase: summed ms}, steps) of the host-loop PISO steps since start."""
+    ms, n = (C.c_double * len(PHASES))(), C.c_int64()
+    _check(lib().difvm_phase_prof_stop(ms, C.byref(n)))
+    return {ph: float(ms[k]) for k, ph in enumerate(PHASES)}, int(n.value)
+
+
 def alg_bytes() -> int:
     """Algorithmic bytes of the Krylov and multigrid kernels launched so far."""
     return int(lib().difvm_alg_bytes())

@@ -225,8 +225,9 @@ def _channel_bc(m):
 
 
 def test_piso_channel_per_step_parity_f64():
-    """Poiseuille channel (64x16 hexes, shuffled ids), one GPU step from the
-    oracle's state at several points of the trajectory: 1e-9 per solved step."""
+    """Poiseuille channel (64x16 hexes, shuffled ids; the run is 200 steps of
+    dt = 0.01): one GPU step from the oracle's state at every tenth step of the
+    whole trajectory: 1e-9 per solved step."""
     m = mg.channel_2d(64, 16, seed=7)
     om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
     nu, dt = 0.05, 0.01
@@ -235,11 +236,14 @@ def test_piso_channel_per_step_parity_f64():
     phi = O.flux_from_U(om, U, Ub)
     pg = _piso(dm, D.F64, nu, dt)
     worst = 0.0
-    for step in range(12):
-        g = _state_to_gpu(dm, U, p, phi, Ub, pb)
-        st, info = pg.step(*g)
-        assert st == D.OK
+    for step in range(200):
+        g = _state_to_gpu(dm, U, p, phi, Ub, pb) if step % 10 == 0 else None
+        if g is not None:
+            st, info = pg.step(*g)
+            assert st == D.OK
         U, p, phi, pb, _, oi = O.piso_step(om, U, p, phi, Ub, pb, nu=nu, dt=dt, tolU=1e-12, tolp=1e-12)
+        if g is None:
+            continue
         for got, ref in ((dm.from_cells(host(g[0])), U), (dm.from_cells(host(g[1])), p),
                          (dm.from_faces(host(g[2])), phi)):
             worst = max(worst, nrel(got, ref))
@@ -249,8 +253,8 @@ def test_piso_channel_per_step_parity_f64():
 
 
 def test_piso_channel_trajectory_f64():
-    """The channel run as a whole trajectory (40 steps): GPU and oracle evolve
-    independently from the same initial state."""
+    """The channel run as a whole trajectory, all 200 steps (dt = 0.01, t = 2):
+    GPU and oracle evolve independently from the same initial state."""
     m = mg.channel_2d(64, 16, seed=3)
     om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
     nu, dt = 0.05, 0.01
@@ -259,12 +263,12 @@ def test_piso_channel_trajectory_f64():
     phi = O.flux_from_U(om, U, Ub)
     g = _state_to_gpu(dm, U, p, phi, Ub, pb)
     pg = _piso(dm, D.F64, nu, dt)
-    for _ in range(40):
+    for _ in range(200):
         assert pg.step(*g)[0] == D.OK
         U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=nu, dt=dt, tolU=1e-12, tolp=1e-12)
-    assert nrel(dm.from_cells(host(g[0])), U) < 1e-8
-    assert nrel(dm.from_cells(host(g[1])), p) < 1e-8
-    assert nrel(dm.from_faces(host(g[2])), phi) < 1e-8
+    errs = (nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p),
+            nrel(dm.from_faces(host(g[2])), phi))
+    assert max(errs) < 1e-8, errs
 
 
 def _cavity(n=6, seed=8):
@@ -412,3 +416,30 @@ def test_piso_f32_refine_within_1e4_of_f64_oracle():
     assert nrel(dm.from_cells(host(g[0])), U) < 1e-4
     assert nrel(dm.from_cells(host(g[1])), p) < 1e-4
     assert nrel(dm.from_faces(host(g[2])), phi) < 1e-4
+
+
+def test_phase_profile_splits_host_loop_steps():
+    # events at the phase boundaries of difvm_piso_step: one record per host-loop
+    # step, none for graph-launched steps; the phases cover the step
+    m, Ub = _cavity()
+    dm = D.Mesh(m)
+    pg = _piso(dm, D.F64, 0.01, 0.05, pref=17)
+    om = O.OMesh.from_mesh(m)
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    g = _state_to_gpu(dm, U, p, O.flux_from_U(om, U, Ub), Ub, pb)
+    torch.cuda.synchronize()
+    D.difvm_phase_prof_start(1000)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(3):
+        assert pg.step(*g)[0] == D.OK
+    b.record()
+    pg.step_graph(*g)
+    torch.cuda.synchronize()
+    ms, n = D.difvm_phase_prof_stop()
+    assert n == 3
+    assert set(ms) == set(D.PHASES)
+    assert ms["momentum_solve"] > 0 and ms["pressure_solve"] > 0 and ms["pressure_assembly"] > 0
+    assert sum(ms.values()) <= a.elapsed_time(b) * 1.01
+    with pytest.raises(D.DifvmError):
+        D.difvm_phase_prof_stop()
