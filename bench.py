@@ -215,6 +215,19 @@ def run_batched(D, torch, K=20, W=3, n_cases=64, seed=4, precond=None, f64=True,
                                                "p": nrel(s32[1], s64[1]), "phi": nrel(s32[2], s64[2])},
                       "f32_over_f64_speed": ms64 / ms32}
         del h64, s64
+    # the multigrid launch shapes first-use timing picked, and the same batch with the
+    # default shapes (difvm_mesh_autotune mode 0 restores them; a new handle captures
+    # a new graph)
+    out["tuned_launch_shapes"] = {f"{k[0]}.{k[1]}.{k[2]}": v for k, v in D.difvm_mesh_tuning(dm).items()
+                                  if k[0] in (5, 6)}
+    if f64 and adjoint:
+        D.difvm_mesh_autotune(dm, 0)
+        hf, sf, msf, gif = timed(D.F32)
+        out["default_launch_shapes"] = {"value": 1e3 / msf, "unit": "steps/s", "ms_per_step": msf,
+                                        "status": int(gif["status"]),
+                                        "tuned_over_default_speed": msf / ms32}
+        D.difvm_mesh_autotune(dm, 2)     # tuned again for the runs that follow
+        del hf, sf
     if adjoint:
         # forward + adjoint of the total kinetic energy after K steps (every step taped)
         V = torch.as_tensor(dm.to_cells(u.V), dtype=torch.float32, device="cuda")
@@ -916,6 +929,7 @@ def run_ours(args):
                    "api": "difvm_piso_step_graph (one CUDA graph per step, solver loops on the device)",
                    "l2": f"working set (~{0.9 * (args.mesh / 64) ** 3:.1f} GB) > 126 MB L2; no flush needed"},
         "gpu_launches": int(r32["launches"]),
+        "tuned_launch_shapes": {f"{k[0]}.{k[1]}.{k[2]}": v for k, v in D.difvm_mesh_tuning(dm).items()},
         "gpu_launches_note": "counted on the host-loop run of the same K steps; the graph replays "
                              "the same kernels plus at most 3 early-exit iterations and one "
                              "loop-condition kernel per pass of each solver loop",

@@ -162,15 +162,22 @@ difvm_status difvm_mesh_create(const difvm_mesh_desc* desc, difvm_mesh_t* out);
  * arguments and keeps the fastest for the mesh.  That first call synchronises
  * with the host; a first call under stream capture launches the default
  * variant and records nothing.  No device memory is allocated.
- * mode 0: no timing, every call launches the default variant; 1: timing on
- * (the default); 2: forget the kept choices and time again.  EINVAL on a bad
- * mode. */
+ * The multigrid preconditioner's launch shapes are tuned the same way, once,
+ * when its hierarchy is built (at the first call that needs it: a workspace
+ * query, difvm_piso_create or a solve): per level below the mesh level, the
+ * lanes per row of its sweeps (2, 4, 8) and per aggregate of its restriction
+ * (1, 8), timed on the level's sparsity.
+ * mode 0: no timing, every call launches the default variant and the multigrid
+ * takes its default shapes back; 1: timing on (the default); 2: forget the kept
+ * choices and time again (the multigrid shapes at once).  Graphs already
+ * captured keep the shapes they were captured with.  EINVAL on a bad mode. */
 difvm_status difvm_mesh_autotune(difvm_mesh_t, int mode);
 /* The kept choices, HOST outputs: keys[k] = operator << 8 | option << 4 |
  * components (operator 1 Gauss gradient, 2 divergence (option 1 upwind),
  * 3 Laplacian (option 1 with the non-orthogonal term), 4 LDU apply) and
- * variants[k] in 0..2; at most cap entries are written, *count gets the
- * number kept. */
+ * variants[k] in 0..2; multigrid: operator 5 (option = level) with the lanes
+ * per row, operator 6 (option = level) with the restriction's lanes per
+ * aggregate; at most cap entries are written, *count gets the number kept. */
 difvm_status difvm_mesh_tuning(difvm_mesh_t, uint32_t* keys, int32_t* variants, int cap, int32_t* count);
 /* Multigrid V-cycle launch shape (DIFVM_PRECOND_AMG): levels of fewer than
  * tail_rows rows, and the coarsest dense solve, run as one cooperative kernel

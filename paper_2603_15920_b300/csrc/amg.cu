@@ -74,6 +74,10 @@ struct AmgHier {
   int nlev = 0;
   std::vector<AmgLev> lev;
   std::vector<void*> allocs;
+  // launch shape per level: lanes per row of the level's sweeps, lanes per
+  // aggregate of its restriction into the next level (the defaults of
+  // amg_default_lanes, or what amg_tune measured fastest)
+  std::vector<int> tpr, rl;
 };
 
 void amg_free(AmgHier* h) {
@@ -325,6 +329,9 @@ std::mutex g_amg_mu;
 
 }  // namespace
 
+void amg_default_lanes(AmgHier* H);
+void amg_tune(difvm_mesh* m, AmgHier* H);
+
 difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
   std::lock_guard<std::mutex> lk(g_amg_mu);
   if (!m->amg) {
@@ -335,10 +342,21 @@ difvm_status amg_hier(difvm_mesh* m, AmgHier** out) {
       amg_free(H);
       return s;
     }
+    amg_default_lanes(H);
+    if (m->autotune) amg_tune(m, H);
     m->amg = H;
   }
   *out = m->amg;
   return DIFVM_OK;
+}
+
+// the mesh's autotune mode changed: 0 puts the default launch shapes back, 2
+// measures them again (a hierarchy not built yet is tuned when it is built)
+void amg_retune(difvm_mesh* m, int mode) {
+  std::lock_guard<std::mutex> lk(g_amg_mu);
+  if (!m->amg) return;
+  if (mode == 0) amg_default_lanes(m->amg);
+  else if (mode == 2) amg_tune(m, m->amg);
 }
 
 // ---------------------------------------------------------- workspace layout
@@ -1111,6 +1129,125 @@ static uint64_t lev_post1_bytes(const AmgLev& L, int n1, uint64_t v) {
 }
 static uint64_t lev_post2_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 5 * v; }
 
+// default launch shapes: lanes per row by amg_tpr; a restriction into a level
+// of at least kAmgBigLevel/4 rows one thread per aggregate (four children in
+// flight), into a smaller one eight lanes per aggregate
+void amg_default_lanes(AmgHier* H) {
+  H->tpr.assign(H->nlev, 1);
+  H->rl.assign(H->nlev, 8);
+  for (int l = 0; l < H->nlev; ++l) {
+    H->tpr[l] = amg_tpr(H->lev[l], l);
+    if (l + 1 < H->nlev) H->rl[l] = H->lev[l + 1].n >= kAmgBigLevel / 4 ? 1 : 8;
+  }
+}
+
+// Autotuning of the V-cycle's launch shapes, once per hierarchy: for every
+// level between the mesh level and the coarsest, its four sweeps (pre-smoothing,
+// residual, corrected and second post-smoothing) are timed with 2, 4 and 8
+// lanes per row, and its restriction with one thread and with eight lanes per
+// aggregate, on the level's own sparsity (the timing of these gathers does not
+// depend on the values, so zeroed operators and vectors stand in); the fastest
+// of each is kept.  FP32, the precision of the V-cycle on the fast path.  On any
+// CUDA error the defaults stay.  Results go to the mesh's tuning record: key
+// 5 << 8 | level << 4 -> lanes per row, 6 << 8 | level << 4 -> restriction lanes.
+void amg_tune(difvm_mesh* m, AmgHier* H) {
+  amg_default_lanes(H);
+  const int nl = H->nlev;
+  if (nl < 3) return;
+  size_t maxn = 1, maxs = 1;
+  for (int l = 1; l < nl; ++l) {
+    maxn = std::max(maxn, (size_t)H->lev[l].n);
+    maxs = std::max(maxs, (size_t)std::max(H->lev[l].nslots, 1));
+  }
+  float* buf = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const size_t nbytes = (7 * maxn + maxs) * sizeof(float) + 256;
+  if (cudaMalloc((void**)&buf, nbytes) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (buf) cudaFree(buf);
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    return;
+  }
+  cudaMemsetAsync(buf, 0, nbytes, s);
+  float *D = buf, *rD = buf + maxn, *r = buf + 2 * maxn, *y = buf + 3 * maxn, *u = buf + 4 * maxn;
+  float *v = buf + 5 * maxn, *xc = buf + 6 * maxn, *Lv = buf + 7 * maxn;
+  const int* done = reinterpret_cast<const int*>(Lv + maxs);   // zero: no early exit
+  const Mat<float> A{};
+  constexpr int kReps = 3;
+  auto timed = [&](auto&& launch) -> float {
+    launch();
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < kReps; ++k) launch();
+    cudaEventRecord(e1, s);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = -1.f;
+    return ms;
+  };
+  bool ok = true;
+  std::vector<int> tpr = H->tpr, rl = H->rl;
+  for (int l = 1; l + 1 < nl && ok; ++l) {
+    const AmgLev& L = H->lev[l];
+    const int n1 = H->lev[l + 1].n;
+    float best = -1.f;
+    for (int lanes : {2, 4, 8}) {
+      const unsigned B = blocks_for((int64_t)L.n * lanes, kAB);
+      const float ms = timed([&] {
+        if (lanes == 2) {
+          k_amg_pre<float, 2><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, done);
+          k_amg_resid<float, 2><<<B, kAB, 0, s>>>(L, A, D, Lv, r, y, u, done);
+          k_amg_post1<float, 2><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, xc, u, done);
+          k_amg_post2<float, 2><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, u, v, done);
+        } else if (lanes == 4) {
+          k_amg_pre<float, 4><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, done);
+          k_amg_resid<float, 4><<<B, kAB, 0, s>>>(L, A, D, Lv, r, y, u, done);
+          k_amg_post1<float, 4><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, xc, u, done);
+          k_amg_post2<float, 4><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, u, v, done);
+        } else {
+          k_amg_pre<float, 8><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, done);
+          k_amg_resid<float, 8><<<B, kAB, 0, s>>>(L, A, D, Lv, r, y, u, done);
+          k_amg_post1<float, 8><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, xc, u, done);
+          k_amg_post2<float, 8><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, u, v, done);
+        }
+      });
+      if (ms < 0.f) { ok = false; break; }
+      if (best < 0.f || ms < best) { best = ms; tpr[l] = lanes; }
+    }
+    best = -1.f;
+    for (int lanes : {1, 8}) {
+      const float ms = timed([&] {
+        if (lanes == 1) k_amg_restrict<float, 1><<<blocks_for(n1, kAB), kAB, 0, s>>>(n1, L, u, xc, done);
+        else k_amg_restrict<float, 8><<<blocks_for((int64_t)n1 * 8, kAB), kAB, 0, s>>>(n1, L, u, xc, done);
+      });
+      if (ms < 0.f) { ok = false; break; }
+      if (best < 0.f || ms < best) { best = ms; rl[l] = lanes; }
+    }
+  }
+  cudaStreamSynchronize(s);
+  ok = ok && cudaGetLastError() == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  cudaFree(buf);
+  cudaGetLastError();
+  if (!ok) return;
+  H->tpr = tpr;
+  H->rl = rl;
+  auto keep = [&](uint32_t key, int val) {
+    for (auto& kv : m->tuned)
+      if (kv.first == key) { kv.second = val; return; }
+    m->tuned.emplace_back(key, val);
+  };
+  for (int l = 1; l + 1 < nl; ++l) {
+    keep((uint32_t)(5 << 8 | l << 4), tpr[l]);
+    keep((uint32_t)(6 << 8 | l << 4), rl[l]);
+  }
+}
+
 // coarse operators of every level from the level-0 matrix (D, L symmetric)
 template <typename T>
 static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cudaStream_t st) {
@@ -1159,8 +1296,8 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
       t.r = R.at(R.Ly.r[l]);
       t.y = R.at(R.Ly.a[l]);
       t.u = R.at(R.Ly.b[l]);
-      t.tpr = amg_tpr(L, l);
-      t.rl = l + 1 < H->nlev && H->lev[l + 1].n >= kAmgBigLevel / 4 ? 1 : 8;
+      t.tpr = H->tpr[l];
+      t.rl = H->rl[l];
     }
     k_amg_tail_desc<T><<<1, 32, 0, st>>>(d, nl, (TailLev<T>*)(R.ws + R.Ly.tail));
     DIFVM_TRY(check_launch("amg_tail_desc"));
@@ -1226,7 +1363,7 @@ static void amg_tail_launch(const AmgRun<T>& R, const int* done, KState* st, int
 template <typename T, int TPR>
 static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, const T* D, const T* rD,
                        const T* Lv, const T* r, T* y, T* u, T* rc, T* xc, T* out, const KWork& w, int first,
-                       int down, cudaStream_t s) {
+                       int down, int rl, cudaStream_t s) {
   const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
   const unsigned B = blocks_for((int64_t)L.n * TPR, kAB);
   const uint64_t v = sizeof(T);
@@ -1239,7 +1376,7 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
     }
     launch_pdl(k_amg_resid<T, TPR>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
     if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
-    if (L1.n >= kAmgBigLevel / 4)
+    if (rl == 1)
       launch_pdl(k_amg_restrict<T, 1>, blocks_for(L1.n, kAB), kAB, s, L1.n, L, u, rc, done);
     else
       launch_pdl(k_amg_restrict<T, 8>, blocks_for((int64_t)L1.n * 8, kAB), kAB, s, L1.n, L, u, rc, done);
@@ -1300,12 +1437,12 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const AmgLev& L1 = H->lev[l + 1];
   T* rc = R.at(R.Ly.r[l + 1]);
   T* xc = R.at(R.Ly.a[l + 1]);   // written by the next level's last sweep
-  const int tpr = amg_tpr(L, l);
+  const int tpr = H->tpr[l], rl = H->rl[l];
   for (int down = 1; down >= 0; --down) {
-    if (tpr == 1) amg_sweeps<T, 1>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
-    else if (tpr == 2) amg_sweeps<T, 2>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
-    else if (tpr == 4) amg_sweeps<T, 4>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
-    else amg_sweeps<T, 8>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, s);
+    if (tpr == 1) amg_sweeps<T, 1>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
+    else if (tpr == 2) amg_sweeps<T, 2>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
+    else if (tpr == 4) amg_sweeps<T, 4>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
+    else amg_sweeps<T, 8>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
     if (down) amg_vcycle(R, l + 1, rc, xc, w, first, s);
   }
 }

@@ -310,6 +310,7 @@ constexpr int kGraphUnroll = 4;
 
 // ------------------------------------- multigrid-preconditioned CG (amg.cu)
 difvm_status amg_hier(difvm_mesh* m, AmgHier** out);
+void amg_retune(difvm_mesh* m, int mode);   // difvm_mesh_autotune's mode, applied to the hierarchy
 size_t amg_workspace_bytes(difvm_mesh* m, size_t elt);
 template <typename T>
 difvm_status amg_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,

@@ -902,6 +902,7 @@ extern "C" difvm_status difvm_mesh_autotune(difvm_mesh_t m, int mode) {
   if (mode < 0 || mode > 2) return set_error(DIFVM_EINVAL, "autotune mode must be 0, 1 or 2 (got %d)", mode);
   if (mode == 2) m->tuned.clear();
   m->autotune = mode != 0;
+  amg_retune(m, mode);
   return DIFVM_OK;
 }
 

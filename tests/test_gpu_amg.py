@@ -251,3 +251,25 @@ def test_fused_coarse_levels_batched_match_per_level_kernels():
         assert st == D.OK
         xs.append((info["iters"], x))
     assert xs[0][0] == xs[1][0] and np.array_equal(xs[0][1], xs[1][1])
+
+
+def test_multigrid_launch_shapes_are_tuned_and_solve_the_same_system():
+    # the hierarchy's lanes per row and restriction lanes are timed when it is
+    # built; the defaults (mode 0) and the tuned shapes solve to the same bar
+    m = mg.shuffle(mg.kuhn_cube(14, 0.2, 21), 22)
+    dm = D.Mesh(m)
+    om, Dg, Lg = _pressure_matrix(m, 11, pin=3)
+    b = np.random.default_rng(12).normal(size=m.n_cells)
+    b -= b.mean()
+    st, info, x = _solve(dm, m, Dg, Lg, b, D.PRECOND_AMG)
+    assert st == D.OK
+    kept = D.difvm_mesh_tuning(dm)
+    lanes = {k: v for k, v in kept.items() if k[0] == 5}
+    rlanes = {k: v for k, v in kept.items() if k[0] == 6}
+    assert lanes and set(lanes.values()) <= {2, 4, 8} and set(rlanes.values()) <= {1, 8}
+    D.difvm_mesh_autotune(dm, 0)
+    st0, info0, x0 = _solve(dm, m, Dg, Lg, b, D.PRECOND_AMG)
+    assert st0 == D.OK
+    ref, _ = O.pcg(om, Dg, Lg, None, b, tol_rel=1e-13, maxit=100000)
+    assert nrel(x, ref) < 1e-7 and nrel(x0, ref) < 1e-7
+    assert abs(info["iters"] - info0["iters"]) <= 1
