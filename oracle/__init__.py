@@ -246,6 +246,33 @@ def pcg_dic(m, D, L, b, rank, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
     return x, dict(iters=info.iters, res0=info.res0, res=info.res, bnorm=info.bnorm, status=info.status)
 
 
+def dilu_factor(m, D, L, U, rank):
+    """The diagonal d of the DILU factorisation (non-symmetric L, U) in the
+    elimination order rank[i]."""
+    d = np.zeros(m.nc)
+    lib().om_dilu_factor(m.ref(), _p(_f64(D)), _p(_f64(np.concatenate([L, [0.0]]))),
+                         _p(_f64(np.concatenate([U, [0.0]]))), _p(_i32(rank)), _p(d))
+    return d
+
+
+def dilu_apply(m, D, L, U, rank, r):
+    """z = M^-1 r with the DILU preconditioner M in the order rank[i]."""
+    z = np.zeros(m.nc)
+    lib().om_dilu_apply(m.ref(), _p(_f64(D)), _p(_f64(np.concatenate([L, [0.0]]))),
+                        _p(_f64(np.concatenate([U, [0.0]]))), _p(_i32(rank)), _p(_f64(r)), _p(z))
+    return z
+
+
+def bicgstab_dilu(m, D, L, U, b, rank, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
+    """BiCGStab right-preconditioned by DILU, cells eliminated in the order rank[i]."""
+    x = np.zeros(m.nc) if x0 is None else np.array(x0, np.float64)
+    info = _Info()
+    lib().om_bicgstab_dilu(m.ref(), _p(_f64(D)), _p(_f64(np.concatenate([L, [0.0]]))),
+                           _p(_f64(np.concatenate([U, [0.0]]))), _p(_i32(rank)), _p(_f64(b)), _p(x),
+                           C.c_double(tol_rel), C.c_double(tol_abs), int(maxit), C.byref(info))
+    return x, dict(iters=info.iters, res0=info.res0, res=info.res, bnorm=info.bnorm, status=info.status)
+
+
 def bicgstab(m, D, L, U, b, x0=None, tol_rel=1e-10, tol_abs=0.0, maxit=10000):
     return _solve("om_bicgstab", m, D, L, U, b, x0, tol_rel, tol_abs, maxit)
 

@@ -555,6 +555,140 @@ int om_pcg_dic(const om_mesh *m, const double *D, const double *L, const int *ra
   return info->status;
 }
 
+/* Diagonal incomplete LU (DILU): the same factorisation for the non-symmetric
+ * momentum matrix (Sec. 2.6.1 names ILU for the solvers).  Row O of an internal
+ * face holds U_f in column N and row N holds L_f in column O (as om_ldu_apply);
+ * in the elimination order rank, a(hi,lo) is the face's entry below the
+ * diagonal and a(lo,hi) the one above it.  With Dd = diag(d), Lo / Up the
+ * strictly lower / upper parts of A in that order,
+ *   M = (Dd + Lo) Dd^-1 (Dd + Up),   d_i = D_i - sum_{f: hi(f)=i} L_f U_f / d_lo(f)
+ * (the product a(hi,lo) a(lo,hi) is L_f U_f whichever side is lower):
+ * diag(M) = diag(A) and M = A on the matrix's sparsity pattern.  U == L (or
+ * NULL) gives the DIC factor. */
+static double dilu_lower(const om_mesh *m, const int *rank, int f, const double *L, const double *U) {
+  return rank[m->owner[f]] < rank[m->neighbour[f]] ? L[f] : U[f];   /* a(hi,lo) */
+}
+static double dilu_upper(const om_mesh *m, const int *rank, int f, const double *L, const double *U) {
+  return rank[m->owner[f]] < rank[m->neighbour[f]] ? U[f] : L[f];   /* a(lo,hi) */
+}
+
+void om_dilu_factor(const om_mesh *m, const double *D, const double *L, const double *U, const int *rank,
+                    double *d) {
+  int *ptr, *idx, *br;
+  if (!U) U = L;
+  dic_tables(m, rank, &ptr, &idx, &br);
+  for (int k = 0; k < m->nc; ++k) {
+    int i = br[k];
+    double s = D[i];
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int f = idx[e], lo, hi;
+      dic_sides(m, rank, f, &lo, &hi);
+      if (hi == i) s -= L[f] * U[f] / d[lo];
+    }
+    d[i] = s;
+  }
+  free(ptr); free(idx); free(br);
+}
+
+/* z = M^-1 r: forward (Dd + Lo) y = r, then backward (I + Dd^-1 Up) z = y */
+static void dilu_apply(const om_mesh *m, const int *rank, const int *ptr, const int *idx, const int *br,
+                       const double *d, const double *L, const double *U, const double *r, double *z) {
+  int nc = m->nc;
+  for (int k = 0; k < nc; ++k) {
+    int i = br[k];
+    double s = r[i];
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int f = idx[e], lo, hi;
+      dic_sides(m, rank, f, &lo, &hi);
+      if (hi == i) s -= dilu_lower(m, rank, f, L, U) * z[lo];
+    }
+    z[i] = s / d[i];
+  }
+  for (int k = nc - 1; k >= 0; --k) {
+    int i = br[k];
+    double s = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int f = idx[e], lo, hi;
+      dic_sides(m, rank, f, &lo, &hi);
+      if (lo == i) s += dilu_upper(m, rank, f, L, U) * z[hi];
+    }
+    z[i] -= s / d[i];
+  }
+}
+
+void om_dilu_apply(const om_mesh *m, const double *D, const double *L, const double *U, const int *rank,
+                   const double *r, double *z) {
+  int *ptr, *idx, *br;
+  if (!U) U = L;
+  double *d = malloc(sizeof(double) * m->nc);
+  om_dilu_factor(m, D, L, U, rank, d);
+  dic_tables(m, rank, &ptr, &idx, &br);
+  dilu_apply(m, rank, ptr, idx, br, d, L, U, r, z);
+  free(d); free(ptr); free(idx); free(br);
+}
+
+/* BiCGStab right-preconditioned by DILU in the elimination order rank: the
+ * steps of om_bicgstab below with y = M^-1 p and z = M^-1 s in place of the
+ * Jacobi scalings; same stopping rule. */
+int om_bicgstab_dilu(const om_mesh *m, const double *D, const double *L, const double *U, const int *rank,
+                     const double *b, double *x, double tol_rel, double tol_abs, int maxit, om_info *info) {
+  int n = m->nc;
+  if (!U) U = L;
+  double *r = malloc(sizeof(double) * n), *rh = malloc(sizeof(double) * n);
+  double *p = calloc(n, sizeof(double)), *v = calloc(n, sizeof(double));
+  double *y = malloc(sizeof(double) * n), *s = malloc(sizeof(double) * n);
+  double *z = malloc(sizeof(double) * n), *t = malloc(sizeof(double) * n);
+  double *d = malloc(sizeof(double) * n);
+  int *ptr, *idx, *br;
+  dic_tables(m, rank, &ptr, &idx, &br);
+  om_dilu_factor(m, D, L, U, rank, d);
+  double bn = sqrt(vdot(n, b, b));
+  info->bnorm = bn; info->iters = 0; info->status = 0;
+  if (bn == 0.0) {
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    info->res0 = info->res = 0.0;
+    goto done;
+  }
+  double tol = fmax(tol_rel * bn, tol_abs);
+  om_ldu_apply(m, 1, D, L, U, x, t);
+  for (int i = 0; i < n; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; }
+  double rn = sqrt(vdot(n, r, r));
+  info->res0 = rn;
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  while (rn > tol && it < maxit) {
+    double rho1 = vdot(n, rh, r);
+    if (rho1 == 0.0 || omega == 0.0) { info->status = 4; break; }
+    double beta = (rho1 / rho) * (alpha / omega);
+    rho = rho1;
+    for (int i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    dilu_apply(m, rank, ptr, idx, br, d, L, U, p, y);
+    om_ldu_apply(m, 1, D, L, U, y, v);
+    alpha = rho / vdot(n, rh, v);
+    for (int i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+    ++it;
+    double sn = sqrt(vdot(n, s, s));
+    if (sn <= tol) {
+      for (int i = 0; i < n; ++i) x[i] += alpha * y[i];
+      rn = sn;
+      break;
+    }
+    dilu_apply(m, rank, ptr, idx, br, d, L, U, s, z);
+    om_ldu_apply(m, 1, D, L, U, z, t);
+    double tt = vdot(n, t, t);
+    omega = tt > 0.0 ? vdot(n, t, s) / tt : 0.0;
+    for (int i = 0; i < n; ++i) { x[i] += alpha * y[i] + omega * z[i]; r[i] = s[i] - omega * t[i]; }
+    rn = sqrt(vdot(n, r, r));
+    if (!isfinite(rn)) { info->status = 5; break; }
+  }
+  info->iters = it; info->res = rn;
+  if (info->status == 0 && rn > tol) info->status = 3;
+done:
+  free(r); free(rh); free(p); free(v); free(y); free(s); free(z); free(t); free(d);
+  free(ptr); free(idx); free(br);
+  return info->status;
+}
+
 /* Right-Jacobi-preconditioned BiCGStab (van der Vorst 1992) for the
  * non-symmetric momentum system (Sec. 2.6.1).  Same stopping rule as om_pcg. */
 int om_bicgstab(const om_mesh *m, const double *D, const double *L, const double *U,
