@@ -613,7 +613,8 @@ def run_ours(args):
         phi = D.difvm_flux_from_U(dm, U, Ub)
         return [U, p, phi, Ub, pb]
 
-    def piso(prec, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND, time_scheme=D.TIME_BE, check_every=None):
+    def piso(prec, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND, time_scheme=D.TIME_BE, check_every=None,
+             precond_U=D.PRECOND_JACOBI):
         # pressure: CG preconditioned by one multigrid V-cycle (or Jacobi); the
         # Jacobi form polls less often since it runs ~50x more iterations
         ce = check_every or (32 if precond == D.PRECOND_JACOBI else 4)
@@ -625,16 +626,17 @@ def run_ours(args):
                                      inner_tol=1e-4, precond=precond),
                 pref_cell=pref, conv=conv, time_scheme=time_scheme))
         return D.Piso(dm, D.F64, D.piso_opts(
-            NU, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-10, max_iter=1000, check_every=4),
+            NU, DT, 2, NONORTH, solve_U=D.solve_opts(D.BICGSTAB, 1e-10, max_iter=1000, check_every=4,
+                                                     precond=precond_U),
             solve_p=D.solve_opts(D.PCG, 1e-10, max_iter=20000, check_every=ce, precond=precond),
             pref_cell=pref))
 
     info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
 
     def timed(prec, W, K, prof_tag=None, graph=False, precond=D.PRECOND_AMG, conv=D.CONV_UPWIND,
-              time_scheme=D.TIME_BE):
+              time_scheme=D.TIME_BE, precond_U=D.PRECOND_JACOBI):
         dt_ = torch.float32 if prec == D.F32 else torch.float64
-        h = piso(prec, precond, conv, time_scheme)
+        h = piso(prec, precond, conv, time_scheme, precond_U=precond_U)
         s = new_state(dt_)
 
         def one():
@@ -755,12 +757,21 @@ def run_ours(args):
     # the paper's preconditioner (diagonal incomplete Cholesky, level-scheduled): FP64, one
     # step (its sweeps advance one dependency level per launch: minutes per step above 64^3)
     if args.mesh <= N_KUHN:
-        rd = timed(D.F64, 1, 1, graph=True, precond=D.PRECOND_DIC)
+        rd = timed(D.F64, 1, 1, precond=D.PRECOND_DIC)
         dic = {"value": 1e3 / rd["ms"], "unit": "steps/s", "ms_per_step": rd["ms"], "steps": 1,
                "status": int(rd["status"]), "pressure_iters_last_step": rd["info"]["itp"][:2],
-               "api": "difvm_piso_step_graph, FP64, pressure CG with DIC (one launch per dependency level)"}
+               "launches_per_step": int(rd["launches"]),
+               "api": "difvm_piso_step, FP64, pressure CG with DIC (factor and each sweep one launch, rows "
+                      "waiting on the rows they depend on)"}
+        # the paper's preconditioning of both solves: DILU momentum BiCGStab, DIC pressure CG
+        ri = timed(D.F64, 1, 1, precond=D.PRECOND_DIC, precond_U=D.PRECOND_DIC)
+        dic["with_dilu_momentum"] = {"value": 1e3 / ri["ms"], "unit": "steps/s", "ms_per_step": ri["ms"],
+                                     "status": int(ri["status"]),
+                                     "pressure_iters_last_step": ri["info"]["itp"][:2],
+                                     "momentum_iters_last_step": ri["info"]["itU"],
+                                     "launches_per_step": int(ri["launches"])}
     else:
-        dic = {"skipped": f"not timed above {N_KUHN}^3 (one launch per dependency level)"}
+        dic = {"skipped": f"not timed above {N_KUHN}^3 (a chain of dependency levels per sweep)"}
     rs = timed(D.F32, W, K, graph=True, conv=D.CONV_SOU)
     sou = {"value": 1e3 * K / rs["ms"], "unit": "steps/s", "ms_per_step": rs["ms"] / K,
            "status": int(rs["status"]), "pressure_iters_last_step": rs["info"]["itp"][:2],

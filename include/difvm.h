@@ -92,14 +92,20 @@ enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
  * operators that the previous AMG solve with the same workspace built; the
  * caller guarantees the matrix is unchanged (e.g. the pressure matrix of the
  * second PISO corrector, which depends only on V/D). */
-/* DIFVM_PRECOND_DIC: diagonal incomplete Cholesky, the preconditioner the paper
- * names (Sec. 2.6.1), cells eliminated in the internal (RCM) numbering:
- * d_i = D_i - sum_{f: N(f)=i} L_f^2 / d_O(f), M = (Dd + Lo) Dd^-1 (Dd + Lo^T)
- * (M = A on the diagonal and on A's pattern).  The factor and the two
- * triangular sweeps run one dependency level per launch (levels built on the
- * host on first use and kept by the mesh; 437 on a 64^3 Kuhn mesh), so it is
- * slow; provided for fidelity and comparison.  Single-RHS CG on a symmetric
- * matrix of a single mesh, FP32 or FP64 without refinement (EINVAL otherwise). */
+/* DIFVM_PRECOND_DIC: the incomplete factorisation the paper names (Sec. 2.6.1),
+ * cells eliminated in the internal (RCM) numbering.  With CG on a symmetric
+ * matrix: diagonal incomplete Cholesky, d_i = D_i - sum_{f: N(f)=i} L_f^2 /
+ * d_O(f), M = (Dd + Lo) Dd^-1 (Dd + Lo^T).  With BiCGStab (1..3 right-hand
+ * sides, e.g. the PISO momentum solve): diagonal incomplete LU of the
+ * non-symmetric matrix, d_i = D_i - sum_{f: N(f)=i} L_f U_f / d_O(f),
+ * M = (Dd + Lo) Dd^-1 (Dd + Up), right preconditioning.  Either way M = A on the
+ * diagonal and on A's pattern.  The factor and each triangular sweep are one
+ * launch whose rows wait (bounded) on the rows they depend on, level by level
+ * (levels built on the host on first use and kept by the mesh; 437 on a 64^3
+ * Kuhn mesh), so an application is a chain of that many dependent steps; a
+ * wait that runs out ends the solve with DIFVM_ETIMEOUT.  Provided for fidelity
+ * and comparison.  A single mesh only; FP32 or FP64 without refinement
+ * (EINVAL otherwise). */
 enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1, DIFVM_PRECOND_AMG = 2,
        DIFVM_PRECOND_AMG_REUSE = 3, DIFVM_PRECOND_DIC = 4 };
 enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };

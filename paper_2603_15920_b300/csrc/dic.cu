@@ -8,10 +8,12 @@
 //                z_i -= (sum_{f: O(f)=i} L_f z_N(f)) / d_i             (backward)
 // with M = (Dd + Lo) Dd^-1 (Dd + Lo^T).  Both recurrences run along dependency
 // levels (level(i) = 1 + the largest level among the cells that i depends on),
-// computed once per mesh on the host: one launch per level for the factor and
-// per sweep, the backward sweep taking the levels in reverse order (every face
-// joins cells of different levels).  On a 64^3 Kuhn mesh that is 437 levels of
-// ~3,600 cells each, so an application costs ~870 dependent launches: the
+// computed once per mesh on the host; the backward sweep takes the levels in
+// reverse order (every face joins cells of different levels).  On a 64^3 Kuhn
+// mesh that is 437 levels of ~3,600 cells each.  Each sweep (and the factor) is
+// one launch whose rows wait on the rows they depend on (see the single-launch
+// sweeps below); the same sweeps apply DILU, the non-symmetric form, to the
+// momentum BiCGStab.  The chain of 437 dependent levels remains: the
 // preconditioner is here for fidelity and comparison; the multigrid V-cycle is
 // the fast one.
 #include <algorithm>
@@ -67,61 +69,227 @@ difvm_status dic_levels(difvm_mesh* m, DicLevels** out) {
   return DIFVM_OK;
 }
 
-constexpr int kDB = 256;
+}  // namespace
 
-// d_i = D_i - sum over faces where i is the neighbour of L_f^2 / d_owner
-template <typename T>
-__global__ void k_dic_factor(int n, const int* cells, Topo t, const T* D, const T* L, T* d) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int i = cells[k];
-  T s = D[i];
-  const int e1 = t.cptr[i + 1];
-  for (int e = t.cptr[i]; e < e1; ++e) {
-    const int ent = t.cent[e], f = ent >> 1;
-    if (f >= t.ni) break;
-    if (ent & 1) {
-      const T l = L[f];
-      s -= l * l / d[t.on[f].x];
+// ------------------------------------------------ single-launch level sweeps
+// The factor and the two triangular sweeps of DIC / DILU in one launch each,
+// instead of one launch per dependency level.  Rows are taken in level order
+// (the cells array: levels ascending; the backward sweep walks it from the
+// end): each warp claims the next 32 positions from a ticket, and a row waits
+// for the rows it depends on (the face partners of lower level) by polling
+// their ready flags, then computes and publishes its own flag.  A row's
+// dependencies come earlier in the order, so they were claimed by warps that
+// are already running: every wait ends (lanes of one warp may wait on each
+// other across a level boundary; independent thread scheduling lets them
+// progress).  A row loads its dependencies' indices and coefficients before it
+// waits.  Each wait is bounded (about 4M polls); one that runs out marks the
+// solver states DIFVM_ETIMEOUT and the row proceeds, so the launch always ends.
+// Flags hold the sweep's epoch (a counter bumped before every sweep), so they
+// need clearing once per solve only.  The sums run in CSR order, as in the
+// per-level kernels, so the results are the same bit for bit.
+struct SweepCtl {
+  unsigned epoch, ticket;
+};
+constexpr int kSB = 256;
+
+__global__ void k_sweep_begin(SweepCtl* c) {
+  c->epoch += 1u;
+  c->ticket = 0u;
+}
+
+__device__ __forceinline__ unsigned ld_acq(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_rlx(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// wait until row j is ready (relaxed polls, then one acquire fence); false if
+// the wait ran out
+__device__ __forceinline__ bool sweep_wait(const unsigned* flag, int j, unsigned epoch) {
+  if (ld_acq(flag + j) == epoch) return true;
+  for (int k = 0; k < (1 << 22); ++k) {
+    if (ld_rlx(flag + j) == epoch) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      return true;
     }
   }
-  d[i] = s;
+  return false;
 }
 
-// forward sweep of one level: z_i = (r_i - sum_{i neighbour} L_f z_owner) / d_i
-template <typename T>
-__global__ void k_dic_fwd(int n, const int* cells, Topo t, const T* L, const T* d, const T* r, T* z,
-                          const int* done) {
-  if (*done) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int i = cells[k];
-  T s = r[i];
-  const int e1 = t.cptr[i + 1];
-  for (int e = t.cptr[i]; e < e1; ++e) {
-    const int ent = t.cent[e], f = ent >> 1;
-    if (f >= t.ni) break;
-    if (ent & 1) s -= L[f] * z[t.on[f].x];
+// MODE 0: factor d_i = D_i - sum_{f: N(f)=i} L_f U_f / d_O(f)
+// MODE 1: forward z_i = (r_i - sum_{f: N(f)=i} L_f z_O(f)) / d_i     (NC components)
+// MODE 2: backward z_i -= (sum_{f: O(f)=i} U_f z_N(f)) / d_i
+template <typename T, int NC, int MODE>
+__global__ void __launch_bounds__(kSB) k_ilu_sweep(int nc, const int* __restrict__ order, Topo t,
+                                                   const T* __restrict__ D, const T* __restrict__ L,
+                                                   const T* __restrict__ U, T* d, const T* r, T* z,
+                                                   unsigned* flag, const SweepCtl* ctl, KState* st, int nst) {
+  if (MODE != 0) {   // a Krylov apply after every component converged: nothing to do
+    bool all = true;
+    for (int c = 0; c < nst; ++c) all = all && st[c].done;
+    if (all) return;
   }
-  z[i] = s / d[i];
+  const unsigned epoch = ctl->epoch;
+  unsigned* ticket = const_cast<unsigned*>(&ctl->ticket);
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (;;) {
+    unsigned cl = 0;
+    if (lane == 0) cl = atomicAdd(ticket, 1u);
+    cl = __shfl_sync(0xffffffffu, cl, 0);
+    const long long k = (long long)cl * 32 + lane;
+    if ((long long)cl * 32 >= nc) break;
+    if (k < nc) {
+      const int i = order[MODE == 2 ? nc - 1 - (int)k : (int)k];
+      const int e0 = t.cptr[i], e1 = t.cptr[i + 1];
+      // the row's dependencies (face partners eliminated before it) and their
+      // coefficients, loaded before any wait; rows of more than kDep such
+      // partners take the rest in a second pass
+      constexpr int kDep = 6;
+      int jd[kDep];
+      T cd[kDep];
+      int nd = 0, e = e0;
+      for (; e < e1 && nd < kDep; ++e) {
+        const int ent = t.cent[e], f = ent >> 1;
+        if (f >= t.ni) break;
+        const bool dep = MODE == 2 ? !(ent & 1) : (ent & 1);
+        if (!dep) continue;
+        const int2 on = t.on[f];
+        jd[nd] = MODE == 2 ? on.y : on.x;
+        cd[nd] = MODE == 0 ? L[f] * U[f] : (MODE == 1 ? L[f] : U[f]);
+        ++nd;
+      }
+      T s[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s[c] = T(0);
+      if (MODE == 0) s[0] = D[i];
+      if (MODE == 1)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] = r[c * nc + i];
+      for (int q = 0; q < nd; ++q) ok = sweep_wait(flag, jd[q], epoch) && ok;
+      for (int q = 0; q < nd; ++q) {
+        if (MODE == 0) s[0] -= cd[q] / __ldcg(d + jd[q]);
+        else if (MODE == 1)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s[c] -= cd[q] * __ldcg(z + c * nc + jd[q]);
+        else
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s[c] += cd[q] * __ldcg(z + c * nc + jd[q]);
+      }
+      for (; e < e1; ++e) {   // rows with more partners than kDep
+        const int ent = t.cent[e], f = ent >> 1;
+        if (f >= t.ni) break;
+        const bool dep = MODE == 2 ? !(ent & 1) : (ent & 1);
+        if (!dep) continue;
+        const int2 on = t.on[f];
+        const int j = MODE == 2 ? on.y : on.x;
+        ok = sweep_wait(flag, j, epoch) && ok;
+        if (MODE == 0) s[0] -= L[f] * U[f] / __ldcg(d + j);
+        else if (MODE == 1)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s[c] -= L[f] * __ldcg(z + c * nc + j);
+        else
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s[c] += U[f] * __ldcg(z + c * nc + j);
+      }
+      if (MODE == 0) {
+        d[i] = s[0];
+      } else if (MODE == 1) {
+        const T di = d[i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z[c * nc + i] = s[c] / di;
+      } else {
+        const T di = d[i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z[c * nc + i] -= s[c] / di;
+      }
+      st_rel(flag + i, epoch);   // release: the row's results are visible before its flag
+    }
+  }
+  if (!ok)
+    for (int c = 0; c < nst; ++c) {
+      st[c].status = DIFVM_ETIMEOUT;
+      st[c].done = 1;
+    }
 }
 
-// backward sweep of one level: z_i -= (sum_{i owner} L_f z_neighbour) / d_i
-template <typename T>
-__global__ void k_dic_bwd(int n, const int* cells, Topo t, const T* L, const T* d, T* z, const int* done) {
-  if (*done) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int i = cells[k];
-  T s = T(0);
-  const int e1 = t.cptr[i + 1];
-  for (int e = t.cptr[i]; e < e1; ++e) {
-    const int ent = t.cent[e], f = ent >> 1;
-    if (f >= t.ni) break;
-    if (!(ent & 1)) s += L[f] * z[t.on[f].y];
-  }
-  z[i] -= s / d[i];
+// workspace of the sweeps: the factor d, the ready flags, the control words
+size_t ilu_extra_bytes(const difvm_mesh* m, size_t elt) {
+  return (((size_t)m->nc * elt + 255) / 256 + ((size_t)m->nc * 4 + 255) / 256 + 1) * 256;
 }
+struct IluWs {
+  char* d;
+  unsigned* flag;
+  SweepCtl* ctl;
+};
+IluWs ilu_ws(const difvm_mesh* m, size_t elt, char* extra) {
+  const size_t a = ((size_t)m->nc * elt + 255) / 256 * 256, b = ((size_t)m->nc * 4 + 255) / 256 * 256;
+  return IluWs{extra, (unsigned*)(extra + a), (SweepCtl*)(extra + a + b)};
+}
+// one block per SM: more resident warps only poll further ahead of the front
+// (measured on the 64^3 Kuhn pressure matrix: 5.1 ms per DIC-CG iteration with
+// one block per SM, 5.6 ms with eight; sleeping between polls was slower)
+int sweep_grid(const difvm_mesh* m) {
+  return std::max(1, std::min((int)blocks_for(m->nc, kSB), m->num_sms));
+}
+
+// d of the DILU (U != L) or DIC (U == L) factor in the mesh's internal order
+template <typename T>
+difvm_status ilu_factor(difvm_mesh* m, const T* D, const T* L, const T* U, char* extra, KState* st, int nst,
+                        cudaStream_t s) {
+  DicLevels* DL = nullptr;
+  DIFVM_TRY(dic_levels(m, &DL));
+  const IluWs w = ilu_ws(m, sizeof(T), extra);
+  DIFVM_CUDA(cudaMemsetAsync(w.flag, 0, (size_t)m->nc * 4, s));
+  DIFVM_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(SweepCtl), s));
+  k_sweep_begin<<<1, 1, 0, s>>>(w.ctl);
+  k_ilu_sweep<T, 1, 0><<<sweep_grid(m), kSB, 0, s>>>(m->nc, DL->cells, m->topo(), D, L, U ? U : L, (T*)w.d,
+                                                      nullptr, nullptr, w.flag, w.ctl, st, nst);
+  count_launch();
+  return check_launch("ilu_factor");
+}
+
+// z = M^-1 r for ncomp components (r, z: [ncomp][nc]); skipped once st[0..nst) are done
+template <typename T>
+difvm_status ilu_apply(difvm_mesh* m, int ncomp, const T* L, const T* U, char* extra, const T* r, T* z,
+                       KState* st, int nst, cudaStream_t s) {
+  DicLevels* DL = m->dic;
+  const IluWs w = ilu_ws(m, sizeof(T), extra);
+  const int G = sweep_grid(m);
+  const Topo t = m->topo();
+  const T* Uu = U ? U : L;
+  k_sweep_begin<<<1, 1, 0, s>>>(w.ctl);
+  switch (ncomp) {
+    case 1: k_ilu_sweep<T, 1, 1><<<G, kSB, 0, s>>>(m->nc, DL->cells, t, nullptr, L, Uu, (T*)w.d, r, z, w.flag, w.ctl, st, nst); break;
+    case 2: k_ilu_sweep<T, 2, 1><<<G, kSB, 0, s>>>(m->nc, DL->cells, t, nullptr, L, Uu, (T*)w.d, r, z, w.flag, w.ctl, st, nst); break;
+    default: k_ilu_sweep<T, 3, 1><<<G, kSB, 0, s>>>(m->nc, DL->cells, t, nullptr, L, Uu, (T*)w.d, r, z, w.flag, w.ctl, st, nst); break;
+  }
+  k_sweep_begin<<<1, 1, 0, s>>>(w.ctl);
+  switch (ncomp) {
+    case 1: k_ilu_sweep<T, 1, 2><<<G, kSB, 0, s>>>(m->nc, DL->cells, t, nullptr, L, Uu, (T*)w.d, r, z, w.flag, w.ctl, st, nst); break;
+    case 2: k_ilu_sweep<T, 2, 2><<<G, kSB, 0, s>>>(m->nc, DL->cells, t, nullptr, L, Uu, (T*)w.d, r, z, w.flag, w.ctl, st, nst); break;
+    default: k_ilu_sweep<T, 3, 2><<<G, kSB, 0, s>>>(m->nc, DL->cells, t, nullptr, L, Uu, (T*)w.d, r, z, w.flag, w.ctl, st, nst); break;
+  }
+  for (int k = 0; k < 3; ++k) count_launch();
+  return check_launch("ilu_apply");
+}
+template difvm_status ilu_factor<float>(difvm_mesh*, const float*, const float*, const float*, char*, KState*, int,
+                                        cudaStream_t);
+template difvm_status ilu_factor<double>(difvm_mesh*, const double*, const double*, const double*, char*, KState*,
+                                         int, cudaStream_t);
+template difvm_status ilu_apply<float>(difvm_mesh*, int, const float*, const float*, char*, const float*, float*,
+                                       KState*, int, cudaStream_t);
+template difvm_status ilu_apply<double>(difvm_mesh*, int, const double*, const double*, char*, const double*,
+                                        double*, KState*, int, cudaStream_t);
+
+namespace {
 
 // r = b - A x; bb, rr; convergence at the start
 template <typename T, int MW>
@@ -216,7 +384,7 @@ __global__ void k_dcg_info(const KState* st, difvm_solve_info* info) {
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct DicLayout {
-  size_t val, r, p, q, z, d, st, part, ticket, total;
+  size_t val, r, p, q, z, st, part, ticket, extra, total;
 };
 DicLayout dic_layout(const difvm_mesh* m, size_t e, int G) {
   DicLayout L{};
@@ -227,10 +395,10 @@ DicLayout dic_layout(const difvm_mesh* m, size_t e, int G) {
   L.p = take((size_t)m->nc * e);
   L.q = take((size_t)m->nc * e);
   L.z = take((size_t)m->nc * e);
-  L.d = take((size_t)m->nc * e);
   L.st = take(sizeof(KState));
   L.part = take((size_t)G * kMaxParts * sizeof(double));
   L.ticket = take(256);
+  L.extra = take(ilu_extra_bytes(m, e));   // factor, ready flags, sweep control
   L.total = o;
   return L;
 }
@@ -255,7 +423,7 @@ static difvm_status dic_solve_mw(difvm_mesh* m, const difvm_solve_opts* o, const
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (DIC)", wsbytes, Ly.total);
   char* W = (char*)ws;
   T *val = (T*)(W + Ly.val), *r = (T*)(W + Ly.r), *p = (T*)(W + Ly.p), *q = (T*)(W + Ly.q);
-  T *z = (T*)(W + Ly.z), *d = (T*)(W + Ly.d);
+  T* z = (T*)(W + Ly.z);
   KWork w;
   w.st = (KState*)(W + Ly.st);
   w.part = (double*)(W + Ly.part);
@@ -270,24 +438,9 @@ static difvm_status dic_solve_mw(difvm_mesh* m, const difvm_solve_opts* o, const
   }
   const Mat<T> A{D, m->ell(), val};
   DIFVM_CUDA(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), st));
-  const int* done = &w.st[0].done;
-  // factor, level by level
-  for (int l = 0; l < DL->nlev; ++l) {
-    const int n = DL->ptr[l + 1] - DL->ptr[l];
-    k_dic_factor<T><<<blocks_for(n, kDB), kDB, 0, st>>>(n, DL->cells + DL->ptr[l], t, D, Lo, d);
-    count_launch();
-  }
-  DIFVM_TRY(check_error("dic_factor"));
+  DIFVM_TRY(ilu_factor<T>(m, D, Lo, Lo, W + Ly.extra, w.st, 1, st));
   auto apply = [&](cudaStream_t s) {   // z = M^-1 r
-    for (int l = 0; l < DL->nlev; ++l) {
-      const int n = DL->ptr[l + 1] - DL->ptr[l];
-      k_dic_fwd<T><<<blocks_for(n, kDB), kDB, 0, s>>>(n, DL->cells + DL->ptr[l], t, Lo, d, r, z, done);
-    }
-    for (int l = DL->nlev - 1; l >= 0; --l) {
-      const int n = DL->ptr[l + 1] - DL->ptr[l];
-      k_dic_bwd<T><<<blocks_for(n, kDB), kDB, 0, s>>>(n, DL->cells + DL->ptr[l], t, Lo, d, z, done);
-    }
-    for (int l = 0; l < 2 * DL->nlev; ++l) count_launch();
+    ilu_apply<T>(m, 1, Lo, Lo, W + Ly.extra, r, z, w.st, 1, s);
   };
   k_dcg_init<T, MW><<<G, kKB, 0, st>>>(t, A, b, x, r, w);
   k_dcg_zero<T><<<G, kKB, 0, st>>>(nc, x, w);

@@ -325,6 +325,16 @@ size_t dic_workspace_bytes(difvm_mesh* m, size_t elt);
 template <typename T>
 difvm_status dic_solve(difvm_mesh* m, const difvm_solve_opts* o, const T* D, const T* Lo, const T* b,
                        T* x, void* ws, size_t wsbytes, difvm_solve_info* info, cudaStream_t st);
+// incomplete factorisations in single-launch level sweeps (dic.cu): DILU of
+// (D, L, U), DIC when U == L or null; `extra` holds ilu_extra_bytes of workspace
+size_t ilu_extra_bytes(const difvm_mesh* m, size_t elt);
+struct KState;
+template <typename T>
+difvm_status ilu_factor(difvm_mesh* m, const T* D, const T* L, const T* U, char* extra, KState* st, int nst,
+                        cudaStream_t s);
+template <typename T>
+difvm_status ilu_apply(difvm_mesh* m, int ncomp, const T* L, const T* U, char* extra, const T* r, T* z,
+                       KState* st, int nst, cudaStream_t s);
 difvm_status check_mesh(const difvm_mesh* m);
 difvm_status check_prec(difvm_prec p);
 

@@ -519,10 +519,13 @@ static difvm_status read_states(KState* host, const KWork& w, cudaStream_t st, b
   return DIFVM_OK;
 }
 
+// Lraw, Uraw, extra: the LDU face coefficients and the DILU workspace, used with
+// DIFVM_PRECOND_DIC (BiCGStab preconditioned by DILU in the internal order)
 template <typename T, int NC, int MW>
 static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A, const T* b, T* x,
                              char* ws, const WsLayout& L, difvm_solve_info* info, cudaStream_t st,
-                             KState* host_state) {
+                             KState* host_state, const T* Lraw = nullptr, const T* Uraw = nullptr,
+                             char* extra = nullptr) {
   const int nc = m->nc;
   const int G = grid_for(m);
   Topo t = m->topo();
@@ -586,19 +589,28 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     k_zero_rhs<T, NC><<<G, kKB, 0, st>>>(nc, x, w);
     DIFVM_TRY(check_launch("zero_rhs"));
     // algorithmic bytes of one iteration: the LDU matrix (owner, neighbour, L, U per
-    // internal face; D) in each of the two products, NC-component vectors once per kernel
+    // internal face; D) in each of the two products, NC-component vectors once per kernel;
+    // a DILU application reads one triangle per sweep, the factor and the vectors
     const uint64_t vb = sizeof(T), ncu = (uint64_t)nc, nq = NC;
     const uint64_t mat = (uint64_t)m->ni * (8 + 2 * vb) + ncu * vb;
-    const uint64_t it_bytes = 4 * nq * ncu * vb + 2 * (ncu * vb + 2 * nq * ncu * vb) +
-                              2 * (mat + 3 * nq * ncu * vb) + 3 * nq * ncu * vb + 8 * nq * ncu * vb;
+    const bool dilu = o->precond == DIFVM_PRECOND_DIC;
+    const uint64_t prec_bytes = dilu ? 2 * ((uint64_t)m->ni * (8 + vb) + ncu * vb + 2 * nq * ncu * vb)
+                                     : ncu * vb + 2 * nq * ncu * vb;
+    const uint64_t it_bytes = 4 * nq * ncu * vb + 2 * prec_bytes + 2 * (mat + 3 * nq * ncu * vb) +
+                              3 * nq * ncu * vb + 8 * nq * ncu * vb;
+    if (dilu) DIFVM_TRY(ilu_factor<T>(m, A.D, Lraw, Uraw, extra, w.st, NC, st));
+    auto precond = [&](const T* a, T* out, cudaStream_t s) {
+      if (dilu) ilu_apply<T>(m, NC, Lraw, Uraw, extra, a, out, w.st, NC, s);
+      else k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, a, rD, out, w);
+    };
     DIFVM_TRY(run([&](cudaStream_t s) {
       count_bytes(it_bytes);
       k_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, w);
-      k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, p, rD, y, w);
+      precond(p, y, s);
       k_bicg_spmv1<T, NC, MW><<<G1, kKB, 0, s>>>(t, A, rh, y, v, w);
       k_bicg_s<T, NC><<<G, kKB, 0, s>>>(nc, r, v, s_, w);
       k_bicg_sfinish<T, NC><<<G, kKB, 0, s>>>(nc, y, x, w);
-      k_bicg_scale<T, NC><<<G, kKB, 0, s>>>(nc, s_, rD, z, w);
+      precond(s_, z, s);
       k_bicg_spmv2<T, NC, MW><<<G2, kKB, 0, s>>>(t, A, z, s_, tv, w);
       k_bicg_update<T, NC><<<Gu, kKB, 0, s>>>(nc, y, z, s_, tv, rh, x, r, w);
       for (int q = 0; q < 8; ++q) count_launch();
@@ -1497,15 +1509,18 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
                                      "symmetric matrix");
     return amg_solve<T>(m, o, (const T*)D, (const T*)L, (const T*)b, (T*)x, ws, wsbytes, info, st);
   }
+  const bool dilu = o->precond == DIFVM_PRECOND_DIC && o->method == DIFVM_BICGSTAB;
   if (o->precond == DIFVM_PRECOND_DIC) {
-    if (o->method != DIFVM_PCG || ncomp != 1 || U || m->seg)
-      return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner serves single-RHS CG on a "
-                                     "symmetric matrix of a single (not batched) mesh");
-    return dic_solve<T>(m, o, (const T*)D, (const T*)L, (const T*)b, (T*)x, ws, wsbytes, info, st);
+    if (m->seg || (o->method == DIFVM_PCG && (ncomp != 1 || U)))
+      return set_error(DIFVM_EINVAL, "the incomplete factorisation serves single-RHS CG on a symmetric "
+                                     "matrix (DIC) or BiCGStab (DILU), on a single (not batched) mesh");
+    if (!dilu) return dic_solve<T>(m, o, (const T*)D, (const T*)L, (const T*)b, (T*)x, ws, wsbytes, info, st);
   }
   WsLayout Ly = layout(m, sizeof(T), o->method, ncomp);
-  if (!ws || wsbytes < Ly.total)
-    return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed", wsbytes, Ly.total);
+  const size_t need = Ly.total + (dilu ? ilu_extra_bytes(m, sizeof(T)) : 0);
+  if (!ws || wsbytes < need)
+    return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed", wsbytes, need);
+  char* extra = dilu ? (char*)ws + Ly.total : nullptr;
   T* val = (T*)((char*)ws + Ly.val_off);
   DIFVM_TRY(fill_ell<T>(m, (const T*)L, (const T*)U, val, st));
   Mat<T> A{(const T*)D, m->ell(), val};
@@ -1527,7 +1542,8 @@ static difvm_status solve_t(difvm_mesh_t m, const difvm_solve_opts* o, const voi
 #undef DIFVM_SOLVE
     return set_error(DIFVM_EINVAL, "ncomp must be 1..3");
   }
-#define DIFVM_SOLVE(NC, MW) solve_nc<T, NC, MW>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs)
+#define DIFVM_SOLVE(NC, MW) solve_nc<T, NC, MW>(m, o, A, (const T*)b, (T*)x, (char*)ws, Ly, info, st, hs, \
+                                               (const T*)L, (const T*)(U ? U : L), extra)
   switch (ncomp * 16 + mw) {
     case 16 + 4: return DIFVM_SOLVE(1, 4);
     case 16 + 8: return DIFVM_SOLVE(1, 8);
@@ -1578,8 +1594,11 @@ extern "C" size_t difvm_krylov_opts_workspace_bytes(difvm_mesh_t m, difvm_prec p
     return amg_workspace_bytes(m, refine ? 4 : (prec == DIFVM_F64 ? 8 : 4));
   }
   if (o->precond == DIFVM_PRECOND_DIC) {
-    if (o->method != DIFVM_PCG || ncomp != 1 || m->seg || refine) return 0;
-    return dic_workspace_bytes(m, prec == DIFVM_F64 ? 8 : 4);
+    if (m->seg || refine) return 0;
+    if (o->method == DIFVM_PCG) return ncomp == 1 ? dic_workspace_bytes(m, prec == DIFVM_F64 ? 8 : 4) : 0;
+    dic_workspace_bytes(m, 4);   // builds the dependency levels
+    const size_t e = prec == DIFVM_F64 ? 8 : 4;
+    return difvm_krylov_workspace_bytes(m, prec, o->method, ncomp) + ilu_extra_bytes(m, e);
   }
   const size_t plain = difvm_krylov_workspace_bytes(m, prec, o->method, ncomp);
   return refine ? std::max(plain, difvm_krylov_refine_workspace_bytes(m, o->method, ncomp)) : plain;

@@ -1405,8 +1405,10 @@ extern "C" difvm_status difvm_piso_create(difvm_mesh_t m, difvm_prec prec, const
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner serves the pressure CG only");
   if (amg_opts(o->solve_p) && o->solve_p.method != DIFVM_PCG)
     return set_error(DIFVM_EINVAL, "the multigrid preconditioner needs CG");
-  if (o->solve_U.precond == DIFVM_PRECOND_DIC)
-    return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner serves the pressure CG only");
+  if (o->solve_U.precond == DIFVM_PRECOND_DIC &&
+      (o->solve_U.method != DIFVM_BICGSTAB || m->seg || (prec == DIFVM_F32 && o->solve_U.refine_max > 0)))
+    return set_error(DIFVM_EINVAL, "the incomplete LU preconditioner of the momentum solve needs BiCGStab "
+                                   "on a single (not batched) mesh");
   if (o->solve_p.precond == DIFVM_PRECOND_DIC &&
       (o->solve_p.method != DIFVM_PCG || m->seg || (prec == DIFVM_F32 && o->solve_p.refine_max > 0)))
     return set_error(DIFVM_EINVAL, "the incomplete-Cholesky preconditioner needs CG without refinement on a "

@@ -1,9 +1,11 @@
-"""GPU parity of the incomplete-Cholesky-preconditioned CG (DIFVM_PRECOND_DIC, the
-preconditioner the paper names, Sec. 2.6.1) against the oracle's DIC CG with the
-same elimination order (the library's internal RCM numbering): FP64 solutions at
-1e-9 with the iteration count within one, FP32 to its tolerance; a PISO step with
-the DIC pressure solve against the oracle's step (1e-9), and its CUDA-graph form
-bitwise equal to the host-driven step."""
+"""GPU parity of the incomplete factorisations (DIFVM_PRECOND_DIC, the
+preconditioning the paper names, Sec. 2.6.1) against the oracle with the same
+elimination order (the library's internal RCM numbering): DIC-preconditioned CG
+(FP64 solutions at 1e-9 with the iteration count within one, FP32 to its
+tolerance) and DILU-preconditioned BiCGStab on non-symmetric matrices (1 and 3
+right-hand sides); PISO steps with the DIC pressure solve and with DILU momentum
+plus DIC pressure against the oracle's step (1e-9), their CUDA-graph forms
+bitwise equal to the host-driven steps."""
 import numpy as np
 import pytest
 
@@ -102,12 +104,119 @@ def test_piso_step_with_dic_pressure_matches_oracle_and_graph():
     assert worst < 1e-9, worst
 
 
-def test_dic_rejects_batched_meshes_and_momentum():
+def test_incomplete_factorisations_reject_batched_meshes():
     ms = [mg.kuhn_cube(3, 0.2, 1), mg.kuhn_cube(4, 0.2, 2)]
     u, cs = mg.batch(ms)
     with pytest.raises(D.DifvmError):
         D.Piso(D.Mesh(u, case_cell_start=cs), D.F64,
                D.piso_opts(0.01, 0.05, 2, 3, solve_p=D.solve_opts(D.PCG, 1e-10, precond=D.PRECOND_DIC)))
     with pytest.raises(D.DifvmError):
-        D.Piso(D.Mesh(ms[0]), D.F64,
+        D.Piso(D.Mesh(u, case_cell_start=cs), D.F64,
                D.piso_opts(0.01, 0.05, 2, 3, solve_U=D.solve_opts(D.BICGSTAB, 1e-10, precond=D.PRECOND_DIC)))
+
+
+def _nonsym(m, seed):
+    """A diagonally dominant convection-diffusion-like LDU matrix (input numbering)."""
+    om = O.OMesh.from_mesh(m)
+    w, c, k = O.face_coeffs(om)
+    rng = np.random.default_rng(seed)
+    ni = m.n_internal
+    a = c[:ni] * rng.uniform(0.5, 2.0, ni)
+    mf = rng.normal(size=ni) * a.mean()
+    L, U = -a - np.maximum(mf, 0.0), -a + np.minimum(mf, 0.0)
+    Dg = np.bincount(m.owner[:ni], -U, m.n_cells) + np.bincount(m.neighbour, -L, m.n_cells) + 0.05 * a.mean()
+    return om, Dg, L, U
+
+
+@pytest.mark.parametrize("nq", [1, 3])
+@pytest.mark.parametrize("n", [5, 10])
+def test_dilu_bicgstab_matches_oracle_in_the_same_order(n, nq):
+    # BiCGStab preconditioned by DILU (DIFVM_PRECOND_DIC on a non-symmetric
+    # matrix), eliminated in the library's internal order, against the oracle's
+    # DILU BiCGStab in that order: FP64 solutions at 1e-9, iteration counts within one
+    m = mg.shuffle(mg.kuhn_cube(n, 0.2, 40 + n), 41 + n)
+    om, Dg, L, U = _nonsym(m, 5)
+    dm = D.Mesh(m)
+    rank = dm.cell_new_of_old.astype(np.int32)
+    ni = m.n_internal
+    fo, flip = dm.face_old_of_new[:ni], dm.face_flip[:ni] != 0
+    Li, Ui = np.where(flip, U[fo], L[fo]), np.where(flip, L[fo], U[fo])
+    B = np.random.default_rng(6).standard_normal((nq, m.n_cells))
+    x = torch.zeros(nq, dm.nc, dtype=torch.float64, device="cuda")
+    st, info = D.difvm_krylov_solve(dm, cuda(dm.to_cells(Dg)), cuda(Li), cuda(Ui), cuda(dm.to_cells(B)), x,
+                                    method=D.BICGSTAB, precond=D.PRECOND_DIC, tol_rel=1e-12, max_iter=2000)
+    assert st == D.OK, info
+    got = dm.from_cells(host(x))
+    for c in range(nq):
+        ref, ri = O.bicgstab_dilu(om, Dg, L, U, B[c], rank, tol_rel=1e-12, maxit=2000)
+        assert ri["status"] == 0
+        assert nrel(got[c], ref) < 1e-9, (c, nrel(got[c], ref))
+        assert abs(info[c]["iters"] - ri["iters"]) <= 1, (c, info[c]["iters"], ri["iters"])
+        _, rj = O.bicgstab(om, Dg, L, U, B[c], tol_rel=1e-12, maxit=2000)
+        assert ri["iters"] < rj["iters"]
+
+
+def test_piso_step_with_dilu_momentum_matches_oracle_and_graph():
+    # the paper's preconditioning of both solves: DILU for the momentum BiCGStab,
+    # DIC for the pressure CG; the solutions are the oracle step's to solver tolerance
+    m = mg.shuffle(mg.kuhn_cube(6, 0.2, 18), 19)
+    Ub = np.zeros((3, m.n_boundary))
+    Ub[0, m.patch_faces("y1") - m.n_internal] = 1.0
+    om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
+    pref = 7
+    o = D.piso_opts(0.01, 0.05, 2, 3,
+                    solve_U=D.solve_opts(D.BICGSTAB, 1e-12, max_iter=2000, precond=D.PRECOND_DIC),
+                    solve_p=D.solve_opts(D.PCG, 1e-12, max_iter=5000, precond=D.PRECOND_DIC),
+                    pref_cell=int(dm.cell_new_of_old[pref]))
+    pg = D.Piso(dm, D.F64, o)
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    phi = O.flux_from_U(om, U, Ub)
+    state = lambda: [cuda(dm.to_cells(U)), cuda(dm.to_cells(p)), cuda(dm.to_faces(phi)), cuda(dm.to_bnd(Ub)),
+                     cuda(dm.to_bnd(pb))]
+    worst = 0.0
+    for _ in range(3):
+        g, gg = state(), state()
+        assert pg.step(*g)[0] == D.OK
+        assert D.decode_piso_info(pg.step_graph(*gg))["status"] == D.OK
+        for a, b in zip(g, gg):
+            assert torch.equal(a, b)
+        U, p, phi, pb, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-12, tolp=1e-12,
+                                          pref_cell=pref, nonorth=3)
+        worst = max(worst, nrel(dm.from_cells(host(g[0])), U), nrel(dm.from_cells(host(g[1])), p),
+                    nrel(dm.from_faces(host(g[2])), phi))
+    assert worst < 1e-9, worst
+
+
+def test_piso_adjoint_with_incomplete_factorisations_matches_oracle():
+    # the step's adjoint solves use the same preconditioners on the transposed
+    # matrices (DILU of A^T for the momentum, DIC for the pressure)
+    m = mg.shuffle(mg.kuhn_cube(5, 0.2, 28), 29)
+    Ub = np.zeros((3, m.n_boundary))
+    Ub[0, m.patch_faces("y1") - m.n_internal] = 1.0
+    om, dm = O.OMesh.from_mesh(m), D.Mesh(m)
+    pref = 3
+    o = D.piso_opts(0.01, 0.05, 2, 3,
+                    solve_U=D.solve_opts(D.BICGSTAB, 1e-13, max_iter=2000, precond=D.PRECOND_DIC),
+                    solve_p=D.solve_opts(D.PCG, 1e-13, max_iter=5000, precond=D.PRECOND_DIC),
+                    pref_cell=int(dm.cell_new_of_old[pref]))
+    pg = D.Piso(dm, D.F64, o)
+    U, p, pb = np.zeros((3, m.n_cells)), np.zeros(m.n_cells), np.zeros(m.n_boundary)
+    phi = O.flux_from_U(om, U, Ub)
+    g = [cuda(dm.to_cells(U)), cuda(dm.to_cells(p)), cuda(dm.to_faces(phi)), cuda(dm.to_bnd(Ub)),
+         cuda(dm.to_bnd(pb))]
+    tape = pg.new_tape("cuda")
+    assert pg.step_record(*g, tape)[0] == D.OK
+    U1, _, _, _, _, _ = O.piso_step(om, U, p, phi, Ub, pb, nu=0.01, dt=0.05, tolU=1e-13, tolp=1e-13,
+                                    pref_cell=pref, nonorth=3)
+    wU = m.V * U1
+    Ubar, pbar, phibar = cuda(dm.to_cells(wU)), cuda(np.zeros(dm.nc)), cuda(np.zeros(dm.nf))
+    Ubbar = torch.zeros_like(g[3])
+    nubar = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st, _ = pg.step_bwd(tape, g[3], None, Ubar, pbar, phibar, None, None, Ubbar, nubar)
+    assert st == D.OK
+    ref = O.piso_step_bwd(om, U, p, phi, Ub, pb, wU, np.zeros(m.n_cells), np.zeros(m.n_faces), nu=0.01,
+                          dt=0.05, tolU=1e-13, tolp=1e-13, pref_cell=pref, nonorth=3)
+    for got, r in ((dm.from_cells(host(Ubar)), ref["U"]), (dm.from_faces(host(phibar)), ref["phi"]),
+                   (dm.from_bnd(host(Ubbar)), ref["Ub"])):
+        assert nrel(got, r) < 1e-9, nrel(got, r)
+    assert abs(float(nubar[0]) - ref["nu"]) < 1e-9 * abs(ref["nu"])
