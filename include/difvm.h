@@ -168,11 +168,13 @@ difvm_status difvm_mesh_create(const difvm_mesh_desc* desc, difvm_mesh_t* out);
  * arguments and keeps the fastest for the mesh.  That first call synchronises
  * with the host; a first call under stream capture launches the default
  * variant and records nothing.  No device memory is allocated.
- * The multigrid preconditioner's launch shapes are tuned the same way, once,
- * when its hierarchy is built (at the first call that needs it: a workspace
- * query, difvm_piso_create or a solve): per level below the mesh level, the
- * lanes per row of its sweeps (2, 4, 8) and per aggregate of its restriction
- * (1, 8), timed on the level's sparsity.
+ * The multigrid preconditioner's launch shapes are tuned once, when its
+ * hierarchy is built (at the first call that needs it: a workspace query,
+ * difvm_piso_create or a solve): per level below the mesh level, the lanes per
+ * row of its sweeps (2, 4, 8) and per aggregate of its restriction (1, 8), by
+ * timing whole V-cycles on a temporary workspace (allocated and freed then)
+ * one level at a time; a shape replaces the default only if the V-cycle is at
+ * least 2% faster.
  * mode 0: no timing, every call launches the default variant and the multigrid
  * takes its default shapes back; 1: timing on (the default); 2: forget the kept
  * choices and time again (the multigrid shapes at once).  Graphs already

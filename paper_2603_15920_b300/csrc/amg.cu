@@ -1141,113 +1141,6 @@ void amg_default_lanes(AmgHier* H) {
   }
 }
 
-// Autotuning of the V-cycle's launch shapes, once per hierarchy: for every
-// level between the mesh level and the coarsest, its four sweeps (pre-smoothing,
-// residual, corrected and second post-smoothing) are timed with 2, 4 and 8
-// lanes per row, and its restriction with one thread and with eight lanes per
-// aggregate, on the level's own sparsity (the timing of these gathers does not
-// depend on the values, so zeroed operators and vectors stand in); the fastest
-// of each is kept.  FP32, the precision of the V-cycle on the fast path.  On any
-// CUDA error the defaults stay.  Results go to the mesh's tuning record: key
-// 5 << 8 | level << 4 -> lanes per row, 6 << 8 | level << 4 -> restriction lanes.
-void amg_tune(difvm_mesh* m, AmgHier* H) {
-  amg_default_lanes(H);
-  const int nl = H->nlev;
-  if (nl < 3) return;
-  size_t maxn = 1, maxs = 1;
-  for (int l = 1; l < nl; ++l) {
-    maxn = std::max(maxn, (size_t)H->lev[l].n);
-    maxs = std::max(maxs, (size_t)std::max(H->lev[l].nslots, 1));
-  }
-  float* buf = nullptr;
-  cudaStream_t s = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  const size_t nbytes = (7 * maxn + maxs) * sizeof(float) + 256;
-  if (cudaMalloc((void**)&buf, nbytes) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    if (buf) cudaFree(buf);
-    if (s) cudaStreamDestroy(s);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaGetLastError();
-    return;
-  }
-  cudaMemsetAsync(buf, 0, nbytes, s);
-  float *D = buf, *rD = buf + maxn, *r = buf + 2 * maxn, *y = buf + 3 * maxn, *u = buf + 4 * maxn;
-  float *v = buf + 5 * maxn, *xc = buf + 6 * maxn, *Lv = buf + 7 * maxn;
-  const int* done = reinterpret_cast<const int*>(Lv + maxs);   // zero: no early exit
-  const Mat<float> A{};
-  constexpr int kReps = 3;
-  auto timed = [&](auto&& launch) -> float {
-    launch();
-    cudaEventRecord(e0, s);
-    for (int k = 0; k < kReps; ++k) launch();
-    cudaEventRecord(e1, s);
-    float ms = -1.f;
-    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = -1.f;
-    return ms;
-  };
-  bool ok = true;
-  std::vector<int> tpr = H->tpr, rl = H->rl;
-  for (int l = 1; l + 1 < nl && ok; ++l) {
-    const AmgLev& L = H->lev[l];
-    const int n1 = H->lev[l + 1].n;
-    float best = -1.f;
-    for (int lanes : {2, 4, 8}) {
-      const unsigned B = blocks_for((int64_t)L.n * lanes, kAB);
-      const float ms = timed([&] {
-        if (lanes == 2) {
-          k_amg_pre<float, 2><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, done);
-          k_amg_resid<float, 2><<<B, kAB, 0, s>>>(L, A, D, Lv, r, y, u, done);
-          k_amg_post1<float, 2><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, xc, u, done);
-          k_amg_post2<float, 2><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, u, v, done);
-        } else if (lanes == 4) {
-          k_amg_pre<float, 4><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, done);
-          k_amg_resid<float, 4><<<B, kAB, 0, s>>>(L, A, D, Lv, r, y, u, done);
-          k_amg_post1<float, 4><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, xc, u, done);
-          k_amg_post2<float, 4><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, u, v, done);
-        } else {
-          k_amg_pre<float, 8><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, done);
-          k_amg_resid<float, 8><<<B, kAB, 0, s>>>(L, A, D, Lv, r, y, u, done);
-          k_amg_post1<float, 8><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, y, xc, u, done);
-          k_amg_post2<float, 8><<<B, kAB, 0, s>>>(L, A, D, rD, Lv, r, u, v, done);
-        }
-      });
-      if (ms < 0.f) { ok = false; break; }
-      if (best < 0.f || ms < best) { best = ms; tpr[l] = lanes; }
-    }
-    best = -1.f;
-    for (int lanes : {1, 8}) {
-      const float ms = timed([&] {
-        if (lanes == 1) k_amg_restrict<float, 1><<<blocks_for(n1, kAB), kAB, 0, s>>>(n1, L, u, xc, done);
-        else k_amg_restrict<float, 8><<<blocks_for((int64_t)n1 * 8, kAB), kAB, 0, s>>>(n1, L, u, xc, done);
-      });
-      if (ms < 0.f) { ok = false; break; }
-      if (best < 0.f || ms < best) { best = ms; rl[l] = lanes; }
-    }
-  }
-  cudaStreamSynchronize(s);
-  ok = ok && cudaGetLastError() == cudaSuccess;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(s);
-  cudaFree(buf);
-  cudaGetLastError();
-  if (!ok) return;
-  H->tpr = tpr;
-  H->rl = rl;
-  auto keep = [&](uint32_t key, int val) {
-    for (auto& kv : m->tuned)
-      if (kv.first == key) { kv.second = val; return; }
-    m->tuned.emplace_back(key, val);
-  };
-  for (int l = 1; l + 1 < nl; ++l) {
-    keep((uint32_t)(5 << 8 | l << 4), tpr[l]);
-    keep((uint32_t)(6 << 8 | l << 4), rl[l]);
-  }
-}
-
 // coarse operators of every level from the level-0 matrix (D, L symmetric)
 template <typename T>
 static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cudaStream_t st) {
@@ -1548,6 +1441,99 @@ static KWork amg_work_t(const AmgRun<T>& R, int k, int maxit, double tol_rel, do
   w.tol_rel = tol_rel;
   w.tol_abs = tol_abs;
   return w;
+}
+
+// Autotuning of the V-cycle's launch shapes, once per hierarchy: whole FP32
+// V-cycles, launched exactly as the solvers launch them (programmatic
+// dependent launch), are timed on a temporary workspace whose operators and
+// vectors are zero (the timing of these gathers does not depend on the
+// values).  Level by level below the mesh level, the lanes per row of the
+// level's sweeps (2, 4, 8) and then the lanes per aggregate of its restriction
+// (1, 8) are varied with the other levels fixed, and a shape replaces the
+// current one only if the V-cycle is at least 2% faster.  The workspace is
+// freed afterwards; on any CUDA error the defaults stay.  Results go to the
+// mesh's tuning record: key 5 << 8 | level << 4 -> lanes per row,
+// 6 << 8 | level << 4 -> restriction lanes.
+void amg_tune(difvm_mesh* m, AmgHier* H) {
+  amg_default_lanes(H);
+  const int nl = H->nlev;
+  if (nl < 3) return;
+  AmgRun<float> R;
+  R.m = m;
+  R.H = H;
+  R.t = m->topo();
+  R.Ly = amg_layout(m, H, 4);
+  R.G = amg_grid(m);
+  const size_t bytes = R.Ly.total + ((size_t)m->nc * 4 + 255) / 256 * 256;
+  char* ws = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc((void**)&ws, bytes) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (ws) cudaFree(ws);
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    return;
+  }
+  cudaMemsetAsync(ws, 0, bytes, s);
+  R.ws = ws;
+  R.A = Mat<float>{(const float*)(ws + R.Ly.total), m->ell(), R.at(R.Ly.val)};
+  const KWork w = amg_work_t(R, 0, 1000, 0.0, 0.0);   // zeroed state: nothing converged
+  count_bytes_pause(true);
+  auto vcycles = [&]() -> float {
+    constexpr int kWarm = 2, kReps = 6;
+    for (int k = 0; k < kWarm; ++k) amg_vcycle(R, 0, R.vec(0), R.vec(3), w, 0, s);
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < kReps; ++k) amg_vcycle(R, 0, R.vec(0), R.vec(3), w, 0, s);
+    cudaEventRecord(e1, s);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = -1.f;
+    return ms;
+  };
+  bool ok = true;
+  float cur = vcycles();
+  ok = cur > 0.f;
+  auto try_shapes = [&](std::vector<int>& field, int l, std::initializer_list<int> cands) {
+    const int keep = field[l];
+    int best = keep;
+    float best_t = cur;
+    for (int c : cands) {
+      if (c == keep || !ok) continue;
+      field[l] = c;
+      const float t = vcycles();
+      if (t < 0.f) { ok = false; break; }
+      if (t < 0.98f * best_t) { best_t = t; best = c; }
+    }
+    field[l] = best;
+    cur = best_t;
+  };
+  for (int l = 1; l + 1 < nl && ok; ++l) {
+    try_shapes(H->tpr, l, {2, 4, 8});
+    try_shapes(H->rl, l, {1, 8});
+  }
+  count_bytes_pause(false);
+  cudaStreamSynchronize(s);
+  ok = ok && cudaGetLastError() == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  cudaFree(ws);
+  cudaGetLastError();
+  if (!ok) {
+    amg_default_lanes(H);
+    return;
+  }
+  auto keep = [&](uint32_t key, int val) {
+    for (auto& kv : m->tuned)
+      if (kv.first == key) { kv.second = val; return; }
+    m->tuned.emplace_back(key, val);
+  };
+  for (int l = 1; l + 1 < nl; ++l) {
+    keep((uint32_t)(5 << 8 | l << 4), H->tpr[l]);
+    keep((uint32_t)(6 << 8 | l << 4), H->rl[l]);
+  }
 }
 
 // Build the ELL values and multigrid operators of the matrix (D, Lo) in the

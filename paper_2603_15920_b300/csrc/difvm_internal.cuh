@@ -19,6 +19,7 @@ void count_launch();
 // write counted once at its logical size: no padding, re-reads or caching);
 // the solver kernels (Krylov, multigrid) add theirs at launch time
 void count_bytes(uint64_t bytes);
+void count_bytes_pause(bool paused);   // while paused (tuning runs), count_bytes adds nothing
 difvm_status check_launch(const char* what);   // counts one launch, then check_error
 difvm_status check_error(const char* what);    // pending launch error -> ECUDA
 

@@ -35,7 +35,11 @@ difvm_status set_error(difvm_status st, const char* fmt, ...) {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static std::atomic<uint64_t> g_alg_bytes{0};
-void count_bytes(uint64_t bytes) { g_alg_bytes.fetch_add(bytes, std::memory_order_relaxed); }
+static thread_local bool g_bytes_paused = false;
+void count_bytes(uint64_t bytes) {
+  if (!g_bytes_paused) g_alg_bytes.fetch_add(bytes, std::memory_order_relaxed);
+}
+void count_bytes_pause(bool paused) { g_bytes_paused = paused; }
 
 struct ProfState {
   int tag = 0;
