@@ -154,12 +154,23 @@ __host__ __device__ __forceinline__ int bc_kind(int cls, int cat) {
 // padding; fid[slot] = face id; nf[slot] = (nb, fid) in one 8-byte word.  The
 // Sw face records are also copied into slot order (a row's records then come
 // in with coalesced loads, without the face id).
+// Compact form (cw, fb; null where the mesh's numbering does not fit it): one
+// 4-byte word per slot carrying both the other cell and the face id.  An
+// internal slot of row i holds bit 31 = 0, bits 30..16 = j - i (15-bit signed,
+// never 0; its sign gives the side: j < i means the row is the neighbour) and
+// bits 15..0 = f - fb[i/32] (16-bit signed), fb[s] = the first face owned by
+// row 32 s; boundary and padding slots hold the nb word (negative).  RCM keeps
+// j - i within the ordering's bandwidth, so the 64^3 Kuhn mesh (|j - i| <= 7.7k,
+// f - fb >= -15.4k) fits.
 struct Hf {
   int W;
   const int* soff;
   const int* nb;
   const int* fid;
   const int2* nf;
+  const int* cw;
+  const int* fb;
+  int ni;
 };
 // boundary face index and patch category of a boundary slot word (v <= -2)
 __device__ __forceinline__ int hf_bface(int v) { return (-2 - v) >> 2; }
@@ -171,6 +182,7 @@ constexpr int kMaxBoundaryFaces = (1 << 29) - 1;
 template <typename T> struct HfGeo {
   const V4<T>* sw;
   const V4<T>* ck;
+  const T* w;     // w_f by face id (internal faces)
 };
 __device__ __forceinline__ void hf_row(const Hf& H, int i, int& base, int& w) {
   if (H.W > 0) {
@@ -256,6 +268,8 @@ struct difvm_mesh {
   int* hf_nb = nullptr;
   int* hf_fid = nullptr;
   int2* hf_nf = nullptr;
+  int* hf_cw = nullptr;      // compact slot words, or null (see difvm::Hf)
+  int* hf_fb = nullptr;      // [slices] first face owned by each slice's first row
   // face-operator launch variants picked by first-use timing (see ops.cu):
   // key -> variant, and whether timing is allowed
   std::vector<std::pair<uint32_t, int>> tuned;
@@ -265,14 +279,16 @@ struct difvm_mesh {
   int amg_tail_rows = -1, amg_tail_bps = -1;
   difvm::V4<double>* hf_sw64 = nullptr;
   difvm::V4<float>* hf_sw32 = nullptr;
+  double* w64 = nullptr;     // [ni] w_f, FP64 and FP32 copies
+  float* w32 = nullptr;
 
   difvm::Topo topo() const {
     return difvm::Topo{nc, ni, nf, nb, on, bown, cptr, cent, bkind, bpatch};
   }
   difvm::Ell ell() const { return difvm::Ell{ell_nsl, ell_w, ell_soff, ell_col, ell_map}; }
-  difvm::Hf hf() const { return difvm::Hf{hf_w, hf_soff, hf_nb, hf_fid, hf_nf}; }
-  difvm::HfGeo<double> hfgeo64() const { return {hf_sw64, nullptr}; }
-  difvm::HfGeo<float> hfgeo32() const { return {hf_sw32, nullptr}; }
+  difvm::Hf hf() const { return difvm::Hf{hf_w, hf_soff, hf_nb, hf_fid, hf_nf, hf_cw, hf_fb, ni}; }
+  difvm::HfGeo<double> hfgeo64() const { return {hf_sw64, nullptr, w64}; }
+  difvm::HfGeo<float> hfgeo32() const { return {hf_sw32, nullptr, w32}; }
   difvm::Geo<double> geo64() const { return {Sw64, ck64, V64, rV64}; }
   difvm::Geo<float> geo32() const { return {Sw32, ck32, V32, rV32}; }
 };

@@ -254,13 +254,21 @@ __global__ void k_hf_fill(int ns, const int* fid, const V4<double>* Sw64, const 
   hsw32[k] = Sw32[f];
 }
 
+// w_f of the internal faces as arrays of their own (read by face id)
+__global__ void k_w_fill(int ni, const V4<double>* Sw64, double* w64, float* w32) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= ni) return;
+  w64[f] = Sw64[f].w;
+  w32[f] = (float)Sw64[f].w;
+}
+
 static void free_mesh(difvm_mesh* m) {
   if (!m) return;
   void* ptrs[] = {m->on,   m->bown, m->cptr, m->cent, m->bkind, m->bpatch, m->Sw64,
                   m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
                   m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map,
                   m->seg_case, m->seg_cb0, m->seg_cs, m->hf_soff, m->hf_nb, m->hf_fid,
-                  m->hf_nf, m->hf_sw64, m->hf_sw32};
+                  m->hf_nf, m->hf_sw64, m->hf_sw32, m->hf_cw, m->hf_fb, m->w64, m->w32};
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
@@ -524,6 +532,36 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
     for (size_t k = 0; k < hnb.size(); ++k) hnf[k] = make_int2(hnb[k], hfid[k]);
     DIFVM_TRY(upload(&m->hf_nf, hnf.data(), hnf.size()));
   }
+  {
+    // compact slot words, where every internal slot fits (see difvm::Hf)
+    std::vector<int> hfb(nsl > 0 ? nsl : 1, 0), hcw(hnb.size(), -1);
+    int f0 = 0;
+    for (int sl = 0; sl < nsl; ++sl) {
+      while (f0 < ni && on[f0].x < 32 * sl) ++f0;
+      hfb[sl] = f0;
+    }
+    bool fits = true;
+    for (int i = 0; i < nc && fits; ++i) {
+      for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
+        const int slot = hsoff[i >> 5] + 32 * (e - cptr[i]) + (i & 31);
+        const int f = cent[e] >> 1;
+        if (f >= ni) {
+          hcw[slot] = hnb[slot];
+          continue;
+        }
+        const int dj = (hnb[slot] >> 1) - i, df = f - hfb[i >> 5];
+        if (dj < -16384 || dj > 16383 || df < -32768 || df > 32767) {
+          fits = false;
+          break;
+        }
+        hcw[slot] = (int)(((unsigned)dj & 0x7fffu) << 16 | ((unsigned)df & 0xffffu));
+      }
+    }
+    if (fits) {
+      DIFVM_TRY(upload(&m->hf_cw, hcw.data(), hcw.size()));
+      DIFVM_TRY(upload(&m->hf_fb, hfb.data(), hfb.size()));
+    }
+  }
   m->bown_host.assign(bown.begin(), bown.begin() + nb);
   if (d->case_cell_start) {
     // block tables of the segmented solvers (the case ranges survive the
@@ -566,6 +604,12 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
     k_hf_fill<<<blocks_for((int64_t)ns, 256), 256>>>((int)ns, m->hf_fid, m->Sw64, m->Sw32, m->hf_sw64,
                                                      m->hf_sw32);
     DIFVM_TRY(check_launch("hf_fill"));
+    DIFVM_TRY(upload<double>(&m->w64, nullptr, std::max(ni, 1)));
+    DIFVM_TRY(upload<float>(&m->w32, nullptr, std::max(ni, 1)));
+    if (ni > 0) {
+      k_w_fill<<<blocks_for(ni, 256), 256>>>(ni, m->Sw64, m->w64, m->w32);
+      DIFVM_TRY(check_launch("w_fill"));
+    }
   }
   DIFVM_CUDA(cudaDeviceSynchronize());
   cudaFree(Sf_d);

@@ -20,6 +20,10 @@ namespace difvm {
 constexpr int kBlock = 256;
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+// a rounded product that the compiler may not fuse into the following add, so
+// that a face message is the same number on both of its cells
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // A row's half-face slots, four at a time: their words (and face ids, or the
 // slot copies of the face records) arrive with coalesced loads issued before
@@ -40,9 +44,32 @@ __device__ __forceinline__ void hf_row_w(const Hf& H, int i, int& base, int& w) 
   }
 }
 
-// words (and, with FID, face ids) of slots k0..k0+3 of a row; -1 past its end
+// first face owned by the slice of row i (compact slot words only)
+__device__ __forceinline__ int hf_fbase(const Hf& H, int i) { return H.cw ? __ldg(H.fb + (i >> 5)) : 0; }
+
+// words (and, with FID, face ids) of slots k0..k0+3 of row i; -1 past its end.
+// With FID the compact words are read where the mesh has them (one 4-byte
+// load per slot instead of 8; fb = hf_fbase(H, i)).
 template <bool FID>
-__device__ __forceinline__ void hf_words(const Hf& H, int base, int k0, int w, int (&v)[4], int (&f)[4]) {
+__device__ __forceinline__ void hf_words(const Hf& H, int i, int fb, int base, int k0, int w, int (&v)[4],
+                                         int (&f)[4]) {
+  if (FID && H.cw) {
+    int q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = k0 + k < w ? __ldg(H.cw + base + 32 * (k0 + k)) : -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (q[k] >= 0) {
+        const int dj = (q[k] << 1) >> 17;           // bits 30..16, sign-extended
+        v[k] = 2 * (i + dj) + (dj < 0 ? 1 : 0);
+        f[k] = fb + (int)(short)(q[k] & 0xffff);
+      } else {
+        v[k] = q[k];
+        f[k] = q[k] <= -2 ? H.ni + hf_bface(q[k]) : 0;
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int slot = base + 32 * (k0 + k);
@@ -63,16 +90,24 @@ __device__ __forceinline__ void hf_words(const Hf& H, int base, int k0, int w, i
 // boundary kind of slot word v (v <= -2) for class cls
 __device__ __forceinline__ int hf_kind(int v, int cls) { return bc_kind(cls, hf_bcat(v)); }
 
-// component c of the value across slot word v: the other cell's (internal
-// face), the boundary value (fixed boundary face), the row's own value
-// (zero-gradient boundary face) or 0 (empty face, padding)
-template <typename T>
-__device__ __forceinline__ T hf_other(int v, int cls, const T* __restrict__ phi, const T* __restrict__ phib,
-                                      int nc, int nb, int c, T own) {
-  if (v >= 0) return ldg(phi + c * nc + (v >> 1));
-  if (v == -1) return T(0);
-  const int kind = hf_kind(v, cls);
-  return kind == DIFVM_FACE_FIXED ? ldg(phib + c * nb + hf_bface(v)) : (kind == DIFVM_FACE_ZEROGRAD ? own : T(0));
+// the NC components of the value across slot word v of row i: the other cell's
+// (internal face), the boundary value (fixed boundary face) or the row's own
+// value (zero-gradient boundary face; also returned for empty faces and
+// padding, which no sum uses).  The source is chosen once per slot, so every
+// component is one load with no per-component branch.
+template <typename T, int NC>
+__device__ __forceinline__ void hf_gather(int v, int cls, const T* __restrict__ phi, const T* __restrict__ phib,
+                                          int nc, int nb, int i, T (&out)[NC]) {
+  const T* src = phi + i;
+  int str = nc;
+  if (v >= 0) {
+    src = phi + (v >> 1);
+  } else if (v <= -2 && hf_kind(v, cls) == DIFVM_FACE_FIXED) {
+    src = phib + hf_bface(v);
+    str = nb;
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = ldg(src + c * str);
 }
 
 // slot k0+k takes no part in a sum: padding, or an empty boundary face
@@ -82,8 +117,10 @@ __device__ __forceinline__ bool hf_skip(int v, int cls) {
 
 // ----------------------------------------------------------- Gauss gradient
 // grad_i = (1/V_i) sum_f sigma phi_f S_f   (Eq. gauss_green).  Face records are
-// read from their slot copies (coalesced, no face id).
-template <typename T, int NC, int WK, int MINB>
+// read from their slot copies (coalesced, no face id), or with FIDGEO by face id
+// from the face arrays (compact slot words: half the index bytes, each record
+// from DRAM once).
+template <typename T, int NC, int WK, int MINB, bool FIDGEO = false>
 __global__ void __launch_bounds__(kBlock, MINB) k_grad_gauss(Topo t, Hf H, HfGeo<T> hg, Geo<T> g, int cls,
                                                              const T* __restrict__ phi,
                                                              const T* __restrict__ phib,
@@ -100,18 +137,21 @@ __global__ void __launch_bounds__(kBlock, MINB) k_grad_gauss(Topo t, Hf H, HfGeo
   const T r = ldg(g.rV + i);
   int base, w;
   hf_row_w<WK>(H, i, base, w);
+  const int fb = FIDGEO ? hf_fbase(H, i) : 0;
   for (int k0 = 0; k0 < w; k0 += 4) {
     int v[4], f[4];
-    hf_words<false>(H, base, k0, w, v, f);
+    hf_words<FIDGEO>(H, i, fb, base, k0, w, v, f);
     V4<T> s[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      s[k] = k0 + k < w ? ld4(hg.sw + base + 32 * (k0 + k)) : V4<T>{T(0), T(0), T(0), T(0)};
+    for (int k = 0; k < 4; ++k) {
+      if (FIDGEO)
+        s[k] = v[k] != -1 ? ld4(g.Sw + f[k]) : V4<T>{T(0), T(0), T(0), T(0)};
+      else
+        s[k] = k0 + k < w ? ld4(hg.sw + base + 32 * (k0 + k)) : V4<T>{T(0), T(0), T(0), T(0)};
+    }
     T pj[4][NC];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) pj[k][c] = hf_other(v[k], cls, phi, phib, nc, nb, c, pi[c]);
+    for (int k = 0; k < 4; ++k) hf_gather<T, NC>(v[k], cls, phi, phib, nc, nb, i, pj[k]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int vk = v[k];
@@ -208,14 +248,10 @@ __global__ void __launch_bounds__(kBlock) k_grad_gauss_bwd(Topo t, Geo<T> g, int
 // ------------------------------------------------------------ convection
 // out_i = sum_f sigma m_f phi_f   (Eqs. conv_face_flux, upwind; tie m=0 -> owner).
 // The face flux (and, for the linear scheme, w_f) is read by face id.
-template <typename T, int NC, bool UPWIND, int WK, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls,
-                                                           const T* __restrict__ mf,
-                                                           const T* __restrict__ phi,
-                                                           const T* __restrict__ phib,
-                                                           T* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= t.nc) return;
+template <typename T, int NC, bool UPWIND, int WK>
+__device__ __forceinline__ void div_row(const Topo& t, const Hf& H, const HfGeo<T>& hg, int cls,
+                                        const T* __restrict__ mf, const T* __restrict__ phi,
+                                        const T* __restrict__ phib, T* __restrict__ out, int i) {
   const int nc = t.nc, nb = t.nb;
   T pi[NC], acc[NC];
 #pragma unroll
@@ -225,39 +261,56 @@ __global__ void __launch_bounds__(kBlock, MINB) k_div_flux(Topo t, Hf H, HfGeo<T
   }
   int base, w;
   hf_row_w<WK>(H, i, base, w);
+  const int fb = hf_fbase(H, i);
   for (int k0 = 0; k0 < w; k0 += 4) {
     int v[4], f[4];
-    hf_words<true>(H, base, k0, w, v, f);
+    hf_words<true>(H, i, fb, base, k0, w, v, f);
     T mk[4], wk[4], pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       mk[k] = v[k] != -1 ? ldg(mf + f[k]) : T(0);
-      wk[k] = (!UPWIND && v[k] >= 0) ? ld4(hg.sw + f[k]).w : T(0);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) pj[k][c] = hf_other(v[k], cls, phi, phib, nc, nb, c, pi[c]);
+      wk[k] = (!UPWIND && v[k] >= 0) ? ldg(hg.w + f[k]) : T(0);
+      hf_gather<T, NC>(v[k], cls, phi, phib, nc, nb, i, pj[k]);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int vk = v[k];
       if (hf_skip(vk, cls)) continue;
-      const T m = mk[k];
-      if (vk >= 0) {
-        const bool nside = vk & 1;
+      // mm: the face flux out of this cell (-m on the neighbour side, exactly);
+      // the message mm * phi_f is then the owner's message or its exact negation
+      const bool nside = vk >= 0 && (vk & 1);
+      const T mm = nside ? -mk[k] : mk[k];
+      if (UPWIND) {
+        // upwind value: the own cell's on outflow, the other's on inflow (a
+        // boundary face always carries its boundary value); at m = 0 the
+        // message is a zero either way
+        const bool oth = vk < 0 || mm < T(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += mul_rn(mm, oth ? pj[k][c] : pi[c]);
+      } else if (vk >= 0) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T pO = nside ? pj[k][c] : pi[c], pN = nside ? pi[c] : pj[k][c];
-          const T pf = UPWIND ? (m >= T(0) ? pO : pN) : wk[k] * pO + (T(1) - wk[k]) * pN;
-          const T F = m * pf;
-          acc[c] += nside ? -F : F;
+          acc[c] += mul_rn(mm, wk[k] * pO + (T(1) - wk[k]) * pN);
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += m * pj[k][c];
+        for (int c = 0; c < NC; ++c) acc[c] += mul_rn(mm, pj[k][c]);
       }
     }
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) out[c * nc + i] = acc[c];
+}
+
+template <typename T, int NC, bool UPWIND, int WK, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_div_flux(Topo t, Hf H, HfGeo<T> hg, int cls,
+                                                           const T* __restrict__ mf,
+                                                           const T* __restrict__ phi,
+                                                           const T* __restrict__ phib,
+                                                           T* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < t.nc) div_row<T, NC, UPWIND, WK>(t, H, hg, cls, mf, phi, phib, out, i);
 }
 
 // Adjoint.  delta_f = obar_O - obar_N (internal) or obar_O (boundary):
@@ -356,17 +409,17 @@ __global__ void __launch_bounds__(kBlock, MINB) k_laplacian(Topo t, Hf H, HfGeo<
   }
   int base, w;
   hf_row_w<WK>(H, i, base, w);
+  const int fb = hf_fbase(H, i);
   for (int k0 = 0; k0 < w; k0 += 4) {
     int v[4], f[4];
-    hf_words<true>(H, base, k0, w, v, f);
+    hf_words<true>(H, i, fb, base, k0, w, v, f);
     V4<T> ck[4];
     T wk[4], pj[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       ck[k] = v[k] != -1 ? ld4(hg.ck + f[k]) : V4<T>{T(0), T(0), T(0), T(0)};
-      wk[k] = (NONORTH && v[k] >= 0) ? ld4(hg.sw + f[k]).w : T(0);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) pj[k][c] = hf_other(v[k], cls, phi, phib, nc, nb, c, pi[c]);
+      wk[k] = (NONORTH && v[k] >= 0) ? ldg(hg.w + f[k]) : T(0);
+      hf_gather<T, NC>(v[k], cls, phi, phib, nc, nb, i, pj[k]);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -480,9 +533,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_ldu_apply(Topo t, Hf H, const 
   for (int c = 0; c < NC; ++c) acc[c] = d * ldg(x + c * nc + i);
   int base, w;
   hf_row_w<WK>(H, i, base, w);
+  const int fb = hf_fbase(H, i);
   for (int k0 = 0; k0 < w; k0 += 4) {
     int v[4], fk[4];
-    hf_words<true>(H, base, k0, w, v, fk);
+    hf_words<true>(H, i, fb, base, k0, w, v, fk);
     T ak[4], xk[4][NC];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -564,7 +618,7 @@ static difvm_status check_cls(int cls) {
 // measurement on the 1.6M-cell Kuhn mesh.
 template <typename T> static HfGeo<T> fgeo(const difvm_mesh* m) {
   const Geo<T> g = geo<T>(m);
-  return HfGeo<T>{g.Sw, g.ck};
+  return HfGeo<T>{g.Sw, g.ck, hfgeo<T>(m).w};
 }
 
 // ------------------------------------------------------------- autotuning
@@ -640,7 +694,7 @@ difvm_status grad_gauss_t(difvm_mesh_t m, int cls, const void* phi, const void* 
     DIFVM_NC_SWITCH(ncomp, DIFVM_TRY(tuned_launch(m, tune_key(kOpGrad, 0, NCc), 0, s, [&](int var) {
       switch (var) {
         case 0: args(k_grad_gauss<T, NCc, 4, 1>); break;
-        case 1: args(k_grad_gauss<T, NCc, 4, 6>); break;
+        case 1: args(k_grad_gauss<T, NCc, 4, 1, true>); break;
         default: args(k_grad_gauss<T, NCc, 4, 8>); break;
       }
     })));
