@@ -44,6 +44,11 @@ constexpr double kAmgW2 = 1.0 / (1.25 - 0.75 * 0.70710678118654752);
 // over-correction of the coarse-grid correction (64^3 Kuhn cavity with the
 // Chebyshev-weighted sweeps: 22 CG iterations at 1.9 against 23 at 1.8 and 24 at 2.0)
 constexpr double kAmgScale = 1.9;
+// the first Jacobi iterate from zero, w1 rD r, rounded twice and never fused into
+// a following add: the restriction stores it for the coarse level's
+// pre-smoothing, and every kernel that forms it on the fly gets the same number
+__device__ __forceinline__ float amg_x1(float rD, float r) { return __fmul_rn(__fmul_rn((float)kAmgW1, rD), r); }
+__device__ __forceinline__ double amg_x1(double rD, double r) { return __dmul_rn(__dmul_rn(kAmgW1, rD), r); }
 constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 x 32)
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAB = 256;            // threads per block of the AMG kernels
@@ -360,16 +365,16 @@ void amg_retune(difvm_mesh* m, int mode) {
 }
 
 // ---------------------------------------------------------- workspace layout
-// [ELL values | r p q z | per level: D rD L r a b | coarsest inverse | states | partials |
+// [ELL values | r p q z | per level: D rD L E r s a b | coarsest inverse | states | partials |
 //  tickets | flags | fused-level descriptors | barrier]; a batched mesh has one state and
 //  one ticket per case
 struct AmgLayout {
   size_t val, vec[4], D[kAmgMaxLevels], rD[kAmgMaxLevels], L[kAmgMaxLevels], E[kAmgMaxLevels],
-      r[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, flag, tail, bar, total;
+      r[kAmgMaxLevels], s[kAmgMaxLevels], a[kAmgMaxLevels], b[kAmgMaxLevels], inv, st, part, ticket, flag, tail,
+      bar, total;
 };
 
 static size_t up256a(size_t b) { return (b + 255) / 256 * 256; }
-constexpr int kBarGroupsL = 16;   // counters of the fused kernel's grid barrier (kBarGroups)
 
 // the CG kernels and the level-0 sweep with r.z: grid-stride, one wave (their
 // grid reductions finish once instead of once per wave of blocks)
@@ -390,6 +395,7 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
     A.L[l] = take((size_t)L.nf * e);
     A.E[l] = take((size_t)(l > 0 ? L.nslots : 1) * e);   // sliced-ELL values (levels >= 1)
     A.r[l] = take((size_t)L.n * e);
+    A.s[l] = take((size_t)(l > 0 ? L.n : 1) * e);       // w1 rD r of a coarse level's r
     A.a[l] = take((size_t)L.n * e);
     A.b[l] = take((size_t)L.n * e);
   }
@@ -403,7 +409,7 @@ static AmgLayout amg_layout(const difvm_mesh* m, const AmgHier* H, size_t e) {
   A.ticket = take((size_t)(m->seg ? m->ncases : 2) * sizeof(unsigned));
   A.flag = take(4 * sizeof(int));
   A.tail = take(kAmgMaxLevels * 256);   // level descriptors of the fused coarse-level kernel
-  A.bar = take((2 + kBarGroupsL) * 128); // its grid barrier (one 128-byte line per counter)
+  A.bar = take(128);                     // its grid barrier's arrival counter
   A.total = o;
   return A;
 }
@@ -616,16 +622,18 @@ __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* 
   }
 }
 
-// pre-smoothing from zero, two sweeps: x1 = w1 rD r, y = x1 + w2 rD (r - A x1)
-template <typename T, int TPR>
+// pre-smoothing from zero, two sweeps: x1 = w1 rD r, y = x1 + w2 rD (r - A x1).
+// PS: x1 comes in formed (sr, written with r by the restriction), so a column
+// costs one gather instead of two.
+template <typename T, int TPR, bool PS>
 __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
-                                                 const T* r, T* y, const int* done) {
+                                                 const T* r, const T* sr, T* y, const int* done) {
   pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
-  const T w1 = (T)kAmgW1, w2 = (T)kAmgW2;
-  auto x1 = [&](int j) { return w1 * rD[j] * r[j]; };
+  const T w2 = (T)kAmgW2;
+  auto x1 = [&](int j) { return PS ? sr[j] : amg_x1(rD[j], r[j]); };
   const T ax = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, x1);
   if (ok && t == 0) y[i] = x1(i) + w2 * rD[i] * (r[i] - ax);
 }
@@ -643,11 +651,13 @@ __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* 
   if (ok && t == 0) res[i] = r[i] - ay;
 }
 
-// restriction: rc_K = sum of res over the cells of K.  RL == 1: one thread
-// per K, four children in flight; RL > 1: RL lanes per K, each summing its
-// children in ascending order, then a fixed xor tree.
+// restriction: rc_K = sum of res over the cells of K, and sc_K = w1 rD_K rc_K
+// (the coarse level's first Jacobi iterate, for its pre-smoothing).  RL == 1:
+// one thread per K, four children in flight; RL > 1: RL lanes per K, each
+// summing its children in ascending order, then a fixed xor tree.
 template <typename T, int RL>
-__global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T* res, T* rc, const int* done) {
+__global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T* res, T* rc, const T* rD1,
+                                                      T* sc, const int* done) {
   pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, K = g / RL, t = g % RL;
@@ -669,7 +679,10 @@ __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T*
   }
 #pragma unroll
   for (int d = RL / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-  if (K < n1 && t == 0) rc[K] = s;
+  if (K < n1 && t == 0) {
+    rc[K] = s;
+    sc[K] = amg_x1(rD1[K], s);
+  }
 }
 
 // coarse correction and the first post-smoothing sweep: z = y + s P xc (formed
@@ -809,50 +822,41 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid barrier of a cooperative launch (every block resident), two-level so that
-// no counter takes more than ~32 arrivals: block b arrives on group counter
-// b % kBarGroups; the last of a group arrives on the root counter; the last at
-// the root resets the root and bumps the generation (group counters are reset
-// by their last arriver).  Waiters spin on the generation, at most ~4M polls
-// (about a second).  bar: [0] generation, [1] root count, [2..] group counts,
-// each on its own 128-byte line.  Returns false in every thread of a block
-// whose wait ran out.
-constexpr int kBarGroups = kBarGroupsL;
-constexpr int kBarStride = 32;   // unsigned per 128-byte line
-__device__ __forceinline__ bool tail_barrier(unsigned* bar, unsigned& gen) {
+// Grid barrier of a cooperative launch (every block resident): one arrival
+// counter that only grows.  Every launch passes the same number of barriers,
+// nbar, so the counter is a multiple of nbar G (G = blocks) when a launch starts
+// (no block can pass the first barrier before all have arrived, so at most G - 1
+// arrivals are ahead of a block that reads it then): base = the counter at the
+// start rounded down to that multiple, and barrier k completes when the counter
+// reaches base + (k + 1) G.  A block's thread 0 arrives with a release add and
+// waits with acquire loads, at most ~4M polls (about a second); a wait that runs
+// out returns false in every thread of its block (the solve is then closed with
+// DIFVM_ETIMEOUT, and the counter is cleared before the next solve).
+struct TailBar {
+  unsigned* ctr;
+  unsigned next;   // the counter value that completes the next barrier
+};
+__device__ __forceinline__ TailBar tail_bar_start(unsigned* ctr, unsigned nbar) {
+  const unsigned G = gridDim.x, span = (nbar > 0 ? nbar : 1u) * G;
+  const unsigned c = threadIdx.x == 0 ? ld_acquire_u32(ctr) : 0u;   // only thread 0 waits
+  return TailBar{ctr, c - c % span + G};
+}
+__device__ __forceinline__ bool tail_barrier(TailBar& b) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = gen;
-    const unsigned nb = gridDim.x, grp = blockIdx.x % kBarGroups;
-    const unsigned ngrp = nb < kBarGroups ? nb : kBarGroups;
-    const unsigned in_grp = nb / kBarGroups + (grp < nb % kBarGroups ? 1u : 0u);
-    __threadfence();
-    unsigned* gc = bar + (2 + grp) * kBarStride;
-    bool last = false;
-    if (atomicAdd(gc, 1u) == in_grp - 1) {
-      *gc = 0u;
-      __threadfence();
-      last = atomicAdd(bar + kBarStride, 1u) == ngrp - 1;
-    }
-    if (last) {
-      bar[kBarStride] = 0u;
-      __threadfence();
-      atomicExch(bar, g + 1);
-    } else {
-      int spins = 0;
-      while (ld_acquire_u32(bar) == g) {
-        if (++spins > (1 << 22)) {
-          ok = 0;
-          break;
-        }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(b.ctr) : "memory");
+    int spins = 0;
+    while ((int)(ld_acquire_u32(b.ctr) - b.next) < 0) {
+      if (++spins > (1 << 22)) {
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
-    gen = g + 1;
     ok_s = ok;
   }
+  b.next += gridDim.x;
   __syncthreads();
   return ok_s != 0;
 }
@@ -869,11 +873,11 @@ __device__ __forceinline__ void tail_rows(int n, F&& body) {
 
 template <typename T, int TPR>
 __device__ void tail_pre(const TailLev<T>& P) {
-  const T w1 = (T)kAmgW1, w2 = (T)kAmgW2;
+  const T w2 = (T)kAmgW2;
   const Mat<T> A{};
   tail_rows<T, TPR>(P.L.n, [&](int i, int t) {
     const bool ok = i < P.L.n;
-    auto x1 = [&](int j) { return w1 * P.rD[j] * __ldcg(P.r + j); };
+    auto x1 = [&](int j) { return amg_x1(P.rD[j], __ldcg(P.r + j)); };
     const T ax = lev_row<T, TPR>(A, P.L, P.D, P.Lv, i, t, ok, x1);
     if (ok && t == 0) P.y[i] = x1(i) + w2 * P.rD[i] * (__ldcg(P.r + i) - ax);
   });
@@ -965,30 +969,29 @@ __global__ void __launch_bounds__(kTB, 2) k_amg_tail(TailArgs<T> P) {
     for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
   }
   __syncthreads();
-  unsigned gen = 0;
-  if (threadIdx.x == 0) gen = ld_acquire_u32(P.bar);
   const int nl = P.nlev;
+  TailBar bar = tail_bar_start(P.bar, 5u * (unsigned)(nl - 1));   // the barriers below, per launch
   bool ok = true;
   for (int k = 0; k + 1 < nl && ok; ++k) {   // down: smooth, residual, restrict
     const TailLev<T>& L = lev[k];
     DIFVM_TAIL_TPR(L.tpr, tail_pre, L);
-    if (!(ok = tail_barrier(P.bar, gen))) break;
+    if (!(ok = tail_barrier(bar))) break;
     DIFVM_TAIL_TPR(L.tpr, tail_resid, L);
-    if (!(ok = tail_barrier(P.bar, gen))) break;
+    if (!(ok = tail_barrier(bar))) break;
     if (L.rl == 1) tail_restrict<T, 1>(L, lev[k + 1].L.n, lev[k + 1].r);
     else tail_restrict<T, 8>(L, lev[k + 1].L.n, lev[k + 1].r);
-    ok = tail_barrier(P.bar, gen);
+    ok = tail_barrier(bar);
   }
   if (ok) {
     tail_coarse<T>(lev[nl - 1], P.Ainv);
-    ok = nl == 1 || tail_barrier(P.bar, gen);
+    ok = nl == 1 || tail_barrier(bar);
   }
   for (int k = nl - 2; k >= 0 && ok; --k) {  // up: corrected sweep, second sweep
     const TailLev<T>& L = lev[k];
     DIFVM_TAIL_TPR(L.tpr, tail_post1, L, (const T*)lev[k + 1].y);
-    if (!(ok = tail_barrier(P.bar, gen))) break;
+    if (!(ok = tail_barrier(bar))) break;
     DIFVM_TAIL_TPR(L.tpr, tail_post2, L);
-    if (k > 0) ok = tail_barrier(P.bar, gen);
+    if (k > 0) ok = tail_barrier(bar);
   }
   if (!ok && threadIdx.x == 0) {
     for (int k = 0; k < P.nst; ++k) {
@@ -1122,7 +1125,7 @@ static uint64_t lev_mat_bytes(const AmgLev& L, uint64_t v) { return (uint64_t)L.
 static uint64_t lev_pre_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 4 * v; }
 static uint64_t lev_resid_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 4 * v; }
 static uint64_t lev_restrict_bytes(const AmgLev& L, int n1, uint64_t v) {
-  return (uint64_t)L.n * (4 + v) + (uint64_t)n1 * v;
+  return (uint64_t)L.n * (4 + v) + (uint64_t)n1 * 3 * v;   // children in; rD1 in, rc and sc out
 }
 static uint64_t lev_post1_bytes(const AmgLev& L, int n1, uint64_t v) {
   return lev_mat_bytes(L, v) + (uint64_t)L.n * (5 * v + 4) + (uint64_t)n1 * v;
@@ -1194,7 +1197,6 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
     }
     k_amg_tail_desc<T><<<1, 32, 0, st>>>(d, nl, (TailLev<T>*)(R.ws + R.Ly.tail));
     DIFVM_TRY(check_launch("amg_tail_desc"));
-    DIFVM_CUDA(cudaMemsetAsync(R.ws + R.Ly.bar, 0, (2 + kBarGroups) * 128, st));
   }
   return DIFVM_OK;
 }
@@ -1255,14 +1257,17 @@ static void amg_tail_launch(const AmgRun<T>& R, const int* done, KState* st, int
 
 template <typename T, int TPR>
 static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, const T* D, const T* rD,
-                       const T* Lv, const T* r, T* y, T* u, T* rc, T* xc, T* out, const KWork& w, int first,
-                       int down, int rl, cudaStream_t s) {
+                       const T* Lv, const T* r, const T* sr, T* y, T* u, T* rc, const T* rD1, T* sc, T* xc,
+                       T* out, const KWork& w, int first, int down, int rl, cudaStream_t s) {
   const int* done = R.seg_done ? R.seg_done : &w.st[0].done;
   const unsigned B = blocks_for((int64_t)L.n * TPR, kAB);
   const uint64_t v = sizeof(T);
   if (down) {
     count_bytes(lev_pre_bytes(L, v) + lev_resid_bytes(L, v) + lev_restrict_bytes(L, L1.n, v));
-    launch_pdl(k_amg_pre<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, done);
+    if (sr)
+      launch_pdl(k_amg_pre<T, TPR, true>, B, kAB, s, L, R.A, D, rD, Lv, r, sr, y, done);
+    else
+      launch_pdl(k_amg_pre<T, TPR, false>, B, kAB, s, L, R.A, D, rD, Lv, r, sr, y, done);
     if (TPR == 1) {
       prof_bytes(DIFVM_PROF_AMG_RESID, lev_resid_bytes(L, v));
       prof_before(DIFVM_PROF_AMG_RESID, s);
@@ -1270,9 +1275,10 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
     launch_pdl(k_amg_resid<T, TPR>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
     if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
     if (rl == 1)
-      launch_pdl(k_amg_restrict<T, 1>, blocks_for(L1.n, kAB), kAB, s, L1.n, L, u, rc, done);
+      launch_pdl(k_amg_restrict<T, 1>, blocks_for(L1.n, kAB), kAB, s, L1.n, L, u, rc, rD1, sc, done);
     else
-      launch_pdl(k_amg_restrict<T, 8>, blocks_for((int64_t)L1.n * 8, kAB), kAB, s, L1.n, L, u, rc, done);
+      launch_pdl(k_amg_restrict<T, 8>, blocks_for((int64_t)L1.n * 8, kAB), kAB, s, L1.n, L, u, rc, rD1, sc,
+                 done);
     count_launch(); count_launch(); count_launch();
     return;
   }
@@ -1329,15 +1335,21 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   T *y = R.at(R.Ly.a[l]), *u = R.at(R.Ly.b[l]);
   const AmgLev& L1 = H->lev[l + 1];
   T* rc = R.at(R.Ly.r[l + 1]);
+  T* sc = R.at(R.Ly.s[l + 1]);
+  const T* rD1 = R.at(R.Ly.rD[l + 1]);
+  const T* sr = fine ? nullptr : R.at(R.Ly.s[l]);   // formed by the restriction into this level
   T* xc = R.at(R.Ly.a[l + 1]);   // written by the next level's last sweep
   const int tpr = H->tpr[l], rl = H->rl[l];
+#define DIFVM_SWEEPS(TPRc) \
+  amg_sweeps<T, TPRc>(R, L, L1, D, rD, Lv, r, sr, y, u, rc, rD1, sc, xc, out, w, first, down, rl, s)
   for (int down = 1; down >= 0; --down) {
-    if (tpr == 1) amg_sweeps<T, 1>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
-    else if (tpr == 2) amg_sweeps<T, 2>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
-    else if (tpr == 4) amg_sweeps<T, 4>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
-    else amg_sweeps<T, 8>(R, L, L1, D, rD, Lv, r, y, u, rc, xc, out, w, first, down, rl, s);
+    if (tpr == 1) DIFVM_SWEEPS(1);
+    else if (tpr == 2) DIFVM_SWEEPS(2);
+    else if (tpr == 4) DIFVM_SWEEPS(4);
+    else DIFVM_SWEEPS(8);
     if (down) amg_vcycle(R, l + 1, rc, xc, w, first, s);
   }
+#undef DIFVM_SWEEPS
 }
 
 // one AMG-preconditioned CG solve of A x = b (x is the initial guess unless
@@ -1417,6 +1429,7 @@ static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws
     return set_error(DIFVM_EINVAL, "workspace of %zu bytes < %zu needed (AMG)", wsbytes, R.Ly.total);
   R.G = amg_grid(m);
   amg_tail_plan(m, H, (int)sizeof(T), R.tail_from, R.tail_grid);
+  if (R.tail_from > 0) DIFVM_CUDA(cudaMemsetAsync(R.ws + R.Ly.bar, 0, sizeof(unsigned), st));
   T* val = R.at(R.Ly.val);
   if (reuse) {
     R.A = Mat<T>{D, m->ell(), val};
