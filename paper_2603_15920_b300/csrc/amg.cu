@@ -563,7 +563,7 @@ __device__ __forceinline__ T lev_row(const Mat<T>& A, const AmgLev& L, const T* 
     if (!ok) return T(0);
     T y = __ldg(A.D + i) * xat<PROL>(x, i, PROL ? __ldg(L.agg + i) : 0);
     if (A.E.W == 4) {
-      const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      const int4 j4 = ell_cols4(A.E, i);
       const int4 g4 = PROL ? __ldg(reinterpret_cast<const int4*>(L.eagg) + i) : make_int4(0, 0, 0, 0);
       T a[4];
       Vec4Load<T>::get(A.val, i, a);
@@ -1857,7 +1857,7 @@ __global__ void __launch_bounds__(kKB) k_fcg_init(Topo t, Mat<float> A, const do
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     double y = (double)A.D[i] * x[i];
     if (MW == 4 && A.E.W == 4) {
-      const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      const int4 j4 = ell_cols4(A.E, i);
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(A.val) + i);
       y = fma((double)a4.x, x[j4.x], y);
       y = fma((double)a4.y, x[j4.y], y);
@@ -1904,7 +1904,7 @@ __global__ void __launch_bounds__(kKB) k_fcg_spmv(Topo t, Mat<float> A, const fl
     const FF pi = pv(i);
     FF y = ff_mul_f(pi, __ldg(A.D + i));
     if (MW == 4 && A.E.W == 4) {
-      const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+      const int4 j4 = ell_cols4(A.E, i);
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(A.val) + i);
       const FF p0 = pv(j4.x), p1 = pv(j4.y), p2 = pv(j4.z), p3 = pv(j4.w);
       y = ff_add(y, ff_mul_f(p0, a4.x));

@@ -249,7 +249,7 @@ __device__ __forceinline__ void spmv_row(const Topo& t, const Mat<T>& A, int i, 
 #pragma unroll
   for (int c = 0; c < NC; ++c) y[c] = (act >> c & 1) ? d * __ldg(x + c * nc + i) : T(0);
   if (MAXW == 4 && A.E.W == 4) {
-    const int4 j4 = __ldg(reinterpret_cast<const int4*>(A.E.col) + i);
+    const int4 j4 = ell_cols4(A.E, i);
     T a[4];
     Vec4Load<T>::get(A.val, i, a);
     const int j[4] = {j4.x, j4.y, j4.z, j4.w};

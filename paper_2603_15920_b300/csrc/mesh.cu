@@ -266,7 +266,7 @@ static void free_mesh(difvm_mesh* m) {
   if (!m) return;
   void* ptrs[] = {m->on,   m->bown, m->cptr, m->cent, m->bkind, m->bpatch, m->Sw64,
                   m->ck64, m->Sw32, m->ck32, m->V64,  m->rV64,  m->C64,    m->Cf64,
-                  m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map,
+                  m->V32,  m->rV32, m->ell_soff, m->ell_col, m->ell_map, m->ell_c16,
                   m->seg_case, m->seg_cb0, m->seg_cs, m->hf_soff, m->hf_nb, m->hf_fid,
                   m->hf_nf, m->hf_sw64, m->hf_sw32, m->hf_cw, m->hf_fb, m->w64, m->w32};
   int cur = -1;
@@ -524,6 +524,19 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload(&m->ell_soff, soff.data(), soff.size()));
   DIFVM_TRY(upload(&m->ell_col, ecol.data(), ecol.size()));
   DIFVM_TRY(upload(&m->ell_map, emap.data(), emap.size()));
+  if (uw == 4 && nc > 0) {
+    std::vector<short4> c16(nc);
+    bool fits = true;
+    for (int i = 0; i < nc && fits; ++i) {
+      int d[4];
+      for (int k = 0; k < 4; ++k) {
+        d[k] = ecol[(size_t)i * 4 + k] - i;
+        fits = fits && d[k] >= -32768 && d[k] <= 32767;
+      }
+      c16[i] = make_short4((short)d[0], (short)d[1], (short)d[2], (short)d[3]);
+    }
+    if (fits) DIFVM_TRY(upload(&m->ell_c16, c16.data(), c16.size()));
+  }
   DIFVM_TRY(upload(&m->hf_soff, hsoff.data(), hsoff.size()));
   DIFVM_TRY(upload(&m->hf_nb, hnb.data(), hnb.size()));
   DIFVM_TRY(upload(&m->hf_fid, hfid.data(), hfid.size()));
