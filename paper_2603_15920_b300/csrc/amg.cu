@@ -49,6 +49,10 @@ constexpr double kAmgScale = 1.9;
 // pre-smoothing, and every kernel that forms it on the fly gets the same number
 __device__ __forceinline__ float amg_x1(float rD, float r) { return __fmul_rn(__fmul_rn((float)kAmgW1, rD), r); }
 __device__ __forceinline__ double amg_x1(double rD, double r) { return __dmul_rn(__dmul_rn(kAmgW1, rD), r); }
+// a prolongated value y + s xc (coarse correction scaled by kAmgScale), one
+// explicit fma, so that a stored and an on-the-fly prolongation agree
+__device__ __forceinline__ float amg_prol(float y, float xc) { return __fmaf_rn((float)kAmgScale, xc, y); }
+__device__ __forceinline__ double amg_prol(double y, double xc) { return __fma_rn(kAmgScale, xc, y); }
 constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 x 32)
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAB = 256;            // threads per block of the AMG kernels
@@ -685,9 +689,10 @@ __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T*
   }
 }
 
-// coarse correction and the first post-smoothing sweep: z = y + s P xc (formed
-// on the fly), out = z + w rD (r - A z)
-template <typename T, int TPR>
+// coarse correction and the first post-smoothing sweep: z = y + s P xc, out =
+// z + w rD (r - A z).  PZ: y already holds z (k_amg_prol ran), a plain sweep;
+// else z is formed on the fly from the per-slot aggregates.
+template <typename T, int TPR, bool PZ>
 __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* D, const T* rD, const T* Lv,
                                                    const T* r, const T* y, const T* xc, T* out,
                                                    const int* done) {
@@ -695,10 +700,26 @@ __global__ void __launch_bounds__(kAB) k_amg_post1(AmgLev L, Mat<T> A, const T* 
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
-  const T w = (T)kAmgW2, sc = (T)kAmgScale;   // first sweep after the correction: w2
-  auto z = [&](int j, int a) { return y[j] + sc * xc[a]; };
-  const T az = lev_row<T, TPR, true>(A, L, D, Lv, i, t, ok, z);
-  if (ok && t == 0) out[i] = z(i, L.agg[i]) + w * rD[i] * (r[i] - az);
+  const T w = (T)kAmgW2;   // first sweep after the correction: w2
+  if (PZ) {
+    auto z = [&](int j) { return y[j]; };
+    const T az = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, z);
+    if (ok && t == 0) out[i] = y[i] + w * rD[i] * (r[i] - az);
+  } else {
+    auto z = [&](int j, int a) { return amg_prol(y[j], xc[a]); };
+    const T az = lev_row<T, TPR, true>(A, L, D, Lv, i, t, ok, z);
+    if (ok && t == 0) out[i] = z(i, L.agg[i]) + w * rD[i] * (r[i] - az);
+  }
+}
+
+// the coarse correction in place, y = y + s P xc (one thread per row), for a
+// large coarse level, whose corrected sweep then gathers one value per column
+template <typename T>
+__global__ void __launch_bounds__(kAB) k_amg_prol(AmgLev L, const T* xc, T* y, const int* done) {
+  pdl_chain();
+  if (*done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.n) y[i] = amg_prol(y[i], xc[__ldg(L.agg + i)]);
 }
 
 // second post-smoothing sweep: v = u + w1 rD (r - A u)
@@ -907,11 +928,11 @@ __device__ void tail_restrict(const TailLev<T>& P, int n1, T* rc) {
 }
 template <typename T, int TPR>
 __device__ void tail_post1(const TailLev<T>& P, const T* xc) {
-  const T w = (T)kAmgW2, sc = (T)kAmgScale;
+  const T w = (T)kAmgW2;
   const Mat<T> A{};
   tail_rows<T, TPR>(P.L.n, [&](int i, int t) {
     const bool ok = i < P.L.n;
-    auto z = [&](int j, int a) { return __ldcg(P.y + j) + sc * __ldcg(xc + a); };
+    auto z = [&](int j, int a) { return amg_prol(__ldcg(P.y + j), __ldcg(xc + a)); };
     const T az = lev_row<T, TPR, true>(A, P.L, P.D, P.Lv, i, t, ok, z);
     if (ok && t == 0) P.u[i] = z(i, P.L.agg[i]) + w * P.rD[i] * (__ldcg(P.r + i) - az);
   });
@@ -1131,6 +1152,10 @@ static uint64_t lev_post1_bytes(const AmgLev& L, int n1, uint64_t v) {
   return lev_mat_bytes(L, v) + (uint64_t)L.n * (5 * v + 4) + (uint64_t)n1 * v;
 }
 static uint64_t lev_post2_bytes(const AmgLev& L, uint64_t v) { return lev_mat_bytes(L, v) + (uint64_t)L.n * 5 * v; }
+// the correction in place: agg and y in, y out, the n1 coarse values once
+static uint64_t lev_prol_bytes(const AmgLev& L, int n1, uint64_t v) {
+  return (uint64_t)L.n * (4 + 2 * v) + (uint64_t)n1 * v;
+}
 
 // default launch shapes: lanes per row by amg_tpr; a restriction into a level
 // of at least kAmgBigLevel/4 rows one thread per aggregate (four children in
@@ -1282,12 +1307,25 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
     count_launch(); count_launch(); count_launch();
     return;
   }
-  count_bytes(lev_post1_bytes(L, L1.n, v) + lev_post2_bytes(L, v));
+  // a large coarse level takes the correction in a kernel of its own (one gather
+  // per row) and then sweeps with one gather per column (~10 us less per V-cycle
+  // on the 327k-row level of the 64^3 mesh); the mesh level and small levels form
+  // it on the fly
+  const bool sep = Lv != nullptr && L.n >= kAmgBigLevel;
+  const uint64_t b1 = sep ? lev_prol_bytes(L, L1.n, v) + lev_post2_bytes(L, v) : lev_post1_bytes(L, L1.n, v);
+  count_bytes(b1 + lev_post2_bytes(L, v));
+  if (sep) {
+    launch_pdl(k_amg_prol<T>, blocks_for(L.n, kAB), kAB, s, L, (const T*)xc, y, done);
+    count_launch();
+  }
   if (TPR == 8) {
-    prof_bytes(DIFVM_PROF_AMG_POST1C, lev_post1_bytes(L, L1.n, v));
+    prof_bytes(DIFVM_PROF_AMG_POST1C, b1);
     prof_before(DIFVM_PROF_AMG_POST1C, s);
   }
-  launch_pdl(k_amg_post1<T, TPR>, B, kAB, s, L, R.A, D, rD, Lv, r, y, xc, u, done);
+  if (sep)
+    launch_pdl(k_amg_post1<T, TPR, true>, B, kAB, s, L, R.A, D, rD, Lv, r, y, xc, u, done);
+  else
+    launch_pdl(k_amg_post1<T, TPR, false>, B, kAB, s, L, R.A, D, rD, Lv, r, y, xc, u, done);
   if (TPR == 8) prof_after(DIFVM_PROF_AMG_POST1C, s);
   if (TPR == 1 && !R.seg_done)
     launch_pdl(k_amg_post2_dot<T>, R.G, kKB, s, L, R.A, rD, r, u, out, w, first);
