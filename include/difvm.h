@@ -109,6 +109,15 @@ enum { DIFVM_PCG = 0, DIFVM_BICGSTAB = 1 };
 enum { DIFVM_PRECOND_NONE = 0, DIFVM_PRECOND_JACOBI = 1, DIFVM_PRECOND_AMG = 2,
        DIFVM_PRECOND_AMG_REUSE = 3, DIFVM_PRECOND_DIC = 4 };
 enum { DIFVM_RENUMBER_RCM = 1u, DIFVM_SORT_FACES = 2u };
+/* Index layouts of the face operators and solvers.  Where the (renumbered)
+ * mesh allows it, a cell's half-face slots are 4-byte words holding both the
+ * other cell and the face id as offsets (|j - i| < 2^14, face id within 2^15 of
+ * the slice's first owned face), and the uniform width-4 ELL of the solvers
+ * also keeps its columns as 16-bit offsets from the row (|j - i| < 2^15); else
+ * the 8-byte (word, face id) slots and 32-bit columns are used.  The flag
+ * DIFVM_WIDE_INDICES selects the wide layouts on any mesh (same results; for
+ * testing both forms on small meshes). */
+enum { DIFVM_WIDE_INDICES = 16u };
 /* Split S_f = Delta_f + k_f of the diffusive flux (Eq. nonortho_flux, Sec. 2.3.2),
  * Delta_f along the cell-to-cell vector d, in bits 2-3 of the mesh flags:
  *   OVERRELAXED (0, the paper's default)  Delta = (|S| / |S^.d^|) d^
@@ -139,7 +148,8 @@ typedef struct difvm_mesh* difvm_mesh_t;
  *     (the result of a case does not depend on the other cases of the batch,
  *     bit for bit).  NULL for a single mesh (the single-mesh solvers).
  *   flags: DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES (internal faces are always
- *     re-oriented so that owner < neighbour) | one DIFVM_NONORTH_* split.
+ *     re-oriented so that owner < neighbour) | one DIFVM_NONORTH_* split |
+ *     DIFVM_WIDE_INDICES (optional).
  *   device: CUDA device ordinal the handle lives on. */
 typedef struct {
   int32_t n_cells, n_internal, n_faces, n_patches;
@@ -206,6 +216,10 @@ difvm_status difvm_mesh_permutation(difvm_mesh_t, int32_t* cell_new_of_old,
                                     int32_t* face_old_of_new, int8_t* face_flip);
 /* Sizes: n_cells, n_internal, n_faces, n_boundary, n_patches, csr_entries. */
 difvm_status difvm_mesh_info(difvm_mesh_t, int64_t out[6]);
+/* Index layouts in use (see DIFVM_WIDE_INDICES), HOST output: out[0] = 1 if
+ * the face operators read the 4-byte compact slot words, out[1] = 1 if the
+ * solvers read 16-bit ELL column offsets (0: the wide forms). */
+difvm_status difvm_mesh_layout(difvm_mesh_t, int32_t out[2]);
 void difvm_mesh_destroy(difvm_mesh_t);
 
 /* Geometry of a polyhedral mesh given by its vertices (the form of an OpenFOAM

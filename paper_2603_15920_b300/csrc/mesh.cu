@@ -296,7 +296,7 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
     return set_error(DIFVM_EINVAL, "bad sizes nc=%d ni=%d nf=%d npatch=%d", nc, ni, nf, np);
   if (!d->owner || (ni > 0 && !d->neighbour) || !d->Sf || !d->Cf || !d->V || !d->C)
     return set_error(DIFVM_EINVAL, "null mesh array");
-  if (d->flags & ~(uint32_t)(DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES | DIFVM_NONORTH_MASK))
+  if (d->flags & ~(uint32_t)(DIFVM_RENUMBER_RCM | DIFVM_SORT_FACES | DIFVM_NONORTH_MASK | DIFVM_WIDE_INDICES))
     return set_error(DIFVM_EINVAL, "unknown mesh flags 0x%x", d->flags);
   if (nb > 0 && (!d->patch_start || !d->patch_size || !d->patch_type))
     return set_error(DIFVM_EINVAL, "boundary faces without patches");
@@ -524,7 +524,8 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
   DIFVM_TRY(upload(&m->ell_soff, soff.data(), soff.size()));
   DIFVM_TRY(upload(&m->ell_col, ecol.data(), ecol.size()));
   DIFVM_TRY(upload(&m->ell_map, emap.data(), emap.size()));
-  if (uw == 4 && nc > 0) {
+  const bool wide = (d->flags & DIFVM_WIDE_INDICES) != 0;
+  if (uw == 4 && nc > 0 && !wide) {
     std::vector<short4> c16(nc);
     bool fits = true;
     for (int i = 0; i < nc && fits; ++i) {
@@ -553,7 +554,7 @@ static difvm_status build(const difvm_mesh_desc* d, difvm_mesh* m) {
       while (f0 < ni && on[f0].x < 32 * sl) ++f0;
       hfb[sl] = f0;
     }
-    bool fits = true;
+    bool fits = !wide;
     for (int i = 0; i < nc && fits; ++i) {
       for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
         const int slot = hsoff[i >> 5] + 32 * (e - cptr[i]) + (i & 31);
@@ -662,6 +663,14 @@ extern "C" difvm_status difvm_mesh_info(difvm_mesh_t m, int64_t out[6]) {
   if (!out) return set_error(DIFVM_EINVAL, "null output");
   out[0] = m->nc; out[1] = m->ni; out[2] = m->nf; out[3] = m->nb; out[4] = m->npatch;
   out[5] = m->nnz;
+  return DIFVM_OK;
+}
+
+extern "C" difvm_status difvm_mesh_layout(difvm_mesh_t m, int32_t out[2]) {
+  DIFVM_TRY(check_mesh(m));
+  if (!out) return set_error(DIFVM_EINVAL, "null output");
+  out[0] = m->hf_cw != nullptr;
+  out[1] = m->ell_c16 != nullptr;
   return DIFVM_OK;
 }
 

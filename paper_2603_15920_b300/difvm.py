@@ -28,6 +28,7 @@ WK_EXACT, WK_FE, WK_BE = 0, 1, 2
 PCG, BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_AMG, PRECOND_AMG_REUSE, PRECOND_DIC = 0, 1, 2, 3, 4
 RENUMBER_RCM, SORT_FACES = 1, 2
+WIDE_INDICES = 16
 # momentum convection of the PISO step: upwind, or second-order upwind by deferred correction
 CONV_UPWIND, CONV_SOU = 0, 1
 # momentum time scheme of the PISO step: backward Euler or Crank-Nicolson
@@ -91,6 +92,7 @@ _SIGS = {
     "difvm_mesh_create": [_vp, _vp],
     "difvm_mesh_permutation": [_vp, _vp, _vp, _vp],
     "difvm_mesh_info": [_vp, _vp],
+    "difvm_mesh_layout": [_vp, _vp],
     "difvm_mesh_autotune": [_vp, _i],
     "difvm_mesh_amg_config": [_vp, _i, _i],
     "difvm_mesh_tuning": [_vp, _vp, _vp, _i, _vp],
@@ -358,6 +360,13 @@ def difvm_mesh_tuning(mesh):
     _check(lib().difvm_mesh_tuning(_mh(mesh), keys, var, cap, C.byref(n)))
     return {(int(keys[k]) >> 8, (int(keys[k]) >> 4) & 15, int(keys[k]) & 15): int(var[k])
             for k in range(min(n.value, cap))}
+
+
+def difvm_mesh_layout(mesh):
+    """Index layouts in use: (compact 4-byte slot words, 16-bit ELL columns)."""
+    out = (C.c_int32 * 2)()
+    _check(lib().difvm_mesh_layout(_mh(mesh), out))
+    return bool(out[0]), bool(out[1])
 
 
 def difvm_mesh_amg_config(mesh, tail_rows=-1, tail_bps=-1):

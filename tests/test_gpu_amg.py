@@ -273,3 +273,31 @@ def test_multigrid_launch_shapes_are_tuned_and_solve_the_same_system():
     ref, _ = O.pcg(om, Dg, Lg, None, b, tol_rel=1e-13, maxit=100000)
     assert nrel(x, ref) < 1e-7 and nrel(x0, ref) < 1e-7
     assert abs(info["iters"] - info0["iters"]) <= 1
+
+
+@pytest.mark.parametrize("prec,refine", [(D.F64, 0), (D.F32, 20)])
+def test_wide_index_layouts_step_bitwise_the_same(prec, refine):
+    # the solvers' 16-bit ELL column offsets (used where the RCM bandwidth allows)
+    # and the 32-bit columns of DIFVM_WIDE_INDICES address the same entries: the
+    # multigrid-CG pressure and BiCGStab momentum solves of a PISO step agree bitwise
+    m, Ub = _cavity(10, 51)
+    dt = torch.float64 if prec == D.F64 else torch.float32
+    outs = []
+    for flags in (D.RENUMBER_RCM | D.SORT_FACES, D.RENUMBER_RCM | D.SORT_FACES | D.WIDE_INDICES):
+        dm = D.Mesh(m, flags=flags)
+        assert D.difvm_mesh_layout(dm) == ((True, True) if not flags & D.WIDE_INDICES else (False, False))
+        D.difvm_mesh_autotune(dm, 0)          # the same launch shapes on both
+        pg = _piso(dm, prec, 3, refine, tol=1e-10)
+        U = torch.zeros((3, dm.nc), dtype=dt, device="cuda")
+        p = torch.zeros(dm.nc, dtype=dt, device="cuda")
+        ub = cuda(dm.to_bnd(Ub), dt)
+        pb = torch.zeros(dm.nb, dtype=dt, device="cuda")
+        phi = D.difvm_flux_from_U(dm, U, ub)
+        info = torch.zeros(D.PISO_INFO_NBYTES, dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            pg.step_graph(U, p, phi, ub, pb, info=info)
+        torch.cuda.synchronize()
+        assert D.decode_piso_info(info)["status"] == D.OK
+        outs.append([dm.from_cells(host(U)), dm.from_cells(host(p))])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)

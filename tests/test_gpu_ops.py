@@ -203,7 +203,7 @@ def test_bad_arguments_raise():
 def test_mesh_create_rejects_unknown_flags():
     m = get("kuhn10")[0]
     with pytest.raises(D.DifvmError):
-        D.Mesh(m, flags=D.RENUMBER_RCM | 16)
+        D.Mesh(m, flags=D.RENUMBER_RCM | 32)
 
 
 def test_mesh_create_rejects_bad_meshes():
@@ -462,3 +462,36 @@ def test_autotuned_variants_agree_and_are_kept():
     assert set(kept) >= set(ops) and all(0 <= v <= 2 for v in kept.values()), kept
     with pytest.raises(D.DifvmError):
         D.difvm_mesh_autotune(dm, 3)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("name", ["kuhn10", "pipe"])
+def test_wide_index_layouts_give_bitwise_the_same_operators(name, dt):
+    # compact 4-byte slot words (other cell and face id as offsets) against the
+    # 8-byte (word, face id) slots that DIFVM_WIDE_INDICES selects (and that large
+    # meshes use): the same faces in the same order, so bitwise the same sums
+    m = get(name)[0]
+    f = mg.random_fields(m, 11)
+    res = []
+    for flags in (D.RENUMBER_RCM | D.SORT_FACES, D.RENUMBER_RCM | D.SORT_FACES | D.WIDE_INDICES):
+        dm = D.Mesh(m, flags=flags)
+        assert D.difvm_mesh_layout(dm)[0] == (not flags & D.WIDE_INDICES)
+        phi, U = cuda(dm.to_cells(f["U"][:1]), dt), cuda(dm.to_cells(f["U"]), dt)
+        phib, Ub = cuda(dm.to_bnd(f["U_b"][:1]), dt), cuda(dm.to_bnd(f["U_b"]), dt)
+        mf = cuda(dm.to_faces(f["m"]), dt)
+        g = D.difvm_grad_gauss(dm, D.BC_ALL_FIXED, phi, phib)
+        rng = np.random.default_rng(5)
+        Dg, L, Uu = (cuda(rng.standard_normal(dm.nc) + 5.0, dt), cuda(rng.standard_normal(dm.ni), dt),
+                     cuda(rng.standard_normal(dm.ni), dt))
+        outs = [g,
+                D.difvm_grad_gauss(dm, D.BC_VELOCITY, U, Ub),
+                D.difvm_grad_gauss(dm, D.BC_PRESSURE, phi, phib),
+                D.difvm_div_flux(dm, D.DIV_UPWIND, D.BC_VELOCITY, mf, U, Ub),
+                D.difvm_div_flux(dm, D.DIV_LINEAR, D.BC_PRESSURE, mf, U, Ub),
+                D.difvm_laplacian(dm, D.BC_ALL_FIXED, 0.3, phi, phib, g),
+                D.difvm_laplacian(dm, D.BC_VELOCITY, 0.3, U, Ub),
+                D.difvm_laplacian_apply(dm, Dg, L, None, phi),
+                D.difvm_laplacian_apply(dm, Dg, L, Uu, U)]
+        res.append([dm.from_cells(o.cpu().numpy()) for o in outs])
+    for k, (a, b) in enumerate(zip(*res)):
+        assert np.array_equal(a, b), k
