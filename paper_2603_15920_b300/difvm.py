@@ -586,6 +586,58 @@ def decode_piso_info(buf):
     return dict(itU=list(s.itU), itp=list(s.itp), status=s.status, Q=list(s.Q), p_out=list(s.p_out))
 
 
+class StepLog:
+    """Per-step metrics of a PISO run as JSON lines, one object per step:
+    the step index (and time, wall milliseconds when given), the BiCGStab
+    iterations of each momentum component and the CG iterations of each
+    pressure corrector, the step status, the outlet flux Q and pressure p_out
+    of each Windkessel outlet and, when the face flux phi is passed, the
+    continuity error of phi: sum over cells of |sum_f sigma_f phi_f|, computed
+    on the device (difvm_div_flux of a unit field with zero-gradient boundary
+    values), absolute and relative to sum_f |phi_f|.  `out` is a path (opened
+    for appending) or a writable text file."""
+
+    def __init__(self, out, mesh=None, n_out=0, n_corr=2):
+        import json as _json
+        self._json = _json
+        self._own = isinstance(out, (str, os.PathLike))
+        self.f = open(out, "a") if self._own else out
+        self.mesh, self.n_out, self.n_corr = mesh, int(n_out), int(n_corr)
+        self._ones = {}
+
+    def continuity(self, phi):
+        """(sum_cells |div phi|, the same relative to sum_f |phi_f|) of a face flux."""
+        key = (phi.dtype, phi.device)
+        if key not in self._ones:
+            self._ones[key] = torch.ones(1, self.mesh.nc, dtype=phi.dtype, device=phi.device)
+        d = difvm_div_flux(self.mesh, DIV_UPWIND, BC_ALL_ZEROGRAD, phi, self._ones[key])
+        tot = torch.stack([d.abs().sum().double(), phi.abs().sum().double()]).cpu()
+        a, b = float(tot[0]), float(tot[1])
+        return a, (a / b if b > 0 else 0.0)
+
+    def log(self, step, info, phi=None, t=None, ms=None):
+        """Write the line of one step (info: the step's PISO info buffer) and return it."""
+        d = decode_piso_info(info)
+        rec = {"step": int(step), "status": int(d["status"]), "itU": d["itU"], "itp": d["itp"][:self.n_corr]}
+        if t is not None:
+            rec["t"] = float(t)
+        if ms is not None:
+            rec["ms"] = float(ms)
+        if self.n_out:
+            rec["Q"] = d["Q"][:self.n_out]
+            rec["p_out"] = d["p_out"][:self.n_out]
+        if phi is not None and self.mesh is not None:
+            rec["continuity_abs"], rec["continuity_rel"] = self.continuity(phi)
+        self.f.write(self._json.dumps(rec) + "\n")
+        self.f.flush()
+        return rec
+
+    def close(self):
+        if self._own and self.f:
+            self.f.close()
+        self.f = None
+
+
 class Piso:
     """difvm_piso_create / difvm_piso_step on one mesh and precision."""
 
