@@ -909,6 +909,9 @@ def run_ours(args):
     same_b = bool(torch.equal(adj["U"], adjb["U"]) and torch.equal(adj["nu"], adjb["nu"]))
     fwd_adj = {"value": fa_ms / fwd_ms, "unit": "time ratio", "steps": K,
                "fwd_ms_per_step": fwd_ms / K, "fwd_adj_ms_per_step": fa_ms / K,
+               "over_headline_graph_step": (fa_ms / K) / ms_local,
+               "over_headline_note": "fwd+adjoint (host-loop forward steps with tapes, then the reverse "
+                                     "sweep) per step over the headline's graph-launched forward step",
                "taping": "every step recorded (tapes resident in HBM)",
                "tape_bytes_per_step": h.tape_bytes(),
                "checkpointed": {"every": CKPT, "value": fc_ms / fwd_ms,
