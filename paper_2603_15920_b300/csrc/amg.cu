@@ -1203,35 +1203,16 @@ static difvm_status amg_setup(const AmgRun<T>& R, const T* D0, const T* L0, cuda
   k_amg_dense_inv<T><<<1, 512, 0, st>>>(Lc, D, Lv, (float*)(R.ws + R.Ly.inv));
   DIFVM_TRY(check_launch("amg_dense_inv"));
   count_bytes((uint64_t)Lc.n * Lc.n * 4 + (uint64_t)Lc.n * v + (uint64_t)Lc.nf * (8 + v));
-  if (R.tail_from > 0) {
-    TailLevs<T> d;
-    const int nl = H->nlev - R.tail_from;
-    for (int k = 0; k < nl; ++k) {
-      const int l = R.tail_from + k;
-      const AmgLev& L = H->lev[l];
-      TailLev<T>& t = d.lev[k];
-      t.L = L;
-      t.D = R.at(R.Ly.D[l]);
-      t.rD = R.at(R.Ly.rD[l]);
-      t.Lv = R.at(R.Ly.E[l]);
-      t.r = R.at(R.Ly.r[l]);
-      t.y = R.at(R.Ly.a[l]);
-      t.u = R.at(R.Ly.b[l]);
-      t.tpr = H->tpr[l];
-      t.rl = H->rl[l];
-    }
-    k_amg_tail_desc<T><<<1, 32, 0, st>>>(d, nl, (TailLev<T>*)(R.ws + R.Ly.tail));
-    DIFVM_TRY(check_launch("amg_tail_desc"));
-  }
   return DIFVM_OK;
 }
 
 // Levels below m->amg_tail_rows rows (and the coarsest solve) run in the fused
 // kernel, with at most m->amg_tail_bps blocks per SM (default 2, at most its
 // occupancy).  Off by default: on the 1.6M-cell Kuhn cavity the per-level
-// kernels, chained by programmatic dependent launch, take 16.0 ms per PISO
-// step against 17.0-19.2 ms with any range of levels fused (barrier and
-// cooperative-launch costs exceed the launch latency they save).
+// kernels, chained by programmatic dependent launch, take 15.6 ms per PISO
+// step against 16.0 ms with levels 3-6 fused and 16.5 ms with levels 2-6 (each
+// phase has a fraction of the threads the per-level kernels keep resident, and
+// the coarse phases are bound by the latency of their dependent loads).
 static void amg_tail_plan(const difvm_mesh* m, const AmgHier* H, int elt, int& from, int& grid) {
   from = 0;
   grid = 0;
@@ -1451,6 +1432,36 @@ __global__ void k_amg_info(const KState* st, difvm_solve_info* info, int refinem
   *info = o;
 }
 
+// the fused kernel's level descriptors (pointers into this workspace and the
+// current launch shapes), written at every solve so that a change of the
+// mesh's configuration or launch shapes between solves is always seen
+template <typename T>
+static difvm_status amg_tail_descs(const AmgRun<T>& R, cudaStream_t st) {
+  const AmgHier* H = R.H;
+  if (R.tail_from > 0) {
+    TailLevs<T> d;
+    const int nl = H->nlev - R.tail_from;
+    for (int k = 0; k < nl; ++k) {
+      const int l = R.tail_from + k;
+      const AmgLev& L = H->lev[l];
+      TailLev<T>& t = d.lev[k];
+      t.L = L;
+      t.D = R.at(R.Ly.D[l]);
+      t.rD = R.at(R.Ly.rD[l]);
+      t.Lv = R.at(R.Ly.E[l]);
+      t.r = R.at(R.Ly.r[l]);
+      t.y = R.at(R.Ly.a[l]);
+      t.u = R.at(R.Ly.b[l]);
+      t.tpr = H->tpr[l];
+      t.rl = H->rl[l];
+    }
+    k_amg_tail_desc<T><<<1, 32, 0, st>>>(d, nl, (TailLev<T>*)(R.ws + R.Ly.tail));
+    DIFVM_TRY(check_launch("amg_tail_desc"));
+  }
+  return DIFVM_OK;
+}
+
+
 // reuse: the ELL values and multigrid operators already in the workspace belong to
 // this same matrix (DIFVM_PRECOND_AMG_REUSE); only the views are set up
 template <typename T>
@@ -1468,6 +1479,7 @@ static difvm_status amg_prepare(difvm_mesh* m, const T* D, const T* Lo, void* ws
   R.G = amg_grid(m);
   amg_tail_plan(m, H, (int)sizeof(T), R.tail_from, R.tail_grid);
   if (R.tail_from > 0) DIFVM_CUDA(cudaMemsetAsync(R.ws + R.Ly.bar, 0, sizeof(unsigned), st));
+  DIFVM_TRY(amg_tail_descs(R, st));
   T* val = R.at(R.Ly.val);
   if (reuse) {
     R.A = Mat<T>{D, m->ell(), val};
