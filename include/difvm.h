@@ -174,8 +174,10 @@ difvm_status difvm_mesh_create(const difvm_mesh_desc* desc, difvm_mesh_t* out);
  * difvm_laplacian, difvm_laplacian_apply) in FP32 on meshes whose rows all have
  * four faces (tetrahedra): the first call of each (operator, scheme or
  * correction, components) on a mesh times the variants -- register budgets
- * for 1, 6 and 8 resident 256-thread blocks per SM -- on that call's own
- * arguments and keeps the fastest for the mesh.  That first call synchronises
+ * for 1, 6 and 8 resident 256-thread blocks per SM; the Gauss gradient's
+ * second variant instead reads its face records by face id -- on that call's own
+ * arguments and keeps the fastest for the mesh (the default unless another is
+ * at least 2% faster).  That first call synchronises
  * with the host; a first call under stream capture launches the default
  * variant and records nothing.  No device memory is allocated.
  * The multigrid preconditioner's launch shapes are tuned once, when its

@@ -625,12 +625,14 @@ template <typename T> static HfGeo<T> fgeo(const difvm_mesh* m) {
 // The F32 kernels of the uniform tetrahedral layout (four slots per row) come
 // in launch variants that differ in the register budget the compiler must meet:
 // variant 0 lets it choose (one block per SM guaranteed), 1 and 2 force six and
-// eight resident 256-thread blocks per SM.  More resident warps hide more of the
+// eight resident 256-thread blocks per SM (the Gauss gradient's variant 1 reads
+// its geometry by face id instead).  More resident warps hide more of the
 // gather latency but may spill; which variant wins depends on the operator,
 // the component count and the mesh.  So the first call of each (operator,
 // components, scheme) on a mesh times every variant on that call's own
 // arguments (a forward operator only writes its output, so running it again
-// changes nothing) and the mesh keeps the fastest; later calls launch it.  A
+// changes nothing) and the mesh keeps the fastest, the default unless another
+// is at least 2% faster; later calls launch it.  A
 // first call under stream capture (no timing possible) launches the default
 // variant without recording a choice.  difvm_mesh_autotune switches timing off
 // (every call then launches the default) or clears the kept choices.
@@ -648,7 +650,7 @@ template <typename F>
 static difvm_status tuned_launch(difvm_mesh* m, uint32_t key, int dflt, cudaStream_t s, F&& launch) {
   int var = tuned_variant(m, key);
   if (var < 0 && m->autotune && !stream_capturing(s)) {
-    constexpr int kReps = 3;
+    constexpr int kReps = 5;
     cudaEvent_t ev[kVariants][2];
     for (int v = 0; v < kVariants; ++v)
       for (int e = 0; e < 2; ++e) DIFVM_CUDA(cudaEventCreate(&ev[v][e]));
@@ -660,18 +662,17 @@ static difvm_status tuned_launch(difvm_mesh* m, uint32_t key, int dflt, cudaStre
       cudaEventRecord(ev[v][1], s);
       st = check_error("autotune");
     }
-    float best = 0.f;
-    for (int v = 0; v < kVariants && st == DIFVM_OK; ++v) {
-      float ms = 0.f;
+    // the default stays unless another variant is at least 2% faster (the
+    // timing of a few launches varies by about that much)
+    float t[kVariants] = {};
+    for (int v = 0; v < kVariants && st == DIFVM_OK; ++v)
       if (cudaEventSynchronize(ev[v][1]) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, ev[v][0], ev[v][1]) != cudaSuccess) {
+          cudaEventElapsedTime(&t[v], ev[v][0], ev[v][1]) != cudaSuccess)
         st = set_error(DIFVM_ECUDA, "autotune timing failed");
-        break;
-      }
-      if (var < 0 || ms < best) {
-        best = ms;
-        var = v;
-      }
+    if (st == DIFVM_OK) {
+      var = dflt;
+      for (int v = 0; v < kVariants; ++v)
+        if (t[v] < 0.98f * t[var]) var = v;
     }
     for (int v = 0; v < kVariants; ++v)
       for (int e = 0; e < 2; ++e) cudaEventDestroy(ev[v][e]);
