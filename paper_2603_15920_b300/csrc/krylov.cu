@@ -203,9 +203,11 @@ __global__ void __launch_bounds__(kKB) k_bicg_init(Topo t, Mat<T> A, int jacobi,
   }
 }
 
-// rho1 = rh.r (kept in s.rz); beta = (rho1/rho)(alpha/omega); p = r + beta (p - omega v)
+// rho1 = rh.r (kept in s.rz); beta = (rho1/rho)(alpha/omega); p = r + beta (p - omega v);
+// with rD (Jacobi) also y = rD p, the preconditioned direction, in the same pass
 template <typename T, int NC>
-__global__ void __launch_bounds__(kKB) k_bicg_p(int nc, const T* r, const T* v, T* p, KWork w) {
+__global__ void __launch_bounds__(kKB) k_bicg_p(int nc, const T* r, const T* v, T* p, const T* rD, T* y,
+                                                KWork w) {
   const unsigned act = active_mask<NC>(w);
   if (!act) return;
   T be[NC], om[NC];   // beta = (rho_new / rho)(alpha / omega), formed once by the last block before
@@ -215,13 +217,17 @@ __global__ void __launch_bounds__(kKB) k_bicg_p(int nc, const T* r, const T* v, 
     be[c] = (T)s.beta;
     om[c] = (T)s.omega;
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const T rd = rD ? rD[i] : T(0);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
       if (act >> c & 1) {
         const int k = c * nc + i;
-        p[k] = r[k] + be[c] * (p[k] - om[c] * v[k]);
+        const T pk = r[k] + be[c] * (p[k] - om[c] * v[k]);
+        p[k] = pk;
+        if (rD) y[k] = pk * rd;
       }
+  }
 }
 
 // v = A (rD p); alpha = rho1 / (rh . v)
@@ -271,24 +277,29 @@ __global__ void k_bicg_scale(int nc, const T* a, const T* rD, T* y, KWork w) {
   }
 }
 
-// s = r - alpha v; test ||s||; if converged x += alpha y
+// s = r - alpha v; test ||s||; if converged x += alpha y.  With rD (Jacobi) also
+// z = rD s, the preconditioned s, in the same pass
 template <typename T, int NC>
-__global__ void __launch_bounds__(kKB) k_bicg_s(int nc, const T* r, const T* v, T* s_, KWork w) {
+__global__ void __launch_bounds__(kKB) k_bicg_s(int nc, const T* r, const T* v, T* s_, const T* rD, T* z,
+                                                KWork w) {
   const unsigned act = active_mask<NC>(w);
   if (!act) return;
   T al[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) al[c] = (T)w.st[c].alpha;
   DotAcc<T> ss[NC];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const T rd = rD ? rD[i] : T(0);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
       if (act >> c & 1) {
         const int k = c * nc + i;
         const T si = r[k] - al[c] * v[k];
         s_[k] = si;
+        if (rD) z[k] = si * rd;
         ss[c].add(si, si);
       }
+  }
   typename DotAcc<T>::part_t vv[NC];
   double tot[NC];
 #pragma unroll
@@ -595,7 +606,7 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     const uint64_t mat = (uint64_t)m->ni * (8 + 2 * vb) + ncu * vb;
     const bool dilu = o->precond == DIFVM_PRECOND_DIC;
     const uint64_t prec_bytes = dilu ? 2 * ((uint64_t)m->ni * (8 + vb) + ncu * vb + 2 * nq * ncu * vb)
-                                     : ncu * vb + 2 * nq * ncu * vb;
+                                     : ncu * vb + nq * ncu * vb;   // rD in, the scaled vector out
     const uint64_t it_bytes = 4 * nq * ncu * vb + 2 * prec_bytes + 2 * (mat + 3 * nq * ncu * vb) +
                               3 * nq * ncu * vb + 8 * nq * ncu * vb;
     if (dilu) DIFVM_TRY(ilu_factor<T>(m, A.D, Lraw, Uraw, extra, w.st, NC, st));
@@ -605,15 +616,16 @@ static difvm_status solve_nc(difvm_mesh_t m, const difvm_solve_opts* o, Mat<T> A
     };
     DIFVM_TRY(run([&](cudaStream_t s) {
       count_bytes(it_bytes);
-      k_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, w);
-      precond(p, y, s);
+      // Jacobi: the scaling by rD rides in the p and s kernels
+      k_bicg_p<T, NC><<<G, kKB, 0, s>>>(nc, r, v, p, dilu ? nullptr : rD, y, w);
+      if (dilu) precond(p, y, s);
       k_bicg_spmv1<T, NC, MW><<<G1, kKB, 0, s>>>(t, A, rh, y, v, w);
-      k_bicg_s<T, NC><<<G, kKB, 0, s>>>(nc, r, v, s_, w);
+      k_bicg_s<T, NC><<<G, kKB, 0, s>>>(nc, r, v, s_, dilu ? nullptr : rD, z, w);
       k_bicg_sfinish<T, NC><<<G, kKB, 0, s>>>(nc, y, x, w);
-      precond(s_, z, s);
+      if (dilu) precond(s_, z, s);
       k_bicg_spmv2<T, NC, MW><<<G2, kKB, 0, s>>>(t, A, z, s_, tv, w);
       k_bicg_update<T, NC><<<Gu, kKB, 0, s>>>(nc, y, z, s_, tv, rh, x, r, w);
-      for (int q = 0; q < 8; ++q) count_launch();
+      for (int q = 0; q < 6; ++q) count_launch();
     }));
   } else {
     return set_error(DIFVM_EINVAL, "unknown Krylov method %d", o->method);
