@@ -75,6 +75,7 @@ struct AmgLev {
   const int* agg;                     // [n] cell -> next-level cell
   const int* eagg;                    // [slots of the level's ELL] agg of the slot's column
   const int *ch_ptr, *ch_idx;         // next-level cell -> its cells
+  const int* cpos;                    // [n] position of the cell in ch_idx (the inverse map)
   const int *ci_ptr, *ci_idx;         // next-level cell -> faces inside it
   const int *cf_ptr, *cf_idx;         // next-level face -> faces mapped to it
 };
@@ -319,6 +320,9 @@ difvm_status build_hier(difvm_mesh* m, AmgHier* H) {
       DIFVM_TRY(upload_vec(H, &L.eagg, eagg));
       DIFVM_TRY(upload_vec(H, &L.ch_ptr, chp));
       DIFVM_TRY(upload_vec(H, &L.ch_idx, chi));
+      std::vector<int> cpos(g.n);
+      for (size_t c = 0; c < chi.size(); ++c) cpos[chi[c]] = (int)c;
+      DIFVM_TRY(upload_vec(H, &L.cpos, cpos));
       DIFVM_TRY(upload_vec(H, &L.ci_ptr, cip));
       DIFVM_TRY(upload_vec(H, &L.ci_idx, cii));
       DIFVM_TRY(upload_vec(H, &L.cf_ptr, cfp));
@@ -642,7 +646,9 @@ __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D,
   if (ok && t == 0) y[i] = x1(i) + w2 * rD[i] * (r[i] - ax);
 }
 
-// residual after pre-smoothing: res = r - A y
+// residual after pre-smoothing: res = r - A y, stored in child order (row i at
+// cpos[i]) so that the restriction sums each aggregate's children from one
+// contiguous range
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* D, const T* Lv, const T* r,
                                                    const T* y, T* res, const int* done) {
@@ -650,9 +656,10 @@ __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* 
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
+  const int pos = ok && t == 0 ? __ldg(L.cpos + i) : 0;
   auto xy = [&](int j) { return y[j]; };
   const T ay = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, xy);
-  if (ok && t == 0) res[i] = r[i] - ay;
+  if (ok && t == 0) res[pos] = r[i] - ay;
 }
 
 // restriction: rc_K = sum of res over the cells of K, and sc_K = w1 rD_K rc_K
@@ -666,20 +673,19 @@ __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T*
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, K = g / RL, t = g % RL;
   T s = T(0);
-  if (K < n1) {
+  if (K < n1) {   // res is in child order: the children of K are res[ch_ptr[K] .. ch_ptr[K+1])
     const int c1 = L.ch_ptr[K + 1];
     int c = L.ch_ptr[K] + t;
     if (RL == 1) {
       for (; c + 4 <= c1; c += 4) {
-        const int i0 = L.ch_idx[c], i1 = L.ch_idx[c + 1], i2 = L.ch_idx[c + 2], i3 = L.ch_idx[c + 3];
-        const T r0 = res[i0], r1 = res[i1], r2 = res[i2], r3 = res[i3];
+        const T r0 = res[c], r1 = res[c + 1], r2 = res[c + 2], r3 = res[c + 3];
         s += r0;
         s += r1;
         s += r2;
         s += r3;
       }
     }
-    for (; c < c1; c += RL) s += res[L.ch_idx[c]];
+    for (; c < c1; c += RL) s += res[c];
   }
 #pragma unroll
   for (int d = RL / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
