@@ -57,6 +57,10 @@ constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAB = 256;            // threads per block of the AMG kernels
 constexpr int kAmgBigLevel = 100000;   // from this size a level's sweeps are bandwidth-bound
+// levels of at most this many rows store their residual in child order (its
+// scattered stores stay in L2): 64^3 cavity 14.90 -> 14.75 ms per step; with the
+// 12.6M-row mesh level of a 128^3 cavity or a 15.8M-row batch it was slower
+constexpr int kAmgChildOrderRows = 4 << 20;
 
 // One level as the kernels see it.  Level 0 is the mesh (its SpMV uses the
 // sliced ELL); on coarser levels `on` / `cptr` / `cent` hold the level's own
@@ -646,17 +650,18 @@ __global__ void __launch_bounds__(kAB) k_amg_pre(AmgLev L, Mat<T> A, const T* D,
   if (ok && t == 0) y[i] = x1(i) + w2 * rD[i] * (r[i] - ax);
 }
 
-// residual after pre-smoothing: res = r - A y, stored in child order (row i at
-// cpos[i]) so that the restriction sums each aggregate's children from one
-// contiguous range
-template <typename T, int TPR>
+// residual after pre-smoothing: res = r - A y.  CO: stored in child order (row
+// i at cpos[i]) so that the restriction sums each aggregate's children from one
+// contiguous range; the scattered stores pay off while the level's residual
+// stays in L2 (kAmgChildOrderRows)
+template <typename T, int TPR, bool CO>
 __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* D, const T* Lv, const T* r,
                                                    const T* y, T* res, const int* done) {
   pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, i = g / TPR, t = g % TPR;
   const bool ok = i < L.n;
-  const int pos = ok && t == 0 ? __ldg(L.cpos + i) : 0;
+  const int pos = CO ? (ok && t == 0 ? __ldg(L.cpos + i) : 0) : i;
   auto xy = [&](int j) { return y[j]; };
   const T ay = lev_row<T, TPR>(A, L, D, Lv, i, t, ok, xy);
   if (ok && t == 0) res[pos] = r[i] - ay;
@@ -666,26 +671,27 @@ __global__ void __launch_bounds__(kAB) k_amg_resid(AmgLev L, Mat<T> A, const T* 
 // (the coarse level's first Jacobi iterate, for its pre-smoothing).  RL == 1:
 // one thread per K, four children in flight; RL > 1: RL lanes per K, each
 // summing its children in ascending order, then a fixed xor tree.
-template <typename T, int RL>
+template <typename T, int RL, bool CO>
 __global__ void __launch_bounds__(kAB) k_amg_restrict(int n1, AmgLev L, const T* res, T* rc, const T* rD1,
                                                       T* sc, const int* done) {
   pdl_chain();
   if (*done) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x, K = g / RL, t = g % RL;
   T s = T(0);
-  if (K < n1) {   // res is in child order: the children of K are res[ch_ptr[K] .. ch_ptr[K+1])
+  if (K < n1) {   // CO: res in child order, the children of K are res[ch_ptr[K] .. ch_ptr[K+1])
+    auto at = [&](int c) { return CO ? res[c] : res[L.ch_idx[c]]; };
     const int c1 = L.ch_ptr[K + 1];
     int c = L.ch_ptr[K] + t;
     if (RL == 1) {
       for (; c + 4 <= c1; c += 4) {
-        const T r0 = res[c], r1 = res[c + 1], r2 = res[c + 2], r3 = res[c + 3];
+        const T r0 = at(c), r1 = at(c + 1), r2 = at(c + 2), r3 = at(c + 3);
         s += r0;
         s += r1;
         s += r2;
         s += r3;
       }
     }
-    for (; c < c1; c += RL) s += res[c];
+    for (; c < c1; c += RL) s += at(c);
   }
 #pragma unroll
   for (int d = RL / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
@@ -1284,13 +1290,17 @@ static void amg_sweeps(const AmgRun<T>& R, const AmgLev& L, const AmgLev& L1, co
       prof_bytes(DIFVM_PROF_AMG_RESID, lev_resid_bytes(L, v));
       prof_before(DIFVM_PROF_AMG_RESID, s);
     }
-    launch_pdl(k_amg_resid<T, TPR>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
-    if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
-    if (rl == 1)
-      launch_pdl(k_amg_restrict<T, 1>, blocks_for(L1.n, kAB), kAB, s, L1.n, L, u, rc, rD1, sc, done);
+    const bool co = L.n <= kAmgChildOrderRows;
+    if (co)
+      launch_pdl(k_amg_resid<T, TPR, true>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
     else
-      launch_pdl(k_amg_restrict<T, 8>, blocks_for((int64_t)L1.n * 8, kAB), kAB, s, L1.n, L, u, rc, rD1, sc,
-                 done);
+      launch_pdl(k_amg_resid<T, TPR, false>, B, kAB, s, L, R.A, D, Lv, r, y, u, done);
+    if (TPR == 1) prof_after(DIFVM_PROF_AMG_RESID, s);
+    const unsigned B1 = blocks_for(L1.n, kAB), B8 = blocks_for((int64_t)L1.n * 8, kAB);
+    if (rl == 1 && co) launch_pdl(k_amg_restrict<T, 1, true>, B1, kAB, s, L1.n, L, u, rc, rD1, sc, done);
+    else if (rl == 1) launch_pdl(k_amg_restrict<T, 1, false>, B1, kAB, s, L1.n, L, u, rc, rD1, sc, done);
+    else if (co) launch_pdl(k_amg_restrict<T, 8, true>, B8, kAB, s, L1.n, L, u, rc, rD1, sc, done);
+    else launch_pdl(k_amg_restrict<T, 8, false>, B8, kAB, s, L1.n, L, u, rc, rD1, sc, done);
     count_launch(); count_launch(); count_launch();
     return;
   }
