@@ -35,8 +35,11 @@
  * Parity pins: see tests/test_oracle_*.py (closed forms, invariants, dense
  * solves, the manufactured Poisson solution of Sec. 3.1.1; the adjoint of a
  * PISO step against central differences of the forward step).
- * Parity unpinned: the interpolation weight on non-uniform meshes (w_f above
- * is a reading; every choice gives 0.5 on the uniform hex meshes that pin it).
+ * The interpolation weight w_f is a reading (the paper says only "linear
+ * interpolation"); its computation is pinned by its defining property (the
+ * interpolated value of a linear field is the field where the segment C_O-C_N
+ * pierces the face plane, on jittered tetrahedra) and by w = 1/2 on uniform
+ * hexes.  What stays open is the reading itself, not its implementation.
  *
  * Multi-core build (compiled with -fopenmp; only the all-cores CPU baseline
  * uses it): the Krylov vector loops run on all threads, the LDU apply visits
