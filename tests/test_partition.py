@@ -160,3 +160,36 @@ def test_two_gloo_ranks_match_the_single_domain_bitwise():
         assert np.array_equal(got["apply"], y[:, got["owned"]])
         assert np.array_equal(got["dot"], dot_ref(torch.as_tensor(xg), torch.as_tensor(xg)).numpy())
         assert np.array_equal(got["cg"], x_ref[got["owned"]].numpy())
+
+
+def test_three_gloo_ranks_exchange_and_apply_bitwise():
+    # a middle slab has two neighbour ranks; the halo exchange and the partitioned
+    # apply stay bitwise (only the FP64 sums over three ranks depend on the
+    # reduction order, so the dot products and CG are checked to rounding)
+    world, port = 3, _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+        res = dict(out)
+    m = _mesh()
+    om, Dg, L = _system(m)
+    part = P.partition_cells(m, world)
+    subs = P.build_subdomains(m, part)
+    assert max(len(s.recv) for s in subs) == 2
+    owned = [np.flatnonzero(part == r) for r in range(world)]
+    xg = np.random.default_rng(5).normal(size=(2, m.n_cells))
+    y = O.ldu_apply(om, Dg, L, None, xg)
+    dot = (xg * xg).sum(axis=-1)
+
+    def dot_ref(a, c):
+        return sum((a[..., o].double() * c[..., o].double()).sum(dim=-1) for o in owned)
+    x_ref = _cg(lambda v: torch.as_tensor(O.ldu_apply(om, Dg, L, None, v.numpy()[None])[0]), dot_ref,
+                torch.as_tensor(Dg), torch.as_tensor(np.random.default_rng(6).normal(size=m.n_cells)), 10)
+    for r in range(world):
+        got = res[r]
+        assert got["halo"]
+        assert np.array_equal(got["apply"], y[:, got["owned"]])
+        np.testing.assert_allclose(got["dot"], dot, rtol=1e-14)
+        np.testing.assert_allclose(got["cg"], x_ref[got["owned"]].numpy(), rtol=1e-10,
+                                   atol=1e-12 * float(x_ref.abs().max()))
