@@ -56,6 +56,7 @@ __device__ __forceinline__ double amg_prol(double y, double xc) { return __fma_r
 constexpr int kAmgCoarsest = 192;   // coarsen until at most this many cells (6 x 32)
 constexpr int kAmgMaxLevels = 16;
 constexpr int kAB = 256;            // threads per block of the AMG kernels
+constexpr int kAmgCoarseTB = 256;   // threads per block of the coarsest solve (8 rows a block)
 constexpr int kAmgBigLevel = 100000;   // from this size a level's sweeps are bandwidth-bound
 // levels of at most this many rows store their residual in child order (its
 // scattered stores stay in L2): 64^3 cavity 14.90 -> 14.75 ms per step; with the
@@ -785,19 +786,21 @@ __global__ void __launch_bounds__(kKB) k_apcg_rz(int nc, const T* r, const T* z,
   s.rz = tot[0];
 }
 
-// coarsest level: x = A^{-1} r (dense inverse, one block)
-// one warp per row (32 warps): each lane's at most kAmgCoarsest/32 entries of
-// the row are loaded together, then a shuffle tree sums the lanes in a fixed order
+// coarsest level: x = A^{-1} r (dense inverse), one warp per row, eight rows a
+// block: each block stages r in shared memory, each lane's at most
+// kAmgCoarsest/32 entries of its row are loaded together, then a shuffle tree
+// sums the lanes in a fixed order
 template <typename T>
-__global__ void __launch_bounds__(1024) k_amg_coarse(int n, const float* Ainv, const T* r, T* x, const int* done) {
+__global__ void __launch_bounds__(kAmgCoarseTB) k_amg_coarse(int n, const float* Ainv, const T* r, T* x,
+                                                            const int* done) {
   pdl_chain();
   if (*done) return;
   constexpr int NJ = kAmgCoarsest / 32;
   __shared__ float rs[kAmgCoarsest];
   for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (float)r[j];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < n; i += nw) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = blockIdx.x * nw + (threadIdx.x >> 5); i < n; i += gridDim.x * nw) {
     float a[NJ];
 #pragma unroll
     for (int q = 0; q < NJ; ++q) {
@@ -1359,7 +1362,9 @@ static void amg_vcycle(const AmgRun<T>& R, int l, const T* r, T* out, const KWor
   const T* Lv = fine ? nullptr : R.at(R.Ly.E[l]);   // row-entry values of a coarse level
   if (l == H->nlev - 1) {
     count_bytes((uint64_t)L.n * L.n * 4 + 2 * (uint64_t)L.n * sizeof(T));
-    launch_pdl(k_amg_coarse<T>, 1, 1024, s, L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
+    // one warp per row, spread over blocks so that every row is one round of loads
+    launch_pdl(k_amg_coarse<T>, std::max(1, (L.n + kAmgCoarseTB / 32 - 1) / (kAmgCoarseTB / 32)), kAmgCoarseTB, s,
+               L.n, (const float*)(R.ws + R.Ly.inv), r, out, done);
     count_launch();
     if (l == 0 && !R.seg_done) {   // a single level: the CG's r.z reduction runs on its own
       k_apcg_rz<T><<<R.G, kKB, 0, s>>>(L.n, r, out, w, first);
